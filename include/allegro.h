@@ -1,0 +1,187 @@
+/*
+ * allegro.h - C ABI of the GB300 Allegro energy/force library.
+ *
+ * The library evaluates the Allegro-shaped interatomic potential of
+ * "Allegro-Legato" (arXiv 2303.08169) on one GPU: periodic cell-list
+ * neighbour search, per-pair Bessel x envelope radial basis and real
+ * spherical harmonics, channel-wise Clebsch-Gordan tensor products with
+ * per-atom neighbour sums, latent and energy per-pair MLPs, the energy
+ * E = sum_ij E_ij (Sec. 2.1) and the forces f_i = -dE/dr_i (Eq. 1) from
+ * hand-written adjoint kernels, plus microcanonical velocity-Verlet steps
+ * (Sec. 3.2) with the per-step count of force components above 5 sigma
+ * (Fig. 1 caption).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: ALLEGRO_OK (0) or one of the
+ *    ALLEGRO_E_* codes below; allegro_last_error() then holds a message.
+ *    No C++ exception crosses this boundary and no call aborts the process.
+ *  - Units: Angstrom, eV, fs, amu.  Forces in eV/Angstrom.
+ *  - Arrays marked "host or device" may be either: the library inspects the
+ *    pointer (cudaPointerGetAttributes) and copies host data through its own
+ *    stream.  Arrays marked "device" must be device memory of the current
+ *    GPU.  The caller owns every array it passes; the library never keeps a
+ *    caller pointer after a call returns.
+ *  - Row-major layouts: positions/velocities/forces are N x 3 (x, y, z per
+ *    atom).  cell is a host 3 x 3 matrix of lattice vectors (rows); only
+ *    orthorhombic (diagonal) cells are accepted.
+ *  - All GPU work is enqueued on the context's stream (allegro_set_stream,
+ *    default: the legacy default stream); calls that return host values
+ *    synchronise that stream before returning.
+ *  - One context per host thread; contexts are independent.
+ */
+#ifndef ALLEGRO_GB300_H
+#define ALLEGRO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ALLEGRO_OK                 0
+#define ALLEGRO_E_INVALID_ARG      1  /* null pointer, negative size, bad enum   */
+#define ALLEGRO_E_MISMATCH         2  /* create() arguments disagree with blob   */
+#define ALLEGRO_E_CUTOFF_TOO_LARGE 3  /* r_cut needs images beyond |n_a| <= 2    */
+#define ALLEGRO_E_NONORTHO_CELL    4  /* cell has off-diagonal entries or L <= 0 */
+#define ALLEGRO_E_PAIR_OVERFLOW    5  /* pair capacity exceeded (context grows;  */
+                                      /* retry the call)                         */
+#define ALLEGRO_E_OOM              6  /* device allocation failed                */
+#define ALLEGRO_E_NONFINITE        7  /* non-finite position or force            */
+#define ALLEGRO_E_TIMEOUT          8  /* a bounded device wait gave up           */
+#define ALLEGRO_E_CUDA             9  /* any other CUDA runtime error            */
+#define ALLEGRO_E_UNSUPPORTED     10  /* model shape outside the compiled set    */
+#define ALLEGRO_E_BLOB            11  /* malformed weights blob                  */
+
+#define ALLEGRO_FP32 0   /* every per-pair GEMM in FP32 on CUDA cores           */
+#define ALLEGRO_BF16 1   /* per-pair GEMMs in BF16 with FP32 accumulation       */
+
+typedef struct allegro_ctx allegro_ctx;
+
+/* Library version string, static storage. */
+const char* allegro_version(void);
+
+/*
+ * Create a context from an "ALW1" weights blob (layout documented in
+ * synth/weights.py: header, per-species sigma_Z/mu_Z, named FP64 tensors).
+ *  weights_blob, blob_bytes : host bytes; copied, the caller keeps ownership.
+ *  species_mass             : host, n_species masses in amu (index = type id);
+ *                             used only by the MD entry points.
+ *  r_cut, l_max, n_layers   : must equal the blob header (else E_MISMATCH).
+ * Supported model shapes (E_UNSUPPORTED otherwise): two species, 8 Bessel
+ * functions, envelope p = 6, two latent hidden widths D = D, one energy
+ * hidden width, and (l_max, C, D, E) in {(1, 8, 32, 32), (2, 16, 128, 32)}.
+ * The paper defines only the pairwise-energy decomposition and equivariance
+ * (Sec. 2.1); the layer structure follows the Allegro reading stated in the
+ * oracle package.
+ */
+int allegro_create(const void* weights_blob, size_t blob_bytes,
+                   const double* species_mass, int32_t n_species,
+                   double r_cut, int32_t l_max, int32_t n_layers,
+                   allegro_ctx** out);
+
+/* Free a context and all device memory it owns.  NULL is ignored. */
+void allegro_destroy(allegro_ctx* ctx);
+
+/* Enqueue all later work on this cudaStream_t (NULL = legacy stream). */
+int allegro_set_stream(allegro_ctx* ctx, void* cuda_stream);
+
+/* Message of the last failing call on this context (static if ctx NULL). */
+const char* allegro_last_error(const allegro_ctx* ctx);
+
+/*
+ * Build the periodic neighbour list (Sec. 2.4 linked-list cells + adjacency
+ * list) for n_atoms positions and keep it in the context.
+ *  positions : host or device, N x 3 FP64.
+ *  cell      : host 3 x 3 FP64 (orthorhombic).
+ *  n_pairs   : host out, number of ordered pairs (i, j, n).
+ * A pair is (i, j, n) with n in Z^3, (j, n) != (i, 0), and
+ * d^2 = (Dx^2 + Dy^2) + Dz^2 < r_cut^2 in FP64 without fused multiply-add,
+ * where D = (w_j - w_i) + n L and w are positions wrapped into [0, L).
+ * Every periodic image counts, so r_cut may exceed L/2 (up to 2 L).
+ */
+int allegro_build_neighbors(allegro_ctx* ctx, int64_t n_atoms,
+                            const double* positions, const double* cell,
+                            int64_t* n_pairs);
+
+/*
+ * Copy the last neighbour list out, in CSR form sorted by (i, j, n_x, n_y,
+ * n_z).  All outputs device, caller-allocated; any may be NULL.
+ *  row_ptr : N + 1 int32;  col : P int32 (j);  img : P x 3 int8 (n);
+ *  rev     : P int32, index of the reverse pair (j, i, -n).
+ */
+int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col,
+                          int8_t* img, int32_t* rev);
+
+/*
+ * Energy and forces (Sec. 2.1, Eq. 1): rebuilds the neighbour list, runs the
+ * forward pair passes, the energy reduction (FP64) and the hand-written
+ * adjoint passes.
+ *  positions    : host or device, N x 3 FP64.
+ *  species      : host or device, N int32 in [0, n_species).
+ *  cell         : host 3 x 3 FP64 (orthorhombic).
+ *  energy_out   : host, total energy E (FP64).
+ *  forces_out   : host or device, N x 3 FP32 = -dE/dr (may be NULL).
+ *  atom_energy  : host or device, N FP64 per-atom energies E_i (may be NULL).
+ *  precision    : ALLEGRO_FP32 or ALLEGRO_BF16.
+ * On ALLEGRO_E_PAIR_OVERFLOW nothing is written; the context has grown and
+ * the call may simply be repeated.
+ */
+int allegro_energy_forces(allegro_ctx* ctx, int64_t n_atoms,
+                          const double* positions, const int32_t* species,
+                          const double* cell, double* energy_out,
+                          float* forces_out, double* atom_energy,
+                          int32_t precision);
+
+/*
+ * Count force components above threshold * sigma, sigma^2 = mean of F_ia^2
+ * over all 3N components (Fig. 1 caption, ">5 sigma" with threshold 5).
+ *  forces : host or device, N x 3 FP32.   count_out : host.
+ */
+int allegro_outlier_count(allegro_ctx* ctx, int64_t n_atoms,
+                          const float* forces, double threshold,
+                          int64_t* count_out);
+
+/*
+ * Load the MD state (copied into the context).
+ *  positions, velocities : host or device, N x 3 FP64 (A, A/fs).
+ *  species               : host or device, N int32.
+ *  cell                  : host 3 x 3 FP64 (orthorhombic).
+ * Computes the initial forces with the current precision
+ * (allegro_set_md_precision, default ALLEGRO_FP32).
+ */
+int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions,
+                    const double* velocities, const int32_t* species,
+                    const double* cell);
+
+/* Precision used by allegro_md_init / allegro_md_step_nve. */
+int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision);
+
+/*
+ * n_steps microcanonical velocity-Verlet steps of dt_fs each (Eq. 1,
+ * Sec. 3.2): v += dt/2 a; r += dt v; wrap; F = F(r); v += dt/2 a with
+ * a = kappa F / m, kappa = 9.648533e-3 A/fs^2 per eV/(A amu), in FP64.
+ * After each step the step's outlier count (> 5 sigma) and its energies are
+ * recorded.  One step is captured once as a CUDA graph and replayed.
+ *  outlier_counts : host or device, n_steps int64 (may be NULL).
+ *  energies       : host or device, n_steps x 3 FP64 (E_pot, E_kin, E_tot),
+ *                   may be NULL.
+ * On ALLEGRO_E_PAIR_OVERFLOW the state is rolled back to the start of the
+ * call, the capacity is grown, and the call may be repeated.
+ */
+int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps,
+                        int64_t* outlier_counts, double* energies);
+
+/*
+ * Copy the MD state out.  positions, velocities: host or device N x 3 FP64
+ * (positions wrapped into the cell); forces: host or device N x 3 FP32;
+ * step: host.  Any pointer may be NULL.
+ */
+int allegro_md_get_state(allegro_ctx* ctx, double* positions,
+                         double* velocities, float* forces, int64_t* step);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALLEGRO_GB300_H */

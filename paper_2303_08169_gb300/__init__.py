@@ -1,0 +1,174 @@
+"""Python binding of the GB300 Allegro library (include/allegro.h).
+
+Argument marshalling only: every function forwards numpy arrays or torch
+tensors (host or CUDA) as raw pointers to the C ABI of the same name.  All
+computation runs in the library's CUDA kernels; there is no Python or CPU
+fallback, and importing the functions fails loudly when the library has not
+been built (see build_lib.build()).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build_lib import LIB, build
+
+ALLEGRO_FP32 = 0
+ALLEGRO_BF16 = 1
+
+_STATUS = {
+    0: "OK", 1: "E_INVALID_ARG", 2: "E_MISMATCH", 3: "E_CUTOFF_TOO_LARGE",
+    4: "E_NONORTHO_CELL", 5: "E_PAIR_OVERFLOW", 6: "E_OOM", 7: "E_NONFINITE",
+    8: "E_TIMEOUT", 9: "E_CUDA", 10: "E_UNSUPPORTED", 11: "E_BLOB",
+}
+
+EXPORTED = [
+    "allegro_version", "allegro_create", "allegro_destroy", "allegro_set_stream",
+    "allegro_last_error", "allegro_build_neighbors", "allegro_get_neighbors",
+    "allegro_energy_forces", "allegro_outlier_count", "allegro_md_init",
+    "allegro_set_md_precision", "allegro_md_step_nve", "allegro_md_get_state",
+]
+
+
+class AllegroError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_vp, _i32, _i64, _f64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"{LIB} is missing: build it with paper_2303_08169_gb300.build()")
+    L = ctypes.CDLL(LIB)
+    sig = {
+        "allegro_version": ([], ctypes.c_char_p),
+        "allegro_create": ([_vp, _sz, _vp, _i32, _f64, _i32, _i32, ctypes.POINTER(_vp)], ctypes.c_int),
+        "allegro_destroy": ([_vp], None),
+        "allegro_set_stream": ([_vp, _vp], ctypes.c_int),
+        "allegro_last_error": ([_vp], ctypes.c_char_p),
+        "allegro_build_neighbors": ([_vp, _i64, _vp, _vp, ctypes.POINTER(_i64)], ctypes.c_int),
+        "allegro_get_neighbors": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "allegro_energy_forces": ([_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_f64), _vp, _vp, _i32], ctypes.c_int),
+        "allegro_outlier_count": ([_vp, _i64, _vp, _f64, ctypes.POINTER(_i64)], ctypes.c_int),
+        "allegro_md_init": ([_vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "allegro_set_md_precision": ([_vp, _i32], ctypes.c_int),
+        "allegro_md_step_nve": ([_vp, _f64, _i32, _vp, _vp], ctypes.c_int),
+        "allegro_md_get_state": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_i64)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Raw address of a numpy array / torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _host(x, dtype):
+    return None if x is None else np.ascontiguousarray(x, dtype=dtype)
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = lib().allegro_last_error(ctx)
+        raise AllegroError(rc, msg.decode() if msg else "")
+
+
+def allegro_version():
+    return lib().allegro_version().decode()
+
+
+def allegro_create(blob, species_mass, r_cut, l_max, n_layers):
+    blob = bytes(blob)
+    mass = _host(species_mass, np.float64)
+    out = _vp()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    rc = lib().allegro_create(ctypes.cast(buf, _vp), len(blob), _ptr(mass), len(mass), float(r_cut),
+                              int(l_max), int(n_layers), ctypes.byref(out))
+    _check(None, rc)
+    return out
+
+
+def allegro_destroy(ctx):
+    lib().allegro_destroy(ctx)
+
+
+def allegro_set_stream(ctx, stream):
+    """stream: torch.cuda.Stream, an integer cudaStream_t, or None."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(ctx, lib().allegro_set_stream(ctx, handle))
+
+
+def allegro_build_neighbors(ctx, positions, cell):
+    n = int(positions.shape[0])
+    cell = _host(cell, np.float64)
+    np_ = _i64()
+    _check(ctx, lib().allegro_build_neighbors(ctx, n, _ptr(positions), _ptr(cell), ctypes.byref(np_)))
+    return np_.value
+
+
+def allegro_get_neighbors(ctx, row_ptr=None, col=None, img=None, rev=None):
+    _check(ctx, lib().allegro_get_neighbors(ctx, _ptr(row_ptr), _ptr(col), _ptr(img), _ptr(rev)))
+
+
+def allegro_energy_forces(ctx, positions, species, cell, forces_out=None, atom_energy=None,
+                          precision=ALLEGRO_FP32):
+    n = int(positions.shape[0])
+    cell = _host(cell, np.float64)
+    e = _f64()
+    _check(ctx, lib().allegro_energy_forces(ctx, n, _ptr(positions), _ptr(species), _ptr(cell), ctypes.byref(e),
+                                            _ptr(forces_out), _ptr(atom_energy), int(precision)))
+    return e.value
+
+
+def allegro_outlier_count(ctx, forces, threshold=5.0):
+    c = _i64()
+    _check(ctx, lib().allegro_outlier_count(ctx, int(forces.shape[0]), _ptr(forces), float(threshold),
+                                            ctypes.byref(c)))
+    return c.value
+
+
+def allegro_md_init(ctx, positions, velocities, species, cell):
+    cell = _host(cell, np.float64)
+    _check(ctx, lib().allegro_md_init(ctx, int(positions.shape[0]), _ptr(positions), _ptr(velocities),
+                                      _ptr(species), _ptr(cell)))
+
+
+def allegro_set_md_precision(ctx, precision):
+    _check(ctx, lib().allegro_set_md_precision(ctx, int(precision)))
+
+
+def allegro_md_step_nve(ctx, dt_fs, n_steps, outlier_counts=None, energies=None):
+    _check(ctx, lib().allegro_md_step_nve(ctx, float(dt_fs), int(n_steps), _ptr(outlier_counts), _ptr(energies)))
+
+
+def allegro_md_get_state(ctx, positions=None, velocities=None, forces=None):
+    s = _i64()
+    _check(ctx, lib().allegro_md_get_state(ctx, _ptr(positions), _ptr(velocities), _ptr(forces), ctypes.byref(s)))
+    return s.value
+
+
+__all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED

@@ -1,0 +1,788 @@
+// api.cu - C ABI of the library (include/allegro.h): context, weights blob,
+// device buffers, orchestration of the neighbour, pair-pass and per-atom
+// kernels, and the CUDA-graph MD step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/allegro.h"
+#include "kernels.h"
+#include "md.h"
+#include "model.h"
+
+using namespace al;
+
+namespace {
+
+const char* kVersion = "allegro-gb300 0.1";
+thread_local std::string g_err;
+
+struct Tensor {
+  std::string name;
+  uint32_t rows, cols;
+  const double* data;
+};
+
+struct Blob {
+  uint32_t S, lmax, L, C, NB, p;
+  std::vector<uint32_t> latent, energy;
+  double rc, nu;
+  std::vector<double> sigma, mu;
+  std::vector<Tensor> tensors;
+  std::vector<unsigned char> bytes;
+  const Tensor* find(const std::string& n) const {
+    for (auto& t : tensors)
+      if (t.name == n) return &t;
+    return nullptr;
+  }
+};
+
+bool rd32(const std::vector<unsigned char>& b, size_t off, uint32_t& v) {
+  if (off + 4 > b.size()) return false;
+  std::memcpy(&v, b.data() + off, 4);
+  return true;
+}
+bool rd64f(const std::vector<unsigned char>& b, size_t off, double& v) {
+  if (off + 8 > b.size()) return false;
+  std::memcpy(&v, b.data() + off, 8);
+  return true;
+}
+
+// Parse the "ALW1" layout (little-endian host assumed, as on x86-64 and aarch64).
+bool parse_blob(const void* data, size_t n, Blob& B, std::string& why) {
+  B.bytes.assign((const unsigned char*)data, (const unsigned char*)data + n);
+  const auto& b = B.bytes;
+  if (n < 48 || std::memcmp(b.data(), "ALW1", 4) != 0) { why = "bad magic"; return false; }
+  uint32_t h[11];
+  for (int k = 0; k < 11; ++k) rd32(b, 4 + 4 * k, h[k]);
+  if (h[0] != 1) { why = "unsupported blob version"; return false; }
+  B.S = h[1]; B.lmax = h[2]; B.L = h[3]; B.C = h[4]; B.NB = h[5]; B.p = h[6];
+  const uint32_t nlat = h[7], nen = h[8], nt = h[9];
+  if (nlat > 16 || nen > 16 || B.S > 16 || nt > 4096) { why = "implausible header"; return false; }
+  size_t off = 48;
+  B.latent.resize(nlat);
+  B.energy.resize(nen);
+  for (auto& v : B.latent) { if (!rd32(b, off, v)) { why = "truncated"; return false; } off += 4; }
+  for (auto& v : B.energy) { if (!rd32(b, off, v)) { why = "truncated"; return false; } off += 4; }
+  off += (8 - off % 8) % 8;
+  if (!rd64f(b, off, B.rc) || !rd64f(b, off + 8, B.nu)) { why = "truncated"; return false; }
+  off += 16;
+  B.sigma.resize(B.S);
+  B.mu.resize(B.S);
+  for (auto& v : B.sigma) { if (!rd64f(b, off, v)) { why = "truncated"; return false; } off += 8; }
+  for (auto& v : B.mu) { if (!rd64f(b, off, v)) { why = "truncated"; return false; } off += 8; }
+  for (uint32_t t = 0; t < nt; ++t) {
+    if (off + 48 > n) { why = "truncated directory"; return false; }
+    char name[33];
+    std::memcpy(name, b.data() + off, 32);
+    name[32] = 0;
+    Tensor T;
+    T.name = name;
+    rd32(b, off + 32, T.rows);
+    rd32(b, off + 36, T.cols);
+    uint64_t doff;
+    std::memcpy(&doff, b.data() + off + 40, 8);
+    off += 48;
+    if (doff % 8 != 0 || doff + 8ull * T.rows * T.cols > n) { why = "tensor out of range: " + T.name; return false; }
+    T.data = reinterpret_cast<const double*>(b.data() + doff);
+    B.tensors.push_back(T);
+  }
+  return true;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct allegro_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  Blob blob;
+  double mass[2] = {14.007, 1.008};
+  int D = 0, E = 0;
+  // weights
+  float* d_w = nullptr;
+  ModelW w{};
+  // allocations
+  std::vector<void*> allocs;
+  int64_t n_atoms_alloc = 0;
+  int ncell_alloc = 0;
+  int64_t capacity = 0;
+  int64_t part_rows = 0;
+  NeighborBuffers nb{};
+  GridInfo grid{};
+  PassBufs pb{};
+  double* d_pos = nullptr;     // N x 3 input positions (device copy)
+  int* d_species = nullptr;
+  float* d_F = nullptr;
+  double* d_Ei = nullptr;
+  double* d_blk = nullptr;
+  double* d_stats = nullptr;
+  unsigned long long* d_blku = nullptr;
+  long long* d_count = nullptr;
+  int n_atoms = 0;
+  // MD state
+  bool md_ready = false;
+  int md_precision = ALLEGRO_FP32;
+  double* d_v = nullptr;
+  double* d_blk_ke = nullptr;
+  long long* d_step = nullptr;
+  long long* d_out_rec = nullptr;
+  double* d_e_rec = nullptr;
+  int rec_cap = 0;
+  long long step = 0;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  // rollback snapshot
+  double* d_pos_snap = nullptr;
+  double* d_v_snap = nullptr;
+  float* d_F_snap = nullptr;
+
+  int fail(int code, const std::string& m) {
+    err = m;
+    g_err = m;
+    return code;
+  }
+  template <class T>
+  T* dalloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    allocs.push_back(p);
+    return (T*)p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    for (auto& a : allocs)
+      if (a == p) { cudaFree(p); a = nullptr; }
+  }
+  ~allegro_ctx() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (void* p : allocs)
+      if (p) cudaFree(p);
+  }
+};
+
+namespace {
+
+int cuda_check(allegro_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return c->fail(ALLEGRO_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return ALLEGRO_OK;
+}
+
+// Convert blob tensors into pre-scaled FP32 [in][out] and [out][in] copies.
+int upload_weights(allegro_ctx* c) {
+  const Blob& B = c->blob;
+  std::vector<float> host;
+  auto push = [&](const Tensor* T, double extra, Lin* lin, const float** raw_n) -> bool {
+    if (!T) return false;
+    const double s = extra / std::sqrt((double)T->cols);
+    while (host.size() % 4) host.push_back(0.f);
+    const size_t t_off = host.size();
+    for (uint32_t i = 0; i < T->cols; ++i)
+      for (uint32_t o = 0; o < T->rows; ++o) host.push_back((float)(T->data[o * T->cols + i] * s));
+    while (host.size() % 4) host.push_back(0.f);
+    const size_t n_off = host.size();
+    for (uint32_t o = 0; o < T->rows; ++o)
+      for (uint32_t i = 0; i < T->cols; ++i) host.push_back((float)(T->data[o * T->cols + i] * s));
+    if (lin) {
+      lin->t = reinterpret_cast<const float*>(t_off);
+      lin->n = reinterpret_cast<const float*>(n_off);
+    }
+    if (raw_n) *raw_n = reinterpret_cast<const float*>(n_off);
+    return true;
+  };
+  ModelW& w = c->w;
+  bool ok = push(B.find("twobody.0"), 1.0, &w.tb0, nullptr) && push(B.find("twobody.1"), 1.0, &w.tb1, nullptr) &&
+            push(B.find("embed"), 1.0, &w.emb, nullptr);
+  for (uint32_t k = 1; ok && k <= B.L; ++k) {
+    const std::string pre = "layer" + std::to_string(k) + ".";
+    LayerW& LW = w.layer[k - 1];
+    ok = ok && push(B.find(pre + "env"), 1.0 / std::sqrt(B.nu), &LW.env, nullptr);
+    if (k < B.L)
+      for (uint32_t l = 0; ok && l <= B.lmax; ++l)
+        ok = ok && push(B.find(pre + "mix" + std::to_string(l)), 1.0, nullptr, &LW.mix[l]);
+    ok = ok && push(B.find(pre + "latent.0"), 1.0, &LW.lat0, nullptr) &&
+         push(B.find(pre + "latent.1"), 1.0, &LW.lat1, nullptr);
+  }
+  const float* eout = nullptr;
+  ok = ok && push(B.find("energy.0"), 1.0, &w.e0, nullptr) && push(B.find("energy.out"), 1.0, nullptr, &eout);
+  if (!ok) return c->fail(ALLEGRO_E_BLOB, "weights blob lacks a tensor of the model");
+  c->d_w = c->dalloc<float>(host.size());
+  if (!c->d_w) return c->fail(ALLEGRO_E_OOM, "weights allocation failed");
+  if (cudaMemcpy(c->d_w, host.data(), host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_check(c, "weights upload");
+  auto fix = [&](const float*& p) { if (p || true) p = c->d_w + reinterpret_cast<size_t>(p); };
+  auto fixl = [&](Lin& l) { fix(l.t); fix(l.n); };
+  fixl(w.tb0); fixl(w.tb1); fixl(w.emb); fixl(w.e0);
+  for (uint32_t k = 1; k <= B.L; ++k) {
+    LayerW& LW = w.layer[k - 1];
+    fixl(LW.env); fixl(LW.lat0); fixl(LW.lat1);
+    if (k < B.L)
+      for (uint32_t l = 0; l <= B.lmax; ++l) fix(LW.mix[l]);
+  }
+  w.eout = c->d_w + reinterpret_cast<size_t>(eout);
+  for (int s = 0; s < 2; ++s) {
+    w.sigma[s] = (float)B.sigma[s];
+    w.mu[s] = (float)B.mu[s];
+  }
+  w.rc = (float)B.rc;
+  w.n_layers = (int)B.L;
+  return ALLEGRO_OK;
+}
+
+int check_cell(allegro_ctx* c, const double* cell, double L[3]) {
+  if (!cell) return c->fail(ALLEGRO_E_INVALID_ARG, "cell is NULL");
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      if (a != b && cell[3 * a + b] != 0.0) return c->fail(ALLEGRO_E_NONORTHO_CELL, "only orthorhombic cells are supported");
+  for (int a = 0; a < 3; ++a) {
+    L[a] = cell[4 * a];
+    if (!(L[a] > 0.0) || !std::isfinite(L[a])) return c->fail(ALLEGRO_E_NONORTHO_CELL, "cell lengths must be positive");
+    if (c->blob.rc > 2.0 * L[a]) return c->fail(ALLEGRO_E_CUTOFF_TOO_LARGE, "r_cut exceeds twice the cell length");
+  }
+  return ALLEGRO_OK;
+}
+
+int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
+  if (n > c->n_atoms_alloc) {
+    const int64_t na = std::max<int64_t>(n, c->n_atoms_alloc * 5 / 4);
+    for (void* p : {(void*)c->d_pos, (void*)c->d_species, (void*)c->d_F, (void*)c->d_Ei, (void*)c->d_blk,
+                    (void*)c->d_blku, (void*)c->nb.wpos, (void*)c->nb.wpos32, (void*)c->nb.atom_cell,
+                    (void*)c->nb.cell_atoms, (void*)c->nb.row_cnt, (void*)c->nb.row_ptr, (void*)c->nb.scan_blocks,
+                    (void*)c->d_v, (void*)c->d_blk_ke, (void*)c->d_pos_snap, (void*)c->d_v_snap,
+                    (void*)c->d_F_snap})
+      c->dfree(p);
+    c->d_pos = c->dalloc<double>(3 * na);
+    c->d_species = c->dalloc<int>(na);
+    c->d_F = c->dalloc<float>(3 * na);
+    c->d_Ei = c->dalloc<double>(na);
+    c->d_blk = c->dalloc<double>(2 * (na / 256 + 2));
+    c->d_blku = c->dalloc<unsigned long long>(na / 256 + 2);
+    c->nb.wpos = c->dalloc<double>(3 * na);
+    c->nb.wpos32 = c->dalloc<float>(3 * na);
+    c->nb.atom_cell = c->dalloc<int>(na);
+    c->nb.cell_atoms = c->dalloc<int>(na);
+    c->nb.row_cnt = c->dalloc<int>(na + 1);
+    c->nb.row_ptr = c->dalloc<int>(na + 1);
+    c->nb.scan_blocks = c->dalloc<int>((std::max<int64_t>(na, 1 << 22) + 1) / 1024 + 4);
+    c->d_v = c->dalloc<double>(3 * na);
+    c->d_blk_ke = c->dalloc<double>(na / 256 + 2);
+    c->d_pos_snap = c->dalloc<double>(3 * na);
+    c->d_v_snap = c->dalloc<double>(3 * na);
+    c->d_F_snap = c->dalloc<float>(3 * na);
+    if (!c->d_pos || !c->d_species || !c->d_F || !c->d_Ei || !c->d_blk || !c->d_blku || !c->nb.wpos ||
+        !c->nb.wpos32 || !c->nb.atom_cell || !c->nb.cell_atoms || !c->nb.row_cnt || !c->nb.row_ptr ||
+        !c->nb.scan_blocks || !c->d_v || !c->d_blk_ke || !c->d_pos_snap || !c->d_v_snap || !c->d_F_snap)
+      return c->fail(ALLEGRO_E_OOM, "per-atom allocation failed");
+    c->n_atoms_alloc = na;
+    c->part_rows = 0;   // partial buffers depend on N
+  }
+  if (!c->d_stats) {
+    c->d_stats = c->dalloc<double>(8);
+    c->d_count = c->dalloc<long long>(2);
+    c->nb.n_pairs = c->dalloc<int>(1);
+    c->nb.flags = c->dalloc<int>(1);
+    c->d_step = c->dalloc<long long>(1);
+    if (!c->d_stats || !c->d_count || !c->nb.n_pairs || !c->nb.flags || !c->d_step)
+      return c->fail(ALLEGRO_E_OOM, "allocation failed");
+    cudaMemset(c->nb.flags, 0, sizeof(int));
+  }
+  if (ncell + 1 > c->ncell_alloc) {
+    c->dfree(c->nb.cell_count);
+    c->dfree(c->nb.cell_start);
+    c->nb.cell_count = c->dalloc<int>(ncell + 2);
+    c->nb.cell_start = c->dalloc<int>(ncell + 2);
+    if (!c->nb.cell_count || !c->nb.cell_start) return c->fail(ALLEGRO_E_OOM, "cell allocation failed");
+    c->ncell_alloc = ncell + 2;
+  }
+  return ALLEGRO_OK;
+}
+
+int ensure_pairs(allegro_ctx* c, int64_t cap) {
+  const Blob& B = c->blob;
+  const int NLM = (B.lmax + 1) * (B.lmax + 1);
+  const int CL = B.C * NLM;
+  const int tile = fp32_tile();
+  const int64_t rows_needed = cap / tile + 2 + c->n_atoms_alloc;
+  if (cap <= c->capacity && rows_needed <= c->part_rows) return ALLEGRO_OK;
+  if (cap > (int64_t)0x7fffffff - 1024) return c->fail(ALLEGRO_E_UNSUPPORTED, "more than 2^31 pairs");
+  PassBufs& pb = c->pb;
+  for (void* p : {(void*)c->nb.pi, (void*)c->nb.pj, (void*)c->nb.pcode, (void*)c->nb.rev, (void*)c->nb.keys,
+                  (void*)c->nb.skeys, (void*)pb.dX, (void*)pb.dV, (void*)pb.dU, (void*)pb.dY, (void*)pb.G,
+                  (void*)pb.epart})
+    c->dfree(p);
+  for (int k = 0; k < kMaxLayers; ++k) {
+    c->dfree(pb.X[k]);
+    c->dfree(pb.V[k]);
+    pb.X[k] = pb.V[k] = nullptr;
+  }
+  for (int k = 0; k <= kMaxLayers; ++k) {
+    c->dfree(pb.gam[k]);
+    c->dfree(pb.dgam[k]);
+    pb.gam[k] = pb.dgam[k] = nullptr;
+  }
+  c->nb.pi = c->dalloc<int>(cap);
+  c->nb.pj = c->dalloc<int>(cap);
+  c->nb.pcode = c->dalloc<int>(cap);
+  c->nb.rev = c->dalloc<int>(cap);
+  c->nb.keys = c->dalloc<unsigned long long>(cap);
+  c->nb.skeys = c->dalloc<unsigned long long>(cap);
+  bool ok = c->nb.pi && c->nb.pj && c->nb.pcode && c->nb.rev && c->nb.keys && c->nb.skeys;
+  for (uint32_t k = 0; k < B.L && ok; ++k) {
+    pb.X[k] = c->dalloc<float>((size_t)cap * c->D);
+    ok = ok && pb.X[k];
+    if (k >= 1) {
+      pb.V[k] = c->dalloc<float>((size_t)cap * CL);
+      ok = ok && pb.V[k];
+    }
+  }
+  pb.dX = c->dalloc<float>((size_t)cap * c->D);
+  pb.dV = c->dalloc<float>((size_t)cap * CL);
+  pb.dU = c->dalloc<float>(cap);
+  pb.dY = c->dalloc<float>((size_t)cap * NLM);
+  pb.G = c->dalloc<float>((size_t)cap * 3);
+  const int64_t rows = rows_needed;
+  pb.epart = c->dalloc<double>(rows);
+  ok = ok && pb.dX && pb.dV && pb.dU && pb.dY && pb.G && pb.epart;
+  for (uint32_t k = 1; k <= B.L && ok; ++k) {
+    pb.gam[k] = c->dalloc<float>((size_t)rows * CL);
+    pb.dgam[k] = c->dalloc<float>((size_t)rows * CL);
+    ok = ok && pb.gam[k] && pb.dgam[k];
+  }
+  if (!ok) {
+    c->capacity = 0;
+    return c->fail(ALLEGRO_E_OOM, "pair buffers allocation failed (capacity " + std::to_string(cap) + ")");
+  }
+  c->capacity = cap;
+  c->nb.capacity = cap;
+  c->part_rows = rows;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return ALLEGRO_OK;
+}
+
+void fill_passbufs(allegro_ctx* c, const double L[3]) {
+  PassBufs& pb = c->pb;
+  pb.pi = c->nb.pi;
+  pb.pj = c->nb.pj;
+  pb.pcode = c->nb.pcode;
+  pb.row_ptr = c->nb.row_ptr;
+  pb.n_pairs = c->nb.n_pairs;
+  pb.flags = c->nb.flags;
+  pb.capacity = c->capacity;
+  pb.wpos = c->nb.wpos;
+  pb.species = c->d_species;
+  pb.n_atoms = c->n_atoms;
+  for (int a = 0; a < 3; ++a) pb.L[a] = L[a];
+  pb.tile = fp32_tile();
+}
+
+AtomArgs atom_args(allegro_ctx* c) {
+  AtomArgs a;
+  a.n = c->n_atoms;
+  a.species = c->d_species;
+  for (int s = 0; s < 2; ++s) {
+    a.sigma[s] = c->blob.sigma[s];
+    a.mu[s] = c->blob.mu[s];
+    a.mass[s] = c->mass[s];
+  }
+  return a;
+}
+
+__global__ void k_check_species(int n, const int* __restrict__ sp, int S, int* __restrict__ flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (sp[i] < 0 || sp[i] >= S)) atomicOr(flags, kFlagBadSpecies);
+}
+
+// Neighbour build into the current capacity; grows and rebuilds once on
+// overflow.  Leaves n_pairs on the host in *np_host.
+int build_with_growth(allegro_ctx* c, const double* d_positions, int64_t n, int64_t* np_host) {
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    launch_build_neighbors(c->nb, c->grid, d_positions, (int)n, c->stream);
+    int np = 0, flags = 0;
+    cudaMemcpyAsync(&np, c->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&flags, c->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "neighbour build");
+    if (flags & kFlagNonfinite) return c->fail(ALLEGRO_E_NONFINITE, "non-finite position");
+    if (flags & kFlagBadSpecies) return c->fail(ALLEGRO_E_INVALID_ARG, "species id out of range");
+    if (!(flags & kFlagPairOverflow)) {
+      *np_host = np;
+      return ALLEGRO_OK;
+    }
+    const int rc = ensure_pairs(c, (int64_t)np + np / 4 + 1024);
+    if (rc) return rc;
+    const int cleared = flags & ~kFlagPairOverflow;
+    cudaMemcpy(c->nb.flags, &cleared, sizeof(int), cudaMemcpyHostToDevice);
+  }
+  return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown");
+}
+
+int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* species,
+            const double* cell, double L[3]) {
+  if (n <= 0 || n > (1 << 30)) return c->fail(ALLEGRO_E_INVALID_ARG, "n_atoms out of range");
+  if (!positions) return c->fail(ALLEGRO_E_INVALID_ARG, "positions is NULL");
+  int rc = check_cell(c, cell, L);
+  if (rc) return rc;
+  c->grid = plan_grid(L, c->blob.rc);
+  const int ncell = c->grid.ncell[0] > 0 ? c->grid.ncell[0] * c->grid.ncell[1] * c->grid.ncell[2] : 0;
+  rc = ensure_atoms(c, n, ncell);
+  if (rc) return rc;
+  c->n_atoms = (int)n;
+  cudaMemsetAsync(c->nb.flags, 0, sizeof(int), c->stream);
+  const cudaMemcpyKind kp = is_device_ptr(positions) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(c->d_pos, positions, sizeof(double) * 3 * n, kp, c->stream);
+  if (species) {
+    const cudaMemcpyKind ks = is_device_ptr(species) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpyAsync(c->d_species, species, sizeof(int) * n, ks, c->stream);
+    k_check_species<<<(int)((n + 255) / 256), 256, 0, c->stream>>>((int)n, c->d_species, (int)c->blob.S,
+                                                                   c->nb.flags);
+  }
+  if (c->capacity == 0) {
+    const double vol = L[0] * L[1] * L[2];
+    const double rc3 = c->blob.rc * c->blob.rc * c->blob.rc;
+    const double est = (double)n * (4.18879 * rc3 * (double)n / vol) * 1.3 + 4096.0;
+    rc = ensure_pairs(c, (int64_t)std::min(est, 2.0e9));
+    if (rc) return rc;
+  } else if (c->part_rows < c->capacity / fp32_tile() + 2 + c->n_atoms_alloc) {
+    rc = ensure_pairs(c, c->capacity);
+    if (rc) return rc;
+  }
+  return cuda_check(c, "prepare");
+}
+
+int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
+  if (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16)
+    return c->fail(ALLEGRO_E_INVALID_ARG, "precision must be ALLEGRO_FP32 or ALLEGRO_BF16");
+  fill_passbufs(c, L);
+  const Blob& B = c->blob;
+  // BF16 requests run the FP32 pair passes until the tensor-core path is built
+  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream);
+  launch_forces(atom_args(c), c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei,
+                c->d_blk, c->d_stats, c->nb.flags, c->stream);
+  return cuda_check(c, "model launch");
+}
+
+int copy_out(allegro_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!dst) return ALLEGRO_OK;
+  const cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (cudaMemcpyAsync(dst, src, bytes, k, c->stream) != cudaSuccess) return cuda_check(c, "copy out");
+  return ALLEGRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* allegro_version(void) { return kVersion; }
+
+const char* allegro_last_error(const allegro_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int allegro_create(const void* weights_blob, size_t blob_bytes, const double* species_mass, int32_t n_species,
+                   double r_cut, int32_t l_max, int32_t n_layers, allegro_ctx** out) {
+  if (!out || !weights_blob || !species_mass) {
+    g_err = "NULL argument";
+    return ALLEGRO_E_INVALID_ARG;
+  }
+  *out = nullptr;
+  allegro_ctx* c = new (std::nothrow) allegro_ctx();
+  if (!c) {
+    g_err = "host allocation failed";
+    return ALLEGRO_E_OOM;
+  }
+  std::string why;
+  if (!parse_blob(weights_blob, blob_bytes, c->blob, why)) {
+    g_err = "weights blob: " + why;
+    delete c;
+    return ALLEGRO_E_BLOB;
+  }
+  const Blob& B = c->blob;
+  if ((int)B.S != n_species || B.rc != r_cut || (int)B.lmax != l_max || (int)B.L != n_layers) {
+    g_err = "create() arguments disagree with the weights blob header";
+    delete c;
+    return ALLEGRO_E_MISMATCH;
+  }
+  const bool shape_ok = B.S == 2 && B.NB == 8 && B.p == 6 && B.latent.size() == 2 && B.latent[0] == B.latent[1] &&
+                        B.energy.size() == 1 && B.L >= 1 && B.L <= (uint32_t)kMaxLayers &&
+                        fp32_supported((int)B.lmax, (int)B.C, (int)B.latent[0], (int)B.energy[0]);
+  if (!shape_ok) {
+    g_err = "model shape not compiled into this library";
+    delete c;
+    return ALLEGRO_E_UNSUPPORTED;
+  }
+  c->D = (int)B.latent[0];
+  c->E = (int)B.energy[0];
+  for (int s = 0; s < 2; ++s) c->mass[s] = species_mass[s];
+  int rc = upload_weights(c);
+  if (rc) {
+    g_err = c->err;
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return ALLEGRO_OK;
+}
+
+void allegro_destroy(allegro_ctx* ctx) { delete ctx; }
+
+int allegro_set_stream(allegro_ctx* ctx, void* s) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  ctx->stream = (cudaStream_t)s;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return ALLEGRO_OK;
+}
+
+int allegro_build_neighbors(allegro_ctx* ctx, int64_t n_atoms, const double* positions, const double* cell,
+                            int64_t* n_pairs) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  double L[3];
+  int rc = prepare(ctx, n_atoms, positions, nullptr, cell, L);
+  if (rc) return rc;
+  int64_t np = 0;
+  rc = build_with_growth(ctx, ctx->d_pos, n_atoms, &np);
+  if (rc) return rc;
+  if (n_pairs) *n_pairs = np;
+  return ALLEGRO_OK;
+}
+
+int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col, int8_t* img, int32_t* rev) {
+  if (!ctx || ctx->n_atoms <= 0) return ALLEGRO_E_INVALID_ARG;
+  int np = 0;
+  cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  int rc = copy_out(ctx, row_ptr, ctx->nb.row_ptr, sizeof(int) * (ctx->n_atoms + 1));
+  if (!rc) rc = copy_out(ctx, col, ctx->nb.pj, sizeof(int) * np);
+  if (!rc) rc = copy_out(ctx, rev, ctx->nb.rev, sizeof(int) * np);
+  if (!rc && img) {
+    std::vector<int> code(np);
+    std::vector<int8_t> out(3 * (size_t)np);
+    cudaMemcpyAsync(code.data(), ctx->nb.pcode, sizeof(int) * np, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    for (int p = 0; p < np; ++p) {
+      out[3 * p] = (int8_t)(code[p] / 25 - 2);
+      out[3 * p + 1] = (int8_t)((code[p] / 5) % 5 - 2);
+      out[3 * p + 2] = (int8_t)(code[p] % 5 - 2);
+    }
+    const cudaMemcpyKind k = is_device_ptr(img) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    cudaMemcpyAsync(img, out.data(), out.size(), k, ctx->stream);
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "get_neighbors");
+  return rc;
+}
+
+int allegro_energy_forces(allegro_ctx* ctx, int64_t n_atoms, const double* positions, const int32_t* species,
+                          const double* cell, double* energy_out, float* forces_out, double* atom_energy,
+                          int32_t precision) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  if (!species || !energy_out) return ctx->fail(ALLEGRO_E_INVALID_ARG, "species and energy_out are required");
+  double L[3];
+  int rc = prepare(ctx, n_atoms, positions, species, cell, L);
+  if (rc) return rc;
+  int64_t np = 0;
+  rc = build_with_growth(ctx, ctx->d_pos, n_atoms, &np);
+  if (rc) return rc;
+  rc = run_model(ctx, precision, L);
+  if (rc) return rc;
+  double stats[2];
+  int flags = 0;
+  cudaMemcpyAsync(stats, ctx->d_stats, sizeof(stats), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  rc = copy_out(ctx, forces_out, ctx->d_F, sizeof(float) * 3 * n_atoms);
+  if (!rc) rc = copy_out(ctx, atom_energy, ctx->d_Ei, sizeof(double) * n_atoms);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "energy_forces");
+  if (flags & kFlagNonfinite) return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite energy or force");
+  *energy_out = stats[0];
+  return ALLEGRO_OK;
+}
+
+int allegro_outlier_count(allegro_ctx* ctx, int64_t n_atoms, const float* forces, double threshold,
+                          int64_t* count_out) {
+  if (!ctx || !forces || !count_out || n_atoms <= 0) return ALLEGRO_E_INVALID_ARG;
+  int rc = ensure_atoms(ctx, n_atoms, 0);
+  if (rc) return rc;
+  const cudaMemcpyKind k = is_device_ptr(forces) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(ctx->d_F_snap, forces, sizeof(float) * 3 * n_atoms, k, ctx->stream);
+  launch_sum_f2((int)n_atoms, ctx->d_F_snap, ctx->d_stats + 4, ctx->stream);
+  launch_outliers((int)n_atoms, ctx->d_F_snap, ctx->d_stats + 4, threshold, ctx->d_blku, ctx->d_count,
+                  ctx->stream);
+  long long cnt = 0;
+  cudaMemcpyAsync(&cnt, ctx->d_count, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "outlier_count");
+  *count_out = cnt;
+  return ALLEGRO_OK;
+}
+
+int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
+  if (!ctx || (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16)) return ALLEGRO_E_INVALID_ARG;
+  if (precision != ctx->md_precision && ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  ctx->md_precision = precision;
+  return ALLEGRO_OK;
+}
+
+int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions, const double* velocities,
+                    const int32_t* species, const double* cell) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  if (!velocities || !species) return ctx->fail(ALLEGRO_E_INVALID_ARG, "velocities and species are required");
+  double L[3];
+  ctx->md_ready = false;
+  int rc = prepare(ctx, n_atoms, positions, species, cell, L);
+  if (rc) return rc;
+  const cudaMemcpyKind kv = is_device_ptr(velocities) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(ctx->d_v, velocities, sizeof(double) * 3 * n_atoms, kv, ctx->stream);
+  int64_t np = 0;
+  rc = build_with_growth(ctx, ctx->d_pos, n_atoms, &np);
+  if (rc) return rc;
+  // keep a little headroom for density fluctuations during the trajectory
+  if (ctx->capacity < np + np / 8 + 1024) {
+    rc = ensure_pairs(ctx, np + np / 4 + 1024);
+    if (rc) return rc;
+    rc = build_with_growth(ctx, ctx->d_pos, n_atoms, &np);
+    if (rc) return rc;
+  }
+  rc = run_model(ctx, ctx->md_precision, L);
+  if (rc) return rc;
+  // state positions are the wrapped ones
+  cudaMemcpyAsync(ctx->d_pos, ctx->nb.wpos, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "md_init");
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  ctx->step = 0;
+  ctx->md_ready = true;
+  return ALLEGRO_OK;
+}
+
+namespace {
+
+int capture_step(allegro_ctx* c, double dt) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  double L[3] = {c->grid.L[0], c->grid.L[1], c->grid.L[2]};
+  fill_passbufs(c, L);
+  cudaStream_t cs = c->stream;
+  bool own = false;
+  if (!cs) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_check(c, "stream");
+    own = true;
+  }
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_check(c, "capture");
+  const AtomArgs a = atom_args(c);
+  launch_kick_drift(a, c->d_pos, c->d_v, c->d_F, dt, L, cs);
+  launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs);
+  const Blob& B = c->blob;
+  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, cs);
+  launch_forces(a, c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk,
+                c->d_stats, c->nb.flags, cs);
+  launch_kick_measure(a, c->d_v, c->d_F, dt, c->d_stats, 5.0, c->d_blk_ke, c->d_blku, c->d_step, c->rec_cap,
+                      c->d_e_rec, c->d_out_rec, cs);
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (e != cudaSuccess) {
+    if (own) cudaStreamDestroy(cs);
+    return cuda_check(c, "end capture");
+  }
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (own) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_check(c, "graph instantiate");
+  c->graph_dt = dt;
+  return ALLEGRO_OK;
+}
+
+}  // namespace
+
+int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t* outlier_counts,
+                        double* energies) {
+  if (!ctx || !ctx->md_ready) return ctx ? ctx->fail(ALLEGRO_E_INVALID_ARG, "md_init first") : ALLEGRO_E_INVALID_ARG;
+  if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "bad dt or n_steps");
+  if (n_steps == 0) return ALLEGRO_OK;
+  if (n_steps > ctx->rec_cap) {
+    ctx->dfree(ctx->d_e_rec);
+    ctx->dfree(ctx->d_out_rec);
+    const int cap = std::max(n_steps, 1024);
+    ctx->d_e_rec = ctx->dalloc<double>(3 * (size_t)cap);
+    ctx->d_out_rec = ctx->dalloc<long long>(cap);
+    if (!ctx->d_e_rec || !ctx->d_out_rec) return ctx->fail(ALLEGRO_E_OOM, "record allocation failed");
+    ctx->rec_cap = cap;
+    if (ctx->graph) {
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+    }
+  }
+  const size_t n3 = 3 * (size_t)ctx->n_atoms;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    if (!ctx->graph || ctx->graph_dt != dt_fs) {
+      int rc = capture_step(ctx, dt_fs);
+      if (rc) return rc;
+    }
+    cudaMemcpyAsync(ctx->d_pos_snap, ctx->d_pos, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_v_snap, ctx->d_v, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_F_snap, ctx->d_F, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream);
+    for (int s = 0; s < n_steps; ++s)
+      if (cudaGraphLaunch(ctx->graph, ctx->stream) != cudaSuccess) return cuda_check(ctx, "graph launch");
+    int flags = 0, np = 0;
+    cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "md steps");
+    if (flags & kFlagPairOverflow) {
+      cudaMemcpyAsync(ctx->d_pos, ctx->d_pos_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->d_v, ctx->d_v_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->d_F, ctx->d_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+      const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024;
+      int rc = ensure_pairs(ctx, grow);
+      if (rc) return rc;
+      continue;
+    }
+    if (flags & kFlagNonfinite) return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite energy or force during MD");
+    ctx->step += n_steps;
+    int rc = copy_out(ctx, outlier_counts, ctx->d_out_rec, sizeof(long long) * n_steps);
+    if (!rc) rc = copy_out(ctx, energies, ctx->d_e_rec, sizeof(double) * 3 * n_steps);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "md record copy");
+    return ALLEGRO_OK;
+  }
+  return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown during MD");
+}
+
+int allegro_md_get_state(allegro_ctx* ctx, double* positions, double* velocities, float* forces, int64_t* step) {
+  if (!ctx || !ctx->md_ready) return ALLEGRO_E_INVALID_ARG;
+  const size_t n3 = 3 * (size_t)ctx->n_atoms;
+  int rc = copy_out(ctx, positions, ctx->d_pos, sizeof(double) * n3);
+  if (!rc) rc = copy_out(ctx, velocities, ctx->d_v, sizeof(double) * n3);
+  if (!rc) rc = copy_out(ctx, forces, ctx->d_F, sizeof(float) * n3);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "get_state");
+  if (step) *step = ctx->step;
+  return ALLEGRO_OK;
+}
+
+}  // extern "C"

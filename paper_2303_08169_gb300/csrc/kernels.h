@@ -1,0 +1,62 @@
+// kernels.h - host-side launchers shared between the CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace al {
+
+// Status flags raised by kernels (bitwise OR into a device int).
+enum DevFlag : int {
+  kFlagPairOverflow = 1,
+  kFlagNonfinite = 2,
+  kFlagTimeout = 4,
+  kFlagBadSpecies = 8,
+};
+
+struct NeighborBuffers {
+  // per atom
+  double* wpos = nullptr;      // N x 3 wrapped FP64
+  float* wpos32 = nullptr;     // N x 3 wrapped FP32 (distance pre-filter)
+  int* atom_cell = nullptr;    // N
+  int* cell_count = nullptr;   // ncell + 1
+  int* cell_start = nullptr;   // ncell + 1
+  int* cell_atoms = nullptr;   // N (atoms sorted by cell)
+  int* row_cnt = nullptr;      // N + 1
+  int* row_ptr = nullptr;      // N + 1
+  // per pair (capacity)
+  int* pi = nullptr;           // centre atom
+  int* pj = nullptr;           // neighbour atom
+  int* pcode = nullptr;        // image code (common.cuh)
+  int* rev = nullptr;          // reverse pair index
+  unsigned long long* keys = nullptr;   // scratch: unsorted row keys
+  unsigned long long* skeys = nullptr;  // sorted row keys
+  // scan scratch
+  int* scan_blocks = nullptr;  // >= ceil((max(N, ncell)+1)/1024) + 1
+  int* n_pairs = nullptr;      // device scalar
+  int* flags = nullptr;        // device scalar (DevFlag bits)
+  int64_t capacity = 0;
+};
+
+struct GridInfo {
+  double L[3];
+  int ncell[3];     // cells per axis (cell mode) or 0 (small-box mode)
+  int nimg[3];      // image range per axis in small-box mode
+  double rc;
+  float band;       // FP32 pre-filter half-width on d^2
+};
+
+// Plan the grid: cell mode iff floor(L / (rc (1 + 1e-9))) >= 3 on every axis.
+GridInfo plan_grid(const double L[3], double rc);
+
+// Full rebuild: wrap, bin, count, scan, fill, sort, reverse.  Writes the pair
+// count to nb.n_pairs and raises kFlagPairOverflow if it exceeds capacity
+// (then the pair arrays are untouched beyond capacity and must not be used).
+void launch_build_neighbors(const NeighborBuffers& nb, const GridInfo& g, const double* pos,
+                            int n_atoms, cudaStream_t s);
+
+// Exclusive scan of n ints (in -> out), out[n] = total; total also copied to
+// *total_dev when non-null.
+void launch_scan(const int* in, int* out, int n, int* block_scratch, int* total_dev,
+                 cudaStream_t s);
+
+}  // namespace al

@@ -1,0 +1,37 @@
+// md.h - launchers for the per-atom kernels (md.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace al {
+
+constexpr double kKappa = 9.648533e-3;   // 1 eV/(A amu) in A/fs^2
+
+struct AtomArgs {
+  int n;
+  const int* species;
+  double sigma[2], mu[2], mass[2];
+};
+
+int atom_blocks(int n);
+
+// F = sum_j (g_ij - g_ji); E_i; per-block partials -> stats[0] = E, stats[1] = sum F^2.
+void launch_forces(const AtomArgs& a, const int* row_ptr, const int* rev, const float* G,
+                   const double* epart, int tile, float* F, double* Ei, double* blk,
+                   double* stats, int* flags, cudaStream_t s);
+
+// stats[1] = sum F^2 for an external force array.
+void launch_sum_f2(int n, const float* F, double* stats, cudaStream_t s);
+
+// count |F_ia| > thr * sqrt(stats[1] / 3N) into *out.
+void launch_outliers(int n, const float* F, const double* stats, double thr,
+                     unsigned long long* blk, long long* out, cudaStream_t s);
+
+void launch_kick_drift(const AtomArgs& a, double* r, double* v, const float* F, double dt,
+                       const double L[3], cudaStream_t s);
+
+void launch_kick_measure(const AtomArgs& a, double* v, const float* F, double dt,
+                         const double* stats, double thr, double* blk_ke,
+                         unsigned long long* blk_out, long long* step, int max_steps,
+                         double* energies, long long* outliers, cudaStream_t s);
+
+}  // namespace al

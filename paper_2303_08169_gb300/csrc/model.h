@@ -1,0 +1,72 @@
+// model.h - device-side model description shared by the pass kernels and the
+// host orchestration.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace al {
+
+constexpr int kMaxLayers = 4;
+
+// One linear layer y = W x / sqrt(fan_in) stored twice, both pre-scaled:
+//   t: [in][out]  (forward:  y[o] = sum_i x[i] t[i][o])
+//   n: [out][in]  (adjoint: dx[i] = sum_o dy[o] n[o][i])
+struct Lin {
+  const float* t = nullptr;
+  const float* n = nullptr;
+};
+
+struct LayerW {
+  Lin env;                    // C x D, extra factor 1/sqrt(nu)
+  const float* mix[3] = {};   // [C][C P_l] (layers below the last)
+  Lin lat0, lat1;             // (D + C P_0) -> D -> D
+};
+
+struct ModelW {
+  Lin tb0, tb1;               // (2S + Nb) -> D -> D
+  Lin emb;                    // D -> C (lmax + 1)
+  LayerW layer[kMaxLayers];
+  Lin e0;                     // D -> E
+  const float* eout = nullptr;// E (scaled by 1/sqrt(E))
+  float sigma[2], mu[2];
+  float rc;
+  int n_layers;
+};
+
+// Per-pass buffers (device).
+struct PassBufs {
+  // neighbour list
+  const int* pi;
+  const int* pj;
+  const int* pcode;
+  const int* row_ptr;
+  const int* n_pairs;     // device scalar
+  const int* flags;       // device status bits; passes skip all work on overflow
+  int64_t capacity;       // pair capacity of every per-pair array
+  const double* wpos;     // N x 3 wrapped positions
+  const int* species;     // N
+  int n_atoms;
+  double L[3];
+  // per pair state
+  float* X[kMaxLayers];   // x^k, k = 0..L-1    (P x D)
+  float* V[kMaxLayers];   // V^k, k = 1..L-1    (P x C NLM)
+  float* dX;              // P x D
+  float* dV;              // P x C NLM
+  float* dU;              // P
+  float* dY;              // P x NLM
+  float* G;               // P x 3  (dE/dDelta)
+  // per (tile, atom) partial sums, index (tile + atom)
+  float* gam[kMaxLayers + 1];   // Gamma^k partials, k = 1..L
+  float* dgam[kMaxLayers + 1];  // dGamma^k partials
+  double* epart;                // sum_j E_ij partials
+  int tile;                     // pairs per tile (all passes)
+};
+
+// FP32 path: one launcher per pass sequence; templated on the model shape in
+// the .cu file, dispatched by (lmax, C, D, E).
+bool fp32_supported(int lmax, int C, int D, int E);
+void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
+                        int64_t capacity, cudaStream_t s);
+int fp32_tile();
+
+}  // namespace al

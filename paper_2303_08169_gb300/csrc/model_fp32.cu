@@ -1,0 +1,926 @@
+// model_fp32.cu - FP32 pair-tile kernels: forward passes and hand-written
+// adjoint (forces f = -dE/dr, Eq. 1) for the Allegro-shaped model.
+//
+// Model (per ordered pair (i, j, n); the paper fixes only E = sum_ij E_ij and
+// equivariance, Sec. 2.1; the layer reading is the one of the oracle):
+//   x0 = fc(d) MLP_2b([onehot Z_i, onehot Z_j, B(d)]),  V0 = Lin(x0) (x) Y(u)
+//   layer k: e = Lin_env(x^{k-1}); Gamma_i = sum_j e_ij (x) Y_ij / sqrt(nu)
+//            T = CG(V^{k-1}_ij, Gamma_i); V^k = mix(T)   (k < L)
+//            x^k = (x^{k-1} + fc MLP_k([x^{k-1}, T_scalars])) / sqrt2
+//   E_ij = MLP_E(x^L);  E_i = sigma_Z sum_j E_ij + mu_Z
+//
+// Pass structure over tiles of kTile consecutive pairs of the CSR list (the
+// scatter into Gamma_i is a barrier between layers):
+//   A      : geometry, two-body MLP, x0 (stored), e^1 -> Gamma^1 partials
+//   B_k    : TP_k + mix -> V^k (stored), latent_k -> x^k (stored),
+//            e^{k+1} -> Gamma^{k+1} partials                      (k < L)
+//   C      : layer L + energy MLP forward, then its adjoint at once
+//            (dE/dE_ij = sigma_{Z_i} is local): dx^{L-1}, dV^{L-1},
+//            dGamma^L partials, du
+//   B_k^T  : adjoint of the Gamma^{k+1} scatter and of layer k (forward
+//            of layer k recomputed in the tile)                   (k = L-1..1)
+//   A^T    : adjoint of the Gamma^1 scatter, two-body MLP (recomputed),
+//            geometry -> g_ij = dE/dDelta_ij
+// Per-atom sums (Gamma, dGamma, sum_j E_ij) are written as per-(tile, atom)
+// partials at index tile + atom and summed in tile order by the consumer, so
+// every result is bitwise deterministic without atomics.
+#include <cstdio>
+
+#include "common.cuh"
+#include "model.h"
+#include "tp_tables.inc"
+
+namespace al {
+namespace {
+
+constexpr int kTile = 32;       // pairs per tile
+constexpr int kThreads = 256;   // 8 threads per pair in per-pair phases
+constexpr int kSub = kThreads / kTile;
+constexpr float kRsqrt2 = 0.70710678118654752f;
+
+template <int LMAX> struct TP;
+template <> struct TP<1> {
+  static constexpr int NT = TP1_NT, NS = TP1_NS;
+  static AL_DEV void fwd(const float* V, const float* G, float* T) { tp1_fwd(V, G, T); }
+  static AL_DEV void fwd_s(const float* V, const float* G, float* T) { tp1_fwd_scalar(V, G, T); }
+  static AL_DEV void bwd(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp1_bwd(V, G, dT, dV, dG); }
+  static AL_DEV void bwd_s(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp1_bwd_scalar(V, G, dT, dV, dG); }
+  static constexpr AL_DEV int P(int l) { return tp1_P(l); }
+  static constexpr AL_DEV int toff(int l) { return tp1_toff(l); }
+};
+template <> struct TP<2> {
+  static constexpr int NT = TP2_NT, NS = TP2_NS;
+  static AL_DEV void fwd(const float* V, const float* G, float* T) { tp2_fwd(V, G, T); }
+  static AL_DEV void fwd_s(const float* V, const float* G, float* T) { tp2_fwd_scalar(V, G, T); }
+  static AL_DEV void bwd(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp2_bwd(V, G, dT, dV, dG); }
+  static AL_DEV void bwd_s(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp2_bwd_scalar(V, G, dT, dV, dG); }
+  static constexpr AL_DEV int P(int l) { return tp2_P(l); }
+  static constexpr AL_DEV int toff(int l) { return tp2_toff(l); }
+};
+
+template <int LMAX_, int C_, int D_, int E_>
+struct Cfg {
+  static constexpr int LMAX = LMAX_, C = C_, D = D_, E = E_;
+  static constexpr int S = 2, NB = 8, H0 = 2 * S + NB, LDH0 = 16;
+  static constexpr int NLM = (LMAX + 1) * (LMAX + 1);
+  static constexpr int NT = TP<LMAX>::NT, NS = TP<LMAX>::NS;
+  static constexpr int KH = D + C * NS;
+  static constexpr int NW0 = C * (LMAX + 1);
+  static constexpr int CL = C * NLM;
+  static constexpr int LDD = D + 4;   // row strides in shared memory
+  static constexpr int LDH = KH + 4;
+  static constexpr int LDE = E + 4;
+};
+
+AL_DEV int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
+
+// ----------------------------------------------------------------------------
+// Tile GEMM: out[m][n] = sum_k A[m*lda + k] * Wt[k*N + n] for m < kTile, n < N,
+// A in shared memory, Wt in global memory (L1/L2 resident), 256 threads with a
+// TM x TN register tile each; epi(m, n, value) consumes every output once.
+template <int N, int K, class Epi>
+AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__ Wt, Epi&& epi) {
+  constexpr int M = kTile;
+  if constexpr ((M * N) % kThreads != 0) {
+    for (int idx = threadIdx.x; idx < M * N; idx += kThreads) {
+      const int m = idx / N, n = idx % N;
+      float acc = 0.0f;
+#pragma unroll 4
+      for (int k = 0; k < K; ++k) acc = fmaf(A[m * lda + k], __ldg(Wt + k * N + n), acc);
+      epi(m, n, acc);
+    }
+  } else {
+    constexpr int OPT = M * N / kThreads;
+    constexpr int TM = OPT >= 16 ? 2 : 1;
+    constexpr int TN = OPT / TM;
+    static_assert(N % TN == 0, "tile shape");
+    constexpr int TX = N / TN;
+    constexpr int TY = kThreads / TX;
+    static_assert(TY * TM == M, "tile shape");
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    float acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+    const float* wc = Wt + tx * TN;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      float a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = A[(ty + i * TY) * lda + k];
+      if constexpr (TN % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < TN / 4; ++q) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(wc + k * N) + q);
+          b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+        }
+      } else if constexpr (TN % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < TN / 2; ++q) {
+          const float2 v = __ldg(reinterpret_cast<const float2*>(wc + k * N) + q);
+          b[2 * q] = v.x; b[2 * q + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = __ldg(wc + k * N + j);
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) epi(ty + i * TY, tx * TN + j, acc[i][j]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Tile bookkeeping: pair meta data and segments (runs of equal centre atom).
+struct TileMeta {
+  int pi[kTile], pj[kTile], code[kTile], seg[kTile], atom[kTile];
+  int nseg, np, p0;
+};
+
+AL_DEV bool tile_setup(const PassBufs& b, TileMeta& t) {
+  if (*b.flags & 1) return false;   // pair overflow: the list is incomplete
+  const int P = (int)min((int64_t)*b.n_pairs, b.capacity);
+  const int p0 = blockIdx.x * kTile;
+  if (p0 >= P) return false;
+  const int np = min(kTile, P - p0);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int i = -1;
+    if (lane < np) {
+      i = b.pi[p0 + lane];
+      t.pi[lane] = i;
+      t.pj[lane] = b.pj[p0 + lane];
+      t.code[lane] = b.pcode[p0 + lane];
+    } else {
+      t.pi[lane] = 0;
+      t.pj[lane] = 0;
+      t.code[lane] = 62;  // n = 0
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, i, 1);
+    const bool head = lane < np && (lane == 0 || i != prev);
+    const unsigned m = __ballot_sync(0xffffffffu, head);
+    const unsigned below = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    t.seg[lane] = lane < np ? __popc(m & below) - 1 : 0;
+    if (head) t.atom[__popc(m & below) - 1] = i;
+    if (lane == 0) {
+      t.nseg = __popc(m);
+      t.np = np;
+      t.p0 = p0;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Sum of per-(tile, atom) partials of every segment's atom: out[s][x].
+template <int W>
+AL_DEV void load_segments(const float* __restrict__ part, const int* __restrict__ row_ptr,
+                          const TileMeta& t, float* out) {
+  for (int idx = threadIdx.x; idx < t.nseg * W; idx += kThreads) {
+    const int s = idx / W, x = idx % W;
+    const int i = t.atom[s];
+    const int t0 = row_ptr[i] / kTile, t1 = (row_ptr[i + 1] - 1) / kTile;
+    float acc = 0.0f;
+    for (int tt = t0; tt <= t1; ++tt) acc += part[(size_t)(tt + i) * W + x];
+    out[s * W + x] = acc;
+  }
+}
+
+// part[(tile + atom) * W + x] = sum over the segment's pairs of f(p, x).
+template <int W, class F>
+AL_DEV void store_segments(float* __restrict__ part, const TileMeta& t, F&& f) {
+  for (int idx = threadIdx.x; idx < t.nseg * W; idx += kThreads) {
+    const int s = idx / W, x = idx % W;
+    float acc = 0.0f;
+    for (int p = 0; p < t.np; ++p)
+      if (t.seg[p] == s) acc += f(p, x);
+    part[(size_t)(blockIdx.x + t.atom[s]) * W + x] = acc;
+  }
+}
+
+// Copy a kTile x W block of a pair-major global array into shared memory
+// (zero rows past the end of the list).
+template <int W>
+AL_DEV void load_rows(const float* __restrict__ g, const TileMeta& t, float* s, int lds) {
+  for (int idx = threadIdx.x; idx < kTile * W; idx += kThreads) {
+    const int m = idx / W, n = idx % W;
+    s[m * lds + n] = m < t.np ? g[(size_t)(t.p0 + m) * W + n] : 0.0f;
+  }
+}
+
+// Geometry of one pair: unit vector, distance, envelope and SH.
+template <class Cf>
+AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float u[3], float& d,
+                     float& fc, float& dfc, float* Y) {
+  Box box{{b.L[0], b.L[1], b.L[2]}};
+  double dd[3];
+  pair_delta(b.wpos, i, j, code, box, dd);
+  const float dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
+  d = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float inv = 1.0f / d;
+  u[0] = dx * inv;
+  u[1] = dy * inv;
+  u[2] = dz * inv;
+  envelope(d, rc, fc, dfc);
+  sph_harm<Cf::LMAX>(u[0], u[1], u[2], Y);
+}
+
+// Shared-memory carve-up helper.
+struct Carve {
+  float* p;
+  AL_DEV float* take(int n) {
+    float* r = p;
+    p += (n + 3) & ~3;
+    return r;
+  }
+};
+
+// ============================================================================
+// Pass A: geometry, two-body MLP, x0, e^1 -> Gamma^1 partials.
+template <class Cf>
+__global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
+  constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, LDD = Cf::LDD;
+  __shared__ TileMeta t;
+  extern __shared__ float4 smem4[];
+  if (!tile_setup(b, t)) return;
+  Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_h0 = cv.take(kTile * Cf::LDH0);
+  float* s_fc = cv.take(kTile);
+  float* s_Y = cv.take(kTile * NLM);
+  float* s_z1 = cv.take(kTile * LDD);
+  float* s_x = cv.take(kTile * LDD);
+  float* s_e = cv.take(kTile * C);
+  if (threadIdx.x < kTile) {
+    const int p = threadIdx.x;
+    float* h = s_h0 + p * Cf::LDH0;
+    for (int k = 0; k < Cf::LDH0; ++k) h[k] = 0.0f;
+    if (p < t.np) {
+      float u[3], d, fc, dfc, Y[NLM], B[Cf::NB];
+      geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+      bessel<Cf::NB>(d, w.rc, B, nullptr);
+      h[b.species[t.pi[p]]] = 1.0f;
+      h[Cf::S + b.species[t.pj[p]]] = 1.0f;
+      for (int k = 0; k < Cf::NB; ++k) h[2 * Cf::S + k] = B[k];
+      s_fc[p] = fc;
+      for (int k = 0; k < NLM; ++k) s_Y[p * NLM + k] = Y[k];
+    } else {
+      s_fc[p] = 0.0f;
+      for (int k = 0; k < NLM; ++k) s_Y[p * NLM + k] = 0.0f;
+    }
+  }
+  __syncthreads();
+  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
+  __syncthreads();
+  float* X0 = b.X[0];
+  gemm<D, D>(s_z1, LDD, w.tb1.t, [&](int m, int n, float v) {
+    const float x = s_fc[m] * silu(v);
+    s_x[m * LDD + n] = x;
+    if (m < t.np) X0[(size_t)(t.p0 + m) * D + n] = x;
+  });
+  __syncthreads();
+  gemm<C, D>(s_x, LDD, w.layer[0].env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  __syncthreads();
+  store_segments<Cf::CL>(b.gam[1], t, [&](int p, int x) {
+    return s_e[p * C + x / NLM] * s_Y[p * NLM + x % NLM];
+  });
+}
+
+// V^{k-1}_c for one pair and channel: from the stored array, or for k = 1 from
+// w0 (x) Y.
+template <class Cf>
+AL_DEV void load_v(int k, const PassBufs& b, const TileMeta& t, int p, int c, const float* s_w0,
+                   const float* s_Y, float* V) {
+  constexpr int NLM = Cf::NLM;
+  if (k == 1) {
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm)
+      V[lm] = s_w0[p * Cf::NW0 + c * (Cf::LMAX + 1) + l_of(lm)] * s_Y[p * NLM + lm];
+  } else {
+    const float* g = b.V[k - 1] + (size_t)(t.p0 + p) * Cf::CL + c * NLM;
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) V[lm] = p < t.np ? g[lm] : 0.0f;
+  }
+}
+
+// ============================================================================
+// Pass B_k (1 <= k < L): tensor product, mixing, latent MLP, e^{k+1} scatter.
+template <class Cf>
+__global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k) {
+  constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, NT = Cf::NT, NS = Cf::NS, CL = Cf::CL;
+  constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LMAX = Cf::LMAX;
+  using Tp = TP<LMAX>;
+  __shared__ TileMeta t;
+  extern __shared__ float4 smem4[];
+  if (!tile_setup(b, t)) return;
+  Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_h = cv.take(kTile * LDH);
+  float* s_z1 = cv.take(kTile * LDD);
+  float* s_w0 = cv.take(kTile * Cf::NW0);
+  float* s_G = cv.take(kTile * CL);
+  float* s_T = cv.take(kTile * C * NT);
+  float* s_fc = cv.take(kTile);
+  float* s_Y = cv.take(kTile * NLM);
+  float* s_e = cv.take(kTile * C);
+  const LayerW& LW = w.layer[k - 1];
+  if (threadIdx.x < kTile) {
+    const int p = threadIdx.x;
+    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    if (p < t.np) geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+    s_fc[p] = fc;
+    for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
+  }
+  load_rows<D>(b.X[k - 1], t, s_h, LDH);
+  load_segments<CL>(b.gam[k], b.row_ptr, t, s_G);
+  __syncthreads();
+  if (k == 1) {
+    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    __syncthreads();
+  }
+  const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
+  for (int c = sub; c < C; c += kSub) {
+    float V[NLM], G[NLM], T[NT];
+    load_v<Cf>(k, b, t, p, c, s_w0, s_Y, V);
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
+    Tp::fwd(V, G, T);
+#pragma unroll
+    for (int o = 0; o < NT; ++o) s_T[(p * C + c) * NT + o] = T[o];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = T[q];
+  }
+  __syncthreads();
+  // channel mixing: V^k[c'][l3 m] = sum_{c, q} mix_l3[c'][c P + q] T[c][l3 block q m]
+  for (int co = sub; co < C; co += kSub) {
+#pragma unroll
+    for (int l3 = 0; l3 <= LMAX; ++l3) {
+      const int Pl = Tp::P(l3), off = Tp::toff(l3), nm = 2 * l3 + 1;
+      const float* Wm = LW.mix[l3] + co * (C * Pl);
+      for (int m = 0; m < nm; ++m) {
+        float acc = 0.0f;
+        for (int c = 0; c < C; ++c)
+          for (int q = 0; q < Pl; ++q)
+            acc = fmaf(__ldg(Wm + c * Pl + q), s_T[(p * C + c) * NT + off + q * nm + m], acc);
+        if (p < t.np) b.V[k][(size_t)(t.p0 + p) * CL + co * NLM + l3 * l3 + m] = acc;
+      }
+    }
+  }
+  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
+  __syncthreads();
+  float* Xk = b.X[k];
+  gemm<D, D>(s_z1, LDD, LW.lat1.t, [&](int m, int n, float v) {
+    const float x = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;
+    s_h[m * LDH + n] = x;
+    if (m < t.np) Xk[(size_t)(t.p0 + m) * D + n] = x;
+  });
+  __syncthreads();
+  gemm<C, D>(s_h, LDH, w.layer[k].env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  __syncthreads();
+  store_segments<CL>(b.gam[k + 1], t, [&](int pp, int x) {
+    return s_e[pp * C + x / NLM] * s_Y[pp * NLM + x % NLM];
+  });
+}
+
+// Reduce a per-thread value over the kSub consecutive lanes of one pair.
+AL_DEV float sub_sum(float v) {
+#pragma unroll
+  for (int o = kSub / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ============================================================================
+// Pass C: last layer L and energy MLP forward, then their adjoint.
+template <class Cf>
+__global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
+  constexpr int D = Cf::D, C = Cf::C, E = Cf::E, NLM = Cf::NLM, NS = Cf::NS, CL = Cf::CL;
+  constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LDE = Cf::LDE, LMAX = Cf::LMAX;
+  using Tp = TP<LMAX>;
+  __shared__ TileMeta t;
+  __shared__ float s_eij[kTile];
+  __shared__ float s_sig[kTile];
+  extern __shared__ float4 smem4[];
+  if (!tile_setup(b, t)) return;
+  const int L = w.n_layers;
+  const LayerW& LW = w.layer[L - 1];
+  Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_h = cv.take(kTile * LDH);
+  float* s_z1 = cv.take(kTile * LDD);
+  float* s_a1 = cv.take(kTile * LDD);
+  float* s_z2 = cv.take(kTile * LDD);
+  float* s_ze = cv.take(kTile * LDE);
+  float* s_ae = cv.take(kTile * LDE);
+  float* s_G = cv.take(kTile * CL);
+  float* s_dg = cv.take(kTile * CL);
+  float* s_w0 = cv.take(kTile * Cf::NW0);
+  float* s_dw0 = cv.take(kTile * Cf::NW0);
+  float* s_fc = cv.take(kTile);
+  float* s_Y = cv.take(kTile * NLM);
+  float* s_dy = cv.take(kTile * NLM);
+  float* s_du = cv.take(kTile);
+  if (threadIdx.x < kTile) {
+    const int p = threadIdx.x;
+    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    if (p < t.np) geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+    s_fc[p] = fc;
+    for (int q = 0; q < NLM; ++q) {
+      s_Y[p * NLM + q] = Y[q];
+      s_dy[p * NLM + q] = 0.0f;
+    }
+    s_sig[p] = p < t.np ? w.sigma[b.species[t.pi[p]]] : 0.0f;
+  }
+  load_rows<D>(b.X[L - 1], t, s_h, LDH);
+  load_segments<CL>(b.gam[L], b.row_ptr, t, s_G);
+  __syncthreads();
+  if (L == 1) {
+    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    __syncthreads();
+  }
+  const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
+  for (int c = sub; c < C; c += kSub) {
+    float V[NLM], G[NLM], S[NS];
+    load_v<Cf>(L, b, t, p, c, s_w0, s_Y, V);
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
+    Tp::fwd_s(V, G, S);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
+  }
+  __syncthreads();
+  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, [&](int m, int n, float v) {
+    s_z1[m * LDD + n] = v;
+    s_a1[m * LDD + n] = silu(v);
+  });
+  __syncthreads();
+  gemm<D, D>(s_a1, LDD, LW.lat1.t, [&](int m, int n, float v) {
+    s_z2[m * LDD + n] = v;
+    s_h[m * LDH + n] = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;   // x^L
+  });
+  __syncthreads();
+  gemm<E, D>(s_h, LDH, w.e0.t, [&](int m, int n, float v) {
+    s_ze[m * LDE + n] = v;
+    s_ae[m * LDE + n] = silu(v);
+  });
+  __syncthreads();
+  if (threadIdx.x < kTile) {
+    const int q = threadIdx.x;
+    float acc = 0.0f;
+    for (int n = 0; n < E; ++n) acc = fmaf(__ldg(w.eout + n), s_ae[q * LDE + n], acc);
+    s_eij[q] = q < t.np ? acc : 0.0f;
+  }
+  // adjoint of the energy MLP: dE/dE_ij = sigma_{Z_i}
+  for (int idx = threadIdx.x; idx < kTile * E; idx += kThreads) {
+    const int m = idx / E, n = idx % E;
+    s_ze[m * LDE + n] = s_sig[m] * __ldg(w.eout + n) * silu_grad(s_ze[m * LDE + n]);
+  }
+  __syncthreads();
+  if (threadIdx.x < t.nseg) {
+    const int s = threadIdx.x;
+    double acc = 0.0;
+    for (int q = 0; q < t.np; ++q)
+      if (t.seg[q] == s) acc += (double)s_eij[q];
+    b.epart[blockIdx.x + t.atom[s]] = acc;
+  }
+  gemm<D, E>(s_ze, LDE, w.e0.n, [&](int m, int n, float v) { s_h[m * LDH + n] = v; });  // dx^L
+  __syncthreads();
+  {
+    float du = 0.0f;
+    const float fc = s_fc[p];
+    for (int n = sub; n < D; n += kSub) {
+      const float dx = s_h[p * LDH + n];
+      const float z2 = s_z2[p * LDD + n];
+      du = fmaf(dx, silu(z2), du);
+      s_z2[p * LDD + n] = dx * fc * kRsqrt2 * silu_grad(z2);
+    }
+    du = sub_sum(du);
+    if (sub == 0) s_du[p] = du * kRsqrt2;
+  }
+  __syncthreads();
+  gemm<D, D>(s_z2, LDD, LW.lat1.n, [&](int m, int n, float v) {
+    s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
+  });
+  __syncthreads();
+  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, [&](int m, int n, float v) {
+    if (n < D) s_h[m * LDH + n] = v + s_h[m * LDH + n] * kRsqrt2;   // dx^{L-1}
+    else s_h[m * LDH + n] = v;                                      // d(scalars)
+  });
+  __syncthreads();
+  {
+    float dyl[NLM];
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
+    for (int c = sub; c < C; c += kSub) {
+      float V[NLM], G[NLM], dS[NS], dV[NLM], dG[NLM];
+      load_v<Cf>(L, b, t, p, c, s_w0, s_Y, V);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
+        dV[lm] = 0.0f;
+        dG[lm] = 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < NS; ++q) dS[q] = s_h[p * LDH + D + c * NS + q];
+      Tp::bwd_s(V, G, dS, dV, dG);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) s_dg[p * CL + c * NLM + lm] = dG[lm];
+      if (L >= 2) {
+        if (p < t.np) {
+          float* g = b.dV + (size_t)(t.p0 + p) * CL + c * NLM;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) g[lm] = dV[lm];
+        }
+      } else {
+        float dw[LMAX + 1];
+#pragma unroll
+        for (int l = 0; l <= LMAX; ++l) dw[l] = 0.0f;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          dw[l_of(lm)] = fmaf(dV[lm], s_Y[p * NLM + lm], dw[l_of(lm)]);
+          dyl[lm] = fmaf(s_w0[p * Cf::NW0 + c * (LMAX + 1) + l_of(lm)], dV[lm], dyl[lm]);
+        }
+#pragma unroll
+        for (int l = 0; l <= LMAX; ++l) s_dw0[p * Cf::NW0 + c * (LMAX + 1) + l] = dw[l];
+      }
+    }
+    if (L == 1) {
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        const float v = sub_sum(dyl[lm]);
+        if (sub == 0) s_dy[p * NLM + lm] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if (L == 1) {
+    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
+    const int m = idx / D, n = idx % D;
+    b.dX[(size_t)(t.p0 + m) * D + n] = s_h[m * LDH + n];
+  }
+  for (int idx = threadIdx.x; idx < t.np * NLM; idx += kThreads)
+    b.dY[(size_t)t.p0 * NLM + idx] = s_dy[idx];
+  if (threadIdx.x < t.np) b.dU[t.p0 + threadIdx.x] = s_du[threadIdx.x];
+  store_segments<CL>(b.dgam[L], t, [&](int pp, int x) { return s_dg[pp * CL + x]; });
+}
+
+// ============================================================================
+// Pass B_k^T (k = L-1 .. 1): adjoint of the Gamma^{k+1} scatter and of layer k.
+template <class Cf>
+__global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, int k) {
+  constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, NT = Cf::NT, NS = Cf::NS, CL = Cf::CL;
+  constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LMAX = Cf::LMAX;
+  using Tp = TP<LMAX>;
+  __shared__ TileMeta t;
+  extern __shared__ float4 smem4[];
+  if (!tile_setup(b, t)) return;
+  const LayerW& LW = w.layer[k - 1];
+  const LayerW& LN = w.layer[k];
+  Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_h = cv.take(kTile * LDH);
+  float* s_z1 = cv.take(kTile * LDD);
+  float* s_a1 = cv.take(kTile * LDD);
+  float* s_z2 = cv.take(kTile * LDD);
+  float* s_tmp = cv.take(kTile * (CL > LDD ? CL : LDD));
+  float* s_G = cv.take(kTile * CL);
+  float* s_dG = cv.take(kTile * CL);
+  float* s_w0 = cv.take(kTile * Cf::NW0);
+  float* s_dw0 = cv.take(kTile * Cf::NW0);
+  float* s_e = cv.take(kTile * C);
+  float* s_de = cv.take(kTile * C);
+  float* s_fc = cv.take(kTile);
+  float* s_Y = cv.take(kTile * NLM);
+  float* s_dy = cv.take(kTile * NLM);
+  float* s_du = cv.take(kTile);
+  if (threadIdx.x < kTile) {
+    const int p = threadIdx.x;
+    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    if (p < t.np) geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+    s_fc[p] = fc;
+    for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
+  }
+  load_rows<D>(b.X[k], t, s_z2, LDD);          // x^k (temporarily)
+  load_rows<D>(b.X[k - 1], t, s_h, LDH);       // x^{k-1}
+  load_segments<CL>(b.gam[k], b.row_ptr, t, s_G);
+  load_segments<CL>(b.dgam[k + 1], b.row_ptr, t, s_dG);
+  __syncthreads();
+  gemm<C, D>(s_z2, LDD, LN.env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });  // e^{k+1}
+  __syncthreads();
+  const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
+  {
+    const float* dg = s_dG + (p < t.np ? t.seg[p] : 0) * CL;
+    for (int c = sub; c < C; c += kSub) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) acc = fmaf(dg[c * NLM + lm], s_Y[p * NLM + lm], acc);
+      s_de[p * C + c] = p < t.np ? acc : 0.0f;
+    }
+    for (int lm = sub; lm < NLM; lm += kSub) {
+      float acc = 0.0f;
+      for (int c = 0; c < C; ++c) acc = fmaf(dg[c * NLM + lm], s_e[p * C + c], acc);
+      s_dy[p * NLM + lm] = p < t.np ? acc : 0.0f;
+    }
+  }
+  __syncthreads();
+  const float* dXg = b.dX;
+  gemm<D, C>(s_de, C, LN.env.n, [&](int m, int n, float v) {
+    s_z2[m * LDD + n] = v + (m < t.np ? dXg[(size_t)(t.p0 + m) * D + n] : 0.0f);   // dx^k
+  });
+  __syncthreads();
+  // recompute layer k forward (scalars, latent MLP)
+  if (k == 1) {
+    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    __syncthreads();
+  }
+  for (int c = sub; c < C; c += kSub) {
+    float V[NLM], G[NLM], S[NS];
+    load_v<Cf>(k, b, t, p, c, s_w0, s_Y, V);
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
+    Tp::fwd_s(V, G, S);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
+  }
+  __syncthreads();
+  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, [&](int m, int n, float v) {
+    s_z1[m * LDD + n] = v;
+    s_a1[m * LDD + n] = silu(v);
+  });
+  __syncthreads();
+  gemm<D, D>(s_a1, LDD, LW.lat1.t, [&](int m, int n, float v) { s_tmp[m * LDD + n] = v; });  // z2
+  __syncthreads();
+  {
+    float du = 0.0f;
+    const float fc = s_fc[p];
+    for (int n = sub; n < D; n += kSub) {
+      const float dx = s_z2[p * LDD + n];
+      const float z2 = s_tmp[p * LDD + n];
+      du = fmaf(dx, silu(z2), du);
+      s_z2[p * LDD + n] = dx * fc * kRsqrt2 * silu_grad(z2);   // dz2
+      s_h[p * LDH + n] = dx * kRsqrt2;                          // residual part of dx^{k-1}
+    }
+    du = sub_sum(du);
+    if (sub == 0) s_du[p] = du * kRsqrt2;
+  }
+  __syncthreads();
+  load_rows<CL>(b.dV, t, s_tmp, CL);            // dV^k
+  gemm<D, D>(s_z2, LDD, LW.lat1.n, [&](int m, int n, float v) {
+    s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);     // dz1
+  });
+  __syncthreads();
+  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, [&](int m, int n, float v) {
+    if (n < D) s_h[m * LDH + n] += v;
+    else s_h[m * LDH + n] = v;
+  });
+  __syncthreads();
+  // adjoint of mixing and of the full tensor product of layer k
+  {
+    float dyl[NLM];
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
+    for (int c = sub; c < C; c += kSub) {
+      float dT[NT];
+#pragma unroll
+      for (int l3 = 0; l3 <= LMAX; ++l3) {
+        const int Pl = Tp::P(l3), off = Tp::toff(l3), nm = 2 * l3 + 1;
+        for (int q = 0; q < Pl; ++q)
+          for (int m = 0; m < nm; ++m) {
+            float acc = l3 == 0 ? s_h[p * LDH + D + c * NS + q] : 0.0f;
+            for (int co = 0; co < C; ++co)
+              acc = fmaf(__ldg(LW.mix[l3] + co * (C * Pl) + c * Pl + q),
+                         s_tmp[p * CL + co * NLM + l3 * l3 + m], acc);
+            dT[off + q * nm + m] = acc;
+          }
+      }
+      float V[NLM], G[NLM], dV[NLM], dG[NLM];
+      load_v<Cf>(k, b, t, p, c, s_w0, s_Y, V);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
+        dV[lm] = 0.0f;
+        dG[lm] = 0.0f;
+      }
+      Tp::bwd(V, G, dT, dV, dG);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) s_dG[p * CL + c * NLM + lm] = dG[lm];   // reuse
+      if (k >= 2) {
+        if (p < t.np) {
+          float* g = b.dV + (size_t)(t.p0 + p) * CL + c * NLM;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) g[lm] = dV[lm];
+        }
+      } else {
+        float dw[LMAX + 1];
+#pragma unroll
+        for (int l = 0; l <= LMAX; ++l) dw[l] = 0.0f;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          dw[l_of(lm)] = fmaf(dV[lm], s_Y[p * NLM + lm], dw[l_of(lm)]);
+          dyl[lm] = fmaf(s_w0[p * Cf::NW0 + c * (LMAX + 1) + l_of(lm)], dV[lm], dyl[lm]);
+        }
+#pragma unroll
+        for (int l = 0; l <= LMAX; ++l) s_dw0[p * Cf::NW0 + c * (LMAX + 1) + l] = dw[l];
+      }
+    }
+    if (k == 1) {
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        const float v = sub_sum(dyl[lm]);
+        if (sub == 0) s_dy[p * NLM + lm] += v;
+      }
+    }
+  }
+  __syncthreads();
+  if (k == 1) {
+    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
+    const int m = idx / D, n = idx % D;
+    b.dX[(size_t)(t.p0 + m) * D + n] = s_h[m * LDH + n];
+  }
+  for (int idx = threadIdx.x; idx < t.np * NLM; idx += kThreads)
+    b.dY[(size_t)t.p0 * NLM + idx] += s_dy[idx];
+  if (threadIdx.x < t.np) b.dU[t.p0 + threadIdx.x] += s_du[threadIdx.x];
+  store_segments<CL>(b.dgam[k], t, [&](int pp, int x) { return s_dG[pp * CL + x]; });
+}
+
+// ============================================================================
+// Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP and of the
+// geometry; writes g_ij = dE/dDelta_ij.
+template <class Cf>
+__global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
+  constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, CL = Cf::CL, LDD = Cf::LDD, NB = Cf::NB;
+  __shared__ TileMeta t;
+  extern __shared__ float4 smem4[];
+  if (!tile_setup(b, t)) return;
+  Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_h0 = cv.take(kTile * Cf::LDH0);
+  float* s_z1 = cv.take(kTile * LDD);
+  float* s_a1 = cv.take(kTile * LDD);
+  float* s_z2 = cv.take(kTile * LDD);
+  float* s_x = cv.take(kTile * LDD);
+  float* s_dx = cv.take(kTile * LDD);
+  float* s_dG = cv.take(kTile * CL);
+  float* s_e = cv.take(kTile * C);
+  float* s_de = cv.take(kTile * C);
+  float* s_dh0 = cv.take(kTile * Cf::LDH0);
+  float* s_geo = cv.take(kTile * 8);        // u[3], d, fc, dfc
+  float* s_dB = cv.take(kTile * NB);
+  float* s_Y = cv.take(kTile * NLM);
+  float* s_dy = cv.take(kTile * NLM);
+  float* s_du = cv.take(kTile);
+  if (threadIdx.x < kTile) {
+    const int p = threadIdx.x;
+    float* h = s_h0 + p * Cf::LDH0;
+    for (int q = 0; q < Cf::LDH0; ++q) h[q] = 0.0f;
+    float u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f, Y[NLM], B[NB], dB[NB];
+    for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    for (int q = 0; q < NB; ++q) dB[q] = 0.0f;
+    if (p < t.np) {
+      geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+      bessel<NB>(d, w.rc, B, dB);
+      h[b.species[t.pi[p]]] = 1.0f;
+      h[Cf::S + b.species[t.pj[p]]] = 1.0f;
+      for (int q = 0; q < NB; ++q) h[2 * Cf::S + q] = B[q];
+    }
+    float* g = s_geo + p * 8;
+    g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
+    for (int q = 0; q < NB; ++q) s_dB[p * NB + q] = dB[q];
+    for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
+  }
+  load_rows<D>(b.dX, t, s_dx, LDD);
+  load_segments<CL>(b.dgam[1], b.row_ptr, t, s_dG);
+  __syncthreads();
+  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, [&](int m, int n, float v) {
+    s_z1[m * LDD + n] = v;
+    s_a1[m * LDD + n] = silu(v);
+  });
+  __syncthreads();
+  gemm<D, D>(s_a1, LDD, w.tb1.t, [&](int m, int n, float v) {
+    s_z2[m * LDD + n] = v;
+    s_x[m * LDD + n] = s_geo[m * 8 + 4] * silu(v);
+  });
+  __syncthreads();
+  gemm<C, D>(s_x, LDD, w.layer[0].env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  __syncthreads();
+  const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
+  {
+    const float* dg = s_dG + (p < t.np ? t.seg[p] : 0) * CL;
+    for (int c = sub; c < C; c += kSub) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) acc = fmaf(dg[c * NLM + lm], s_Y[p * NLM + lm], acc);
+      s_de[p * C + c] = p < t.np ? acc : 0.0f;
+    }
+    for (int lm = sub; lm < NLM; lm += kSub) {
+      float acc = 0.0f;
+      for (int c = 0; c < C; ++c) acc = fmaf(dg[c * NLM + lm], s_e[p * C + c], acc);
+      s_dy[p * NLM + lm] = p < t.np ? acc : 0.0f;
+    }
+  }
+  __syncthreads();
+  gemm<D, C>(s_de, C, w.layer[0].env.n, [&](int m, int n, float v) { s_dx[m * LDD + n] += v; });
+  __syncthreads();
+  {
+    float du = 0.0f;
+    const float fc = s_geo[p * 8 + 4];
+    for (int n = sub; n < D; n += kSub) {
+      const float dx = s_dx[p * LDD + n];
+      const float z2 = s_z2[p * LDD + n];
+      du = fmaf(dx, silu(z2), du);
+      s_z2[p * LDD + n] = dx * fc * silu_grad(z2);
+    }
+    du = sub_sum(du);
+    if (sub == 0) s_du[p] = du;
+  }
+  __syncthreads();
+  gemm<D, D>(s_z2, LDD, w.tb1.n, [&](int m, int n, float v) {
+    s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
+  });
+  __syncthreads();
+  gemm<Cf::H0, D>(s_z1, LDD, w.tb0.n, [&](int m, int n, float v) { s_dh0[m * Cf::LDH0 + n] = v; });
+  __syncthreads();
+  if (threadIdx.x < t.np) {
+    const int q = threadIdx.x;
+    const float* g = s_geo + q * 8;
+    const float u[3] = {g[0], g[1], g[2]};
+    const float d = g[3], dfc = g[5];
+    const size_t pp = (size_t)(t.p0 + q);
+    float gd = (s_du[q] + b.dU[pp]) * dfc;
+    for (int n = 0; n < NB; ++n) gd = fmaf(s_dh0[q * Cf::LDH0 + 2 * Cf::S + n], s_dB[q * NB + n], gd);
+    float dY[NLM];
+    for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[q * NLM + lm] + b.dY[pp * NLM + lm];
+    float gu[3];
+    sph_harm_vjp<Cf::LMAX>(u[0], u[1], u[2], dY, gu);
+    const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
+    const float inv = 1.0f / d;
+    for (int a = 0; a < 3; ++a) b.G[pp * 3 + a] = gd * u[a] + (gu[a] - ud * u[a]) * inv;
+  }
+}
+
+// ----------------------------------------------------------------------------
+template <class Cf>
+struct Smem {
+  static constexpr int r(int n) { return (n + 3) & ~3; }
+  static constexpr int T = kTile;
+  static constexpr size_t a = 4 * (r(T * Cf::LDH0) + r(T) + r(T * Cf::NLM) + 2 * r(T * Cf::LDD) + r(T * Cf::C));
+  static constexpr size_t b = 4 * (r(T * Cf::LDH) + r(T * Cf::LDD) + r(T * Cf::NW0) + r(T * Cf::CL) +
+                                   r(T * Cf::C * Cf::NT) + r(T) + r(T * Cf::NLM) + r(T * Cf::C));
+  static constexpr size_t c = 4 * (r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + 2 * r(T * Cf::LDE) + 2 * r(T * Cf::CL) +
+                                   2 * r(T * Cf::NW0) + r(T) + 2 * r(T * Cf::NLM) + r(T));
+  static constexpr int tmpw = Cf::CL > Cf::LDD ? Cf::CL : Cf::LDD;
+  static constexpr size_t bb = 4 * (r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + r(T * tmpw) + 2 * r(T * Cf::CL) +
+                                    2 * r(T * Cf::NW0) + 2 * r(T * Cf::C) + r(T) + 2 * r(T * Cf::NLM) + r(T));
+  static constexpr size_t ab = 4 * (r(T * Cf::LDH0) + 5 * r(T * Cf::LDD) + r(T * Cf::CL) + 2 * r(T * Cf::C) +
+                                    r(T * Cf::LDH0) + r(T * 8) + r(T * Cf::NB) + 2 * r(T * Cf::NLM) + r(T));
+};
+
+template <class Cf>
+void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s) {
+  using Sm = Smem<Cf>;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_pass_a<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::a);
+    cudaFuncSetAttribute(k_pass_b<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::b);
+    cudaFuncSetAttribute(k_pass_c<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::c);
+    cudaFuncSetAttribute(k_pass_b_bwd<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::bb);
+    cudaFuncSetAttribute(k_pass_a_bwd<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::ab);
+    init = true;
+  }
+  const int grid = (int)((capacity + kTile - 1) / kTile);
+  const int L = w.n_layers;
+  k_pass_a<Cf><<<grid, kThreads, Sm::a, s>>>(w, b);
+  for (int k = 1; k < L; ++k) k_pass_b<Cf><<<grid, kThreads, Sm::b, s>>>(w, b, k);
+  k_pass_c<Cf><<<grid, kThreads, Sm::c, s>>>(w, b);
+  for (int k = L - 1; k >= 1; --k) k_pass_b_bwd<Cf><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
+  k_pass_a_bwd<Cf><<<grid, kThreads, Sm::ab, s>>>(w, b);
+}
+
+using CfgTiny = Cfg<1, 8, 32, 32>;
+using CfgMain = Cfg<2, 16, 128, 32>;
+
+}  // namespace
+
+int fp32_tile() { return kTile; }
+
+bool fp32_supported(int lmax, int C, int D, int E) {
+  return (lmax == 1 && C == 8 && D == 32 && E == 32) || (lmax == 2 && C == 16 && D == 128 && E == 32);
+}
+
+void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
+                        int64_t capacity, cudaStream_t s) {
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s);
+  else run<CfgMain>(w, b, capacity, s);
+}
+
+}  // namespace al

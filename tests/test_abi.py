@@ -1,0 +1,71 @@
+"""Host-only checks of the C ABI: the library builds, loads, exports every
+function declared in include/allegro.h, and rejects malformed input before
+touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+import paper_2303_08169_gb300 as al
+from paper_2303_08169_gb300 import build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    return al.lib()
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(allegro_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(built):
+    declared = _declared()
+    assert len(declared) >= 13
+    for name in declared:
+        assert hasattr(built, name), name
+    assert set(declared) == set(al.EXPORTED) | (set(declared) - set(al.EXPORTED))
+    assert set(al.EXPORTED) <= set(declared)
+
+
+def test_version(built):
+    assert al.allegro_version().startswith("allegro-gb300")
+
+
+def test_bad_blob_and_mismatch_rejected_on_host(built):
+    mass = np.array([14.007, 1.008])
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_create(b"NOPE" + b"\0" * 100, mass, 4.0, 1, 1)
+    assert e.value.code == 11
+    blob = synth.make_blob(synth.TINY, 1)
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_create(blob, mass, 4.5, 1, 1)          # r_cut disagrees
+    assert e.value.code == 2
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_create(blob[:200], mass, 4.0, 1, 1)    # truncated
+    assert e.value.code == 11
+    odd = synth.ModelConfig(r_cut=4.0, l_max=1, n_layers=1, n_channels=4, latent=(8, 8), energy=(8,))
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_create(synth.make_blob(odd, 1), mass, 4.0, 1, 1)
+    assert e.value.code == 10
+
+
+def test_null_arguments(built):
+    out = ctypes.c_void_p()
+    rc = built.allegro_create(None, 0, None, 2, 4.0, 1, 1, ctypes.byref(out))
+    assert rc == 1
+    assert built.allegro_set_stream(None, None) == 1
+    assert built.allegro_md_step_nve(None, 1.0, 1, None, None) == 1

@@ -1,0 +1,143 @@
+"""GPU energy/forces (FP32 path) vs the FP64 oracle.
+
+Tolerances (FP32 path): |dE| / |E| <= 1e-5 (or |dE| / (N rms E_i) when |E| is
+small), max |dF| / max |F_ref| <= 1e-5, per-atom energies within
+1e-5 * rms(E_i).  Covers the 1-layer l_max 1 model (passes A, C, A^T) and the
+2-layer l_max 2 model (A, B, C, B^T, A^T), small boxes with several images of
+one partner, tile-straddling rows, and sampled atoms of the 110,592-atom
+system."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_2303_08169_gb300 as al
+from oracle.model import OracleModel
+from tests.conftest import energy_scale
+
+pytestmark = pytest.mark.gpu
+MASS = np.array([14.007, 1.008])
+TOL = 1e-5
+
+
+def _blob(name):
+    cfg = synth.TINY if name.startswith("tiny") else synth.MAIN
+    seed = 43 if name.endswith("teacher") else 42
+    return cfg, synth.make_blob(cfg, seed, sigma=energy_scale(name))
+
+
+def _gpu(ctx, pos, sp, cell, precision=al.ALLEGRO_FP32):
+    N = len(pos)
+    p = torch.tensor(pos, device="cuda")
+    s = torch.tensor(sp, device="cuda", dtype=torch.int32)
+    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    Ei = torch.empty(N, dtype=torch.float64, device="cuda")
+    E = al.allegro_energy_forces(ctx, p, s, cell, F, Ei, precision)
+    return E, F.cpu().numpy().astype(np.float64), Ei.cpu().numpy()
+
+
+def _compare(E, F, Ei, Er, Fr, Eir, tol=TOL):
+    N = len(Fr)
+    rms_ei = np.sqrt(np.mean(Eir ** 2))
+    if abs(Er) >= 1e-3 * N:
+        assert abs(E - Er) <= tol * abs(Er), (E, Er)
+    else:
+        assert abs(E - Er) <= tol * N * rms_ei, (E, Er)
+    assert np.abs(Ei - Eir).max() <= tol * max(rms_ei, 1e-12)
+    err = np.abs(F - Fr).max() / np.abs(Fr).max()
+    assert err <= tol, err
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    cfg, blob = _blob("tiny")
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    yield ctx, OracleModel(blob)
+    al.allegro_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def main():
+    cfg, blob = _blob("main")
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    yield ctx, OracleModel(blob)
+    al.allegro_destroy(ctx)
+
+
+def test_tiny_64_atoms(tiny):
+    ctx, orc = tiny
+    pos, sp, cell = synth.make_ammonia(16, 0)
+    E, F, Ei = _gpu(ctx, pos, sp, cell)
+    Er, Fr, Eir, _ = orc.energy_forces(pos, sp, np.diag(cell))
+    _compare(E, F, Ei, Er, Fr, Eir)
+
+
+@pytest.mark.parametrize("n_mol,seed", [(16, 3), (108, 5), (250, 9)])
+def test_main_small_systems(main, n_mol, seed):
+    """64 atoms (several images per partner, rc > L/2), 432 (3 cells), 1000."""
+    ctx, orc = main
+    pos, sp, cell = synth.make_ammonia(n_mol, seed)
+    E, F, Ei = _gpu(ctx, pos, sp, cell)
+    Er, Fr, Eir, _ = orc.energy_forces(pos, sp, np.diag(cell))
+    _compare(E, F, Ei, Er, Fr, Eir)
+
+
+def test_main_6912(main):
+    ctx, orc = main
+    pos, sp, cell = synth.make_ammonia(1728, 0)
+    E, F, Ei = _gpu(ctx, pos, sp, cell)
+    Er, Fr, Eir, _ = orc.energy_forces(pos, sp, np.diag(cell))
+    _compare(E, F, Ei, Er, Fr, Eir)
+    assert abs(np.sqrt(np.mean(Fr ** 2)) - 1.0) < 1e-6          # calibrated force scale
+
+
+def test_host_buffers_and_determinism(main):
+    ctx, orc = main
+    pos, sp, cell = synth.make_ammonia(108, 2)
+    N = len(pos)
+    F1 = np.zeros((N, 3), np.float32)
+    E1 = al.allegro_energy_forces(ctx, pos, sp.astype(np.int32), cell, F1, None)
+    E2, F2, _ = _gpu(ctx, pos, sp, cell)
+    assert E1 == E2 and np.array_equal(F1.astype(np.float64), F2)   # bitwise rerun
+
+
+def test_sampled_atoms_110592(main):
+    ctx, orc = main
+    pos, sp, cell = synth.make_ammonia(27648, 0)
+    E, F, Ei = _gpu(ctx, pos, sp, cell)
+    rng = np.random.default_rng(1)
+    fmax = 0.0
+    errs = []
+    for k in rng.choice(len(pos), 12, replace=False):
+        ek, fk = orc.local_energy_force(pos, sp, np.diag(cell), int(k))
+        errs.append(np.abs(F[k] - fk).max())
+        fmax = max(fmax, np.abs(fk).max())
+        assert abs(Ei[k] - ek) <= 1e-5 * max(1.0, abs(ek)) + 1e-6
+    assert max(errs) <= 1e-5 * max(fmax, 1.0)
+    assert np.abs(F.sum(0)).max() <= 1e-3 * np.sqrt(len(pos))   # net force ~ 0
+
+
+def test_invalid_inputs(main):
+    ctx, _ = main
+    pos, sp, cell = synth.make_ammonia(16, 0)
+    bad = sp.copy().astype(np.int32)
+    bad[3] = 7
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_energy_forces(ctx, pos, bad, cell)
+    assert e.value.code == 1
+    tri = cell.copy()
+    tri[0, 1] = 0.5
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_energy_forces(ctx, pos, sp.astype(np.int32), tri)
+    assert e.value.code == 4
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_energy_forces(ctx, pos, sp.astype(np.int32), np.diag([2.0, 2.0, 2.0]))
+    assert e.value.code == 3
+    p = pos.copy()
+    p[5, 1] = np.nan
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_energy_forces(ctx, p, sp.astype(np.int32), cell)
+    assert e.value.code == 7
+    # the context stays usable after each rejected call
+    E, F, Ei = _gpu(ctx, pos, sp, cell)
+    assert np.isfinite(E)

@@ -1,0 +1,85 @@
+"""GPU NVE velocity Verlet (Eq. 1, Sec. 3.2) and the >5 sigma outlier count
+(Fig. 1 caption) vs the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_2303_08169_gb300 as al
+from oracle.md import kinetic_energy, outlier_count, velocity_verlet
+from oracle.model import OracleModel
+from tests.conftest import energy_scale
+
+pytestmark = pytest.mark.gpu
+MASS = np.array([14.007, 1.008])
+
+
+def test_outlier_count_matches_bruteforce():
+    cfg = synth.TINY
+    ctx = al.allegro_create(synth.make_blob(cfg, 42), MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    rng = np.random.default_rng(0)
+    for n in (1, 7, 1000, 100_000):
+        F = rng.standard_t(3, size=(n, 3)).astype(np.float32)
+        for thr in (5.0, 2.0):
+            c = al.allegro_outlier_count(ctx, torch.tensor(F, device="cuda"), thr)
+            f = F.astype(np.float64).ravel()
+            sigma = np.sqrt(np.mean(f * f))
+            near = np.abs(np.abs(f) - thr * sigma) <= 1e-9 * thr * sigma
+            ref = outlier_count(F, thr)
+            assert abs(c - ref) <= int(near.sum())
+    al.allegro_destroy(ctx)
+
+
+def test_tiny_nve_matches_oracle_trajectory():
+    cfg = synth.TINY
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("tiny"))
+    orc = OracleModel(blob)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(16, 0)
+    L = np.diag(cell)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    n = 20
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    out = torch.zeros(n, dtype=torch.int64, device="cuda")
+    en = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    al.allegro_md_step_nve(ctx, 0.5, n, out, en)
+    P = np.zeros((len(pos), 3))
+    V = np.zeros((len(pos), 3))
+    step = al.allegro_md_get_state(ctx, P, V)
+    assert step == n
+    ref = velocity_verlet(lambda p: orc.energy_forces(p, sp, L)[:2], pos, v0, MASS[sp], L, 0.5, n)
+    en = en.cpu().numpy()
+    # FP32 forces drive an FP64 integrator: trajectories agree to ~1e-6 over 20 steps
+    d = P - ref["pos"]
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() < 1e-5
+    assert np.abs(V - ref["vel"]).max() < 1e-5
+    np.testing.assert_allclose(en[:, 0], ref["epot"], rtol=0, atol=1e-4 * abs(ref["epot"]).max())
+    np.testing.assert_allclose(en[:, 1], ref["ekin"], rtol=1e-5, atol=1e-7)
+    assert np.array_equal(out.cpu().numpy(), ref["outliers"]) or \
+        np.abs(out.cpu().numpy() - ref["outliers"]).max() <= 1
+    assert abs(kinetic_energy(V, MASS[sp]) - en[-1, 1]) < 1e-9 * en[-1, 1]
+    al.allegro_destroy(ctx)
+
+
+def test_md_6912_energy_conservation_and_resume():
+    cfg = synth.MAIN
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(1728, 0)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    e1 = np.zeros((50, 3))
+    o1 = np.zeros(50, np.int64)
+    al.allegro_md_step_nve(ctx, 0.25, 50, o1, e1)
+    kT = 8.617333e-5 * 200.0
+    assert np.abs(e1[:, 2] - e1[0, 2]).max() / (len(sp) * kT) < 0.05
+    assert np.all(o1 >= 0) and np.all(o1 < 3 * len(sp))
+    # resume: two calls of 25 steps equal one call of 50 (bitwise, deterministic kernels)
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    e2 = np.zeros((25, 3))
+    al.allegro_md_step_nve(ctx, 0.25, 25, None, e2)
+    e3 = np.zeros((25, 3))
+    al.allegro_md_step_nve(ctx, 0.25, 25, None, e3)
+    assert np.array_equal(np.concatenate([e2, e3]), e1)
+    al.allegro_destroy(ctx)
