@@ -196,4 +196,4 @@ class OracleModel:
         inner[kk] = True
         Esub = Ei[inner].sum()
         (g,) = torch.autograd.grad(Esub, r)
-        return float(Ei[kk]), -g[kk].numpy()
+        return float(Ei[kk].detach()), -g[kk].numpy()

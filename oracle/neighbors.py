@@ -134,7 +134,10 @@ def pairs_auto(pos, lengths, r_cut):
     nimg = 1
     for r in _image_range(lengths, r_cut):
         nimg *= 2 * r + 1
-    if n * n * nimg <= 4_000_000:
+    ncell = 1
+    for L in lengths:
+        ncell *= max(1, int(math.floor(float(L) / r_cut)))
+    if n * n * nimg <= 4_000_000 or ncell > 4 * n:     # small or sparse: brute force
         return pairs_bruteforce(pos, lengths, r_cut)
     return pairs_cells(pos, lengths, r_cut)
 
