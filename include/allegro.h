@@ -180,6 +180,28 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps,
 int allegro_md_get_state(allegro_ctx* ctx, double* positions,
                          double* velocities, float* forces, int64_t* step);
 
+/* Keys of allegro_query. */
+#define ALLEGRO_Q_N_PAIRS      0  /* ordered pairs of the last neighbour build   */
+#define ALLEGRO_Q_CAPACITY     1  /* pair capacity currently allocated           */
+#define ALLEGRO_Q_STEP_KERNELS 2  /* kernel launches in one captured MD step     */
+#define ALLEGRO_Q_N_ATOMS      3  /* atoms of the current state                  */
+
+/* Read one integer property of the context into *value (host). */
+int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);
+
+/*
+ * Instrumentation (not part of the paper's method): mean device time in ms of
+ * each phase of one energy+forces evaluation at the current MD state, over
+ * n_reps evaluations timed with CUDA events on the context stream:
+ *   ms_out[0] neighbour build   [1] pass A (two-body)   [2] passes B (layers
+ *   below the last)   [3] pass C (last layer + energy, forward and adjoint)
+ *   [4] passes B^T   [5] pass A^T (+ geometry adjoint)   [6] force assembly
+ *   and reductions.
+ * ms_out: host, n_out >= 7.  The MD state is unchanged (the evaluation is
+ * deterministic).  Requires allegro_md_init.
+ */
+int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_t n_out);
+
 #ifdef __cplusplus
 }
 #endif

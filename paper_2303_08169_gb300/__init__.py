@@ -27,7 +27,14 @@ EXPORTED = [
     "allegro_last_error", "allegro_build_neighbors", "allegro_get_neighbors",
     "allegro_energy_forces", "allegro_outlier_count", "allegro_md_init",
     "allegro_set_md_precision", "allegro_md_step_nve", "allegro_md_get_state",
+    "allegro_query", "allegro_phase_times",
 ]
+
+ALLEGRO_Q_N_PAIRS = 0
+ALLEGRO_Q_CAPACITY = 1
+ALLEGRO_Q_STEP_KERNELS = 2
+ALLEGRO_Q_N_ATOMS = 3
+PHASES = ["neighbors", "pass_a", "pass_b", "pass_c", "pass_b_adjoint", "pass_a_adjoint", "forces"]
 
 
 class AllegroError(RuntimeError):
@@ -63,6 +70,8 @@ def lib():
         "allegro_set_md_precision": ([_vp, _i32], ctypes.c_int),
         "allegro_md_step_nve": ([_vp, _f64, _i32, _vp, _vp], ctypes.c_int),
         "allegro_md_get_state": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_i64)], ctypes.c_int),
+        "allegro_query": ([_vp, _i32, ctypes.POINTER(_i64)], ctypes.c_int),
+        "allegro_phase_times": ([_vp, _i32, _vp, _i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -169,6 +178,19 @@ def allegro_md_get_state(ctx, positions=None, velocities=None, forces=None):
     s = _i64()
     _check(ctx, lib().allegro_md_get_state(ctx, _ptr(positions), _ptr(velocities), _ptr(forces), ctypes.byref(s)))
     return s.value
+
+
+def allegro_query(ctx, what):
+    v = _i64()
+    _check(ctx, lib().allegro_query(ctx, int(what), ctypes.byref(v)))
+    return v.value
+
+
+def allegro_phase_times(ctx, n_reps=10):
+    """Mean ms per phase (keys of PHASES) of one energy+forces evaluation."""
+    out = np.zeros(len(PHASES))
+    _check(ctx, lib().allegro_phase_times(ctx, int(n_reps), _ptr(out), len(PHASES)))
+    return dict(zip(PHASES, out.tolist()))
 
 
 __all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED

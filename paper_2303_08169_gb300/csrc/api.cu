@@ -143,6 +143,7 @@ struct allegro_ctx {
   long long step = 0;
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
+  int64_t graph_kernels = 0;
   // rollback snapshot
   double* d_pos_snap = nullptr;
   double* d_v_snap = nullptr;
@@ -707,6 +708,15 @@ int capture_step(allegro_ctx* c, double dt) {
     if (own) cudaStreamDestroy(cs);
     return cuda_check(c, "end capture");
   }
+  size_t n_nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &n_nodes);
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+  c->graph_kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) c->graph_kernels++;
+  }
   e = cudaGraphInstantiate(&c->graph, g, 0);
   cudaGraphDestroy(g);
   if (own) cudaStreamDestroy(cs);
@@ -771,6 +781,58 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
     return ALLEGRO_OK;
   }
   return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown during MD");
+}
+
+int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
+  if (!ctx || !value) return ALLEGRO_E_INVALID_ARG;
+  switch (what) {
+    case ALLEGRO_Q_N_PAIRS: {
+      int np = 0;
+      if (ctx->nb.n_pairs) {
+        cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "query");
+      }
+      *value = np;
+      return ALLEGRO_OK;
+    }
+    case ALLEGRO_Q_CAPACITY: *value = ctx->capacity; return ALLEGRO_OK;
+    case ALLEGRO_Q_STEP_KERNELS: *value = ctx->graph_kernels; return ALLEGRO_OK;
+    case ALLEGRO_Q_N_ATOMS: *value = ctx->n_atoms; return ALLEGRO_OK;
+    default: return ctx->fail(ALLEGRO_E_INVALID_ARG, "unknown query key");
+  }
+}
+
+int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_t n_out) {
+  if (!ctx || !ms_out || n_out < 7 || n_reps < 1) return ALLEGRO_E_INVALID_ARG;
+  if (!ctx->md_ready) return ctx->fail(ALLEGRO_E_INVALID_ARG, "md_init first");
+  cudaEvent_t ev[8];
+  for (auto& e : ev) cudaEventCreate(&e);
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double L[3] = {ctx->grid.L[0], ctx->grid.L[1], ctx->grid.L[2]};
+  fill_passbufs(ctx, L);
+  const Blob& B = ctx->blob;
+  int rc = ALLEGRO_OK;
+  for (int r = 0; r < n_reps && !rc; ++r) {
+    cudaEventRecord(ev[0], ctx->stream);
+    launch_build_neighbors(ctx->nb, ctx->grid, ctx->d_pos, ctx->n_atoms, ctx->stream);
+    fp32_energy_forces((int)B.lmax, (int)B.C, ctx->D, ctx->E, ctx->w, ctx->pb, ctx->capacity, ctx->stream, ev + 1);
+    launch_forces(atom_args(ctx), ctx->nb.row_ptr, ctx->nb.rev, ctx->pb.G, ctx->pb.epart, fp32_tile(), ctx->d_F,
+                  ctx->d_Ei, ctx->d_blk, ctx->d_stats, ctx->nb.flags, ctx->stream);
+    cudaEventRecord(ev[7], ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      rc = cuda_check(ctx, "phase times");
+      break;
+    }
+    for (int k = 0; k < 7; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (int k = 0; k < 7; ++k) ms_out[k] = acc[k] / n_reps;
+  return ALLEGRO_OK;
 }
 
 int allegro_md_get_state(allegro_ctx* ctx, double* positions, double* velocities, float* forces, int64_t* step) {

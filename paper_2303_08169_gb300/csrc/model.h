@@ -65,8 +65,10 @@ struct PassBufs {
 // FP32 path: one launcher per pass sequence; templated on the model shape in
 // the .cu file, dispatched by (lmax, C, D, E).
 bool fp32_supported(int lmax, int C, int D, int E);
+// ev (optional, 6 events): recorded before pass A, after A, after the B
+// passes, after C, after the B^T passes and after A^T.
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
-                        int64_t capacity, cudaStream_t s);
+                        int64_t capacity, cudaStream_t s, cudaEvent_t* ev = nullptr);
 int fp32_tile();
 
 }  // namespace al

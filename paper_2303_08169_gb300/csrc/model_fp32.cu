@@ -886,7 +886,7 @@ struct Smem {
 };
 
 template <class Cf>
-void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s) {
+void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
   using Sm = Smem<Cf>;
   static bool init = false;
   if (!init) {
@@ -899,11 +899,20 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s) {
   }
   const int grid = (int)((capacity + kTile - 1) / kTile);
   const int L = w.n_layers;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], s);
+  };
+  mark(0);
   k_pass_a<Cf><<<grid, kThreads, Sm::a, s>>>(w, b);
+  mark(1);
   for (int k = 1; k < L; ++k) k_pass_b<Cf><<<grid, kThreads, Sm::b, s>>>(w, b, k);
+  mark(2);
   k_pass_c<Cf><<<grid, kThreads, Sm::c, s>>>(w, b);
+  mark(3);
   for (int k = L - 1; k >= 1; --k) k_pass_b_bwd<Cf><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
+  mark(4);
   k_pass_a_bwd<Cf><<<grid, kThreads, Sm::ab, s>>>(w, b);
+  mark(5);
 }
 
 using CfgTiny = Cfg<1, 8, 32, 32>;
@@ -918,9 +927,9 @@ bool fp32_supported(int lmax, int C, int D, int E) {
 }
 
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
-                        int64_t capacity, cudaStream_t s) {
-  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s);
-  else run<CfgMain>(w, b, capacity, s);
+                        int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s, ev);
+  else run<CfgMain>(w, b, capacity, s, ev);
 }
 
 }  // namespace al
