@@ -110,7 +110,7 @@ AL_DEV void envelope(float d, float rc, float& u, float& du) {
   du = x5 * (-168.0f + x * (336.0f - 168.0f * x)) / rc;
 }
 
-AL_DEV float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
+AL_DEV float sigmoidf_(float z) { return __frcp_rn(1.0f + __expf(-z)); }
 AL_DEV float silu(float z) { return z * sigmoidf_(z); }
 // d silu / dz = s (1 + z (1 - s)), s = sigmoid(z)
 AL_DEV float silu_grad(float z) {

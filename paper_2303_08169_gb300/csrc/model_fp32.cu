@@ -38,6 +38,34 @@ constexpr int kThreads = 256;   // 8 threads per pair in per-pair phases
 constexpr int kSub = kThreads / kTile;
 constexpr float kRsqrt2 = 0.70710678118654752f;
 
+// ----------------------------------------------------------------------------
+// Weight staging: K-chunks of kKC rows of a [K][N] matrix are copied into a
+// double-buffered shared-memory ring with cp.async while the previous chunk
+// is consumed.
+constexpr int kKC = 16;
+
+AL_DEV void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+AL_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int n>
+AL_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(n)); }
+
+// Stage n floats (n % 4 == 0, 16-byte aligned source) into shared memory.
+AL_DEV void stage(float* dst, const float* __restrict__ src, int n) {
+  for (int q = threadIdx.x; q < n / 4; q += kThreads) cp_async16(dst + 4 * q, src + 4 * q);
+}
+
+template <int N, int K>
+AL_DEV void load_chunk(float* wbuf, const float* __restrict__ Wt, int ch) {
+  const int k0 = ch * kKC;
+  const int kc = min(kKC, K - k0);
+  stage(wbuf + (ch & 1) * kKC * N, Wt + (size_t)k0 * N, kc * N);
+  cp_async_commit();
+}
+
+
 template <int LMAX> struct TP;
 template <> struct TP<1> {
   static constexpr int NT = TP1_NT, NS = TP1_NS;
@@ -70,24 +98,70 @@ struct Cfg {
   static constexpr int LDD = D + 4;   // row strides in shared memory
   static constexpr int LDH = KH + 4;
   static constexpr int LDE = E + 4;
+  static constexpr int WB = 2 * kKC * (KH > D ? KH : D);   // weight staging ring
+  static constexpr int MIXW = C * C * (LMAX == 1 ? 4 : 11); // all mixing matrices
 };
 
 AL_DEV int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
 
-// ----------------------------------------------------------------------------
-// Tile GEMM: out[m][n] = sum_k A[m*lda + k] * Wt[k*N + n] for m < kTile, n < N,
-// A in shared memory, Wt in global memory (L1/L2 resident), 256 threads with a
-// TM x TN register tile each; epi(m, n, value) consumes every output once.
+// Offset of mix_l inside the concatenated shared-memory copy of the mixing
+// matrices ([C][C P_l] each, l = 0 .. l_max).
+template <class Cf>
+AL_DEV int mix_off(int l) {
+  int o = 0;
+  for (int q = 0; q < l; ++q) o += Cf::C * Cf::C * TP<Cf::LMAX>::P(q);
+  return o;
+}
+
+template <class Cf>
+AL_DEV void stage_mix(const LayerW& LW, float* s_mix) {
+  for (int l = 0; l <= Cf::LMAX; ++l)
+    stage(s_mix + mix_off<Cf>(l), LW.mix[l], Cf::C * Cf::C * TP<Cf::LMAX>::P(l));
+  cp_async_commit();
+}
+
+// Tile GEMM: out[m][n] = sum_k A[m*lda + k] * Wt[k*N + n] for m < kTile, n < N.
+// A in shared memory, Wt ([K][N], 16-byte aligned) staged through wbuf
+// (>= 2 kKC N floats of shared memory); 256 threads with a TM x TN register
+// tile each; epi(m, n, value) consumes every output once.  All threads of the
+// block must call it; it begins and ends with a block barrier.
 template <int N, int K, class Epi>
-AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__ Wt, Epi&& epi) {
+AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__ Wt, float* wbuf,
+                 Epi&& epi) {
   constexpr int M = kTile;
+  constexpr int NCH = (K + kKC - 1) / kKC;
+  static_assert(N % 4 == 0, "weights are staged in 16-byte units");
+  __syncthreads();
+  load_chunk<N, K>(wbuf, Wt, 0);
   if constexpr ((M * N) % kThreads != 0) {
-    for (int idx = threadIdx.x; idx < M * N; idx += kThreads) {
-      const int m = idx / N, n = idx % N;
-      float acc = 0.0f;
-#pragma unroll 4
-      for (int k = 0; k < K; ++k) acc = fmaf(A[m * lda + k], __ldg(Wt + k * N + n), acc);
-      epi(m, n, acc);
+    constexpr int R = (M * N + kThreads - 1) / kThreads;
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+    for (int ch = 0; ch < NCH; ++ch) {
+      if (ch + 1 < NCH) {
+        load_chunk<N, K>(wbuf, Wt, ch + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const float* wb = wbuf + (ch & 1) * kKC * N;
+      const int k0 = ch * kKC, kc = min(kKC, K - k0);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        if (idx < M * N) {
+          const int m = idx / N, n = idx % N;
+          for (int k = 0; k < kc; ++k) acc[r] = fmaf(A[m * lda + k0 + k], wb[k * N + n], acc[r]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = threadIdx.x + r * kThreads;
+      if (idx < M * N) epi(idx / N, idx % N, acc[r]);
     }
   } else {
     constexpr int OPT = M * N / kThreads;
@@ -103,32 +177,49 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
-    const float* wc = Wt + tx * TN;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      float a[TM], b[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = A[(ty + i * TY) * lda + k];
-      if constexpr (TN % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < TN / 4; ++q) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(wc + k * N) + q);
-          b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
-        }
-      } else if constexpr (TN % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < TN / 2; ++q) {
-          const float2 v = __ldg(reinterpret_cast<const float2*>(wc + k * N) + q);
-          b[2 * q] = v.x; b[2 * q + 1] = v.y;
-        }
+    for (int ch = 0; ch < NCH; ++ch) {
+      if (ch + 1 < NCH) {
+        load_chunk<N, K>(wbuf, Wt, ch + 1);
+        cp_async_wait<1>();
       } else {
-#pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = __ldg(wc + k * N + j);
+        cp_async_wait<0>();
       }
+      __syncthreads();
+      const float* wc = wbuf + (ch & 1) * kKC * N + tx * TN;
+      const int k0 = ch * kKC;
+      const float* a0 = A + ty * lda + k0;
+      auto step = [&](int k) {
+        float a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TM; ++i) a[i] = a0[i * TY * lda + k];
+        if constexpr (TN % 4 == 0) {
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          for (int q = 0; q < TN / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(wc + k * N)[q];
+            b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+          }
+        } else if constexpr (TN % 2 == 0) {
+#pragma unroll
+          for (int q = 0; q < TN / 2; ++q) {
+            const float2 v = reinterpret_cast<const float2*>(wc + k * N)[q];
+            b[2 * q] = v.x; b[2 * q + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < TN; ++j) b[j] = wc[k * N + j];
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      };
+      if (K - k0 >= kKC) {
+#pragma unroll
+        for (int k = 0; k < kKC; ++k) step(k);
+      } else {
+        for (int k = 0; k < K - k0; ++k) step(k);
+      }
+      __syncthreads();
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -251,6 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_wb = cv.take(Cf::WB);
   float* s_h0 = cv.take(kTile * Cf::LDH0);
   float* s_fc = cv.take(kTile);
   float* s_Y = cv.take(kTile * NLM);
@@ -276,16 +368,16 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
     }
   }
   __syncthreads();
-  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
+  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
   __syncthreads();
   float* X0 = b.X[0];
-  gemm<D, D>(s_z1, LDD, w.tb1.t, [&](int m, int n, float v) {
+  gemm<D, D>(s_z1, LDD, w.tb1.t, s_wb, [&](int m, int n, float v) {
     const float x = s_fc[m] * silu(v);
     s_x[m * LDD + n] = x;
     if (m < t.np) X0[(size_t)(t.p0 + m) * D + n] = x;
   });
   __syncthreads();
-  gemm<C, D>(s_x, LDD, w.layer[0].env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  gemm<C, D>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
   __syncthreads();
   store_segments<Cf::CL>(b.gam[1], t, [&](int p, int x) {
     return s_e[p * C + x / NLM] * s_Y[p * NLM + x % NLM];
@@ -320,6 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_wb = cv.take(Cf::WB);
   float* s_h = cv.take(kTile * LDH);
   float* s_z1 = cv.take(kTile * LDD);
   float* s_w0 = cv.take(kTile * Cf::NW0);
@@ -328,7 +421,9 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
   float* s_fc = cv.take(kTile);
   float* s_Y = cv.take(kTile * NLM);
   float* s_e = cv.take(kTile * C);
+  float* s_mix = cv.take(Cf::MIXW);
   const LayerW& LW = w.layer[k - 1];
+  stage_mix<Cf>(LW, s_mix);
   if (threadIdx.x < kTile) {
     const int p = threadIdx.x;
     float u[3], d, fc = 0.0f, dfc, Y[NLM];
@@ -341,7 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
   load_segments<CL>(b.gam[k], b.row_ptr, t, s_G);
   __syncthreads();
   if (k == 1) {
-    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -356,32 +451,33 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
 #pragma unroll
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = T[q];
   }
+  cp_async_wait<0>();
   __syncthreads();
   // channel mixing: V^k[c'][l3 m] = sum_{c, q} mix_l3[c'][c P + q] T[c][l3 block q m]
   for (int co = sub; co < C; co += kSub) {
 #pragma unroll
     for (int l3 = 0; l3 <= LMAX; ++l3) {
       const int Pl = Tp::P(l3), off = Tp::toff(l3), nm = 2 * l3 + 1;
-      const float* Wm = LW.mix[l3] + co * (C * Pl);
+      const float* Wm = s_mix + mix_off<Cf>(l3) + co * (C * Pl);
       for (int m = 0; m < nm; ++m) {
         float acc = 0.0f;
         for (int c = 0; c < C; ++c)
           for (int q = 0; q < Pl; ++q)
-            acc = fmaf(__ldg(Wm + c * Pl + q), s_T[(p * C + c) * NT + off + q * nm + m], acc);
+            acc = fmaf(Wm[c * Pl + q], s_T[(p * C + c) * NT + off + q * nm + m], acc);
         if (p < t.np) b.V[k][(size_t)(t.p0 + p) * CL + co * NLM + l3 * l3 + m] = acc;
       }
     }
   }
-  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
+  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
   __syncthreads();
   float* Xk = b.X[k];
-  gemm<D, D>(s_z1, LDD, LW.lat1.t, [&](int m, int n, float v) {
+  gemm<D, D>(s_z1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) {
     const float x = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;
     s_h[m * LDH + n] = x;
     if (m < t.np) Xk[(size_t)(t.p0 + m) * D + n] = x;
   });
   __syncthreads();
-  gemm<C, D>(s_h, LDH, w.layer[k].env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  gemm<C, D>(s_h, LDH, w.layer[k].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
   __syncthreads();
   store_segments<CL>(b.gam[k + 1], t, [&](int pp, int x) {
     return s_e[pp * C + x / NLM] * s_Y[pp * NLM + x % NLM];
@@ -410,6 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   const int L = w.n_layers;
   const LayerW& LW = w.layer[L - 1];
   Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_wb = cv.take(Cf::WB);
   float* s_h = cv.take(kTile * LDH);
   float* s_z1 = cv.take(kTile * LDD);
   float* s_a1 = cv.take(kTile * LDD);
@@ -440,7 +537,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   load_segments<CL>(b.gam[L], b.row_ptr, t, s_G);
   __syncthreads();
   if (L == 1) {
-    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -454,17 +551,17 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
   }
   __syncthreads();
-  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, [&](int m, int n, float v) {
+  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D>(s_a1, LDD, LW.lat1.t, [&](int m, int n, float v) {
+  gemm<D, D>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) {
     s_z2[m * LDD + n] = v;
     s_h[m * LDH + n] = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;   // x^L
   });
   __syncthreads();
-  gemm<E, D>(s_h, LDH, w.e0.t, [&](int m, int n, float v) {
+  gemm<E, D>(s_h, LDH, w.e0.t, s_wb, [&](int m, int n, float v) {
     s_ze[m * LDE + n] = v;
     s_ae[m * LDE + n] = silu(v);
   });
@@ -488,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
       if (t.seg[q] == s) acc += (double)s_eij[q];
     b.epart[blockIdx.x + t.atom[s]] = acc;
   }
-  gemm<D, E>(s_ze, LDE, w.e0.n, [&](int m, int n, float v) { s_h[m * LDH + n] = v; });  // dx^L
+  gemm<D, E>(s_ze, LDE, w.e0.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] = v; });  // dx^L
   __syncthreads();
   {
     float du = 0.0f;
@@ -503,11 +600,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     if (sub == 0) s_du[p] = du * kRsqrt2;
   }
   __syncthreads();
-  gemm<D, D>(s_z2, LDD, LW.lat1.n, [&](int m, int n, float v) {
+  gemm<D, D>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
-  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, [&](int m, int n, float v) {
+  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, float v) {
     if (n < D) s_h[m * LDH + n] = v + s_h[m * LDH + n] * kRsqrt2;   // dx^{L-1}
     else s_h[m * LDH + n] = v;                                      // d(scalars)
   });
@@ -559,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   }
   __syncthreads();
   if (L == 1) {
-    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
+    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
@@ -585,6 +682,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   const LayerW& LW = w.layer[k - 1];
   const LayerW& LN = w.layer[k];
   Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_wb = cv.take(Cf::WB);
   float* s_h = cv.take(kTile * LDH);
   float* s_z1 = cv.take(kTile * LDD);
   float* s_a1 = cv.take(kTile * LDD);
@@ -600,6 +698,8 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   float* s_Y = cv.take(kTile * NLM);
   float* s_dy = cv.take(kTile * NLM);
   float* s_du = cv.take(kTile);
+  float* s_mix = cv.take(Cf::MIXW);
+  stage_mix<Cf>(LW, s_mix);
   if (threadIdx.x < kTile) {
     const int p = threadIdx.x;
     float u[3], d, fc = 0.0f, dfc, Y[NLM];
@@ -608,12 +708,13 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     s_fc[p] = fc;
     for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
   }
+  cp_async_wait<0>();
   load_rows<D>(b.X[k], t, s_z2, LDD);          // x^k (temporarily)
   load_rows<D>(b.X[k - 1], t, s_h, LDH);       // x^{k-1}
   load_segments<CL>(b.gam[k], b.row_ptr, t, s_G);
   load_segments<CL>(b.dgam[k + 1], b.row_ptr, t, s_dG);
   __syncthreads();
-  gemm<C, D>(s_z2, LDD, LN.env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });  // e^{k+1}
+  gemm<C, D>(s_z2, LDD, LN.env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });  // e^{k+1}
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   {
@@ -632,13 +733,13 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   }
   __syncthreads();
   const float* dXg = b.dX;
-  gemm<D, C>(s_de, C, LN.env.n, [&](int m, int n, float v) {
+  gemm<D, C>(s_de, C, LN.env.n, s_wb, [&](int m, int n, float v) {
     s_z2[m * LDD + n] = v + (m < t.np ? dXg[(size_t)(t.p0 + m) * D + n] : 0.0f);   // dx^k
   });
   __syncthreads();
   // recompute layer k forward (scalars, latent MLP)
   if (k == 1) {
-    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   for (int c = sub; c < C; c += kSub) {
@@ -651,12 +752,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
   }
   __syncthreads();
-  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, [&](int m, int n, float v) {
+  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D>(s_a1, LDD, LW.lat1.t, [&](int m, int n, float v) { s_tmp[m * LDD + n] = v; });  // z2
+  gemm<D, D>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) { s_tmp[m * LDD + n] = v; });  // z2
   __syncthreads();
   {
     float du = 0.0f;
@@ -673,11 +774,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   }
   __syncthreads();
   load_rows<CL>(b.dV, t, s_tmp, CL);            // dV^k
-  gemm<D, D>(s_z2, LDD, LW.lat1.n, [&](int m, int n, float v) {
+  gemm<D, D>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);     // dz1
   });
   __syncthreads();
-  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, [&](int m, int n, float v) {
+  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, float v) {
     if (n < D) s_h[m * LDH + n] += v;
     else s_h[m * LDH + n] = v;
   });
@@ -696,7 +797,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
           for (int m = 0; m < nm; ++m) {
             float acc = l3 == 0 ? s_h[p * LDH + D + c * NS + q] : 0.0f;
             for (int co = 0; co < C; ++co)
-              acc = fmaf(__ldg(LW.mix[l3] + co * (C * Pl) + c * Pl + q),
+              acc = fmaf(s_mix[mix_off<Cf>(l3) + co * (C * Pl) + c * Pl + q],
                          s_tmp[p * CL + co * NLM + l3 * l3 + m], acc);
             dT[off + q * nm + m] = acc;
           }
@@ -741,7 +842,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   }
   __syncthreads();
   if (k == 1) {
-    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
+    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
@@ -764,6 +865,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   Carve cv{reinterpret_cast<float*>(smem4)};
+  float* s_wb = cv.take(Cf::WB);
   float* s_h0 = cv.take(kTile * Cf::LDH0);
   float* s_z1 = cv.take(kTile * LDD);
   float* s_a1 = cv.take(kTile * LDD);
@@ -801,17 +903,17 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   load_rows<D>(b.dX, t, s_dx, LDD);
   load_segments<CL>(b.dgam[1], b.row_ptr, t, s_dG);
   __syncthreads();
-  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, [&](int m, int n, float v) {
+  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D>(s_a1, LDD, w.tb1.t, [&](int m, int n, float v) {
+  gemm<D, D>(s_a1, LDD, w.tb1.t, s_wb, [&](int m, int n, float v) {
     s_z2[m * LDD + n] = v;
     s_x[m * LDD + n] = s_geo[m * 8 + 4] * silu(v);
   });
   __syncthreads();
-  gemm<C, D>(s_x, LDD, w.layer[0].env.t, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  gemm<C, D>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   {
@@ -829,7 +931,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
     }
   }
   __syncthreads();
-  gemm<D, C>(s_de, C, w.layer[0].env.n, [&](int m, int n, float v) { s_dx[m * LDD + n] += v; });
+  gemm<D, C>(s_de, C, w.layer[0].env.n, s_wb, [&](int m, int n, float v) { s_dx[m * LDD + n] += v; });
   __syncthreads();
   {
     float du = 0.0f;
@@ -844,11 +946,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
     if (sub == 0) s_du[p] = du;
   }
   __syncthreads();
-  gemm<D, D>(s_z2, LDD, w.tb1.n, [&](int m, int n, float v) {
+  gemm<D, D>(s_z2, LDD, w.tb1.n, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
-  gemm<Cf::H0, D>(s_z1, LDD, w.tb0.n, [&](int m, int n, float v) { s_dh0[m * Cf::LDH0 + n] = v; });
+  gemm<Cf::H0, D>(s_z1, LDD, w.tb0.n, s_wb, [&](int m, int n, float v) { s_dh0[m * Cf::LDH0 + n] = v; });
   __syncthreads();
   if (threadIdx.x < t.np) {
     const int q = threadIdx.x;
@@ -873,15 +975,17 @@ template <class Cf>
 struct Smem {
   static constexpr int r(int n) { return (n + 3) & ~3; }
   static constexpr int T = kTile;
-  static constexpr size_t a = 4 * (r(T * Cf::LDH0) + r(T) + r(T * Cf::NLM) + 2 * r(T * Cf::LDD) + r(T * Cf::C));
-  static constexpr size_t b = 4 * (r(T * Cf::LDH) + r(T * Cf::LDD) + r(T * Cf::NW0) + r(T * Cf::CL) +
-                                   r(T * Cf::C * Cf::NT) + r(T) + r(T * Cf::NLM) + r(T * Cf::C));
-  static constexpr size_t c = 4 * (r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + 2 * r(T * Cf::LDE) + 2 * r(T * Cf::CL) +
+  static constexpr size_t a = 4 * (r(Cf::WB) + r(T * Cf::LDH0) + r(T) + r(T * Cf::NLM) + 2 * r(T * Cf::LDD) + r(T * Cf::C));
+  static constexpr size_t b = 4 * (r(Cf::WB) + r(T * Cf::LDH) + r(T * Cf::LDD) + r(T * Cf::NW0) +
+                                   r(T * Cf::CL) + r(T * Cf::C * Cf::NT) + r(T) + r(T * Cf::NLM) +
+                                   r(T * Cf::C) + r(Cf::MIXW));
+  static constexpr size_t c = 4 * (r(Cf::WB) + r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + 2 * r(T * Cf::LDE) + 2 * r(T * Cf::CL) +
                                    2 * r(T * Cf::NW0) + r(T) + 2 * r(T * Cf::NLM) + r(T));
   static constexpr int tmpw = Cf::CL > Cf::LDD ? Cf::CL : Cf::LDD;
-  static constexpr size_t bb = 4 * (r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + r(T * tmpw) + 2 * r(T * Cf::CL) +
-                                    2 * r(T * Cf::NW0) + 2 * r(T * Cf::C) + r(T) + 2 * r(T * Cf::NLM) + r(T));
-  static constexpr size_t ab = 4 * (r(T * Cf::LDH0) + 5 * r(T * Cf::LDD) + r(T * Cf::CL) + 2 * r(T * Cf::C) +
+  static constexpr size_t bb = 4 * (r(Cf::WB) + r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + r(T * tmpw) +
+                                    2 * r(T * Cf::CL) + 2 * r(T * Cf::NW0) + 2 * r(T * Cf::C) + r(T) +
+                                    2 * r(T * Cf::NLM) + r(T) + r(Cf::MIXW));
+  static constexpr size_t ab = 4 * (r(Cf::WB) + r(T * Cf::LDH0) + 5 * r(T * Cf::LDD) + r(T * Cf::CL) + 2 * r(T * Cf::C) +
                                     r(T * Cf::LDH0) + r(T * 8) + r(T * Cf::NB) + 2 * r(T * Cf::NLM) + r(T));
 };
 
