@@ -1,0 +1,38 @@
+"""The tensor-core tile GEMM building block (tcgen05.mma kind::f16, BF16
+operands in 128-byte-swizzled shared memory, FP32 accumulation in TMEM)
+against torch on the same BF16-rounded operands.  Shapes cover every
+(N, K) the BF16 pair passes use: N in {16, 32, 48, 128, 176, 256}, K from 16
+(one MMA) to 192 (three swizzle blocks) and the K = 176 partial block."""
+import ctypes
+
+import pytest
+import torch
+
+import paper_2303_08169_gb300 as al
+
+pytestmark = pytest.mark.gpu
+
+
+def _selftest(A, B):
+    L = al.lib()
+    fn = L.allegro_selftest_mma
+    fn.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    N, K = B.shape
+    D = torch.full((128, N), float("nan"), device="cuda")
+    rc = fn(N, K, A.data_ptr(), B.data_ptr(), D.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == 0, rc
+    return D
+
+
+@pytest.mark.parametrize("N,K", [(16, 16), (128, 16), (32, 128), (48, 128), (16, 128), (128, 128),
+                                 (128, 176), (176, 128), (128, 192), (256, 64), (256, 256)])
+def test_tile_gemm_matches_torch(N, K):
+    g = torch.Generator(device="cuda").manual_seed(N * 1000 + K)
+    A = torch.randn(128, K, device="cuda", generator=g)
+    B = torch.randn(N, K, device="cuda", generator=g)
+    D = _selftest(A, B)
+    ref = A.bfloat16().double() @ B.bfloat16().double().T
+    err = (D.double() - ref).abs().max().item()
+    assert err <= 1e-5 * ref.abs().max().item() + 1e-5, err
