@@ -202,6 +202,29 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);
  */
 int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_t n_out);
 
+/*
+ * Diagnostic (not part of the paper's method): one 128 x n tile GEMM
+ * D = bf16(A) bf16(B)^T with FP32 accumulation, run through the same
+ * tensor-core building blocks (tcgen05.mma, swizzled shared-memory operands,
+ * TMEM accumulator) as the BF16 pair passes, for checking them against a
+ * host reference.  a: device 128 x k FP32; b: device n x k FP32; d: device
+ * 128 x n FP32 (row-major).  16 <= n <= 256, n % 16 == 0, 16 <= k <= 256,
+ * k % 16 == 0, else ALLEGRO_E_INVALID_ARG; ALLEGRO_E_TIMEOUT if the bounded
+ * wait for the MMA gave up.  Runs on the legacy default stream and
+ * synchronises.
+ */
+int allegro_selftest_mma(int32_t n, int32_t k, const float* a, const float* b, float* d);
+
+/*
+ * Same diagnostic with the B-operand form selectable: mode 0 is the call
+ * above; mode 1 computes d = bf16(a) (128 x k) bf16(b) (k x n, row-major),
+ * reading the K-major image of b as an MN-major operand (the form the BF16
+ * adjoint passes use to apply W^T without a transposed copy); mode 2 is mode 1
+ * with the two descriptor strides exchanged (kept to verify which reading of
+ * the descriptor the hardware follows).
+ */
+int allegro_selftest_mma_mode(int32_t n, int32_t k, const float* a, const float* b, float* d, int32_t mode);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ EXPORTED = [
     "allegro_last_error", "allegro_build_neighbors", "allegro_get_neighbors",
     "allegro_energy_forces", "allegro_outlier_count", "allegro_md_init",
     "allegro_set_md_precision", "allegro_md_step_nve", "allegro_md_get_state",
-    "allegro_query", "allegro_phase_times",
+    "allegro_query", "allegro_phase_times", "allegro_selftest_mma",
+    "allegro_selftest_mma_mode",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -72,6 +73,8 @@ def lib():
         "allegro_md_get_state": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_i64)], ctypes.c_int),
         "allegro_query": ([_vp, _i32, ctypes.POINTER(_i64)], ctypes.c_int),
         "allegro_phase_times": ([_vp, _i32, _vp, _i32], ctypes.c_int),
+        "allegro_selftest_mma": ([_i32, _i32, _vp, _vp, _vp], ctypes.c_int),
+        "allegro_selftest_mma_mode": ([_i32, _i32, _vp, _vp, _vp, _i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -191,6 +194,17 @@ def allegro_phase_times(ctx, n_reps=10):
     out = np.zeros(len(PHASES))
     _check(ctx, lib().allegro_phase_times(ctx, int(n_reps), _ptr(out), len(PHASES)))
     return dict(zip(PHASES, out.tolist()))
+
+
+def allegro_selftest_mma(a, b, d):
+    """d (128 x n) = bf16(a) (128 x k) @ bf16(b)^T (n x k), all CUDA float32 tensors."""
+    _check(None, lib().allegro_selftest_mma(int(b.shape[0]), int(b.shape[1]), _ptr(a), _ptr(b), _ptr(d)))
+
+
+def allegro_selftest_mma_mode(a, b, d, mode):
+    """mode 0: d = a @ b^T (b: n x k); modes 1, 2: d = a @ b (b: k x n, MN-major read)."""
+    n, k = (b.shape[0], b.shape[1]) if mode == 0 else (b.shape[1], b.shape[0])
+    _check(None, lib().allegro_selftest_mma_mode(int(n), int(k), _ptr(a), _ptr(b), _ptr(d), int(mode)))
 
 
 __all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED

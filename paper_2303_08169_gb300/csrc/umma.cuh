@@ -49,11 +49,26 @@ UM_DEV uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Descriptor of an SW128 tile used as an MN-major operand: the K-major image
+// of a [P x Q] matrix (rows P, 128-byte rows along Q) read as an operand whose
+// MN dimension is Q and K dimension is P.  Swizzle atoms are 8 rows (K) x 64
+// elements (MN); lbo = byte stride between atoms along MN (one 64-column
+// block of the image, P * 128 bytes), sbo = 1024 between atoms along K.
+UM_DEV uint64_t desc_sw128_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9
 // = 1), B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (b_mn_major ? (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
@@ -130,6 +145,23 @@ UM_DEV void mma_tile(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int N,
     const uint32_t aoff = (uint32_t)((k >> 2) * (128 * 128) + (k & 3) * 32);
     const uint32_t boff = (uint32_t)((k >> 2) * (N * 128) + (k & 3) * 32);
     mma_bf16(d_tmem, desc_sw128(a_saddr + aoff), desc_sw128(b_saddr + boff), idesc,
+             (accumulate || k > 0) ? 1u : 0u);
+  }
+}
+
+// Issue D[128 x N] (+)= A[128 x K] * W[K x N] where the B operand is the
+// K-major image of W^T... i.e. the image of a [K x N] matrix W stored with K
+// rows of N elements (the forward image of a layer whose output dim is K):
+// MN-major B, N = number of image columns, K = number of image rows (P).
+UM_DEV void mma_tile_bmn(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int N, int P, int nk,
+                         bool accumulate, bool swap_lbo_sbo) {
+  const uint32_t idesc = idesc_bf16(128, N, true);
+  const uint32_t lbo = swap_lbo_sbo ? 1024u : (uint32_t)(P * 128);
+  const uint32_t sbo = swap_lbo_sbo ? (uint32_t)(P * 128) : 1024u;
+  for (int k = 0; k < nk; ++k) {
+    const uint32_t aoff = (uint32_t)((k >> 2) * (128 * 128) + (k & 3) * 32);
+    const uint32_t boff = (uint32_t)(k * 16 * 128);   // 16 image rows per MMA
+    mma_bf16(d_tmem, desc_sw128(a_saddr + aoff), desc_sw128_mn(b_saddr + boff, lbo, sbo), idesc,
              (accumulate || k > 0) ? 1u : 0u);
   }
 }

@@ -36,3 +36,20 @@ def test_tile_gemm_matches_torch(N, K):
     ref = A.bfloat16().double() @ B.bfloat16().double().T
     err = (D.double() - ref).abs().max().item()
     assert err <= 1e-5 * ref.abs().max().item() + 1e-5, err
+
+
+@pytest.mark.parametrize("N,K", [(128, 128), (128, 32), (176, 128), (48, 16), (128, 48), (16, 128), (192, 64)])
+def test_mn_major_b_operand(N, K):
+    """d = a @ w with w (K x N) kept in its K-major image and read MN-major:
+    the descriptor reading with lbo = K * 128 (stride between 64-column
+    blocks) and sbo = 1024 (8 rows) must match torch; the exchanged reading is
+    recorded but only one of the two can be right."""
+    g = torch.Generator(device="cuda").manual_seed(7 * N + K)
+    A = torch.randn(128, K, device="cuda", generator=g)
+    W = torch.randn(K, N, device="cuda", generator=g)
+    ref = A.bfloat16().double() @ W.bfloat16().double()
+    D = torch.full((128, N), float("nan"), device="cuda")
+    al.allegro_selftest_mma_mode(A, W, D, 1)
+    torch.cuda.synchronize()
+    err = (D.double() - ref).abs().max().item()
+    assert err <= 1e-5 * ref.abs().max().item() + 1e-5, err
