@@ -11,6 +11,7 @@
 #include "kernels.h"
 #include "md.h"
 #include "model.h"
+#include "umma.cuh"
 
 using namespace al;
 
@@ -113,6 +114,9 @@ struct allegro_ctx {
   // weights
   float* d_w = nullptr;
   ModelW w{};
+  uint8_t* d_bw = nullptr;     // BF16 swizzled weight images
+  BfW bw{};
+  bool bf16_ok = false;
   // allocations
   std::vector<void*> allocs;
   int64_t n_atoms_alloc = 0;
@@ -246,6 +250,65 @@ int upload_weights(allegro_ctx* c) {
   return ALLEGRO_OK;
 }
 
+uint16_t f2bf(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even (finite inputs)
+  return (uint16_t)(u >> 16);
+}
+
+// BF16 tensor-core images (layout of umma.cuh) of every linear layer of the
+// main model, pre-scaled like the FP32 copies.
+int upload_weights_bf16(allegro_ctx* c) {
+  const Blob& B = c->blob;
+  std::vector<uint8_t> img;
+  auto add = [&](const Tensor* T, double extra, int Rimg, int Kimg) -> size_t {
+    const size_t base = (img.size() + 1023) / 1024 * 1024;
+    img.resize(base + al::umma::sw128_bytes(Rimg, Kimg), 0);
+    const double s = extra / std::sqrt((double)T->cols);
+    for (uint32_t r = 0; r < T->rows; ++r)
+      for (uint32_t k = 0; k < T->cols; ++k) {
+        const uint16_t h = f2bf((float)(T->data[r * T->cols + k] * s));
+        std::memcpy(img.data() + base + al::umma::sw128_off((int)r, (int)k, Rimg), &h, 2);
+      }
+    return base;
+  };
+  size_t o_tb0 = add(B.find("twobody.0"), 1.0, 128, 64);
+  size_t o_tb1 = add(B.find("twobody.1"), 1.0, 128, 128);
+  size_t o_emb = add(B.find("embed"), 1.0, 48, 128);
+  size_t o_e0 = add(B.find("energy.0"), 1.0, 32, 128);
+  size_t o_env[kMaxLayers], o_l0[kMaxLayers], o_l1[kMaxLayers], o_mix[kMaxLayers][3];
+  for (uint32_t k = 1; k <= B.L; ++k) {
+    const std::string pre = "layer" + std::to_string(k) + ".";
+    o_env[k - 1] = add(B.find(pre + "env"), 1.0 / std::sqrt(B.nu), 16, 128);
+    o_l0[k - 1] = add(B.find(pre + "latent.0"), 1.0, 128, 192);
+    o_l1[k - 1] = add(B.find(pre + "latent.1"), 1.0, 128, 128);
+    if (k < B.L)
+      for (int l = 0; l < 3; ++l) o_mix[k - 1][l] = add(B.find(pre + "mix" + std::to_string(l)), 1.0, 16, 64);
+  }
+  c->d_bw = c->dalloc<uint8_t>(img.size());
+  if (!c->d_bw) return c->fail(ALLEGRO_E_OOM, "BF16 weights allocation failed");
+  if (cudaMemcpy(c->d_bw, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_check(c, "BF16 weights upload");
+  BfW& w = c->bw;
+  w.tb0 = c->d_bw + o_tb0;
+  w.tb1 = c->d_bw + o_tb1;
+  w.emb = c->d_bw + o_emb;
+  w.e0 = c->d_bw + o_e0;
+  for (uint32_t k = 1; k <= B.L; ++k) {
+    w.env[k - 1] = c->d_bw + o_env[k - 1];
+    w.lat0[k - 1] = c->d_bw + o_l0[k - 1];
+    w.lat1[k - 1] = c->d_bw + o_l1[k - 1];
+    if (k < B.L)
+      for (int l = 0; l < 3; ++l) w.mix[k - 1][l] = c->d_bw + o_mix[k - 1][l];
+  }
+  w.eout = c->w.eout;
+  for (int s = 0; s < 2; ++s) w.sigma[s] = (float)B.sigma[s];
+  w.rc = (float)B.rc;
+  w.n_layers = (int)B.L;
+  return ALLEGRO_OK;
+}
+
 int check_cell(allegro_ctx* c, const double* cell, double L[3]) {
   if (!cell) return c->fail(ALLEGRO_E_INVALID_ARG, "cell is NULL");
   for (int a = 0; a < 3; ++a)
@@ -357,6 +420,21 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   pb.dU = c->dalloc<float>(cap);
   pb.dY = c->dalloc<float>((size_t)cap * NLM);
   pb.G = c->dalloc<float>((size_t)cap * 3);
+  for (int k = 0; k < kMaxLayers; ++k) {
+    c->dfree(pb.S[k]);
+    pb.S[k] = nullptr;
+  }
+  c->dfree(pb.dS);
+  pb.dS = nullptr;
+  if (c->bf16_ok) {
+    const int NSC = B.C * 3;
+    for (uint32_t k = 1; k < B.L && ok; ++k) {
+      pb.S[k] = c->dalloc<float>((size_t)cap * NSC);
+      ok = ok && pb.S[k];
+    }
+    pb.dS = c->dalloc<float>((size_t)cap * NSC);
+    ok = ok && pb.dS;
+  }
   const int64_t rows = rows_needed;
   pb.epart = c->dalloc<double>(rows);
   ok = ok && pb.dX && pb.dV && pb.dU && pb.dY && pb.G && pb.epart;
@@ -468,15 +546,28 @@ int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* s
   return cuda_check(c, "prepare");
 }
 
+// Pair passes of the requested precision followed by force assembly.
+void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, cudaEvent_t* ev) {
+  const Blob& B = c->blob;
+  int tile;
+  if (precision == ALLEGRO_BF16) {
+    bf16_energy_forces(c->bw, c->pb, c->capacity, s, ev);
+    tile = bf16_tile();
+  } else {
+    fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, ev);
+    tile = fp32_tile();
+  }
+  launch_forces(atom_args(c), c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, tile, c->d_F, c->d_Ei, c->d_blk,
+                c->d_stats, c->nb.flags, s);
+}
+
 int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
   if (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16)
     return c->fail(ALLEGRO_E_INVALID_ARG, "precision must be ALLEGRO_FP32 or ALLEGRO_BF16");
+  if (precision == ALLEGRO_BF16 && !c->bf16_ok)
+    return c->fail(ALLEGRO_E_UNSUPPORTED, "the BF16 tensor-core path is built for the 2+-layer l_max 2 model only");
   fill_passbufs(c, L);
-  const Blob& B = c->blob;
-  // BF16 requests run the FP32 pair passes until the tensor-core path is built
-  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream);
-  launch_forces(atom_args(c), c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei,
-                c->d_blk, c->d_stats, c->nb.flags, c->stream);
+  launch_model(c, precision, c->stream, nullptr);
   return cuda_check(c, "model launch");
 }
 
@@ -531,6 +622,8 @@ int allegro_create(const void* weights_blob, size_t blob_bytes, const double* sp
   c->E = (int)B.energy[0];
   for (int s = 0; s < 2; ++s) c->mass[s] = species_mass[s];
   int rc = upload_weights(c);
+  c->bf16_ok = bf16_supported((int)B.lmax, (int)B.C, c->D, c->E, (int)B.L);
+  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c);
   if (rc) {
     g_err = c->err;
     delete c;
@@ -697,10 +790,7 @@ int capture_step(allegro_ctx* c, double dt) {
   const AtomArgs a = atom_args(c);
   launch_kick_drift(a, c->d_pos, c->d_v, c->d_F, dt, L, cs);
   launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs);
-  const Blob& B = c->blob;
-  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, cs);
-  launch_forces(a, c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk,
-                c->d_stats, c->nb.flags, cs);
+  launch_model(c, c->md_precision, cs, nullptr);
   launch_kick_measure(a, c->d_v, c->d_F, dt, c->d_stats, 5.0, c->d_blk_ke, c->d_blku, c->d_step, c->rec_cap,
                       c->d_e_rec, c->d_out_rec, cs);
   cudaError_t e = cudaStreamEndCapture(cs, &g);
@@ -810,14 +900,11 @@ int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   double L[3] = {ctx->grid.L[0], ctx->grid.L[1], ctx->grid.L[2]};
   fill_passbufs(ctx, L);
-  const Blob& B = ctx->blob;
   int rc = ALLEGRO_OK;
   for (int r = 0; r < n_reps && !rc; ++r) {
     cudaEventRecord(ev[0], ctx->stream);
     launch_build_neighbors(ctx->nb, ctx->grid, ctx->d_pos, ctx->n_atoms, ctx->stream);
-    fp32_energy_forces((int)B.lmax, (int)B.C, ctx->D, ctx->E, ctx->w, ctx->pb, ctx->capacity, ctx->stream, ev + 1);
-    launch_forces(atom_args(ctx), ctx->nb.row_ptr, ctx->nb.rev, ctx->pb.G, ctx->pb.epart, fp32_tile(), ctx->d_F,
-                  ctx->d_Ei, ctx->d_blk, ctx->d_stats, ctx->nb.flags, ctx->stream);
+    launch_model(ctx, ctx->md_precision, ctx->stream, ev + 1);
     cudaEventRecord(ev[7], ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
       rc = cuda_check(ctx, "phase times");

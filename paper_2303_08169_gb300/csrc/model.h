@@ -55,12 +55,36 @@ struct PassBufs {
   float* dU;              // P
   float* dY;              // P x NLM
   float* G;               // P x 3  (dE/dDelta)
+  float* S[kMaxLayers];   // BF16 path: tensor-product scalars of layer k (P x C P_0)
+  float* dS;              // BF16 path: their gradient (P x C P_0)
   // per (tile, atom) partial sums, index (tile + atom)
   float* gam[kMaxLayers + 1];   // Gamma^k partials, k = 1..L
   float* dgam[kMaxLayers + 1];  // dGamma^k partials
   double* epart;                // sum_j E_ij partials
   int tile;                     // pairs per tile (all passes)
 };
+
+// BF16 path weights: pre-scaled BF16 images in the 128-byte-swizzled K-major
+// layout of the tensor-core operands (umma.cuh), one per linear layer.
+struct BfW {
+  const uint8_t* tb0 = nullptr;   // [128 x 64]  (12 inputs used)
+  const uint8_t* tb1 = nullptr;   // [128 x 128]
+  const uint8_t* emb = nullptr;   // [48 x 128]
+  const uint8_t* e0 = nullptr;    // [32 x 128]
+  const uint8_t* env[kMaxLayers] = {};
+  const uint8_t* lat0[kMaxLayers] = {};   // [128 x 192] (176 inputs used)
+  const uint8_t* lat1[kMaxLayers] = {};
+  const uint8_t* mix[kMaxLayers][3] = {}; // [16 x 64] (C P_l inputs used)
+  const float* eout = nullptr;    // 32 FP32
+  float sigma[2];
+  float rc;
+  int n_layers;
+};
+
+bool bf16_supported(int lmax, int C, int D, int E, int L);
+int bf16_tile();
+void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s,
+                        cudaEvent_t* ev = nullptr);
 
 // FP32 path: one launcher per pass sequence; templated on the model shape in
 // the .cu file, dispatched by (lmax, C, D, E).

@@ -1,0 +1,1208 @@
+// model_bf16.cu - BF16 tensor-core pair passes (tcgen05.mma, FP32 accumulation
+// in TMEM) for the 2-layer, l_max 2, 16-channel, latent-128, energy-32 model.
+//
+// Same model and same pass order as the FP32 path (model_fp32.cu): forward
+// passes, a fused last-layer forward + adjoint, then the adjoint passes
+// (forces f = -dE/dr, Eq. 1).  Differences:
+//  * tiles of 128 pairs, one persistent CTA of 256 threads per SM; thread t
+//    owns tile row r = t % 128 (its TMEM lane) and column half t / 128;
+//  * every per-pair GEMM (two-body, embedding, env, mixing, latent, energy
+//    and their adjoints) runs on tcgen05.mma with BF16 operands in
+//    128-byte-swizzled shared memory and FP32 accumulators in TMEM; the
+//    adjoint GEMMs read the forward weight images as MN-major operands;
+//  * pre-activations stay in TMEM between a GEMM and its adjoint;
+//  * channel mixing is 9 MMAs, one per output component (l3, m), over
+//    K-slices of one tile holding the tensor-product outputs;
+//  * the layer-k pass is split in two (TP + mixing; latent MLP) so that the
+//    weights of every kernel stay resident in shared memory;
+//  * sigmoid via tanh.approx.f32.
+// Everything else (geometry, tensor products, envelope, residuals,
+// reductions) is FP32 on CUDA cores; x^k, V^k and all gradients are stored in
+// FP32.  Per-atom sums use the per-(tile, atom) partials of the FP32 path with
+// 128-pair tiles.
+#include <cstdio>
+
+#include "common.cuh"
+#include "model.h"
+#include "tp_tables.inc"
+#include "umma.cuh"
+
+namespace al {
+namespace {
+
+using namespace umma;
+
+constexpr int kT = 128;
+constexpr int kThr = 256;
+constexpr int D = 128, C = 16, E = 32, NLM = 9, NS = 3, KH = 176, NW0 = 48, CL = 144, NB = 8;
+constexpr float kR2 = 0.70710678118654752f;
+
+constexpr uint32_t kImgTb0 = sw128_bytes(128, 64);
+constexpr uint32_t kImgTb1 = sw128_bytes(128, 128);
+constexpr uint32_t kImgEmb = sw128_bytes(48, 128);
+constexpr uint32_t kImgE0 = sw128_bytes(32, 128);
+constexpr uint32_t kImgEnv = sw128_bytes(16, 128);
+constexpr uint32_t kImgLat0 = sw128_bytes(128, 192);
+constexpr uint32_t kImgLat1 = sw128_bytes(128, 128);
+constexpr uint32_t kImgMix = sw128_bytes(16, 64);
+constexpr uint32_t kOp128 = sw128_bytes(128, 128);
+constexpr uint32_t kOp64 = sw128_bytes(128, 64);
+constexpr uint32_t kOpH = sw128_bytes(128, 192);
+constexpr uint32_t kOpT = sw128_bytes(128, 576);
+
+// mixing: output component j = l*l + m (0..8) reads the K-slice of the
+// tensor-product tile starting at column kSlice[j] (width C P_l)
+__device__ __constant__ int kSlice[9] = {0, 48, 112, 176, 240, 304, 368, 432, 496};
+AL_DEV int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
+
+AL_DEV float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+AL_DEV float sgm(float z) { return fmaf(0.5f, tanh_fast(0.5f * z), 0.5f); }
+AL_DEV float silu_b(float z) { return z * sgm(z); }
+AL_DEV float dsilu_b(float z) {
+  const float s = sgm(z);
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// ---------------------------------------------------------------------------
+struct Meta {
+  int pi[kT], pj[kT], code[kT], seg[kT], atom[kT], sstart[kT + 1];
+  int nseg, np, p0, tile;
+  int wc[4];
+};
+
+AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
+  const int t = threadIdx.x;
+  const int p0 = tile * kT;
+  const int np = min(kT, P - p0);
+  if (t < kT) {
+    int i = -1;
+    if (t < np) {
+      i = b.pi[p0 + t];
+      m.pi[t] = i;
+      m.pj[t] = b.pj[p0 + t];
+      m.code[t] = b.pcode[p0 + t];
+    } else {
+      m.pi[t] = 0;
+      m.pj[t] = 0;
+      m.code[t] = 62;
+    }
+    int prev = __shfl_up_sync(0xffffffffu, i, 1);
+    if ((t & 31) == 0) prev = (t > 0 && t - 1 < np) ? b.pi[p0 + t - 1] : -1;
+    const bool head = t < np && (t == 0 || i != prev);
+    const unsigned mask = __ballot_sync(0xffffffffu, head);
+    if ((t & 31) == 0) m.wc[t >> 5] = __popc(mask);
+    __syncwarp();
+    m.seg[t] = 0;
+    // stash the ballot in sstart temporarily is not needed: recompute below
+    m.atom[t] = head ? 1 : 0;
+  }
+  __syncthreads();
+  if (t < kT) {
+    int base = 0;
+    for (int w = 0; w < (t >> 5); ++w) base += m.wc[w];
+    const bool head = m.atom[t] != 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, head);
+    const unsigned below = (t & 31) == 31 ? 0xffffffffu : ((2u << (t & 31)) - 1u);
+    const int s = base + __popc(mask & below) - 1;
+    m.seg[t] = t < np ? s : 0;
+    __syncwarp();
+    if (head) m.sstart[s] = t;
+  }
+  __syncthreads();
+  if (t < kT) {
+    // atom of each segment (read pi of the segment's first pair)
+    const int nseg = m.wc[0] + m.wc[1] + m.wc[2] + m.wc[3];
+    if (t < nseg) m.atom[t] = m.pi[m.sstart[t]];
+    if (t == 0) {
+      m.nseg = nseg;
+      m.np = np;
+      m.p0 = p0;
+      m.tile = tile;
+      m.sstart[nseg] = np;
+    }
+  }
+  __syncthreads();
+}
+
+// part[(tile + atom) * W + x] = sum over the segment's pairs of f(p, x)
+template <class F>
+AL_DEV void seg_store(float* __restrict__ part, const Meta& m, int W, F&& f) {
+  for (int idx = threadIdx.x; idx < m.nseg * W; idx += kThr) {
+    const int s = idx / W, x = idx % W;
+    float acc = 0.0f;
+    for (int p = m.sstart[s]; p < m.sstart[s + 1]; ++p) acc += f(p, x);
+    part[(size_t)(m.tile + m.atom[s]) * W + x] = acc;
+  }
+}
+
+// Gamma (or dGamma) of atom i, channel c: sum of its partials in tile order
+AL_DEV void load_g(const float* __restrict__ part, const int* __restrict__ row_ptr, int i, int c, float* G) {
+  const int t0 = row_ptr[i] / kT, t1 = (row_ptr[i + 1] - 1) / kT;
+#pragma unroll
+  for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+  for (int tt = t0; tt <= t1; ++tt) {
+    const float* g = part + (size_t)(tt + i) * CL + c * NLM;
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) G[lm] += g[lm];
+  }
+}
+
+AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float u[3], float& d, float& fc,
+                     float& dfc, float* Y) {
+  Box box{{b.L[0], b.L[1], b.L[2]}};
+  double dd[3];
+  pair_delta(b.wpos, i, j, code, box, dd);
+  const float dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
+  d = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float inv = 1.0f / d;
+  u[0] = dx * inv;
+  u[1] = dy * inv;
+  u[2] = dz * inv;
+  envelope(d, rc, fc, dfc);
+  sph_harm<2>(u[0], u[1], u[2], Y);
+}
+
+// ---- MMA issue helpers (single thread) ----
+// D[128 x N] = A[128 x K-slice from k-step kk0, nk steps] * B, B either the
+// K-major image of an [N x K] matrix or (b_mn) the image of a [P x N] matrix
+// read MN-major.
+AL_DEV void mma_k(uint32_t d, const uint8_t* A, int kk0, const uint8_t* B, int N, int nk, bool b_mn, int P) {
+  const uint32_t idesc = idesc_bf16(128, N, b_mn);
+  const uint32_t a = smem_u32(A), bb = smem_u32(B);
+  for (int i = 0; i < nk; ++i) {
+    const int kk = kk0 + i;
+    const uint32_t aoff = (uint32_t)((kk >> 2) * (128 * 128) + (kk & 3) * 32);
+    uint64_t bd;
+    if (b_mn) bd = desc_sw128_mn(bb + (uint32_t)(i * 16 * 128), (uint32_t)(P * 128), 1024u);
+    else bd = desc_sw128(bb + (uint32_t)((i >> 2) * (N * 128) + (i & 3) * 32));
+    mma_bf16(d, desc_sw128(a + aoff), bd, idesc, i > 0 ? 1u : 0u);
+  }
+}
+
+struct Mma {
+  uint64_t* bar;
+  uint32_t phase;
+  int* err;
+  // all threads: publish smem operands, thread 0 issues, everyone waits
+  template <class F>
+  AL_DEV void run(F&& issue) {
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    const bool skip = *err != 0;
+    if (!skip) {
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        issue();
+        mma_commit(bar);
+      }
+      if (!mbar_wait(bar, phase)) *err = 1;
+      phase ^= 1u;
+    }
+    tc_fence_after();
+  }
+};
+
+AL_DEV uint32_t lanes(uint32_t tmem) { return tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16); }
+
+// thread (r, h) visits columns [h N/2, (h+1) N/2) of an N-wide accumulator at
+// TMEM column col0, 16 at a time: f(r, n0, v[16])
+template <class F>
+AL_DEV void epi(uint32_t tmem, int col0, int N, F&& f) {
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  const uint32_t base = lanes(tmem);
+  for (int n0 = h * (N / 2); n0 < (h + 1) * (N / 2); n0 += 16) {
+    float v[16];
+    tmem_ld16(base + (uint32_t)(col0 + n0), v);
+    f(r, n0, v);
+  }
+}
+
+AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
+  st_bf16x8(A, sw128_off(r, c0, 128), v);
+  st_bf16x8(A, sw128_off(r, c0 + 8, 128), v + 8);
+}
+AL_DEV void st1(uint8_t* A, int r, int c, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(A + sw128_off(r, c, 128)) = __float2bfloat16_rn(v);
+}
+
+// row r of a pair-major FP32 array (W wide) converted into columns [c0, c0+n)
+AL_DEV void row_to_op(uint8_t* A, int r, const float* __restrict__ g, bool valid, int c0, int n) {
+  for (int k = 0; k < n; k += 16) {
+    float v[16];
+    if (valid) {
+      const float4* s = reinterpret_cast<const float4*>(g + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 x = s[q];
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+    }
+    st16(A, r, c0 + k, v);
+  }
+}
+
+AL_DEV uint8_t* align1024(uint8_t* p) {
+  const uint32_t a = smem_u32(p);
+  return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
+// Common prologue/epilogue of every persistent pass kernel.
+#define BF_PROLOGUE(WBYTES, LOADS)                                                \
+  extern __shared__ uint8_t smem_raw[];                                           \
+  __shared__ Meta m;                                                              \
+  __shared__ uint64_t bars[2];                                                    \
+  __shared__ uint32_t tslot;                                                      \
+  __shared__ int err;                                                             \
+  uint8_t* sm = align1024(smem_raw);                                              \
+  if (threadIdx.x < 32) tmem_alloc(&tslot, 512);                                  \
+  if (threadIdx.x == 0) {                                                         \
+    mbar_init(&bars[0], 1);                                                       \
+    mbar_init(&bars[1], 1);                                                       \
+    mbar_fence_init();                                                            \
+    err = 0;                                                                      \
+  }                                                                               \
+  tc_fence_before();                                                              \
+  __syncthreads();                                                                \
+  tc_fence_after();                                                               \
+  const uint32_t tmem = tslot;                                                    \
+  if (threadIdx.x == 0) {                                                         \
+    mbar_expect_tx(&bars[1], (WBYTES));                                           \
+    LOADS;                                                                        \
+  }                                                                               \
+  if (!mbar_wait(&bars[1], 0)) err = 1;                                           \
+  __syncthreads();                                                                \
+  Mma mm{&bars[0], 0u, &err};                                                     \
+  const int P = (int)min((int64_t)*b.n_pairs, b.capacity);                        \
+  const int ntiles = (*b.flags & 1) ? 0 : (P + kT - 1) / kT;
+
+#define BF_EPILOGUE                                                               \
+  tc_fence_before();                                                              \
+  __syncthreads();                                                                \
+  if (threadIdx.x < 32) tmem_dealloc(tmem, 512);                                  \
+  if (err && threadIdx.x == 0) atomicOr(const_cast<int*>(b.flags), kFlagTimeoutBit);
+
+constexpr int kFlagTimeoutBit = 4;
+
+// ============================================================================
+// Pass A: geometry, two-body MLP (12 -> 128 -> 128), x0, env1 -> Gamma^1.
+__global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
+  BF_PROLOGUE(kImgTb0 + kImgTb1 + kImgEnv, {
+    bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
+    bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
+    bulk_g2s(sm + kImgTb0 + kImgTb1, w.env[0], kImgEnv, &bars[1]);
+  })
+  uint8_t* Wtb0 = sm;
+  uint8_t* Wtb1 = Wtb0 + kImgTb0;
+  uint8_t* Wenv = Wtb1 + kImgTb1;
+  uint8_t* H0 = Wenv + kImgEnv;
+  uint8_t* A1 = H0 + kOp64;
+  uint8_t* X = A1 + kOp128;
+  float* s_fc = reinterpret_cast<float*>(X + kOp128);
+  float* s_Y = s_fc + kT;
+  float* s_e = s_Y + kT * NLM;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    if (threadIdx.x < kT) {
+      const int r = threadIdx.x;
+      float h0[16], Y[NLM], fc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) h0[q] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (r < m.np) {
+        float u[3], d, dfc, B[NB];
+        geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+        bessel<NB>(d, w.rc, B, nullptr);
+        h0[b.species[m.pi[r]]] = 1.0f;
+        h0[2 + b.species[m.pj[r]]] = 1.0f;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
+      }
+      s_fc[r] = fc;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+      st16(H0, r, 0, h0);
+    }
+    mm.run([&] { mma_k(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });
+    epi(tmem, 0, 128, [&](int r, int n0, const float* v) {
+      float o[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
+      st16(A1, r, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });
+    epi(tmem, 128, 128, [&](int r, int n0, const float* v) {
+      float o[16];
+      const float fc = s_fc[r];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
+      st16(X, r, n0, o);
+      if (r < m.np) {
+        float4* g = reinterpret_cast<float4*>(b.X[0] + (size_t)(m.p0 + r) * D + n0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      }
+    });
+    mm.run([&] { mma_k(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
+    if (threadIdx.x < kT) {
+      float v[16];
+      tmem_ld16(lanes(tmem) + 256, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) s_e[threadIdx.x * 16 + q] = v[q];
+    }
+    __syncthreads();
+    seg_store(b.gam[1], m, CL, [&](int p, int x) { return s_e[p * 16 + x / NLM] * s_Y[p * NLM + x % NLM]; });
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// ============================================================================
+// Pass B1_k: tensor product of layer k and channel mixing -> V^k, scalars S^k.
+__global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
+  BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
+    bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
+    for (int l = 0; l < 3; ++l) bulk_g2s(sm + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
+  })
+  uint8_t* Wemb = sm;
+  uint8_t* Wmix = Wemb + kImgEmb;
+  uint8_t* X = Wmix + 3 * kImgMix;
+  uint8_t* T = X + kOp128;
+  float* s_Y = reinterpret_cast<float*>(T + kOpT);
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    if (threadIdx.x < kT) {
+      float u[3], d, fc, dfc, Y[NLM];
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (r < m.np) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+    }
+    const bool valid = r < m.np;
+    if (k == 1) {
+      row_to_op(X, r, b.X[0] + (size_t)(m.p0 + r) * D + 64 * h, valid, 64 * h, 64);
+      mm.run([&] { mma_k(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
+    } else {
+      __syncthreads();
+    }
+    float w0[32];
+    if (k == 1) {
+      tmem_ld16(lanes(tmem) + 24 * h, w0);
+      tmem_ld16(lanes(tmem) + 24 * h + 16, w0 + 16);
+    }
+    const int i = m.pi[r];
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = 8 * h + cc;
+      float V[NLM], G[NLM], Tv[TP2_NT];
+      if (k == 1) {
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[cc * 3 + l_of(lm)] * s_Y[r * NLM + lm];
+      } else {
+        const float* g = b.V[k - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? g[lm] : 0.0f;
+      }
+      if (valid) load_g(b.gam[k], b.row_ptr, i, c, G);
+      else
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+      tp2_fwd(V, G, Tv);
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        const int l3 = l_of(j), mm3 = j - l3 * l3, Pl = tp2_P(l3), nm = 2 * l3 + 1;
+#pragma unroll
+        for (int q = 0; q < Pl; ++q) st1(T, r, kSlice[j] + c * Pl + q, Tv[tp2_toff(l3) + q * nm + mm3]);
+      }
+      if (valid) {
+        float* s = b.S[k] + (size_t)(m.p0 + r) * (C * NS) + c * NS;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) s[q] = Tv[q];
+      }
+    }
+    mm.run([&] {
+      for (int j = 0; j < 9; ++j) {
+        const int l3 = l_of(j), Pl = tp2_P(l3);
+        mma_k(tmem + 64 + 16 * j, T, kSlice[j] / 16, Wmix + l3 * kImgMix, 16, C * Pl / 16, false, 0);
+      }
+    });
+    {
+      const uint32_t base = lanes(tmem);
+      for (int j = (h == 0 ? 0 : 5); j < (h == 0 ? 5 : 9); ++j) {
+        float v[16];
+        tmem_ld16(base + 64 + 16 * j, v);
+        if (valid) {
+          float* g = b.V[k] + (size_t)(m.p0 + r) * CL + j;
+#pragma unroll
+          for (int co = 0; co < C; ++co) g[co * NLM] = v[co];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// ============================================================================
+// Pass B2_k: latent MLP of layer k (x^k) and env of layer k+1 -> Gamma^{k+1}.
+__global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
+  BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgEnv, {
+    bulk_g2s(sm, w.lat0[k - 1], kImgLat0, &bars[1]);
+    bulk_g2s(sm + kImgLat0, w.lat1[k - 1], kImgLat1, &bars[1]);
+    bulk_g2s(sm + kImgLat0 + kImgLat1, w.env[k], kImgEnv, &bars[1]);
+  })
+  uint8_t* Wl0 = sm;
+  uint8_t* Wl1 = Wl0 + kImgLat0;
+  uint8_t* Wenv = Wl1 + kImgLat1;
+  uint8_t* HA = Wenv + kImgEnv;
+  uint8_t* A1 = HA + kOpH;
+  float* s_fc = reinterpret_cast<float*>(A1 + kOp128);
+  float* s_Y = s_fc + kT;
+  float* s_e = s_Y + kT * NLM;
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    const bool valid = r < m.np;
+    if (threadIdx.x < kT) {
+      float u[3], d, fc = 0.0f, dfc, Y[NLM];
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      s_fc[r] = fc;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+    }
+    const float* xg = b.X[k - 1] + (size_t)(m.p0 + r) * D;
+    row_to_op(HA, r, xg + 64 * h, valid, 64 * h, 64);
+    if (h == 1) {
+      row_to_op(HA, r, b.S[k] + (size_t)(m.p0 + r) * (C * NS), valid, 128, 48);
+      float z[16] = {};
+      st16(HA, r, 176, z);
+    }
+    mm.run([&] { mma_k(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
+    epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
+      st16(A1, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+      const float fc = s_fc[rr];
+      const float4* xo = reinterpret_cast<const float4*>(xg + n0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 x = valid ? xo[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        o[4 * q] = (x.x + fc * silu_b(v[4 * q])) * kR2;
+        o[4 * q + 1] = (x.y + fc * silu_b(v[4 * q + 1])) * kR2;
+        o[4 * q + 2] = (x.z + fc * silu_b(v[4 * q + 2])) * kR2;
+        o[4 * q + 3] = (x.w + fc * silu_b(v[4 * q + 3])) * kR2;
+      }
+      st16(HA, rr, n0, o);
+      if (valid) {
+        float4* g = reinterpret_cast<float4*>(b.X[k] + (size_t)(m.p0 + rr) * D + n0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      }
+    });
+    mm.run([&] { mma_k(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
+    if (threadIdx.x < kT) {
+      float v[16];
+      tmem_ld16(lanes(tmem) + 256, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) s_e[r * 16 + q] = v[q];
+    }
+    __syncthreads();
+    seg_store(b.gam[k + 1], m, CL, [&](int p, int x) { return s_e[p * 16 + x / NLM] * s_Y[p * NLM + x % NLM]; });
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// ============================================================================
+// Pass C: last layer + energy MLP forward, dE/dE_ij = sigma_Z, and their
+// adjoint: dx^{L-1}, dV^{L-1}, dGamma^L partials, du, energy partials.
+__global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
+  const int L = w.n_layers;
+  BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgE0, {
+    bulk_g2s(sm, w.lat0[L - 1], kImgLat0, &bars[1]);
+    bulk_g2s(sm + kImgLat0, w.lat1[L - 1], kImgLat1, &bars[1]);
+    bulk_g2s(sm + kImgLat0 + kImgLat1, w.e0, kImgE0, &bars[1]);
+  })
+  uint8_t* Wl0 = sm;
+  uint8_t* Wl1 = Wl0 + kImgLat0;
+  uint8_t* We0 = Wl1 + kImgLat1;
+  uint8_t* HA = We0 + kImgE0;
+  uint8_t* A1 = HA + kOpH;
+  uint8_t* AE = A1 + kOp128;
+  float* s_dg = reinterpret_cast<float*>(HA);          // reuses HA + A1 after the last MMA
+  float* s_fc = reinterpret_cast<float*>(AE + kOp64);
+  float* s_sig = s_fc + kT;
+  float* s_eij = s_sig + kT;
+  float* s_du = s_eij + kT;                            // [2][kT]
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    const bool valid = r < m.np;
+    float Y[NLM];
+    {
+      float u[3], d, fc = 0.0f, dfc;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      if (h == 0) {
+        s_fc[r] = fc;
+        s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
+      }
+    }
+    const int i = m.pi[r];
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = 8 * h + cc;
+      float V[NLM], G[NLM], S[NS];
+      const float* g = b.V[L - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? g[lm] : 0.0f;
+      if (valid) load_g(b.gam[L], b.row_ptr, i, c, G);
+      else
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+      tp2_fwd_scalar(V, G, S);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) st1(HA, r, D + c * NS + q, S[q]);
+    }
+    const float* xg = b.X[L - 1] + (size_t)(m.p0 + r) * D;
+    row_to_op(HA, r, xg + 64 * h, valid, 64 * h, 64);
+    if (h == 1) {
+      float z[16] = {};
+      st16(HA, r, 176, z);
+    }
+    mm.run([&] { mma_k(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
+    epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
+      st16(A1, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+      const float fc = s_fc[rr];
+      const float4* xo = reinterpret_cast<const float4*>(xg + n0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 x = valid ? xo[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        o[4 * q] = (x.x + fc * silu_b(v[4 * q])) * kR2;
+        o[4 * q + 1] = (x.y + fc * silu_b(v[4 * q + 1])) * kR2;
+        o[4 * q + 2] = (x.z + fc * silu_b(v[4 * q + 2])) * kR2;
+        o[4 * q + 3] = (x.w + fc * silu_b(v[4 * q + 3])) * kR2;
+      }
+      st16(HA, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 256, HA, 0, We0, 32, 8, false, 0); });
+    if (threadIdx.x < kT) {
+      float ze[32];
+      tmem_ld16(lanes(tmem) + 256, ze);
+      tmem_ld16(lanes(tmem) + 272, ze + 16);
+      const float sig = s_sig[r];
+      float e = 0.0f, dz[32];
+#pragma unroll
+      for (int n = 0; n < E; ++n) {
+        const float wo = __ldg(w.eout + n);
+        e = fmaf(wo, silu_b(ze[n]), e);
+        dz[n] = sig * wo * dsilu_b(ze[n]);
+      }
+      s_eij[r] = valid ? e : 0.0f;
+      st16(AE, r, 0, dz);
+      st16(AE, r, 16, dz + 16);
+    }
+    mm.run([&] { mma_k(tmem + 288, AE, 0, We0, 128, 2, true, 32); });      // dx^L
+    {
+      float du = 0.0f;
+      epi(tmem, 288, 128, [&](int rr, int n0, const float* dx) {
+        float z2[16], o[16];
+        tmem_ld16(lanes(tmem) + 128 + n0, z2);
+        const float fc = s_fc[rr];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          du = fmaf(dx[q], silu_b(z2[q]), du);
+          o[q] = dx[q] * fc * kR2 * dsilu_b(z2[q]);
+        }
+        st16(A1, rr, n0, o);
+      });
+      s_du[h * kT + r] = du * kR2;
+    }
+    mm.run([&] { mma_k(tmem + 128, A1, 0, Wl1, 128, 8, true, 128); });    // da1
+    epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
+      float z1[16], o[16];
+      tmem_ld16(lanes(tmem) + n0, z1);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
+      st16(HA, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 0, HA, 0, Wl0, 176, 8, true, 128); });      // [dx^{L-1}, ds]
+    epi(tmem, 0, 128, [&](int rr, int n0, const float* dh) {
+      float dx[16];
+      tmem_ld16(lanes(tmem) + 288 + n0, dx);
+      if (valid) {
+        float4* g = reinterpret_cast<float4*>(b.dX + (size_t)(m.p0 + rr) * D + n0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          g[q] = make_float4(dh[4 * q] + dx[4 * q] * kR2, dh[4 * q + 1] + dx[4 * q + 1] * kR2,
+                             dh[4 * q + 2] + dx[4 * q + 2] * kR2, dh[4 * q + 3] + dx[4 * q + 3] * kR2);
+      }
+    });
+    {
+      float ds[32];
+      tmem_ld16(lanes(tmem) + 128 + 24 * h, ds);
+      tmem_ld16(lanes(tmem) + 128 + 24 * h + 16, ds + 16);
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = 8 * h + cc;
+        float V[NLM], G[NLM], dV[NLM], dG[NLM];
+        const float* g = b.V[L - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          V[lm] = valid ? g[lm] : 0.0f;
+          dV[lm] = 0.0f;
+          dG[lm] = 0.0f;
+        }
+        if (valid) load_g(b.gam[L], b.row_ptr, i, c, G);
+        else
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+        tp2_bwd_scalar(V, G, ds + cc * NS, dV, dG);
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) s_dg[r * CL + c * NLM + lm] = dG[lm];
+        if (valid) {
+          float* o = b.dV + (size_t)(m.p0 + r) * CL + c * NLM;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) o[lm] = dV[lm];
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < m.nseg) {
+      const int s = threadIdx.x;
+      double acc = 0.0;
+      for (int p = m.sstart[s]; p < m.sstart[s + 1]; ++p) acc += (double)s_eij[p];
+      b.epart[m.tile + m.atom[s]] = acc;
+    }
+    if (threadIdx.x < kT && valid) {
+      b.dU[m.p0 + r] = s_du[r] + s_du[kT + r];
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) b.dY[(size_t)(m.p0 + r) * NLM + lm] = 0.0f;
+    }
+    seg_store(b.dgam[L], m, CL, [&](int p, int x) { return s_dg[p * CL + x]; });
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// ============================================================================
+// Pass B2_k^T: adjoint of the Gamma^{k+1} scatter and of the latent MLP of
+// layer k (its forward recomputed in the tile): dx^{k-1} (residual + latent
+// parts, without the embedding term), ds -> dS, du, dY.
+__global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
+  BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1, {
+    bulk_g2s(sm, w.env[k], kImgEnv, &bars[1]);
+    bulk_g2s(sm + kImgEnv, w.lat0[k - 1], kImgLat0, &bars[1]);
+    bulk_g2s(sm + kImgEnv + kImgLat0, w.lat1[k - 1], kImgLat1, &bars[1]);
+  })
+  uint8_t* Wenv = sm;
+  uint8_t* Wl0 = Wenv + kImgEnv;
+  uint8_t* Wl1 = Wl0 + kImgLat0;
+  uint8_t* HA = Wl1 + kImgLat1;
+  uint8_t* A1 = HA + kOpH;
+  uint8_t* DE = A1 + kOp128;
+  float* s_fc = reinterpret_cast<float*>(DE + kOp64);
+  float* s_Y = s_fc + kT;
+  float* s_dy = s_Y + kT * NLM;
+  float* s_du = s_dy + kT * NLM;   // [2][kT]
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    const bool valid = r < m.np;
+    if (threadIdx.x < kT) {
+      float u[3], d, fc = 0.0f, dfc, Y[NLM];
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      s_fc[r] = fc;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+    }
+    row_to_op(HA, r, b.X[k] + (size_t)(m.p0 + r) * D + 64 * h, valid, 64 * h, 64);
+    mm.run([&] { mma_k(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
+    if (threadIdx.x < kT) {
+      float e[16], de[16];
+      tmem_ld16(lanes(tmem) + 0, e);
+      float dy[NLM];
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
+      for (int c = 0; c < C; ++c) {
+        float dG[NLM];
+        if (valid) load_g(b.dgam[k + 1], b.row_ptr, m.pi[r], c, dG);
+        else
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) dG[lm] = 0.0f;
+        float acc = 0.0f;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          acc = fmaf(dG[lm], s_Y[r * NLM + lm], acc);
+          dy[lm] = fmaf(dG[lm], e[c], dy[lm]);
+        }
+        de[c] = acc;
+      }
+      st16(DE, r, 0, de);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) s_dy[r * NLM + lm] = dy[lm];
+    }
+    mm.run([&] { mma_k(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
+    const float* xg = b.X[k - 1] + (size_t)(m.p0 + r) * D;
+    row_to_op(HA, r, xg + 64 * h, valid, 64 * h, 64);
+    if (h == 1) {
+      row_to_op(HA, r, b.S[k] + (size_t)(m.p0 + r) * (C * NS), valid, 128, 48);
+      float z[16] = {};
+      st16(HA, r, 176, z);
+    }
+    mm.run([&] { mma_k(tmem + 32, HA, 0, Wl0, 128, 11, false, 0); });     // z1
+    epi(tmem, 32, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
+      st16(A1, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 160, A1, 0, Wl1, 128, 8, false, 0); });     // z2
+    {
+      float du = 0.0f;
+      float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
+        float z2[16], o[16], dx[16];
+        tmem_ld16(lanes(tmem) + 160 + n0, z2);
+        const float fc = s_fc[rr];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dx[q] = dxe[q] + (valid ? dxg[n0 + q] : 0.0f);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          du = fmaf(dx[q], silu_b(z2[q]), du);
+          o[q] = dx[q] * fc * kR2 * dsilu_b(z2[q]);
+        }
+        st16(A1, rr, n0, o);
+        if (valid)
+#pragma unroll
+          for (int q = 0; q < 16; ++q) dxg[n0 + q] = dx[q] * kR2;
+      });
+      s_du[h * kT + r] = du * kR2;
+    }
+    mm.run([&] { mma_k(tmem + 160, A1, 0, Wl1, 128, 8, true, 128); });    // da1
+    epi(tmem, 160, 128, [&](int rr, int n0, const float* da) {
+      float z1[16], o[16];
+      tmem_ld16(lanes(tmem) + 32 + n0, z1);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
+      st16(HA, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 288, HA, 0, Wl0, 176, 8, true, 128); });    // [dx, ds]
+    {
+      float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      epi(tmem, 288, 128, [&](int rr, int n0, const float* dh) {
+        if (valid)
+#pragma unroll
+          for (int q = 0; q < 16; ++q) dxg[n0 + q] += dh[q];
+      });
+      float ds[32];
+      tmem_ld16(lanes(tmem) + 288 + 128 + 24 * h, ds);
+      tmem_ld16(lanes(tmem) + 288 + 128 + 24 * h + 16, ds + 16);
+      if (valid) {
+        float* o = b.dS + (size_t)(m.p0 + r) * (C * NS) + 24 * h;
+#pragma unroll
+        for (int q = 0; q < 24; ++q) o[q] = ds[q];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kT && valid) {
+      b.dU[m.p0 + r] += s_du[r] + s_du[kT + r];
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) b.dY[(size_t)(m.p0 + r) * NLM + lm] += s_dy[r * NLM + lm];
+    }
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// ============================================================================
+// Pass B1_k^T: adjoint of mixing and of the tensor product of layer k:
+// dV^{k-1} (k >= 2) or, for k = 1, the embedding adjoint into dx^0 and dY;
+// dGamma^k partials.
+__global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
+  BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
+    bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
+    for (int l = 0; l < 3; ++l) bulk_g2s(sm + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
+  })
+  uint8_t* Wemb = sm;
+  uint8_t* Wmix = Wemb + kImgEmb;
+  uint8_t* DVT = Wmix + 3 * kImgMix;
+  uint8_t* X = DVT + kOpH;
+  uint8_t* DW0 = X + kOp128;
+  float* s_Y = reinterpret_cast<float*>(DW0 + kOp64);
+  float* s_dg = s_Y + kT * NLM;           // [kT][CL]
+  float* s_dy = s_dg + kT * CL;           // [2][kT][NLM]
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    const bool valid = r < m.np;
+    if (threadIdx.x < kT) {
+      float u[3], d, fc, dfc, Y[NLM];
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+    }
+    {
+      const float* g = b.dV + (size_t)(m.p0 + r) * CL;
+      for (int co = 8 * h; co < 8 * h + 8; ++co)
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) st1(DVT, r, 16 * lm + co, valid ? g[co * NLM + lm] : 0.0f);
+    }
+    if (k == 1) {
+      row_to_op(X, r, b.X[0] + (size_t)(m.p0 + r) * D + 64 * h, valid, 64 * h, 64);
+      mm.run([&] { mma_k(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });       // w0
+    }
+    float w0[32];
+    if (k == 1) {
+      tmem_ld16(lanes(tmem) + 24 * h, w0);
+      tmem_ld16(lanes(tmem) + 24 * h + 16, w0 + 16);
+    }
+    const int i = m.pi[r];
+    const float* dsg = b.dS + (size_t)(m.p0 + r) * (C * NS);
+    float dyl[NLM];
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
+    // channels are processed 4 at a time (per thread); for each group the
+    // mixing adjoint is issued in two rounds (l3 <= 1, then l3 = 2) because
+    // all nine products together exceed the TMEM columns
+    for (int g4 = 0; g4 < 2; ++g4) {
+      const int cb = 8 * h + 4 * g4;
+      float dVa[4][NLM];
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4)
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) dVa[c4][lm] = 0.0f;
+      for (int round = 0; round < 2; ++round) {
+        if (round == 0) {
+          mm.run([&] {
+            mma_k(tmem + 64, DVT, 0, Wmix, 48, 1, true, 16);
+            for (int j = 1; j < 4; ++j) mma_k(tmem + 112 + 64 * (j - 1), DVT, j, Wmix + kImgMix, 64, 1, true, 16);
+          });
+        } else {
+          mm.run([&] {
+            for (int j = 4; j < 9; ++j) mma_k(tmem + 64 + 64 * (j - 4), DVT, j, Wmix + 2 * kImgMix, 64, 1, true, 16);
+          });
+        }
+        float tv[5][16];
+        if (round == 0) {
+          tmem_ld16(lanes(tmem) + 64 + cb * 3, tv[0]);
+          for (int j = 1; j < 4; ++j) tmem_ld16(lanes(tmem) + 112 + 64 * (j - 1) + cb * 4, tv[j]);
+        } else {
+          for (int j = 4; j < 9; ++j) tmem_ld16(lanes(tmem) + 64 + 64 * (j - 4) + cb * 4, tv[j - 4]);
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const int c = cb + c4, cc = 4 * g4 + c4;
+          float dT[TP2_NT];
+#pragma unroll
+          for (int o = 0; o < TP2_NT; ++o) dT[o] = 0.0f;
+          if (round == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) dT[q] = tv[0][c4 * 3 + q] + (valid ? dsg[c * NS + q] : 0.0f);
+#pragma unroll
+            for (int mm1 = 0; mm1 < 3; ++mm1)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) dT[3 + q * 3 + mm1] = tv[1 + mm1][c4 * 4 + q];
+          } else {
+#pragma unroll
+            for (int mm2 = 0; mm2 < 5; ++mm2)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = tv[mm2][c4 * 4 + q];
+          }
+          float V[NLM], G[NLM], dG[NLM];
+          if (k == 1) {
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[cc * 3 + l_of(lm)] * s_Y[r * NLM + lm];
+          } else {
+            const float* gv = b.V[k - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? gv[lm] : 0.0f;
+          }
+          if (valid) load_g(b.gam[k], b.row_ptr, i, c, G);
+          else
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) dG[lm] = round == 0 ? 0.0f : s_dg[r * CL + c * NLM + lm];
+          tp2_bwd(V, G, dT, dVa[c4], dG);
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) s_dg[r * CL + c * NLM + lm] = dG[lm];
+        }
+      }
+      if (k >= 2) {
+        if (valid) {
+          float* o = b.dV + (size_t)(m.p0 + r) * CL + cb * NLM;
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) o[c4 * NLM + lm] = dVa[c4][lm];
+        }
+      } else {
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const int cc = 4 * g4 + c4;
+          float dw[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) {
+            dw[l_of(lm)] = fmaf(dVa[c4][lm], s_Y[r * NLM + lm], dw[l_of(lm)]);
+            dyl[lm] = fmaf(w0[cc * 3 + l_of(lm)], dVa[c4][lm], dyl[lm]);
+          }
+#pragma unroll
+          for (int l = 0; l < 3; ++l) st1(DW0, r, (cb + c4) * 3 + l, dw[l]);
+        }
+      }
+    }
+    if (k == 1) {
+      mm.run([&] { mma_k(tmem + 384, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
+      float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      epi(tmem, 384, 128, [&](int rr, int n0, const float* v) {
+        if (valid)
+#pragma unroll
+          for (int q = 0; q < 16; ++q) dxg[n0 + q] += v[q];
+      });
+    }
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dyl[lm];
+    __syncthreads();
+    if (threadIdx.x < kT && valid && k == 1) {
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm)
+        b.dY[(size_t)(m.p0 + r) * NLM + lm] += s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm];
+    }
+    seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CL + x]; });
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// ============================================================================
+// Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP (recomputed)
+// and of the geometry; writes g_ij = dE/dDelta_ij.
+__global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
+  BF_PROLOGUE(kImgTb0 + kImgTb1 + kImgEnv, {
+    bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
+    bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
+    bulk_g2s(sm + kImgTb0 + kImgTb1, w.env[0], kImgEnv, &bars[1]);
+  })
+  uint8_t* Wtb0 = sm;
+  uint8_t* Wtb1 = Wtb0 + kImgTb0;
+  uint8_t* Wenv = Wtb1 + kImgTb1;
+  uint8_t* H0 = Wenv + kImgEnv;
+  uint8_t* A1 = H0 + kOp64;
+  uint8_t* X = A1 + kOp128;
+  uint8_t* DE = X + kOp128;
+  float* s_geo = reinterpret_cast<float*>(DE + kOp64);   // [kT][8]: u, d, fc, dfc
+  float* s_dB = s_geo + kT * 8;                           // [kT][NB]
+  float* s_Y = s_dB + kT * NB;
+  float* s_dy = s_Y + kT * NLM;
+  float* s_du = s_dy + kT * NLM;                          // [2][kT]
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
+    meta_setup(b, tile, P, m);
+    const bool valid = r < m.np;
+    if (threadIdx.x < kT) {
+      float h0[16], Y[NLM], u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f, B[NB], dB[NB];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) h0[q] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) dB[q] = 0.0f;
+      if (valid) {
+        geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+        bessel<NB>(d, w.rc, B, dB);
+        h0[b.species[m.pi[r]]] = 1.0f;
+        h0[2 + b.species[m.pj[r]]] = 1.0f;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
+      }
+      float* g = s_geo + r * 8;
+      g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) s_dB[r * NB + q] = dB[q];
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+      st16(H0, r, 0, h0);
+    }
+    mm.run([&] { mma_k(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });       // z1
+    epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
+      st16(A1, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });    // z2
+    epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
+      float o[16];
+      const float fc = s_geo[rr * 8 + 4];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
+      st16(X, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });      // e^1
+    if (threadIdx.x < kT) {
+      float e[16], de[16], dy[NLM];
+      tmem_ld16(lanes(tmem) + 256, e);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
+      for (int c = 0; c < C; ++c) {
+        float dG[NLM];
+        if (valid) load_g(b.dgam[1], b.row_ptr, m.pi[r], c, dG);
+        else
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) dG[lm] = 0.0f;
+        float acc = 0.0f;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          acc = fmaf(dG[lm], s_Y[r * NLM + lm], acc);
+          dy[lm] = fmaf(dG[lm], e[c], dy[lm]);
+        }
+        de[c] = acc;
+      }
+      st16(DE, r, 0, de);
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) s_dy[r * NLM + lm] = dy[lm];
+    }
+    mm.run([&] { mma_k(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });    // env1^T de
+    {
+      float du = 0.0f;
+      const float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
+        float z2[16], o[16];
+        tmem_ld16(lanes(tmem) + 128 + n0, z2);
+        const float fc = s_geo[rr * 8 + 4];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float dx = dxe[q] + (valid ? dxg[n0 + q] : 0.0f);
+          du = fmaf(dx, silu_b(z2[q]), du);
+          o[q] = dx * fc * dsilu_b(z2[q]);
+        }
+        st16(A1, rr, n0, o);
+      });
+      s_du[h * kT + r] = du;
+    }
+    mm.run([&] { mma_k(tmem + 128, A1, 0, Wtb1, 128, 8, true, 128); });   // da1
+    epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
+      float z1[16], o[16];
+      tmem_ld16(lanes(tmem) + n0, z1);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
+      st16(X, rr, n0, o);
+    });
+    mm.run([&] { mma_k(tmem + 416, X, 0, Wtb0, 16, 8, true, 128); });     // dh0
+    if (threadIdx.x < kT) {
+      float dh[16];
+      tmem_ld16(lanes(tmem) + 416, dh);
+      if (valid) {
+        const float* g = s_geo + r * 8;
+        const float u[3] = {g[0], g[1], g[2]};
+        const float d = g[3], dfc = g[5];
+        const size_t pp = (size_t)(m.p0 + r);
+        float gd = (s_du[r] + s_du[kT + r] + b.dU[pp]) * dfc;
+#pragma unroll
+        for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * NB + n], gd);
+        float dY[NLM];
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[pp * NLM + lm];
+        float gu[3];
+        sph_harm_vjp<2>(u[0], u[1], u[2], dY, gu);
+        const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
+        const float inv = 1.0f / d;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) b.G[pp * 3 + a] = gd * u[a] + (gu[a] - ud * u[a]) * inv;
+      }
+    }
+    __syncthreads();
+  }
+  BF_EPILOGUE
+}
+
+// shared-memory bytes of each kernel (+1024 for the manual 1024-byte alignment)
+constexpr size_t kSmA = 1024 + kImgTb0 + kImgTb1 + kImgEnv + kOp64 + 2 * kOp128 + 4 * (kT + kT * NLM + kT * 16);
+constexpr size_t kSmB1 = 1024 + kImgEmb + 3 * kImgMix + kOp128 + kOpT + 4 * (kT * NLM);
+constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * 16);
+constexpr size_t kSmC = 1024 + kImgLat0 + kImgLat1 + kImgE0 + kOpH + kOp128 + kOp64 + 4 * (5 * kT);
+constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 + 4 * (kT + 2 * kT * NLM + 2 * kT);
+constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 + 4 * (kT * NLM + kT * CL + 2 * kT * NLM);
+constexpr size_t kSmAT = 1024 + kImgTb0 + kImgTb1 + kImgEnv + kOp64 + 2 * kOp128 + kOp64 +
+                         4 * (kT * 8 + kT * NB + 2 * kT * NLM + 2 * kT);
+static_assert(kSmB1 <= 232448 && kSmC <= 232448 && kSmB2T <= 232448 && kSmB1T <= 232448, "smem");
+static_assert(kOpH + kOp128 >= 4 * kT * CL, "pass C reuses HA + A1 for the dGamma contributions");
+
+int g_sms = 0;
+
+}  // namespace
+
+bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
+  return lmax == 2 && C_ == C && D_ == D && E_ == E && L >= 2 && L <= kMaxLayers;
+}
+
+int bf16_tile() { return kT; }
+
+void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_bf_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
+    cudaFuncSetAttribute(k_bf_b1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1);
+    cudaFuncSetAttribute(k_bf_b2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
+    cudaFuncSetAttribute(k_bf_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
+    cudaFuncSetAttribute(k_bf_b2t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2T);
+    cudaFuncSetAttribute(k_bf_b1t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
+    cudaFuncSetAttribute(k_bf_at, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    init = true;
+  }
+  const int64_t tiles = (capacity + kT - 1) / kT;
+  const int grid = (int)std::min<int64_t>(tiles, g_sms > 0 ? g_sms : 148);
+  const int L = w.n_layers;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], s);
+  };
+  mark(0);
+  k_bf_a<<<grid, kThr, kSmA, s>>>(w, b);
+  mark(1);
+  for (int k = 1; k < L; ++k) {
+    k_bf_b1<<<grid, kThr, kSmB1, s>>>(w, b, k);
+    k_bf_b2<<<grid, kThr, kSmB2, s>>>(w, b, k);
+  }
+  mark(2);
+  k_bf_c<<<grid, kThr, kSmC, s>>>(w, b);
+  mark(3);
+  for (int k = L - 1; k >= 1; --k) {
+    k_bf_b2t<<<grid, kThr, kSmB2T, s>>>(w, b, k);
+    k_bf_b1t<<<grid, kThr, kSmB1T, s>>>(w, b, k);
+  }
+  mark(4);
+  k_bf_at<<<grid, kThr, kSmAT, s>>>(w, b);
+  mark(5);
+}
+
+}  // namespace al
