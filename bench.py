@@ -43,6 +43,8 @@ ALG_MAC_PER_PAIR = {
 
 WORKLOADS = {
     "fp32_6912": dict(n_mol=1728, precision=0, dt=0.25, model="main", dtype="f32"),
+    "bf16_110592": dict(n_mol=27648, precision=1, dt=0.25, model="main", dtype="bf16"),
+    "bf16_6912": dict(n_mol=1728, precision=1, dt=0.25, model="main", dtype="bf16"),
 }
 
 

@@ -54,7 +54,9 @@ extern "C" {
 #define ALLEGRO_E_BLOB            11  /* malformed weights blob                  */
 
 #define ALLEGRO_FP32 0   /* every per-pair GEMM in FP32 on CUDA cores           */
-#define ALLEGRO_BF16 1   /* per-pair GEMMs in BF16 with FP32 accumulation       */
+#define ALLEGRO_BF16 1   /* per-pair GEMMs on tensor cores, BF16 operands,      */
+                         /* FP32 accumulation (2-layer l_max 2 model)           */
+#define ALLEGRO_FP16 2   /* same tensor-core path with FP16 operands            */
 
 typedef struct allegro_ctx allegro_ctx;
 
@@ -123,7 +125,9 @@ int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col,
  *  energy_out   : host, total energy E (FP64).
  *  forces_out   : host or device, N x 3 FP32 = -dE/dr (may be NULL).
  *  atom_energy  : host or device, N FP64 per-atom energies E_i (may be NULL).
- *  precision    : ALLEGRO_FP32 or ALLEGRO_BF16.
+ *  precision    : ALLEGRO_FP32, ALLEGRO_BF16 or ALLEGRO_FP16 (the last two:
+ *                 E_UNSUPPORTED unless l_max = 2, C = 16, D = 128, E = 32,
+ *                 at least two layers).
  * On ALLEGRO_E_PAIR_OVERFLOW nothing is written; the context has grown and
  * the call may simply be repeated.
  */

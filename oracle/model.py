@@ -57,7 +57,15 @@ def envelope(d, r_cut, p=6):
 
 
 class OracleModel:
-    def __init__(self, blob):
+    """emulate: None (exact FP64), "bf16" or "fp16".  With emulation, every
+    per-pair GEMM (two-body, embedding, env, mixing, latent and energy hidden
+    layers) rounds its input and its pre-scaled weight matrix (1/sqrt(fan_in),
+    and 1/sqrt(nu) for env, folded in first) to that type and accumulates in
+    FP64: the operand precision of the tensor-core path, used to check that
+    path separately from the sensitivity of the model to rounding.  The energy
+    output layer, tensor products and all elementwise steps stay FP64."""
+
+    def __init__(self, blob, emulate=None):
         cfg, w, names = read_blob(blob)
         self.cfg = cfg
         self.names = names
@@ -72,6 +80,20 @@ class OracleModel:
         self.cg = {p: torch.tensor(real_cg(*p), dtype=F64) for p in self.paths}
         if cfg["poly_p"] != 6:
             raise ValueError("poly_p = 6 only")
+        if emulate not in (None, "bf16", "fp16"):
+            raise ValueError("emulate must be None, 'bf16' or 'fp16'")
+        self.emulate = emulate
+        self._qdt = {"bf16": torch.bfloat16, "fp16": torch.float16}.get(emulate)
+
+    def _q(self, x):
+        return x if self._qdt is None else x.to(self._qdt).to(F64)
+
+    def _qlin(self, x, W, extra=1.0):
+        """Linear layer; in emulation mode the GEMM operands are rounded."""
+        if self._qdt is None:
+            return self._lin(x, W)
+        s = extra / math.sqrt(W.shape[1])
+        return self._q(x) @ self._q(W * s).T
 
     # ------------------------------------------------------------------ helpers
     def params(self):
@@ -84,7 +106,7 @@ class OracleModel:
 
     def _mlp(self, x, Ws, last_act=True):
         for k, W in enumerate(Ws):
-            x = self._lin(x, W)
+            x = self._qlin(x, W)
             if last_act or k + 1 < len(Ws):
                 x = silu(x)
         return x
@@ -125,14 +147,17 @@ class OracleModel:
         h = torch.cat([onehot[Z[i]], onehot[Z[j]], B], dim=1)
         nlat = len(cfg["latent"])
         x = fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)])
-        w0 = self._lin(x, w["embed"]).view(P, C, lmax + 1)
+        w0 = self._qlin(x, w["embed"]).view(P, C, lmax + 1)
         V = [w0[:, :, l, None] * Y[l][:, None, :] for l in range(lmax + 1)]
         for layer in range(1, self.L + 1):
             last = layer == self.L
-            e = self._lin(x, w[f"layer{layer}.env"])                 # (P, C)
+            if self._qdt is None:
+                e = self._lin(x, w[f"layer{layer}.env"]) / math.sqrt(self.nu)   # (P, C)
+            else:
+                e = self._qlin(x, w[f"layer{layer}.env"], 1.0 / math.sqrt(self.nu))
             G = []
             for l in range(lmax + 1):
-                contrib = e[:, :, None] * Y[l][:, None, :] / math.sqrt(self.nu)
+                contrib = e[:, :, None] * Y[l][:, None, :]
                 Gl = torch.zeros((N, C, 2 * l + 1), dtype=F64).index_add(0, i, contrib)
                 G.append(Gl[i])
             T = {}
@@ -150,7 +175,11 @@ class OracleModel:
                     Tl = torch.stack([T[p] for p in ps], dim=2)        # (P, C, Pl, 2l3+1)
                     Tl = Tl.reshape(P, C * len(ps), 2 * l3 + 1)
                     Wm = w[f"layer{layer}.mix{l3}"]
-                    newV.append(torch.einsum("oi,pim->pom", Wm, Tl) / math.sqrt(C * len(ps)))
+                    if self._qdt is None:
+                        newV.append(torch.einsum("oi,pim->pom", Wm, Tl) / math.sqrt(C * len(ps)))
+                    else:
+                        Wq = self._q(Wm / math.sqrt(C * len(ps)))
+                        newV.append(torch.einsum("oi,pim->pom", Wq, self._q(Tl)))
                 V = newV
             m = self._mlp(torch.cat([x, s], dim=1),
                           [w[f"layer{layer}.latent.{k}"] for k in range(nlat)])

@@ -15,6 +15,7 @@ from .build_lib import LIB, build
 
 ALLEGRO_FP32 = 0
 ALLEGRO_BF16 = 1
+ALLEGRO_FP16 = 2
 
 _STATUS = {
     0: "OK", 1: "E_INVALID_ARG", 2: "E_MISMATCH", 3: "E_CUTOFF_TOO_LARGE",
@@ -207,4 +208,4 @@ def allegro_selftest_mma_mode(a, b, d, mode):
     _check(None, lib().allegro_selftest_mma_mode(int(n), int(k), _ptr(a), _ptr(b), _ptr(d), int(mode)))
 
 
-__all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED
+__all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "ALLEGRO_FP16", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED

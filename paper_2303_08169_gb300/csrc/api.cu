@@ -116,6 +116,8 @@ struct allegro_ctx {
   ModelW w{};
   uint8_t* d_bw = nullptr;     // BF16 swizzled weight images
   BfW bw{};
+  uint8_t* d_hw = nullptr;     // FP16 swizzled weight images
+  BfW hw{};
   bool bf16_ok = false;
   // allocations
   std::vector<void*> allocs;
@@ -250,6 +252,8 @@ int upload_weights(allegro_ctx* c) {
   return ALLEGRO_OK;
 }
 
+uint16_t f2h(float f) { return __half_as_ushort(__float2half_rn(f)); }
+
 uint16_t f2bf(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -257,9 +261,9 @@ uint16_t f2bf(float f) {
   return (uint16_t)(u >> 16);
 }
 
-// BF16 tensor-core images (layout of umma.cuh) of every linear layer of the
-// main model, pre-scaled like the FP32 copies.
-int upload_weights_bf16(allegro_ctx* c) {
+// BF16 (or FP16) tensor-core images (layout of umma.cuh) of every linear
+// layer of the main model, pre-scaled like the FP32 copies.
+int upload_weights_bf16(allegro_ctx* c, bool fp16) {
   const Blob& B = c->blob;
   std::vector<uint8_t> img;
   auto add = [&](const Tensor* T, double extra, int Rimg, int Kimg) -> size_t {
@@ -268,7 +272,8 @@ int upload_weights_bf16(allegro_ctx* c) {
     const double s = extra / std::sqrt((double)T->cols);
     for (uint32_t r = 0; r < T->rows; ++r)
       for (uint32_t k = 0; k < T->cols; ++k) {
-        const uint16_t h = f2bf((float)(T->data[r * T->cols + k] * s));
+        const float x = (float)(T->data[r * T->cols + k] * s);
+        const uint16_t h = fp16 ? f2h(x) : f2bf(x);
         std::memcpy(img.data() + base + al::umma::sw128_off((int)r, (int)k, Rimg), &h, 2);
       }
     return base;
@@ -286,21 +291,22 @@ int upload_weights_bf16(allegro_ctx* c) {
     if (k < B.L)
       for (int l = 0; l < 3; ++l) o_mix[k - 1][l] = add(B.find(pre + "mix" + std::to_string(l)), 1.0, 16, 64);
   }
-  c->d_bw = c->dalloc<uint8_t>(img.size());
-  if (!c->d_bw) return c->fail(ALLEGRO_E_OOM, "BF16 weights allocation failed");
-  if (cudaMemcpy(c->d_bw, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-    return cuda_check(c, "BF16 weights upload");
-  BfW& w = c->bw;
-  w.tb0 = c->d_bw + o_tb0;
-  w.tb1 = c->d_bw + o_tb1;
-  w.emb = c->d_bw + o_emb;
-  w.e0 = c->d_bw + o_e0;
+  uint8_t* dev = c->dalloc<uint8_t>(img.size());
+  if (!dev) return c->fail(ALLEGRO_E_OOM, "tensor-core weights allocation failed");
+  if (cudaMemcpy(dev, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_check(c, "tensor-core weights upload");
+  (fp16 ? c->d_hw : c->d_bw) = dev;
+  BfW& w = fp16 ? c->hw : c->bw;
+  w.tb0 = dev + o_tb0;
+  w.tb1 = dev + o_tb1;
+  w.emb = dev + o_emb;
+  w.e0 = dev + o_e0;
   for (uint32_t k = 1; k <= B.L; ++k) {
-    w.env[k - 1] = c->d_bw + o_env[k - 1];
-    w.lat0[k - 1] = c->d_bw + o_l0[k - 1];
-    w.lat1[k - 1] = c->d_bw + o_l1[k - 1];
+    w.env[k - 1] = dev + o_env[k - 1];
+    w.lat0[k - 1] = dev + o_l0[k - 1];
+    w.lat1[k - 1] = dev + o_l1[k - 1];
     if (k < B.L)
-      for (int l = 0; l < 3; ++l) w.mix[k - 1][l] = c->d_bw + o_mix[k - 1][l];
+      for (int l = 0; l < 3; ++l) w.mix[k - 1][l] = dev + o_mix[k - 1][l];
   }
   w.eout = c->w.eout;
   for (int s = 0; s < 2; ++s) w.sigma[s] = (float)B.sigma[s];
@@ -400,6 +406,8 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
     c->dfree(pb.dgam[k]);
     pb.gam[k] = pb.dgam[k] = nullptr;
   }
+  // per-pair arrays of the BF16 path are tile-SoA over 128-pair tiles
+  const int64_t capr = (cap + 127) / 128 * 128;
   c->nb.pi = c->dalloc<int>(cap);
   c->nb.pj = c->dalloc<int>(cap);
   c->nb.pcode = c->dalloc<int>(cap);
@@ -408,18 +416,18 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   c->nb.skeys = c->dalloc<unsigned long long>(cap);
   bool ok = c->nb.pi && c->nb.pj && c->nb.pcode && c->nb.rev && c->nb.keys && c->nb.skeys;
   for (uint32_t k = 0; k < B.L && ok; ++k) {
-    pb.X[k] = c->dalloc<float>((size_t)cap * c->D);
+    pb.X[k] = c->dalloc<float>((size_t)capr * c->D);
     ok = ok && pb.X[k];
     if (k >= 1) {
-      pb.V[k] = c->dalloc<float>((size_t)cap * CL);
+      pb.V[k] = c->dalloc<float>((size_t)capr * CL);
       ok = ok && pb.V[k];
     }
   }
-  pb.dX = c->dalloc<float>((size_t)cap * c->D);
-  pb.dV = c->dalloc<float>((size_t)cap * CL);
-  pb.dU = c->dalloc<float>(cap);
-  pb.dY = c->dalloc<float>((size_t)cap * NLM);
-  pb.G = c->dalloc<float>((size_t)cap * 3);
+  pb.dX = c->dalloc<float>((size_t)capr * c->D);
+  pb.dV = c->dalloc<float>((size_t)capr * CL);
+  pb.dU = c->dalloc<float>(capr);
+  pb.dY = c->dalloc<float>((size_t)capr * NLM);
+  pb.G = c->dalloc<float>((size_t)capr * 3);
   for (int k = 0; k < kMaxLayers; ++k) {
     c->dfree(pb.S[k]);
     pb.S[k] = nullptr;
@@ -429,10 +437,10 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   if (c->bf16_ok) {
     const int NSC = B.C * 3;
     for (uint32_t k = 1; k < B.L && ok; ++k) {
-      pb.S[k] = c->dalloc<float>((size_t)cap * NSC);
+      pb.S[k] = c->dalloc<float>((size_t)capr * NSC);
       ok = ok && pb.S[k];
     }
-    pb.dS = c->dalloc<float>((size_t)cap * NSC);
+    pb.dS = c->dalloc<float>((size_t)capr * NSC);
     ok = ok && pb.dS;
   }
   const int64_t rows = rows_needed;
@@ -550,8 +558,9 @@ int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* s
 void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, cudaEvent_t* ev) {
   const Blob& B = c->blob;
   int tile;
-  if (precision == ALLEGRO_BF16) {
-    bf16_energy_forces(c->bw, c->pb, c->capacity, s, ev);
+  if (precision == ALLEGRO_BF16 || precision == ALLEGRO_FP16) {
+    const bool h = precision == ALLEGRO_FP16;
+    bf16_energy_forces(h ? c->hw : c->bw, c->pb, c->capacity, s, ev, h);
     tile = bf16_tile();
   } else {
     fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, ev);
@@ -562,10 +571,10 @@ void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, cudaEvent_t
 }
 
 int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
-  if (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16)
-    return c->fail(ALLEGRO_E_INVALID_ARG, "precision must be ALLEGRO_FP32 or ALLEGRO_BF16");
-  if (precision == ALLEGRO_BF16 && !c->bf16_ok)
-    return c->fail(ALLEGRO_E_UNSUPPORTED, "the BF16 tensor-core path is built for the 2+-layer l_max 2 model only");
+  if (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16 && precision != ALLEGRO_FP16)
+    return c->fail(ALLEGRO_E_INVALID_ARG, "precision must be ALLEGRO_FP32, ALLEGRO_BF16 or ALLEGRO_FP16");
+  if (precision != ALLEGRO_FP32 && !c->bf16_ok)
+    return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
   fill_passbufs(c, L);
   launch_model(c, precision, c->stream, nullptr);
   return cuda_check(c, "model launch");
@@ -623,7 +632,8 @@ int allegro_create(const void* weights_blob, size_t blob_bytes, const double* sp
   for (int s = 0; s < 2; ++s) c->mass[s] = species_mass[s];
   int rc = upload_weights(c);
   c->bf16_ok = bf16_supported((int)B.lmax, (int)B.C, c->D, c->E, (int)B.L);
-  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c);
+  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, false);
+  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, true);
   if (rc) {
     g_err = c->err;
     delete c;
@@ -727,7 +737,10 @@ int allegro_outlier_count(allegro_ctx* ctx, int64_t n_atoms, const float* forces
 }
 
 int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
-  if (!ctx || (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16)) return ALLEGRO_E_INVALID_ARG;
+  if (!ctx || (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16 && precision != ALLEGRO_FP16))
+    return ALLEGRO_E_INVALID_ARG;
+  if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
+    return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
   if (precision != ctx->md_precision && ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;

@@ -83,8 +83,9 @@ struct BfW {
 
 bool bf16_supported(int lmax, int C, int D, int E, int L);
 int bf16_tile();
+// fp16: operands in FP16 (images of w must then be FP16 too), else BF16.
 void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s,
-                        cudaEvent_t* ev = nullptr);
+                        cudaEvent_t* ev = nullptr, bool fp16 = false);
 
 // FP32 path: one launcher per pass sequence; templated on the model shape in
 // the .cu file, dispatched by (lmax, C, D, E).

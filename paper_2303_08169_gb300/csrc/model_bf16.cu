@@ -55,6 +55,19 @@ constexpr uint32_t kOpT = sw128_bytes(128, 576);
 __device__ __constant__ int kSlice[9] = {0, 48, 112, 176, 240, 304, 368, 432, 496};
 AL_DEV int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
 
+// Operand type of the tensor-core GEMMs: BF16 (the precision the method
+// names for per-pair GEMMs) or FP16 (same tensor-core rate, 3 more mantissa
+// bits).  Both accumulate in FP32.
+template <class T> struct Op;
+template <> struct Op<__nv_bfloat16> {
+  static constexpr uint32_t fmt = 1;
+  static AL_DEV uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+};
+template <> struct Op<__half> {
+  static constexpr uint32_t fmt = 0;
+  static AL_DEV uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+};
+
 AL_DEV float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -151,6 +164,41 @@ AL_DEV void load_g(const float* __restrict__ part, const int* __restrict__ row_p
   }
 }
 
+// Per-pair arrays of this path use a tile-SoA layout: element (pair p,
+// feature f) of a W-wide array lives at ((p / 128) * W + f) * 128 + p % 128,
+// so the 32 lanes of a warp (consecutive tile rows) touch consecutive floats.
+AL_DEV size_t sidx(const Meta& m, int W, int f, int r) { return ((size_t)m.tile * W + f) * kT + r; }
+
+// Gamma (or dGamma) of the tile's first kSegCap centre atoms, summed once per
+// tile into shared memory; rows of later segments read the partials directly.
+constexpr int kSegCap = 8;
+AL_DEV void stage_g(const float* __restrict__ part, const int* __restrict__ row_ptr, const Meta& m, float* s) {
+  const int ns = min(m.nseg, kSegCap);
+  for (int idx = threadIdx.x; idx < ns * CL; idx += kThr) {
+    const int sg = idx / CL, x = idx % CL;
+    const int i = m.atom[sg];
+    const int t0 = row_ptr[i] / kT, t1 = (row_ptr[i + 1] - 1) / kT;
+    float acc = 0.0f;
+    for (int tt = t0; tt <= t1; ++tt) acc += part[(size_t)(tt + i) * CL + x];
+    s[sg * CL + x] = acc;
+  }
+}
+AL_DEV void get_g(const float* s, const float* __restrict__ part, const int* __restrict__ row_ptr, const Meta& m,
+                  int r, bool valid, int c, float* G) {
+  if (!valid) {
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+    return;
+  }
+  const int sg = m.seg[r];
+  if (sg < kSegCap) {
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) G[lm] = s[sg * CL + c * NLM + lm];
+  } else {
+    load_g(part, row_ptr, m.pi[r], c, G);
+  }
+}
+
 AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float u[3], float& d, float& fc,
                      float& dfc, float* Y) {
   Box box{{b.L[0], b.L[1], b.L[2]}};
@@ -170,8 +218,9 @@ AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float 
 // D[128 x N] = A[128 x K-slice from k-step kk0, nk steps] * B, B either the
 // K-major image of an [N x K] matrix or (b_mn) the image of a [P x N] matrix
 // read MN-major.
+template <class Tin>
 AL_DEV void mma_k(uint32_t d, const uint8_t* A, int kk0, const uint8_t* B, int N, int nk, bool b_mn, int P) {
-  const uint32_t idesc = idesc_bf16(128, N, b_mn);
+  const uint32_t idesc = idesc_f16kind(128, N, b_mn, Op<Tin>::fmt);
   const uint32_t a = smem_u32(A), bb = smem_u32(B);
   for (int i = 0; i < nk; ++i) {
     const int kk = kk0 + i;
@@ -222,30 +271,33 @@ AL_DEV void epi(uint32_t tmem, int col0, int N, F&& f) {
   }
 }
 
-AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
-  st_bf16x8(A, sw128_off(r, c0, 128), v);
-  st_bf16x8(A, sw128_off(r, c0 + 8, 128), v + 8);
+template <class Tin>
+AL_DEV void st8(uint8_t* A, uint32_t off, const float* v) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = (uint32_t)Op<Tin>::bits(v[2 * q]) | ((uint32_t)Op<Tin>::bits(v[2 * q + 1]) << 16);
+  *reinterpret_cast<uint4*>(A + off) = make_uint4(w[0], w[1], w[2], w[3]);
 }
+template <class Tin>
+AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
+  st8<Tin>(A, sw128_off(r, c0, 128), v);
+  st8<Tin>(A, sw128_off(r, c0 + 8, 128), v + 8);
+}
+template <class Tin>
 AL_DEV void st1(uint8_t* A, int r, int c, float v) {
-  *reinterpret_cast<__nv_bfloat16*>(A + sw128_off(r, c, 128)) = __float2bfloat16_rn(v);
+  *reinterpret_cast<uint16_t*>(A + sw128_off(r, c, 128)) = Op<Tin>::bits(v);
 }
 
-// row r of a pair-major FP32 array (W wide) converted into columns [c0, c0+n)
-AL_DEV void row_to_op(uint8_t* A, int r, const float* __restrict__ g, bool valid, int c0, int n) {
+// features [f0, f0+n) of tile row r of a tile-SoA FP32 array (W wide),
+// converted into operand columns [c0, c0+n)
+template <class Tin>
+AL_DEV void row_to_op(uint8_t* A, const Meta& m, int r, const float* __restrict__ g, int W, int f0, bool valid,
+                      int c0, int n) {
   for (int k = 0; k < n; k += 16) {
     float v[16];
-    if (valid) {
-      const float4* s = reinterpret_cast<const float4*>(g + k);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 x = s[q];
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-    }
-    st16(A, r, c0 + k, v);
+    for (int q = 0; q < 16; ++q) v[q] = valid ? g[sidx(m, W, f0 + k + q, r)] : 0.0f;
+    st16<Tin>(A, r, c0 + k, v);
   }
 }
 
@@ -293,6 +345,7 @@ constexpr int kFlagTimeoutBit = 4;
 
 // ============================================================================
 // Pass A: geometry, two-body MLP (12 -> 128 -> 128), x0, env1 -> Gamma^1.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
   BF_PROLOGUE(kImgTb0 + kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
@@ -329,29 +382,27 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-      st16(H0, r, 0, h0);
+      st16<Tin>(H0, r, 0, h0);
     }
-    mm.run([&] { mma_k(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });
     epi(tmem, 0, 128, [&](int r, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16(A1, r, n0, o);
+      st16<Tin>(A1, r, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int r, int n0, const float* v) {
       float o[16];
       const float fc = s_fc[r];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
-      st16(X, r, n0, o);
-      if (r < m.np) {
-        float4* g = reinterpret_cast<float4*>(b.X[0] + (size_t)(m.p0 + r) * D + n0);
+      st16<Tin>(X, r, n0, o);
+      if (r < m.np)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) g[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      }
+        for (int q = 0; q < 16; ++q) b.X[0][sidx(m, D, n0 + q, r)] = o[q];
     });
-    mm.run([&] { mma_k(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -367,6 +418,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
 
 // ============================================================================
 // Pass B1_k: tensor product of layer k and channel mixing -> V^k, scalars S^k.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
     bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
@@ -377,6 +429,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   uint8_t* X = Wmix + 3 * kImgMix;
   uint8_t* T = X + kOp128;
   float* s_Y = reinterpret_cast<float*>(T + kOpT);
+  float* s_g = s_Y + kT * NLM;            // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -390,9 +443,11 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     const bool valid = r < m.np;
     if (k == 1) {
-      row_to_op(X, r, b.X[0] + (size_t)(m.p0 + r) * D + 64 * h, valid, 64 * h, 64);
-      mm.run([&] { mma_k(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
+      row_to_op<Tin>(X, m, r, b.X[0], D, 64 * h, valid, 64 * h, 64);
+      stage_g(b.gam[k], b.row_ptr, m, s_g);
+      mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
     } else {
+      stage_g(b.gam[k], b.row_ptr, m, s_g);
       __syncthreads();
     }
     float w0[32];
@@ -408,31 +463,25 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[cc * 3 + l_of(lm)] * s_Y[r * NLM + lm];
       } else {
-        const float* g = b.V[k - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? g[lm] : 0.0f;
+        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
       }
-      if (valid) load_g(b.gam[k], b.row_ptr, i, c, G);
-      else
-#pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+      get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
       tp2_fwd(V, G, Tv);
 #pragma unroll
       for (int j = 0; j < 9; ++j) {
         const int l3 = l_of(j), mm3 = j - l3 * l3, Pl = tp2_P(l3), nm = 2 * l3 + 1;
 #pragma unroll
-        for (int q = 0; q < Pl; ++q) st1(T, r, kSlice[j] + c * Pl + q, Tv[tp2_toff(l3) + q * nm + mm3]);
+        for (int q = 0; q < Pl; ++q) st1<Tin>(T, r, kSlice[j] + c * Pl + q, Tv[tp2_toff(l3) + q * nm + mm3]);
       }
-      if (valid) {
-        float* s = b.S[k] + (size_t)(m.p0 + r) * (C * NS) + c * NS;
+      if (valid)
 #pragma unroll
-        for (int q = 0; q < NS; ++q) s[q] = Tv[q];
-      }
+        for (int q = 0; q < NS; ++q) b.S[k][sidx(m, C * NS, c * NS + q, r)] = Tv[q];
     }
     mm.run([&] {
       for (int j = 0; j < 9; ++j) {
         const int l3 = l_of(j), Pl = tp2_P(l3);
-        mma_k(tmem + 64 + 16 * j, T, kSlice[j] / 16, Wmix + l3 * kImgMix, 16, C * Pl / 16, false, 0);
+        mma_k<Tin>(tmem + 64 + 16 * j, T, kSlice[j] / 16, Wmix + l3 * kImgMix, 16, C * Pl / 16, false, 0);
       }
     });
     {
@@ -440,11 +489,9 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       for (int j = (h == 0 ? 0 : 5); j < (h == 0 ? 5 : 9); ++j) {
         float v[16];
         tmem_ld16(base + 64 + 16 * j, v);
-        if (valid) {
-          float* g = b.V[k] + (size_t)(m.p0 + r) * CL + j;
+        if (valid)
 #pragma unroll
-          for (int co = 0; co < C; ++co) g[co * NLM] = v[co];
-        }
+          for (int co = 0; co < C; ++co) b.V[k][sidx(m, CL, co * NLM + j, r)] = v[co];
       }
     }
     __syncthreads();
@@ -454,6 +501,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
 
 // ============================================================================
 // Pass B2_k: latent MLP of layer k (x^k) and env of layer k+1 -> Gamma^{k+1}.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgEnv, {
     bulk_g2s(sm, w.lat0[k - 1], kImgLat0, &bars[1]);
@@ -481,41 +529,35 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    const float* xg = b.X[k - 1] + (size_t)(m.p0 + r) * D;
-    row_to_op(HA, r, xg + 64 * h, valid, 64 * h, 64);
+    const float* xg = b.X[k - 1];
+    row_to_op<Tin>(HA, m, r, xg, D, 64 * h, valid, 64 * h, 64);
     if (h == 1) {
-      row_to_op(HA, r, b.S[k] + (size_t)(m.p0 + r) * (C * NS), valid, 128, 48);
+      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 0, valid, 128, 48);
       float z[16] = {};
-      st16(HA, r, 176, z);
+      st16<Tin>(HA, r, 176, z);
     }
-    mm.run([&] { mma_k(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16(A1, rr, n0, o);
+      st16<Tin>(A1, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16];
       const float fc = s_fc[rr];
-      const float4* xo = reinterpret_cast<const float4*>(xg + n0);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 x = valid ? xo[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        o[4 * q] = (x.x + fc * silu_b(v[4 * q])) * kR2;
-        o[4 * q + 1] = (x.y + fc * silu_b(v[4 * q + 1])) * kR2;
-        o[4 * q + 2] = (x.z + fc * silu_b(v[4 * q + 2])) * kR2;
-        o[4 * q + 3] = (x.w + fc * silu_b(v[4 * q + 3])) * kR2;
+      for (int q = 0; q < 16; ++q) {
+        const float x = valid ? xg[sidx(m, D, n0 + q, rr)] : 0.0f;
+        o[q] = (x + fc * silu_b(v[q])) * kR2;
       }
-      st16(HA, rr, n0, o);
-      if (valid) {
-        float4* g = reinterpret_cast<float4*>(b.X[k] + (size_t)(m.p0 + rr) * D + n0);
+      st16<Tin>(HA, rr, n0, o);
+      if (valid)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) g[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      }
+        for (int q = 0; q < 16; ++q) b.X[k][sidx(m, D, n0 + q, rr)] = o[q];
     });
-    mm.run([&] { mma_k(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -532,6 +574,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 // ============================================================================
 // Pass C: last layer + energy MLP forward, dE/dE_ij = sigma_Z, and their
 // adjoint: dx^{L-1}, dV^{L-1}, dGamma^L partials, du, energy partials.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
   const int L = w.n_layers;
   BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgE0, {
@@ -550,6 +593,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
   float* s_sig = s_fc + kT;
   float* s_eij = s_sig + kT;
   float* s_du = s_eij + kT;                            // [2][kT]
+  float* s_g = s_du + 2 * kT;                          // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -565,50 +609,43 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
       }
     }
-    const int i = m.pi[r];
+    stage_g(b.gam[L], b.row_ptr, m, s_g);
+    __syncthreads();
     for (int cc = 0; cc < 8; ++cc) {
       const int c = 8 * h + cc;
       float V[NLM], G[NLM], S[NS];
-      const float* g = b.V[L - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? g[lm] : 0.0f;
-      if (valid) load_g(b.gam[L], b.row_ptr, i, c, G);
-      else
-#pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+      for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+      get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
       tp2_fwd_scalar(V, G, S);
 #pragma unroll
-      for (int q = 0; q < NS; ++q) st1(HA, r, D + c * NS + q, S[q]);
+      for (int q = 0; q < NS; ++q) st1<Tin>(HA, r, D + c * NS + q, S[q]);
     }
-    const float* xg = b.X[L - 1] + (size_t)(m.p0 + r) * D;
-    row_to_op(HA, r, xg + 64 * h, valid, 64 * h, 64);
+    const float* xg = b.X[L - 1];
+    row_to_op<Tin>(HA, m, r, xg, D, 64 * h, valid, 64 * h, 64);
     if (h == 1) {
       float z[16] = {};
-      st16(HA, r, 176, z);
+      st16<Tin>(HA, r, 176, z);
     }
-    mm.run([&] { mma_k(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16(A1, rr, n0, o);
+      st16<Tin>(A1, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16];
       const float fc = s_fc[rr];
-      const float4* xo = reinterpret_cast<const float4*>(xg + n0);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 x = valid ? xo[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        o[4 * q] = (x.x + fc * silu_b(v[4 * q])) * kR2;
-        o[4 * q + 1] = (x.y + fc * silu_b(v[4 * q + 1])) * kR2;
-        o[4 * q + 2] = (x.z + fc * silu_b(v[4 * q + 2])) * kR2;
-        o[4 * q + 3] = (x.w + fc * silu_b(v[4 * q + 3])) * kR2;
+      for (int q = 0; q < 16; ++q) {
+        const float x = valid ? xg[sidx(m, D, n0 + q, rr)] : 0.0f;
+        o[q] = (x + fc * silu_b(v[q])) * kR2;
       }
-      st16(HA, rr, n0, o);
+      st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 256, HA, 0, We0, 32, 8, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, We0, 32, 8, false, 0); });
     if (threadIdx.x < kT) {
       float ze[32];
       tmem_ld16(lanes(tmem) + 256, ze);
@@ -622,10 +659,10 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         dz[n] = sig * wo * dsilu_b(ze[n]);
       }
       s_eij[r] = valid ? e : 0.0f;
-      st16(AE, r, 0, dz);
-      st16(AE, r, 16, dz + 16);
+      st16<Tin>(AE, r, 0, dz);
+      st16<Tin>(AE, r, 16, dz + 16);
     }
-    mm.run([&] { mma_k(tmem + 288, AE, 0, We0, 128, 2, true, 32); });      // dx^L
+    mm.run([&] { mma_k<Tin>(tmem + 288, AE, 0, We0, 128, 2, true, 32); });      // dx^L
     {
       float du = 0.0f;
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dx) {
@@ -637,29 +674,25 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
           du = fmaf(dx[q], silu_b(z2[q]), du);
           o[q] = dx[q] * fc * kR2 * dsilu_b(z2[q]);
         }
-        st16(A1, rr, n0, o);
+        st16<Tin>(A1, rr, n0, o);
       });
       s_du[h * kT + r] = du * kR2;
     }
-    mm.run([&] { mma_k(tmem + 128, A1, 0, Wl1, 128, 8, true, 128); });    // da1
+    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, true, 128); });    // da1
     epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
       float z1[16], o[16];
       tmem_ld16(lanes(tmem) + n0, z1);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
-      st16(HA, rr, n0, o);
+      st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 0, HA, 0, Wl0, 176, 8, true, 128); });      // [dx^{L-1}, ds]
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 176, 8, true, 128); });      // [dx^{L-1}, ds]
     epi(tmem, 0, 128, [&](int rr, int n0, const float* dh) {
       float dx[16];
       tmem_ld16(lanes(tmem) + 288 + n0, dx);
-      if (valid) {
-        float4* g = reinterpret_cast<float4*>(b.dX + (size_t)(m.p0 + rr) * D + n0);
+      if (valid)
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          g[q] = make_float4(dh[4 * q] + dx[4 * q] * kR2, dh[4 * q + 1] + dx[4 * q + 1] * kR2,
-                             dh[4 * q + 2] + dx[4 * q + 2] * kR2, dh[4 * q + 3] + dx[4 * q + 3] * kR2);
-      }
+        for (int q = 0; q < 16; ++q) b.dX[sidx(m, D, n0 + q, rr)] = dh[q] + dx[q] * kR2;
     });
     {
       float ds[32];
@@ -668,25 +701,19 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
       for (int cc = 0; cc < 8; ++cc) {
         const int c = 8 * h + cc;
         float V[NLM], G[NLM], dV[NLM], dG[NLM];
-        const float* g = b.V[L - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
-          V[lm] = valid ? g[lm] : 0.0f;
+          V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
           dV[lm] = 0.0f;
           dG[lm] = 0.0f;
         }
-        if (valid) load_g(b.gam[L], b.row_ptr, i, c, G);
-        else
-#pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+        get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
         tp2_bwd_scalar(V, G, ds + cc * NS, dV, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CL + c * NLM + lm] = dG[lm];
-        if (valid) {
-          float* o = b.dV + (size_t)(m.p0 + r) * CL + c * NLM;
+        if (valid)
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) o[lm] = dV[lm];
-        }
+          for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(m, CL, c * NLM + lm, r)] = dV[lm];
       }
     }
     __syncthreads();
@@ -697,9 +724,9 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
       b.epart[m.tile + m.atom[s]] = acc;
     }
     if (threadIdx.x < kT && valid) {
-      b.dU[m.p0 + r] = s_du[r] + s_du[kT + r];
+      b.dU[sidx(m, 1, 0, r)] = s_du[r] + s_du[kT + r];
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) b.dY[(size_t)(m.p0 + r) * NLM + lm] = 0.0f;
+      for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(m, NLM, lm, r)] = 0.0f;
     }
     seg_store(b.dgam[L], m, CL, [&](int p, int x) { return s_dg[p * CL + x]; });
     __syncthreads();
@@ -711,6 +738,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
 // Pass B2_k^T: adjoint of the Gamma^{k+1} scatter and of the latent MLP of
 // layer k (its forward recomputed in the tile): dx^{k-1} (residual + latent
 // parts, without the embedding term), ds -> dS, du, dY.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1, {
     bulk_g2s(sm, w.env[k], kImgEnv, &bars[1]);
@@ -727,6 +755,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   float* s_Y = s_fc + kT;
   float* s_dy = s_Y + kT * NLM;
   float* s_du = s_dy + kT * NLM;   // [2][kT]
+  float* s_g = s_du + 2 * kT;      // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -740,8 +769,9 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    row_to_op(HA, r, b.X[k] + (size_t)(m.p0 + r) * D + 64 * h, valid, 64 * h, 64);
-    mm.run([&] { mma_k(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
+    row_to_op<Tin>(HA, m, r, b.X[k], D, 64 * h, valid, 64 * h, 64);
+    stage_g(b.dgam[k + 1], b.row_ptr, m, s_g);
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
     if (threadIdx.x < kT) {
       float e[16], de[16];
       tmem_ld16(lanes(tmem) + 0, e);
@@ -750,10 +780,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
       for (int c = 0; c < C; ++c) {
         float dG[NLM];
-        if (valid) load_g(b.dgam[k + 1], b.row_ptr, m.pi[r], c, dG);
-        else
-#pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) dG[lm] = 0.0f;
+        get_g(s_g, b.dgam[k + 1], b.row_ptr, m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -762,77 +789,74 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
         }
         de[c] = acc;
       }
-      st16(DE, r, 0, de);
+      st16<Tin>(DE, r, 0, de);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) s_dy[r * NLM + lm] = dy[lm];
     }
-    mm.run([&] { mma_k(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
-    const float* xg = b.X[k - 1] + (size_t)(m.p0 + r) * D;
-    row_to_op(HA, r, xg + 64 * h, valid, 64 * h, 64);
+    mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
+    row_to_op<Tin>(HA, m, r, b.X[k - 1], D, 64 * h, valid, 64 * h, 64);
     if (h == 1) {
-      row_to_op(HA, r, b.S[k] + (size_t)(m.p0 + r) * (C * NS), valid, 128, 48);
+      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 0, valid, 128, 48);
       float z[16] = {};
-      st16(HA, r, 176, z);
+      st16<Tin>(HA, r, 176, z);
     }
-    mm.run([&] { mma_k(tmem + 32, HA, 0, Wl0, 128, 11, false, 0); });     // z1
+    mm.run([&] { mma_k<Tin>(tmem + 32, HA, 0, Wl0, 128, 11, false, 0); });     // z1
     epi(tmem, 32, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16(A1, rr, n0, o);
+      st16<Tin>(A1, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 160, A1, 0, Wl1, 128, 8, false, 0); });     // z2
+    mm.run([&] { mma_k<Tin>(tmem + 160, A1, 0, Wl1, 128, 8, false, 0); });     // z2
     {
       float du = 0.0f;
-      float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      float* dxg = b.dX;
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
         float z2[16], o[16], dx[16];
         tmem_ld16(lanes(tmem) + 160 + n0, z2);
         const float fc = s_fc[rr];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) dx[q] = dxe[q] + (valid ? dxg[n0 + q] : 0.0f);
+        for (int q = 0; q < 16; ++q) dx[q] = dxe[q] + (valid ? dxg[sidx(m, D, n0 + q, rr)] : 0.0f);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           du = fmaf(dx[q], silu_b(z2[q]), du);
           o[q] = dx[q] * fc * kR2 * dsilu_b(z2[q]);
         }
-        st16(A1, rr, n0, o);
+        st16<Tin>(A1, rr, n0, o);
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[n0 + q] = dx[q] * kR2;
+          for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] = dx[q] * kR2;
       });
       s_du[h * kT + r] = du * kR2;
     }
-    mm.run([&] { mma_k(tmem + 160, A1, 0, Wl1, 128, 8, true, 128); });    // da1
+    mm.run([&] { mma_k<Tin>(tmem + 160, A1, 0, Wl1, 128, 8, true, 128); });    // da1
     epi(tmem, 160, 128, [&](int rr, int n0, const float* da) {
       float z1[16], o[16];
       tmem_ld16(lanes(tmem) + 32 + n0, z1);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
-      st16(HA, rr, n0, o);
+      st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 288, HA, 0, Wl0, 176, 8, true, 128); });    // [dx, ds]
+    mm.run([&] { mma_k<Tin>(tmem + 288, HA, 0, Wl0, 176, 8, true, 128); });    // [dx, ds]
     {
-      float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      float* dxg = b.dX;
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dh) {
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[n0 + q] += dh[q];
+          for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] += dh[q];
       });
       float ds[32];
       tmem_ld16(lanes(tmem) + 288 + 128 + 24 * h, ds);
       tmem_ld16(lanes(tmem) + 288 + 128 + 24 * h + 16, ds + 16);
-      if (valid) {
-        float* o = b.dS + (size_t)(m.p0 + r) * (C * NS) + 24 * h;
+      if (valid)
 #pragma unroll
-        for (int q = 0; q < 24; ++q) o[q] = ds[q];
-      }
+        for (int q = 0; q < 24; ++q) b.dS[sidx(m, C * NS, 24 * h + q, r)] = ds[q];
     }
     __syncthreads();
     if (threadIdx.x < kT && valid) {
-      b.dU[m.p0 + r] += s_du[r] + s_du[kT + r];
+      b.dU[sidx(m, 1, 0, r)] += s_du[r] + s_du[kT + r];
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) b.dY[(size_t)(m.p0 + r) * NLM + lm] += s_dy[r * NLM + lm];
+      for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(m, NLM, lm, r)] += s_dy[r * NLM + lm];
     }
     __syncthreads();
   }
@@ -843,6 +867,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 // Pass B1_k^T: adjoint of mixing and of the tensor product of layer k:
 // dV^{k-1} (k >= 2) or, for k = 1, the embedding adjoint into dx^0 and dY;
 // dGamma^k partials.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
     bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
@@ -856,6 +881,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   float* s_Y = reinterpret_cast<float*>(DW0 + kOp64);
   float* s_dg = s_Y + kT * NLM;           // [kT][CL]
   float* s_dy = s_dg + kT * CL;           // [2][kT][NLM]
+  float* s_g = s_dy + 2 * kT * NLM;       // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -868,15 +894,13 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    {
-      const float* g = b.dV + (size_t)(m.p0 + r) * CL;
-      for (int co = 8 * h; co < 8 * h + 8; ++co)
+    for (int co = 8 * h; co < 8 * h + 8; ++co)
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) st1(DVT, r, 16 * lm + co, valid ? g[co * NLM + lm] : 0.0f);
-    }
+      for (int lm = 0; lm < NLM; ++lm) st1<Tin>(DVT, r, 16 * lm + co, valid ? b.dV[sidx(m, CL, co * NLM + lm, r)] : 0.0f);
+    stage_g(b.gam[k], b.row_ptr, m, s_g);
     if (k == 1) {
-      row_to_op(X, r, b.X[0] + (size_t)(m.p0 + r) * D + 64 * h, valid, 64 * h, 64);
-      mm.run([&] { mma_k(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });       // w0
+      row_to_op<Tin>(X, m, r, b.X[0], D, 64 * h, valid, 64 * h, 64);
+      mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });       // w0
     }
     float w0[32];
     if (k == 1) {
@@ -884,7 +908,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       tmem_ld16(lanes(tmem) + 24 * h + 16, w0 + 16);
     }
     const int i = m.pi[r];
-    const float* dsg = b.dS + (size_t)(m.p0 + r) * (C * NS);
+    const float* dsg = b.dS;
     float dyl[NLM];
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
@@ -901,12 +925,12 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       for (int round = 0; round < 2; ++round) {
         if (round == 0) {
           mm.run([&] {
-            mma_k(tmem + 64, DVT, 0, Wmix, 48, 1, true, 16);
-            for (int j = 1; j < 4; ++j) mma_k(tmem + 112 + 64 * (j - 1), DVT, j, Wmix + kImgMix, 64, 1, true, 16);
+            mma_k<Tin>(tmem + 64, DVT, 0, Wmix, 48, 1, true, 16);
+            for (int j = 1; j < 4; ++j) mma_k<Tin>(tmem + 112 + 64 * (j - 1), DVT, j, Wmix + kImgMix, 64, 1, true, 16);
           });
         } else {
           mm.run([&] {
-            for (int j = 4; j < 9; ++j) mma_k(tmem + 64 + 64 * (j - 4), DVT, j, Wmix + 2 * kImgMix, 64, 1, true, 16);
+            for (int j = 4; j < 9; ++j) mma_k<Tin>(tmem + 64 + 64 * (j - 4), DVT, j, Wmix + 2 * kImgMix, 64, 1, true, 16);
           });
         }
         float tv[5][16];
@@ -924,7 +948,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
           for (int o = 0; o < TP2_NT; ++o) dT[o] = 0.0f;
           if (round == 0) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) dT[q] = tv[0][c4 * 3 + q] + (valid ? dsg[c * NS + q] : 0.0f);
+            for (int q = 0; q < 3; ++q) dT[q] = tv[0][c4 * 3 + q] + (valid ? dsg[sidx(m, C * NS, c * NS + q, r)] : 0.0f);
 #pragma unroll
             for (int mm1 = 0; mm1 < 3; ++mm1)
 #pragma unroll
@@ -940,14 +964,10 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
             for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[cc * 3 + l_of(lm)] * s_Y[r * NLM + lm];
           } else {
-            const float* gv = b.V[k - 1] + (size_t)(m.p0 + r) * CL + c * NLM;
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? gv[lm] : 0.0f;
+            for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
           }
-          if (valid) load_g(b.gam[k], b.row_ptr, i, c, G);
-          else
-#pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
+          get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) dG[lm] = round == 0 ? 0.0f : s_dg[r * CL + c * NLM + lm];
           tp2_bwd(V, G, dT, dVa[c4], dG);
@@ -956,13 +976,11 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
         }
       }
       if (k >= 2) {
-        if (valid) {
-          float* o = b.dV + (size_t)(m.p0 + r) * CL + cb * NLM;
+        if (valid)
 #pragma unroll
           for (int c4 = 0; c4 < 4; ++c4)
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) o[c4 * NLM + lm] = dVa[c4][lm];
-        }
+            for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(m, CL, (cb + c4) * NLM + lm, r)] = dVa[c4][lm];
       } else {
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) {
@@ -974,17 +992,17 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
             dyl[lm] = fmaf(w0[cc * 3 + l_of(lm)], dVa[c4][lm], dyl[lm]);
           }
 #pragma unroll
-          for (int l = 0; l < 3; ++l) st1(DW0, r, (cb + c4) * 3 + l, dw[l]);
+          for (int l = 0; l < 3; ++l) st1<Tin>(DW0, r, (cb + c4) * 3 + l, dw[l]);
         }
       }
     }
     if (k == 1) {
-      mm.run([&] { mma_k(tmem + 384, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
-      float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      mm.run([&] { mma_k<Tin>(tmem + 384, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
+      float* dxg = b.dX;
       epi(tmem, 384, 128, [&](int rr, int n0, const float* v) {
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[n0 + q] += v[q];
+          for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] += v[q];
       });
     }
 #pragma unroll
@@ -993,7 +1011,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     if (threadIdx.x < kT && valid && k == 1) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        b.dY[(size_t)(m.p0 + r) * NLM + lm] += s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm];
+        b.dY[sidx(m, NLM, lm, r)] += s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm];
     }
     seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CL + x]; });
     __syncthreads();
@@ -1004,6 +1022,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 // ============================================================================
 // Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP (recomputed)
 // and of the geometry; writes g_ij = dE/dDelta_ij.
+template <class Tin>
 __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
   BF_PROLOGUE(kImgTb0 + kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
@@ -1022,6 +1041,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
   float* s_Y = s_dB + kT * NB;
   float* s_dy = s_Y + kT * NLM;
   float* s_du = s_dy + kT * NLM;                          // [2][kT]
+  float* s_g = s_du + 2 * kT;                             // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -1048,24 +1068,25 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
       for (int q = 0; q < NB; ++q) s_dB[r * NB + q] = dB[q];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-      st16(H0, r, 0, h0);
+      st16<Tin>(H0, r, 0, h0);
     }
-    mm.run([&] { mma_k(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });       // z1
+    stage_g(b.dgam[1], b.row_ptr, m, s_g);
+    mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });       // z1
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16(A1, rr, n0, o);
+      st16<Tin>(A1, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });    // z2
+    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });    // z2
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16];
       const float fc = s_geo[rr * 8 + 4];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
-      st16(X, rr, n0, o);
+      st16<Tin>(X, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });      // e^1
+    mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });      // e^1
     if (threadIdx.x < kT) {
       float e[16], de[16], dy[NLM];
       tmem_ld16(lanes(tmem) + 256, e);
@@ -1073,10 +1094,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
       for (int c = 0; c < C; ++c) {
         float dG[NLM];
-        if (valid) load_g(b.dgam[1], b.row_ptr, m.pi[r], c, dG);
-        else
-#pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) dG[lm] = 0.0f;
+        get_g(s_g, b.dgam[1], b.row_ptr, m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -1085,37 +1103,37 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
         }
         de[c] = acc;
       }
-      st16(DE, r, 0, de);
+      st16<Tin>(DE, r, 0, de);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) s_dy[r * NLM + lm] = dy[lm];
     }
-    mm.run([&] { mma_k(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });    // env1^T de
+    mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });    // env1^T de
     {
       float du = 0.0f;
-      const float* dxg = b.dX + (size_t)(m.p0 + r) * D;
+      const float* dxg = b.dX;
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
         float z2[16], o[16];
         tmem_ld16(lanes(tmem) + 128 + n0, z2);
         const float fc = s_geo[rr * 8 + 4];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const float dx = dxe[q] + (valid ? dxg[n0 + q] : 0.0f);
+          const float dx = dxe[q] + (valid ? dxg[sidx(m, D, n0 + q, rr)] : 0.0f);
           du = fmaf(dx, silu_b(z2[q]), du);
           o[q] = dx * fc * dsilu_b(z2[q]);
         }
-        st16(A1, rr, n0, o);
+        st16<Tin>(A1, rr, n0, o);
       });
       s_du[h * kT + r] = du;
     }
-    mm.run([&] { mma_k(tmem + 128, A1, 0, Wtb1, 128, 8, true, 128); });   // da1
+    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wtb1, 128, 8, true, 128); });   // da1
     epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
       float z1[16], o[16];
       tmem_ld16(lanes(tmem) + n0, z1);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
-      st16(X, rr, n0, o);
+      st16<Tin>(X, rr, n0, o);
     });
-    mm.run([&] { mma_k(tmem + 416, X, 0, Wtb0, 16, 8, true, 128); });     // dh0
+    mm.run([&] { mma_k<Tin>(tmem + 416, X, 0, Wtb0, 16, 8, true, 128); });     // dh0
     if (threadIdx.x < kT) {
       float dh[16];
       tmem_ld16(lanes(tmem) + 416, dh);
@@ -1124,12 +1142,12 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
         const float u[3] = {g[0], g[1], g[2]};
         const float d = g[3], dfc = g[5];
         const size_t pp = (size_t)(m.p0 + r);
-        float gd = (s_du[r] + s_du[kT + r] + b.dU[pp]) * dfc;
+        float gd = (s_du[r] + s_du[kT + r] + b.dU[sidx(m, 1, 0, r)]) * dfc;
 #pragma unroll
         for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * NB + n], gd);
         float dY[NLM];
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[pp * NLM + lm];
+        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[sidx(m, NLM, lm, r)];
         float gu[3];
         sph_harm_vjp<2>(u[0], u[1], u[2], dY, gu);
         const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
@@ -1145,36 +1163,32 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
 
 // shared-memory bytes of each kernel (+1024 for the manual 1024-byte alignment)
 constexpr size_t kSmA = 1024 + kImgTb0 + kImgTb1 + kImgEnv + kOp64 + 2 * kOp128 + 4 * (kT + kT * NLM + kT * 16);
-constexpr size_t kSmB1 = 1024 + kImgEmb + 3 * kImgMix + kOp128 + kOpT + 4 * (kT * NLM);
+constexpr size_t kSmB1 = 1024 + kImgEmb + 3 * kImgMix + kOp128 + kOpT + 4 * (kT * NLM + kSegCap * CL);
 constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * 16);
-constexpr size_t kSmC = 1024 + kImgLat0 + kImgLat1 + kImgE0 + kOpH + kOp128 + kOp64 + 4 * (5 * kT);
-constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 + 4 * (kT + 2 * kT * NLM + 2 * kT);
-constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 + 4 * (kT * NLM + kT * CL + 2 * kT * NLM);
+constexpr size_t kSmC = 1024 + kImgLat0 + kImgLat1 + kImgE0 + kOpH + kOp128 + kOp64 + 4 * (5 * kT + kSegCap * CL);
+constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 +
+                          4 * (kT + 2 * kT * NLM + 2 * kT + kSegCap * CL);
+constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 +
+                          4 * (kT * NLM + kT * CL + 2 * kT * NLM + kSegCap * CL);
 constexpr size_t kSmAT = 1024 + kImgTb0 + kImgTb1 + kImgEnv + kOp64 + 2 * kOp128 + kOp64 +
-                         4 * (kT * 8 + kT * NB + 2 * kT * NLM + 2 * kT);
-static_assert(kSmB1 <= 232448 && kSmC <= 232448 && kSmB2T <= 232448 && kSmB1T <= 232448, "smem");
+                         4 * (kT * 8 + kT * NB + 2 * kT * NLM + 2 * kT + kSegCap * CL);
+static_assert(kSmB1 + 4096 <= 232448 && kSmC + 4096 <= 232448 && kSmB2T + 4096 <= 232448 &&
+                  kSmB1T + 4096 <= 232448 && kSmAT + 4096 <= 232448, "smem (incl. static Meta)");
 static_assert(kOpH + kOp128 >= 4 * kT * CL, "pass C reuses HA + A1 for the dGamma contributions");
 
 int g_sms = 0;
 
-}  // namespace
-
-bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
-  return lmax == 2 && C_ == C && D_ == D && E_ == E && L >= 2 && L <= kMaxLayers;
-}
-
-int bf16_tile() { return kT; }
-
-void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
+template <class Tin>
+void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_bf_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
-    cudaFuncSetAttribute(k_bf_b1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1);
-    cudaFuncSetAttribute(k_bf_b2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
-    cudaFuncSetAttribute(k_bf_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
-    cudaFuncSetAttribute(k_bf_b2t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2T);
-    cudaFuncSetAttribute(k_bf_b1t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
-    cudaFuncSetAttribute(k_bf_at, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
+    cudaFuncSetAttribute(k_bf_a<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
+    cudaFuncSetAttribute(k_bf_b1<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1);
+    cudaFuncSetAttribute(k_bf_b2<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
+    cudaFuncSetAttribute(k_bf_c<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
+    cudaFuncSetAttribute(k_bf_b2t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2T);
+    cudaFuncSetAttribute(k_bf_b1t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
+    cudaFuncSetAttribute(k_bf_at<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1187,22 +1201,36 @@ void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaS
     if (ev) cudaEventRecord(ev[k], s);
   };
   mark(0);
-  k_bf_a<<<grid, kThr, kSmA, s>>>(w, b);
+  k_bf_a<Tin><<<grid, kThr, kSmA, s>>>(w, b);
   mark(1);
   for (int k = 1; k < L; ++k) {
-    k_bf_b1<<<grid, kThr, kSmB1, s>>>(w, b, k);
-    k_bf_b2<<<grid, kThr, kSmB2, s>>>(w, b, k);
+    k_bf_b1<Tin><<<grid, kThr, kSmB1, s>>>(w, b, k);
+    k_bf_b2<Tin><<<grid, kThr, kSmB2, s>>>(w, b, k);
   }
   mark(2);
-  k_bf_c<<<grid, kThr, kSmC, s>>>(w, b);
+  k_bf_c<Tin><<<grid, kThr, kSmC, s>>>(w, b);
   mark(3);
   for (int k = L - 1; k >= 1; --k) {
-    k_bf_b2t<<<grid, kThr, kSmB2T, s>>>(w, b, k);
-    k_bf_b1t<<<grid, kThr, kSmB1T, s>>>(w, b, k);
+    k_bf_b2t<Tin><<<grid, kThr, kSmB2T, s>>>(w, b, k);
+    k_bf_b1t<Tin><<<grid, kThr, kSmB1T, s>>>(w, b, k);
   }
   mark(4);
-  k_bf_at<<<grid, kThr, kSmAT, s>>>(w, b);
+  k_bf_at<Tin><<<grid, kThr, kSmAT, s>>>(w, b);
   mark(5);
+}
+
+}  // namespace
+
+bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
+  return lmax == 2 && C_ == C && D_ == D && E_ == E && L >= 2 && L <= kMaxLayers;
+}
+
+int bf16_tile() { return kT; }
+
+void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev,
+                        bool fp16) {
+  if (fp16) run_tc<__half>(w, b, capacity, s, ev);
+  else run_tc<__nv_bfloat16>(w, b, capacity, s, ev);
 }
 
 }  // namespace al

@@ -13,6 +13,7 @@
 // inside a block and by R * 128 bytes across blocks.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -67,6 +68,13 @@ UM_DEV uint64_t desc_sw128_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9
 // = 1), B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+// Same with the operand type selectable: fmt 1 = BF16, 0 = FP16 (both
+// operands alike, as kind::f16 requires).
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, bool b_mn_major, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (b_mn_major ? (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major = false) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (b_mn_major ? (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
