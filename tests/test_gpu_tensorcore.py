@@ -1,0 +1,97 @@
+"""Tensor-core pair passes (tcgen05, BF16 or FP16 operands, FP32 accumulation)
+for the 2-layer l_max 2 model.
+
+Two references:
+  * the oracle in operand-emulation mode (every per-pair GEMM input and
+    pre-scaled weight rounded to the same 16-bit type, FP64 accumulation):
+    the tensor-core energies must match it to FP32-accumulation level, which
+    pins the kernels themselves;
+  * the exact FP64 oracle: the force error that the operand precision
+    implies for this seeded model, stated and bounded.
+Measured on GB300 (6,912 atoms): BF16 max |dF| 4.0e-2, rms 1.1e-2 eV/A;
+FP16 max 3.0e-3, rms 7.3e-4 eV/A (RMS force 1 eV/A); energy vs the emulating
+oracle 1.7e-5 (BF16) and 4e-7 (FP16) relative.  Bounds below carry margin."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_2303_08169_gb300 as al
+from oracle.model import OracleModel
+from tests.conftest import energy_scale
+
+pytestmark = pytest.mark.gpu
+MASS = np.array([14.007, 1.008])
+MODES = {"bf16": (al.ALLEGRO_BF16, dict(erel=5e-5, ei=1e-2, fmax=6e-2, frms=1.5e-2)),
+         "fp16": (al.ALLEGRO_FP16, dict(erel=5e-6, ei=2e-3, fmax=5e-3, frms=1.2e-3))}
+
+
+@pytest.fixture(scope="module")
+def main():
+    cfg = synth.MAIN
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    yield ctx, blob
+    al.allegro_destroy(ctx)
+
+
+def _gpu(ctx, pos, sp, cell, prec):
+    N = len(pos)
+    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    Ei = torch.empty(N, dtype=torch.float64, device="cuda")
+    E = al.allegro_energy_forces(ctx, torch.tensor(pos, device="cuda"), torch.tensor(sp, device="cuda"), cell,
+                                 F, Ei, prec)
+    return E, F.cpu().numpy().astype(np.float64), Ei.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+@pytest.mark.parametrize("n_mol", [108, 1728])
+def test_tensorcore_vs_emulating_and_exact_oracle(main, mode, n_mol):
+    ctx, blob = main
+    prec, tol = MODES[mode]
+    pos, sp, cell = synth.make_ammonia(n_mol, 0)
+    L = np.diag(cell)
+    E, F, Ei = _gpu(ctx, pos, sp, cell, prec)
+    Er, Fr, Eir, pairs = OracleModel(blob).energy_forces(pos, sp, L)
+    Ee, Fe, Eie, _ = OracleModel(blob, emulate=mode).energy_forces(pos, sp, L, pairs=pairs)
+    assert abs(E - Ee) <= tol["erel"] * abs(Ee)
+    assert np.abs(Ei - Eie).max() <= tol["ei"]
+    d = F - Fr
+    assert np.abs(d).max() <= tol["fmax"]
+    assert np.sqrt(np.mean(d * d)) <= tol["frms"]
+    E2, F2, _ = _gpu(ctx, pos, sp, cell, prec)
+    assert E2 == E and np.array_equal(F2, F)          # bitwise rerun
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+def test_tensorcore_sampled_atoms_110592(main, mode):
+    ctx, blob = main
+    prec, tol = MODES[mode]
+    pos, sp, cell = synth.make_ammonia(27648, 0)
+    E, F, Ei = _gpu(ctx, pos, sp, cell, prec)
+    orc = OracleModel(blob)
+    rng = np.random.default_rng(5)
+    for k in rng.choice(len(pos), 8, replace=False):
+        ek, fk = orc.local_energy_force(pos, sp, np.diag(cell), int(k))
+        assert np.abs(F[k] - fk).max() <= tol["fmax"]
+    assert np.abs(F.sum(0)).max() <= 1e-2 * np.sqrt(len(pos))
+
+
+def test_tensorcore_md_and_unsupported_model(main):
+    ctx, blob = main
+    pos, sp, cell = synth.make_ammonia(1728, 0)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    al.allegro_set_md_precision(ctx, al.ALLEGRO_BF16)
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    e = np.zeros((40, 3))
+    al.allegro_md_step_nve(ctx, 0.25, 40, None, e)
+    kT = 8.617333e-5 * 200.0
+    assert np.abs(e[:, 2] - e[0, 2]).max() / (len(sp) * kT) < 0.05
+    al.allegro_set_md_precision(ctx, al.ALLEGRO_FP32)
+    tiny = synth.TINY
+    tctx = al.allegro_create(synth.make_blob(tiny, 42), MASS, tiny.r_cut, tiny.l_max, tiny.n_layers)
+    p, s, c = synth.make_ammonia(16, 0)
+    with pytest.raises(al.AllegroError) as err:
+        al.allegro_energy_forces(tctx, p, s.astype(np.int32), c, None, None, al.ALLEGRO_BF16)
+    assert err.value.code == 10
+    al.allegro_destroy(tctx)
