@@ -184,6 +184,32 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps,
 int allegro_md_get_state(allegro_ctx* ctx, double* positions,
                          double* velocities, float* forces, int64_t* step);
 
+/*
+ * The outlier count of allegro_outlier_count without allocating device
+ * memory, for callers that cannot allocate: code running while a CUDA graph
+ * is being captured (cudaMalloc is not allowed there), applications whose own
+ * allocator holds all device memory, and latency-bound loops where
+ * cudaMalloc/cudaFree would synchronise the device.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *  n_atoms   : 1 .. 4,194,304 (the fixed scratch size), else
+ *              ALLEGRO_E_INVALID_ARG with a message in allegro_last_error(NULL).
+ *  forces    : device, N x 3 FP32.
+ *  threshold : count components with |F| > threshold * sigma (5 for >5 sigma).
+ *  count_out : device, one int64, written asynchronously on the stream.
+ *  cuda_stream : cudaStream_t (NULL = legacy default stream); the call only
+ *              enqueues kernels, synchronise before reading count_out.
+ * The reduction scratch is a fixed 256 KB array in device global memory that
+ * every GPU loading the library keeps until the process exits.  All calls
+ * share it and it keeps the last call's contents; every kernel overwrites the
+ * slots it later reads, so nothing needs clearing, but calls that overlap on
+ * the GPU (different streams, or different host threads on one device) race
+ * on it and must be serialised by the caller.  The first call on each device
+ * looks the array's device address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.
+ */
+int allegro_outlier_count_noalloc(int64_t n_atoms, const float* forces, double threshold,
+                                  int64_t* count_out, void* cuda_stream);
+
 /* Keys of allegro_query. */
 #define ALLEGRO_Q_N_PAIRS      0  /* ordered pairs of the last neighbour build   */
 #define ALLEGRO_Q_CAPACITY     1  /* pair capacity currently allocated           */

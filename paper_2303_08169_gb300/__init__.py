@@ -29,7 +29,7 @@ EXPORTED = [
     "allegro_energy_forces", "allegro_outlier_count", "allegro_md_init",
     "allegro_set_md_precision", "allegro_md_step_nve", "allegro_md_get_state",
     "allegro_query", "allegro_phase_times", "allegro_selftest_mma",
-    "allegro_selftest_mma_mode",
+    "allegro_selftest_mma_mode", "allegro_outlier_count_noalloc",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -76,6 +76,7 @@ def lib():
         "allegro_phase_times": ([_vp, _i32, _vp, _i32], ctypes.c_int),
         "allegro_selftest_mma": ([_i32, _i32, _vp, _vp, _vp], ctypes.c_int),
         "allegro_selftest_mma_mode": ([_i32, _i32, _vp, _vp, _vp, _i32], ctypes.c_int),
+        "allegro_outlier_count_noalloc": ([_i64, _vp, _f64, _vp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -168,6 +169,14 @@ def allegro_md_init(ctx, positions, velocities, species, cell):
     cell = _host(cell, np.float64)
     _check(ctx, lib().allegro_md_init(ctx, int(positions.shape[0]), _ptr(positions), _ptr(velocities),
                                       _ptr(species), _ptr(cell)))
+
+
+def allegro_outlier_count_noalloc(forces, threshold, count_out, stream=None):
+    """Outlier count into the device int64 count_out, with no device
+    allocation (see include/allegro.h); enqueued on stream, not synchronised."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(None, lib().allegro_outlier_count_noalloc(int(forces.shape[0]), _ptr(forces), float(threshold),
+                                                     _ptr(count_out), handle))
 
 
 def allegro_set_md_precision(ctx, precision):

@@ -13,12 +13,20 @@
 #include "model.h"
 #include "umma.cuh"
 
+namespace {
+thread_local std::string g_err;
+}
+
+namespace al {
+// message returned by allegro_last_error(NULL) (entry points without a context)
+void set_global_error(const std::string& msg) { g_err = msg; }
+}  // namespace al
+
 using namespace al;
 
 namespace {
 
 const char* kVersion = "allegro-gb300 0.1";
-thread_local std::string g_err;
 
 struct Tensor {
   std::string name;
