@@ -210,11 +210,59 @@ int allegro_md_get_state(allegro_ctx* ctx, double* positions,
 int allegro_outlier_count_noalloc(int64_t n_atoms, const float* forces, double threshold,
                                   int64_t* count_out, void* cuda_stream);
 
+/*
+ * A batch of structures for training (SAM, Eq. 3).  All arrays host.
+ *  atom_offset : n_structs + 1, structure k owns atoms [off[k], off[k+1]).
+ *  positions   : N_tot x 3 FP64;  species: N_tot int32;
+ *  cells       : n_structs x 9 FP64 (orthorhombic, row-major 3 x 3);
+ *  e_target    : n_structs FP64 target energies;  f_target: N_tot x 3 FP32.
+ */
+typedef struct allegro_batch {
+  int32_t n_structs;
+  const int64_t* atom_offset;
+  const double* positions;
+  const int32_t* species;
+  const double* cells;
+  const double* e_target;
+  const float* f_target;
+} allegro_batch;
+
+/*
+ * Loss and its weight gradient (FP32 passes).  Loss (per-atom MSE, Table 5,
+ * weights as arguments):
+ *   L = (w_energy / B) sum_b ((E_b - E*_b) / N_b)^2
+ *       + (w_force / (3 sum_b N_b)) sum |F - F*|^2.
+ * The gradient is the hand-written weight adjoint of the pair passes; the
+ * force term's mixed derivative -d/dw (v . dE/dr), v = dL/dF, is a central
+ * difference of that adjoint along v (displacement at most 0.01 A).
+ *  loss_out : host (may be NULL);  grad_out: host or device, n_params FP32 in
+ *  blob order (may be NULL; see ALLEGRO_Q_N_PARAMS).
+ * Models of at most two layers (E_UNSUPPORTED otherwise).
+ */
+int allegro_loss_grad(allegro_ctx* ctx, const allegro_batch* batch, double w_energy, double w_force,
+                      double* loss_out, float* grad_out);
+
+/*
+ * One sharpness-aware minimisation step (Eq. 3) with Adam as the base
+ * optimizer (Table 5: beta = (0.9, 0.999), eps = 1e-8):
+ *   g = grad L(w);  w' = w + rho g / ||g|| (w' = w if g = 0);
+ *   g' = grad L(w');  w <- Adam(w, g') with step size lr.
+ * Updates the context's weights and Adam state.  loss_out: host, L(w).
+ */
+int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double rho, double lr,
+                           double w_energy, double w_force, double* loss_out);
+
+/* The trainable weights as one FP32 vector in blob order (every weight
+ * matrix row-major, sigma/mu excluded); host or device, n = n_params. */
+int allegro_get_weights(allegro_ctx* ctx, float* out, int64_t n);
+int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n);
+
 /* Keys of allegro_query. */
 #define ALLEGRO_Q_N_PAIRS      0  /* ordered pairs of the last neighbour build   */
 #define ALLEGRO_Q_CAPACITY     1  /* pair capacity currently allocated           */
 #define ALLEGRO_Q_STEP_KERNELS 2  /* kernel launches in one captured MD step     */
 #define ALLEGRO_Q_N_ATOMS      3  /* atoms of the current state                  */
+#define ALLEGRO_Q_N_PARAMS     4  /* trainable parameters (weights vector length) */
 
 /* Read one integer property of the context into *value (host). */
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);

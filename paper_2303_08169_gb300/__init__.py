@@ -30,12 +30,21 @@ EXPORTED = [
     "allegro_set_md_precision", "allegro_md_step_nve", "allegro_md_get_state",
     "allegro_query", "allegro_phase_times", "allegro_selftest_mma",
     "allegro_selftest_mma_mode", "allegro_outlier_count_noalloc",
+    "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
 ALLEGRO_Q_CAPACITY = 1
 ALLEGRO_Q_STEP_KERNELS = 2
 ALLEGRO_Q_N_ATOMS = 3
+ALLEGRO_Q_N_PARAMS = 4
+
+
+class _Batch(ctypes.Structure):
+    _fields_ = [("n_structs", ctypes.c_int32), ("atom_offset", ctypes.c_void_p),
+                ("positions", ctypes.c_void_p), ("species", ctypes.c_void_p),
+                ("cells", ctypes.c_void_p), ("e_target", ctypes.c_void_p),
+                ("f_target", ctypes.c_void_p)]
 PHASES = ["neighbors", "pass_a", "pass_b", "pass_c", "pass_b_adjoint", "pass_a_adjoint", "forces"]
 
 
@@ -77,6 +86,10 @@ def lib():
         "allegro_selftest_mma": ([_i32, _i32, _vp, _vp, _vp], ctypes.c_int),
         "allegro_selftest_mma_mode": ([_i32, _i32, _vp, _vp, _vp, _i32], ctypes.c_int),
         "allegro_outlier_count_noalloc": ([_i64, _vp, _f64, _vp, _vp], ctypes.c_int),
+        "allegro_loss_grad": ([_vp, _vp, _f64, _f64, ctypes.POINTER(_f64), _vp], ctypes.c_int),
+        "allegro_sam_train_step": ([_vp, _vp, _f64, _f64, _f64, _f64, ctypes.POINTER(_f64)], ctypes.c_int),
+        "allegro_get_weights": ([_vp, _vp, _i64], ctypes.c_int),
+        "allegro_set_weights": ([_vp, _vp, _i64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -177,6 +190,45 @@ def allegro_outlier_count_noalloc(forces, threshold, count_out, stream=None):
     handle = getattr(stream, "cuda_stream", stream)
     _check(None, lib().allegro_outlier_count_noalloc(int(forces.shape[0]), _ptr(forces), float(threshold),
                                                      _ptr(count_out), handle))
+
+
+def make_batch(structs):
+    """Host arrays of an allegro_batch from a list of dicts with keys pos,
+    species, cell (3x3), e_target, f_target.  Returns (batch, keepalive)."""
+    off = np.zeros(len(structs) + 1, dtype=np.int64)
+    for k, s in enumerate(structs):
+        off[k + 1] = off[k] + len(s["species"])
+    pos = np.ascontiguousarray(np.concatenate([s["pos"] for s in structs]), dtype=np.float64)
+    sp = np.ascontiguousarray(np.concatenate([s["species"] for s in structs]), dtype=np.int32)
+    cells = np.ascontiguousarray(np.stack([np.asarray(s["cell"], dtype=np.float64).reshape(9) for s in structs]))
+    et = np.ascontiguousarray([float(s["e_target"]) for s in structs], dtype=np.float64)
+    ft = np.ascontiguousarray(np.concatenate([s["f_target"] for s in structs]), dtype=np.float32)
+    keep = (off, pos, sp, cells, et, ft)
+    b = _Batch(len(structs), off.ctypes.data, pos.ctypes.data, sp.ctypes.data, cells.ctypes.data,
+               et.ctypes.data, ft.ctypes.data)
+    return b, keep
+
+
+def allegro_loss_grad(ctx, batch, w_energy=1.0, w_force=100.0, grad_out=None):
+    loss = _f64()
+    _check(ctx, lib().allegro_loss_grad(ctx, ctypes.byref(batch), float(w_energy), float(w_force),
+                                        ctypes.byref(loss), _ptr(grad_out)))
+    return loss.value
+
+
+def allegro_sam_train_step(ctx, batch, rho, lr, w_energy=1.0, w_force=100.0):
+    loss = _f64()
+    _check(ctx, lib().allegro_sam_train_step(ctx, ctypes.byref(batch), float(rho), float(lr), float(w_energy),
+                                             float(w_force), ctypes.byref(loss)))
+    return loss.value
+
+
+def allegro_get_weights(ctx, out):
+    _check(ctx, lib().allegro_get_weights(ctx, _ptr(out), int(out.shape[0])))
+
+
+def allegro_set_weights(ctx, w):
+    _check(ctx, lib().allegro_set_weights(ctx, _ptr(w), int(w.shape[0])))
 
 
 def allegro_set_md_precision(ctx, precision):

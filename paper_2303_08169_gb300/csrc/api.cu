@@ -11,6 +11,8 @@
 #include "kernels.h"
 #include "md.h"
 #include "model.h"
+#include "tp_tables.inc"
+#include "train.h"
 #include "umma.cuh"
 
 namespace {
@@ -113,8 +115,32 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+// One trainable tensor: its slice of the flat parameter vector (blob order)
+// and its pre-scaled FP32 copies ([in][out] and [out][in]) in the weights
+// buffer.
+struct WInfo {
+  std::string name;
+  int rows, cols;
+  size_t flat_off;
+  float scale;
+  size_t t_off, n_off;   // offsets in floats inside d_w (t unused for some)
+  bool has_t;
+};
+
 struct allegro_ctx {
   std::string err;
+  std::vector<WInfo> winfo;
+  int64_t n_params = 0;
+  float* d_master = nullptr;   // flat parameter vector (FP32, blob order)
+  float* d_grad = nullptr;
+  float* d_adam_m = nullptr;
+  float* d_adam_v = nullptr;
+  float* d_wtmp = nullptr;
+  double* d_norm2 = nullptr;
+  int adam_t = 0;
+  bool tc_dirty = false;       // tensor-core images lag behind d_master
+  TrainBufs tr{};
+  int64_t tr_cap = 0;
   cudaStream_t stream = nullptr;
   Blob blob;
   double mass[2] = {14.007, 1.008};
@@ -203,6 +229,8 @@ int cuda_check(allegro_ctx* c, const char* where) {
 int upload_weights(allegro_ctx* c) {
   const Blob& B = c->blob;
   std::vector<float> host;
+  size_t flat = 0;
+  c->winfo.clear();
   auto push = [&](const Tensor* T, double extra, Lin* lin, const float** raw_n) -> bool {
     if (!T) return false;
     const double s = extra / std::sqrt((double)T->cols);
@@ -219,6 +247,8 @@ int upload_weights(allegro_ctx* c) {
       lin->n = reinterpret_cast<const float*>(n_off);
     }
     if (raw_n) *raw_n = reinterpret_cast<const float*>(n_off);
+    c->winfo.push_back(WInfo{T->name, (int)T->rows, (int)T->cols, flat, (float)s, t_off, n_off, true});
+    flat += (size_t)T->rows * T->cols;
     return true;
   };
   ModelW& w = c->w;
@@ -251,6 +281,7 @@ int upload_weights(allegro_ctx* c) {
       for (uint32_t l = 0; l <= B.lmax; ++l) fix(LW.mix[l]);
   }
   w.eout = c->d_w + reinterpret_cast<size_t>(eout);
+  c->n_params = (int64_t)flat;
   for (int s = 0; s < 2; ++s) {
     w.sigma[s] = (float)B.sigma[s];
     w.mu[s] = (float)B.mu[s];
@@ -578,11 +609,17 @@ void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, cudaEvent_t
                 c->d_stats, c->nb.flags, s);
 }
 
+int refresh_tc(allegro_ctx* c);
+
 int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
   if (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16 && precision != ALLEGRO_FP16)
     return c->fail(ALLEGRO_E_INVALID_ARG, "precision must be ALLEGRO_FP32, ALLEGRO_BF16 or ALLEGRO_FP16");
   if (precision != ALLEGRO_FP32 && !c->bf16_ok)
     return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
+  if (precision != ALLEGRO_FP32) {
+    const int rc = refresh_tc(c);
+    if (rc) return rc;
+  }
   fill_passbufs(c, L);
   launch_model(c, precision, c->stream, nullptr);
   return cuda_check(c, "model launch");
@@ -592,6 +629,209 @@ int copy_out(allegro_ctx* c, void* dst, const void* src, size_t bytes) {
   if (!dst) return ALLEGRO_OK;
   const cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (cudaMemcpyAsync(dst, src, bytes, k, c->stream) != cudaSuccess) return cuda_check(c, "copy out");
+  return ALLEGRO_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Training (SAM, Eq. 3): master weights, weight gradients, Adam.
+
+int init_master(allegro_ctx* c) {
+  if (c->d_master) return ALLEGRO_OK;
+  const size_t n = (size_t)c->n_params;
+  std::vector<float> h(n);
+  size_t off = 0;
+  for (const auto& wi : c->winfo) {
+    const Tensor* T = c->blob.find(wi.name);
+    for (size_t q = 0; q < (size_t)wi.rows * wi.cols; ++q) h[off + q] = (float)T->data[q];
+    off += (size_t)wi.rows * wi.cols;
+  }
+  c->d_master = c->dalloc<float>(n);
+  c->d_grad = c->dalloc<float>(n);
+  c->d_adam_m = c->dalloc<float>(n);
+  c->d_adam_v = c->dalloc<float>(n);
+  c->d_wtmp = c->dalloc<float>(n);
+  c->d_norm2 = c->dalloc<double>(1);
+  if (!c->d_master || !c->d_grad || !c->d_adam_m || !c->d_adam_v || !c->d_wtmp || !c->d_norm2)
+    return c->fail(ALLEGRO_E_OOM, "training buffers allocation failed");
+  cudaMemcpy(c->d_master, h.data(), n * 4, cudaMemcpyHostToDevice);
+  cudaMemset(c->d_adam_m, 0, n * 4);
+  cudaMemset(c->d_adam_v, 0, n * 4);
+  c->adam_t = 0;
+  return cuda_check(c, "init master weights");
+}
+
+// FP32 pass weights <- flat vector (pre-scaled copies of every tensor)
+void apply_flat(allegro_ctx* c, const float* flat) {
+  for (const auto& wi : c->winfo)
+    launch_apply(flat + wi.flat_off, wi.rows, wi.cols, wi.scale, c->d_w + wi.t_off, c->d_w + wi.n_off, c->stream);
+  c->tc_dirty = true;
+}
+
+// Tensor-core images <- d_master (through the blob's FP64 tensor storage).
+int refresh_tc(allegro_ctx* c) {
+  if (!c->tc_dirty || !c->bf16_ok || !c->d_master) return ALLEGRO_OK;
+  std::vector<float> h((size_t)c->n_params);
+  if (cudaMemcpy(h.data(), c->d_master, h.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_check(c, "download weights");
+  for (const auto& wi : c->winfo) {
+    double* dst = const_cast<double*>(c->blob.find(wi.name)->data);
+    for (size_t q = 0; q < (size_t)wi.rows * wi.cols; ++q) dst[q] = h[wi.flat_off + q];
+  }
+  c->dfree(c->d_bw);
+  c->dfree(c->d_hw);
+  int rc = upload_weights_bf16(c, false);
+  if (!rc) rc = upload_weights_bf16(c, true);
+  if (!rc) c->tc_dirty = false;
+  return rc;
+}
+
+const WInfo* winfo(allegro_ctx* c, const std::string& name) {
+  for (const auto& wi : c->winfo)
+    if (wi.name == name) return &wi;
+  return nullptr;
+}
+
+int ensure_train(allegro_ctx* c) {
+  const int64_t cap = c->capacity;
+  if (cap <= c->tr_cap) return ALLEGRO_OK;
+  const Blob& B = c->blob;
+  const int D = c->D, C = (int)B.C, E = c->E, L = (int)B.L;
+  const int NS = B.lmax == 1 ? TP1_NS : TP2_NS, NT = B.lmax == 1 ? TP1_NT : TP2_NT;
+  const int NW0 = C * ((int)B.lmax + 1);
+  TrainBufs& t = c->tr;
+  auto re = [&](float*& p, size_t w) {
+    c->dfree(p);
+    p = c->dalloc<float>((size_t)cap * w);
+    return p != nullptr;
+  };
+  bool ok = re(t.h0, 16) && re(t.a1_tb, D) && re(t.dz1_tb, D) && re(t.dz2_tb, D) && re(t.dw0, NW0) &&
+            re(t.xL, D) && re(t.ae, E) && re(t.dze, E) && re(t.dEij, 1);
+  for (int j = 0; j < L && ok; ++j) ok = re(t.de[j], C);
+  for (int k = 1; k <= L && ok; ++k)
+    ok = re(t.s[k], C * NS) && re(t.a1_l[k], D) && re(t.dz1_l[k], D) && re(t.dz2_l[k], D) &&
+         (k == L || re(t.T[k], C * NT));
+  if (!ok) return c->fail(ALLEGRO_E_OOM, "training dump allocation failed");
+  c->tr_cap = cap;
+  return ALLEGRO_OK;
+}
+
+// Add the weight gradient of seed * E at the current positions into d_grad
+// (FP32 passes in training mode, then the per-layer reductions).
+int train_eval(allegro_ctx* c, int64_t n, const double* pos, const int32_t* sp, const double* cell, double seed) {
+  double L[3];
+  int rc = prepare(c, n, pos, sp, cell, L);
+  if (rc) return rc;
+  int64_t np = 0;
+  rc = build_with_growth(c, c->d_pos, n, &np);
+  if (!rc) rc = ensure_train(c);
+  if (rc) return rc;
+  fill_passbufs(c, L);
+  c->pb.tr = c->tr;
+  c->pb.tr.seed = (float)seed;
+  c->pb.train = 1;
+  const Blob& B = c->blob;
+  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream);
+  c->pb.train = 0;
+  c->pb.tr.seed = 1.0f;
+  const int P = (int)np, D = c->D, C = (int)B.C, E = c->E, Lz = (int)B.L;
+  const int NS = B.lmax == 1 ? TP1_NS : TP2_NS, NT = B.lmax == 1 ? TP1_NT : TP2_NT;
+  const int NLM = ((int)B.lmax + 1) * ((int)B.lmax + 1), NW0 = C * ((int)B.lmax + 1), KH = D + C * NS;
+  const TrainBufs& t = c->tr;
+  cudaStream_t s = c->stream;
+  auto g = [&](const std::string& name) { return c->d_grad + winfo(c, name)->flat_off; };
+  const float isD = 1.0f / std::sqrt((float)D);
+  launch_wgrad(t.dz1_tb, D, t.h0, 16, P, D, 2 * (int)B.S + 8, 1.0f / std::sqrt((float)(2 * B.S + 8)),
+               g("twobody.0"), 2 * (int)B.S + 8, 0, s);
+  launch_wgrad(t.dz2_tb, D, t.a1_tb, D, P, D, D, isD, g("twobody.1"), D, 0, s);
+  launch_wgrad(t.dw0, NW0, c->pb.X[0], D, P, NW0, D, isD, g("embed"), D, 0, s);
+  for (int j = 0; j < Lz; ++j)
+    launch_wgrad(t.de[j], C, c->pb.X[j], D, P, C, D, isD / (float)std::sqrt(B.nu),
+                 g("layer" + std::to_string(j + 1) + ".env"), D, 0, s);
+  for (int k = 1; k <= Lz; ++k) {
+    const std::string pre = "layer" + std::to_string(k) + ".";
+    const float sh = 1.0f / std::sqrt((float)KH);
+    launch_wgrad(t.dz1_l[k], D, c->pb.X[k - 1], D, P, D, D, sh, g(pre + "latent.0"), KH, 0, s);
+    launch_wgrad(t.dz1_l[k], D, t.s[k], C * NS, P, D, C * NS, sh, g(pre + "latent.0"), KH, D, s);
+    launch_wgrad(t.dz2_l[k], D, t.a1_l[k], D, P, D, D, isD, g(pre + "latent.1"), D, 0, s);
+    if (k < Lz)
+      for (int l = 0; l <= (int)B.lmax; ++l) {
+        const int Pl = B.lmax == 1 ? tp1_P(l) : tp2_P(l), toff = B.lmax == 1 ? tp1_toff(l) : tp2_toff(l);
+        launch_wgrad_mix(c->pb.dV, t.T[k], P, C, NLM, NT, l, Pl, toff, 1.0f / std::sqrt((float)(C * Pl)),
+                         g(pre + "mix" + std::to_string(l)), s);
+      }
+  }
+  launch_wgrad(t.dze, E, t.xL, D, P, E, D, isD, g("energy.0"), D, 0, s);
+  launch_wgrad(t.dEij, 1, t.ae, E, P, 1, E, 1.0f / std::sqrt((float)E), g("energy.out"), E, 0, s);
+  return cuda_check(c, "weight gradient");
+}
+
+// Loss (per-atom MSE, energy:force weights) and its weight gradient into
+// d_grad.  The force term's gradient -d/dw sum_i v_i . dE/dr_i
+// (v = 2 c (F - F*), c = w_force / (3 N)) is the weight gradient of the
+// directional derivative of E along v, taken as a central difference of the
+// hand-written weight adjoint at r +/- h v (h v at most 0.01 A).
+int loss_grad_impl(allegro_ctx* c, const allegro_batch* b, double w_energy, double w_force, double* loss_out) {
+  const Blob& B = c->blob;
+  if (B.L > 2) return c->fail(ALLEGRO_E_UNSUPPORTED, "training is built for models of at most two layers");
+  int rc = init_master(c);
+  if (rc) return rc;
+  cudaMemsetAsync(c->d_grad, 0, sizeof(float) * c->n_params, c->stream);
+  const int nb = b->n_structs;
+  int64_t ntot = 0;
+  for (int k = 0; k < nb; ++k) ntot += b->atom_offset[k + 1] - b->atom_offset[k];
+  const double cf = w_force / (3.0 * (double)ntot);
+  double loss = 0.0;
+  const double delta = 1e-2;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t a0 = b->atom_offset[k], n = b->atom_offset[k + 1] - a0;
+    const double* pos = b->positions + 3 * a0;
+    const int32_t* sp = b->species + a0;
+    const double* cell = b->cells + 9 * k;
+    double L[3];
+    rc = prepare(c, n, pos, sp, cell, L);
+    int64_t np = 0;
+    if (!rc) rc = build_with_growth(c, c->d_pos, n, &np);
+    if (!rc) rc = run_model(c, ALLEGRO_FP32, L);
+    if (rc) return rc;
+    std::vector<float> F(3 * (size_t)n);
+    double stats[2];
+    cudaMemcpyAsync(F.data(), c->d_F, F.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(stats, c->d_stats, sizeof(stats), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "loss forward");
+    const double dE = stats[0] - b->e_target[k];
+    loss += w_energy / nb * (dE / n) * (dE / n);
+    std::vector<double> v(3 * (size_t)n), pp(3 * (size_t)n), pm(3 * (size_t)n);
+    double vmax = 0.0;
+    for (size_t q = 0; q < v.size(); ++q) {
+      const double r = (double)F[q] - (double)b->f_target[3 * a0 + q];
+      loss += cf * r * r;
+      v[q] = 2.0 * cf * r;
+      vmax = std::max(vmax, std::fabs(v[q]));
+    }
+    rc = train_eval(c, n, pos, sp, cell, 2.0 * w_energy * dE / ((double)nb * n * n));
+    if (rc) return rc;
+    if (vmax > 0.0) {
+      const double h = delta / vmax;
+      for (size_t q = 0; q < v.size(); ++q) {
+        pp[q] = pos[q] + h * v[q];
+        pm[q] = pos[q] - h * v[q];
+      }
+      rc = train_eval(c, n, pp.data(), sp, cell, -0.5 / h);
+      if (!rc) rc = train_eval(c, n, pm.data(), sp, cell, 0.5 / h);
+      if (rc) return rc;
+    }
+  }
+  if (loss_out) *loss_out = loss;
+  return ALLEGRO_OK;
+}
+
+int check_batch(allegro_ctx* c, const allegro_batch* b) {
+  if (!b || b->n_structs < 1 || !b->atom_offset || !b->positions || !b->species || !b->cells || !b->e_target ||
+      !b->f_target)
+    return c->fail(ALLEGRO_E_INVALID_ARG, "incomplete batch");
+  for (int k = 0; k < b->n_structs; ++k)
+    if (b->atom_offset[k + 1] <= b->atom_offset[k]) return c->fail(ALLEGRO_E_INVALID_ARG, "empty structure in batch");
   return ALLEGRO_OK;
 }
 
@@ -909,6 +1149,7 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
     case ALLEGRO_Q_CAPACITY: *value = ctx->capacity; return ALLEGRO_OK;
     case ALLEGRO_Q_STEP_KERNELS: *value = ctx->graph_kernels; return ALLEGRO_OK;
     case ALLEGRO_Q_N_ATOMS: *value = ctx->n_atoms; return ALLEGRO_OK;
+    case ALLEGRO_Q_N_PARAMS: *value = ctx->n_params; return ALLEGRO_OK;
     default: return ctx->fail(ALLEGRO_E_INVALID_ARG, "unknown query key");
   }
 }
@@ -952,6 +1193,68 @@ int allegro_md_get_state(allegro_ctx* ctx, double* positions, double* velocities
   if (rc) return rc;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "get_state");
   if (step) *step = ctx->step;
+  return ALLEGRO_OK;
+}
+
+int allegro_loss_grad(allegro_ctx* ctx, const allegro_batch* batch, double w_energy, double w_force,
+                      double* loss_out, float* grad_out) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  int rc = check_batch(ctx, batch);
+  if (!rc) rc = loss_grad_impl(ctx, batch, w_energy, w_force, loss_out);
+  if (!rc) rc = copy_out(ctx, grad_out, ctx->d_grad, sizeof(float) * ctx->n_params);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "loss_grad");
+  return rc;
+}
+
+int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double rho, double lr, double w_energy,
+                           double w_force, double* loss_out) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  if (!(rho >= 0.0) || !(lr >= 0.0)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "rho and lr must be >= 0");
+  int rc = check_batch(ctx, batch);
+  if (!rc) rc = loss_grad_impl(ctx, batch, w_energy, w_force, loss_out);      // g at w
+  if (rc) return rc;
+  const int n = (int)ctx->n_params;
+  launch_sumsq(ctx->d_grad, n, ctx->d_norm2, ctx->stream);
+  launch_ascent(ctx->d_master, ctx->d_grad, n, rho, ctx->d_norm2, ctx->d_wtmp, ctx->stream);   // w' = w + rho g/|g|
+  apply_flat(ctx, ctx->d_wtmp);
+  rc = loss_grad_impl(ctx, batch, w_energy, w_force, nullptr);                // g' at w'
+  if (rc) {
+    apply_flat(ctx, ctx->d_master);
+    return rc;
+  }
+  ctx->adam_t += 1;
+  launch_adam(ctx->d_master, ctx->d_grad, ctx->d_adam_m, ctx->d_adam_v, n, lr, ctx->adam_t, ctx->stream);
+  apply_flat(ctx, ctx->d_master);
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "sam step");
+  return ALLEGRO_OK;
+}
+
+int allegro_get_weights(allegro_ctx* ctx, float* out, int64_t n) {
+  if (!ctx || !out) return ALLEGRO_E_INVALID_ARG;
+  if (n != ctx->n_params) return ctx->fail(ALLEGRO_E_INVALID_ARG, "n must equal the parameter count");
+  int rc = init_master(ctx);
+  if (!rc) rc = copy_out(ctx, out, ctx->d_master, sizeof(float) * n);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "get_weights");
+  return rc;
+}
+
+int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n) {
+  if (!ctx || !in) return ALLEGRO_E_INVALID_ARG;
+  if (n != ctx->n_params) return ctx->fail(ALLEGRO_E_INVALID_ARG, "n must equal the parameter count");
+  int rc = init_master(ctx);
+  if (rc) return rc;
+  const cudaMemcpyKind k = is_device_ptr(in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(ctx->d_master, in, sizeof(float) * n, k, ctx->stream);
+  apply_flat(ctx, ctx->d_master);
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "set_weights");
   return ALLEGRO_OK;
 }
 

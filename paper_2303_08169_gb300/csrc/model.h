@@ -33,6 +33,28 @@ struct ModelW {
   int n_layers;
 };
 
+// Training mode of the FP32 passes: every linear layer's input and the
+// gradient of its pre-activation are written per pair (row-major [P][W]) so
+// that the weight gradients dW = sum_pairs dz (x) x can be reduced afterwards.
+struct TrainBufs {
+  float seed = 1.0f;                  // dL/dE of this evaluation (scales sigma_Z)
+  float* h0 = nullptr;                // [P][16] two-body input (12 used)
+  float* a1_tb = nullptr;             // [P][D]  SiLU of the first two-body layer
+  float* dz1_tb = nullptr;            // [P][D]
+  float* dz2_tb = nullptr;            // [P][D]
+  float* de[kMaxLayers] = {};         // [P][C]  gradient of env_{j+1}
+  float* dw0 = nullptr;               // [P][C (lmax+1)] gradient of the embedding output
+  float* s[kMaxLayers + 1] = {};      // [P][C P_0] tensor-product scalars of layer k
+  float* T[kMaxLayers] = {};          // [P][C NT] tensor-product outputs of layer k < L
+  float* a1_l[kMaxLayers + 1] = {};   // [P][D]  SiLU of latent layer k, first linear
+  float* dz1_l[kMaxLayers + 1] = {};  // [P][D]
+  float* dz2_l[kMaxLayers + 1] = {};  // [P][D]
+  float* xL = nullptr;                // [P][D]  x^L
+  float* ae = nullptr;                // [P][E]  energy-MLP hidden activation
+  float* dze = nullptr;               // [P][E]
+  float* dEij = nullptr;              // [P]     seed * sigma_Z
+};
+
 // Per-pass buffers (device).
 struct PassBufs {
   // neighbour list
@@ -62,6 +84,8 @@ struct PassBufs {
   float* dgam[kMaxLayers + 1];  // dGamma^k partials
   double* epart;                // sum_j E_ij partials
   int tile;                     // pairs per tile (all passes)
+  TrainBufs tr;                 // training dumps (FP32 path)
+  int train;                    // nonzero: write the TrainBufs dumps
 };
 
 // BF16 path weights: pre-scaled BF16 images in the 128-byte-swizzled K-major

@@ -323,6 +323,17 @@ AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float 
   sph_harm<Cf::LMAX>(u[0], u[1], u[2], Y);
 }
 
+// Training dumps: copy a kTile x W block of shared memory (row stride lds)
+// into a per-pair array (row-major [P][W]); no-op for a null array.
+template <int W>
+AL_DEV void dump_rows(float* g, const TileMeta& t, const float* s, int lds) {
+  if (!g) return;
+  for (int idx = threadIdx.x; idx < t.np * W; idx += kThreads) {
+    const int m = idx / W, n = idx % W;
+    g[(size_t)(t.p0 + m) * W + n] = s[m * lds + n];
+  }
+}
+
 // Shared-memory carve-up helper.
 struct Carve {
   float* p;
@@ -453,6 +464,10 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
   }
   cp_async_wait<0>();
   __syncthreads();
+  if (b.train) {
+    dump_rows<C * NS>(b.tr.s[k], t, s_h + D, LDH);
+    dump_rows<C * NT>(b.tr.T[k], t, s_T, C * NT);
+  }
   // channel mixing: V^k[c'][l3 m] = sum_{c, q} mix_l3[c'][c P + q] T[c][l3 block q m]
   for (int co = sub; co < C; co += kSub) {
 #pragma unroll
@@ -531,7 +546,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
       s_Y[p * NLM + q] = Y[q];
       s_dy[p * NLM + q] = 0.0f;
     }
-    s_sig[p] = p < t.np ? w.sigma[b.species[t.pi[p]]] : 0.0f;
+    s_sig[p] = p < t.np ? b.tr.seed * w.sigma[b.species[t.pi[p]]] : 0.0f;
   }
   load_rows<D>(b.X[L - 1], t, s_h, LDH);
   load_segments<CL>(b.gam[L], b.row_ptr, t, s_G);
@@ -551,6 +566,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
   }
   __syncthreads();
+  if (b.train) dump_rows<C * NS>(b.tr.s[L], t, s_h + D, LDH);
   gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
@@ -566,6 +582,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     s_ae[m * LDE + n] = silu(v);
   });
   __syncthreads();
+  if (b.train) {
+    dump_rows<D>(b.tr.a1_l[L], t, s_a1, LDD);
+    dump_rows<D>(b.tr.xL, t, s_h, LDH);
+    dump_rows<E>(b.tr.ae, t, s_ae, LDE);
+    dump_rows<1>(b.tr.dEij, t, s_sig, 1);
+  }
   if (threadIdx.x < kTile) {
     const int q = threadIdx.x;
     float acc = 0.0f;
@@ -585,6 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
       if (t.seg[q] == s) acc += (double)s_eij[q];
     b.epart[blockIdx.x + t.atom[s]] = acc;
   }
+  if (b.train) dump_rows<E>(b.tr.dze, t, s_ze, LDE);
   gemm<D, E>(s_ze, LDE, w.e0.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] = v; });  // dx^L
   __syncthreads();
   {
@@ -600,10 +623,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     if (sub == 0) s_du[p] = du * kRsqrt2;
   }
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.dz2_l[L], t, s_z2, LDD);
   gemm<D, D>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.dz1_l[L], t, s_z1, LDD);
   gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, float v) {
     if (n < D) s_h[m * LDH + n] = v + s_h[m * LDH + n] * kRsqrt2;   // dx^{L-1}
     else s_h[m * LDH + n] = v;                                      // d(scalars)
@@ -656,6 +681,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   }
   __syncthreads();
   if (L == 1) {
+    if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, t, s_dw0, Cf::NW0);
     gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
@@ -732,6 +758,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     }
   }
   __syncthreads();
+  if (b.train) dump_rows<C>(b.tr.de[k], t, s_de, C);
   const float* dXg = b.dX;
   gemm<D, C>(s_de, C, LN.env.n, s_wb, [&](int m, int n, float v) {
     s_z2[m * LDD + n] = v + (m < t.np ? dXg[(size_t)(t.p0 + m) * D + n] : 0.0f);   // dx^k
@@ -759,6 +786,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   __syncthreads();
   gemm<D, D>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) { s_tmp[m * LDD + n] = v; });  // z2
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.a1_l[k], t, s_a1, LDD);
   {
     float du = 0.0f;
     const float fc = s_fc[p];
@@ -773,11 +801,13 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     if (sub == 0) s_du[p] = du * kRsqrt2;
   }
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.dz2_l[k], t, s_z2, LDD);
   load_rows<CL>(b.dV, t, s_tmp, CL);            // dV^k
   gemm<D, D>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);     // dz1
   });
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.dz1_l[k], t, s_z1, LDD);
   gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, float v) {
     if (n < D) s_h[m * LDH + n] += v;
     else s_h[m * LDH + n] = v;
@@ -842,6 +872,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   }
   __syncthreads();
   if (k == 1) {
+    if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, t, s_dw0, Cf::NW0);
     gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
@@ -913,6 +944,10 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
     s_x[m * LDD + n] = s_geo[m * 8 + 4] * silu(v);
   });
   __syncthreads();
+  if (b.train) {
+    dump_rows<Cf::LDH0>(b.tr.h0, t, s_h0, Cf::LDH0);
+    dump_rows<D>(b.tr.a1_tb, t, s_a1, LDD);
+  }
   gemm<C, D>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -931,6 +966,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
     }
   }
   __syncthreads();
+  if (b.train) dump_rows<C>(b.tr.de[0], t, s_de, C);
   gemm<D, C>(s_de, C, w.layer[0].env.n, s_wb, [&](int m, int n, float v) { s_dx[m * LDD + n] += v; });
   __syncthreads();
   {
@@ -946,10 +982,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
     if (sub == 0) s_du[p] = du;
   }
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.dz2_tb, t, s_z2, LDD);
   gemm<D, D>(s_z2, LDD, w.tb1.n, s_wb, [&](int m, int n, float v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
+  if (b.train) dump_rows<D>(b.tr.dz1_tb, t, s_z1, LDD);
   gemm<Cf::H0, D>(s_z1, LDD, w.tb0.n, s_wb, [&](int m, int n, float v) { s_dh0[m * Cf::LDH0 + n] = v; });
   __syncthreads();
   if (threadIdx.x < t.np) {

@@ -1,0 +1,147 @@
+// train.cu - weight gradients and the SAM update (Eq. 3) on the GPU.
+//
+// dL/dW of a linear layer z = (W s) x (s = 1/sqrt(fan_in), extra factors
+// folded in) is s * sum_pairs dz (x) x, reduced here from the per-pair dumps
+// the FP32 passes write in training mode.  The SAM step (Eq. 3) then runs on
+// the flat parameter vector (blob order): the ascent w' = w + rho g/||g||,
+// and Adam (Table 5: beta = (0.9, 0.999)) with the gradient taken at w'.
+#include "train.h"
+
+namespace al {
+namespace {
+
+constexpr int kWT = 32;       // output tile (rows n, cols k) of the reduction
+constexpr int kWP = 64;       // pairs staged per step
+
+// dW[n * ldw + k0 + k] += scale * sum_{p in chunk} dz[p * ldz + n] * x[p * ldx + k]
+__global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int ldz, const float* __restrict__ x,
+                                               int ldx, int P, int N, int K, float scale, float* __restrict__ dW,
+                                               int ldw, int k0, int chunk) {
+  __shared__ float sz[kWP][kWT + 1];
+  __shared__ float sx[kWP][kWT + 1];
+  const int n0 = blockIdx.x * kWT, kb = blockIdx.y * kWT;
+  const int pb = blockIdx.z * chunk, pe = min(P, pb + chunk);
+  const int tn = threadIdx.x >> 3, tk = (threadIdx.x & 7) * 4;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int p0 = pb; p0 < pe; p0 += kWP) {
+    for (int idx = threadIdx.x; idx < kWP * kWT; idx += blockDim.x) {
+      const int pp = idx / kWT, c = idx % kWT;
+      const int p = p0 + pp;
+      sz[pp][c] = (p < pe && n0 + c < N) ? dz[(size_t)p * ldz + n0 + c] : 0.0f;
+      sx[pp][c] = (p < pe && kb + c < K) ? x[(size_t)p * ldx + kb + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int pp = 0; pp < kWP; ++pp) {
+      const float a = sz[pp][tn];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fmaf(a, sx[pp][tk + j], acc[j]);
+    }
+    __syncthreads();
+  }
+  const int n = n0 + tn;
+  if (n < N)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (kb + tk + j < K) atomicAdd(&dW[(size_t)n * ldw + k0 + kb + tk + j], scale * acc[j]);
+}
+
+// Mixing of order l: dW[c'][c Pl + q] += scale sum_p sum_m dV[p][c' NLM + l l + m] T[p][c NT + toff + q (2l+1) + m]
+__global__ void __launch_bounds__(256) k_wgrad_mix(const float* __restrict__ dV, const float* __restrict__ T, int P,
+                                                   int C, int NLM, int NT, int l, int Pl, int toff, float scale,
+                                                   float* __restrict__ dW, int chunk) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= C * C * Pl) return;
+  const int co = o / (C * Pl), rem = o % (C * Pl), c = rem / Pl, q = rem % Pl;
+  const int nm = 2 * l + 1;
+  const int pb = blockIdx.y * chunk, pe = min(P, pb + chunk);
+  float acc = 0.0f;
+  for (int p = pb; p < pe; ++p) {
+    const float* dv = dV + (size_t)p * C * NLM + co * NLM + l * l;
+    const float* t = T + (size_t)p * C * NT + c * NT + toff + q * nm;
+    for (int m = 0; m < nm; ++m) acc = fmaf(dv[m], t[m], acc);
+  }
+  atomicAdd(&dW[o], scale * acc);
+}
+
+__global__ void k_sumsq(const float* __restrict__ g, int n, double* __restrict__ out) {
+  __shared__ double sh[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)g[i] * (double)g[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += sh[k];
+    *out = t;
+  }
+}
+
+// w_out = w + rho g / ||g||  (w_out = w when ||g|| = 0)
+__global__ void k_ascent(const float* __restrict__ w, const float* __restrict__ g, int n, double rho,
+                         const double* __restrict__ norm2, float* __restrict__ w_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double nn = *norm2;
+  w_out[i] = nn > 0.0 ? (float)((double)w[i] + rho * (double)g[i] / sqrt(nn)) : w[i];
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, double lr, double b1, double b2, double eps, int t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gi = g[i];
+  const double mi = b1 * (double)m[i] + (1.0 - b1) * gi;
+  const double vi = b2 * (double)v[i] + (1.0 - b2) * gi * gi;
+  m[i] = (float)mi;
+  v[i] = (float)vi;
+  const double mh = mi / (1.0 - pow(b1, (double)t));
+  const double vh = vi / (1.0 - pow(b2, (double)t));
+  w[i] = (float)((double)w[i] - lr * mh / (sqrt(vh) + eps));
+}
+
+// scaled FP32 copies of one tensor: t [in][out], n [out][in]
+__global__ void k_apply(const float* __restrict__ flat, int rows, int cols, float scale, float* __restrict__ t_out,
+                        float* __restrict__ n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int o = i / cols, k = i % cols;
+  const float v = flat[i] * scale;
+  if (t_out) t_out[k * rows + o] = v;
+  if (n_out) n_out[i] = v;
+}
+
+}  // namespace
+
+void launch_wgrad(const float* dz, int ldz, const float* x, int ldx, int P, int N, int K, float scale, float* dW,
+                  int ldw, int k0, cudaStream_t s) {
+  if (P <= 0) return;
+  const int chunk = 2048;
+  dim3 grid((N + kWT - 1) / kWT, (K + kWT - 1) / kWT, (P + chunk - 1) / chunk);
+  k_wgrad<<<grid, 256, 0, s>>>(dz, ldz, x, ldx, P, N, K, scale, dW, ldw, k0, chunk);
+}
+
+void launch_wgrad_mix(const float* dV, const float* T, int P, int C, int NLM, int NT, int l, int Pl, int toff,
+                      float scale, float* dW, cudaStream_t s) {
+  if (P <= 0) return;
+  const int chunk = 1024;
+  dim3 grid((C * C * Pl + 255) / 256, (P + chunk - 1) / chunk);
+  k_wgrad_mix<<<grid, 256, 0, s>>>(dV, T, P, C, NLM, NT, l, Pl, toff, scale, dW, chunk);
+}
+
+void launch_sumsq(const float* g, int n, double* out, cudaStream_t s) { k_sumsq<<<1, 1024, 0, s>>>(g, n, out); }
+
+void launch_ascent(const float* w, const float* g, int n, double rho, const double* norm2, float* w_out,
+                   cudaStream_t s) {
+  k_ascent<<<(n + 255) / 256, 256, 0, s>>>(w, g, n, rho, norm2, w_out);
+}
+
+void launch_adam(float* w, const float* g, float* m, float* v, int n, double lr, int t, cudaStream_t s) {
+  k_adam<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, 0.9, 0.999, 1e-8, t);
+}
+
+void launch_apply(const float* flat, int rows, int cols, float scale, float* t_out, float* n_out, cudaStream_t s) {
+  k_apply<<<(rows * cols + 255) / 256, 256, 0, s>>>(flat, rows, cols, scale, t_out, n_out);
+}
+
+}  // namespace al
