@@ -255,6 +255,8 @@ int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double 
 /* The trainable weights as one FP32 vector in blob order (every weight
  * matrix row-major, sigma/mu excluded); host or device, n = n_params. */
 int allegro_get_weights(allegro_ctx* ctx, float* out, int64_t n);
+/* Replace the weights (host or device input) and reset the Adam state (moments
+ * zero, step count 0): the next SAM step is the first of a new run. */
 int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n);
 
 /* Keys of allegro_query. */

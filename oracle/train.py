@@ -61,7 +61,7 @@ def loss_and_grad(model, wvec, batch, w_energy=1.0, w_force=100.0, need_grad=Tru
     if not need_grad:
         return float(loss), None
     (gw,) = torch.autograd.grad(loss, vec)
-    return float(loss), gw.numpy()
+    return float(loss.detach()), gw.numpy()
 
 
 def adam_update(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -1249,6 +1249,9 @@ int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n) {
   if (rc) return rc;
   const cudaMemcpyKind k = is_device_ptr(in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaMemcpyAsync(ctx->d_master, in, sizeof(float) * n, k, ctx->stream);
+  cudaMemsetAsync(ctx->d_adam_m, 0, sizeof(float) * n, ctx->stream);     // new start: fresh Adam moments
+  cudaMemsetAsync(ctx->d_adam_v, 0, sizeof(float) * n, ctx->stream);
+  ctx->adam_t = 0;
   apply_flat(ctx, ctx->d_master);
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
