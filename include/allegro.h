@@ -57,6 +57,9 @@ extern "C" {
 #define ALLEGRO_BF16 1   /* per-pair GEMMs on tensor cores, BF16 operands,      */
                          /* FP32 accumulation (2-layer l_max 2 model)           */
 #define ALLEGRO_FP16 2   /* same tensor-core path with FP16 operands            */
+#define ALLEGRO_FP16_SPLIT 3  /* FP16 operands; the two-body MLP and the energy   */
+                         /* hidden layer with split operands x = hi + lo, three */
+                         /* MMAs per product (about twice the mantissa bits)    */
 
 typedef struct allegro_ctx allegro_ctx;
 
@@ -125,9 +128,10 @@ int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col,
  *  energy_out   : host, total energy E (FP64).
  *  forces_out   : host or device, N x 3 FP32 = -dE/dr (may be NULL).
  *  atom_energy  : host or device, N FP64 per-atom energies E_i (may be NULL).
- *  precision    : ALLEGRO_FP32, ALLEGRO_BF16 or ALLEGRO_FP16 (the last two:
- *                 E_UNSUPPORTED unless l_max = 2, C = 16, D = 128, E = 32,
- *                 at least two layers).
+ *  precision    : ALLEGRO_FP32, ALLEGRO_BF16, ALLEGRO_FP16 or
+ *                 ALLEGRO_FP16_SPLIT (the tensor-core modes: E_UNSUPPORTED
+ *                 unless l_max = 2, C = 16, D = 128, E = 32, at least two
+ *                 layers).
  * On ALLEGRO_E_PAIR_OVERFLOW nothing is written; the context has grown and
  * the call may simply be repeated.
  */
@@ -276,7 +280,10 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);
  *   ms_out[0] neighbour build   [1] pass A (two-body)   [2] passes B (layers
  *   below the last)   [3] pass C (last layer + energy, forward and adjoint)
  *   [4] passes B^T   [5] pass A^T (+ geometry adjoint)   [6] force assembly
- *   and reductions.
+ *   and reductions.  With n_out >= 11, the two kernels of each layer pass
+ *   of the tensor-core path, summed over layers: [7] B1 (tensor product +
+ *   mixing)  [8] B2 (latent MLP + env)  [9] B2^T  [10] B1^T; the FP32 path
+ *   has one kernel per layer pass ([7] = [2], [9] = [4], [8] = [10] = 0).
  * ms_out: host, n_out >= 7.  The MD state is unchanged (the evaluation is
  * deterministic).  Requires allegro_md_init.
  */

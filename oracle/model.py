@@ -57,12 +57,15 @@ def envelope(d, r_cut, p=6):
 
 
 class OracleModel:
-    """emulate: None (exact FP64), "bf16" or "fp16".  With emulation, every
-    per-pair GEMM (two-body, embedding, env, mixing, latent and energy hidden
-    layers) rounds its input and its pre-scaled weight matrix (1/sqrt(fan_in),
-    and 1/sqrt(nu) for env, folded in first) to that type and accumulates in
-    FP64: the operand precision of the tensor-core path, used to check that
-    path separately from the sensitivity of the model to rounding.  The energy
+    """emulate: None (exact FP64), "bf16", "fp16" or "fp16split".  With
+    emulation, every per-pair GEMM (two-body, embedding, env, mixing, latent
+    and energy hidden layers) rounds its input and its pre-scaled weight
+    matrix (1/sqrt(fan_in), and 1/sqrt(nu) for env, folded in first) to that
+    type and accumulates in FP64: the operand precision of the tensor-core
+    path, used to check that path separately from the sensitivity of the
+    model to rounding.  "fp16split" is "fp16" with the two-body MLP and the
+    energy hidden layer left unrounded (the tensor-core path splits their
+    operands into two FP16 parts, which carry about 22 bits).  The energy
     output layer, tensor products and all elementwise steps stay FP64."""
 
     def __init__(self, blob, emulate=None):
@@ -80,10 +83,11 @@ class OracleModel:
         self.cg = {p: torch.tensor(real_cg(*p), dtype=F64) for p in self.paths}
         if cfg["poly_p"] != 6:
             raise ValueError("poly_p = 6 only")
-        if emulate not in (None, "bf16", "fp16"):
-            raise ValueError("emulate must be None, 'bf16' or 'fp16'")
+        if emulate not in (None, "bf16", "fp16", "fp16split"):
+            raise ValueError("emulate must be None, 'bf16', 'fp16' or 'fp16split'")
         self.emulate = emulate
-        self._qdt = {"bf16": torch.bfloat16, "fp16": torch.float16}.get(emulate)
+        self._qdt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp16split": torch.float16}.get(emulate)
+        self._split = emulate == "fp16split"
 
     def _q(self, x):
         return x if self._qdt is None else x.to(self._qdt).to(F64)
@@ -104,9 +108,9 @@ class OracleModel:
     def _lin(x, W):
         return x @ W.T / math.sqrt(W.shape[1])
 
-    def _mlp(self, x, Ws, last_act=True):
+    def _mlp(self, x, Ws, last_act=True, exact=False):
         for k, W in enumerate(Ws):
-            x = self._qlin(x, W)
+            x = self._lin(x, W) if exact else self._qlin(x, W)
             if last_act or k + 1 < len(Ws):
                 x = silu(x)
         return x
@@ -146,7 +150,7 @@ class OracleModel:
         onehot = torch.eye(S, dtype=F64)
         h = torch.cat([onehot[Z[i]], onehot[Z[j]], B], dim=1)
         nlat = len(cfg["latent"])
-        x = fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)])
+        x = fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)], exact=self._split)
         w0 = self._qlin(x, w["embed"]).view(P, C, lmax + 1)
         V = [w0[:, :, l, None] * Y[l][:, None, :] for l in range(lmax + 1)]
         for layer in range(1, self.L + 1):
@@ -185,7 +189,7 @@ class OracleModel:
                           [w[f"layer{layer}.latent.{k}"] for k in range(nlat)])
             x = (x + fc[:, None] * m) / math.sqrt(2.0)
         ne = len(cfg["energy"])
-        hdn = self._mlp(x, [w[f"energy.{k}"] for k in range(ne)])
+        hdn = self._mlp(x, [w[f"energy.{k}"] for k in range(ne)], exact=self._split)
         Eij = self._lin(hdn, w["energy.out"])[:, 0]
         Esum = torch.zeros(N, dtype=F64).index_add(0, i, Eij)
         return sig * Esum + mu

@@ -16,6 +16,7 @@ from .build_lib import LIB, build
 ALLEGRO_FP32 = 0
 ALLEGRO_BF16 = 1
 ALLEGRO_FP16 = 2
+ALLEGRO_FP16_SPLIT = 3
 
 _STATUS = {
     0: "OK", 1: "E_INVALID_ARG", 2: "E_MISMATCH", 3: "E_CUTOFF_TOO_LARGE",
@@ -45,7 +46,8 @@ class _Batch(ctypes.Structure):
                 ("positions", ctypes.c_void_p), ("species", ctypes.c_void_p),
                 ("cells", ctypes.c_void_p), ("e_target", ctypes.c_void_p),
                 ("f_target", ctypes.c_void_p)]
-PHASES = ["neighbors", "pass_a", "pass_b", "pass_c", "pass_b_adjoint", "pass_a_adjoint", "forces"]
+PHASES = ["neighbors", "pass_a", "pass_b", "pass_c", "pass_b_adjoint", "pass_a_adjoint", "forces",
+          "pass_b1", "pass_b2", "pass_b2_adjoint", "pass_b1_adjoint"]
 
 
 class AllegroError(RuntimeError):
@@ -269,4 +271,4 @@ def allegro_selftest_mma_mode(a, b, d, mode):
     _check(None, lib().allegro_selftest_mma_mode(int(n), int(k), _ptr(a), _ptr(b), _ptr(d), int(mode)))
 
 
-__all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "ALLEGRO_FP16", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED
+__all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "ALLEGRO_FP16", "ALLEGRO_FP16_SPLIT", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED

@@ -152,6 +152,8 @@ struct allegro_ctx {
   BfW bw{};
   uint8_t* d_hw = nullptr;     // FP16 swizzled weight images
   BfW hw{};
+  uint8_t* d_sw = nullptr;     // FP16 images with split two-body / energy layers
+  BfW sw{};
   bool bf16_ok = false;
   // allocations
   std::vector<void*> allocs;
@@ -300,27 +302,57 @@ uint16_t f2bf(float f) {
   return (uint16_t)(u >> 16);
 }
 
+float bf2f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 // BF16 (or FP16) tensor-core images (layout of umma.cuh) of every linear
 // layer of the main model, pre-scaled like the FP32 copies.
-int upload_weights_bf16(allegro_ctx* c, bool fp16) {
+// Swizzled weight images of one tensor-core mode.  Split mode: FP16 images
+// plus the lo parts rn(w - rn(w)) of twobody.1 and energy.0, and twobody.0
+// packed as [hi | hi | lo] in columns 0, 16 and 32.
+int upload_weights_bf16(allegro_ctx* c, TcMode mode) {
   const Blob& B = c->blob;
+  const bool fp16 = mode != TcMode::kBf16;
+  const bool split = mode == TcMode::kFp16Split;
   std::vector<uint8_t> img;
-  auto add = [&](const Tensor* T, double extra, int Rimg, int Kimg) -> size_t {
+  auto cvt = [&](float x) { return fp16 ? f2h(x) : f2bf(x); };
+  auto back = [&](uint16_t h) { return fp16 ? __half2float(__ushort_as_half(h)) : bf2f(h); };
+  // part 0: rn(x); part 1: rn(x - rn(x)); copies at column offsets col_off
+  auto add_parts = [&](const Tensor* T, double extra, int Rimg, int Kimg, std::initializer_list<int> parts,
+                       std::initializer_list<int> col_off) -> size_t {
     const size_t base = (img.size() + 1023) / 1024 * 1024;
     img.resize(base + al::umma::sw128_bytes(Rimg, Kimg), 0);
     const double s = extra / std::sqrt((double)T->cols);
     for (uint32_t r = 0; r < T->rows; ++r)
       for (uint32_t k = 0; k < T->cols; ++k) {
         const float x = (float)(T->data[r * T->cols + k] * s);
-        const uint16_t h = fp16 ? f2h(x) : f2bf(x);
-        std::memcpy(img.data() + base + al::umma::sw128_off((int)r, (int)k, Rimg), &h, 2);
+        const uint16_t hi = cvt(x);
+        const uint16_t lo = cvt(x - back(hi));
+        auto po = parts.begin();
+        for (int off : col_off) {
+          const uint16_t h = *po++ == 0 ? hi : lo;
+          std::memcpy(img.data() + base + al::umma::sw128_off((int)r, (int)k + off, Rimg), &h, 2);
+        }
       }
     return base;
   };
-  size_t o_tb0 = add(B.find("twobody.0"), 1.0, 128, 64);
+  auto add = [&](const Tensor* T, double extra, int Rimg, int Kimg) {
+    return add_parts(T, extra, Rimg, Kimg, {0}, {0});
+  };
+  size_t o_tb0 = split ? add_parts(B.find("twobody.0"), 1.0, 128, 64, {0, 0, 1}, {0, 16, 32})
+                       : add(B.find("twobody.0"), 1.0, 128, 64);
   size_t o_tb1 = add(B.find("twobody.1"), 1.0, 128, 128);
   size_t o_emb = add(B.find("embed"), 1.0, 48, 128);
   size_t o_e0 = add(B.find("energy.0"), 1.0, 32, 128);
+  size_t o_tb1_lo = 0, o_e0_lo = 0;
+  if (split) {
+    o_tb1_lo = add_parts(B.find("twobody.1"), 1.0, 128, 128, {1}, {0});
+    o_e0_lo = add_parts(B.find("energy.0"), 1.0, 32, 128, {1}, {0});
+  }
   size_t o_env[kMaxLayers], o_l0[kMaxLayers], o_l1[kMaxLayers], o_mix[kMaxLayers][3];
   for (uint32_t k = 1; k <= B.L; ++k) {
     const std::string pre = "layer" + std::to_string(k) + ".";
@@ -334,12 +366,14 @@ int upload_weights_bf16(allegro_ctx* c, bool fp16) {
   if (!dev) return c->fail(ALLEGRO_E_OOM, "tensor-core weights allocation failed");
   if (cudaMemcpy(dev, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_check(c, "tensor-core weights upload");
-  (fp16 ? c->d_hw : c->d_bw) = dev;
-  BfW& w = fp16 ? c->hw : c->bw;
+  (split ? c->d_sw : fp16 ? c->d_hw : c->d_bw) = dev;
+  BfW& w = split ? c->sw : fp16 ? c->hw : c->bw;
   w.tb0 = dev + o_tb0;
   w.tb1 = dev + o_tb1;
   w.emb = dev + o_emb;
   w.e0 = dev + o_e0;
+  w.tb1_lo = split ? dev + o_tb1_lo : nullptr;
+  w.e0_lo = split ? dev + o_e0_lo : nullptr;
   for (uint32_t k = 1; k <= B.L; ++k) {
     w.env[k - 1] = dev + o_env[k - 1];
     w.lat0[k - 1] = dev + o_l0[k - 1];
@@ -593,16 +627,25 @@ int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* s
   return cuda_check(c, "prepare");
 }
 
+bool valid_precision(int32_t p) {
+  return p == ALLEGRO_FP32 || p == ALLEGRO_BF16 || p == ALLEGRO_FP16 || p == ALLEGRO_FP16_SPLIT;
+}
+
 // Pair passes of the requested precision followed by force assembly.
-void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, cudaEvent_t* ev) {
+void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, KernelMarks* km) {
   const Blob& B = c->blob;
   int tile;
-  if (precision == ALLEGRO_BF16 || precision == ALLEGRO_FP16) {
-    const bool h = precision == ALLEGRO_FP16;
-    bf16_energy_forces(h ? c->hw : c->bw, c->pb, c->capacity, s, ev, h);
+  if (precision == ALLEGRO_BF16) {
+    bf16_energy_forces(c->bw, c->pb, c->capacity, s, km, TcMode::kBf16);
+    tile = bf16_tile();
+  } else if (precision == ALLEGRO_FP16) {
+    bf16_energy_forces(c->hw, c->pb, c->capacity, s, km, TcMode::kFp16);
+    tile = bf16_tile();
+  } else if (precision == ALLEGRO_FP16_SPLIT) {
+    bf16_energy_forces(c->sw, c->pb, c->capacity, s, km, TcMode::kFp16Split);
     tile = bf16_tile();
   } else {
-    fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, ev);
+    fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km);
     tile = fp32_tile();
   }
   launch_forces(atom_args(c), c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, tile, c->d_F, c->d_Ei, c->d_blk,
@@ -612,8 +655,9 @@ void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, cudaEvent_t
 int refresh_tc(allegro_ctx* c);
 
 int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
-  if (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16 && precision != ALLEGRO_FP16)
-    return c->fail(ALLEGRO_E_INVALID_ARG, "precision must be ALLEGRO_FP32, ALLEGRO_BF16 or ALLEGRO_FP16");
+  if (!valid_precision(precision))
+    return c->fail(ALLEGRO_E_INVALID_ARG,
+                   "precision must be ALLEGRO_FP32, ALLEGRO_BF16, ALLEGRO_FP16 or ALLEGRO_FP16_SPLIT");
   if (precision != ALLEGRO_FP32 && !c->bf16_ok)
     return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
   if (precision != ALLEGRO_FP32) {
@@ -680,8 +724,10 @@ int refresh_tc(allegro_ctx* c) {
   }
   c->dfree(c->d_bw);
   c->dfree(c->d_hw);
-  int rc = upload_weights_bf16(c, false);
-  if (!rc) rc = upload_weights_bf16(c, true);
+  c->dfree(c->d_sw);
+  int rc = upload_weights_bf16(c, TcMode::kBf16);
+  if (!rc) rc = upload_weights_bf16(c, TcMode::kFp16);
+  if (!rc) rc = upload_weights_bf16(c, TcMode::kFp16Split);
   if (!rc) c->tc_dirty = false;
   return rc;
 }
@@ -880,8 +926,9 @@ int allegro_create(const void* weights_blob, size_t blob_bytes, const double* sp
   for (int s = 0; s < 2; ++s) c->mass[s] = species_mass[s];
   int rc = upload_weights(c);
   c->bf16_ok = bf16_supported((int)B.lmax, (int)B.C, c->D, c->E, (int)B.L);
-  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, false);
-  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, true);
+  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, TcMode::kBf16);
+  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, TcMode::kFp16);
+  if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, TcMode::kFp16Split);
   if (rc) {
     g_err = c->err;
     delete c;
@@ -985,8 +1032,7 @@ int allegro_outlier_count(allegro_ctx* ctx, int64_t n_atoms, const float* forces
 }
 
 int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
-  if (!ctx || (precision != ALLEGRO_FP32 && precision != ALLEGRO_BF16 && precision != ALLEGRO_FP16))
-    return ALLEGRO_E_INVALID_ARG;
+  if (!ctx || !valid_precision(precision)) return ALLEGRO_E_INVALID_ARG;
   if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
     return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
   if (precision != ctx->md_precision && ctx->graph) {
@@ -1157,30 +1203,52 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
 int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_t n_out) {
   if (!ctx || !ms_out || n_out < 7 || n_reps < 1) return ALLEGRO_E_INVALID_ARG;
   if (!ctx->md_ready) return ctx->fail(ALLEGRO_E_INVALID_ARG, "md_init first");
-  cudaEvent_t ev[8];
-  for (auto& e : ev) cudaEventCreate(&e);
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  KernelMarks km;
+  for (auto& e : km.ev) cudaEventCreate(&e);
+  cudaEvent_t e_begin, e_end;
+  cudaEventCreate(&e_begin);
+  cudaEventCreate(&e_end);
+  double kind_ms[kKindCount] = {}, nb_ms = 0.0, f_ms = 0.0;
   double L[3] = {ctx->grid.L[0], ctx->grid.L[1], ctx->grid.L[2]};
   fill_passbufs(ctx, L);
   int rc = ALLEGRO_OK;
   for (int r = 0; r < n_reps && !rc; ++r) {
-    cudaEventRecord(ev[0], ctx->stream);
+    km.n = 0;
+    cudaEventRecord(e_begin, ctx->stream);
     launch_build_neighbors(ctx->nb, ctx->grid, ctx->d_pos, ctx->n_atoms, ctx->stream);
-    launch_model(ctx, ctx->md_precision, ctx->stream, ev + 1);
-    cudaEventRecord(ev[7], ctx->stream);
+    launch_model(ctx, ctx->md_precision, ctx->stream, &km);
+    cudaEventRecord(e_end, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
       rc = cuda_check(ctx, "phase times");
       break;
     }
-    for (int k = 0; k < 7; ++k) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-      acc[k] += ms;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e_begin, km.ev[0]);
+    nb_ms += ms;
+    for (int i = 0; i + 1 < km.n; ++i) {
+      cudaEventElapsedTime(&ms, km.ev[i], km.ev[i + 1]);
+      kind_ms[km.kind[i + 1]] += ms;
     }
+    cudaEventElapsedTime(&ms, km.ev[km.n - 1], e_end);
+    f_ms += ms;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : km.ev) cudaEventDestroy(e);
+  cudaEventDestroy(e_begin);
+  cudaEventDestroy(e_end);
   if (rc) return rc;
-  for (int k = 0; k < 7; ++k) ms_out[k] = acc[k] / n_reps;
+  const double n = n_reps;
+  const double out[11] = {nb_ms / n,
+                          kind_ms[kKA] / n,
+                          (kind_ms[kKB] + kind_ms[kKB2]) / n,
+                          kind_ms[kKC] / n,
+                          (kind_ms[kKBT] + kind_ms[kKBT2]) / n,
+                          kind_ms[kKAT] / n,
+                          f_ms / n,
+                          kind_ms[kKB] / n,
+                          kind_ms[kKB2] / n,
+                          kind_ms[kKBT] / n,
+                          kind_ms[kKBT2] / n};
+  for (int k = 0; k < std::min(n_out, 11); ++k) ms_out[k] = out[k];
   return ALLEGRO_OK;
 }
 

@@ -99,6 +99,10 @@ struct BfW {
   const uint8_t* lat0[kMaxLayers] = {};   // [128 x 192] (176 inputs used)
   const uint8_t* lat1[kMaxLayers] = {};
   const uint8_t* mix[kMaxLayers][3] = {}; // [16 x 64] (C P_l inputs used)
+  // split mode: tb0 holds [W_hi | W_hi | W_lo] in columns 0, 16, 32; lo images
+  // of twobody.1 and energy.0
+  const uint8_t* tb1_lo = nullptr;
+  const uint8_t* e0_lo = nullptr;
   const float* eout = nullptr;    // 32 FP32
   float sigma[2];
   float rc;
@@ -107,9 +111,28 @@ struct BfW {
 
 bool bf16_supported(int lmax, int C, int D, int E, int L);
 int bf16_tile();
-// fp16: operands in FP16 (images of w must then be FP16 too), else BF16.
+// Optional launch timing: mark(kind) records an event on the stream after a
+// pass kernel, tagged with its kind; interval i lies between event i and
+// event i + 1 and belongs to kind[i + 1].
+enum KernelKind { kKStart = -1, kKA = 0, kKB, kKB2, kKC, kKBT, kKBT2, kKAT, kKindCount };
+struct KernelMarks {
+  static constexpr int kMax = 48;
+  cudaEvent_t ev[kMax];
+  int kind[kMax];
+  int n = 0;
+  void mark(int k, cudaStream_t s) {
+    if (n < kMax) {
+      cudaEventRecord(ev[n], s);
+      kind[n++] = k;
+    }
+  }
+};
+
+// Operand type of the tensor-core passes; the images in w must match
+// (kFp16Split: FP16 images with the split two-body and energy layers).
+enum class TcMode { kBf16, kFp16, kFp16Split };
 void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s,
-                        cudaEvent_t* ev = nullptr, bool fp16 = false);
+                        KernelMarks* km, TcMode mode);
 
 // FP32 path: one launcher per pass sequence; templated on the model shape in
 // the .cu file, dispatched by (lmax, C, D, E).
@@ -117,7 +140,7 @@ bool fp32_supported(int lmax, int C, int D, int E);
 // ev (optional, 6 events): recorded before pass A, after A, after the B
 // passes, after C, after the B^T passes and after A^T.
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
-                        int64_t capacity, cudaStream_t s, cudaEvent_t* ev = nullptr);
+                        int64_t capacity, cudaStream_t s, KernelMarks* km = nullptr);
 int fp32_tile();
 
 }  // namespace al

@@ -36,6 +36,8 @@ constexpr int kT = 128;
 constexpr int kThr = 256;
 constexpr int D = 128, C = 16, E = 32, NLM = 9, NS = 3, KH = 176, NW0 = 48, CL = 144, NB = 8;
 constexpr float kR2 = 0.70710678118654752f;
+// odd row strides of per-row shared arrays (32 consecutive rows hit 32 banks)
+constexpr int CLP = CL + 1, EP = C + 1, GP = 9;
 
 constexpr uint32_t kImgTb0 = sw128_bytes(128, 64);
 constexpr uint32_t kImgTb1 = sw128_bytes(128, 128);
@@ -62,11 +64,18 @@ template <class T> struct Op;
 template <> struct Op<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   static AL_DEV uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+  static AL_DEV float round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 };
 template <> struct Op<__half> {
   static constexpr uint32_t fmt = 0;
   static AL_DEV uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+  static AL_DEV float round(float x) { return __half2float(__float2half_rn(x)); }
 };
+
+// Split operands (the two-body MLP and the energy hidden layer in the split
+// mode): x = hi + lo with hi = rn(x), lo = rn(x - hi), and a product
+// A B ~ A_hi B_hi + A_lo B_hi + A_hi B_lo as three MMAs into one FP32
+// accumulator, which keeps about twice the operand type's mantissa bits.
 
 AL_DEV float tanh_fast(float x) {
   float y;
@@ -219,7 +228,8 @@ AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float 
 // K-major image of an [N x K] matrix or (b_mn) the image of a [P x N] matrix
 // read MN-major.
 template <class Tin>
-AL_DEV void mma_k(uint32_t d, const uint8_t* A, int kk0, const uint8_t* B, int N, int nk, bool b_mn, int P) {
+AL_DEV void mma_k(uint32_t d, const uint8_t* A, int kk0, const uint8_t* B, int N, int nk, bool b_mn, int P,
+                  bool acc = false) {
   const uint32_t idesc = idesc_f16kind(128, N, b_mn, Op<Tin>::fmt);
   const uint32_t a = smem_u32(A), bb = smem_u32(B);
   for (int i = 0; i < nk; ++i) {
@@ -228,7 +238,7 @@ AL_DEV void mma_k(uint32_t d, const uint8_t* A, int kk0, const uint8_t* B, int N
     uint64_t bd;
     if (b_mn) bd = desc_sw128_mn(bb + (uint32_t)(i * 16 * 128), (uint32_t)(P * 128), 1024u);
     else bd = desc_sw128(bb + (uint32_t)((i >> 2) * (N * 128) + (i & 3) * 32));
-    mma_bf16(d, desc_sw128(a + aoff), bd, idesc, i > 0 ? 1u : 0u);
+    mma_bf16(d, desc_sw128(a + aoff), bd, idesc, (i > 0 || acc) ? 1u : 0u);
   }
 }
 
@@ -282,6 +292,24 @@ template <class Tin>
 AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
   st8<Tin>(A, sw128_off(r, c0, 128), v);
   st8<Tin>(A, sw128_off(r, c0 + 8, 128), v + 8);
+}
+// hi part into Ahi, lo part into Alo (same row and columns)
+template <class Tin>
+AL_DEV void st16_split(uint8_t* Ahi, uint8_t* Alo, int r, int c0, const float* v) {
+  float hi[16], lo[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    hi[q] = Op<Tin>::round(v[q]);
+    lo[q] = v[q] - hi[q];
+  }
+  st16<Tin>(Ahi, r, c0, hi);
+  st16<Tin>(Alo, r, c0, lo);
+}
+// operand store of an epilogue: hi (and lo) parts in split mode
+template <class Tin, bool kSplit>
+AL_DEV void st16_op(uint8_t* A, uint8_t* Alo, int r, int c0, const float* v) {
+  if (kSplit) st16_split<Tin>(A, Alo, r, c0, v);
+  else st16<Tin>(A, r, c0, v);
 }
 template <class Tin>
 AL_DEV void st1(uint8_t* A, int r, int c, float v) {
@@ -343,22 +371,57 @@ AL_DEV uint8_t* align1024(uint8_t* p) {
 
 constexpr int kFlagTimeoutBit = 4;
 
+// two-body input row (16 columns, 12 used); split mode: [hi | lo | hi]
+template <class Tin, bool kSplit>
+AL_DEV void st_h0(uint8_t* H0, int r, const float* h0) {
+  if (kSplit) {
+    float hi[16], lo[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      hi[q] = Op<Tin>::round(h0[q]);
+      lo[q] = h0[q] - hi[q];
+    }
+    st16<Tin>(H0, r, 0, hi);
+    st16<Tin>(H0, r, 16, lo);
+    st16<Tin>(H0, r, 32, hi);
+  } else {
+    st16<Tin>(H0, r, 0, h0);
+  }
+}
+
+// D = A B (one thread issues): plain, or the three split products
+template <class Tin, bool kSplit>
+AL_DEV void mma_split(uint32_t d, const uint8_t* A, const uint8_t* Alo, const uint8_t* B, const uint8_t* Blo, int N,
+                      int nk, bool b_mn, int P) {
+  mma_k<Tin>(d, A, 0, B, N, nk, b_mn, P);
+  if (kSplit) {
+    mma_k<Tin>(d, Alo, 0, B, N, nk, b_mn, P, true);
+    mma_k<Tin>(d, A, 0, Blo, N, nk, b_mn, P, true);
+  }
+}
+
 // ============================================================================
 // Pass A: geometry, two-body MLP (12 -> 128 -> 128), x0, env1 -> Gamma^1.
-template <class Tin>
+// Split mode: the two-body MLP GEMMs take split operands.  The first one packs
+// [h_hi | h_lo | h_hi] against the image [W_hi | W_hi | W_lo] along K (12
+// inputs fit a 16-column K-step), the second adds the lo MMAs.
+template <class Tin, bool kSplit>
 __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
-  BF_PROLOGUE(kImgTb0 + kImgTb1 + kImgEnv, {
+  BF_PROLOGUE(kImgTb0 + (kSplit ? 2 : 1) * kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
     bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
     bulk_g2s(sm + kImgTb0 + kImgTb1, w.env[0], kImgEnv, &bars[1]);
+    if (kSplit) bulk_g2s(sm + kImgTb0 + kImgTb1 + kImgEnv, w.tb1_lo, kImgTb1, &bars[1]);
   })
   uint8_t* Wtb0 = sm;
   uint8_t* Wtb1 = Wtb0 + kImgTb0;
   uint8_t* Wenv = Wtb1 + kImgTb1;
-  uint8_t* H0 = Wenv + kImgEnv;
+  uint8_t* Wtb1lo = Wenv + kImgEnv;                      // split mode only
+  uint8_t* H0 = Wtb1lo + (kSplit ? kImgTb1 : 0);
   uint8_t* A1 = H0 + kOp64;
   uint8_t* X = A1 + kOp128;
-  float* s_fc = reinterpret_cast<float*>(X + kOp128);
+  uint8_t* A1lo = X + kOp128;                            // split mode only
+  float* s_fc = reinterpret_cast<float*>(A1lo + (kSplit ? kOp128 : 0));
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
@@ -382,16 +445,16 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-      st16<Tin>(H0, r, 0, h0);
+      st_h0<Tin, kSplit>(H0, r, h0);
     }
-    mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });
     epi(tmem, 0, 128, [&](int r, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16<Tin>(A1, r, n0, o);
+      st16_op<Tin, kSplit>(A1, A1lo, r, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });
+    mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int r, int n0, const float* v) {
       float o[16];
       const float fc = s_fc[r];
@@ -407,10 +470,10 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) s_e[threadIdx.x * 16 + q] = v[q];
+      for (int q = 0; q < 16; ++q) s_e[threadIdx.x * EP + q] = v[q];
     }
     __syncthreads();
-    seg_store(b.gam[1], m, CL, [&](int p, int x) { return s_e[p * 16 + x / NLM] * s_Y[p * NLM + x % NLM]; });
+    seg_store(b.gam[1], m, CL, [&](int p, int x) { return s_e[p * EP + x / NLM] * s_Y[p * NLM + x % NLM]; });
     __syncthreads();
   }
   BF_EPILOGUE
@@ -562,10 +625,10 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) s_e[r * 16 + q] = v[q];
+      for (int q = 0; q < 16; ++q) s_e[r * EP + q] = v[q];
     }
     __syncthreads();
-    seg_store(b.gam[k + 1], m, CL, [&](int p, int x) { return s_e[p * 16 + x / NLM] * s_Y[p * NLM + x % NLM]; });
+    seg_store(b.gam[k + 1], m, CL, [&](int p, int x) { return s_e[p * EP + x / NLM] * s_Y[p * NLM + x % NLM]; });
     __syncthreads();
   }
   BF_EPILOGUE
@@ -574,18 +637,23 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 // ============================================================================
 // Pass C: last layer + energy MLP forward, dE/dE_ij = sigma_Z, and their
 // adjoint: dx^{L-1}, dV^{L-1}, dGamma^L partials, du, energy partials.
-template <class Tin>
+// Split mode: the energy hidden layer takes split operands; the lo part of
+// x^L goes to A1 (free after the second latent MMA) and dz_E keeps its hi and
+// lo parts side by side in the 64 columns of AE.
+template <class Tin, bool kSplit>
 __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
   const int L = w.n_layers;
-  BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgE0, {
+  BF_PROLOGUE(kImgLat0 + kImgLat1 + (kSplit ? 2 : 1) * kImgE0, {
     bulk_g2s(sm, w.lat0[L - 1], kImgLat0, &bars[1]);
     bulk_g2s(sm + kImgLat0, w.lat1[L - 1], kImgLat1, &bars[1]);
     bulk_g2s(sm + kImgLat0 + kImgLat1, w.e0, kImgE0, &bars[1]);
+    if (kSplit) bulk_g2s(sm + kImgLat0 + kImgLat1 + kImgE0, w.e0_lo, kImgE0, &bars[1]);
   })
   uint8_t* Wl0 = sm;
   uint8_t* Wl1 = Wl0 + kImgLat0;
   uint8_t* We0 = Wl1 + kImgLat1;
-  uint8_t* HA = We0 + kImgE0;
+  uint8_t* We0lo = We0 + kImgE0;                       // split mode only
+  uint8_t* HA = We0lo + (kSplit ? kImgE0 : 0);
   uint8_t* A1 = HA + kOpH;
   uint8_t* AE = A1 + kOp128;
   float* s_dg = reinterpret_cast<float*>(HA);          // reuses HA + A1 after the last MMA
@@ -643,9 +711,9 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         const float x = valid ? xg[sidx(m, D, n0 + q, rr)] : 0.0f;
         o[q] = (x + fc * silu_b(v[q])) * kR2;
       }
-      st16<Tin>(HA, rr, n0, o);
+      st16_op<Tin, kSplit>(HA, A1, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, We0, 32, 8, false, 0); });
+    mm.run([&] { mma_split<Tin, kSplit>(tmem + 256, HA, A1, We0, We0lo, 32, 8, false, 0); });
     if (threadIdx.x < kT) {
       float ze[32];
       tmem_ld16(lanes(tmem) + 256, ze);
@@ -659,10 +727,29 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         dz[n] = sig * wo * dsilu_b(ze[n]);
       }
       s_eij[r] = valid ? e : 0.0f;
-      st16<Tin>(AE, r, 0, dz);
-      st16<Tin>(AE, r, 16, dz + 16);
+      if (kSplit) {                                   // hi in columns 0..31, lo in 32..63
+        float hi[32], lo[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          hi[q] = Op<Tin>::round(dz[q]);
+          lo[q] = dz[q] - hi[q];
+        }
+        st16<Tin>(AE, r, 0, hi);
+        st16<Tin>(AE, r, 16, hi + 16);
+        st16<Tin>(AE, r, 32, lo);
+        st16<Tin>(AE, r, 48, lo + 16);
+      } else {
+        st16<Tin>(AE, r, 0, dz);
+        st16<Tin>(AE, r, 16, dz + 16);
+      }
     }
-    mm.run([&] { mma_k<Tin>(tmem + 288, AE, 0, We0, 128, 2, true, 32); });      // dx^L
+    mm.run([&] {                                                                // dx^L
+      mma_k<Tin>(tmem + 288, AE, 0, We0, 128, 2, true, 32);
+      if (kSplit) {
+        mma_k<Tin>(tmem + 288, AE, 2, We0, 128, 2, true, 32, true);
+        mma_k<Tin>(tmem + 288, AE, 0, We0lo, 128, 2, true, 32, true);
+      }
+    });
     {
       float du = 0.0f;
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dx) {
@@ -710,7 +797,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
         tp2_bwd_scalar(V, G, ds + cc * NS, dV, dG);
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) s_dg[r * CL + c * NLM + lm] = dG[lm];
+        for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
         if (valid)
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(m, CL, c * NLM + lm, r)] = dV[lm];
@@ -728,7 +815,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(m, NLM, lm, r)] = 0.0f;
     }
-    seg_store(b.dgam[L], m, CL, [&](int p, int x) { return s_dg[p * CL + x]; });
+    seg_store(b.dgam[L], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
     __syncthreads();
   }
   BF_EPILOGUE
@@ -879,8 +966,8 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   uint8_t* X = DVT + kOpH;
   uint8_t* DW0 = X + kOp128;
   float* s_Y = reinterpret_cast<float*>(DW0 + kOp64);
-  float* s_dg = s_Y + kT * NLM;           // [kT][CL]
-  float* s_dy = s_dg + kT * CL;           // [2][kT][NLM]
+  float* s_dg = s_Y + kT * NLM;           // [kT][CLP]
+  float* s_dy = s_dg + kT * CLP;          // [2][kT][NLM]
   float* s_g = s_dy + 2 * kT * NLM;       // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
@@ -969,10 +1056,10 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
           }
           get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) dG[lm] = round == 0 ? 0.0f : s_dg[r * CL + c * NLM + lm];
+          for (int lm = 0; lm < NLM; ++lm) dG[lm] = round == 0 ? 0.0f : s_dg[r * CLP + c * NLM + lm];
           tp2_bwd(V, G, dT, dVa[c4], dG);
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) s_dg[r * CL + c * NLM + lm] = dG[lm];
+          for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
         }
       }
       if (k >= 2) {
@@ -1013,7 +1100,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       for (int lm = 0; lm < NLM; ++lm)
         b.dY[sidx(m, NLM, lm, r)] += s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm];
     }
-    seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CL + x]; });
+    seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
     __syncthreads();
   }
   BF_EPILOGUE
@@ -1022,23 +1109,30 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 // ============================================================================
 // Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP (recomputed)
 // and of the geometry; writes g_ij = dE/dDelta_ij.
-template <class Tin>
+// DE shares H0's buffer (H0 is dead after the first MMA).  Split mode: both
+// two-body GEMMs and their adjoints take split operands; A1lo holds the lo
+// part of silu(z1), then of dz2, then of dz1.  The dh0 adjoint reads the
+// packed image [W_hi | W_hi | W_lo] (48 columns): dh0 = block 0 + block 2.
+template <class Tin, bool kSplit>
 __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
-  BF_PROLOGUE(kImgTb0 + kImgTb1 + kImgEnv, {
+  BF_PROLOGUE(kImgTb0 + (kSplit ? 2 : 1) * kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
     bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
     bulk_g2s(sm + kImgTb0 + kImgTb1, w.env[0], kImgEnv, &bars[1]);
+    if (kSplit) bulk_g2s(sm + kImgTb0 + kImgTb1 + kImgEnv, w.tb1_lo, kImgTb1, &bars[1]);
   })
   uint8_t* Wtb0 = sm;
   uint8_t* Wtb1 = Wtb0 + kImgTb0;
   uint8_t* Wenv = Wtb1 + kImgTb1;
-  uint8_t* H0 = Wenv + kImgEnv;
+  uint8_t* Wtb1lo = Wenv + kImgEnv;                      // split mode only
+  uint8_t* H0 = Wtb1lo + (kSplit ? kImgTb1 : 0);
+  uint8_t* DE = H0;
   uint8_t* A1 = H0 + kOp64;
   uint8_t* X = A1 + kOp128;
-  uint8_t* DE = X + kOp128;
-  float* s_geo = reinterpret_cast<float*>(DE + kOp64);   // [kT][8]: u, d, fc, dfc
-  float* s_dB = s_geo + kT * 8;                           // [kT][NB]
-  float* s_Y = s_dB + kT * NB;
+  uint8_t* A1lo = X + kOp128;                            // split mode only
+  float* s_geo = reinterpret_cast<float*>(A1lo + (kSplit ? kOp128 : 0));   // [kT][GP]: u, d, fc, dfc
+  float* s_dB = s_geo + kT * GP;                          // [kT][GP]: dB
+  float* s_Y = s_dB + kT * GP;
   float* s_dy = s_Y + kT * NLM;
   float* s_du = s_dy + kT * NLM;                          // [2][kT]
   float* s_g = s_du + 2 * kT;                             // [kSegCap][CL]
@@ -1062,26 +1156,26 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
       }
-      float* g = s_geo + r * 8;
+      float* g = s_geo + r * GP;
       g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
 #pragma unroll
-      for (int q = 0; q < NB; ++q) s_dB[r * NB + q] = dB[q];
+      for (int q = 0; q < NB; ++q) s_dB[r * GP + q] = dB[q];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-      st16<Tin>(H0, r, 0, h0);
+      st_h0<Tin, kSplit>(H0, r, h0);
     }
     stage_g(b.dgam[1], b.row_ptr, m, s_g);
-    mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, 1, false, 0); });       // z1
+    mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });   // z1
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16<Tin>(A1, rr, n0, o);
+      st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wtb1, 128, 8, false, 0); });    // z2
+    mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });   // z2
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16];
-      const float fc = s_geo[rr * 8 + 4];
+      const float fc = s_geo[rr * GP + 4];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
       st16<Tin>(X, rr, n0, o);
@@ -1114,37 +1208,46 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
         float z2[16], o[16];
         tmem_ld16(lanes(tmem) + 128 + n0, z2);
-        const float fc = s_geo[rr * 8 + 4];
+        const float fc = s_geo[rr * GP + 4];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const float dx = dxe[q] + (valid ? dxg[sidx(m, D, n0 + q, rr)] : 0.0f);
           du = fmaf(dx, silu_b(z2[q]), du);
           o[q] = dx * fc * dsilu_b(z2[q]);
         }
-        st16<Tin>(A1, rr, n0, o);
+        st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o);
       });
       s_du[h * kT + r] = du;
     }
-    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wtb1, 128, 8, true, 128); });   // da1
+    mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, true, 128); });   // da1
     epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
       float z1[16], o[16];
       tmem_ld16(lanes(tmem) + n0, z1);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
-      st16<Tin>(X, rr, n0, o);
+      st16_op<Tin, kSplit>(X, A1lo, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 416, X, 0, Wtb0, 16, 8, true, 128); });     // dh0
+    mm.run([&] {                                                                // dh0
+      mma_k<Tin>(tmem + 416, X, 0, Wtb0, kSplit ? 48 : 16, 8, true, 128);
+      if (kSplit) mma_k<Tin>(tmem + 416, A1lo, 0, Wtb0, 48, 8, true, 128, true);
+    });
     if (threadIdx.x < kT) {
       float dh[16];
       tmem_ld16(lanes(tmem) + 416, dh);
+      if (kSplit) {
+        float dl[16];
+        tmem_ld16(lanes(tmem) + 448, dl);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dh[q] += dl[q];
+      }
       if (valid) {
-        const float* g = s_geo + r * 8;
+        const float* g = s_geo + r * GP;
         const float u[3] = {g[0], g[1], g[2]};
         const float d = g[3], dfc = g[5];
         const size_t pp = (size_t)(m.p0 + r);
         float gd = (s_du[r] + s_du[kT + r] + b.dU[sidx(m, 1, 0, r)]) * dfc;
 #pragma unroll
-        for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * NB + n], gd);
+        for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * GP + n], gd);
         float dY[NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[sidx(m, NLM, lm, r)];
@@ -1162,33 +1265,44 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
 }
 
 // shared-memory bytes of each kernel (+1024 for the manual 1024-byte alignment)
-constexpr size_t kSmA = 1024 + kImgTb0 + kImgTb1 + kImgEnv + kOp64 + 2 * kOp128 + 4 * (kT + kT * NLM + kT * 16);
+constexpr size_t sm_a(bool split) {
+  return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
+         4 * (kT + kT * NLM + kT * EP);
+}
 constexpr size_t kSmB1 = 1024 + kImgEmb + 3 * kImgMix + kOp128 + kOpT + 4 * (kT * NLM + kSegCap * CL);
-constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * 16);
-constexpr size_t kSmC = 1024 + kImgLat0 + kImgLat1 + kImgE0 + kOpH + kOp128 + kOp64 + 4 * (5 * kT + kSegCap * CL);
+constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * EP);
+constexpr size_t sm_c(bool split) {
+  return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 + 4 * (5 * kT + kSegCap * CL);
+}
 constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 +
                           4 * (kT + 2 * kT * NLM + 2 * kT + kSegCap * CL);
 constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 +
-                          4 * (kT * NLM + kT * CL + 2 * kT * NLM + kSegCap * CL);
-constexpr size_t kSmAT = 1024 + kImgTb0 + kImgTb1 + kImgEnv + kOp64 + 2 * kOp128 + kOp64 +
-                         4 * (kT * 8 + kT * NB + 2 * kT * NLM + 2 * kT + kSegCap * CL);
-static_assert(kSmB1 + 4096 <= 232448 && kSmC + 4096 <= 232448 && kSmB2T + 4096 <= 232448 &&
-                  kSmB1T + 4096 <= 232448 && kSmAT + 4096 <= 232448, "smem (incl. static Meta)");
-static_assert(kOpH + kOp128 >= 4 * kT * CL, "pass C reuses HA + A1 for the dGamma contributions");
+                          4 * (kT * NLM + kT * CLP + 2 * kT * NLM + kSegCap * CL);
+constexpr size_t sm_at(bool split) {
+  return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
+         4 * (2 * kT * GP + 2 * kT * NLM + 2 * kT + kSegCap * CL);
+}
+// 4 KB left for the static Meta, barriers and flags of every kernel
+constexpr size_t kSmLimit = 232448 - 4096;
+static_assert(sm_a(true) <= kSmLimit && kSmB1 <= kSmLimit && kSmB2 <= kSmLimit && sm_c(true) <= kSmLimit &&
+                  kSmB2T <= kSmLimit && kSmB1T <= kSmLimit && sm_at(true) <= kSmLimit,
+              "shared memory per kernel");
+static_assert(kOpH + kOp128 >= 4 * kT * CLP, "pass C reuses HA + A1 for the dGamma contributions");
 
 int g_sms = 0;
 
-template <class Tin>
-void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
+template <class Tin, bool kSplit>
+void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km) {
+  constexpr size_t kSmA = sm_a(kSplit), kSmC = sm_c(kSplit), kSmAT = sm_at(kSplit);
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_bf_a<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
+    cudaFuncSetAttribute(k_bf_a<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
     cudaFuncSetAttribute(k_bf_b1<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1);
     cudaFuncSetAttribute(k_bf_b2<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
-    cudaFuncSetAttribute(k_bf_c<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
+    cudaFuncSetAttribute(k_bf_c<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
     cudaFuncSetAttribute(k_bf_b2t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2T);
     cudaFuncSetAttribute(k_bf_b1t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
-    cudaFuncSetAttribute(k_bf_at<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
+    cudaFuncSetAttribute(k_bf_at<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1198,25 +1312,27 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, c
   const int grid = (int)std::min<int64_t>(tiles, g_sms > 0 ? g_sms : 148);
   const int L = w.n_layers;
   auto mark = [&](int k) {
-    if (ev) cudaEventRecord(ev[k], s);
+    if (km) km->mark(k, s);
   };
-  mark(0);
-  k_bf_a<Tin><<<grid, kThr, kSmA, s>>>(w, b);
-  mark(1);
+  mark(kKStart);
+  k_bf_a<Tin, kSplit><<<grid, kThr, kSmA, s>>>(w, b);
+  mark(kKA);
   for (int k = 1; k < L; ++k) {
     k_bf_b1<Tin><<<grid, kThr, kSmB1, s>>>(w, b, k);
+    mark(kKB);
     k_bf_b2<Tin><<<grid, kThr, kSmB2, s>>>(w, b, k);
+    mark(kKB2);
   }
-  mark(2);
-  k_bf_c<Tin><<<grid, kThr, kSmC, s>>>(w, b);
-  mark(3);
+  k_bf_c<Tin, kSplit><<<grid, kThr, kSmC, s>>>(w, b);
+  mark(kKC);
   for (int k = L - 1; k >= 1; --k) {
     k_bf_b2t<Tin><<<grid, kThr, kSmB2T, s>>>(w, b, k);
+    mark(kKBT);
     k_bf_b1t<Tin><<<grid, kThr, kSmB1T, s>>>(w, b, k);
+    mark(kKBT2);
   }
-  mark(4);
-  k_bf_at<Tin><<<grid, kThr, kSmAT, s>>>(w, b);
-  mark(5);
+  k_bf_at<Tin, kSplit><<<grid, kThr, kSmAT, s>>>(w, b);
+  mark(kKAT);
 }
 
 }  // namespace
@@ -1227,10 +1343,13 @@ bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
 
 int bf16_tile() { return kT; }
 
-void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev,
-                        bool fp16) {
-  if (fp16) run_tc<__half>(w, b, capacity, s, ev);
-  else run_tc<__nv_bfloat16>(w, b, capacity, s, ev);
+void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km,
+                        TcMode mode) {
+  switch (mode) {
+    case TcMode::kBf16: run_tc<__nv_bfloat16, false>(w, b, capacity, s, km); break;
+    case TcMode::kFp16: run_tc<__half, false>(w, b, capacity, s, km); break;
+    case TcMode::kFp16Split: run_tc<__half, true>(w, b, capacity, s, km); break;
+  }
 }
 
 }  // namespace al

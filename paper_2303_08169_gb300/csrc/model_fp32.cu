@@ -1028,7 +1028,7 @@ struct Smem {
 };
 
 template <class Cf>
-void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
+void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km) {
   using Sm = Smem<Cf>;
   static bool init = false;
   if (!init) {
@@ -1042,19 +1042,23 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, c
   const int grid = (int)((capacity + kTile - 1) / kTile);
   const int L = w.n_layers;
   auto mark = [&](int k) {
-    if (ev) cudaEventRecord(ev[k], s);
+    if (km) km->mark(k, s);
   };
-  mark(0);
+  mark(kKStart);
   k_pass_a<Cf><<<grid, kThreads, Sm::a, s>>>(w, b);
-  mark(1);
-  for (int k = 1; k < L; ++k) k_pass_b<Cf><<<grid, kThreads, Sm::b, s>>>(w, b, k);
-  mark(2);
+  mark(kKA);
+  for (int k = 1; k < L; ++k) {
+    k_pass_b<Cf><<<grid, kThreads, Sm::b, s>>>(w, b, k);
+    mark(kKB);
+  }
   k_pass_c<Cf><<<grid, kThreads, Sm::c, s>>>(w, b);
-  mark(3);
-  for (int k = L - 1; k >= 1; --k) k_pass_b_bwd<Cf><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
-  mark(4);
+  mark(kKC);
+  for (int k = L - 1; k >= 1; --k) {
+    k_pass_b_bwd<Cf><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
+    mark(kKBT);
+  }
   k_pass_a_bwd<Cf><<<grid, kThreads, Sm::ab, s>>>(w, b);
-  mark(5);
+  mark(kKAT);
 }
 
 using CfgTiny = Cfg<1, 8, 32, 32>;
@@ -1069,9 +1073,9 @@ bool fp32_supported(int lmax, int C, int D, int E) {
 }
 
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
-                        int64_t capacity, cudaStream_t s, cudaEvent_t* ev) {
-  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s, ev);
-  else run<CfgMain>(w, b, capacity, s, ev);
+                        int64_t capacity, cudaStream_t s, KernelMarks* km) {
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s, km);
+  else run<CfgMain>(w, b, capacity, s, km);
 }
 
 }  // namespace al
