@@ -4,17 +4,28 @@
 One step = neighbour-list rebuild (no skin) + energy + forces (forward pair
 passes, FP64 energy reduction, hand-written adjoint) + FP64 velocity-Verlet
 update + per-step >5 sigma outlier count, replayed as a captured CUDA graph.
-Workloads (synthetic liquid ammonia at 0.68 g/cm^3, seeded Gaussian weights):
-  fp32_6912   6,912 atoms (1,728 NH3), 2 layers, l_max 2, 16 channels,
-              latent [128, 128], energy [32], r_cut 5 A, dt 0.25 fs, FP32 path.
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
-the host cores on a bounded sample of the same workload.
+Synthetic liquid ammonia at 0.68 g/cm^3 and seeded Gaussian weights of the
+2-layer, l_max 2, 16-channel, latent [128, 128], energy [32], r_cut 5 A model;
+dt 0.25 fs from 200 K.  Workloads:
+  tc_110592    110,592 atoms (27,648 NH3), tensor-core path, FP16 operands
+               with split (hi + lo) two-body and energy-hidden GEMMs: the
+               mixed-precision mode that meets the 2e-3 eV/A force bound
+               (headline, the default)
+  bf16_110592  same, BF16 operands throughout
+  fp16_110592  same, FP16 operands throughout
+  fp32_6912    6,912 atoms (1,728 NH3), every per-pair GEMM in FP32
+Prints one JSON line (rank 0): the headline workload timed over --steps, the
+other paths timed over min(--steps, 200) steps under "paths", each path's
+force error against the FP64 oracle on the 6,912-atom cell, per-kernel
+device times and the roofline of the dominant kernel.  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded sample.
 Multi-GPU: independent replicas, one per rank (no data-path collective).
 """
 import argparse
+import hashlib
 import json
-import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -26,26 +37,50 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "MD atom-steps/s on 1 GB300 (E+F), BF16 vs FP32 path at stated force error"
 KB_T200 = 8.617333e-5 * 200.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FORCE_BOUND = 2e-3                                   # eV/A, max |dF| of the mixed-precision path
 
-# Algorithmic multiply-adds per pair of each pass for the 2-layer l_max 2
-# model (D 128, C 16, E 32; 11 coupling paths, 83 CG terms per channel).  Each
-# model operation is counted once forward and once in its adjoint (input
-# gradients only); the forward recomputed inside the adjoint passes is not.
-ALG_MAC_PER_PAIR = {
-    "pass_a": 1536 + 16384 + 2048 + 144,                        # two-body, env1, scatter
-    "pass_b": 6144 + 1328 + 8960 + 22528 + 16384 + 2048 + 144,  # embed, TP, mix, latent, env2
-    "pass_c": (144 + 22528 + 16384 + 4096 + 32) * 2,            # layer 2 + energy, fwd + adjoint
+# Algorithmic multiply-adds per pair of each pass kernel for the 2-layer
+# l_max 2 model (D 128, C 16, E 32; 11 coupling paths, 83 CG terms per
+# channel).  Each model operation is counted once forward and once in its
+# adjoint (input gradients only); forward work recomputed inside an adjoint
+# kernel is not counted.
+#   GEMM: per-pair dense products (tensor cores on the tensor-core path)
+GEMM_MAC_PER_PAIR = {
+    "pass_a": 1536 + 16384 + 2048,                        # two-body 12->128->128, env1 128->16
+    "pass_b1": 6144 + 8960,                               # embedding 128->48, mixing
+    "pass_b2": 22528 + 16384 + 2048,                      # latent 176->128->128, env2
+    "pass_c": 2 * (22528 + 16384 + 4096),                 # latent + energy hidden, fwd + adjoint
+    "pass_b2_adjoint": 2048 + 16384 + 22528,
+    "pass_b1_adjoint": 8960 + 6144,
+    "pass_a_adjoint": 2048 + 16384 + 1536,
+}
+#   all multiply-adds incl. tensor products, scatters, energy output (FP32 path)
+ALL_MAC_PER_PAIR = {
+    "pass_a": 1536 + 16384 + 2048 + 144,
+    "pass_b": 6144 + 1328 + 8960 + 22528 + 16384 + 2048 + 144,
+    "pass_c": (144 + 22528 + 16384 + 4096 + 32) * 2,
     "pass_b_adjoint": 288 + 2048 + 16384 + 22528 + 8960 + 2656 + 6144 + 288,
     "pass_a_adjoint": 288 + 2048 + 16384 + 1536,
 }
+TC_KERNELS = {"pass_a": "k_bf_a", "pass_b1": "k_bf_b1", "pass_b2": "k_bf_b2", "pass_c": "k_bf_c",
+              "pass_b2_adjoint": "k_bf_b2t", "pass_b1_adjoint": "k_bf_b1t", "pass_a_adjoint": "k_bf_at"}
+FP32_KERNELS = {"pass_a": "k_pass_a", "pass_b": "k_pass_b", "pass_c": "k_pass_c",
+                "pass_b_adjoint": "k_pass_b_bwd", "pass_a_adjoint": "k_pass_a_bwd"}
 
 WORKLOADS = {
-    "fp32_6912": dict(n_mol=1728, precision=0, dt=0.25, model="main", dtype="f32"),
-    "bf16_110592": dict(n_mol=27648, precision=1, dt=0.25, model="main", dtype="bf16"),
-    "bf16_6912": dict(n_mol=1728, precision=1, dt=0.25, model="main", dtype="bf16"),
+    "tc_110592": dict(n_mol=27648, precision=3, dt=0.25,
+                      dtype="f16 operands (two-body and energy-hidden GEMMs split hi+lo), f32 accumulate"),
+    "bf16_110592": dict(n_mol=27648, precision=1, dt=0.25, dtype="bf16 operands, f32 accumulate"),
+    "fp16_110592": dict(n_mol=27648, precision=2, dt=0.25, dtype="f16 operands, f32 accumulate"),
+    "fp32_6912": dict(n_mol=1728, precision=0, dt=0.25, dtype="f32"),
+    "tc_6912": dict(n_mol=1728, precision=3, dt=0.25,
+                    dtype="f16 operands (two-body and energy-hidden GEMMs split hi+lo), f32 accumulate"),
 }
+SECONDARY = ["bf16_110592", "fp16_110592", "fp32_6912"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tc_110592_kernels.md")
 
 
 def _env_int(name, default):
@@ -53,6 +88,14 @@ def _env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 class ClockSampler:
@@ -102,42 +145,68 @@ def _energy_scale(name):
         return json.load(f)[name]["sigma"]
 
 
-def _workload(name):
+def _model():
     import synth
-    w = WORKLOADS[name]
-    cfg = synth.MAIN if w["model"] == "main" else synth.TINY
-    blob = synth.make_blob(cfg, 42, sigma=_energy_scale(w["model"]))
-    pos, sp, cell = synth.make_ammonia(w["n_mol"], 0)
+    cfg = synth.MAIN
+    return cfg, synth.make_blob(cfg, 42, sigma=_energy_scale("main"))
+
+
+def _system(n_mol):
+    import synth
+    pos, sp, cell = synth.make_ammonia(n_mol, 0)
     vel = synth.make_velocities(sp, 200.0, 1)
-    return w, cfg, blob, pos, sp, cell, vel
+    return pos, sp, cell, vel
 
 
-def cpu_baseline(name, max_seconds=30.0):
-    """FP64 oracle on the host cores: velocity-Verlet steps of the full
-    workload until max_seconds of CPU work (at least one step)."""
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2303_08169_gb300", "csrc", "model_bf16.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(kernel):
+    """DRAM bytes per pair of one kernel from the committed ncu summary, or
+    None when the summary is missing or the kernel source changed since."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != _kernel_source_hash():
+        return None
+    m = re.search(rf"dram_bytes_per_pair\.{kernel}:\s*([0-9.eE+-]+)", text)
+    return float(m.group(1)) if m else None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(max_seconds=30.0):
+    """FP64 oracle on the host cores: velocity-Verlet steps of the 6,912-atom
+    cell of the same generator until max_seconds of CPU work (1 to 3 steps).
+    Also returns the oracle forces at the initial positions."""
     import torch
+    import synth
     from oracle.md import velocity_verlet
     from oracle.model import OracleModel
     torch.set_num_threads(os.cpu_count() or 1)
-    w, cfg, blob, pos, sp, cell, vel = _workload(name)
+    cfg, blob = _model()
+    pos, sp, cell, vel = _system(1728)
     orc = OracleModel(blob)
     L = np.diag(cell)
-    import synth
     f = lambda p: orc.energy_forces(p, sp, L)[:2]      # noqa: E731
     t0 = time.perf_counter()
-    f(pos)                                               # initial forces (not counted)
+    E0, F0 = f(pos)                                      # initial forces (not counted)
     t1 = time.perf_counter()
-    steps = max(1, int(max_seconds // max(t1 - t0, 1e-3)) - 1)
-    steps = min(steps, 3)
+    steps = min(3, max(1, int(max_seconds // max(t1 - t0, 1e-3)) - 1))
     t2 = time.perf_counter()
-    velocity_verlet(f, pos, vel, synth.MASS_AMU[sp], L, w["dt"], steps)
+    velocity_verlet(f, pos, vel, synth.MASS_AMU[sp], L, 0.25, steps)
     t3 = time.perf_counter()
-    # velocity_verlet evaluates forces once up front and once per step
-    per_step = (t3 - t2) / (steps + 1)
-    return {"value": len(sp) / per_step, "unit": "atom-steps/s", "cores": torch.get_num_threads(),
+    per_step = (t3 - t2) / (steps + 1)                  # one force call up front + one per step
+    base = {"value": len(sp) / per_step, "unit": "atom-steps/s", "cores": torch.get_num_threads(),
             "kind": "oracle",
-            "sample": f"{steps} FP64 velocity-Verlet step(s) of the full {len(sp)}-atom workload "
-                      f"(torch-CPU float64 + autograd forces), {per_step:.2f} s/step"}
+            "sample": f"{steps} FP64 velocity-Verlet step(s) of the {len(sp)}-atom cell of the same "
+                      f"generator and model (torch-CPU float64 + autograd forces), {per_step:.2f} s/step"}
+    return base, (pos, sp, cell, E0, F0)
 
 
 def run_reference(args):
@@ -146,14 +215,14 @@ def run_reference(args):
     if rank != 0:
         return 0
     import torch
+    import synth
     from oracle.md import velocity_verlet
     from oracle.model import OracleModel
-    import synth
     torch.set_num_threads(os.cpu_count() or 1)
-    w, cfg, blob, _, _, _, _ = _workload(args.config)
-    # bounded sample: 432 atoms (108 NH3) of the same generator and density
-    pos, sp, cell = synth.make_ammonia(108, 0)
-    vel = synth.make_velocities(sp, 200.0, 1)
+    w = WORKLOADS[args.config]
+    cfg, blob = _model()
+    # bounded sample: 432 atoms (108 NH3) of the same generator, density and model
+    pos, sp, cell, vel = _system(108)
     L = np.diag(cell)
     orc = OracleModel(blob)
     f = lambda p: orc.energy_forces(p, sp, L)[:2]      # noqa: E731
@@ -167,7 +236,7 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = len(sp) * steps / el
     line = {
-        "impl": "reference", "metric": "MD atom-steps/s on 1 GB300 (E+F)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "atom-steps/s", "n_gpus": 0, "steps": steps, "steps_requested": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -182,6 +251,116 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+class Runner:
+    def __init__(self, al, torch, dev, blob, cfg):
+        self.al, self.torch, self.dev = al, torch, dev
+        self.ctx = al.allegro_create(blob, np.array([14.007, 1.008]), cfg.r_cut, cfg.l_max, cfg.n_layers)
+        self.stream = torch.cuda.Stream(device=dev)
+        al.allegro_set_stream(self.ctx, self.stream)
+
+    def md(self, name, K, W, clocks=None, barrier=None):
+        """K graph-captured MD steps after W warm-up steps; returns a dict."""
+        al, torch, dev = self.al, self.torch, self.dev
+        w = WORKLOADS[name]
+        pos, sp, cell, vel = _system(w["n_mol"])
+        al.allegro_set_md_precision(self.ctx, w["precision"])
+        al.allegro_md_init(self.ctx, torch.tensor(pos, device=dev), torch.tensor(vel, device=dev),
+                           torch.tensor(sp, device=dev, dtype=torch.int32), cell)
+        outl = torch.zeros(K, dtype=torch.int64, device=dev)
+        ener = torch.zeros((K, 3), dtype=torch.float64, device=dev)
+        al.allegro_md_step_nve(self.ctx, w["dt"], W)        # graph capture + warm-up
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+        ev0.record(self.stream)
+        al.allegro_md_step_nve(self.ctx, w["dt"], K, outl, ener)
+        ev1.record(self.stream)
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+        clk = clocks.stop() if clocks else None
+        ms = ev0.elapsed_time(ev1)
+        en = ener.cpu().numpy()
+        N = len(sp)
+        return {"ms": ms, "N": N, "K": K, "clocks": clk,
+                "n_pairs": al.allegro_query(self.ctx, al.ALLEGRO_Q_N_PAIRS),
+                "step_kernels": al.allegro_query(self.ctx, al.ALLEGRO_Q_STEP_KERNELS),
+                "drift": float(np.abs(en[:, 2] - en[0, 2]).max() / (N * KB_T200)),
+                "outliers_last": int(outl[-1].item()), "outliers_max": int(outl.max().item()),
+                "pos": pos, "sp": sp, "cell": cell}
+
+    def phases(self, n_reps=20):
+        """Per-kernel device times at the current MD state (CUDA events on
+        the library stream) and the pair count of that state."""
+        ph = self.al.allegro_phase_times(self.ctx, n_reps)
+        return ph, self.al.allegro_query(self.ctx, self.al.ALLEGRO_Q_N_PAIRS)
+
+    def forces(self, pos, sp, cell, precision):
+        al, torch, dev = self.al, self.torch, self.dev
+        F = torch.empty((len(pos), 3), dtype=torch.float32, device=dev)
+        E = al.allegro_energy_forces(self.ctx, torch.tensor(pos, device=dev),
+                                     torch.tensor(sp, device=dev, dtype=torch.int32), cell, F, None, precision)
+        return E, F.cpu().numpy().astype(np.float64)
+
+    def e2e(self, name, n_iter):
+        """energy+forces through the C ABI from pinned host positions to
+        pinned host forces, wall-clock per call (H2D, rebuild, passes, D2H)."""
+        al, torch = self.al, self.torch
+        w = WORKLOADS[name]
+        pos, sp, cell, _ = _system(w["n_mol"])
+        pos_h = torch.tensor(pos, dtype=torch.float64).pin_memory()
+        sp_h = torch.tensor(sp, dtype=torch.int32).pin_memory()
+        F_h = torch.empty((len(sp), 3), dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            al.allegro_energy_forces(self.ctx, pos_h, sp_h, cell, F_h, None, w["precision"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_iter):
+            al.allegro_energy_forces(self.ctx, pos_h, sp_h, cell, F_h, None, w["precision"])
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / n_iter
+        return {"value": len(sp) / dt, "unit": "atom-steps/s",
+                "h2d_bytes_per_step": 24 * len(sp) + 4 * len(sp), "d2h_bytes_per_step": 12 * len(sp) + 8,
+                "ms_per_call": 1e3 * dt,
+                "note": "allegro_energy_forces (one E+F step) with pinned host positions and species in "
+                        "and host forces and energy out, wall clock"}
+
+    def close(self):
+        self.al.allegro_destroy(self.ctx)
+
+
+def roofline(phases, n_pairs, tensor_path, peaks):
+    if tensor_path:
+        times = {k: phases[k] for k in GEMM_MAC_PER_PAIR}
+        dom = max(times, key=times.get)
+        flops = 2.0 * GEMM_MAC_PER_PAIR[dom] * n_pairs
+        peak = peaks.get("bf16_tflops")
+        src = "measured bf16 dense burst (kind::f16 runs FP16 at the BF16 rate), MEASURED_PEAKS.json"
+        if peak is None:
+            peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
+        traffic = _profile_traffic(TC_KERNELS[dom])
+        traffic = None if traffic is None else traffic * n_pairs
+        achieved = flops / (times[dom] * 1e-3) / 1e12
+        return {"bound": "tensor", "kernel": TC_KERNELS[dom], "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_flops_per_launch": flops, "launch_ms": times[dom], "peak_source": src,
+                "frac_label": "of measured"}
+    times = {k: phases[k] for k in ALL_MAC_PER_PAIR}
+    dom = max(times, key=times.get)
+    flops = 2.0 * ALL_MAC_PER_PAIR[dom] * n_pairs
+    achieved = flops / (times[dom] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": FP32_KERNELS[dom], "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "algorithmic_flops_per_launch": flops, "launch_ms": times[dom],
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "frac_label": "of derived"}
+
+
 def run_ours(args):
     import torch
     import paper_2303_08169_gb300 as al
@@ -190,84 +369,59 @@ def run_ours(args):
     world = _env_int("WORLD_SIZE", 1)
     local = _env_int("LOCAL_RANK", 0)
     dist = None
+    torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w, cfg, blob, pos, sp, cell, vel = _workload(args.config)
-    N = len(sp)
-    ctx = al.allegro_create(blob, np.array([14.007, 1.008]), cfg.r_cut, cfg.l_max, cfg.n_layers)
-    stream = torch.cuda.Stream(device=dev)
-    al.allegro_set_stream(ctx, stream)
-    al.allegro_set_md_precision(ctx, w["precision"])
-    pos_d = torch.tensor(pos, device=dev)
-    vel_d = torch.tensor(vel, device=dev)
-    sp_d = torch.tensor(sp, device=dev, dtype=torch.int32)
-    al.allegro_md_init(ctx, pos_d, vel_d, sp_d, cell)
+    barrier = dist.barrier if dist else None
+    cfg, blob = _model()
+    run = Runner(al, torch, dev, blob, cfg)
     K, W = args.steps, args.warmup
-    outl = torch.zeros(K, dtype=torch.int64, device=dev)
-    ener = torch.zeros((K, 3), dtype=torch.float64, device=dev)
-    al.allegro_md_step_nve(ctx, w["dt"], W)                 # graph capture + warm-up
-    n_pairs = al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS)
-    step_kernels = al.allegro_query(ctx, al.ALLEGRO_Q_STEP_KERNELS)
-    clocks = ClockSampler(local)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    al.allegro_md_step_nve(ctx, w["dt"], K, outl, ener)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    w = WORKLOADS[args.config]
+    tensor_path = w["precision"] != 0
+
+    head = run.md(args.config, K, W, ClockSampler(local), barrier)
+    ms = head["ms"]
     if dist:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    en = ener.cpu().numpy()
-    drift = float(np.abs(en[:, 2] - en[0, 2]).max() / (N * KB_T200))
-    outliers = outl.cpu().numpy()
+    phases, n_pairs_ph = run.phases()
+    roof = roofline(phases, n_pairs_ph, tensor_path, _measured_peaks())
 
-    # per-kernel device times (CUDA events on the library stream) at the final state
-    phases = al.allegro_phase_times(ctx, 20)
-    dom = max(ALG_MAC_PER_PAIR, key=lambda k: phases[k])
-    achieved = 2.0 * ALG_MAC_PER_PAIR[dom] * n_pairs / (phases[dom] * 1e-3) / 1e12
-
-    # end to end: energy+forces through the C ABI from pinned host positions to
-    # pinned host forces (H2D + rebuild + passes + D2H inside the timed region)
-    pos_h = torch.tensor(pos, dtype=torch.float64).pin_memory()
-    F_h = torch.empty((N, 3), dtype=torch.float32).pin_memory()
-    for _ in range(3):
-        al.allegro_energy_forces(ctx, pos_h, sp_d, cell, F_h, None, w["precision"])
-    n_e2e = max(10, min(K, 200))
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(n_e2e):
-        al.allegro_energy_forces(ctx, pos_h, sp_d, cell, F_h, None, w["precision"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
-
+    paths = {}
+    accuracy = {}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.config)
-    al.allegro_destroy(ctx)
+    if not args.only_headline:
+        e2e = run.e2e(args.config, max(10, min(K, 100)))
+        K2 = min(K, 200)
+        for name in [args.config] + [s for s in SECONDARY if s != args.config]:
+            r = head if name == args.config else run.md(name, K2, W)
+            paths[name] = {"value": r["N"] * r["K"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / r["K"],
+                           "atoms": r["N"], "pairs": r["n_pairs"], "steps": r["K"], "dtype": WORKLOADS[name]["dtype"]}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu, (pos, sp, cell, E0, F0) = cpu_baseline()
+            # force error of every path against the FP64 oracle on the 6,912-atom cell
+            for name in paths:
+                prec = WORKLOADS[name]["precision"]
+                E, F = run.forces(pos, sp, cell, prec)
+                d = F - F0
+                accuracy[name] = {"max_abs_dF": float(np.abs(d).max()), "rms_dF": float(np.sqrt(np.mean(d * d))),
+                                  "abs_dE_per_atom": abs(E - E0) / len(sp)}
+            for name, acc in accuracy.items():
+                paths[name]["max_abs_dF_eV_per_A"] = acc["max_abs_dF"]
+                paths[name]["rms_dF_eV_per_A"] = acc["rms_dF"]
+    else:
+        e2e = None
+    run.close()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
+    N = head["N"]
     line = {
-        "metric": "MD atom-steps/s on 1 GB300 (E+F), BF16 vs FP32 path at stated force error",
+        "metric": METRIC,
         "value": world * N * K / (ms * 1e-3),
         "unit": "atom-steps/s",
         "n_gpus": world,
@@ -279,21 +433,23 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": w["dtype"],
         "data": "synthetic",
-        "config": {"workload": args.config, "atoms": N, "pairs": n_pairs, "dt_fs": w["dt"],
-                   "l2": "working set above L2 (per-pair state ~1 GB per step)",
+        "config": {"workload": args.config, "atoms": N, "pairs": head["n_pairs"], "dt_fs": w["dt"],
+                   "l2": "inputs larger than L2 (per-pair state of ~6 GB per step at 110,592 atoms)",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": N / (e2e_ms * 1e-3), "unit": "atom-steps/s",
-                "h2d_bytes_per_step": 24 * N, "d2h_bytes_per_step": 12 * N + 8,
-                "note": "allegro_energy_forces with pinned host positions in and host forces out"},
-        "gpu_launches": int(step_kernels * K),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
-        "phases_ms": phases,
-        "physics": {"energy_drift_over_NkT": drift, "outliers_last": int(outliers[-1]),
-                    "outliers_max": int(outliers.max())},
-        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": int(head["step_kernels"] * K),
+        "roofline": roof,
+        "kernel_ms": {k: round(v, 4) for k, v in phases.items()},
+        "physics": {"energy_drift_over_NkT": head["drift"], "outliers_last": head["outliers_last"],
+                    "outliers_max": head["outliers_max"]},
+        "clocks": head["clocks"],
     }
+    if paths:
+        line["paths"] = paths
+    if accuracy:
+        line["accuracy_vs_fp64_oracle_6912"] = {
+            "bound_max_abs_dF": FORCE_BOUND, "headline_within_bound": accuracy[args.config]["max_abs_dF"] <= FORCE_BOUND
+            if args.config in accuracy else None, **accuracy}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -308,8 +464,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="fp32_6912", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="tc_110592", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline workload only (no other paths, e2e, accuracy or CPU baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

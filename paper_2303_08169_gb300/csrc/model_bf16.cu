@@ -518,28 +518,41 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       tmem_ld16(lanes(tmem) + 24 * h, w0);
       tmem_ld16(lanes(tmem) + 24 * h + 16, w0 + 16);
     }
-    const int i = m.pi[r];
-    for (int cc = 0; cc < 8; ++cc) {
-      const int c = 8 * h + cc;
-      float V[NLM], G[NLM], Tv[TP2_NT];
-      if (k == 1) {
+    // channel pairs: for l3 >= 1 the P_l = 4 paths of channels c, c + 1 fill
+    // one 16-byte chunk of a mixing K-slice; the l3 = 0 slice (P_0 = 3) is
+    // written per element
+    for (int cc = 0; cc < 8; cc += 2) {
+      float Tv[2][TP2_NT];
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[cc * 3 + l_of(lm)] * s_Y[r * NLM + lm];
-      } else {
+      for (int e = 0; e < 2; ++e) {
+        const int c = 8 * h + cc + e;
+        float V[NLM], G[NLM];
+        if (k == 1) {
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[(cc + e) * 3 + l_of(lm)] * s_Y[r * NLM + lm];
+        } else {
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+        }
+        get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
+        tp2_fwd(V, G, Tv[e]);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) st1<Tin>(T, r, c * NS + q, Tv[e][q]);
+        if (valid)
+#pragma unroll
+          for (int q = 0; q < NS; ++q) b.S[k][sidx(m, C * NS, c * NS + q, r)] = Tv[e][q];
       }
-      get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
-      tp2_fwd(V, G, Tv);
+      const int c0 = 8 * h + cc;
 #pragma unroll
-      for (int j = 0; j < 9; ++j) {
-        const int l3 = l_of(j), mm3 = j - l3 * l3, Pl = tp2_P(l3), nm = 2 * l3 + 1;
+      for (int j = 1; j < 9; ++j) {
+        const int l3 = l_of(j), mm3 = j - l3 * l3, nm = 2 * l3 + 1;
+        float v8[8];
 #pragma unroll
-        for (int q = 0; q < Pl; ++q) st1<Tin>(T, r, kSlice[j] + c * Pl + q, Tv[tp2_toff(l3) + q * nm + mm3]);
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v8[4 * e + q] = Tv[e][tp2_toff(l3) + q * nm + mm3];
+        st8<Tin>(T, sw128_off(r, kSlice[j] + c0 * 4, 128), v8);
       }
-      if (valid)
-#pragma unroll
-        for (int q = 0; q < NS; ++q) b.S[k][sidx(m, C * NS, c * NS + q, r)] = Tv[q];
     }
     mm.run([&] {
       for (int j = 0; j < 9; ++j) {
@@ -679,15 +692,19 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
     }
     stage_g(b.gam[L], b.row_ptr, m, s_g);
     __syncthreads();
-    for (int cc = 0; cc < 8; ++cc) {
-      const int c = 8 * h + cc;
-      float V[NLM], G[NLM], S[NS];
+    {
+      float S[8 * NS];                                 // columns D + 24 h .. D + 24 h + 23: three chunks
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
-      get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
-      tp2_fwd_scalar(V, G, S);
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = 8 * h + cc;
+        float V[NLM], G[NLM];
 #pragma unroll
-      for (int q = 0; q < NS; ++q) st1<Tin>(HA, r, D + c * NS + q, S[q]);
+        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+        get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
+        tp2_fwd_scalar(V, G, S + cc * NS);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) st8<Tin>(HA, sw128_off(r, D + 24 * h + 8 * q, 128), S + 8 * q);
     }
     const float* xg = b.X[L - 1];
     row_to_op<Tin>(HA, m, r, xg, D, 64 * h, valid, 64 * h, 64);
@@ -981,9 +998,14 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    for (int co = 8 * h; co < 8 * h + 8; ++co)
+    // column 16 lm + co: this thread's 8 channels of one lm are one 16-byte chunk
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) st1<Tin>(DVT, r, 16 * lm + co, valid ? b.dV[sidx(m, CL, co * NLM + lm, r)] : 0.0f);
+    for (int lm = 0; lm < NLM; ++lm) {
+      float v8[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v8[q] = valid ? b.dV[sidx(m, CL, (8 * h + q) * NLM + lm, r)] : 0.0f;
+      st8<Tin>(DVT, sw128_off(r, 16 * lm + 8 * h, 128), v8);
+    }
     stage_g(b.gam[k], b.row_ptr, m, s_g);
     if (k == 1) {
       row_to_op<Tin>(X, m, r, b.X[0], D, 64 * h, valid, 64 * h, 64);
