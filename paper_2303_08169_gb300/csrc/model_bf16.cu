@@ -33,7 +33,8 @@ namespace {
 using namespace umma;
 
 constexpr int kT = 128;
-constexpr int kThr = 256;
+constexpr int kThr = 256;    // threads of a CTA: row r = t % 128, column half t / 128
+constexpr int kThr4 = 512;   // kernels with four column quarters per row (more warps per SM)
 constexpr int D = 128, C = 16, E = 32, NLM = 9, NS = 3, KH = 176, NW0 = 48, CL = 144, NB = 8;
 constexpr float kR2 = 0.70710678118654752f;
 // odd row strides of per-row shared arrays (32 consecutive rows hit 32 banks)
@@ -153,7 +154,7 @@ AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
 // part[(tile + atom) * W + x] = sum over the segment's pairs of f(p, x)
 template <class F>
 AL_DEV void seg_store(float* __restrict__ part, const Meta& m, int W, F&& f) {
-  for (int idx = threadIdx.x; idx < m.nseg * W; idx += kThr) {
+  for (int idx = threadIdx.x; idx < m.nseg * W; idx += blockDim.x) {
     const int s = idx / W, x = idx % W;
     float acc = 0.0f;
     for (int p = m.sstart[s]; p < m.sstart[s + 1]; ++p) acc += f(p, x);
@@ -183,7 +184,7 @@ AL_DEV size_t sidx(const Meta& m, int W, int f, int r) { return ((size_t)m.tile 
 constexpr int kSegCap = 8;
 AL_DEV void stage_g(const float* __restrict__ part, const int* __restrict__ row_ptr, const Meta& m, float* s) {
   const int ns = min(m.nseg, kSegCap);
-  for (int idx = threadIdx.x; idx < ns * CL; idx += kThr) {
+  for (int idx = threadIdx.x; idx < ns * CL; idx += blockDim.x) {
     const int sg = idx / CL, x = idx % CL;
     const int i = m.atom[sg];
     const int t0 = row_ptr[i] / kT, t1 = (row_ptr[i + 1] - 1) / kT;
@@ -268,13 +269,15 @@ struct Mma {
 
 AL_DEV uint32_t lanes(uint32_t tmem) { return tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16); }
 
-// thread (r, h) visits columns [h N/2, (h+1) N/2) of an N-wide accumulator at
-// TMEM column col0, 16 at a time: f(r, n0, v[16])
+// thread (r, h) of a CTA with nq = blockDim / 128 column groups visits
+// columns [h N/nq, (h+1) N/nq) of an N-wide accumulator at TMEM column col0,
+// 16 at a time: f(r, n0, v[16])
 template <class F>
 AL_DEV void epi(uint32_t tmem, int col0, int N, F&& f) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  const int w = N / (int)(blockDim.x >> 7);
   const uint32_t base = lanes(tmem);
-  for (int n0 = h * (N / 2); n0 < (h + 1) * (N / 2); n0 += 16) {
+  for (int n0 = h * w; n0 < (h + 1) * w; n0 += 16) {
     float v[16];
     tmem_ld16(base + (uint32_t)(col0 + n0), v);
     f(r, n0, v);
@@ -650,11 +653,14 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 // ============================================================================
 // Pass C: last layer + energy MLP forward, dE/dE_ij = sigma_Z, and their
 // adjoint: dx^{L-1}, dV^{L-1}, dGamma^L partials, du, energy partials.
+// 512 threads: thread (r, h) owns tile row r and column quarter h of every
+// epilogue, channels 4h..4h+3 of the tensor products and energy hidden units
+// 8h..8h+7.
 // Split mode: the energy hidden layer takes split operands; the lo part of
 // x^L goes to A1 (free after the second latent MMA) and dz_E keeps its hi and
 // lo parts side by side in the 64 columns of AE.
 template <class Tin, bool kSplit>
-__global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   const int L = w.n_layers;
   BF_PROLOGUE(kImgLat0 + kImgLat1 + (kSplit ? 2 : 1) * kImgE0, {
     bulk_g2s(sm, w.lat0[L - 1], kImgLat0, &bars[1]);
@@ -672,31 +678,26 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
   float* s_dg = reinterpret_cast<float*>(HA);          // reuses HA + A1 after the last MMA
   float* s_fc = reinterpret_cast<float*>(AE + kOp64);
   float* s_sig = s_fc + kT;
-  float* s_eij = s_sig + kT;
-  float* s_du = s_eij + kT;                            // [2][kT]
-  float* s_g = s_du + 2 * kT;                          // [kSegCap][CL]
+  float* s_eq = s_sig + kT;                            // [4][kT] energy partials per quarter
+  float* s_du = s_eq + 4 * kT;                         // [4][kT]
+  float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     const bool valid = r < m.np;
-    float Y[NLM];
-    {
-      float u[3], d, fc = 0.0f, dfc;
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    if (h == 0) {
+      float u[3], d, fc = 0.0f, dfc, Y[NLM];
       if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
-      if (h == 0) {
-        s_fc[r] = fc;
-        s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
-      }
+      s_fc[r] = fc;
+      s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
     }
     stage_g(b.gam[L], b.row_ptr, m, s_g);
     __syncthreads();
     {
-      float S[8 * NS];                                 // columns D + 24 h .. D + 24 h + 23: three chunks
+      float S[4 * NS];                                 // columns D + 12 h .. D + 12 h + 11
 #pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
-        const int c = 8 * h + cc;
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * h + cc;
         float V[NLM], G[NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
@@ -704,11 +705,11 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         tp2_fwd_scalar(V, G, S + cc * NS);
       }
 #pragma unroll
-      for (int q = 0; q < 3; ++q) st8<Tin>(HA, sw128_off(r, D + 24 * h + 8 * q, 128), S + 8 * q);
+      for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
     }
     const float* xg = b.X[L - 1];
-    row_to_op<Tin>(HA, m, r, xg, D, 64 * h, valid, 64 * h, 64);
-    if (h == 1) {
+    row_to_op<Tin>(HA, m, r, xg, D, 32 * h, valid, 32 * h, 32);
+    if (h == 3) {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
     }
@@ -731,33 +732,29 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
       st16_op<Tin, kSplit>(HA, A1, rr, n0, o);
     });
     mm.run([&] { mma_split<Tin, kSplit>(tmem + 256, HA, A1, We0, We0lo, 32, 8, false, 0); });
-    if (threadIdx.x < kT) {
-      float ze[32];
-      tmem_ld16(lanes(tmem) + 256, ze);
-      tmem_ld16(lanes(tmem) + 272, ze + 16);
+    {
+      float ze[8], dz[8];
+      tmem_ld8(lanes(tmem) + 256 + 8 * h, ze);
       const float sig = s_sig[r];
-      float e = 0.0f, dz[32];
+      float e = 0.0f;
 #pragma unroll
-      for (int n = 0; n < E; ++n) {
-        const float wo = __ldg(w.eout + n);
+      for (int n = 0; n < 8; ++n) {
+        const float wo = __ldg(w.eout + 8 * h + n);
         e = fmaf(wo, silu_b(ze[n]), e);
         dz[n] = sig * wo * dsilu_b(ze[n]);
       }
-      s_eij[r] = valid ? e : 0.0f;
+      s_eq[h * kT + r] = valid ? e : 0.0f;
       if (kSplit) {                                   // hi in columns 0..31, lo in 32..63
-        float hi[32], lo[32];
+        float hi[8], lo[8];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < 8; ++q) {
           hi[q] = Op<Tin>::round(dz[q]);
           lo[q] = dz[q] - hi[q];
         }
-        st16<Tin>(AE, r, 0, hi);
-        st16<Tin>(AE, r, 16, hi + 16);
-        st16<Tin>(AE, r, 32, lo);
-        st16<Tin>(AE, r, 48, lo + 16);
+        st8<Tin>(AE, sw128_off(r, 8 * h, 128), hi);
+        st8<Tin>(AE, sw128_off(r, 32 + 8 * h, 128), lo);
       } else {
-        st16<Tin>(AE, r, 0, dz);
-        st16<Tin>(AE, r, 16, dz + 16);
+        st8<Tin>(AE, sw128_off(r, 8 * h, 128), dz);
       }
     }
     mm.run([&] {                                                                // dx^L
@@ -799,11 +796,11 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
         for (int q = 0; q < 16; ++q) b.dX[sidx(m, D, n0 + q, rr)] = dh[q] + dx[q] * kR2;
     });
     {
-      float ds[32];
-      tmem_ld16(lanes(tmem) + 128 + 24 * h, ds);
-      tmem_ld16(lanes(tmem) + 128 + 24 * h + 16, ds + 16);
-      for (int cc = 0; cc < 8; ++cc) {
-        const int c = 8 * h + cc;
+      float ds[16];                                    // columns D + 12 h ..: ds of channels 4h..4h+3
+      tmem_ld16(lanes(tmem) + 128 + 12 * h, ds);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * h + cc;
         float V[NLM], G[NLM], dV[NLM], dG[NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -822,13 +819,14 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_c(BfW w, PassBufs b) {
     }
     __syncthreads();
     if (threadIdx.x < m.nseg) {
-      const int s = threadIdx.x;
+      const int sg = threadIdx.x;
       double acc = 0.0;
-      for (int p = m.sstart[s]; p < m.sstart[s + 1]; ++p) acc += (double)s_eij[p];
-      b.epart[m.tile + m.atom[s]] = acc;
+      for (int p = m.sstart[sg]; p < m.sstart[sg + 1]; ++p)
+        acc += (double)((s_eq[p] + s_eq[kT + p]) + (s_eq[2 * kT + p] + s_eq[3 * kT + p]));
+      b.epart[m.tile + m.atom[sg]] = acc;
     }
     if (threadIdx.x < kT && valid) {
-      b.dU[sidx(m, 1, 0, r)] = s_du[r] + s_du[kT + r];
+      b.dU[sidx(m, 1, 0, r)] = (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(m, NLM, lm, r)] = 0.0f;
     }
@@ -1294,7 +1292,7 @@ constexpr size_t sm_a(bool split) {
 constexpr size_t kSmB1 = 1024 + kImgEmb + 3 * kImgMix + kOp128 + kOpT + 4 * (kT * NLM + kSegCap * CL);
 constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * EP);
 constexpr size_t sm_c(bool split) {
-  return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 + 4 * (5 * kT + kSegCap * CL);
+  return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 + 4 * (10 * kT + kSegCap * CL);
 }
 constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 +
                           4 * (kT + 2 * kT * NLM + 2 * kT + kSegCap * CL);
@@ -1345,7 +1343,7 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     k_bf_b2<Tin><<<grid, kThr, kSmB2, s>>>(w, b, k);
     mark(kKB2);
   }
-  k_bf_c<Tin, kSplit><<<grid, kThr, kSmC, s>>>(w, b);
+  k_bf_c<Tin, kSplit><<<grid, kThr4, kSmC, s>>>(w, b);
   mark(kKC);
   for (int k = L - 1; k >= 1; --k) {
     k_bf_b2t<Tin><<<grid, kThr, kSmB2T, s>>>(w, b, k);
