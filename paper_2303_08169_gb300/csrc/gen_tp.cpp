@@ -18,6 +18,8 @@
 //   tpL_fwd_scalar(V, G, S)   l3 = 0 paths only
 //   tpL_bwd(V, G, dT, dV, dG) adjoint of tpL_fwd (accumulates into dV, dG)
 //   tpL_bwd_scalar(V, G, dS, dV, dG)
+//   tpL_bwd_l3lt2 / tpL_bwd_l3ge2: the terms of tpL_bwd with output order
+//   l3 <= 1 / l3 = 2 (their sum is tpL_bwd)
 // V and G hold one channel's (l_max+1)^2 components, index l*l + (m + l).
 // T is grouped by output order l3: block l3 starts at TPL_TOFF[l3] and holds
 // TPL_P[l3] paths (in lexicographic path order) of 2 l3 + 1 components each.
@@ -221,6 +223,12 @@ void emit(FILE* f, int lmax) {
   fwd("fwd_scalar", sterms, P[0]);
   bwd("bwd", terms);
   bwd("bwd_scalar", sterms);
+  // the adjoint split by output order (l3 <= 1, l3 = 2): the two halves add
+  // up to tpL_bwd and read only their own entries of dT
+  std::vector<Term> lo, hi;
+  for (auto& t : terms) (t.o < toff[std::min(2, lmax)] || lmax < 2 ? lo : hi).push_back(t);
+  bwd("bwd_l3lt2", lo);
+  bwd("bwd_l3ge2", hi);
 }
 
 }  // namespace

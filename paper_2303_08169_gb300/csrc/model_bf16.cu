@@ -296,6 +296,12 @@ AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
   st8<Tin>(A, sw128_off(r, c0, 128), v);
   st8<Tin>(A, sw128_off(r, c0 + 8, 128), v + 8);
 }
+template <class Tin>
+AL_DEV void st4(uint8_t* A, uint32_t off, const float* v) {
+  const uint32_t w0 = (uint32_t)Op<Tin>::bits(v[0]) | ((uint32_t)Op<Tin>::bits(v[1]) << 16);
+  const uint32_t w1 = (uint32_t)Op<Tin>::bits(v[2]) | ((uint32_t)Op<Tin>::bits(v[3]) << 16);
+  *reinterpret_cast<uint2*>(A + off) = make_uint2(w0, w1);
+}
 // hi part into Ahi, lo part into Alo (same row and columns)
 template <class Tin>
 AL_DEV void st16_split(uint8_t* Ahi, uint8_t* Alo, int r, int c0, const float* v) {
@@ -840,8 +846,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 // Pass B2_k^T: adjoint of the Gamma^{k+1} scatter and of the latent MLP of
 // layer k (its forward recomputed in the tile): dx^{k-1} (residual + latent
 // parts, without the embedding term), ds -> dS, du, dY.
+// 512 threads: thread (r, h) owns tile row r, column quarter h of every
+// epilogue and channels 4h..4h+3 of the env adjoint.
 template <class Tin>
-__global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1, {
     bulk_g2s(sm, w.env[k], kImgEnv, &bars[1]);
     bulk_g2s(sm + kImgEnv, w.lat0[k - 1], kImgLat0, &bars[1]);
@@ -855,14 +863,14 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   uint8_t* DE = A1 + kOp128;
   float* s_fc = reinterpret_cast<float*>(DE + kOp64);
   float* s_Y = s_fc + kT;
-  float* s_dy = s_Y + kT * NLM;
-  float* s_du = s_dy + kT * NLM;   // [2][kT]
-  float* s_g = s_du + 2 * kT;      // [kSegCap][CL]
+  float* s_dy = s_Y + kT * NLM;    // [4][kT][NLM]
+  float* s_du = s_dy + 4 * kT * NLM;   // [4][kT]
+  float* s_g = s_du + 4 * kT;      // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     const bool valid = r < m.np;
-    if (threadIdx.x < kT) {
+    if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
@@ -871,34 +879,35 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    row_to_op<Tin>(HA, m, r, b.X[k], D, 64 * h, valid, 64 * h, 64);
+    row_to_op<Tin>(HA, m, r, b.X[k], D, 32 * h, valid, 32 * h, 32);
     stage_g(b.dgam[k + 1], b.row_ptr, m, s_g);
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
-    if (threadIdx.x < kT) {
-      float e[16], de[16];
-      tmem_ld16(lanes(tmem) + 0, e);
-      float dy[NLM];
+    {
+      float e[8], dy[NLM];
+      tmem_ld8(lanes(tmem) + 4 * h, e);              // e of channels 4h..4h+3 in e[0..3]
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
-      for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * h + cc;
         float dG[NLM];
         get_g(s_g, b.dgam[k + 1], b.row_ptr, m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
           acc = fmaf(dG[lm], s_Y[r * NLM + lm], acc);
-          dy[lm] = fmaf(dG[lm], e[c], dy[lm]);
+          dy[lm] = fmaf(dG[lm], e[cc], dy[lm]);
         }
-        de[c] = acc;
+        st1<Tin>(DE, r, c, acc);
       }
-      st16<Tin>(DE, r, 0, de);
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) s_dy[r * NLM + lm] = dy[lm];
+      for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dy[lm];
     }
     mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
-    row_to_op<Tin>(HA, m, r, b.X[k - 1], D, 64 * h, valid, 64 * h, 64);
-    if (h == 1) {
-      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 0, valid, 128, 48);
+    row_to_op<Tin>(HA, m, r, b.X[k - 1], D, 32 * h, valid, 32 * h, 32);
+    if (h >= 1) {
+      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
+    } else {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
     }
@@ -947,18 +956,19 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] += dh[q];
       });
-      float ds[32];
-      tmem_ld16(lanes(tmem) + 288 + 128 + 24 * h, ds);
-      tmem_ld16(lanes(tmem) + 288 + 128 + 24 * h + 16, ds + 16);
+      float ds[16];                                   // ds columns 12 h .. 12 h + 11
+      tmem_ld16(lanes(tmem) + 288 + 128 + 12 * h, ds);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 24; ++q) b.dS[sidx(m, C * NS, 24 * h + q, r)] = ds[q];
+        for (int q = 0; q < 12; ++q) b.dS[sidx(m, C * NS, 12 * h + q, r)] = ds[q];
     }
     __syncthreads();
     if (threadIdx.x < kT && valid) {
-      b.dU[sidx(m, 1, 0, r)] += s_du[r] + s_du[kT + r];
+      b.dU[sidx(m, 1, 0, r)] += (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(m, NLM, lm, r)] += s_dy[r * NLM + lm];
+      for (int lm = 0; lm < NLM; ++lm)
+        b.dY[sidx(m, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
+                                     (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]);
     }
     __syncthreads();
   }
@@ -969,8 +979,13 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 // Pass B1_k^T: adjoint of mixing and of the tensor product of layer k:
 // dV^{k-1} (k >= 2) or, for k = 1, the embedding adjoint into dx^0 and dY;
 // dGamma^k partials.
+// 512 threads: thread (r, h) owns tile row r and channels 4h..4h+3.  The
+// mixing adjoint is issued in two rounds (l3 <= 1, then l3 = 2) because all
+// nine products together exceed the TMEM columns; each round runs only its
+// own terms of the tensor-product adjoint.  The embedding-adjoint inputs
+// (dw0, dY) are linear in dV and accumulate over the rounds.
 template <class Tin>
-__global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
     bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
     for (int l = 0; l < 3; ++l) bulk_g2s(sm + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
@@ -982,13 +997,13 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   uint8_t* DW0 = X + kOp128;
   float* s_Y = reinterpret_cast<float*>(DW0 + kOp64);
   float* s_dg = s_Y + kT * NLM;           // [kT][CLP]
-  float* s_dy = s_dg + kT * CLP;          // [2][kT][NLM]
-  float* s_g = s_dy + 2 * kT * NLM;       // [kSegCap][CL]
+  float* s_dy = s_dg + kT * CLP;          // [4][kT][NLM]
+  float* s_g = s_dy + 4 * kT * NLM;       // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     const bool valid = r < m.np;
-    if (threadIdx.x < kT) {
+    if (h == 0) {
       float u[3], d, fc, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
@@ -996,114 +1011,103 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    // column 16 lm + co: this thread's 8 channels of one lm are one 16-byte chunk
+    // column 16 lm + c: this thread's 4 channels of one lm are 8 contiguous bytes
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) {
-      float v8[8];
+      float v4[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v8[q] = valid ? b.dV[sidx(m, CL, (8 * h + q) * NLM + lm, r)] : 0.0f;
-      st8<Tin>(DVT, sw128_off(r, 16 * lm + 8 * h, 128), v8);
+      for (int q = 0; q < 4; ++q) v4[q] = valid ? b.dV[sidx(m, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
+      st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), v4);
     }
     stage_g(b.gam[k], b.row_ptr, m, s_g);
     if (k == 1) {
-      row_to_op<Tin>(X, m, r, b.X[0], D, 64 * h, valid, 64 * h, 64);
+      row_to_op<Tin>(X, m, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
       mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });       // w0
     }
-    float w0[32];
-    if (k == 1) {
-      tmem_ld16(lanes(tmem) + 24 * h, w0);
-      tmem_ld16(lanes(tmem) + 24 * h + 16, w0 + 16);
-    }
-    const int i = m.pi[r];
+    float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc * 3 + l]
+    if (k == 1) tmem_ld16(lanes(tmem) + 12 * h, w0);
     const float* dsg = b.dS;
-    float dyl[NLM];
+    float dw[12], dyl[NLM];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) dw[q] = 0.0f;
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
-    // channels are processed 4 at a time (per thread); for each group the
-    // mixing adjoint is issued in two rounds (l3 <= 1, then l3 = 2) because
-    // all nine products together exceed the TMEM columns
-    for (int g4 = 0; g4 < 2; ++g4) {
-      const int cb = 8 * h + 4 * g4;
-      float dVa[4][NLM];
-#pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4)
-#pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) dVa[c4][lm] = 0.0f;
-      for (int round = 0; round < 2; ++round) {
-        if (round == 0) {
-          mm.run([&] {
-            mma_k<Tin>(tmem + 64, DVT, 0, Wmix, 48, 1, true, 16);
-            for (int j = 1; j < 4; ++j) mma_k<Tin>(tmem + 112 + 64 * (j - 1), DVT, j, Wmix + kImgMix, 64, 1, true, 16);
-          });
-        } else {
-          mm.run([&] {
-            for (int j = 4; j < 9; ++j) mma_k<Tin>(tmem + 64 + 64 * (j - 4), DVT, j, Wmix + 2 * kImgMix, 64, 1, true, 16);
-          });
-        }
-        float tv[5][16];
-        if (round == 0) {
-          tmem_ld16(lanes(tmem) + 64 + cb * 3, tv[0]);
-          for (int j = 1; j < 4; ++j) tmem_ld16(lanes(tmem) + 112 + 64 * (j - 1) + cb * 4, tv[j]);
-        } else {
-          for (int j = 4; j < 9; ++j) tmem_ld16(lanes(tmem) + 64 + 64 * (j - 4) + cb * 4, tv[j - 4]);
-        }
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const int c = cb + c4, cc = 4 * g4 + c4;
-          float dT[TP2_NT];
-#pragma unroll
-          for (int o = 0; o < TP2_NT; ++o) dT[o] = 0.0f;
-          if (round == 0) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) dT[q] = tv[0][c4 * 3 + q] + (valid ? dsg[sidx(m, C * NS, c * NS + q, r)] : 0.0f);
-#pragma unroll
-            for (int mm1 = 0; mm1 < 3; ++mm1)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) dT[3 + q * 3 + mm1] = tv[1 + mm1][c4 * 4 + q];
-          } else {
-#pragma unroll
-            for (int mm2 = 0; mm2 < 5; ++mm2)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = tv[mm2][c4 * 4 + q];
-          }
-          float V[NLM], G[NLM], dG[NLM];
-          if (k == 1) {
-#pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[cc * 3 + l_of(lm)] * s_Y[r * NLM + lm];
-          } else {
-#pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
-          }
-          get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
-#pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) dG[lm] = round == 0 ? 0.0f : s_dg[r * CLP + c * NLM + lm];
-          tp2_bwd(V, G, dT, dVa[c4], dG);
-#pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
-        }
-      }
-      if (k >= 2) {
-        if (valid)
-#pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4)
-#pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(m, CL, (cb + c4) * NLM + lm, r)] = dVa[c4][lm];
+    for (int round = 0; round < 2; ++round) {
+      if (round == 0) {
+        mm.run([&] {
+          mma_k<Tin>(tmem + 64, DVT, 0, Wmix, 48, 1, true, 16);
+          for (int j = 1; j < 4; ++j) mma_k<Tin>(tmem + 112 + 64 * (j - 1), DVT, j, Wmix + kImgMix, 64, 1, true, 16);
+        });
       } else {
+        mm.run([&] {
+          for (int j = 4; j < 9; ++j) mma_k<Tin>(tmem + 64 + 64 * (j - 4), DVT, j, Wmix + 2 * kImgMix, 64, 1, true, 16);
+        });
+      }
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const int cc = 4 * g4 + c4;
-          float dw[3] = {0.f, 0.f, 0.f};
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const int c = 4 * h + c4;
+        float dT[TP2_NT];
+        uint32_t t[20];
+        if (round == 0) {
+          tmem_ld4_raw(lanes(tmem) + 64 + 3 * c, t);                  // l3 = 0: columns 3c + q
+#pragma unroll
+          for (int j = 1; j < 4; ++j) tmem_ld4_raw(lanes(tmem) + 112 + 64 * (j - 1) + 4 * c, t + 4 * j);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) tmem_wait4(t + 4 * g);
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            dT[q] = __uint_as_float(t[q]) + (valid ? dsg[sidx(m, C * NS, c * NS + q, r)] : 0.0f);
+#pragma unroll
+          for (int mm1 = 0; mm1 < 3; ++mm1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dT[3 + q * 3 + mm1] = __uint_as_float(t[4 + 4 * mm1 + q]);
+        } else {
+#pragma unroll
+          for (int j = 4; j < 9; ++j) tmem_ld4_raw(lanes(tmem) + 64 + 64 * (j - 4) + 4 * c, t + 4 * (j - 4));
+#pragma unroll
+          for (int g = 0; g < 5; ++g) tmem_wait4(t + 4 * g);
+#pragma unroll
+          for (int mm2 = 0; mm2 < 5; ++mm2)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = __uint_as_float(t[4 * mm2 + q]);
+        }
+        float V[NLM], G[NLM], dG[NLM], dVp[NLM];
+        if (k == 1) {
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[c4 * 3 + l_of(lm)] * s_Y[r * NLM + lm];
+        } else {
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+        }
+        get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          dG[lm] = round == 0 ? 0.0f : s_dg[r * CLP + c * NLM + lm];
+          dVp[lm] = 0.0f;
+        }
+        if (round == 0) tp2_bwd_l3lt2(V, G, dT, dVp, dG);
+        else tp2_bwd_l3ge2(V, G, dT, dVp, dG);
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
+        if (k >= 2) {
+          if (valid)
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) {
+              float* dv = &b.dV[sidx(m, CL, c * NLM + lm, r)];
+              *dv = round == 0 ? dVp[lm] : *dv + dVp[lm];
+            }
+        } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
-            dw[l_of(lm)] = fmaf(dVa[c4][lm], s_Y[r * NLM + lm], dw[l_of(lm)]);
-            dyl[lm] = fmaf(w0[cc * 3 + l_of(lm)], dVa[c4][lm], dyl[lm]);
+            dw[c4 * 3 + l_of(lm)] = fmaf(dVp[lm], s_Y[r * NLM + lm], dw[c4 * 3 + l_of(lm)]);
+            dyl[lm] = fmaf(w0[c4 * 3 + l_of(lm)], dVp[lm], dyl[lm]);
           }
-#pragma unroll
-          for (int l = 0; l < 3; ++l) st1<Tin>(DW0, r, (cb + c4) * 3 + l, dw[l]);
         }
       }
     }
     if (k == 1) {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) st1<Tin>(DW0, r, 12 * h + q, dw[q]);
       mm.run([&] { mma_k<Tin>(tmem + 384, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
       float* dxg = b.dX;
       epi(tmem, 384, 128, [&](int rr, int n0, const float* v) {
@@ -1118,7 +1122,8 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     if (threadIdx.x < kT && valid && k == 1) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        b.dY[sidx(m, NLM, lm, r)] += s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm];
+        b.dY[sidx(m, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
+                                     (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]);
     }
     seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
     __syncthreads();
@@ -1295,9 +1300,9 @@ constexpr size_t sm_c(bool split) {
   return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 + 4 * (10 * kT + kSegCap * CL);
 }
 constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 +
-                          4 * (kT + 2 * kT * NLM + 2 * kT + kSegCap * CL);
+                          4 * (kT + 5 * kT * NLM + 4 * kT + kSegCap * CL);
 constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 +
-                          4 * (kT * NLM + kT * CLP + 2 * kT * NLM + kSegCap * CL);
+                          4 * (kT * NLM + kT * CLP + 4 * kT * NLM + kSegCap * CL);
 constexpr size_t sm_at(bool split) {
   return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
          4 * (2 * kT * GP + 2 * kT * NLM + 2 * kT + kSegCap * CL);
@@ -1346,9 +1351,9 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
   k_bf_c<Tin, kSplit><<<grid, kThr4, kSmC, s>>>(w, b);
   mark(kKC);
   for (int k = L - 1; k >= 1; --k) {
-    k_bf_b2t<Tin><<<grid, kThr, kSmB2T, s>>>(w, b, k);
+    k_bf_b2t<Tin><<<grid, kThr4, kSmB2T, s>>>(w, b, k);
     mark(kKBT);
-    k_bf_b1t<Tin><<<grid, kThr, kSmB1T, s>>>(w, b, k);
+    k_bf_b1t<Tin><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
     mark(kKBT2);
   }
   k_bf_at<Tin, kSplit><<<grid, kThr, kSmAT, s>>>(w, b);

@@ -206,6 +206,18 @@ UM_DEV void tmem_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 4 columns without waiting: the caller issues several loads and then calls
+// tmem_wait4 on each group; the first wait waits for all of them, and tying
+// the registers to it keeps every use of them after the wait.
+UM_DEV void tmem_ld4_raw(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+UM_DEV void tmem_wait4(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])::"memory");
+}
+
 UM_DEV void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile(
