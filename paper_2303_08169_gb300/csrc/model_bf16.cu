@@ -4,8 +4,8 @@
 // Same model and same pass order as the FP32 path (model_fp32.cu): forward
 // passes, a fused last-layer forward + adjoint, then the adjoint passes
 // (forces f = -dE/dr, Eq. 1).  Differences:
-//  * tiles of 128 pairs, one persistent CTA of 256 threads per SM; thread t
-//    owns tile row r = t % 128 (its TMEM lane) and column half t / 128;
+//  * tiles of 128 pairs, one persistent CTA of 512 threads per SM; thread t
+//    owns tile row r = t % 128 (its TMEM lane) and column quarter t / 128;
 //  * every per-pair GEMM (two-body, embedding, env, mixing, latent, energy
 //    and their adjoints) runs on tcgen05.mma with BF16 operands in
 //    128-byte-swizzled shared memory and FP32 accumulators in TMEM; the
@@ -33,8 +33,9 @@ namespace {
 using namespace umma;
 
 constexpr int kT = 128;
-constexpr int kThr = 256;    // threads of a CTA: row r = t % 128, column half t / 128
-constexpr int kThr4 = 512;   // kernels with four column quarters per row (more warps per SM)
+// threads of a CTA: thread t owns tile row r = t % 128 (its TMEM lane) and
+// column quarter h = t / 128 of every epilogue (16 warps per SM)
+constexpr int kThr4 = 512;
 constexpr int D = 128, C = 16, E = 32, NLM = 9, NS = 3, KH = 176, NW0 = 48, CL = 144, NB = 8;
 constexpr float kR2 = 0.70710678118654752f;
 // odd row strides of per-row shared arrays (32 consecutive rows hit 32 banks)
@@ -415,7 +416,7 @@ AL_DEV void mma_split(uint32_t d, const uint8_t* A, const uint8_t* Alo, const ui
 // [h_hi | h_lo | h_hi] against the image [W_hi | W_hi | W_lo] along K (12
 // inputs fit a 16-column K-step), the second adds the lo MMAs.
 template <class Tin, bool kSplit>
-__global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
   BF_PROLOGUE(kImgTb0 + (kSplit ? 2 : 1) * kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
     bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
@@ -446,8 +447,12 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
         float u[3], d, dfc, B[NB];
         geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
         bessel<NB>(d, w.rc, B, nullptr);
-        h0[b.species[m.pi[r]]] = 1.0f;
-        h0[2 + b.species[m.pj[r]]] = 1.0f;
+        const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {                 // one-hot species (no dynamic register index)
+          h0[q] = zi == q ? 1.0f : 0.0f;
+          h0[2 + q] = zj == q ? 1.0f : 0.0f;
+        }
 #pragma unroll
         for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
       }
@@ -490,8 +495,9 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_a(BfW w, PassBufs b) {
 
 // ============================================================================
 // Pass B1_k: tensor product of layer k and channel mixing -> V^k, scalars S^k.
+// 512 threads: thread (r, h) owns tile row r and channels 4h..4h+3.
 template <class Tin>
-__global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
     bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
     for (int l = 0; l < 3; ++l) bulk_g2s(sm + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
@@ -515,26 +521,24 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     const bool valid = r < m.np;
     if (k == 1) {
-      row_to_op<Tin>(X, m, r, b.X[0], D, 64 * h, valid, 64 * h, 64);
+      row_to_op<Tin>(X, m, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
       stage_g(b.gam[k], b.row_ptr, m, s_g);
       mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
     } else {
       stage_g(b.gam[k], b.row_ptr, m, s_g);
       __syncthreads();
     }
-    float w0[32];
-    if (k == 1) {
-      tmem_ld16(lanes(tmem) + 24 * h, w0);
-      tmem_ld16(lanes(tmem) + 24 * h + 16, w0 + 16);
-    }
+    float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc * 3 + l]
+    if (k == 1) tmem_ld16(lanes(tmem) + 12 * h, w0);
     // channel pairs: for l3 >= 1 the P_l = 4 paths of channels c, c + 1 fill
     // one 16-byte chunk of a mixing K-slice; the l3 = 0 slice (P_0 = 3) is
     // written per element
-    for (int cc = 0; cc < 8; cc += 2) {
+#pragma unroll
+    for (int cc = 0; cc < 4; cc += 2) {
       float Tv[2][TP2_NT];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const int c = 8 * h + cc + e;
+        const int c = 4 * h + cc + e;
         float V[NLM], G[NLM];
         if (k == 1) {
 #pragma unroll
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
 #pragma unroll
           for (int q = 0; q < NS; ++q) b.S[k][sidx(m, C * NS, c * NS + q, r)] = Tv[e][q];
       }
-      const int c0 = 8 * h + cc;
+      const int c0 = 4 * h + cc;
 #pragma unroll
       for (int j = 1; j < 9; ++j) {
         const int l3 = l_of(j), mm3 = j - l3 * l3, nm = 2 * l3 + 1;
@@ -571,7 +575,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     });
     {
       const uint32_t base = lanes(tmem);
-      for (int j = (h == 0 ? 0 : 5); j < (h == 0 ? 5 : 9); ++j) {
+      for (int j = h; j < 9; j += 4) {                // components h, h + 4, h + 8
         float v[16];
         tmem_ld16(base + 64 + 16 * j, v);
         if (valid)
@@ -586,8 +590,9 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b1(BfW w, PassBufs b, int k) {
 
 // ============================================================================
 // Pass B2_k: latent MLP of layer k (x^k) and env of layer k+1 -> Gamma^{k+1}.
+// 512 threads: column quarters for every epilogue.
 template <class Tin>
-__global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgEnv, {
     bulk_g2s(sm, w.lat0[k - 1], kImgLat0, &bars[1]);
     bulk_g2s(sm + kImgLat0, w.lat1[k - 1], kImgLat1, &bars[1]);
@@ -615,9 +620,10 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
     const float* xg = b.X[k - 1];
-    row_to_op<Tin>(HA, m, r, xg, D, 64 * h, valid, 64 * h, 64);
-    if (h == 1) {
-      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 0, valid, 128, 48);
+    row_to_op<Tin>(HA, m, r, xg, D, 32 * h, valid, 32 * h, 32);
+    if (h >= 1) {
+      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
+    } else {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
     }
@@ -1138,8 +1144,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 // two-body GEMMs and their adjoints take split operands; A1lo holds the lo
 // part of silu(z1), then of dz2, then of dz1.  The dh0 adjoint reads the
 // packed image [W_hi | W_hi | W_lo] (48 columns): dh0 = block 0 + block 2.
+// 512 threads: column quarters for every epilogue; the env adjoint's
+// channels are spread over the quarters.
 template <class Tin, bool kSplit>
-__global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
+__global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
   BF_PROLOGUE(kImgTb0 + (kSplit ? 2 : 1) * kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
     bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
@@ -1158,9 +1166,13 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
   float* s_geo = reinterpret_cast<float*>(A1lo + (kSplit ? kOp128 : 0));   // [kT][GP]: u, d, fc, dfc
   float* s_dB = s_geo + kT * GP;                          // [kT][GP]: dB
   float* s_Y = s_dB + kT * GP;
-  float* s_dy = s_Y + kT * NLM;
-  float* s_du = s_dy + kT * NLM;                          // [2][kT]
-  float* s_g = s_du + 2 * kT;                             // [kSegCap][CL]
+  float* s_dy = s_Y + kT * NLM;                           // [kT][NLM]
+  float* s_du = s_dy + kT * NLM;                          // [4][kT]
+  float* s_g = s_du + 4 * kT;                             // [kSegCap][CL]
+  // [4][kT][NLM] per-quarter dY partials: X is dead from the end of the e^1
+  // MMA until the dz1 epilogue, and the partials are summed right after the
+  // env1^T MMA
+  float* s_dyq = reinterpret_cast<float*>(X);
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -1176,8 +1188,12 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
       if (valid) {
         geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
         bessel<NB>(d, w.rc, B, dB);
-        h0[b.species[m.pi[r]]] = 1.0f;
-        h0[2 + b.species[m.pj[r]]] = 1.0f;
+        const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {                 // one-hot species (no dynamic register index)
+          h0[q] = zi == q ? 1.0f : 0.0f;
+          h0[2 + q] = zj == q ? 1.0f : 0.0f;
+        }
 #pragma unroll
         for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
       }
@@ -1206,27 +1222,33 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
       st16<Tin>(X, rr, n0, o);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });      // e^1
-    if (threadIdx.x < kT) {
-      float e[16], de[16], dy[NLM];
-      tmem_ld16(lanes(tmem) + 256, e);
+    {
+      float e[8], dy[NLM];
+      tmem_ld8(lanes(tmem) + 256 + 4 * h, e);         // e of channels 4h..4h+3 in e[0..3]
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
-      for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * h + cc;
         float dG[NLM];
         get_g(s_g, b.dgam[1], b.row_ptr, m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
           acc = fmaf(dG[lm], s_Y[r * NLM + lm], acc);
-          dy[lm] = fmaf(dG[lm], e[c], dy[lm]);
+          dy[lm] = fmaf(dG[lm], e[cc], dy[lm]);
         }
-        de[c] = acc;
+        st1<Tin>(DE, r, c, acc);
       }
-      st16<Tin>(DE, r, 0, de);
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) s_dy[r * NLM + lm] = dy[lm];
+      for (int lm = 0; lm < NLM; ++lm) s_dyq[(h * kT + r) * NLM + lm] = dy[lm];
     }
     mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });    // env1^T de
+    if (h == 0)
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm)
+        s_dy[r * NLM + lm] = (s_dyq[r * NLM + lm] + s_dyq[(kT + r) * NLM + lm]) +
+                             (s_dyq[(2 * kT + r) * NLM + lm] + s_dyq[(3 * kT + r) * NLM + lm]);
     {
       float du = 0.0f;
       const float* dxg = b.dX;
@@ -1270,7 +1292,7 @@ __global__ void __launch_bounds__(kThr, 1) k_bf_at(BfW w, PassBufs b) {
         const float u[3] = {g[0], g[1], g[2]};
         const float d = g[3], dfc = g[5];
         const size_t pp = (size_t)(m.p0 + r);
-        float gd = (s_du[r] + s_du[kT + r] + b.dU[sidx(m, 1, 0, r)]) * dfc;
+        float gd = ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]) + b.dU[sidx(m, 1, 0, r)]) * dfc;
 #pragma unroll
         for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * GP + n], gd);
         float dY[NLM];
@@ -1305,7 +1327,7 @@ constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 +
                           4 * (kT * NLM + kT * CLP + 4 * kT * NLM + kSegCap * CL);
 constexpr size_t sm_at(bool split) {
   return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
-         4 * (2 * kT * GP + 2 * kT * NLM + 2 * kT + kSegCap * CL);
+         4 * (2 * kT * GP + 2 * kT * NLM + 4 * kT + kSegCap * CL);
 }
 // 4 KB left for the static Meta, barriers and flags of every kernel
 constexpr size_t kSmLimit = 232448 - 4096;
@@ -1313,6 +1335,7 @@ static_assert(sm_a(true) <= kSmLimit && kSmB1 <= kSmLimit && kSmB2 <= kSmLimit &
                   kSmB2T <= kSmLimit && kSmB1T <= kSmLimit && sm_at(true) <= kSmLimit,
               "shared memory per kernel");
 static_assert(kOpH + kOp128 >= 4 * kT * CLP, "pass C reuses HA + A1 for the dGamma contributions");
+static_assert(kOp128 >= 4 * 4 * kT * NLM, "pass A^T keeps the dY partials in X");
 
 int g_sms = 0;
 
@@ -1340,12 +1363,12 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     if (km) km->mark(k, s);
   };
   mark(kKStart);
-  k_bf_a<Tin, kSplit><<<grid, kThr, kSmA, s>>>(w, b);
+  k_bf_a<Tin, kSplit><<<grid, kThr4, kSmA, s>>>(w, b);
   mark(kKA);
   for (int k = 1; k < L; ++k) {
-    k_bf_b1<Tin><<<grid, kThr, kSmB1, s>>>(w, b, k);
+    k_bf_b1<Tin><<<grid, kThr4, kSmB1, s>>>(w, b, k);
     mark(kKB);
-    k_bf_b2<Tin><<<grid, kThr, kSmB2, s>>>(w, b, k);
+    k_bf_b2<Tin><<<grid, kThr4, kSmB2, s>>>(w, b, k);
     mark(kKB2);
   }
   k_bf_c<Tin, kSplit><<<grid, kThr4, kSmC, s>>>(w, b);
@@ -1356,7 +1379,7 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     k_bf_b1t<Tin><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
     mark(kKBT2);
   }
-  k_bf_at<Tin, kSplit><<<grid, kThr, kSmAT, s>>>(w, b);
+  k_bf_at<Tin, kSplit><<<grid, kThr4, kSmAT, s>>>(w, b);
   mark(kKAT);
 }
 
