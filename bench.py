@@ -335,6 +335,39 @@ class Runner:
         self.al.allegro_destroy(self.ctx)
 
 
+def sam_timing(al, torch, steps=5):
+    """SAM training step (Eq. 3) on 32 seeded ammonia structures of 64-512
+    atoms; targets from a teacher model (weights seed 43) evaluated by the
+    library's FP32 path.  Wall clock per allegro_sam_train_step."""
+    import synth
+    cfg = synth.MAIN
+    teacher = synth.make_blob(cfg, 43, sigma=_energy_scale("main_teacher"))
+    _, student = _model()
+    batch = synth.make_sam_batch()
+    tctx = al.allegro_create(teacher, np.array([14.007, 1.008]), cfg.r_cut, cfg.l_max, cfg.n_layers)
+    structs = []
+    for pos, sp, cell in batch:
+        F = np.zeros((len(sp), 3), np.float32)
+        E = al.allegro_energy_forces(tctx, pos, sp.astype(np.int32), cell, F)
+        structs.append(dict(pos=pos, species=sp, cell=cell, e_target=E, f_target=F))
+    al.allegro_destroy(tctx)
+    ctx = al.allegro_create(student, np.array([14.007, 1.008]), cfg.r_cut, cfg.l_max, cfg.n_layers)
+    b, keep = al.make_batch(structs)
+    losses = [al.allegro_sam_train_step(ctx, b, 0.05, 2e-3, 1.0, 100.0)]     # warm-up (allocations)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        losses.append(al.allegro_sam_train_step(ctx, b, 0.05, 2e-3, 1.0, 100.0))
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    al.allegro_destroy(ctx)
+    n_atoms = int(sum(len(s["species"]) for s in structs))
+    return {"structures": len(structs), "atoms": n_atoms, "ms_per_step": 1e3 * dt, "steps": steps,
+            "rho": 0.05, "lr": 2e-3, "loss_first": losses[0], "loss_last": losses[-1],
+            "note": "FP32 passes with per-pair dumps; two loss gradients (w, w + eps) per step, "
+                    "each three pass sequences per structure (forward + central difference)"}
+
+
 def roofline(phases, n_pairs, tensor_path, peaks):
     if tensor_path:
         times = {k: phases[k] for k in GEMM_MAC_PER_PAIR}
@@ -400,6 +433,7 @@ def run_ours(args):
             r = head if name == args.config else run.md(name, K2, W)
             paths[name] = {"value": r["N"] * r["K"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / r["K"],
                            "atoms": r["N"], "pairs": r["n_pairs"], "steps": r["K"], "dtype": WORKLOADS[name]["dtype"]}
+        sam = sam_timing(al, torch)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             cpu, (pos, sp, cell, E0, F0) = cpu_baseline()
             # force error of every path against the FP64 oracle on the 6,912-atom cell
@@ -414,6 +448,7 @@ def run_ours(args):
                 paths[name]["rms_dF_eV_per_A"] = acc["rms_dF"]
     else:
         e2e = None
+        sam = None
     run.close()
     if rank != 0:
         if dist:
@@ -450,6 +485,8 @@ def run_ours(args):
         line["accuracy_vs_fp64_oracle_6912"] = {
             "bound_max_abs_dF": FORCE_BOUND, "headline_within_bound": accuracy[args.config]["max_abs_dF"] <= FORCE_BOUND
             if args.config in accuracy else None, **accuracy}
+    if sam:
+        line["sam_train_step"] = sam
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

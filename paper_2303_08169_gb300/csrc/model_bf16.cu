@@ -178,7 +178,9 @@ AL_DEV void load_g(const float* __restrict__ part, const int* __restrict__ row_p
 // Per-pair arrays of this path use a tile-SoA layout: element (pair p,
 // feature f) of a W-wide array lives at ((p / 128) * W + f) * 128 + p % 128,
 // so the 32 lanes of a warp (consecutive tile rows) touch consecutive floats.
-AL_DEV size_t sidx(const Meta& m, int W, int f, int r) { return ((size_t)m.tile * W + f) * kT + r; }
+// (tile from a register: with W and f known at compile time the feature
+// offsets fold into the load/store immediates)
+AL_DEV size_t sidx(int tile, int W, int f, int r) { return ((size_t)tile * W + f) * kT + r; }
 
 // Gamma (or dGamma) of the tile's first kSegCap centre atoms, summed once per
 // tile into shared memory; rows of later segments read the partials directly.
@@ -329,12 +331,13 @@ AL_DEV void st1(uint8_t* A, int r, int c, float v) {
 // features [f0, f0+n) of tile row r of a tile-SoA FP32 array (W wide),
 // converted into operand columns [c0, c0+n)
 template <class Tin>
-AL_DEV void row_to_op(uint8_t* A, const Meta& m, int r, const float* __restrict__ g, int W, int f0, bool valid,
+AL_DEV void row_to_op(uint8_t* A, int tile, int r, const float* __restrict__ g, int W, int f0, bool valid,
                       int c0, int n) {
+#pragma unroll 2
   for (int k = 0; k < n; k += 16) {
     float v[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = valid ? g[sidx(m, W, f0 + k + q, r)] : 0.0f;
+    for (int q = 0; q < 16; ++q) v[q] = valid ? g[sidx(tile, W, f0 + k + q, r)] : 0.0f;
     st16<Tin>(A, r, c0 + k, v);
   }
 }
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       st16<Tin>(X, r, n0, o);
       if (r < m.np)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) b.X[0][sidx(m, D, n0 + q, r)] = o[q];
+        for (int q = 0; q < 16; ++q) b.X[0][sidx(tile, D, n0 + q, r)] = o[q];
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
     if (threadIdx.x < kT) {
@@ -521,7 +524,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     const bool valid = r < m.np;
     if (k == 1) {
-      row_to_op<Tin>(X, m, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
+      row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
       stage_g(b.gam[k], b.row_ptr, m, s_g);
       mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
     } else {
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
           for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[(cc + e) * 3 + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
         }
         get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
         tp2_fwd(V, G, Tv[e]);
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
         for (int q = 0; q < NS; ++q) st1<Tin>(T, r, c * NS + q, Tv[e][q]);
         if (valid)
 #pragma unroll
-          for (int q = 0; q < NS; ++q) b.S[k][sidx(m, C * NS, c * NS + q, r)] = Tv[e][q];
+          for (int q = 0; q < NS; ++q) b.S[k][sidx(tile, C * NS, c * NS + q, r)] = Tv[e][q];
       }
       const int c0 = 4 * h + cc;
 #pragma unroll
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
         tmem_ld16(base + 64 + 16 * j, v);
         if (valid)
 #pragma unroll
-          for (int co = 0; co < C; ++co) b.V[k][sidx(m, CL, co * NLM + j, r)] = v[co];
+          for (int co = 0; co < C; ++co) b.V[k][sidx(tile, CL, co * NLM + j, r)] = v[co];
       }
     }
     __syncthreads();
@@ -620,9 +623,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
     const float* xg = b.X[k - 1];
-    row_to_op<Tin>(HA, m, r, xg, D, 32 * h, valid, 32 * h, 32);
+    row_to_op<Tin>(HA, tile, r, xg, D, 32 * h, valid, 32 * h, 32);
     if (h >= 1) {
-      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
+      row_to_op<Tin>(HA, tile, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
     } else {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
@@ -640,13 +643,13 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       const float fc = s_fc[rr];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float x = valid ? xg[sidx(m, D, n0 + q, rr)] : 0.0f;
+        const float x = valid ? xg[sidx(tile, D, n0 + q, rr)] : 0.0f;
         o[q] = (x + fc * silu_b(v[q])) * kR2;
       }
       st16<Tin>(HA, rr, n0, o);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) b.X[k][sidx(m, D, n0 + q, rr)] = o[q];
+        for (int q = 0; q < 16; ++q) b.X[k][sidx(tile, D, n0 + q, rr)] = o[q];
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
     if (threadIdx.x < kT) {
@@ -712,7 +715,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         const int c = 4 * h + cc;
         float V[NLM], G[NLM];
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
         get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
         tp2_fwd_scalar(V, G, S + cc * NS);
       }
@@ -720,7 +723,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
     }
     const float* xg = b.X[L - 1];
-    row_to_op<Tin>(HA, m, r, xg, D, 32 * h, valid, 32 * h, 32);
+    row_to_op<Tin>(HA, tile, r, xg, D, 32 * h, valid, 32 * h, 32);
     if (h == 3) {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
@@ -738,7 +741,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       const float fc = s_fc[rr];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float x = valid ? xg[sidx(m, D, n0 + q, rr)] : 0.0f;
+        const float x = valid ? xg[sidx(tile, D, n0 + q, rr)] : 0.0f;
         o[q] = (x + fc * silu_b(v[q])) * kR2;
       }
       st16_op<Tin, kSplit>(HA, A1, rr, n0, o);
@@ -805,7 +808,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       tmem_ld16(lanes(tmem) + 288 + n0, dx);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) b.dX[sidx(m, D, n0 + q, rr)] = dh[q] + dx[q] * kR2;
+        for (int q = 0; q < 16; ++q) b.dX[sidx(tile, D, n0 + q, rr)] = dh[q] + dx[q] * kR2;
     });
     {
       float ds[16];                                    // columns D + 12 h ..: ds of channels 4h..4h+3
@@ -816,7 +819,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         float V[NLM], G[NLM], dV[NLM], dG[NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
-          V[lm] = valid ? b.V[L - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+          V[lm] = valid ? b.V[L - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
           dV[lm] = 0.0f;
           dG[lm] = 0.0f;
         }
@@ -826,7 +829,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
         if (valid)
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(m, CL, c * NLM + lm, r)] = dV[lm];
+          for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(tile, CL, c * NLM + lm, r)] = dV[lm];
       }
     }
     __syncthreads();
@@ -838,9 +841,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       b.epart[m.tile + m.atom[sg]] = acc;
     }
     if (threadIdx.x < kT && valid) {
-      b.dU[sidx(m, 1, 0, r)] = (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
+      b.dU[sidx(tile, 1, 0, r)] = (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(m, NLM, lm, r)] = 0.0f;
+      for (int lm = 0; lm < NLM; ++lm) b.dY[sidx(tile, NLM, lm, r)] = 0.0f;
     }
     seg_store(b.dgam[L], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
     __syncthreads();
@@ -885,7 +888,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    row_to_op<Tin>(HA, m, r, b.X[k], D, 32 * h, valid, 32 * h, 32);
+    row_to_op<Tin>(HA, tile, r, b.X[k], D, 32 * h, valid, 32 * h, 32);
     stage_g(b.dgam[k + 1], b.row_ptr, m, s_g);
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
     {
@@ -910,9 +913,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dy[lm];
     }
     mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
-    row_to_op<Tin>(HA, m, r, b.X[k - 1], D, 32 * h, valid, 32 * h, 32);
+    row_to_op<Tin>(HA, tile, r, b.X[k - 1], D, 32 * h, valid, 32 * h, 32);
     if (h >= 1) {
-      row_to_op<Tin>(HA, m, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
+      row_to_op<Tin>(HA, tile, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
     } else {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
@@ -933,7 +936,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
         tmem_ld16(lanes(tmem) + 160 + n0, z2);
         const float fc = s_fc[rr];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) dx[q] = dxe[q] + (valid ? dxg[sidx(m, D, n0 + q, rr)] : 0.0f);
+        for (int q = 0; q < 16; ++q) dx[q] = dxe[q] + (valid ? dxg[sidx(tile, D, n0 + q, rr)] : 0.0f);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           du = fmaf(dx[q], silu_b(z2[q]), du);
@@ -942,7 +945,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
         st16<Tin>(A1, rr, n0, o);
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] = dx[q] * kR2;
+          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] = dx[q] * kR2;
       });
       s_du[h * kT + r] = du * kR2;
     }
@@ -960,20 +963,20 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dh) {
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] += dh[q];
+          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] += dh[q];
       });
       float ds[16];                                   // ds columns 12 h .. 12 h + 11
       tmem_ld16(lanes(tmem) + 288 + 128 + 12 * h, ds);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 12; ++q) b.dS[sidx(m, C * NS, 12 * h + q, r)] = ds[q];
+        for (int q = 0; q < 12; ++q) b.dS[sidx(tile, C * NS, 12 * h + q, r)] = ds[q];
     }
     __syncthreads();
     if (threadIdx.x < kT && valid) {
-      b.dU[sidx(m, 1, 0, r)] += (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
+      b.dU[sidx(tile, 1, 0, r)] += (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        b.dY[sidx(m, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
+        b.dY[sidx(tile, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
                                      (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]);
     }
     __syncthreads();
@@ -1022,12 +1025,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     for (int lm = 0; lm < NLM; ++lm) {
       float v4[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v4[q] = valid ? b.dV[sidx(m, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
+      for (int q = 0; q < 4; ++q) v4[q] = valid ? b.dV[sidx(tile, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
       st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), v4);
     }
     stage_g(b.gam[k], b.row_ptr, m, s_g);
     if (k == 1) {
-      row_to_op<Tin>(X, m, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
+      row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
       mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });       // w0
     }
     float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc * 3 + l]
@@ -1062,7 +1065,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
           for (int g = 0; g < 4; ++g) tmem_wait4(t + 4 * g);
 #pragma unroll
           for (int q = 0; q < 3; ++q)
-            dT[q] = __uint_as_float(t[q]) + (valid ? dsg[sidx(m, C * NS, c * NS + q, r)] : 0.0f);
+            dT[q] = __uint_as_float(t[q]) + (valid ? dsg[sidx(tile, C * NS, c * NS + q, r)] : 0.0f);
 #pragma unroll
           for (int mm1 = 0; mm1 < 3; ++mm1)
 #pragma unroll
@@ -1083,7 +1086,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
           for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[c4 * 3 + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(m, CL, c * NLM + lm, r)] : 0.0f;
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
         }
         get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
 #pragma unroll
@@ -1099,7 +1102,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
           if (valid)
 #pragma unroll
             for (int lm = 0; lm < NLM; ++lm) {
-              float* dv = &b.dV[sidx(m, CL, c * NLM + lm, r)];
+              float* dv = &b.dV[sidx(tile, CL, c * NLM + lm, r)];
               *dv = round == 0 ? dVp[lm] : *dv + dVp[lm];
             }
         } else {
@@ -1119,7 +1122,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       epi(tmem, 384, 128, [&](int rr, int n0, const float* v) {
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(m, D, n0 + q, rr)] += v[q];
+          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] += v[q];
       });
     }
 #pragma unroll
@@ -1128,7 +1131,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     if (threadIdx.x < kT && valid && k == 1) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        b.dY[sidx(m, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
+        b.dY[sidx(tile, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
                                      (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]);
     }
     seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
@@ -1258,7 +1261,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
         const float fc = s_geo[rr * GP + 4];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const float dx = dxe[q] + (valid ? dxg[sidx(m, D, n0 + q, rr)] : 0.0f);
+          const float dx = dxe[q] + (valid ? dxg[sidx(tile, D, n0 + q, rr)] : 0.0f);
           du = fmaf(dx, silu_b(z2[q]), du);
           o[q] = dx * fc * dsilu_b(z2[q]);
         }
@@ -1292,12 +1295,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
         const float u[3] = {g[0], g[1], g[2]};
         const float d = g[3], dfc = g[5];
         const size_t pp = (size_t)(m.p0 + r);
-        float gd = ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]) + b.dU[sidx(m, 1, 0, r)]) * dfc;
+        float gd = ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]) + b.dU[sidx(tile, 1, 0, r)]) * dfc;
 #pragma unroll
         for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * GP + n], gd);
         float dY[NLM];
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[sidx(m, NLM, lm, r)];
+        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[sidx(tile, NLM, lm, r)];
         float gu[3];
         sph_harm_vjp<2>(u[0], u[1], u[2], dY, gu);
         const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];

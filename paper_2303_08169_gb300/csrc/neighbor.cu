@@ -171,6 +171,10 @@ k_count(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __
   if ((threadIdx.x & 31) == 0) row_cnt[i] = cnt;
 }
 
+// rows of up to kRowCap pairs are ranked in shared memory (every lane reads
+// the same key at a time: broadcasts); longer rows use the global key buffer
+constexpr int kRowCap = 192;
+
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_fill(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __restrict__ w64,
        const int* __restrict__ atom_cell, const int* __restrict__ cell_start,
@@ -178,6 +182,7 @@ k_fill(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __r
        const int* __restrict__ n_pairs, int64_t capacity, unsigned long long* __restrict__ keys,
        unsigned long long* __restrict__ skeys, int* __restrict__ pi, int* __restrict__ pj,
        int* __restrict__ pcode, int* __restrict__ flags) {
+  __shared__ unsigned long long s_keys[kWarpsPerBlock][kRowCap];
   if ((int64_t)(*n_pairs) > capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, kFlagPairOverflow);
     return;
@@ -187,6 +192,7 @@ k_fill(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __r
   const int lane = threadIdx.x & 31;
   const int base = row_ptr[i];
   const int len = row_ptr[i + 1] - base;
+  unsigned long long* kb = len <= kRowCap ? s_keys[threadIdx.x >> 5] : keys + base;
   int cnt = 0;
   for_each_candidate(i, g, w32, w64, atom_cell, cell_start, cell_atoms, n_atoms,
                      [&](bool hit, int j, const int* n) {
@@ -194,25 +200,21 @@ k_fill(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __r
                        if (hit) {
                          const int pos = cnt + __popc(m & ((1u << lane) - 1u));
                          if (pos < len)
-                           keys[base + pos] = ((unsigned long long)j << 7) |
-                                              (unsigned long long)img_code(n[0], n[1], n[2]);
+                           kb[pos] = ((unsigned long long)j << 7) | (unsigned long long)img_code(n[0], n[1], n[2]);
                        }
                        cnt += __popc(m);
                      });
   __syncwarp();
-  // rank sort of the row (keys are unique within a row)
+  // rank sort of the row (keys are unique within a row); outputs written at
+  // their rank
   for (int e = lane; e < len; e += 32) {
-    const unsigned long long k = keys[base + e];
+    const unsigned long long k = kb[e];
     int rank = 0;
-    for (int t = 0; t < len; ++t) rank += keys[base + t] < k ? 1 : 0;
+    for (int t = 0; t < len; ++t) rank += kb[t] < k ? 1 : 0;
     skeys[base + rank] = k;
-  }
-  __syncwarp();
-  for (int e = lane; e < len; e += 32) {
-    const unsigned long long k = skeys[base + e];
-    pi[base + e] = i;
-    pj[base + e] = (int)(k >> 7);
-    pcode[base + e] = (int)(k & 127ull);
+    pi[base + rank] = i;
+    pj[base + rank] = (int)(k >> 7);
+    pcode[base + rank] = (int)(k & 127ull);
   }
 }
 
