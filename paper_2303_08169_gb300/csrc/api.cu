@@ -479,14 +479,16 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
     c->dfree(pb.dgam[k]);
     pb.gam[k] = pb.dgam[k] = nullptr;
   }
-  // per-pair arrays of the BF16 path are tile-SoA over 128-pair tiles
+  // per-pair arrays of the tensor-core path are tile-SoA over 128-pair tiles;
+  // every per-pair array holds whole tiles (the passes prefetch the next
+  // tile's slices into L2)
   const int64_t capr = (cap + 127) / 128 * 128;
-  c->nb.pi = c->dalloc<int>(cap);
-  c->nb.pj = c->dalloc<int>(cap);
-  c->nb.pcode = c->dalloc<int>(cap);
-  c->nb.rev = c->dalloc<int>(cap);
-  c->nb.keys = c->dalloc<unsigned long long>(cap);
-  c->nb.skeys = c->dalloc<unsigned long long>(cap);
+  c->nb.pi = c->dalloc<int>(capr);
+  c->nb.pj = c->dalloc<int>(capr);
+  c->nb.pcode = c->dalloc<int>(capr);
+  c->nb.rev = c->dalloc<int>(capr);
+  c->nb.keys = c->dalloc<unsigned long long>(capr);
+  c->nb.skeys = c->dalloc<unsigned long long>(capr);
   bool ok = c->nb.pi && c->nb.pj && c->nb.pcode && c->nb.rev && c->nb.keys && c->nb.skeys;
   for (uint32_t k = 0; k < B.L && ok; ++k) {
     pb.X[k] = c->dalloc<float>((size_t)capr * c->D);

@@ -182,6 +182,20 @@ AL_DEV void load_g(const float* __restrict__ part, const int* __restrict__ row_p
 // offsets fold into the load/store immediates)
 AL_DEV size_t sidx(int tile, int W, int f, int r) { return ((size_t)tile * W + f) * kT + r; }
 
+// L2 prefetch of tile nt's block of a tile-SoA array (W features x 128 rows,
+// contiguous) and of its slice of the neighbour list: issued by one thread
+// one tile ahead, so that the next tile's loads hit L2
+AL_DEV void prefetch_rows(const float* a, int W, int nt) {
+  const char* p = reinterpret_cast<const char*>(a + (size_t)nt * W * kT);
+  const uint32_t bytes = (uint32_t)W * kT * 4;
+  for (uint32_t o = 0; o < bytes; o += 32768u) bulk_prefetch_l2(p + o, min(32768u, bytes - o));
+}
+AL_DEV void prefetch_meta(const PassBufs& b, int nt) {
+  bulk_prefetch_l2(b.pi + (size_t)nt * kT, kT * 4);
+  bulk_prefetch_l2(b.pj + (size_t)nt * kT, kT * 4);
+  bulk_prefetch_l2(b.pcode + (size_t)nt * kT, kT * 4);
+}
+
 // Gamma (or dGamma) of the tile's first kSegCap centre atoms, summed once per
 // tile into shared memory; rows of later segments read the partials directly.
 constexpr int kSegCap = 8;
@@ -439,6 +453,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
   float* s_e = s_Y + kT * NLM;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+    }
     if (threadIdx.x < kT) {
       const int r = threadIdx.x;
       float h0[16], Y[NLM], fc = 0.0f;
@@ -514,6 +532,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+      if (k == 1) prefetch_rows(b.X[0], D, nt);
+      else prefetch_rows(b.V[k - 1], CL, nt);
+    }
     if (threadIdx.x < kT) {
       float u[3], d, fc, dfc, Y[NLM];
 #pragma unroll
@@ -612,6 +636,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+      prefetch_rows(b.X[k - 1], D, nt);
+      prefetch_rows(b.S[k], C * NS, nt);
+    }
     const bool valid = r < m.np;
     if (threadIdx.x < kT) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
@@ -699,6 +729,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+      prefetch_rows(b.V[L - 1], CL, nt);
+      prefetch_rows(b.X[L - 1], D, nt);
+    }
     const bool valid = r < m.np;
     if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
@@ -878,6 +914,16 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+      prefetch_rows(b.X[k], D, nt);
+      prefetch_rows(b.X[k - 1], D, nt);
+      prefetch_rows(b.S[k], C * NS, nt);
+      prefetch_rows(b.dX, D, nt);
+      prefetch_rows(b.dU, 1, nt);
+      prefetch_rows(b.dY, NLM, nt);
+    }
     const bool valid = r < m.np;
     if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
@@ -1011,6 +1057,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+      prefetch_rows(b.dV, CL, nt);
+      prefetch_rows(b.dS, C * NS, nt);
+      if (k == 1) {
+        prefetch_rows(b.X[0], D, nt);
+        prefetch_rows(b.dX, D, nt);
+        prefetch_rows(b.dY, NLM, nt);
+      } else {
+        prefetch_rows(b.V[k - 1], CL, nt);
+      }
+    }
     const bool valid = r < m.np;
     if (h == 0) {
       float u[3], d, fc, dfc, Y[NLM];
@@ -1179,6 +1238,13 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      const int nt = tile + (int)gridDim.x;
+      prefetch_meta(b, nt);
+      prefetch_rows(b.dX, D, nt);
+      prefetch_rows(b.dU, 1, nt);
+      prefetch_rows(b.dY, NLM, nt);
+    }
     const bool valid = r < m.np;
     if (threadIdx.x < kT) {
       float h0[16], Y[NLM], u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f, B[NB], dB[NB];

@@ -132,6 +132,12 @@ UM_DEV void bulk_g2s(void* smem, const void* gmem, uint32_t bytes, uint64_t* mba
       : "memory");
 }
 
+// Hint only: bring [gmem, gmem + bytes) into L2 (16-byte aligned, bytes a
+// multiple of 16); nothing waits for it.
+UM_DEV void bulk_prefetch_l2(const void* gmem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
+
 // ---- MMA ----
 UM_DEV void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t acc) {
   asm volatile(
