@@ -21,6 +21,7 @@
 // FP32.  Per-atom sums use the per-(tile, atom) partials of the FP32 path with
 // 128-pair tiles.
 #include <cstdio>
+#include <cstring>
 
 #include "common.cuh"
 #include "model.h"
@@ -67,11 +68,26 @@ template <> struct Op<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   static AL_DEV uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
   static AL_DEV float round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+  // (a, b) rounded into one 32-bit word, a in the low half; one conversion
+  static AL_DEV uint32_t pack2(float a, float b, float2* back = nullptr) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    if (back) *back = __bfloat1622float2(h);
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+  }
 };
 template <> struct Op<__half> {
   static constexpr uint32_t fmt = 0;
   static AL_DEV uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
   static AL_DEV float round(float x) { return __half2float(__float2half_rn(x)); }
+  static AL_DEV uint32_t pack2(float a, float b, float2* back = nullptr) {
+    const __half2 h = __floats2half2_rn(a, b);
+    if (back) *back = __half22float2(h);
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+  }
 };
 
 // Split operands (the two-body MLP and the energy hidden layer in the split
@@ -305,8 +321,21 @@ template <class Tin>
 AL_DEV void st8(uint8_t* A, uint32_t off, const float* v) {
   uint32_t w[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) w[q] = (uint32_t)Op<Tin>::bits(v[2 * q]) | ((uint32_t)Op<Tin>::bits(v[2 * q + 1]) << 16);
+  for (int q = 0; q < 4; ++q) w[q] = Op<Tin>::pack2(v[2 * q], v[2 * q + 1]);
   *reinterpret_cast<uint4*>(A + off) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+// v = hi + lo: hi into Ahi at off, lo into Alo at off_lo (8 elements each)
+template <class Tin>
+AL_DEV void st8_split(uint8_t* Ahi, uint32_t off, uint8_t* Alo, uint32_t off_lo, const float* v) {
+  uint32_t wh[4], wl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 hb;
+    wh[q] = Op<Tin>::pack2(v[2 * q], v[2 * q + 1], &hb);
+    wl[q] = Op<Tin>::pack2(v[2 * q] - hb.x, v[2 * q + 1] - hb.y);
+  }
+  *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+  *reinterpret_cast<uint4*>(Alo + off_lo) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
 }
 template <class Tin>
 AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
@@ -315,21 +344,16 @@ AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
 }
 template <class Tin>
 AL_DEV void st4(uint8_t* A, uint32_t off, const float* v) {
-  const uint32_t w0 = (uint32_t)Op<Tin>::bits(v[0]) | ((uint32_t)Op<Tin>::bits(v[1]) << 16);
-  const uint32_t w1 = (uint32_t)Op<Tin>::bits(v[2]) | ((uint32_t)Op<Tin>::bits(v[3]) << 16);
+  const uint32_t w0 = Op<Tin>::pack2(v[0], v[1]);
+  const uint32_t w1 = Op<Tin>::pack2(v[2], v[3]);
   *reinterpret_cast<uint2*>(A + off) = make_uint2(w0, w1);
 }
 // hi part into Ahi, lo part into Alo (same row and columns)
 template <class Tin>
 AL_DEV void st16_split(uint8_t* Ahi, uint8_t* Alo, int r, int c0, const float* v) {
-  float hi[16], lo[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    hi[q] = Op<Tin>::round(v[q]);
-    lo[q] = v[q] - hi[q];
-  }
-  st16<Tin>(Ahi, r, c0, hi);
-  st16<Tin>(Alo, r, c0, lo);
+  const uint32_t o0 = sw128_off(r, c0, 128), o1 = sw128_off(r, c0 + 8, 128);
+  st8_split<Tin>(Ahi, o0, Alo, o0, v);
+  st8_split<Tin>(Ahi, o1, Alo, o1, v + 8);
 }
 // operand store of an epilogue: hi (and lo) parts in split mode
 template <class Tin, bool kSplit>
@@ -408,7 +432,7 @@ AL_DEV void st_h0(uint8_t* H0, int r, const float* h0) {
       hi[q] = Op<Tin>::round(h0[q]);
       lo[q] = h0[q] - hi[q];
     }
-    st16<Tin>(H0, r, 0, hi);
+    st16<Tin>(H0, r, 0, hi);                          // rounding hi again is exact
     st16<Tin>(H0, r, 16, lo);
     st16<Tin>(H0, r, 32, hi);
   } else {
@@ -796,14 +820,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       }
       s_eq[h * kT + r] = valid ? e : 0.0f;
       if (kSplit) {                                   // hi in columns 0..31, lo in 32..63
-        float hi[8], lo[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          hi[q] = Op<Tin>::round(dz[q]);
-          lo[q] = dz[q] - hi[q];
-        }
-        st8<Tin>(AE, sw128_off(r, 8 * h, 128), hi);
-        st8<Tin>(AE, sw128_off(r, 32 + 8 * h, 128), lo);
+        st8_split<Tin>(AE, sw128_off(r, 8 * h, 128), AE, sw128_off(r, 32 + 8 * h, 128), dz);
       } else {
         st8<Tin>(AE, sw128_off(r, 8 * h, 128), dz);
       }
