@@ -118,8 +118,11 @@ AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
   const int t = threadIdx.x;
   const int p0 = tile * kT;
   const int np = min(kT, P - p0);
+  bool head = false;
+  unsigned mask = 0u;
+  int i = -1;
+  // (every pass ends its tile with a barrier, so the previous tile is done with m)
   if (t < kT) {
-    int i = -1;
     if (t < np) {
       i = b.pi[p0 + t];
       m.pi[t] = i;
@@ -132,32 +135,23 @@ AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
     }
     int prev = __shfl_up_sync(0xffffffffu, i, 1);
     if ((t & 31) == 0) prev = (t > 0 && t - 1 < np) ? b.pi[p0 + t - 1] : -1;
-    const bool head = t < np && (t == 0 || i != prev);
-    const unsigned mask = __ballot_sync(0xffffffffu, head);
+    head = t < np && (t == 0 || i != prev);          // first pair of a centre atom's run
+    mask = __ballot_sync(0xffffffffu, head);
     if ((t & 31) == 0) m.wc[t >> 5] = __popc(mask);
-    __syncwarp();
-    m.seg[t] = 0;
-    // stash the ballot in sstart temporarily is not needed: recompute below
-    m.atom[t] = head ? 1 : 0;
   }
   __syncthreads();
   if (t < kT) {
     int base = 0;
     for (int w = 0; w < (t >> 5); ++w) base += m.wc[w];
-    const bool head = m.atom[t] != 0;
-    const unsigned mask = __ballot_sync(0xffffffffu, head);
     const unsigned below = (t & 31) == 31 ? 0xffffffffu : ((2u << (t & 31)) - 1u);
-    const int s = base + __popc(mask & below) - 1;
-    m.seg[t] = t < np ? s : 0;
-    __syncwarp();
-    if (head) m.sstart[s] = t;
-  }
-  __syncthreads();
-  if (t < kT) {
-    // atom of each segment (read pi of the segment's first pair)
-    const int nseg = m.wc[0] + m.wc[1] + m.wc[2] + m.wc[3];
-    if (t < nseg) m.atom[t] = m.pi[m.sstart[t]];
+    const int sg = base + __popc(mask & below) - 1;
+    m.seg[t] = t < np ? sg : 0;
+    if (head) {
+      m.sstart[sg] = t;
+      m.atom[sg] = i;
+    }
     if (t == 0) {
+      const int nseg = m.wc[0] + m.wc[1] + m.wc[2] + m.wc[3];
       m.nseg = nseg;
       m.np = np;
       m.p0 = p0;
@@ -310,6 +304,13 @@ AL_DEV void epi(uint32_t tmem, int col0, int N, F&& f) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   const int w = N / (int)(blockDim.x >> 7);
   const uint32_t base = lanes(tmem);
+  if (w == 32) {                                     // one 32-column load and wait
+    float v[32];
+    tmem_ld32(base + (uint32_t)(col0 + 32 * h), v);
+    f(r, 32 * h, v);
+    f(r, 32 * h + 16, v + 16);
+    return;
+  }
   for (int n0 = h * w; n0 < (h + 1) * w; n0 += 16) {
     float v[16];
     tmem_ld16(base + (uint32_t)(col0 + n0), v);
