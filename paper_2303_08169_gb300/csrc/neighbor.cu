@@ -72,14 +72,15 @@ __global__ void k_cell_fill(int n, const int* __restrict__ atom_cell,
 }
 
 // Exact FP64 membership test (the defining rule).
-AL_DEV bool exact_in(const double* __restrict__ w, int i, int j, const int n[3], const GridInfo& g) {
-  double d[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    d[a] = __dadd_rn(__dsub_rn(w[3 * j + a], w[3 * i + a]), (double)n[a] * g.L[a]);
-  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
-                              __dmul_rn(d[2], d[2]));
-  return d2 < __dmul_rn(g.rc, g.rc);
+// Not inlined: a real call is taken only by warps with a candidate in the band,
+// instead of predicated FP64 work on every candidate (FP64 is slow on this part).
+__device__ __noinline__ bool exact_in(const double* __restrict__ w, int i, int j, int nx, int ny, int nz,
+                                     double Lx, double Ly, double Lz, double rc) {
+  const double dx = __dadd_rn(__dsub_rn(w[3 * j], w[3 * i]), (double)nx * Lx);
+  const double dy = __dadd_rn(__dsub_rn(w[3 * j + 1], w[3 * i + 1]), (double)ny * Ly);
+  const double dz = __dadd_rn(__dsub_rn(w[3 * j + 2], w[3 * i + 2]), (double)nz * Lz);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  return d2 < __dmul_rn(rc, rc);
 }
 
 // Visit every candidate (j, n) of centre i, lanes striding over candidates.
@@ -123,7 +124,7 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
           const bool self = (j == i) && n[0] == 0 && n[1] == 0 && n[2] == 0;
           if (!self) {
             if (d2 < lo) hit = true;
-            else if (d2 <= hi) hit = exact_in(w64, i, j, n, g);
+            else if (d2 <= hi) hit = exact_in(w64, i, j, n[0], n[1], n[2], g.L[0], g.L[1], g.L[2], g.rc);
           }
         }
         f(hit, j, n);
@@ -151,7 +152,7 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
         const bool self = (j == i) && n[0] == 0 && n[1] == 0 && n[2] == 0;
         if (!self) {
           if (d2 < lo) hit = true;
-          else if (d2 <= hi) hit = exact_in(w64, i, j, n, g);
+          else if (d2 <= hi) hit = exact_in(w64, i, j, n[0], n[1], n[2], g.L[0], g.L[1], g.L[2], g.rc);
         }
       }
       f(hit, j, n);
