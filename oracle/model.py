@@ -65,8 +65,12 @@ class OracleModel:
     path, used to check that path separately from the sensitivity of the
     model to rounding.  "fp16split" is "fp16" with the two-body MLP and the
     energy hidden layer left unrounded (the tensor-core path splits their
-    operands into two FP16 parts, which carry about 22 bits).  The energy
-    output layer, tensor products and all elementwise steps stay FP64."""
+    operands into two FP16 parts, which carry about 22 bits).  In every
+    emulation mode the per-pair values that the tensor-core path keeps in
+    FP16 between its passes (x^k and the tensor-product scalars of layers
+    k < L, V^k) are rounded to FP16 in the forward direction only (their
+    gradients stay FP32 there).  The energy output layer, tensor products and
+    all elementwise steps stay FP64."""
 
     def __init__(self, blob, emulate=None):
         cfg, w, names = read_blob(blob)
@@ -91,6 +95,12 @@ class OracleModel:
 
     def _q(self, x):
         return x if self._qdt is None else x.to(self._qdt).to(F64)
+
+    def _qs(self, x):
+        """Emulation: FP16 storage of a forward value (gradient unchanged)."""
+        if self._qdt is None:
+            return x
+        return x + (x.to(torch.float16).to(F64) - x).detach()
 
     def _qlin(self, x, W, extra=1.0):
         """Linear layer; in emulation mode the GEMM operands are rounded."""
@@ -150,7 +160,7 @@ class OracleModel:
         onehot = torch.eye(S, dtype=F64)
         h = torch.cat([onehot[Z[i]], onehot[Z[j]], B], dim=1)
         nlat = len(cfg["latent"])
-        x = fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)], exact=self._split)
+        x = self._qs(fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)], exact=self._split))
         w0 = self._qlin(x, w["embed"]).view(P, C, lmax + 1)
         V = [w0[:, :, l, None] * Y[l][:, None, :] for l in range(lmax + 1)]
         for layer in range(1, self.L + 1):
@@ -184,10 +194,14 @@ class OracleModel:
                     else:
                         Wq = self._q(Wm / math.sqrt(C * len(ps)))
                         newV.append(torch.einsum("oi,pim->pom", Wq, self._q(Tl)))
-                V = newV
+                V = [self._qs(v) for v in newV]
+            if not last:
+                s = self._qs(s)
             m = self._mlp(torch.cat([x, s], dim=1),
                           [w[f"layer{layer}.latent.{k}"] for k in range(nlat)])
             x = (x + fc[:, None] * m) / math.sqrt(2.0)
+            if not last:
+                x = self._qs(x)
         ne = len(cfg["energy"])
         hdn = self._mlp(x, [w[f"energy.{k}"] for k in range(ne)], exact=self._split)
         Eij = self._lin(hdn, w["energy.out"])[:, 0]

@@ -192,12 +192,31 @@ AL_DEV void load_g(const float* __restrict__ part, const int* __restrict__ row_p
 // offsets fold into the load/store immediates)
 AL_DEV size_t sidx(int tile, int W, int f, int r) { return ((size_t)tile * W + f) * kT + r; }
 
+// The forward per-pair state of these passes (x^k, S^k, V^k) is stored in
+// FP16 between passes, two features per 32-bit word in tile-SoA order: word
+// (tile, f / 2, r) holds features f (low half) and f + 1 (high half) of tile
+// row r.  V^k is stored component-major (feature lm C + c), so that two
+// neighbouring channels share a word.  Gradients stay FP32.  (The buffers are
+// the FP32 path's, of which these passes use the first half.)
+AL_DEV size_t hidx(int tile, int W, int f, int r) { return ((size_t)tile * (W >> 1) + (f >> 1)) * kT + r; }
+// the stored value: producers that also feed an operand use it too, so that
+// every consumer of x^k sees the same (FP16) value
+AL_DEV float r16(float x) { return __half2float(__float2half_rn(x)); }
+AL_DEV float2 ldh2(const float* a, size_t i) { return __half22float2(reinterpret_cast<const __half2*>(a)[i]); }
+AL_DEV void sth2(float* a, size_t i, float x, float y) { reinterpret_cast<__half2*>(a)[i] = __floats2half2_rn(x, y); }
+
 // L2 prefetch of tile nt's block of a tile-SoA array (W features x 128 rows,
 // contiguous) and of its slice of the neighbour list: issued by one thread
 // one tile ahead, so that the next tile's loads hit L2
 AL_DEV void prefetch_rows(const float* a, int W, int nt) {
   const char* p = reinterpret_cast<const char*>(a + (size_t)nt * W * kT);
   const uint32_t bytes = (uint32_t)W * kT * 4;
+  for (uint32_t o = 0; o < bytes; o += 32768u) bulk_prefetch_l2(p + o, min(32768u, bytes - o));
+}
+// the same for an FP16-pair array (W features, W / 2 words per row)
+AL_DEV void prefetch_rows_h(const float* a, int W, int nt) {
+  const char* p = reinterpret_cast<const char*>(a) + (size_t)nt * (W / 2) * kT * 4;
+  const uint32_t bytes = (uint32_t)(W / 2) * kT * 4;
   for (uint32_t o = 0; o < bytes; o += 32768u) bulk_prefetch_l2(p + o, min(32768u, bytes - o));
 }
 AL_DEV void prefetch_meta(const PassBufs& b, int nt) {
@@ -367,8 +386,8 @@ AL_DEV void st1(uint8_t* A, int r, int c, float v) {
   *reinterpret_cast<uint16_t*>(A + sw128_off(r, c, 128)) = Op<Tin>::bits(v);
 }
 
-// features [f0, f0+n) of tile row r of a tile-SoA FP32 array (W wide),
-// converted into operand columns [c0, c0+n)
+// features [f0, f0+n) (f0 even) of tile row r of an FP16-pair array (W
+// wide), into operand columns [c0, c0+n)
 template <class Tin>
 AL_DEV void row_to_op(uint8_t* A, int tile, int r, const float* __restrict__ g, int W, int f0, bool valid,
                       int c0, int n) {
@@ -376,7 +395,11 @@ AL_DEV void row_to_op(uint8_t* A, int tile, int r, const float* __restrict__ g, 
   for (int k = 0; k < n; k += 16) {
     float v[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = valid ? g[sidx(tile, W, f0 + k + q, r)] : 0.0f;
+    for (int q = 0; q < 16; q += 2) {
+      const float2 t = valid ? ldh2(g, hidx(tile, W, f0 + k + q, r)) : make_float2(0.0f, 0.0f);
+      v[q] = t.x;
+      v[q + 1] = t.y;
+    }
     st16<Tin>(A, r, c0 + k, v);
   }
 }
@@ -519,11 +542,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       float o[16];
       const float fc = s_fc[r];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
+      for (int q = 0; q < 16; ++q) o[q] = r16(fc * silu_b(v[q]));
       st16<Tin>(X, r, n0, o);
       if (r < m.np)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) b.X[0][sidx(tile, D, n0 + q, r)] = o[q];
+        for (int q = 0; q < 16; q += 2) sth2(b.X[0], hidx(tile, D, n0 + q, r), o[q], o[q + 1]);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
     if (threadIdx.x < kT) {
@@ -560,8 +583,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
-      if (k == 1) prefetch_rows(b.X[0], D, nt);
-      else prefetch_rows(b.V[k - 1], CL, nt);
+      if (k == 1) prefetch_rows_h(b.X[0], D, nt);
+      else prefetch_rows_h(b.V[k - 1], CL, nt);
     }
     if (threadIdx.x < kT) {
       float u[3], d, fc, dfc, Y[NLM];
@@ -597,15 +620,21 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
           for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[(cc + e) * 3 + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
+          for (int lm = 0; lm < NLM; ++lm) {
+            const float2 t = valid ? ldh2(b.V[k - 1], hidx(tile, CL, lm * C + (c & ~1), r)) : make_float2(0.f, 0.f);
+            V[lm] = (c & 1) ? t.y : t.x;
+          }
         }
         get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
         tp2_fwd(V, G, Tv[e]);
 #pragma unroll
         for (int q = 0; q < NS; ++q) st1<Tin>(T, r, c * NS + q, Tv[e][q]);
-        if (valid)
-#pragma unroll
-          for (int q = 0; q < NS; ++q) b.S[k][sidx(tile, C * NS, c * NS + q, r)] = Tv[e][q];
+      }
+      if (valid) {                                    // S of channels c0, c0 + 1: features 3 c0 .. 3 c0 + 5
+        const int f0 = (4 * h + cc) * NS;
+        sth2(b.S[k], hidx(tile, C * NS, f0, r), Tv[0][0], Tv[0][1]);
+        sth2(b.S[k], hidx(tile, C * NS, f0 + 2, r), Tv[0][2], Tv[1][0]);
+        sth2(b.S[k], hidx(tile, C * NS, f0 + 4, r), Tv[1][1], Tv[1][2]);
       }
       const int c0 = 4 * h + cc;
 #pragma unroll
@@ -632,7 +661,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
         tmem_ld16(base + 64 + 16 * j, v);
         if (valid)
 #pragma unroll
-          for (int co = 0; co < C; ++co) b.V[k][sidx(tile, CL, co * NLM + j, r)] = v[co];
+          for (int co = 0; co < C; co += 2) sth2(b.V[k], hidx(tile, CL, j * C + co, r), v[co], v[co + 1]);
       }
     }
     __syncthreads();
@@ -664,8 +693,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
-      prefetch_rows(b.X[k - 1], D, nt);
-      prefetch_rows(b.S[k], C * NS, nt);
+      prefetch_rows_h(b.X[k - 1], D, nt);
+      prefetch_rows_h(b.S[k], C * NS, nt);
     }
     const bool valid = r < m.np;
     if (threadIdx.x < kT) {
@@ -697,14 +726,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       float o[16];
       const float fc = s_fc[rr];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float x = valid ? xg[sidx(tile, D, n0 + q, rr)] : 0.0f;
-        o[q] = (x + fc * silu_b(v[q])) * kR2;
+      for (int q = 0; q < 16; q += 2) {
+        const float2 x = valid ? ldh2(xg, hidx(tile, D, n0 + q, rr)) : make_float2(0.f, 0.f);
+        o[q] = r16((x.x + fc * silu_b(v[q])) * kR2);
+        o[q + 1] = r16((x.y + fc * silu_b(v[q + 1])) * kR2);
       }
       st16<Tin>(HA, rr, n0, o);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) b.X[k][sidx(tile, D, n0 + q, rr)] = o[q];
+        for (int q = 0; q < 16; q += 2) sth2(b.X[k], hidx(tile, D, n0 + q, rr), o[q], o[q + 1]);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
     if (threadIdx.x < kT) {
@@ -757,8 +787,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
-      prefetch_rows(b.V[L - 1], CL, nt);
-      prefetch_rows(b.X[L - 1], D, nt);
+      prefetch_rows_h(b.V[L - 1], CL, nt);
+      prefetch_rows_h(b.X[L - 1], D, nt);
     }
     const bool valid = r < m.np;
     if (h == 0) {
@@ -772,13 +802,20 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     {
       float S[4 * NS];                                 // columns D + 12 h .. D + 12 h + 11
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int c = 4 * h + cc;
-        float V[NLM], G[NLM];
+      for (int cp = 0; cp < 4; cp += 2) {             // channel pairs share the V words
+        float V2[2][NLM];
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[L - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
-        get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
-        tp2_fwd_scalar(V, G, S + cc * NS);
+        for (int lm = 0; lm < NLM; ++lm) {
+          const float2 t = valid ? ldh2(b.V[L - 1], hidx(tile, CL, lm * C + 4 * h + cp, r)) : make_float2(0.f, 0.f);
+          V2[0][lm] = t.x;
+          V2[1][lm] = t.y;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          float G[NLM];
+          get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, 4 * h + cp + e, G);
+          tp2_fwd_scalar(V2[e], G, S + (cp + e) * NS);
+        }
       }
 #pragma unroll
       for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
@@ -801,9 +838,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       float o[16];
       const float fc = s_fc[rr];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float x = valid ? xg[sidx(tile, D, n0 + q, rr)] : 0.0f;
-        o[q] = (x + fc * silu_b(v[q])) * kR2;
+      for (int q = 0; q < 16; q += 2) {
+        const float2 x = valid ? ldh2(xg, hidx(tile, D, n0 + q, rr)) : make_float2(0.f, 0.f);
+        o[q] = (x.x + fc * silu_b(v[q])) * kR2;
+        o[q + 1] = (x.y + fc * silu_b(v[q + 1])) * kR2;
       }
       st16_op<Tin, kSplit>(HA, A1, rr, n0, o);
     });
@@ -873,7 +911,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         float V[NLM], G[NLM], dV[NLM], dG[NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
-          V[lm] = valid ? b.V[L - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
+          const float2 t = valid ? ldh2(b.V[L - 1], hidx(tile, CL, lm * C + (c & ~1), r)) : make_float2(0.f, 0.f);
+          V[lm] = (cc & 1) ? t.y : t.x;
           dV[lm] = 0.0f;
           dG[lm] = 0.0f;
         }
@@ -935,9 +974,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
-      prefetch_rows(b.X[k], D, nt);
-      prefetch_rows(b.X[k - 1], D, nt);
-      prefetch_rows(b.S[k], C * NS, nt);
+      prefetch_rows_h(b.X[k], D, nt);
+      prefetch_rows_h(b.X[k - 1], D, nt);
+      prefetch_rows_h(b.S[k], C * NS, nt);
       prefetch_rows(b.dX, D, nt);
       prefetch_rows(b.dU, 1, nt);
       prefetch_rows(b.dY, NLM, nt);
@@ -1081,11 +1120,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       prefetch_rows(b.dV, CL, nt);
       prefetch_rows(b.dS, C * NS, nt);
       if (k == 1) {
-        prefetch_rows(b.X[0], D, nt);
+        prefetch_rows_h(b.X[0], D, nt);
         prefetch_rows(b.dX, D, nt);
         prefetch_rows(b.dY, NLM, nt);
       } else {
-        prefetch_rows(b.V[k - 1], CL, nt);
+        prefetch_rows_h(b.V[k - 1], CL, nt);
       }
     }
     const bool valid = r < m.np;
@@ -1163,7 +1202,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
           for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[c4 * 3 + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = valid ? b.V[k - 1][sidx(tile, CL, c * NLM + lm, r)] : 0.0f;
+          for (int lm = 0; lm < NLM; ++lm) {
+            const float2 t = valid ? ldh2(b.V[k - 1], hidx(tile, CL, lm * C + (c & ~1), r)) : make_float2(0.f, 0.f);
+            V[lm] = (c4 & 1) ? t.y : t.x;
+          }
         }
         get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
 #pragma unroll
@@ -1305,7 +1347,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       float o[16];
       const float fc = s_geo[rr * GP + 4];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = fc * silu_b(v[q]);
+      for (int q = 0; q < 16; ++q) o[q] = r16(fc * silu_b(v[q]));   // as pass A
       st16<Tin>(X, rr, n0, o);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });      // e^1

