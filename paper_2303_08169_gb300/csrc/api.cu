@@ -127,6 +127,27 @@ struct WInfo {
   bool has_t;
 };
 
+// Training batch (see build_batch): concatenated neighbour lists and atoms
+// of all structures, and the per-atom / per-structure loss buffers.
+struct TrainBatch {
+  BatchArrays a{};
+  int n_structs = 0;
+  int64_t n_atoms = 0, n_pairs = 0;
+  int64_t cap_atoms = 0, cap_pairs = 0;
+  int cap_structs = 0;
+  int* d_np = nullptr;          // device copy of n_pairs
+  double* wdisp = nullptr;      // displaced positions (N x 3)
+  float* v = nullptr;           // dL/dF (N x 3)
+  float* seed = nullptr;        // dL/dE_i of the current evaluation (N)
+  float* f_target = nullptr;    // N x 3
+  int64_t* atom_off = nullptr;  // n_structs + 1
+  double* e_target = nullptr;
+  double* dE = nullptr;         // E_b - E*_b
+  unsigned* vmax = nullptr;     // max |v| per structure (float bits)
+  double* loss_blk = nullptr;
+  double* loss = nullptr;
+};
+
 struct allegro_ctx {
   std::string err;
   std::vector<WInfo> winfo;
@@ -164,6 +185,7 @@ struct allegro_ctx {
   NeighborBuffers nb{};
   GridInfo grid{};
   PassBufs pb{};
+  TrainBatch bt{};
   double* d_pos = nullptr;     // N x 3 input positions (device copy)
   int* d_species = nullptr;
   float* d_F = nullptr;
@@ -553,6 +575,7 @@ void fill_passbufs(allegro_ctx* c, const double L[3]) {
   pb.species = c->d_species;
   pb.n_atoms = c->n_atoms;
   for (int a = 0; a < 3; ++a) pb.L[a] = L[a];
+  pb.atomL = nullptr;
   pb.tile = fp32_tile();
 }
 
@@ -764,25 +787,11 @@ int ensure_train(allegro_ctx* c) {
   return ALLEGRO_OK;
 }
 
-// Add the weight gradient of seed * E at the current positions into d_grad
-// (FP32 passes in training mode, then the per-layer reductions).
-int train_eval(allegro_ctx* c, int64_t n, const double* pos, const int32_t* sp, const double* cell, double seed) {
-  double L[3];
-  int rc = prepare(c, n, pos, sp, cell, L);
-  if (rc) return rc;
-  int64_t np = 0;
-  rc = build_with_growth(c, c->d_pos, n, &np);
-  if (!rc) rc = ensure_train(c);
-  if (rc) return rc;
-  fill_passbufs(c, L);
-  c->pb.tr = c->tr;
-  c->pb.tr.seed = (float)seed;
-  c->pb.train = 1;
+// Weight gradients of the per-pair dumps of the last training-mode pass
+// sequence (P pairs), added into d_grad.
+int reduce_wgrad(allegro_ctx* c, int P) {
   const Blob& B = c->blob;
-  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream);
-  c->pb.train = 0;
-  c->pb.tr.seed = 1.0f;
-  const int P = (int)np, D = c->D, C = (int)B.C, E = c->E, Lz = (int)B.L;
+  const int D = c->D, C = (int)B.C, E = c->E, Lz = (int)B.L;
   const int NS = B.lmax == 1 ? TP1_NS : TP2_NS, NT = B.lmax == 1 ? TP1_NT : TP2_NT;
   const int NLM = ((int)B.lmax + 1) * ((int)B.lmax + 1), NW0 = C * ((int)B.lmax + 1), KH = D + C * NS;
   const TrainBufs& t = c->tr;
@@ -814,62 +823,188 @@ int train_eval(allegro_ctx* c, int64_t n, const double* pos, const int32_t* sp, 
   return cuda_check(c, "weight gradient");
 }
 
-// Loss (per-atom MSE, energy:force weights) and its weight gradient into
-// d_grad.  The force term's gradient -d/dw sum_i v_i . dE/dr_i
-// (v = 2 c (F - F*), c = w_force / (3 N)) is the weight gradient of the
-// directional derivative of E along v, taken as a central difference of the
-// hand-written weight adjoint at r +/- h v (h v at most 0.01 A).
-int loss_grad_impl(allegro_ctx* c, const allegro_batch* b, double w_energy, double w_force, double* loss_out) {
+// ---- training batches ----
+// Every structure's neighbour list, built with its own box, is appended to
+// one list (atom and pair indices offset) with per-atom box lengths, so that
+// one pass sequence evaluates the whole batch.
+template <class T>
+int bt_grow(allegro_ctx* c, T*& p, int64_t n_new, int64_t n_keep) {
+  T* q = c->dalloc<T>((size_t)n_new);
+  if (!q) return c->fail(ALLEGRO_E_OOM, "training batch allocation failed");
+  if (p && n_keep > 0) cudaMemcpyAsync(q, p, sizeof(T) * (size_t)n_keep, cudaMemcpyDeviceToDevice, c->stream);
+  c->dfree(p);
+  p = q;
+  return ALLEGRO_OK;
+}
+
+int bt_reserve(allegro_ctx* c, int64_t atoms, int64_t pairs, int structs, int64_t keep_atoms, int64_t keep_pairs) {
+  TrainBatch& t = c->bt;
+  int rc = ALLEGRO_OK;
+  if (atoms > t.cap_atoms) {
+    const int64_t na = std::max<int64_t>(atoms, t.cap_atoms * 5 / 4);
+    rc = bt_grow(c, t.a.row_ptr, na + 1, keep_atoms + 1);
+    if (!rc) rc = bt_grow(c, t.a.wpos, 3 * na, 3 * keep_atoms);
+    if (!rc) rc = bt_grow(c, t.a.atomL, 3 * na, 3 * keep_atoms);
+    if (!rc) rc = bt_grow(c, t.a.species, na, keep_atoms);
+    if (!rc) rc = bt_grow(c, t.a.sid, na, keep_atoms);
+    if (!rc) rc = bt_grow(c, t.wdisp, 3 * na, 0);
+    if (!rc) rc = bt_grow(c, t.v, 3 * na, 0);
+    if (!rc) rc = bt_grow(c, t.seed, na, 0);
+    if (!rc) rc = bt_grow(c, t.f_target, 3 * na, 0);
+    if (!rc) rc = bt_grow(c, t.loss_blk, na / 256 + 2, 0);
+    if (rc) return rc;
+    t.cap_atoms = na;
+  }
+  if (pairs > t.cap_pairs) {
+    const int64_t np = std::max<int64_t>(pairs, t.cap_pairs * 5 / 4);
+    rc = bt_grow(c, t.a.pi, np, keep_pairs);
+    if (!rc) rc = bt_grow(c, t.a.pj, np, keep_pairs);
+    if (!rc) rc = bt_grow(c, t.a.pcode, np, keep_pairs);
+    if (!rc) rc = bt_grow(c, t.a.rev, np, keep_pairs);
+    if (rc) return rc;
+    t.cap_pairs = np;
+  }
+  if (structs > t.cap_structs) {
+    rc = bt_grow(c, t.atom_off, structs + 1, 0);
+    if (!rc) rc = bt_grow(c, t.e_target, structs, 0);
+    if (!rc) rc = bt_grow(c, t.dE, structs, 0);
+    if (!rc) rc = bt_grow(c, t.vmax, structs, 0);
+    if (!rc && !t.d_np) t.d_np = c->dalloc<int>(1);
+    if (!rc && !t.loss) t.loss = c->dalloc<double>(1);
+    if (rc || !t.d_np || !t.loss) return rc ? rc : c->fail(ALLEGRO_E_OOM, "training batch allocation failed");
+    t.cap_structs = structs;
+  }
+  return ALLEGRO_OK;
+}
+
+int build_batch(allegro_ctx* c, const allegro_batch* b) {
+  TrainBatch& t = c->bt;
+  const int nb = b->n_structs;
+  const int64_t base = b->atom_offset[0];
+  const int64_t N = b->atom_offset[nb] - base;
+  // a training batch replaces the single-system state
+  c->md_ready = false;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  int rc = bt_reserve(c, N, std::max<int64_t>(t.cap_pairs, 64 * N), nb, 0, 0);
+  if (rc) return rc;
+  int64_t P0 = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t a0 = b->atom_offset[k] - base, n = b->atom_offset[k + 1] - b->atom_offset[k];
+    double L[3];
+    rc = prepare(c, n, b->positions + 3 * (b->atom_offset[k]), b->species + b->atom_offset[k], b->cells + 9 * k, L);
+    int64_t np = 0;
+    if (!rc) rc = build_with_growth(c, c->d_pos, n, &np);
+    if (!rc) rc = bt_reserve(c, N, P0 + np, nb, N, P0);
+    if (rc) return rc;
+    launch_append(t.a, (int)n, (int)np, a0, P0, k, c->nb.pi, c->nb.pj, c->nb.pcode, c->nb.rev, c->nb.row_ptr,
+                  c->nb.wpos, c->d_species, L, c->stream);
+    P0 += np;
+  }
+  if (P0 > 0x7ffffff0) return c->fail(ALLEGRO_E_UNSUPPORTED, "more than 2^31 pairs in a training batch");
+  t.n_structs = nb;
+  t.n_atoms = N;
+  t.n_pairs = P0;
+  std::vector<int64_t> off(nb + 1);
+  for (int k = 0; k <= nb; ++k) off[k] = b->atom_offset[k] - base;
+  const int np32 = (int)P0;
+  cudaMemcpyAsync(t.atom_off, off.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(t.e_target, b->e_target, sizeof(double) * nb,
+                  is_device_ptr(b->e_target) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(t.f_target, b->f_target + 3 * base, sizeof(float) * 3 * N,
+                  is_device_ptr(b->f_target) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(t.d_np, &np32, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  // per-atom outputs and per-pair state for the whole batch
+  rc = ensure_atoms(c, N, 0);
+  if (!rc) rc = ensure_pairs(c, std::max<int64_t>(P0, c->capacity));
+  if (!rc) rc = ensure_train(c);
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = cuda_check(c, "training batch");
+  return rc;
+}
+
+// pass buffers of the batch with positions wpos (wrapped or displaced)
+void fill_batch_passbufs(allegro_ctx* c, const double* wpos) {
+  const TrainBatch& t = c->bt;
+  PassBufs& pb = c->pb;
+  pb.pi = t.a.pi;
+  pb.pj = t.a.pj;
+  pb.pcode = t.a.pcode;
+  pb.row_ptr = t.a.row_ptr;
+  pb.n_pairs = t.d_np;
+  pb.flags = c->nb.flags;
+  pb.capacity = c->capacity;
+  pb.wpos = wpos;
+  pb.species = t.a.species;
+  pb.n_atoms = (int)t.n_atoms;
+  pb.atomL = t.a.atomL;
+  for (int a = 0; a < 3; ++a) pb.L[a] = 0.0;
+  pb.tile = fp32_tile();
+}
+
+// training-mode pass sequence over the batch at positions wpos with per-atom
+// seeds dL/dE_i, then the weight-gradient reductions into d_grad
+int batch_train_eval(allegro_ctx* c, const double* wpos, const float* seed) {
+  const Blob& B = c->blob;
+  fill_batch_passbufs(c, wpos);
+  c->pb.tr = c->tr;
+  c->pb.tr.seed_atom = seed;
+  c->pb.train = 1;
+  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream);
+  c->pb.train = 0;
+  c->pb.tr.seed_atom = nullptr;
+  const int rc = reduce_wgrad(c, (int)c->bt.n_pairs);
+  c->pb.atomL = nullptr;
+  return rc;
+}
+
+// Loss (per-atom MSE, energy:force weights) of the built batch and its weight
+// gradient into d_grad, all structures at once.  The force term's gradient
+// -d/dw sum_i v_i . dE/dr_i (v = 2 c (F - F*), c = w_force / (3 N)) is the
+// weight gradient of the directional derivative of E along v, taken per
+// structure as a central difference of the hand-written weight adjoint at
+// r +/- h v (h v at most 0.01 A; the pair list of r is kept, which differs
+// from the lists at r +/- h v only by pairs within 0.01 A of r_c, whose
+// energy vanishes there to third order).
+int loss_grad_impl(allegro_ctx* c, double w_energy, double w_force, double* loss_out) {
   const Blob& B = c->blob;
   if (B.L > 2) return c->fail(ALLEGRO_E_UNSUPPORTED, "training is built for models of at most two layers");
   int rc = init_master(c);
   if (rc) return rc;
-  cudaMemsetAsync(c->d_grad, 0, sizeof(float) * c->n_params, c->stream);
-  const int nb = b->n_structs;
-  int64_t ntot = 0;
-  for (int k = 0; k < nb; ++k) ntot += b->atom_offset[k + 1] - b->atom_offset[k];
-  const double cf = w_force / (3.0 * (double)ntot);
-  double loss = 0.0;
+  TrainBatch& t = c->bt;
+  cudaStream_t s = c->stream;
+  cudaMemsetAsync(c->d_grad, 0, sizeof(float) * c->n_params, s);
+  cudaMemsetAsync(c->nb.flags, 0, sizeof(int), s);
+  const int nbk = (int)t.n_structs;
+  const int64_t N = t.n_atoms;
+  const double cf = w_force / (3.0 * (double)N);
   const double delta = 1e-2;
-  for (int k = 0; k < nb; ++k) {
-    const int64_t a0 = b->atom_offset[k], n = b->atom_offset[k + 1] - a0;
-    const double* pos = b->positions + 3 * a0;
-    const int32_t* sp = b->species + a0;
-    const double* cell = b->cells + 9 * k;
-    double L[3];
-    rc = prepare(c, n, pos, sp, cell, L);
-    int64_t np = 0;
-    if (!rc) rc = build_with_growth(c, c->d_pos, n, &np);
-    if (!rc) rc = run_model(c, ALLEGRO_FP32, L);
-    if (rc) return rc;
-    std::vector<float> F(3 * (size_t)n);
-    double stats[2];
-    cudaMemcpyAsync(F.data(), c->d_F, F.size() * 4, cudaMemcpyDeviceToHost, c->stream);
-    cudaMemcpyAsync(stats, c->d_stats, sizeof(stats), cudaMemcpyDeviceToHost, c->stream);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "loss forward");
-    const double dE = stats[0] - b->e_target[k];
-    loss += w_energy / nb * (dE / n) * (dE / n);
-    std::vector<double> v(3 * (size_t)n), pp(3 * (size_t)n), pm(3 * (size_t)n);
-    double vmax = 0.0;
-    for (size_t q = 0; q < v.size(); ++q) {
-      const double r = (double)F[q] - (double)b->f_target[3 * a0 + q];
-      loss += cf * r * r;
-      v[q] = 2.0 * cf * r;
-      vmax = std::max(vmax, std::fabs(v[q]));
-    }
-    rc = train_eval(c, n, pos, sp, cell, 2.0 * w_energy * dE / ((double)nb * n * n));
-    if (rc) return rc;
-    if (vmax > 0.0) {
-      const double h = delta / vmax;
-      for (size_t q = 0; q < v.size(); ++q) {
-        pp[q] = pos[q] + h * v[q];
-        pm[q] = pos[q] - h * v[q];
-      }
-      rc = train_eval(c, n, pp.data(), sp, cell, -0.5 / h);
-      if (!rc) rc = train_eval(c, n, pm.data(), sp, cell, 0.5 / h);
-      if (rc) return rc;
-    }
+  // forward over the batch: forces and per-atom energies
+  fill_batch_passbufs(c, t.a.wpos);
+  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+  AtomArgs aa = atom_args(c);
+  aa.n = (int)N;
+  aa.species = t.a.species;
+  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk, c->d_stats,
+                c->nb.flags, s);
+  c->pb.atomL = nullptr;
+  launch_batch_loss(nbk, N, t.atom_off, t.a.sid, c->d_Ei, t.e_target, c->d_F, t.f_target, w_energy, cf, t.dE, t.v,
+                    t.vmax, t.loss_blk, t.loss, s);
+  // energy term at r, then the central difference along v
+  launch_seed_energy(nbk, N, t.atom_off, t.a.sid, t.dE, w_energy, t.seed, s);
+  rc = batch_train_eval(c, t.a.wpos, t.seed);
+  for (int sg = 0; sg < 2 && !rc; ++sg) {
+    launch_displace(N, t.a.sid, t.a.wpos, t.v, t.vmax, delta, sg == 0 ? 1.0 : -1.0, t.wdisp, t.seed, s);
+    rc = batch_train_eval(c, t.wdisp, t.seed);
   }
+  if (rc) return rc;
+  double loss = 0.0;
+  int flags = 0;
+  cudaMemcpyAsync(&loss, t.loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&flags, c->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "loss gradient");
+  if (flags & kFlagPairOverflow) return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "training batch exceeds the pair capacity");
   if (loss_out) *loss_out = loss;
   return ALLEGRO_OK;
 }
@@ -1270,7 +1405,8 @@ int allegro_loss_grad(allegro_ctx* ctx, const allegro_batch* batch, double w_ene
                       double* loss_out, float* grad_out) {
   if (!ctx) return ALLEGRO_E_INVALID_ARG;
   int rc = check_batch(ctx, batch);
-  if (!rc) rc = loss_grad_impl(ctx, batch, w_energy, w_force, loss_out);
+  if (!rc) rc = build_batch(ctx, batch);
+  if (!rc) rc = loss_grad_impl(ctx, w_energy, w_force, loss_out);
   if (!rc) rc = copy_out(ctx, grad_out, ctx->d_grad, sizeof(float) * ctx->n_params);
   if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "loss_grad");
   return rc;
@@ -1281,13 +1417,14 @@ int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double 
   if (!ctx) return ALLEGRO_E_INVALID_ARG;
   if (!(rho >= 0.0) || !(lr >= 0.0)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "rho and lr must be >= 0");
   int rc = check_batch(ctx, batch);
-  if (!rc) rc = loss_grad_impl(ctx, batch, w_energy, w_force, loss_out);      // g at w
+  if (!rc) rc = build_batch(ctx, batch);
+  if (!rc) rc = loss_grad_impl(ctx, w_energy, w_force, loss_out);            // g at w
   if (rc) return rc;
   const int n = (int)ctx->n_params;
   launch_sumsq(ctx->d_grad, n, ctx->d_norm2, ctx->stream);
   launch_ascent(ctx->d_master, ctx->d_grad, n, rho, ctx->d_norm2, ctx->d_wtmp, ctx->stream);   // w' = w + rho g/|g|
   apply_flat(ctx, ctx->d_wtmp);
-  rc = loss_grad_impl(ctx, batch, w_energy, w_force, nullptr);                // g' at w'
+  rc = loss_grad_impl(ctx, w_energy, w_force, nullptr);                       // g' at w' (same batch)
   if (rc) {
     apply_flat(ctx, ctx->d_master);
     return rc;

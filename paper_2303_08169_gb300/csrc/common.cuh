@@ -103,7 +103,13 @@ AL_DEV void bessel(float d, float rc, float* B, float* dB) {
 
 // Polynomial envelope (p = 6): u(x) = 1 - 28 x^6 + 48 x^7 - 21 x^8, x = d/rc,
 // and du/dd = (-168 x^5 + 336 x^6 - 168 x^7) / rc.
+// (zero at and beyond r_c, where a pair contributes nothing: C^2 continuous)
 AL_DEV void envelope(float d, float rc, float& u, float& du) {
+  if (d >= rc) {
+    u = 0.0f;
+    du = 0.0f;
+    return;
+  }
   const float x = d / rc;
   const float x2 = x * x, x5 = x2 * x2 * x, x6 = x5 * x;
   u = 1.0f + x6 * (-28.0f + x * (48.0f - 21.0f * x));

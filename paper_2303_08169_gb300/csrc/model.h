@@ -38,6 +38,7 @@ struct ModelW {
 // that the weight gradients dW = sum_pairs dz (x) x can be reduced afterwards.
 struct TrainBufs {
   float seed = 1.0f;                  // dL/dE of this evaluation (scales sigma_Z)
+  const float* seed_atom = nullptr;   // [N] per-atom dL/dE_i instead of seed (training batches)
   float* h0 = nullptr;                // [P][16] two-body input (12 used)
   float* a1_tb = nullptr;             // [P][D]  SiLU of the first two-body layer
   float* dz1_tb = nullptr;            // [P][D]
@@ -69,6 +70,7 @@ struct PassBufs {
   const int* species;     // N
   int n_atoms;
   double L[3];
+  const double* atomL = nullptr;  // training batches: N x 3 box lengths per atom (else L)
   // per pair state
   float* X[kMaxLayers];   // x^k, k = 0..L-1    (P x D)
   float* V[kMaxLayers];   // V^k, k = 1..L-1    (P x C NLM)

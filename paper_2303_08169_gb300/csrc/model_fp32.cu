@@ -311,6 +311,7 @@ template <class Cf>
 AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float u[3], float& d,
                      float& fc, float& dfc, float* Y) {
   Box box{{b.L[0], b.L[1], b.L[2]}};
+  if (b.atomL) box = Box{{b.atomL[3 * i], b.atomL[3 * i + 1], b.atomL[3 * i + 2]}};
   double dd[3];
   pair_delta(b.wpos, i, j, code, box, dd);
   const float dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
@@ -546,7 +547,8 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
       s_Y[p * NLM + q] = Y[q];
       s_dy[p * NLM + q] = 0.0f;
     }
-    s_sig[p] = p < t.np ? b.tr.seed * w.sigma[b.species[t.pi[p]]] : 0.0f;
+    s_sig[p] = p < t.np ? (b.tr.seed_atom ? b.tr.seed_atom[t.pi[p]] : b.tr.seed) * w.sigma[b.species[t.pi[p]]]
+                        : 0.0f;
   }
   load_rows<D>(b.X[L - 1], t, s_h, LDH);
   load_segments<CL>(b.gam[L], b.row_ptr, t, s_G);

@@ -7,6 +7,8 @@
 // and Adam (Table 5: beta = (0.9, 0.999)) with the gradient taken at w'.
 #include "train.h"
 
+#include <algorithm>
+
 namespace al {
 namespace {
 
@@ -111,7 +113,133 @@ __global__ void k_apply(const float* __restrict__ flat, int rows, int cols, floa
   if (n_out) n_out[i] = v;
 }
 
+__global__ void k_append(BatchArrays bt, int n, int np, int64_t A0, int64_t P0, int b,
+                         const int* __restrict__ pi, const int* __restrict__ pj, const int* __restrict__ pcode,
+                         const int* __restrict__ rev, const int* __restrict__ row_ptr,
+                         const double* __restrict__ wpos, const int* __restrict__ species, double Lx, double Ly,
+                         double Lz) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < np) {
+    bt.pi[P0 + k] = pi[k] + (int)A0;
+    bt.pj[P0 + k] = pj[k] + (int)A0;
+    bt.pcode[P0 + k] = pcode[k];
+    bt.rev[P0 + k] = rev[k] + (int)P0;
+  }
+  if (k <= n) bt.row_ptr[A0 + k] = row_ptr[k] + (int)P0;
+  if (k < n) {
+    const int64_t a = A0 + k;
+    for (int d = 0; d < 3; ++d) bt.wpos[3 * a + d] = wpos[3 * k + d];
+    bt.atomL[3 * a] = Lx;
+    bt.atomL[3 * a + 1] = Ly;
+    bt.atomL[3 * a + 2] = Lz;
+    bt.species[a] = species[k];
+    bt.sid[a] = b;
+  }
+}
+
+// one block per structure: E_b - E*_b, atoms summed in a fixed order
+__global__ void k_struct_dE(const int64_t* __restrict__ off, const double* __restrict__ Ei,
+                            const double* __restrict__ e_target, double* __restrict__ dE) {
+  __shared__ double sh[256];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = off[b] + threadIdx.x; i < off[b + 1]; i += blockDim.x) s += Ei[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += sh[k];
+    dE[b] = t - e_target[b];
+  }
+}
+
+__global__ void k_force_resid(int64_t N, const int* __restrict__ sid, const float* __restrict__ F,
+                              const float* __restrict__ ft, double cf, float* __restrict__ v,
+                              unsigned* __restrict__ vmax, double* __restrict__ blk) {
+  __shared__ double sh[256];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (i < N) {
+    float m = 0.0f;
+    for (int d = 0; d < 3; ++d) {
+      const double r = (double)F[3 * i + d] - (double)ft[3 * i + d];
+      l += cf * r * r;
+      const float vv = (float)(2.0 * cf * r);
+      v[3 * i + d] = vv;
+      m = fmaxf(m, fabsf(vv));
+    }
+    atomicMax(&vmax[sid[i]], __float_as_uint(m));   // non-negative floats order like their bits
+  }
+  sh[threadIdx.x] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += sh[k];
+    blk[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_loss_total(int B, const int64_t* __restrict__ off, const double* __restrict__ dE, double wE,
+                             const double* __restrict__ blk, int nblk, double* __restrict__ loss) {
+  if (threadIdx.x != 0) return;
+  double l = 0.0;
+  for (int b = 0; b < B; ++b) {
+    const double e = dE[b] / (double)(off[b + 1] - off[b]);
+    l += wE / B * e * e;
+  }
+  for (int k = 0; k < nblk; ++k) l += blk[k];
+  *loss = l;
+}
+
+__global__ void k_seed_energy(int B, int64_t N, const int64_t* __restrict__ off, const int* __restrict__ sid,
+                              const double* __restrict__ dE, double wE, float* __restrict__ seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int b = sid[i];
+  const double n = (double)(off[b + 1] - off[b]);
+  seed[i] = (float)(2.0 * wE * dE[b] / ((double)B * n * n));
+}
+
+__global__ void k_displace(int64_t N, const int* __restrict__ sid, const double* __restrict__ wpos,
+                           const float* __restrict__ v, const unsigned* __restrict__ vmax, double delta, double sign,
+                           double* __restrict__ wdisp, float* __restrict__ seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double vm = (double)__uint_as_float(vmax[sid[i]]);
+  const double h = vm > 0.0 ? delta / vm : 0.0;
+  for (int d = 0; d < 3; ++d) wdisp[3 * i + d] = wpos[3 * i + d] + sign * h * (double)v[3 * i + d];
+  seed[i] = h > 0.0 ? (float)(-sign * 0.5 / h) : 0.0f;
+}
+
 }  // namespace
+
+void launch_append(const BatchArrays& bt, int n, int np, int64_t A0, int64_t P0, int b, const int* pi, const int* pj,
+                   const int* pcode, const int* rev, const int* row_ptr, const double* wpos, const int* species,
+                   const double L[3], cudaStream_t s) {
+  const int m = std::max(n + 1, np);
+  k_append<<<(m + 255) / 256, 256, 0, s>>>(bt, n, np, A0, P0, b, pi, pj, pcode, rev, row_ptr, wpos, species, L[0],
+                                           L[1], L[2]);
+}
+
+void launch_batch_loss(int B, int64_t N, const int64_t* off, const int* sid, const double* Ei, const double* e_target,
+                       const float* F, const float* f_target, double w_energy, double cf, double* dE, float* v,
+                       unsigned* vmax, double* blk, double* loss, cudaStream_t s) {
+  const int nblk = (int)((N + 255) / 256);
+  cudaMemsetAsync(vmax, 0, sizeof(unsigned) * B, s);
+  k_struct_dE<<<B, 256, 0, s>>>(off, Ei, e_target, dE);
+  k_force_resid<<<nblk, 256, 0, s>>>(N, sid, F, f_target, cf, v, vmax, blk);
+  k_loss_total<<<1, 32, 0, s>>>(B, off, dE, w_energy, blk, nblk, loss);
+}
+
+void launch_seed_energy(int B, int64_t N, const int64_t* off, const int* sid, const double* dE, double w_energy,
+                        float* seed, cudaStream_t s) {
+  k_seed_energy<<<(int)((N + 255) / 256), 256, 0, s>>>(B, N, off, sid, dE, w_energy, seed);
+}
+
+void launch_displace(int64_t N, const int* sid, const double* wpos, const float* v, const unsigned* vmax, double delta,
+                     double sign, double* wdisp, float* seed, cudaStream_t s) {
+  k_displace<<<(int)((N + 255) / 256), 256, 0, s>>>(N, sid, wpos, v, vmax, delta, sign, wdisp, seed);
+}
 
 void launch_wgrad(const float* dz, int ldz, const float* x, int ldx, int P, int N, int K, float scale, float* dW,
                   int ldw, int k0, cudaStream_t s) {

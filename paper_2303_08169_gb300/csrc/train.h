@@ -16,4 +16,34 @@ void launch_ascent(const float* w, const float* g, int n, double rho, const doub
 void launch_adam(float* w, const float* g, float* m, float* v, int n, double lr, int t, cudaStream_t s);
 void launch_apply(const float* flat, int rows, int cols, float scale, float* t_out, float* n_out, cudaStream_t s);
 
+// ---- training batches: all structures in one pass sequence ----
+// Append one structure's neighbour list and atoms at atom offset A0 and pair
+// offset P0 of the batch arrays (indices shifted, box lengths per atom).
+struct BatchArrays {
+  int* pi;
+  int* pj;
+  int* pcode;
+  int* rev;
+  int* row_ptr;
+  double* wpos;
+  double* atomL;
+  int* species;
+  int* sid;
+};
+void launch_append(const BatchArrays& bt, int n, int np, int64_t A0, int64_t P0, int b, const int* pi, const int* pj,
+                   const int* pcode, const int* rev, const int* row_ptr, const double* wpos, const int* species,
+                   const double L[3], cudaStream_t s);
+// Loss of Eq. 3's objective (per-atom energy MSE + force MSE) on the batch and
+// the seeds of its weight gradient: dE[b] = E_b - E*_b; v = 2 cf (F - F*);
+// vmax[b] = max |v| over structure b (float bits); *loss.
+void launch_batch_loss(int B, int64_t N, const int64_t* off, const int* sid, const double* Ei, const double* e_target,
+                       const float* F, const float* f_target, double w_energy, double cf, double* dE, float* v,
+                       unsigned* vmax, double* blk, double* loss, cudaStream_t s);
+// seed_i = 2 w_E dE_b / (B N_b^2) for atom i of structure b
+void launch_seed_energy(int B, int64_t N, const int64_t* off, const int* sid, const double* dE, double w_energy,
+                        float* seed, cudaStream_t s);
+// r_i + sign h_b v_i with h_b = delta / vmax_b, seed_i = -sign / (2 h_b) (0 where vmax_b = 0)
+void launch_displace(int64_t N, const int* sid, const double* wpos, const float* v, const unsigned* vmax, double delta,
+                     double sign, double* wdisp, float* seed, cudaStream_t s);
+
 }  // namespace al
