@@ -1345,7 +1345,7 @@ int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_
   cudaEvent_t e_begin, e_end;
   cudaEventCreate(&e_begin);
   cudaEventCreate(&e_end);
-  double kind_ms[kKindCount] = {}, nb_ms = 0.0, f_ms = 0.0;
+  double kind_ms[kPhCount] = {}, nb_ms = 0.0, f_ms = 0.0;
   double L[3] = {ctx->grid.L[0], ctx->grid.L[1], ctx->grid.L[2]};
   fill_passbufs(ctx, L);
   int rc = ALLEGRO_OK;
@@ -1364,7 +1364,8 @@ int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_
     nb_ms += ms;
     for (int i = 0; i + 1 < km.n; ++i) {
       cudaEventElapsedTime(&ms, km.ev[i], km.ev[i + 1]);
-      kind_ms[km.kind[i + 1]] += ms;
+      const int kd = km.kind[i + 1];
+      if (kd >= 0 && kd < kPhCount) kind_ms[kd] += ms;
     }
     cudaEventElapsedTime(&ms, km.ev[km.n - 1], e_end);
     f_ms += ms;
@@ -1375,16 +1376,16 @@ int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_
   if (rc) return rc;
   const double n = n_reps;
   const double out[11] = {nb_ms / n,
-                          kind_ms[kKA] / n,
-                          (kind_ms[kKB] + kind_ms[kKB2]) / n,
-                          kind_ms[kKC] / n,
-                          (kind_ms[kKBT] + kind_ms[kKBT2]) / n,
-                          kind_ms[kKAT] / n,
+                          kind_ms[kPhA] / n,
+                          (kind_ms[kPhB] + kind_ms[kPhB2]) / n,
+                          kind_ms[kPhC] / n,
+                          (kind_ms[kPhBT] + kind_ms[kPhBT2]) / n,
+                          kind_ms[kPhAT] / n,
                           f_ms / n,
-                          kind_ms[kKB] / n,
-                          kind_ms[kKB2] / n,
-                          kind_ms[kKBT] / n,
-                          kind_ms[kKBT2] / n};
+                          kind_ms[kPhB] / n,
+                          kind_ms[kPhB2] / n,
+                          kind_ms[kPhBT] / n,
+                          kind_ms[kPhBT2] / n};
   for (int k = 0; k < std::min(n_out, 11); ++k) ms_out[k] = out[k];
   return ALLEGRO_OK;
 }

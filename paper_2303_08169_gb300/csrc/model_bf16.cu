@@ -1491,25 +1491,25 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
   auto mark = [&](int k) {
     if (km) km->mark(k, s);
   };
-  mark(kKStart);
+  mark(kPhStart);
   k_bf_a<Tin, kSplit><<<grid, kThr4, kSmA, s>>>(w, b);
-  mark(kKA);
+  mark(kPhA);
   for (int k = 1; k < L; ++k) {
     k_bf_b1<Tin><<<grid, kThr4, kSmB1, s>>>(w, b, k);
-    mark(kKB);
+    mark(kPhB);
     k_bf_b2<Tin><<<grid, kThr4, kSmB2, s>>>(w, b, k);
-    mark(kKB2);
+    mark(kPhB2);
   }
   k_bf_c<Tin, kSplit><<<grid, kThr4, kSmC, s>>>(w, b);
-  mark(kKC);
+  mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
     k_bf_b2t<Tin><<<grid, kThr4, kSmB2T, s>>>(w, b, k);
-    mark(kKBT);
+    mark(kPhBT);
     k_bf_b1t<Tin><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
-    mark(kKBT2);
+    mark(kPhBT2);
   }
   k_bf_at<Tin, kSplit><<<grid, kThr4, kSmAT, s>>>(w, b);
-  mark(kKAT);
+  mark(kPhAT);
 }
 
 }  // namespace

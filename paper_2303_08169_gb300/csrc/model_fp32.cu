@@ -185,7 +185,9 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
         cp_async_wait<0>();
       }
       __syncthreads();
-      const float* wc = wbuf + (ch & 1) * kKC * N + tx * TN;
+      // TN % 4 == 0: float4 group q of thread tx covers columns q TX 4 + tx 4 ..+3, so
+      // that the 16-byte loads of a warp are contiguous (no bank conflicts)
+      const float* wc = wbuf + (ch & 1) * kKC * N + (TN % 4 == 0 ? tx * 4 : tx * TN);
       const int k0 = ch * kKC;
       const float* a0 = A + ty * lda + k0;
       auto step = [&](int k) {
@@ -195,7 +197,7 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
         if constexpr (TN % 4 == 0) {
 #pragma unroll
           for (int q = 0; q < TN / 4; ++q) {
-            const float4 v = reinterpret_cast<const float4*>(wc + k * N)[q];
+            const float4 v = *reinterpret_cast<const float4*>(wc + k * N + q * TX * 4);
             b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
           }
         } else if constexpr (TN % 2 == 0) {
@@ -224,7 +226,8 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) epi(ty + i * TY, tx * TN + j, acc[i][j]);
+      for (int j = 0; j < TN; ++j)
+        epi(ty + i * TY, TN % 4 == 0 ? (j / 4) * TX * 4 + tx * 4 + (j % 4) : tx * TN + j, acc[i][j]);
   }
 }
 
@@ -1046,21 +1049,21 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
   auto mark = [&](int k) {
     if (km) km->mark(k, s);
   };
-  mark(kKStart);
+  mark(kPhStart);
   k_pass_a<Cf><<<grid, kThreads, Sm::a, s>>>(w, b);
-  mark(kKA);
+  mark(kPhA);
   for (int k = 1; k < L; ++k) {
     k_pass_b<Cf><<<grid, kThreads, Sm::b, s>>>(w, b, k);
-    mark(kKB);
+    mark(kPhB);
   }
   k_pass_c<Cf><<<grid, kThreads, Sm::c, s>>>(w, b);
-  mark(kKC);
+  mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
     k_pass_b_bwd<Cf><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
-    mark(kKBT);
+    mark(kPhBT);
   }
   k_pass_a_bwd<Cf><<<grid, kThreads, Sm::ab, s>>>(w, b);
-  mark(kKAT);
+  mark(kPhAT);
 }
 
 using CfgTiny = Cfg<1, 8, 32, 32>;
