@@ -364,8 +364,9 @@ def sam_timing(al, torch, steps=5):
     n_atoms = int(sum(len(s["species"]) for s in structs))
     return {"structures": len(structs), "atoms": n_atoms, "ms_per_step": 1e3 * dt, "steps": steps,
             "rho": 0.05, "lr": 2e-3, "loss_first": losses[0], "loss_last": losses[-1],
-            "note": "FP32 passes with per-pair dumps; two loss gradients (w, w + eps) per step, "
-                    "each three pass sequences per structure (forward + central difference)"}
+            "note": "FP32 passes with per-pair dumps over all 32 structures at once (one concatenated "
+                    "pair list); two loss gradients (w, w + eps) per step, each one forward and three "
+                    "training-mode pass sequences (energy seed, central difference along dL/dF)"}
 
 
 def roofline(phases, n_pairs, tensor_path, peaks):
