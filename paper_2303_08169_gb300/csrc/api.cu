@@ -531,6 +531,8 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   }
   c->dfree(pb.dS);
   pb.dS = nullptr;
+  c->dfree(pb.dR);
+  pb.dR = nullptr;
   if (c->bf16_ok) {
     const int NSC = B.C * 3;
     for (uint32_t k = 1; k < B.L && ok; ++k) {
@@ -539,6 +541,8 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
     }
     pb.dS = c->dalloc<float>((size_t)capr * NSC);
     ok = ok && pb.dS;
+    pb.dR = c->dalloc<float>((size_t)capr * 3);
+    ok = ok && pb.dR;
   }
   const int64_t rows = rows_needed;
   pb.epart = c->dalloc<double>(rows);

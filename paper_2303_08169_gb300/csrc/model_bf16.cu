@@ -255,12 +255,8 @@ AL_DEV void get_g(const float* s, const float* __restrict__ part, const int* __r
   }
 }
 
-AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float u[3], float& d, float& fc,
-                     float& dfc, float* Y) {
-  Box box{{b.L[0], b.L[1], b.L[2]}};
-  double dd[3];
-  pair_delta(b.wpos, i, j, code, box, dd);
-  const float dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
+AL_DEV void geo_from_delta(float dx, float dy, float dz, float rc, float u[3], float& d, float& fc, float& dfc,
+                           float* Y) {
   d = sqrtf(dx * dx + dy * dy + dz * dz);
   const float inv = 1.0f / d;
   u[0] = dx * inv;
@@ -268,6 +264,26 @@ AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float 
   u[2] = dz * inv;
   envelope(d, rc, fc, dfc);
   sph_harm<2>(u[0], u[1], u[2], Y);
+}
+
+// Pass A: the pair separation in FP64 (the arithmetic that decides pair
+// membership), rounded to FP32 and kept per pair (tile-SoA, 3 floats) for the
+// later passes, which read it instead of gathering two FP64 positions.
+AL_DEV void geometry_first(const PassBufs& b, int tile, int r, float rc, int i, int j, int code, float u[3],
+                           float& d, float& fc, float& dfc, float* Y) {
+  Box box{{b.L[0], b.L[1], b.L[2]}};
+  double dd[3];
+  pair_delta(b.wpos, i, j, code, box, dd);
+  const float dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
+  b.dR[sidx(tile, 3, 0, r)] = dx;
+  b.dR[sidx(tile, 3, 1, r)] = dy;
+  b.dR[sidx(tile, 3, 2, r)] = dz;
+  geo_from_delta(dx, dy, dz, rc, u, d, fc, dfc, Y);
+}
+AL_DEV void geometry(const PassBufs& b, int tile, int r, float rc, float u[3], float& d, float& fc, float& dfc,
+                     float* Y) {
+  geo_from_delta(b.dR[sidx(tile, 3, 0, r)], b.dR[sidx(tile, 3, 1, r)], b.dR[sidx(tile, 3, 2, r)], rc, u, d, fc, dfc,
+                 Y);
 }
 
 // ---- MMA issue helpers (single thread) ----
@@ -514,7 +530,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
       if (r < m.np) {
         float u[3], d, dfc, B[NB];
-        geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+        geometry_first(b, tile, r, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
         bessel<NB>(d, w.rc, B, nullptr);
         const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
 #pragma unroll
@@ -583,6 +599,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
+      prefetch_rows(b.dR, 3, nt);
       if (k == 1) prefetch_rows_h(b.X[0], D, nt);
       else prefetch_rows_h(b.V[k - 1], CL, nt);
     }
@@ -590,7 +607,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       float u[3], d, fc, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (r < m.np) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      if (r < m.np) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
@@ -693,6 +710,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
+      prefetch_rows(b.dR, 3, nt);
       prefetch_rows_h(b.X[k - 1], D, nt);
       prefetch_rows_h(b.S[k], C * NS, nt);
     }
@@ -701,7 +719,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
@@ -787,13 +805,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
+      prefetch_rows(b.dR, 3, nt);
       prefetch_rows_h(b.V[L - 1], CL, nt);
       prefetch_rows_h(b.X[L - 1], D, nt);
     }
     const bool valid = r < m.np;
     if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
-      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
       s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
     }
@@ -974,6 +993,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
+      prefetch_rows(b.dR, 3, nt);
       prefetch_rows_h(b.X[k], D, nt);
       prefetch_rows_h(b.X[k - 1], D, nt);
       prefetch_rows_h(b.S[k], C * NS, nt);
@@ -986,7 +1006,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
@@ -1117,6 +1137,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
+      prefetch_rows(b.dR, 3, nt);
       prefetch_rows(b.dV, CL, nt);
       prefetch_rows(b.dS, C * NS, nt);
       if (k == 1) {
@@ -1132,7 +1153,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       float u[3], d, fc, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
@@ -1301,6 +1322,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
+      prefetch_rows(b.dR, 3, nt);
       prefetch_rows(b.dX, D, nt);
       prefetch_rows(b.dU, 1, nt);
       prefetch_rows(b.dY, NLM, nt);
@@ -1315,7 +1337,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
 #pragma unroll
       for (int q = 0; q < NB; ++q) dB[q] = 0.0f;
       if (valid) {
-        geometry(b, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+        geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
         bessel<NB>(d, w.rc, B, dB);
         const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
 #pragma unroll
