@@ -163,13 +163,23 @@ AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
 }
 
 // part[(tile + atom) * W + x] = sum over the segment's pairs of f(p, x)
+// (four interleaved partial sums in a fixed order: a quarter of the
+// dependent chain)
 template <class F>
 AL_DEV void seg_store(float* __restrict__ part, const Meta& m, int W, F&& f) {
   for (int idx = threadIdx.x; idx < m.nseg * W; idx += blockDim.x) {
     const int s = idx / W, x = idx % W;
-    float acc = 0.0f;
-    for (int p = m.sstart[s]; p < m.sstart[s + 1]; ++p) acc += f(p, x);
-    part[(size_t)(m.tile + m.atom[s]) * W + x] = acc;
+    const int s1 = m.sstart[s + 1];
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    int p = m.sstart[s];
+    for (; p + 3 < s1; p += 4) {
+      a0 += f(p, x);
+      a1 += f(p + 1, x);
+      a2 += f(p + 2, x);
+      a3 += f(p + 3, x);
+    }
+    for (; p < s1; ++p) a0 += f(p, x);
+    part[(size_t)(m.tile + m.atom[s]) * W + x] = (a0 + a1) + (a2 + a3);
   }
 }
 
@@ -945,12 +955,18 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       }
     }
     __syncthreads();
-    if (threadIdx.x < m.nseg) {
-      const int sg = threadIdx.x;
-      double acc = 0.0;
-      for (int p = m.sstart[sg]; p < m.sstart[sg + 1]; ++p)
-        acc += (double)((s_eq[p] + s_eq[kT + p]) + (s_eq[2 * kT + p] + s_eq[3 * kT + p]));
-      b.epart[m.tile + m.atom[sg]] = acc;
+    {
+      // energy partials in FP64, one warp per segment: lanes stride the
+      // segment's pairs, then a shuffle tree (fixed order)
+      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int sg = wid; sg < m.nseg; sg += (int)(blockDim.x >> 5)) {
+        double acc = 0.0;
+        for (int p = m.sstart[sg] + lane; p < m.sstart[sg + 1]; p += 32)
+          acc += (double)((s_eq[p] + s_eq[kT + p]) + (s_eq[2 * kT + p] + s_eq[3 * kT + p]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) b.epart[m.tile + m.atom[sg]] = acc;
+      }
     }
     if (threadIdx.x < kT && valid) {
       b.dU[sidx(tile, 1, 0, r)] = (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
