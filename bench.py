@@ -14,6 +14,8 @@ dt 0.25 fs from 200 K.  Workloads:
   bf16_110592  same, BF16 operands throughout
   fp16_110592  same, FP16 operands throughout
   fp32_6912    6,912 atoms (1,728 NH3), every per-pair GEMM in FP32
+  tc_1000000   10^6 atoms (250,000 NH3, edge 218 A, ~5.2e7 pairs, ~216 GB of
+               device memory), FP16_SPLIT, 200 steps
 Prints one JSON line (rank 0): the headline workload timed over --steps, the
 other paths timed over min(--steps, 200) steps under "paths", each path's
 force error against the FP64 oracle on the 6,912-atom cell, per-kernel
@@ -78,8 +80,11 @@ WORKLOADS = {
     "fp32_6912": dict(n_mol=1728, precision=0, dt=0.25, dtype="f32"),
     "tc_6912": dict(n_mol=1728, precision=3, dt=0.25,
                     dtype="f16 operands (two-body and energy-hidden GEMMs split hi+lo), f32 accumulate"),
+    "tc_1000000": dict(n_mol=250000, precision=3, dt=0.25,
+                       dtype="f16 operands (two-body and energy-hidden GEMMs split hi+lo), f32 accumulate"),
 }
 SECONDARY = ["bf16_110592", "fp16_110592", "fp32_6912"]
+SCALE = "tc_1000000"   # own context (most of the device memory), run after the others
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tc_110592_kernels.md")
 
 
@@ -435,6 +440,12 @@ def run_ours(args):
             paths[name] = {"value": r["N"] * r["K"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / r["K"],
                            "atoms": r["N"], "pairs": r["n_pairs"], "steps": r["K"], "dtype": WORKLOADS[name]["dtype"]}
         sam = sam_timing(al, torch)
+        if args.config != SCALE and not args.no_scale:
+            big = Runner(al, torch, dev, blob, cfg)
+            r = big.md(SCALE, min(K, 200), W)
+            big.close()
+            paths[SCALE] = {"value": r["N"] * r["K"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / r["K"],
+                            "atoms": r["N"], "pairs": r["n_pairs"], "steps": r["K"], "dtype": WORKLOADS[SCALE]["dtype"]}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             cpu, (pos, sp, cell, E0, F0) = cpu_baseline()
             # force error of every path against the FP64 oracle on the 6,912-atom cell
@@ -504,6 +515,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="tc_110592", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 10^6-atom path")
     ap.add_argument("--only-headline", action="store_true",
                     help="time the headline workload only (no other paths, e2e, accuracy or CPU baseline)")
     args = ap.parse_args()
