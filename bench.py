@@ -95,6 +95,22 @@ def _env_int(name, default):
         return default
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The job's time: the slowest rank's elapsed milliseconds."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, atoms, steps, ms):
+    """Whole-job atom-steps/s: every rank advances its own replica of `atoms`
+    atoms by `steps` steps in the job time `ms` (weak scaling)."""
+    return world * atoms * steps / (ms * 1e-3)
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -421,11 +437,7 @@ def run_ours(args):
     tensor_path = w["precision"] != 0
 
     head = run.md(args.config, K, W, ClockSampler(local), barrier)
-    ms = head["ms"]
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(head["ms"], dist, dev)
     phases, n_pairs_ph = run.phases()
     roof = roofline(phases, n_pairs_ph, tensor_path, _measured_peaks())
 
@@ -469,7 +481,7 @@ def run_ours(args):
     N = head["N"]
     line = {
         "metric": METRIC,
-        "value": world * N * K / (ms * 1e-3),
+        "value": job_throughput(world, N, K, ms),
         "unit": "atom-steps/s",
         "n_gpus": world,
         "steps": K,
