@@ -416,6 +416,25 @@ def roofline(phases, n_pairs, tensor_path, peaks):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "frac_label": "of derived"}
 
 
+def roofline_step(phases, n_pairs, peaks):
+    """Whole E+F of the tensor-core path: algorithmic GEMM FLOPs of all seven
+    pass kernels over their summed device time (tensor view), and their DRAM
+    bytes (committed ncu figures, when the source matches) over the same time
+    (HBM view)."""
+    t = sum(phases[k] for k in GEMM_MAC_PER_PAIR)
+    flops = 2.0 * sum(GEMM_MAC_PER_PAIR.values()) * n_pairs
+    peak = peaks.get("bf16_tflops", 1900.0)
+    per = [_profile_traffic(TC_KERNELS[k]) for k in GEMM_MAC_PER_PAIR]
+    traffic = None if any(x is None for x in per) else sum(per) * n_pairs
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"kernels_ms": t, "algorithmic_flops": flops, "achieved_tflops": flops / (t * 1e-3) / 1e12,
+           "peak_tflops": peak, "frac_tensor": flops / (t * 1e-3) / 1e12 / peak, "traffic": traffic}
+    if traffic is not None:
+        out["achieved_gbs"] = traffic / (t * 1e-3) / 1e9
+        out["frac_hbm"] = out["achieved_gbs"] / hbm
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2303_08169_gb300 as al
@@ -440,6 +459,7 @@ def run_ours(args):
     ms = max_over_ranks(head["ms"], dist, dev)
     phases, n_pairs_ph = run.phases()
     roof = roofline(phases, n_pairs_ph, tensor_path, _measured_peaks())
+    roof_step = roofline_step(phases, n_pairs_ph, _measured_peaks()) if tensor_path else None
 
     paths = {}
     accuracy = {}
@@ -498,6 +518,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(head["step_kernels"] * K),
         "roofline": roof,
+        "roofline_step": roof_step,
         "kernel_ms": {k: round(v, 4) for k, v in phases.items()},
         "physics": {"energy_drift_over_NkT": head["drift"], "outliers_last": head["outliers_last"],
                     "outliers_max": head["outliers_max"]},

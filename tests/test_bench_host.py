@@ -73,3 +73,18 @@ def test_traffic_needs_the_captured_source(tmp_path, monkeypatch):
     assert bench._profile_traffic("k_bf_c") is None                 # another kernel source
     f.write_text(f"source_sha256_16: {bench._kernel_source_hash()}\ndram_bytes_per_pair.k_bf_c: 1500\n")
     assert bench._profile_traffic("k_bf_c") == 1500.0
+
+
+def test_step_roofline_sums_the_seven_pass_kernels(tmp_path, monkeypatch):
+    phases = {k: 2.0 for k in bench.GEMM_MAC_PER_PAIR}
+    r = bench.roofline_step(phases, 1_000_000, {"bf16_tflops": 2000.0, "hbm_gbs": 5000.0})
+    flops = 2.0 * 238_080 * 1_000_000
+    assert r["kernels_ms"] == pytest.approx(2.0 * len(bench.GEMM_MAC_PER_PAIR))
+    assert r["frac_tensor"] == pytest.approx(flops / (r["kernels_ms"] * 1e-3) / 1e12 / 2000.0)
+    f = tmp_path / "kernels.md"
+    f.write_text(f"source_sha256_16: {bench._kernel_source_hash()}\n"
+                 + "".join(f"dram_bytes_per_pair.{bench.TC_KERNELS[k]}: 100\n" for k in bench.GEMM_MAC_PER_PAIR))
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(f))
+    r = bench.roofline_step(phases, 1_000_000, {"bf16_tflops": 2000.0, "hbm_gbs": 5000.0})
+    assert r["traffic"] == pytest.approx(100.0 * len(bench.GEMM_MAC_PER_PAIR) * 1_000_000)
+    assert r["frac_hbm"] == pytest.approx(r["traffic"] / (r["kernels_ms"] * 1e-3) / 1e9 / 5000.0)
