@@ -826,6 +826,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       s_fc[r] = fc;
       s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
     }
+    // V^{L-1} of this thread's channel pairs (4h, 4h+1), (4h+2, 4h+3): one
+    // FP16 pair per word, loaded ahead of the Gamma staging
+    __half2 vw[2][NLM];
+#pragma unroll
+    for (int cp = 0; cp < 2; ++cp)
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm)
+        vw[cp][lm] = valid ? reinterpret_cast<const __half2*>(b.V[L - 1])[hidx(tile, CL, lm * C + 4 * h + 2 * cp, r)]
+                           : __floats2half2_rn(0.f, 0.f);
     stage_g(b.gam[L], b.row_ptr, m, s_g);
     __syncthreads();
     {
@@ -835,7 +844,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         float V2[2][NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
-          const float2 t = valid ? ldh2(b.V[L - 1], hidx(tile, CL, lm * C + 4 * h + cp, r)) : make_float2(0.f, 0.f);
+          const float2 t = __half22float2(vw[cp / 2][lm]);
           V2[0][lm] = t.x;
           V2[1][lm] = t.y;
         }
@@ -924,6 +933,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       st16<Tin>(HA, rr, n0, o);
     });
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 176, 8, true, 128); });      // [dx^{L-1}, ds]
+#pragma unroll
+    for (int cp = 0; cp < 2; ++cp)                    // again, for the tensor-product adjoint
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm)
+        vw[cp][lm] = valid ? reinterpret_cast<const __half2*>(b.V[L - 1])[hidx(tile, CL, lm * C + 4 * h + 2 * cp, r)]
+                           : __floats2half2_rn(0.f, 0.f);
     epi(tmem, 0, 128, [&](int rr, int n0, const float* dh) {
       float dx[16];
       tmem_ld16(lanes(tmem) + 288 + n0, dx);
@@ -940,7 +955,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         float V[NLM], G[NLM], dV[NLM], dG[NLM];
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
-          const float2 t = valid ? ldh2(b.V[L - 1], hidx(tile, CL, lm * C + (c & ~1), r)) : make_float2(0.f, 0.f);
+          const float2 t = __half22float2(vw[cc / 2][lm]);
           V[lm] = (cc & 1) ? t.y : t.x;
           dV[lm] = 0.0f;
           dG[lm] = 0.0f;
@@ -1059,6 +1074,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
     }
+    float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
+#pragma unroll
+    for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
     mm.run([&] { mma_k<Tin>(tmem + 32, HA, 0, Wl0, 128, 11, false, 0); });     // z1
     epi(tmem, 32, 128, [&](int rr, int n0, const float* v) {
       float o[16];
@@ -1068,24 +1086,29 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
     });
     mm.run([&] { mma_k<Tin>(tmem + 160, A1, 0, Wl1, 128, 8, false, 0); });     // z2
     {
+      // dx = dx^k + env^T de; its residual part dx / sqrt 2 goes back into
+      // the same TMEM columns, where the [dx, ds] MMA below accumulates onto it
       float du = 0.0f;
-      float* dxg = b.dX;
-      epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
-        float z2[16], o[16], dx[16];
-        tmem_ld16(lanes(tmem) + 160 + n0, z2);
-        const float fc = s_fc[rr];
+      float dx[32];
+      tmem_ld32(lanes(tmem) + 288 + 32 * h, dx);
+      const float fc = s_fc[r];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) dx[q] = dxe[q] + (valid ? dxg[sidx(tile, D, n0 + q, rr)] : 0.0f);
+      for (int hf = 0; hf < 2; ++hf) {
+        float z2[16], o[16];
+        tmem_ld16(lanes(tmem) + 160 + 32 * h + 16 * hf, z2);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          du = fmaf(dx[q], silu_b(z2[q]), du);
-          o[q] = dx[q] * fc * kR2 * dsilu_b(z2[q]);
+          const float x = dx[16 * hf + q] + dxo[16 * hf + q];
+          du = fmaf(x, silu_b(z2[q]), du);
+          o[q] = x * fc * kR2 * dsilu_b(z2[q]);
+          dx[16 * hf + q] = x * kR2;
         }
-        st16<Tin>(A1, rr, n0, o);
-        if (valid)
-#pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] = dx[q] * kR2;
-      });
+        st16<Tin>(A1, r, 32 * h + 16 * hf, o);
+      }
+      tmem_st32(lanes(tmem) + 288 + 32 * h, dx);
+      float z[16] = {};
+      tmem_st16(lanes(tmem) + 416 + 12 * h, z);       // ds columns 416..463 start from zero
+      tmem_wait_st();
       s_du[h * kT + r] = du * kR2;
     }
     mm.run([&] { mma_k<Tin>(tmem + 160, A1, 0, Wl1, 128, 8, true, 128); });    // da1
@@ -1096,13 +1119,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
       st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 288, HA, 0, Wl0, 176, 8, true, 128); });    // [dx, ds]
+    mm.run([&] { mma_k<Tin>(tmem + 288, HA, 0, Wl0, 176, 8, true, 128, true); });  // [dx, ds] += dz1 W
+    float duo = 0.0f, dyo[NLM];
+    if (threadIdx.x < kT) {                           // loaded ahead of the barrier below
+      duo = valid ? b.dU[sidx(tile, 1, 0, r)] : 0.0f;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
+    }
     {
       float* dxg = b.dX;
       epi(tmem, 288, 128, [&](int rr, int n0, const float* dh) {
         if (valid)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] += dh[q];
+          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] = dh[q];
       });
       float ds[16];                                   // ds columns 12 h .. 12 h + 11
       tmem_ld16(lanes(tmem) + 288 + 128 + 12 * h, ds);
@@ -1112,11 +1141,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
     }
     __syncthreads();
     if (threadIdx.x < kT && valid) {
-      b.dU[sidx(tile, 1, 0, r)] += (s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]);
+      b.dU[sidx(tile, 1, 0, r)] = duo + ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]));
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        b.dY[sidx(tile, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
-                                     (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]);
+        b.dY[sidx(tile, NLM, lm, r)] = dyo[lm] + ((s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
+                                                  (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]));
     }
     __syncthreads();
   }
@@ -1127,11 +1156,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 // Pass B1_k^T: adjoint of mixing and of the tensor product of layer k:
 // dV^{k-1} (k >= 2) or, for k = 1, the embedding adjoint into dx^0 and dY;
 // dGamma^k partials.
-// 512 threads: thread (r, h) owns tile row r and channels 4h..4h+3.  The
-// mixing adjoint is issued in two rounds (l3 <= 1, then l3 = 2) because all
-// nine products together exceed the TMEM columns; each round runs only its
-// own terms of the tensor-product adjoint.  The embedding-adjoint inputs
-// (dw0, dY) are linear in dV and accumulate over the rounds.
+// The mixing adjoint of all nine components and sixteen channels (560
+// accumulator columns) exceeds the 512 TMEM columns, so it is issued in two
+// rounds of eight channels each: round hf holds, for every component j >= 1,
+// the 32 columns of channels 8 hf .. 8 hf + 7 (the B operand starts 64 bytes
+// into the 128-byte rows of the mixing image for hf = 1); the l3 = 0
+// component of all channels (48 columns) comes with round 0.  Each channel's
+// whole tensor-product adjoint then runs in one round.
+// 512 threads: thread (r, h) owns tile row r and channels 2h, 2h + 1 of each
+// round (8 hf + 2h + e).
 template <class Tin>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
@@ -1147,6 +1180,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   float* s_dg = s_Y + kT * NLM;           // [kT][CLP]
   float* s_dy = s_dg + kT * CLP;          // [4][kT][NLM]
   float* s_g = s_dy + 4 * kT * NLM;       // [kSegCap][CL]
+  // TMEM columns: l3 = 0 component [0, 48); components j >= 1 of a round at
+  // 64 + 32 (j - 1); w0 at 320; emb^T dw0 at 384
+  constexpr int kJ0 = 0, kJ = 64, kW0 = 320, kDX = 384;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
@@ -1173,6 +1209,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
+    // dS of this thread's four channels, loaded ahead of the MMA waits
+    float dsv[2][2][NS];
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+          dsv[hf][e][q] = valid ? b.dS[sidx(tile, C * NS, (8 * hf + 2 * h + e) * NS + q, r)] : 0.0f;
     // column 16 lm + c: this thread's 4 channels of one lm are 8 contiguous bytes
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) {
@@ -1182,113 +1227,103 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), v4);
     }
     stage_g(b.gam[k], b.row_ptr, m, s_g);
+    float w0[2][8];                                   // w0 of channels 8 hf + 2h + e: w0[hf][3 e + l]
     if (k == 1) {
       row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
-      mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });       // w0
+      mm.run([&] { mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0); });
+      tmem_ld8(lanes(tmem) + kW0 + 6 * h, w0[0]);
+      tmem_ld8(lanes(tmem) + kW0 + 24 + 6 * h, w0[1]);
     }
-    float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc * 3 + l]
-    if (k == 1) tmem_ld16(lanes(tmem) + 12 * h, w0);
-    const float* dsg = b.dS;
-    float dw[12], dyl[NLM];
+    float dw[2][2 * 3], dyl[NLM];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) dw[q] = 0.0f;
+    for (int q = 0; q < 6; ++q) dw[0][q] = dw[1][q] = 0.0f;
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
-    for (int round = 0; round < 2; ++round) {
-      if (round == 0) {
-        mm.run([&] {
-          mma_k<Tin>(tmem + 64, DVT, 0, Wmix, 48, 1, true, 16);
-          for (int j = 1; j < 4; ++j) mma_k<Tin>(tmem + 112 + 64 * (j - 1), DVT, j, Wmix + kImgMix, 64, 1, true, 16);
-        });
-      } else {
-        mm.run([&] {
-          for (int j = 4; j < 9; ++j) mma_k<Tin>(tmem + 64 + 64 * (j - 4), DVT, j, Wmix + 2 * kImgMix, 64, 1, true, 16);
-        });
-      }
 #pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4) {
-        const int c = 4 * h + c4;
+    for (int hf = 0; hf < 2; ++hf) {
+      mm.run([&] {
+        if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, 48, 1, true, 16);
+        for (int j = 1; j < 9; ++j)
+          mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l_of(j) * kImgMix + 64 * hf, 32, 1, true, 16);
+      });
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = 8 * hf + 2 * h + e;
+        uint32_t t[36];
+        tmem_ld4_raw(lanes(tmem) + kJ0 + 3 * c, t);                         // l3 = 0: columns 3c + q
+#pragma unroll
+        for (int j = 1; j < 9; ++j) tmem_ld4_raw(lanes(tmem) + kJ + 32 * (j - 1) + 4 * (2 * h + e), t + 4 * j);
+#pragma unroll
+        for (int g = 0; g < 9; ++g) tmem_wait4(t + 4 * g);
         float dT[TP2_NT];
-        uint32_t t[20];
-        if (round == 0) {
-          tmem_ld4_raw(lanes(tmem) + 64 + 3 * c, t);                  // l3 = 0: columns 3c + q
 #pragma unroll
-          for (int j = 1; j < 4; ++j) tmem_ld4_raw(lanes(tmem) + 112 + 64 * (j - 1) + 4 * c, t + 4 * j);
+        for (int q = 0; q < 3; ++q) dT[q] = __uint_as_float(t[q]) + dsv[hf][e][q];
 #pragma unroll
-          for (int g = 0; g < 4; ++g) tmem_wait4(t + 4 * g);
+        for (int mm1 = 0; mm1 < 3; ++mm1)
 #pragma unroll
-          for (int q = 0; q < 3; ++q)
-            dT[q] = __uint_as_float(t[q]) + (valid ? dsg[sidx(tile, C * NS, c * NS + q, r)] : 0.0f);
+          for (int q = 0; q < 4; ++q) dT[3 + q * 3 + mm1] = __uint_as_float(t[4 + 4 * mm1 + q]);
 #pragma unroll
-          for (int mm1 = 0; mm1 < 3; ++mm1)
+        for (int mm2 = 0; mm2 < 5; ++mm2)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dT[3 + q * 3 + mm1] = __uint_as_float(t[4 + 4 * mm1 + q]);
-        } else {
-#pragma unroll
-          for (int j = 4; j < 9; ++j) tmem_ld4_raw(lanes(tmem) + 64 + 64 * (j - 4) + 4 * c, t + 4 * (j - 4));
-#pragma unroll
-          for (int g = 0; g < 5; ++g) tmem_wait4(t + 4 * g);
-#pragma unroll
-          for (int mm2 = 0; mm2 < 5; ++mm2)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = __uint_as_float(t[4 * mm2 + q]);
-        }
+          for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = __uint_as_float(t[16 + 4 * mm2 + q]);
         float V[NLM], G[NLM], dG[NLM], dVp[NLM];
         if (k == 1) {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[c4 * 3 + l_of(lm)] * s_Y[r * NLM + lm];
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[hf][3 * e + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
-            const float2 t = valid ? ldh2(b.V[k - 1], hidx(tile, CL, lm * C + (c & ~1), r)) : make_float2(0.f, 0.f);
-            V[lm] = (c4 & 1) ? t.y : t.x;
+            const float2 v2 = valid ? ldh2(b.V[k - 1], hidx(tile, CL, lm * C + (c & ~1), r)) : make_float2(0.f, 0.f);
+            V[lm] = e ? v2.y : v2.x;
           }
         }
         get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) {
-          dG[lm] = round == 0 ? 0.0f : s_dg[r * CLP + c * NLM + lm];
-          dVp[lm] = 0.0f;
-        }
-        if (round == 0) tp2_bwd_l3lt2(V, G, dT, dVp, dG);
-        else tp2_bwd_l3ge2(V, G, dT, dVp, dG);
+        for (int lm = 0; lm < NLM; ++lm) dG[lm] = dVp[lm] = 0.0f;
+        tp2_bwd(V, G, dT, dVp, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
         if (k >= 2) {
           if (valid)
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) {
-              float* dv = &b.dV[sidx(tile, CL, c * NLM + lm, r)];
-              *dv = round == 0 ? dVp[lm] : *dv + dVp[lm];
-            }
+            for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(tile, CL, c * NLM + lm, r)] = dVp[lm];
         } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
-            dw[c4 * 3 + l_of(lm)] = fmaf(dVp[lm], s_Y[r * NLM + lm], dw[c4 * 3 + l_of(lm)]);
-            dyl[lm] = fmaf(w0[c4 * 3 + l_of(lm)], dVp[lm], dyl[lm]);
+            dw[hf][3 * e + l_of(lm)] = fmaf(dVp[lm], s_Y[r * NLM + lm], dw[hf][3 * e + l_of(lm)]);
+            dyl[lm] = fmaf(w0[hf][3 * e + l_of(lm)], dVp[lm], dyl[lm]);
           }
         }
       }
     }
     if (k == 1) {
-#pragma unroll
-      for (int q = 0; q < 12; ++q) st1<Tin>(DW0, r, 12 * h + q, dw[q]);
-      mm.run([&] { mma_k<Tin>(tmem + 384, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
       float* dxg = b.dX;
-      epi(tmem, 384, 128, [&](int rr, int n0, const float* v) {
-        if (valid)
+      float dxo[32];                                  // columns 32h..32h+31, loaded ahead of the MMA wait
 #pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] += v[q];
-      });
+      for (int q = 0; q < 32; ++q) dxo[q] = valid ? dxg[sidx(tile, D, 32 * h + q, r)] : 0.0f;
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) st1<Tin>(DW0, r, 3 * (8 * hf + 2 * h) + q, dw[hf][q]);
+      mm.run([&] { mma_k<Tin>(tmem + kDX, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
+      float v[32];
+      tmem_ld32(lanes(tmem) + kDX + 32 * h, v);
+      if (valid)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) dxg[sidx(tile, D, 32 * h + q, r)] = dxo[q] + v[q];
     }
+    float dyo[NLM];
+    if (threadIdx.x < kT && k == 1)
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dyl[lm];
     __syncthreads();
     if (threadIdx.x < kT && valid && k == 1) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        b.dY[sidx(tile, NLM, lm, r)] += (s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
-                                     (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]);
+        b.dY[sidx(tile, NLM, lm, r)] = dyo[lm] + ((s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
+                                                  (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]));
     }
     seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
     __syncthreads();

@@ -180,6 +180,24 @@ UM_DEV void mma_tile_bmn(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, in
   }
 }
 
+// tcgen05.wait::ld with the loaded registers tied to it (in/out operands): no
+// use of them can be scheduled before the wait.  TMEM loads touch no generic
+// memory, so the wait carries no memory clobber and ordinary loads and stores
+// may be scheduled across it.
+template <int N>
+UM_DEV void tmem_wait_tied(uint32_t* r) {
+  static_assert(N % 8 == 0, "groups of 8");
+#pragma unroll
+  for (int g = 0; g < N; g += 8) {
+    if (g == 0)
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                   : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+    else
+      asm volatile("" : "+r"(r[g]), "+r"(r[g + 1]), "+r"(r[g + 2]), "+r"(r[g + 3]), "+r"(r[g + 4]), "+r"(r[g + 5]),
+                   "+r"(r[g + 6]), "+r"(r[g + 7]));
+  }
+}
+
 // ---- TMEM -> registers: 32 lanes x 32 columns (thread t of the warp gets
 // lane base + t, registers = consecutive columns) ----
 UM_DEV void tmem_ld32(uint32_t taddr, float* v) {
@@ -194,7 +212,7 @@ UM_DEV void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
         "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  tmem_wait_tied<32>(r);
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
@@ -207,7 +225,7 @@ UM_DEV void tmem_ld16(uint32_t taddr, float* v) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  tmem_wait_tied<16>(r);
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
@@ -221,7 +239,7 @@ UM_DEV void tmem_ld4_raw(uint32_t taddr, uint32_t* r) {
                : "r"(taddr));
 }
 UM_DEV void tmem_wait4(uint32_t* r) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])::"memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
 }
 
 UM_DEV void tmem_ld8(uint32_t taddr, float* v) {
@@ -230,10 +248,31 @@ UM_DEV void tmem_ld8(uint32_t taddr, float* v) {
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  tmem_wait_tied<8>(r);
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
+
+// registers -> TMEM (thread t of the warp writes lane base + t); the caller
+// waits with tmem_wait_st before the columns are read by an MMA
+UM_DEV void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31]));
+}
+UM_DEV void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]));
+}
+UM_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // Pack 8 floats as bf16 (round to nearest even) and store 16 bytes.
 UM_DEV void st_bf16x8(uint8_t* tile, uint32_t off, const float* v) {

@@ -19,6 +19,8 @@ cannot follow those flips: measured 5.7e-6 (BF16), 4.7e-6 (FP16) and 5.3e-5
 (FP16_SPLIT) relative at 432 atoms.  Bounds below carry margin, except the
 split mode's max |dF|, which is the 2e-3 eV/A acceptance bound of the
 mixed-precision path."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -104,3 +106,31 @@ def test_tensorcore_md_and_unsupported_model(main):
         al.allegro_energy_forces(tctx, p, s.astype(np.int32), c, None, None, al.ALLEGRO_BF16)
     assert err.value.code == 10
     al.allegro_destroy(tctx)
+
+
+@pytest.mark.parametrize("mode", ["fp16", "fp16split"])
+def test_tensorcore_three_layers(mode):
+    """Three layers run the inner-layer passes twice (k = 1, 2): pass B1^T of
+    k = 2 writes dV^1 instead of the embedding adjoint.  The deeper model makes
+    the FP16 storage roundings more sensitive to their inputs: the emulating
+    oracle itself moves by 1.4e-6 relative in energy and 8e-4 eV/A in force
+    under 1e-8 A of random position noise (1e-7 and 2.7e-5 at 1e-10 A), and
+    the kernels' FP32 pair separations differ from FP64 by ~1e-7 A, so the
+    energy bound against the emulation is 1e-4 relative here."""
+    cfg = dataclasses.replace(synth.MAIN, n_layers=3)
+    blob = synth.make_blob(cfg, 44, sigma=energy_scale("main"))
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        prec, tol = MODES[mode]
+        pos, sp, cell = synth.make_ammonia(108, 0)
+        E, F, Ei = _gpu(ctx, pos, sp, cell, prec)
+        Er, Fr, _, pairs = OracleModel(blob).energy_forces(pos, sp, np.diag(cell))
+        Ee, Fe, _, _ = OracleModel(blob, emulate=mode).energy_forces(pos, sp, np.diag(cell), pairs=pairs)
+        E32, F32, _ = _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP32)
+    finally:
+        al.allegro_destroy(ctx)
+    assert abs(E32 - Er) <= 1e-5 * abs(Er) and np.abs(F32 - Fr).max() <= 1e-4 * max(1.0, np.abs(Fr).max())
+    assert abs(E - Ee) <= max(tol["erel"], 1e-4) * abs(Ee)
+    d = F - Fe
+    assert np.abs(d).max() <= tol["fmax"] and np.sqrt(np.mean(d * d)) <= tol["frms"]
+    assert np.abs(F - Fr).max() <= 2 * tol["fmax"]     # one more layer of operand rounding
