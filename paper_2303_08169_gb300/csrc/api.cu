@@ -499,7 +499,9 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   for (int k = 0; k <= kMaxLayers; ++k) {
     c->dfree(pb.gam[k]);
     c->dfree(pb.dgam[k]);
-    pb.gam[k] = pb.dgam[k] = nullptr;
+    c->dfree(pb.gsum[k]);
+    c->dfree(pb.dgsum[k]);
+    pb.gam[k] = pb.dgam[k] = pb.gsum[k] = pb.dgsum[k] = nullptr;
   }
   // per-pair arrays of the tensor-core path are tile-SoA over 128-pair tiles;
   // every per-pair array holds whole tiles (the passes prefetch the next
@@ -551,6 +553,11 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
     pb.gam[k] = c->dalloc<float>((size_t)rows * CL);
     pb.dgam[k] = c->dalloc<float>((size_t)rows * CL);
     ok = ok && pb.gam[k] && pb.dgam[k];
+    if (c->bf16_ok && ok) {
+      pb.gsum[k] = c->dalloc<float>((size_t)std::max<int64_t>(c->n_atoms_alloc, 1) * CL);
+      pb.dgsum[k] = c->dalloc<float>((size_t)std::max<int64_t>(c->n_atoms_alloc, 1) * CL);
+      ok = pb.gsum[k] && pb.dgsum[k];
+    }
   }
   if (!ok) {
     c->capacity = 0;

@@ -85,6 +85,9 @@ struct PassBufs {
   // per (tile, atom) partial sums, index (tile + atom)
   float* gam[kMaxLayers + 1];   // Gamma^k partials, k = 1..L
   float* dgam[kMaxLayers + 1];  // dGamma^k partials
+  // tensor-core path: per-atom sums of those partials (N x C NLM)
+  float* gsum[kMaxLayers + 1] = {};
+  float* dgsum[kMaxLayers + 1] = {};
   double* epart;                // sum_j E_ij partials
   int tile;                     // pairs per tile (all passes)
   TrainBufs tr;                 // training dumps (FP32 path)

@@ -183,18 +183,6 @@ AL_DEV void seg_store(float* __restrict__ part, const Meta& m, int W, F&& f) {
   }
 }
 
-// Gamma (or dGamma) of atom i, channel c: sum of its partials in tile order
-AL_DEV void load_g(const float* __restrict__ part, const int* __restrict__ row_ptr, int i, int c, float* G) {
-  const int t0 = row_ptr[i] / kT, t1 = (row_ptr[i + 1] - 1) / kT;
-#pragma unroll
-  for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
-  for (int tt = t0; tt <= t1; ++tt) {
-    const float* g = part + (size_t)(tt + i) * CL + c * NLM;
-#pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) G[lm] += g[lm];
-  }
-}
-
 // Per-pair arrays of this path use a tile-SoA layout: element (pair p,
 // feature f) of a W-wide array lives at ((p / 128) * W + f) * 128 + p % 128,
 // so the 32 lanes of a warp (consecutive tile rows) touch consecutive floats.
@@ -235,33 +223,51 @@ AL_DEV void prefetch_meta(const PassBufs& b, int nt) {
   bulk_prefetch_l2(b.pcode + (size_t)nt * kT, kT * 4);
 }
 
-// Gamma (or dGamma) of the tile's first kSegCap centre atoms, summed once per
-// tile into shared memory; rows of later segments read the partials directly.
+// Gamma (or dGamma) per atom: k_atom_sums reduces the per-(tile, atom)
+// partials of the producing pass (in tile order) into gsum[i][x]; the
+// consumers copy the rows of the tile's first kSegCap centre atoms into
+// shared memory, and rows of later segments read gsum directly.
 constexpr int kSegCap = 8;
-AL_DEV void stage_g(const float* __restrict__ part, const int* __restrict__ row_ptr, const Meta& m, float* s) {
+AL_DEV void stage_g(const float* __restrict__ gsum, const Meta& m, float* s) {
   const int ns = min(m.nseg, kSegCap);
-  for (int idx = threadIdx.x; idx < ns * CL; idx += blockDim.x) {
-    const int sg = idx / CL, x = idx % CL;
-    const int i = m.atom[sg];
-    const int t0 = row_ptr[i] / kT, t1 = (row_ptr[i + 1] - 1) / kT;
-    float acc = 0.0f;
-    for (int tt = t0; tt <= t1; ++tt) acc += part[(size_t)(tt + i) * CL + x];
-    s[sg * CL + x] = acc;
+  for (int idx = threadIdx.x; idx < ns * (CL / 4); idx += blockDim.x) {
+    const int sg = idx / (CL / 4), x = idx % (CL / 4);
+    reinterpret_cast<float4*>(s + sg * CL)[x] = reinterpret_cast<const float4*>(gsum + (size_t)m.atom[sg] * CL)[x];
   }
 }
-AL_DEV void get_g(const float* s, const float* __restrict__ part, const int* __restrict__ row_ptr, const Meta& m,
-                  int r, bool valid, int c, float* G) {
+AL_DEV void get_g(const float* s, const float* __restrict__ gsum, const Meta& m, int r, bool valid, int c, float* G) {
   if (!valid) {
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
     return;
   }
   const int sg = m.seg[r];
-  if (sg < kSegCap) {
+  const float* g = sg < kSegCap ? s + sg * CL + c * NLM : gsum + (size_t)m.pi[r] * CL + c * NLM;
 #pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) G[lm] = s[sg * CL + c * NLM + lm];
-  } else {
-    load_g(part, row_ptr, m.pi[r], c, G);
+  for (int lm = 0; lm < NLM; ++lm) G[lm] = g[lm];
+}
+
+// gsum[i][x] = sum over the tiles t0..t1 that hold atom i's pairs of the
+// partial row (t + i), in tile order (zero for an atom without pairs)
+__global__ void k_atom_sums(const float* __restrict__ part, const int* __restrict__ row_ptr, int n,
+                            const int* __restrict__ flags, float* __restrict__ gsum) {
+  if (*flags & 1) return;
+  constexpr int nq = CL / 4;
+  const int64_t total = (int64_t)n * nq;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / nq), x = (int)(idx % nq);
+    const int p0 = row_ptr[i], p1 = row_ptr[i + 1];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p1 > p0)
+      for (int tt = p0 / kT; tt <= (p1 - 1) / kT; ++tt) {
+        const float4 v = reinterpret_cast<const float4*>(part + (size_t)(tt + i) * CL)[x];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+      }
+    reinterpret_cast<float4*>(gsum + (size_t)i * CL)[x] = acc;
   }
 }
 
@@ -624,10 +630,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     const bool valid = r < m.np;
     if (k == 1) {
       row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
-      stage_g(b.gam[k], b.row_ptr, m, s_g);
+      stage_g(b.gsum[k], m, s_g);
       mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
     } else {
-      stage_g(b.gam[k], b.row_ptr, m, s_g);
+      stage_g(b.gsum[k], m, s_g);
       __syncthreads();
     }
     float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc * 3 + l]
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
             V[lm] = (c & 1) ? t.y : t.x;
           }
         }
-        get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
+        get_g(s_g, b.gsum[k], m, r, valid, c, G);
         tp2_fwd(V, G, Tv[e]);
 #pragma unroll
         for (int q = 0; q < NS; ++q) st1<Tin>(T, r, c * NS + q, Tv[e][q]);
@@ -835,7 +841,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       for (int lm = 0; lm < NLM; ++lm)
         vw[cp][lm] = valid ? reinterpret_cast<const __half2*>(b.V[L - 1])[hidx(tile, CL, lm * C + 4 * h + 2 * cp, r)]
                            : __floats2half2_rn(0.f, 0.f);
-    stage_g(b.gam[L], b.row_ptr, m, s_g);
+    stage_g(b.gsum[L], m, s_g);
     __syncthreads();
     {
       float S[4 * NS];                                 // columns D + 12 h .. D + 12 h + 11
@@ -851,7 +857,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           float G[NLM];
-          get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, 4 * h + cp + e, G);
+          get_g(s_g, b.gsum[L], m, r, valid, 4 * h + cp + e, G);
           tp2_fwd_scalar(V2[e], G, S + (cp + e) * NS);
         }
       }
@@ -960,7 +966,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
           dV[lm] = 0.0f;
           dG[lm] = 0.0f;
         }
-        get_g(s_g, b.gam[L], b.row_ptr, m, r, valid, c, G);
+        get_g(s_g, b.gsum[L], m, r, valid, c, G);
         tp2_bwd_scalar(V, G, ds + cc * NS, dV, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
@@ -1043,7 +1049,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
     row_to_op<Tin>(HA, tile, r, b.X[k], D, 32 * h, valid, 32 * h, 32);
-    stage_g(b.dgam[k + 1], b.row_ptr, m, s_g);
+    stage_g(b.dgsum[k + 1], m, s_g);
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
     {
       float e[8], dy[NLM];
@@ -1054,7 +1060,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
         float dG[NLM];
-        get_g(s_g, b.dgam[k + 1], b.row_ptr, m, r, valid, c, dG);
+        get_g(s_g, b.dgsum[k + 1], m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -1226,7 +1232,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       for (int q = 0; q < 4; ++q) v4[q] = valid ? b.dV[sidx(tile, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
       st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), v4);
     }
-    stage_g(b.gam[k], b.row_ptr, m, s_g);
+    stage_g(b.gsum[k], m, s_g);
     float w0[2][8];                                   // w0 of channels 8 hf + 2h + e: w0[hf][3 e + l]
     if (k == 1) {
       row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
@@ -1277,7 +1283,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
             V[lm] = e ? v2.y : v2.x;
           }
         }
-        get_g(s_g, b.gam[k], b.row_ptr, m, r, valid, c, G);
+        get_g(s_g, b.gsum[k], m, r, valid, c, G);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) dG[lm] = dVp[lm] = 0.0f;
         tp2_bwd(V, G, dT, dVp, dG);
@@ -1407,7 +1413,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
       st_h0<Tin, kSplit>(H0, r, h0);
     }
-    stage_g(b.dgam[1], b.row_ptr, m, s_g);
+    stage_g(b.dgsum[1], m, s_g);
     mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });   // z1
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
@@ -1433,7 +1439,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
         float dG[NLM];
-        get_g(s_g, b.dgam[1], b.row_ptr, m, r, valid, c, dG);
+        get_g(s_g, b.dgsum[1], m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -1564,21 +1570,32 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
   auto mark = [&](int k) {
     if (km) km->mark(k, s);
   };
+  // per-atom sums of a pass's Gamma partials (timed with that pass)
+  auto sums = [&](const float* part, float* gsum) {
+    const int64_t items = (int64_t)b.n_atoms * (CL / 4);
+    if (items == 0) return;
+    const int blocks = (int)std::min<int64_t>((items + 255) / 256, (int64_t)(g_sms > 0 ? g_sms : 148) * 16);
+    k_atom_sums<<<blocks, 256, 0, s>>>(part, b.row_ptr, b.n_atoms, b.flags, gsum);
+  };
   mark(kPhStart);
   k_bf_a<Tin, kSplit><<<grid, kThr4, kSmA, s>>>(w, b);
+  sums(b.gam[1], b.gsum[1]);
   mark(kPhA);
   for (int k = 1; k < L; ++k) {
     k_bf_b1<Tin><<<grid, kThr4, kSmB1, s>>>(w, b, k);
     mark(kPhB);
     k_bf_b2<Tin><<<grid, kThr4, kSmB2, s>>>(w, b, k);
+    sums(b.gam[k + 1], b.gsum[k + 1]);
     mark(kPhB2);
   }
   k_bf_c<Tin, kSplit><<<grid, kThr4, kSmC, s>>>(w, b);
+  sums(b.dgam[L], b.dgsum[L]);
   mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
     k_bf_b2t<Tin><<<grid, kThr4, kSmB2T, s>>>(w, b, k);
     mark(kPhBT);
     k_bf_b1t<Tin><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
+    sums(b.dgam[k], b.dgsum[k]);
     mark(kPhBT2);
   }
   k_bf_at<Tin, kSplit><<<grid, kThr4, kSmAT, s>>>(w, b);
