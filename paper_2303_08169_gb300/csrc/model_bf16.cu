@@ -418,21 +418,34 @@ AL_DEV void st1(uint8_t* A, int r, int c, float v) {
   *reinterpret_cast<uint16_t*>(A + sw128_off(r, c, 128)) = Op<Tin>::bits(v);
 }
 
-// features [f0, f0+n) (f0 even) of tile row r of an FP16-pair array (W
-// wide), into operand columns [c0, c0+n)
-template <class Tin>
-AL_DEV void row_to_op(uint8_t* A, int tile, int r, const float* __restrict__ g, int W, int f0, bool valid,
-                      int c0, int n) {
-#pragma unroll 2
-  for (int k = 0; k < n; k += 16) {
-    float v[16];
+// Operand staging of FP16-pair state in two steps, so that a tile's loads
+// are all issued before any of them is waited for: ld_row reads the N / 2
+// words of features [f0, f0 + N) (f0 even) of tile row r of a W-wide array
+// (zeros for an invalid row); st_row writes them into operand columns
+// [c0, c0 + N) of row r (FP16 operands take the words as they are).
+template <int N>
+AL_DEV void ld_row(uint32_t* w, const float* __restrict__ g, int tile, int r, int W, int f0, bool valid) {
 #pragma unroll
-    for (int q = 0; q < 16; q += 2) {
-      const float2 t = valid ? ldh2(g, hidx(tile, W, f0 + k + q, r)) : make_float2(0.0f, 0.0f);
-      v[q] = t.x;
-      v[q + 1] = t.y;
+  for (int q = 0; q < N / 2; ++q)
+    w[q] = valid ? reinterpret_cast<const uint32_t*>(g)[hidx(tile, W, f0 + 2 * q, r)] : 0u;
+}
+template <class Tin, int N>
+AL_DEV void st_row(uint8_t* A, int r, int c0, const uint32_t* w) {
+#pragma unroll
+  for (int k = 0; k < N; k += 8) {
+    uint32_t u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (Op<Tin>::fmt == 0) {
+        u[q] = w[k / 2 + q];
+      } else {
+        __half2 hh;
+        memcpy(&hh, &w[k / 2 + q], 4);
+        const float2 f = __half22float2(hh);
+        u[q] = Op<Tin>::pack2(f.x, f.y);
+      }
     }
-    st16<Tin>(A, r, c0 + k, v);
+    *reinterpret_cast<uint4*>(A + sw128_off(r, c0 + k, 128)) = make_uint4(u[0], u[1], u[2], u[3]);
   }
 }
 
@@ -610,6 +623,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   float* s_Y = reinterpret_cast<float*>(T + kOpT);
   float* s_g = s_Y + kT * NLM;            // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  uint32_t xw[16];                                    // x^0 operand words (k = 1), one tile ahead
+  ld_row<32>(xw, b.X[0], blockIdx.x, r, D, 32 * h, k == 1 && r < min(kT, P - (int)blockIdx.x * kT));
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -619,6 +634,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       if (k == 1) prefetch_rows_h(b.X[0], D, nt);
       else prefetch_rows_h(b.V[k - 1], CL, nt);
     }
+    const bool valid = r < m.np;
     if (threadIdx.x < kT) {
       float u[3], d, fc, dfc, Y[NLM];
 #pragma unroll
@@ -627,9 +643,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    const bool valid = r < m.np;
     if (k == 1) {
-      row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
+      st_row<Tin, 32>(X, r, 32 * h, xw);
       stage_g(b.gsum[k], m, s_g);
       mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
     } else {
@@ -688,6 +703,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       }
     });
     {
+      const int nt = tile + (int)gridDim.x;
+      ld_row<32>(xw, b.X[0], nt, r, D, 32 * h, k == 1 && r < min(kT, P - nt * kT));
+    }
+    {
       const uint32_t base = lanes(tmem);
       for (int j = h; j < 9; j += 4) {                // components h, h + 4, h + 8
         float v[16];
@@ -721,6 +740,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  uint32_t xw[16], sw[8];                             // [x^{k-1}, S^k] operand words, one tile ahead
+  {
+    const bool vt = r < min(kT, P - (int)blockIdx.x * kT);
+    ld_row<32>(xw, b.X[k - 1], blockIdx.x, r, D, 32 * h, vt);
+    ld_row<16>(sw, b.S[k], blockIdx.x, r, C * NS, 16 * max(h - 1, 0), vt && h >= 1);
+  }
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -731,6 +756,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       prefetch_rows_h(b.S[k], C * NS, nt);
     }
     const bool valid = r < m.np;
+    const float* xg = b.X[k - 1];
     if (threadIdx.x < kT) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
@@ -740,10 +766,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    const float* xg = b.X[k - 1];
-    row_to_op<Tin>(HA, tile, r, xg, D, 32 * h, valid, 32 * h, 32);
+    st_row<Tin, 32>(HA, r, 32 * h, xw);
     if (h >= 1) {
-      row_to_op<Tin>(HA, tile, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
+      st_row<Tin, 16>(HA, r, 128 + 16 * (h - 1), sw);
     } else {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
@@ -771,6 +796,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
         for (int q = 0; q < 16; q += 2) sth2(b.X[k], hidx(tile, D, n0 + q, rr), o[q], o[q + 1]);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
+    {
+      const int nt = tile + (int)gridDim.x;
+      const bool vt = r < min(kT, P - nt * kT);
+      ld_row<32>(xw, b.X[k - 1], nt, r, D, 32 * h, vt);
+      ld_row<16>(sw, b.S[k], nt, r, C * NS, 16 * max(h - 1, 0), vt && h >= 1);
+    }
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -782,6 +813,20 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     __syncthreads();
   }
   BF_EPILOGUE
+}
+
+// V^{L-1} words of channel pairs (4h, 4h+1), (4h+2, 4h+3) and the x^{L-1}
+// operand words of pass C for tile t, thread (r, h) (zeros past the last tile)
+AL_DEV void c_loads(const PassBufs& b, int L, int t, int P, int r, int h, __half2 (&vw)[2][NLM],
+                    uint32_t (&xw)[16]) {
+  const bool vt = r < min(kT, P - t * kT);
+#pragma unroll
+  for (int cp = 0; cp < 2; ++cp)
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm)
+      vw[cp][lm] = vt ? reinterpret_cast<const __half2*>(b.V[L - 1])[hidx(t, CL, lm * C + 4 * h + 2 * cp, r)]
+                      : __floats2half2_rn(0.f, 0.f);
+  ld_row<32>(xw, b.X[L - 1], t, r, D, 32 * h, vt);
 }
 
 // ============================================================================
@@ -816,6 +861,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   float* s_du = s_eq + 4 * kT;                         // [4][kT]
   float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  // V^{L-1} (one FP16 channel pair per word) and x^{L-1} operand words of a
+  // tile, in registers; the next tile's are loaded during this tile's tail
+  __half2 vw[2][NLM];
+  uint32_t xw[16];
+  c_loads(b, L, blockIdx.x, P, r, h, vw, xw);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -826,21 +876,13 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       prefetch_rows_h(b.X[L - 1], D, nt);
     }
     const bool valid = r < m.np;
+    const float* xg = b.X[L - 1];
     if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
       if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
       s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
     }
-    // V^{L-1} of this thread's channel pairs (4h, 4h+1), (4h+2, 4h+3): one
-    // FP16 pair per word, loaded ahead of the Gamma staging
-    __half2 vw[2][NLM];
-#pragma unroll
-    for (int cp = 0; cp < 2; ++cp)
-#pragma unroll
-      for (int lm = 0; lm < NLM; ++lm)
-        vw[cp][lm] = valid ? reinterpret_cast<const __half2*>(b.V[L - 1])[hidx(tile, CL, lm * C + 4 * h + 2 * cp, r)]
-                           : __floats2half2_rn(0.f, 0.f);
     stage_g(b.gsum[L], m, s_g);
     __syncthreads();
     {
@@ -864,8 +906,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 #pragma unroll
       for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
     }
-    const float* xg = b.X[L - 1];
-    row_to_op<Tin>(HA, tile, r, xg, D, 32 * h, valid, 32 * h, 32);
+    st_row<Tin, 32>(HA, r, 32 * h, xw);
     if (h == 3) {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
@@ -975,6 +1016,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
           for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(tile, CL, c * NLM + lm, r)] = dV[lm];
       }
     }
+    c_loads(b, L, tile + (int)gridDim.x, P, r, h, vw, xw);
     __syncthreads();
     {
       // energy partials in FP64, one warp per segment: lanes stride the
@@ -1025,6 +1067,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   float* s_du = s_dy + 4 * kT * NLM;   // [4][kT]
   float* s_g = s_du + 4 * kT;      // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  uint32_t xw[16];                                    // x^k operand words, one tile ahead
+  ld_row<32>(xw, b.X[k], blockIdx.x, r, D, 32 * h, r < min(kT, P - (int)blockIdx.x * kT));
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -1048,8 +1092,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    row_to_op<Tin>(HA, tile, r, b.X[k], D, 32 * h, valid, 32 * h, 32);
+    st_row<Tin, 32>(HA, r, 32 * h, xw);
     stage_g(b.dgsum[k + 1], m, s_g);
+    uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env MMAs
+    ld_row<32>(xw2, b.X[k - 1], tile, r, D, 32 * h, valid);
+    if (h >= 1) ld_row<16>(sw, b.S[k], tile, r, C * NS, 16 * (h - 1), valid);
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
     {
       float e[8], dy[NLM];
@@ -1073,9 +1120,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dy[lm];
     }
     mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
-    row_to_op<Tin>(HA, tile, r, b.X[k - 1], D, 32 * h, valid, 32 * h, 32);
+    st_row<Tin, 32>(HA, r, 32 * h, xw2);
     if (h >= 1) {
-      row_to_op<Tin>(HA, tile, r, b.S[k], C * NS, 16 * (h - 1), valid, 128 + 16 * (h - 1), 16);
+      st_row<Tin, 16>(HA, r, 128 + 16 * (h - 1), sw);
     } else {
       float z[16] = {};
       st16<Tin>(HA, r, 176, z);
@@ -1139,6 +1186,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] = dh[q];
       });
+      const int nt = tile + (int)gridDim.x;
+      ld_row<32>(xw, b.X[k], nt, r, D, 32 * h, r < min(kT, P - nt * kT));
       float ds[16];                                   // ds columns 12 h .. 12 h + 11
       tmem_ld16(lanes(tmem) + 288 + 128 + 12 * h, ds);
       if (valid)
@@ -1159,6 +1208,24 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 }
 
 // ============================================================================
+// per-pair inputs of pass B1^T for tile t, thread (r, h)
+AL_DEV void b1t_loads(const PassBufs& b, int k, int t, int P, int r, int h, float (&dv)[NLM][4],
+                      float (&dsv)[2][2][NS], uint32_t (&xw)[16]) {
+  const bool vt = r < min(kT, P - t * kT);
+#pragma unroll
+  for (int lm = 0; lm < NLM; ++lm)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dv[lm][q] = vt ? b.dV[sidx(t, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+        dsv[hf][e][q] = vt ? b.dS[sidx(t, C * NS, (8 * hf + 2 * h + e) * NS + q, r)] : 0.0f;
+  ld_row<32>(xw, b.X[0], t, r, D, 32 * h, vt && k == 1);
+}
+
 // Pass B1_k^T: adjoint of mixing and of the tensor product of layer k:
 // dV^{k-1} (k >= 2) or, for k = 1, the embedding adjoint into dx^0 and dY;
 // dGamma^k partials.
@@ -1190,6 +1257,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   // 64 + 32 (j - 1); w0 at 320; emb^T dw0 at 384
   constexpr int kJ0 = 0, kJ = 64, kW0 = 320, kDX = 384;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  // per-pair inputs of a tile, in registers: dV (4 channels x 9 components),
+  // dS of this thread's four channels, the x^0 operand columns.  The next
+  // tile's are loaded during this tile's tail (software pipelining).
+  float dv[NLM][4], dsv[2][2][NS];
+  uint32_t xw[16];
+  b1t_loads(b, k, blockIdx.x, P, r, h, dv, dsv, xw);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -1215,27 +1288,13 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    // dS of this thread's four channels, loaded ahead of the MMA waits
-    float dsv[2][2][NS];
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-#pragma unroll
-        for (int q = 0; q < NS; ++q)
-          dsv[hf][e][q] = valid ? b.dS[sidx(tile, C * NS, (8 * hf + 2 * h + e) * NS + q, r)] : 0.0f;
     // column 16 lm + c: this thread's 4 channels of one lm are 8 contiguous bytes
 #pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) {
-      float v4[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v4[q] = valid ? b.dV[sidx(tile, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
-      st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), v4);
-    }
+    for (int lm = 0; lm < NLM; ++lm) st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), dv[lm]);
     stage_g(b.gsum[k], m, s_g);
     float w0[2][8];                                   // w0 of channels 8 hf + 2h + e: w0[hf][3 e + l]
     if (k == 1) {
-      row_to_op<Tin>(X, tile, r, b.X[0], D, 32 * h, valid, 32 * h, 32);
+      st_row<Tin, 32>(X, r, 32 * h, xw);
       mm.run([&] { mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0); });
       tmem_ld8(lanes(tmem) + kW0 + 6 * h, w0[0]);
       tmem_ld8(lanes(tmem) + kW0 + 24 + 6 * h, w0[1]);
@@ -1318,6 +1377,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) dxg[sidx(tile, D, 32 * h + q, r)] = dxo[q] + v[q];
     }
+    b1t_loads(b, k, tile + (int)gridDim.x, P, r, h, dv, dsv, xw);   // zeros past the last tile
     float dyo[NLM];
     if (threadIdx.x < kT && k == 1)
 #pragma unroll
