@@ -1445,18 +1445,25 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       prefetch_rows(b.dY, NLM, nt);
     }
     const bool valid = r < m.np;
-    if (threadIdx.x < kT) {
-      float h0[16], Y[NLM], u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f, B[NB], dB[NB];
+    if (h == 0) {                                     // geometry, envelope, harmonics
+      float Y[NLM], u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
+      float* g = s_geo + r * GP;
+      g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+    } else if (h == 1) {                              // two-body input row: species, Bessel basis
+      float h0[16], B[NB], dB[NB];
 #pragma unroll
       for (int q = 0; q < 16; ++q) h0[q] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-#pragma unroll
       for (int q = 0; q < NB; ++q) dB[q] = 0.0f;
       if (valid) {
-        geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
-        bessel<NB>(d, w.rc, B, dB);
+        const float dx = b.dR[sidx(tile, 3, 0, r)], dy = b.dR[sidx(tile, 3, 1, r)], dz = b.dR[sidx(tile, 3, 2, r)];
         const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
+        bessel<NB>(sqrtf(dx * dx + dy * dy + dz * dz), w.rc, B, dB);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {                 // one-hot species (no dynamic register index)
           h0[q] = zi == q ? 1.0f : 0.0f;
@@ -1465,12 +1472,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
       }
-      float* g = s_geo + r * GP;
-      g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
 #pragma unroll
       for (int q = 0; q < NB; ++q) s_dB[r * GP + q] = dB[q];
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
       st_h0<Tin, kSplit>(H0, r, h0);
     }
     stage_g(b.dgsum[1], m, s_g);
