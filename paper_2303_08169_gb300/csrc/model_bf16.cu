@@ -114,7 +114,29 @@ struct Meta {
   int wc[4];
 };
 
-AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
+// Neighbour-list entries of tile row t (threads t < 128), loaded one tile
+// ahead into registers: i, j, image code, and for the first lane of each warp
+// the centre atom of the row before it
+struct MetaPre {
+  int i, j, code, prev;
+};
+AL_DEV MetaPre meta_load(const PassBufs& b, int tile, int P) {
+  MetaPre q{-1, 0, 62, -1};
+  const int t = threadIdx.x;
+  if (t < kT) {
+    const int p0 = tile * kT;
+    const int np = min(kT, P - p0);
+    if (t < np) {
+      q.i = b.pi[p0 + t];
+      q.j = b.pj[p0 + t];
+      q.code = b.pcode[p0 + t];
+    }
+    if ((t & 31) == 0 && t > 0 && t - 1 < np) q.prev = b.pi[p0 + t - 1];
+  }
+  return q;
+}
+
+AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m, const MetaPre& q) {
   const int t = threadIdx.x;
   const int p0 = tile * kT;
   const int np = min(kT, P - p0);
@@ -124,17 +146,17 @@ AL_DEV void meta_setup(const PassBufs& b, int tile, int P, Meta& m) {
   // (every pass ends its tile with a barrier, so the previous tile is done with m)
   if (t < kT) {
     if (t < np) {
-      i = b.pi[p0 + t];
+      i = q.i;
       m.pi[t] = i;
-      m.pj[t] = b.pj[p0 + t];
-      m.code[t] = b.pcode[p0 + t];
+      m.pj[t] = q.j;
+      m.code[t] = q.code;
     } else {
       m.pi[t] = 0;
       m.pj[t] = 0;
       m.code[t] = 62;
     }
     int prev = __shfl_up_sync(0xffffffffu, i, 1);
-    if ((t & 31) == 0) prev = (t > 0 && t - 1 < np) ? b.pi[p0 + t - 1] : -1;
+    if ((t & 31) == 0) prev = q.prev;
     head = t < np && (t == 0 || i != prev);          // first pair of a centre atom's run
     mask = __ballot_sync(0xffffffffu, head);
     if ((t & 31) == 0) m.wc[t >> 5] = __popc(mask);
@@ -544,8 +566,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
   float* s_fc = reinterpret_cast<float*>(A1lo + (kSplit ? kOp128 : 0));
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -594,6 +617,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
         for (int q = 0; q < 16; q += 2) sth2(b.X[0], hidx(tile, D, n0 + q, r), o[q], o[q + 1]);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
+    mq = meta_load(b, tile + (int)gridDim.x, P);
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -625,8 +649,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   uint32_t xw[16];                                    // x^0 operand words (k = 1), one tile ahead
   ld_row<32>(xw, b.X[0], blockIdx.x, r, D, 32 * h, k == 1 && r < min(kT, P - (int)blockIdx.x * kT));
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -705,6 +730,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     {
       const int nt = tile + (int)gridDim.x;
       ld_row<32>(xw, b.X[0], nt, r, D, 32 * h, k == 1 && r < min(kT, P - nt * kT));
+      mq = meta_load(b, nt, P);
     }
     {
       const uint32_t base = lanes(tmem);
@@ -746,8 +772,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     ld_row<32>(xw, b.X[k - 1], blockIdx.x, r, D, 32 * h, vt);
     ld_row<16>(sw, b.S[k], blockIdx.x, r, C * NS, 16 * max(h - 1, 0), vt && h >= 1);
   }
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -801,6 +828,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       const bool vt = r < min(kT, P - nt * kT);
       ld_row<32>(xw, b.X[k - 1], nt, r, D, 32 * h, vt);
       ld_row<16>(sw, b.S[k], nt, r, C * NS, 16 * max(h - 1, 0), vt && h >= 1);
+      mq = meta_load(b, nt, P);
     }
     if (threadIdx.x < kT) {
       float v[16];
@@ -866,8 +894,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   __half2 vw[2][NLM];
   uint32_t xw[16];
   c_loads(b, L, blockIdx.x, P, r, h, vw, xw);
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -1017,6 +1046,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       }
     }
     c_loads(b, L, tile + (int)gridDim.x, P, r, h, vw, xw);
+    mq = meta_load(b, tile + (int)gridDim.x, P);
     __syncthreads();
     {
       // energy partials in FP64, one warp per segment: lanes stride the
@@ -1069,8 +1099,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   uint32_t xw[16];                                    // x^k operand words, one tile ahead
   ld_row<32>(xw, b.X[k], blockIdx.x, r, D, 32 * h, r < min(kT, P - (int)blockIdx.x * kT));
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -1119,7 +1150,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dy[lm];
     }
-    mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });     // env^T de
+    // [x^{k-1}, S^k] replaces x^k in HA (the env MMA has completed); env^T de
+    // and z1 are independent and go in one commit
     st_row<Tin, 32>(HA, r, 32 * h, xw2);
     if (h >= 1) {
       st_row<Tin, 16>(HA, r, 128 + 16 * (h - 1), sw);
@@ -1130,7 +1162,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
     float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
 #pragma unroll
     for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
-    mm.run([&] { mma_k<Tin>(tmem + 32, HA, 0, Wl0, 128, 11, false, 0); });     // z1
+    mm.run([&] {
+      mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16);                    // env^T de
+      mma_k<Tin>(tmem + 32, HA, 0, Wl0, 128, 11, false, 0);                     // z1
+    });
     epi(tmem, 32, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
@@ -1188,6 +1223,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       });
       const int nt = tile + (int)gridDim.x;
       ld_row<32>(xw, b.X[k], nt, r, D, 32 * h, r < min(kT, P - nt * kT));
+      mq = meta_load(b, nt, P);
       float ds[16];                                   // ds columns 12 h .. 12 h + 11
       tmem_ld16(lanes(tmem) + 288 + 128 + 12 * h, ds);
       if (valid)
@@ -1263,8 +1299,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   float dv[NLM][4], dsv[2][2][NS];
   uint32_t xw[16];
   b1t_loads(b, k, blockIdx.x, P, r, h, dv, dsv, xw);
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -1293,12 +1330,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     for (int lm = 0; lm < NLM; ++lm) st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), dv[lm]);
     stage_g(b.gsum[k], m, s_g);
     float w0[2][8];                                   // w0 of channels 8 hf + 2h + e: w0[hf][3 e + l]
-    if (k == 1) {
-      st_row<Tin, 32>(X, r, 32 * h, xw);
-      mm.run([&] { mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0); });
-      tmem_ld8(lanes(tmem) + kW0 + 6 * h, w0[0]);
-      tmem_ld8(lanes(tmem) + kW0 + 24 + 6 * h, w0[1]);
-    }
+    if (k == 1) st_row<Tin, 32>(X, r, 32 * h, xw);
     float dw[2][2 * 3], dyl[NLM];
 #pragma unroll
     for (int q = 0; q < 6; ++q) dw[0][q] = dw[1][q] = 0.0f;
@@ -1307,10 +1339,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
       mm.run([&] {
+        if (hf == 0 && k == 1) mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0);   // w0 = emb x^0
         if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, 48, 1, true, 16);
         for (int j = 1; j < 9; ++j)
           mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l_of(j) * kImgMix + 64 * hf, 32, 1, true, 16);
       });
+      if (hf == 0 && k == 1) {
+        tmem_ld8(lanes(tmem) + kW0 + 6 * h, w0[0]);
+        tmem_ld8(lanes(tmem) + kW0 + 24 + 6 * h, w0[1]);
+      }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int c = 8 * hf + 2 * h + e;
@@ -1378,6 +1415,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
         for (int q = 0; q < 32; ++q) dxg[sidx(tile, D, 32 * h + q, r)] = dxo[q] + v[q];
     }
     b1t_loads(b, k, tile + (int)gridDim.x, P, r, h, dv, dsv, xw);   // zeros past the last tile
+    mq = meta_load(b, tile + (int)gridDim.x, P);
     float dyo[NLM];
     if (threadIdx.x < kT && k == 1)
 #pragma unroll
@@ -1434,8 +1472,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
   // env1^T MMA
   float* s_dyq = reinterpret_cast<float*>(X);
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m);
+    meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
@@ -1514,6 +1553,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) s_dyq[(h * kT + r) * NLM + lm] = dy[lm];
     }
+    float dxo[32];                                    // dx^0, columns 32h..32h+31, in flight during the MMA
+#pragma unroll
+    for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
     mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });    // env1^T de
     if (h == 0)
 #pragma unroll
@@ -1521,20 +1563,21 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
         s_dy[r * NLM + lm] = (s_dyq[r * NLM + lm] + s_dyq[(kT + r) * NLM + lm]) +
                              (s_dyq[(2 * kT + r) * NLM + lm] + s_dyq[(3 * kT + r) * NLM + lm]);
     {
-      float du = 0.0f;
-      const float* dxg = b.dX;
-      epi(tmem, 288, 128, [&](int rr, int n0, const float* dxe) {
+      float du = 0.0f, dxe[32];
+      tmem_ld32(lanes(tmem) + 288 + 32 * h, dxe);
+      const float fc = s_geo[r * GP + 4];
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
         float z2[16], o[16];
-        tmem_ld16(lanes(tmem) + 128 + n0, z2);
-        const float fc = s_geo[rr * GP + 4];
+        tmem_ld16(lanes(tmem) + 128 + 32 * h + 16 * hf, z2);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const float dx = dxe[q] + (valid ? dxg[sidx(tile, D, n0 + q, rr)] : 0.0f);
+          const float dx = dxe[16 * hf + q] + dxo[16 * hf + q];
           du = fmaf(dx, silu_b(z2[q]), du);
           o[q] = dx * fc * dsilu_b(z2[q]);
         }
-        st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o);
-      });
+        st16_op<Tin, kSplit>(A1, A1lo, r, 32 * h + 16 * hf, o);
+      }
       s_du[h * kT + r] = du;
     }
     mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, true, 128); });   // da1
@@ -1545,10 +1588,17 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
       st16_op<Tin, kSplit>(X, A1lo, rr, n0, o);
     });
+    float duo = 0.0f, dyo[NLM];                       // loaded ahead of the MMA wait
+    if (threadIdx.x < kT) {
+      duo = valid ? b.dU[sidx(tile, 1, 0, r)] : 0.0f;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
+    }
     mm.run([&] {                                                                // dh0
       mma_k<Tin>(tmem + 416, X, 0, Wtb0, kSplit ? 48 : 16, 8, true, 128);
       if (kSplit) mma_k<Tin>(tmem + 416, A1lo, 0, Wtb0, 48, 8, true, 128, true);
     });
+    mq = meta_load(b, tile + (int)gridDim.x, P);
     if (threadIdx.x < kT) {
       float dh[16];
       tmem_ld16(lanes(tmem) + 416, dh);
@@ -1563,12 +1613,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
         const float u[3] = {g[0], g[1], g[2]};
         const float d = g[3], dfc = g[5];
         const size_t pp = (size_t)(m.p0 + r);
-        float gd = ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]) + b.dU[sidx(tile, 1, 0, r)]) * dfc;
+        float gd = ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]) + duo) * dfc;
 #pragma unroll
         for (int n = 0; n < NB; ++n) gd = fmaf(dh[4 + n], s_dB[r * GP + n], gd);
         float dY[NLM];
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + b.dY[sidx(tile, NLM, lm, r)];
+        for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + dyo[lm];
         float gu[3];
         sph_harm_vjp<2>(u[0], u[1], u[2], dY, gu);
         const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
