@@ -224,6 +224,12 @@ AL_DEV size_t hidx(int tile, int W, int f, int r) { return ((size_t)tile * (W >>
 AL_DEV float r16(float x) { return __half2float(__float2half_rn(x)); }
 AL_DEV float2 ldh2(const float* a, size_t i) { return __half22float2(reinterpret_cast<const __half2*>(a)[i]); }
 AL_DEV void sth2(float* a, size_t i, float x, float y) { reinterpret_cast<__half2*>(a)[i] = __floats2half2_rn(x, y); }
+// dV^k is consumed only as the mixing-adjoint MMA operand of pass B1^T, so
+// it is stored in the operand type itself (component-major, two channels per
+// word, the layout of V^k): the same values the operand held when dV^k was
+// FP32, at half the bytes
+template <class Tin>
+AL_DEV void st_opw(float* a, size_t i, float x, float y) { reinterpret_cast<uint32_t*>(a)[i] = Op<Tin>::pack2(x, y); }
 
 // L2 prefetch of tile nt's block of a tile-SoA array (W features x 128 rows,
 // contiguous) and of its slice of the neighbour list: issued by one thread
@@ -1025,6 +1031,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     {
       float ds[16];                                    // columns D + 12 h ..: ds of channels 4h..4h+3
       tmem_ld16(lanes(tmem) + 128 + 12 * h, ds);
+      float dVe[NLM];                                  // dV of the even channel of a pair
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
@@ -1040,9 +1047,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         tp2_bwd_scalar(V, G, ds + cc * NS, dV, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
-        if (valid)
+        if (cc & 1) {
+          if (valid)
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(tile, CL, c * NLM + lm, r)] = dV[lm];
+            for (int lm = 0; lm < NLM; ++lm) st_opw<Tin>(b.dV, hidx(tile, CL, lm * C + c - 1, r), dVe[lm], dV[lm]);
+        } else {
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) dVe[lm] = dV[lm];
+        }
       }
     }
     c_loads(b, L, tile + (int)gridDim.x, P, r, h, vw, xw);
@@ -1245,13 +1257,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 
 // ============================================================================
 // per-pair inputs of pass B1^T for tile t, thread (r, h)
-AL_DEV void b1t_loads(const PassBufs& b, int k, int t, int P, int r, int h, float (&dv)[NLM][4],
+AL_DEV void b1t_loads(const PassBufs& b, int k, int t, int P, int r, int h, uint32_t (&dvw)[NLM][2],
                       float (&dsv)[2][2][NS], uint32_t (&xw)[16]) {
   const bool vt = r < min(kT, P - t * kT);
 #pragma unroll
   for (int lm = 0; lm < NLM; ++lm)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dv[lm][q] = vt ? b.dV[sidx(t, CL, (4 * h + q) * NLM + lm, r)] : 0.0f;
+    for (int q = 0; q < 2; ++q)
+      dvw[lm][q] = vt ? reinterpret_cast<const uint32_t*>(b.dV)[hidx(t, CL, lm * C + 4 * h + 2 * q, r)] : 0u;
 #pragma unroll
   for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
@@ -1274,7 +1287,7 @@ AL_DEV void b1t_loads(const PassBufs& b, int k, int t, int P, int r, int h, floa
 // whole tensor-product adjoint then runs in one round.
 // 512 threads: thread (r, h) owns tile row r and channels 2h, 2h + 1 of each
 // round (8 hf + 2h + e).
-template <class Tin>
+template <class Tin, bool kEmb>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
     bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
@@ -1296,9 +1309,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
   // per-pair inputs of a tile, in registers: dV (4 channels x 9 components),
   // dS of this thread's four channels, the x^0 operand columns.  The next
   // tile's are loaded during this tile's tail (software pipelining).
-  float dv[NLM][4], dsv[2][2][NS];
+  uint32_t dvw[NLM][2];                               // dV^k words (operand type): channels 4h..4h+3
+  float dsv[2][2][NS];
   uint32_t xw[16];
-  b1t_loads(b, k, blockIdx.x, P, r, h, dv, dsv, xw);
+  b1t_loads(b, k, blockIdx.x, P, r, h, dvw, dsv, xw);
   MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m, mq);
@@ -1306,9 +1320,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
       prefetch_rows(b.dR, 3, nt);
-      prefetch_rows(b.dV, CL, nt);
+      prefetch_rows_h(b.dV, CL, nt);
       prefetch_rows(b.dS, C * NS, nt);
-      if (k == 1) {
+      if (kEmb) {
         prefetch_rows_h(b.X[0], D, nt);
         prefetch_rows(b.dX, D, nt);
         prefetch_rows(b.dY, NLM, nt);
@@ -1327,24 +1341,26 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
     }
     // column 16 lm + c: this thread's 4 channels of one lm are 8 contiguous bytes
 #pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) st4<Tin>(DVT, sw128_off(r, 16 * lm + 4 * h, 128), dv[lm]);
+    for (int lm = 0; lm < NLM; ++lm)
+      *reinterpret_cast<uint2*>(DVT + sw128_off(r, 16 * lm + 4 * h, 128)) = make_uint2(dvw[lm][0], dvw[lm][1]);
     stage_g(b.gsum[k], m, s_g);
     float w0[2][8];                                   // w0 of channels 8 hf + 2h + e: w0[hf][3 e + l]
-    if (k == 1) st_row<Tin, 32>(X, r, 32 * h, xw);
+    if (kEmb) st_row<Tin, 32>(X, r, 32 * h, xw);
     float dw[2][2 * 3], dyl[NLM];
 #pragma unroll
     for (int q = 0; q < 6; ++q) dw[0][q] = dw[1][q] = 0.0f;
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
+    float dVe[NLM];                                   // !kEmb: dV^{k-1} of the even channel of a pair
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
       mm.run([&] {
-        if (hf == 0 && k == 1) mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0);   // w0 = emb x^0
+        if (hf == 0 && kEmb) mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0);   // w0 = emb x^0
         if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, 48, 1, true, 16);
         for (int j = 1; j < 9; ++j)
           mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l_of(j) * kImgMix + 64 * hf, 32, 1, true, 16);
       });
-      if (hf == 0 && k == 1) {
+      if (hf == 0 && kEmb) {
         tmem_ld8(lanes(tmem) + kW0 + 6 * h, w0[0]);
         tmem_ld8(lanes(tmem) + kW0 + 24 + 6 * h, w0[1]);
       }
@@ -1369,7 +1385,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = __uint_as_float(t[16 + 4 * mm2 + q]);
         float V[NLM], G[NLM], dG[NLM], dVp[NLM];
-        if (k == 1) {
+        if (kEmb) {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[hf][3 * e + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
@@ -1385,10 +1401,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
         tp2_bwd(V, G, dT, dVp, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
-        if (k >= 2) {
-          if (valid)
+        if (!kEmb) {                                 // dV^{k-1}: channel pairs (8 hf + 2h, + 1)
+          if (e == 0) {
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) b.dV[sidx(tile, CL, c * NLM + lm, r)] = dVp[lm];
+            for (int lm = 0; lm < NLM; ++lm) dVe[lm] = dVp[lm];
+          } else if (valid) {
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) st_opw<Tin>(b.dV, hidx(tile, CL, lm * C + c - 1, r), dVe[lm], dVp[lm]);
+          }
         } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
@@ -1398,7 +1418,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
         }
       }
     }
-    if (k == 1) {
+    if (kEmb) {
       float* dxg = b.dX;
       float dxo[32];                                  // columns 32h..32h+31, loaded ahead of the MMA wait
 #pragma unroll
@@ -1414,16 +1434,16 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) dxg[sidx(tile, D, 32 * h + q, r)] = dxo[q] + v[q];
     }
-    b1t_loads(b, k, tile + (int)gridDim.x, P, r, h, dv, dsv, xw);   // zeros past the last tile
+    b1t_loads(b, k, tile + (int)gridDim.x, P, r, h, dvw, dsv, xw);   // zeros past the last tile
     mq = meta_load(b, tile + (int)gridDim.x, P);
     float dyo[NLM];
-    if (threadIdx.x < kT && k == 1)
+    if (threadIdx.x < kT && kEmb)
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dyl[lm];
     __syncthreads();
-    if (threadIdx.x < kT && valid && k == 1) {
+    if (threadIdx.x < kT && valid && kEmb) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
         b.dY[sidx(tile, NLM, lm, r)] = dyo[lm] + ((s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
@@ -1670,7 +1690,8 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     cudaFuncSetAttribute(k_bf_b2<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
     cudaFuncSetAttribute(k_bf_c<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
     cudaFuncSetAttribute(k_bf_b2t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2T);
-    cudaFuncSetAttribute(k_bf_b1t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
+    cudaFuncSetAttribute(k_bf_b1t<Tin, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
+    cudaFuncSetAttribute(k_bf_b1t<Tin, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
     cudaFuncSetAttribute(k_bf_at<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1707,7 +1728,8 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
   for (int k = L - 1; k >= 1; --k) {
     k_bf_b2t<Tin><<<grid, kThr4, kSmB2T, s>>>(w, b, k);
     mark(kPhBT);
-    k_bf_b1t<Tin><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
+    if (k == 1) k_bf_b1t<Tin, true><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
+    else k_bf_b1t<Tin, false><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
     sums(b.dgam[k], b.dgsum[k]);
     mark(kPhBT2);
   }
