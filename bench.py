@@ -55,8 +55,7 @@ GEMM_MAC_PER_PAIR = {
     "pass_b1": 6144 + 8960,                               # embedding 128->48, mixing
     "pass_b2": 22528 + 16384 + 2048,                      # latent 176->128->128, env2
     "pass_c": 2 * (22528 + 16384 + 4096),                 # latent + energy hidden, fwd + adjoint
-    "pass_b2_adjoint": 2048 + 16384 + 22528,
-    "pass_b1_adjoint": 8960 + 6144,
+    "pass_b_adjoint": 2048 + 16384 + 22528 + 8960 + 6144,    # env, latent, mixing, embedding adjoints
     "pass_a_adjoint": 2048 + 16384 + 1536,
 }
 #   all multiply-adds incl. tensor products, scatters, energy output (FP32 path)
@@ -68,7 +67,7 @@ ALL_MAC_PER_PAIR = {
     "pass_a_adjoint": 288 + 2048 + 16384 + 1536,
 }
 TC_KERNELS = {"pass_a": "k_bf_a", "pass_b1": "k_bf_b1", "pass_b2": "k_bf_b2", "pass_c": "k_bf_c",
-              "pass_b2_adjoint": "k_bf_b2t", "pass_b1_adjoint": "k_bf_b1t", "pass_a_adjoint": "k_bf_at"}
+              "pass_b_adjoint": "k_bf_bt", "pass_a_adjoint": "k_bf_at"}
 FP32_KERNELS = {"pass_a": "k_pass_a", "pass_b": "k_pass_b", "pass_c": "k_pass_c",
                 "pass_b_adjoint": "k_pass_b_bwd", "pass_a_adjoint": "k_pass_a_bwd"}
 

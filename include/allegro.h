@@ -280,10 +280,11 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);
  *   ms_out[0] neighbour build   [1] pass A (two-body)   [2] passes B (layers
  *   below the last)   [3] pass C (last layer + energy, forward and adjoint)
  *   [4] passes B^T   [5] pass A^T (+ geometry adjoint)   [6] force assembly
- *   and reductions.  With n_out >= 11, the two kernels of each layer pass
- *   of the tensor-core path, summed over layers: [7] B1 (tensor product +
- *   mixing)  [8] B2 (latent MLP + env)  [9] B2^T  [10] B1^T; the FP32 path
- *   has one kernel per layer pass ([7] = [2], [9] = [4], [8] = [10] = 0).
+ *   and reductions.  With n_out >= 9, the two kernels of each forward layer
+ *   pass of the tensor-core path, summed over layers: [7] B1 (tensor product
+ *   + mixing)  [8] B2 (latent MLP + env); the FP32 path has one kernel per
+ *   layer pass ([7] = [2], [8] = 0).  The layer adjoint B^T is one kernel in
+ *   both paths.
  * ms_out: host, n_out >= 7.  The MD state is unchanged (the evaluation is
  * deterministic).  Requires allegro_md_init.
  */

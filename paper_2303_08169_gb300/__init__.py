@@ -47,7 +47,7 @@ class _Batch(ctypes.Structure):
                 ("cells", ctypes.c_void_p), ("e_target", ctypes.c_void_p),
                 ("f_target", ctypes.c_void_p)]
 PHASES = ["neighbors", "pass_a", "pass_b", "pass_c", "pass_b_adjoint", "pass_a_adjoint", "forces",
-          "pass_b1", "pass_b2", "pass_b2_adjoint", "pass_b1_adjoint"]
+          "pass_b1", "pass_b2"]
 
 
 class AllegroError(RuntimeError):

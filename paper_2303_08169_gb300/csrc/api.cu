@@ -1386,18 +1386,16 @@ int allegro_phase_times(allegro_ctx* ctx, int32_t n_reps, double* ms_out, int32_
   cudaEventDestroy(e_end);
   if (rc) return rc;
   const double n = n_reps;
-  const double out[11] = {nb_ms / n,
-                          kind_ms[kPhA] / n,
-                          (kind_ms[kPhB] + kind_ms[kPhB2]) / n,
-                          kind_ms[kPhC] / n,
-                          (kind_ms[kPhBT] + kind_ms[kPhBT2]) / n,
-                          kind_ms[kPhAT] / n,
-                          f_ms / n,
-                          kind_ms[kPhB] / n,
-                          kind_ms[kPhB2] / n,
-                          kind_ms[kPhBT] / n,
-                          kind_ms[kPhBT2] / n};
-  for (int k = 0; k < std::min(n_out, 11); ++k) ms_out[k] = out[k];
+  const double out[9] = {nb_ms / n,
+                         kind_ms[kPhA] / n,
+                         (kind_ms[kPhB] + kind_ms[kPhB2]) / n,
+                         kind_ms[kPhC] / n,
+                         kind_ms[kPhBT] / n,
+                         kind_ms[kPhAT] / n,
+                         f_ms / n,
+                         kind_ms[kPhB] / n,
+                         kind_ms[kPhB2] / n};
+  for (int k = 0; k < std::min(n_out, 9); ++k) ms_out[k] = out[k];
   return ALLEGRO_OK;
 }
 

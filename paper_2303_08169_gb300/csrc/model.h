@@ -120,7 +120,7 @@ int bf16_tile();
 // Optional launch timing: mark(kind) records an event on the stream after a
 // pass kernel, tagged with its kind; interval i lies between event i and
 // event i + 1 and belongs to kind[i + 1].
-enum KernelKind { kPhStart = -1, kPhA = 0, kPhB, kPhB2, kPhC, kPhBT, kPhBT2, kPhAT, kPhCount };
+enum KernelKind { kPhStart = -1, kPhA = 0, kPhB, kPhB2, kPhC, kPhBT, kPhAT, kPhCount };
 struct KernelMarks {
   static constexpr int kMax = 48;
   cudaEvent_t ev[kMax];

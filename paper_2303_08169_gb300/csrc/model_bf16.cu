@@ -13,13 +13,15 @@
 //  * pre-activations stay in TMEM between a GEMM and its adjoint;
 //  * channel mixing is 9 MMAs, one per output component (l3, m), over
 //    K-slices of one tile holding the tensor-product outputs;
-//  * the layer-k pass is split in two (TP + mixing; latent MLP) so that the
-//    weights of every kernel stay resident in shared memory;
+//  * the forward layer-k pass is split in two (TP + mixing; latent MLP) so
+//    that the weights of every kernel stay resident in shared memory; its
+//    adjoint is one kernel (no per-atom sum lies between its two halves);
 //  * sigmoid via tanh.approx.f32.
 // Everything else (geometry, tensor products, envelope, residuals,
-// reductions) is FP32 on CUDA cores; x^k, V^k and all gradients are stored in
-// FP32.  Per-atom sums use the per-(tile, atom) partials of the FP32 path with
-// 128-pair tiles.
+// reductions) is FP32 on CUDA cores.  x^k, S^k and V^k are stored in FP16
+// between passes, dV in the operand type, the other gradients in FP32.
+// Per-atom sums use the per-(tile, atom) partials of the FP32 path with
+// 128-pair tiles, reduced per atom once per producing pass.
 #include <cstdio>
 #include <cstring>
 
@@ -249,6 +251,25 @@ AL_DEV void prefetch_meta(const PassBufs& b, int nt) {
   bulk_prefetch_l2(b.pi + (size_t)nt * kT, kT * 4);
   bulk_prefetch_l2(b.pj + (size_t)nt * kT, kT * 4);
   bulk_prefetch_l2(b.pcode + (size_t)nt * kT, kT * 4);
+}
+
+// the same for columns [x0, x0 + nx) of W-wide partial rows, f(p, x - x0)
+template <class F>
+AL_DEV void seg_store_cols(float* __restrict__ part, const Meta& m, int W, int x0, int nx, F&& f) {
+  for (int idx = threadIdx.x; idx < m.nseg * nx; idx += blockDim.x) {
+    const int s = idx / nx, x = idx % nx;
+    const int s1 = m.sstart[s + 1];
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    int p = m.sstart[s];
+    for (; p + 3 < s1; p += 4) {
+      a0 += f(p, x);
+      a1 += f(p + 1, x);
+      a2 += f(p + 2, x);
+      a3 += f(p + 3, x);
+    }
+    for (; p < s1; ++p) a0 += f(p, x);
+    part[(size_t)(m.tile + m.atom[s]) * W + x0 + x] = (a0 + a1) + (a2 + a3);
+  }
 }
 
 // Gamma (or dGamma) per atom: k_atom_sums reduces the per-(tile, atom)
@@ -1085,32 +1106,65 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 }
 
 // ============================================================================
-// Pass B2_k^T: adjoint of the Gamma^{k+1} scatter and of the latent MLP of
-// layer k (its forward recomputed in the tile): dx^{k-1} (residual + latent
-// parts, without the embedding term), ds -> dS, du, dY.
+// Pass B_k^T: adjoint of layer k.  First the Gamma^{k+1} scatter and the
+// latent MLP (forward recomputed), then mixing and the tensor product, and
+// for k = 1 the embedding; no per-atom sum lies between the two halves, so
+// they share one kernel.  dS^k stays in TMEM and dx^{k-1} is
+// accumulated in one set of TMEM columns (residual dx / sqrt 2, then
+// dz1 W_0, then emb^T dw0) and written once.
+// Shared memory: HA holds x^k, then [x^{k-1}, S^k], dz1, the dV^k operand
+// and at the end dw0 and the dy partials; A1 holds de, SiLU(z1), dz2 and
+// during the mixing-adjoint rounds the dGamma^k staging of eight channels.
+// TMEM columns: e [0, 16); z1 [32, 160); z2 and da1 [160, 288); dx [288,
+// 416); ds [416, 464); w0 [464, 512); in the rounds, the l3 = 0 component of
+// all channels [416, 464) and components j >= 1 of eight channels [0, 256).
 // 512 threads: thread (r, h) owns tile row r, column quarter h of every
-// epilogue and channels 4h..4h+3 of the env adjoint.
-template <class Tin>
-__global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
-  BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1, {
+// epilogue, channels 4h..4h+3 of the env adjoint and channels 8 hf + 2h + e
+// of mixing-adjoint round hf.
+constexpr int CLH = CL / 2 + 1;                     // odd stride of the half-round dGamma staging
+constexpr uint32_t kRegA1 = (4 * kT * CLH + 1023) / 1024 * 1024;
+static_assert(kRegA1 >= kOp128, "A1 region holds an operand tile");
+template <class Tin, bool kEmb>
+__global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
+  BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1 + kImgEmb + 3 * kImgMix, {
     bulk_g2s(sm, w.env[k], kImgEnv, &bars[1]);
     bulk_g2s(sm + kImgEnv, w.lat0[k - 1], kImgLat0, &bars[1]);
     bulk_g2s(sm + kImgEnv + kImgLat0, w.lat1[k - 1], kImgLat1, &bars[1]);
+    bulk_g2s(sm + kImgEnv + kImgLat0 + kImgLat1, w.emb, kImgEmb, &bars[1]);
+    for (int l = 0; l < 3; ++l)
+      bulk_g2s(sm + kImgEnv + kImgLat0 + kImgLat1 + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
   })
   uint8_t* Wenv = sm;
   uint8_t* Wl0 = Wenv + kImgEnv;
   uint8_t* Wl1 = Wl0 + kImgLat0;
-  uint8_t* HA = Wl1 + kImgLat1;
+  uint8_t* Wemb = Wl1 + kImgLat1;
+  uint8_t* Wmix = Wemb + kImgEmb;
+  uint8_t* HA = Wmix + 3 * kImgMix;
   uint8_t* A1 = HA + kOpH;
-  uint8_t* DE = A1 + kOp128;
-  float* s_fc = reinterpret_cast<float*>(DE + kOp64);
+  uint8_t* DE = A1;
+  uint8_t* DVT = HA;
+  uint8_t* DW0 = HA;
+  float* s_dg = reinterpret_cast<float*>(A1);          // [kT][CLH], rounds only
+  float* s_dy = reinterpret_cast<float*>(HA + kOp64);  // [4][kT][NLM], tile end only
+  float* s_fc = reinterpret_cast<float*>(A1 + kRegA1);
   float* s_Y = s_fc + kT;
-  float* s_dy = s_Y + kT * NLM;    // [4][kT][NLM]
-  float* s_du = s_dy + 4 * kT * NLM;   // [4][kT]
-  float* s_g = s_du + 4 * kT;      // [kSegCap][CL]
+  float* s_du = s_Y + kT * NLM;                        // [4][kT]
+  float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
+  constexpr int kE = 0, kZ1 = 32, kZ2 = 160, kDX = 288, kDS = 416, kW0 = 464, kJ0 = 416, kJ = 0;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
-  uint32_t xw[16];                                    // x^k operand words, one tile ahead
-  ld_row<32>(xw, b.X[k], blockIdx.x, r, D, 32 * h, r < min(kT, P - (int)blockIdx.x * kT));
+  // the next tile's x^k operand words, dV^k words (channels 4h..4h+3) and
+  // neighbour-list rows, loaded during this tile's tail
+  uint32_t xw[16], dvw[NLM][2];
+  auto ld_next = [&](int t) {
+    const bool vt = r < min(kT, P - t * kT);
+    ld_row<32>(xw, b.X[k], t, r, D, 32 * h, vt);
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        dvw[lm][q] = vt ? reinterpret_cast<const uint32_t*>(b.dV)[hidx(t, CL, lm * C + 4 * h + 2 * q, r)] : 0u;
+  };
+  ld_next(blockIdx.x);
   MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m, mq);
@@ -1121,9 +1175,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
       prefetch_rows_h(b.X[k], D, nt);
       prefetch_rows_h(b.X[k - 1], D, nt);
       prefetch_rows_h(b.S[k], C * NS, nt);
+      prefetch_rows_h(b.dV, CL, nt);
       prefetch_rows(b.dX, D, nt);
       prefetch_rows(b.dU, 1, nt);
       prefetch_rows(b.dY, NLM, nt);
+      if (!kEmb) prefetch_rows_h(b.V[k - 1], CL, nt);
     }
     const bool valid = r < m.np;
     if (h == 0) {
@@ -1137,13 +1193,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
     }
     st_row<Tin, 32>(HA, r, 32 * h, xw);
     stage_g(b.dgsum[k + 1], m, s_g);
-    uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env MMAs
+    uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env MMA
     ld_row<32>(xw2, b.X[k - 1], tile, r, D, 32 * h, valid);
-    if (h >= 1) ld_row<16>(sw, b.S[k], tile, r, C * NS, 16 * (h - 1), valid);
-    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wenv, 16, 8, false, 0); });        // e^{k+1}
+    ld_row<16>(sw, b.S[k], tile, r, C * NS, 16 * max(h - 1, 0), valid && h >= 1);
+    mm.run([&] { mma_k<Tin>(tmem + kE, HA, 0, Wenv, 16, 8, false, 0); });       // e^{k+1}
+    float dy[NLM];                                    // dY of this thread's channels (env and embedding)
     {
-      float e[8], dy[NLM];
-      tmem_ld8(lanes(tmem) + 4 * h, e);              // e of channels 4h..4h+3 in e[0..3]
+      float e[8];
+      tmem_ld8(lanes(tmem) + kE + 4 * h, e);          // e of channels 4h..4h+3 in e[0..3]
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
 #pragma unroll
@@ -1159,11 +1216,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
         }
         st1<Tin>(DE, r, c, acc);
       }
-#pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dy[lm];
     }
-    // [x^{k-1}, S^k] replaces x^k in HA (the env MMA has completed); env^T de
-    // and z1 are independent and go in one commit
     st_row<Tin, 32>(HA, r, 32 * h, xw2);
     if (h >= 1) {
       st_row<Tin, 16>(HA, r, 128 + 16 * (h - 1), sw);
@@ -1175,27 +1228,28 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
 #pragma unroll
     for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
     mm.run([&] {
-      mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16);                    // env^T de
-      mma_k<Tin>(tmem + 32, HA, 0, Wl0, 128, 11, false, 0);                     // z1
+      mma_k<Tin>(tmem + kDX, DE, 0, Wenv, 128, 1, true, 16);                    // env^T de
+      mma_k<Tin>(tmem + kZ1, HA, 0, Wl0, 128, 11, false, 0);                    // z1
+      if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, 48, 8, false, 0);           // w0 = emb x^0
     });
-    epi(tmem, 32, 128, [&](int rr, int n0, const float* v) {
+    epi(tmem, kZ1, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
       st16<Tin>(A1, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 160, A1, 0, Wl1, 128, 8, false, 0); });     // z2
+    mm.run([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, false, 0); });     // z2
     {
       // dx = dx^k + env^T de; its residual part dx / sqrt 2 goes back into
-      // the same TMEM columns, where the [dx, ds] MMA below accumulates onto it
+      // the same TMEM columns, where the later MMAs accumulate onto it
       float du = 0.0f;
       float dx[32];
-      tmem_ld32(lanes(tmem) + 288 + 32 * h, dx);
+      tmem_ld32(lanes(tmem) + kDX + 32 * h, dx);
       const float fc = s_fc[r];
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float z2[16], o[16];
-        tmem_ld16(lanes(tmem) + 160 + 32 * h + 16 * hf, z2);
+        tmem_ld16(lanes(tmem) + kZ2 + 32 * h + 16 * hf, z2);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const float x = dx[16 * hf + q] + dxo[16 * hf + q];
@@ -1205,165 +1259,46 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2t(BfW w, PassBufs b, int k) {
         }
         st16<Tin>(A1, r, 32 * h + 16 * hf, o);
       }
-      tmem_st32(lanes(tmem) + 288 + 32 * h, dx);
-      float z[16] = {};
-      tmem_st16(lanes(tmem) + 416 + 12 * h, z);       // ds columns 416..463 start from zero
+      tmem_st32(lanes(tmem) + kDX + 32 * h, dx);
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};       // ds columns start from zero (exactly its 48)
+#pragma unroll
+      for (int q = 0; q < 12; q += 4) tmem_st4(lanes(tmem) + kDS + 12 * h + q, z);
       tmem_wait_st();
       s_du[h * kT + r] = du * kR2;
     }
-    mm.run([&] { mma_k<Tin>(tmem + 160, A1, 0, Wl1, 128, 8, true, 128); });    // da1
-    epi(tmem, 160, 128, [&](int rr, int n0, const float* da) {
+    mm.run([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, true, 128); });    // da1
+    epi(tmem, kZ2, 128, [&](int rr, int n0, const float* da) {
       float z1[16], o[16];
-      tmem_ld16(lanes(tmem) + 32 + n0, z1);
+      tmem_ld16(lanes(tmem) + kZ1 + n0, z1);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
       st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 288, HA, 0, Wl0, 176, 8, true, 128, true); });  // [dx, ds] += dz1 W
-    float duo = 0.0f, dyo[NLM];
-    if (threadIdx.x < kT) {                           // loaded ahead of the barrier below
-      duo = valid ? b.dU[sidx(tile, 1, 0, r)] : 0.0f;
+    mm.run([&] { mma_k<Tin>(tmem + kDX, HA, 0, Wl0, 176, 8, true, 128, true); });  // [dx, ds] += dz1 W
+    // ---- mixing and tensor-product adjoint of layer k ----
+    // ds and w0 of this thread's round channels (8 hf + 2h + e): 3 columns each
+    float dsv[2][6], w0[2][6];
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
+    for (int hf = 0; hf < 2; ++hf) {
+      tmem_ld6(lanes(tmem) + kDS + 3 * (8 * hf + 2 * h), dsv[hf]);
+      if (kEmb) tmem_ld6(lanes(tmem) + kW0 + 3 * (8 * hf + 2 * h), w0[hf]);
     }
-    {
-      float* dxg = b.dX;
-      epi(tmem, 288, 128, [&](int rr, int n0, const float* dh) {
-        if (valid)
-#pragma unroll
-          for (int q = 0; q < 16; ++q) dxg[sidx(tile, D, n0 + q, rr)] = dh[q];
-      });
-      const int nt = tile + (int)gridDim.x;
-      ld_row<32>(xw, b.X[k], nt, r, D, 32 * h, r < min(kT, P - nt * kT));
-      mq = meta_load(b, nt, P);
-      float ds[16];                                   // ds columns 12 h .. 12 h + 11
-      tmem_ld16(lanes(tmem) + 288 + 128 + 12 * h, ds);
-      if (valid)
-#pragma unroll
-        for (int q = 0; q < 12; ++q) b.dS[sidx(tile, C * NS, 12 * h + q, r)] = ds[q];
-    }
-    __syncthreads();
-    if (threadIdx.x < kT && valid) {
-      b.dU[sidx(tile, 1, 0, r)] = duo + ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]));
-#pragma unroll
-      for (int lm = 0; lm < NLM; ++lm)
-        b.dY[sidx(tile, NLM, lm, r)] = dyo[lm] + ((s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
-                                                  (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]));
-    }
-    __syncthreads();
-  }
-  BF_EPILOGUE
-}
-
-// ============================================================================
-// per-pair inputs of pass B1^T for tile t, thread (r, h)
-AL_DEV void b1t_loads(const PassBufs& b, int k, int t, int P, int r, int h, uint32_t (&dvw)[NLM][2],
-                      float (&dsv)[2][2][NS], uint32_t (&xw)[16]) {
-  const bool vt = r < min(kT, P - t * kT);
-#pragma unroll
-  for (int lm = 0; lm < NLM; ++lm)
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-      dvw[lm][q] = vt ? reinterpret_cast<const uint32_t*>(b.dV)[hidx(t, CL, lm * C + 4 * h + 2 * q, r)] : 0u;
-#pragma unroll
-  for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-      for (int q = 0; q < NS; ++q)
-        dsv[hf][e][q] = vt ? b.dS[sidx(t, C * NS, (8 * hf + 2 * h + e) * NS + q, r)] : 0.0f;
-  ld_row<32>(xw, b.X[0], t, r, D, 32 * h, vt && k == 1);
-}
-
-// Pass B1_k^T: adjoint of mixing and of the tensor product of layer k:
-// dV^{k-1} (k >= 2) or, for k = 1, the embedding adjoint into dx^0 and dY;
-// dGamma^k partials.
-// The mixing adjoint of all nine components and sixteen channels (560
-// accumulator columns) exceeds the 512 TMEM columns, so it is issued in two
-// rounds of eight channels each: round hf holds, for every component j >= 1,
-// the 32 columns of channels 8 hf .. 8 hf + 7 (the B operand starts 64 bytes
-// into the 128-byte rows of the mixing image for hf = 1); the l3 = 0
-// component of all channels (48 columns) comes with round 0.  Each channel's
-// whole tensor-product adjoint then runs in one round.
-// 512 threads: thread (r, h) owns tile row r and channels 2h, 2h + 1 of each
-// round (8 hf + 2h + e).
-template <class Tin, bool kEmb>
-__global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
-  BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
-    bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
-    for (int l = 0; l < 3; ++l) bulk_g2s(sm + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
-  })
-  uint8_t* Wemb = sm;
-  uint8_t* Wmix = Wemb + kImgEmb;
-  uint8_t* DVT = Wmix + 3 * kImgMix;
-  uint8_t* X = DVT + kOpH;
-  uint8_t* DW0 = X + kOp128;
-  float* s_Y = reinterpret_cast<float*>(DW0 + kOp64);
-  float* s_dg = s_Y + kT * NLM;           // [kT][CLP]
-  float* s_dy = s_dg + kT * CLP;          // [4][kT][NLM]
-  float* s_g = s_dy + 4 * kT * NLM;       // [kSegCap][CL]
-  // TMEM columns: l3 = 0 component [0, 48); components j >= 1 of a round at
-  // 64 + 32 (j - 1); w0 at 320; emb^T dw0 at 384
-  constexpr int kJ0 = 0, kJ = 64, kW0 = 320, kDX = 384;
-  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
-  // per-pair inputs of a tile, in registers: dV (4 channels x 9 components),
-  // dS of this thread's four channels, the x^0 operand columns.  The next
-  // tile's are loaded during this tile's tail (software pipelining).
-  uint32_t dvw[NLM][2];                               // dV^k words (operand type): channels 4h..4h+3
-  float dsv[2][2][NS];
-  uint32_t xw[16];
-  b1t_loads(b, k, blockIdx.x, P, r, h, dvw, dsv, xw);
-  MetaPre mq = meta_load(b, blockIdx.x, P);
-  for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
-    meta_setup(b, tile, P, m, mq);
-    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
-      const int nt = tile + (int)gridDim.x;
-      prefetch_meta(b, nt);
-      prefetch_rows(b.dR, 3, nt);
-      prefetch_rows_h(b.dV, CL, nt);
-      prefetch_rows(b.dS, C * NS, nt);
-      if (kEmb) {
-        prefetch_rows_h(b.X[0], D, nt);
-        prefetch_rows(b.dX, D, nt);
-        prefetch_rows(b.dY, NLM, nt);
-      } else {
-        prefetch_rows_h(b.V[k - 1], CL, nt);
-      }
-    }
-    const bool valid = r < m.np;
-    if (h == 0) {
-      float u[3], d, fc, dfc, Y[NLM];
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-    }
-    // column 16 lm + c: this thread's 4 channels of one lm are 8 contiguous bytes
+    // column 16 lm + c of the operand: this thread's 4 channels of one lm
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
       *reinterpret_cast<uint2*>(DVT + sw128_off(r, 16 * lm + 4 * h, 128)) = make_uint2(dvw[lm][0], dvw[lm][1]);
     stage_g(b.gsum[k], m, s_g);
-    float w0[2][8];                                   // w0 of channels 8 hf + 2h + e: w0[hf][3 e + l]
-    if (kEmb) st_row<Tin, 32>(X, r, 32 * h, xw);
-    float dw[2][2 * 3], dyl[NLM];
+    float dw[2][6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) dw[0][q] = dw[1][q] = 0.0f;
-#pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
-    float dVe[NLM];                                   // !kEmb: dV^{k-1} of the even channel of a pair
+    float dVe[NLM];                                   // k >= 2: dV^{k-1} of the even channel of a pair
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
       mm.run([&] {
-        if (hf == 0 && kEmb) mma_k<Tin>(tmem + kW0, X, 0, Wemb, 48, 8, false, 0);   // w0 = emb x^0
         if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, 48, 1, true, 16);
         for (int j = 1; j < 9; ++j)
           mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l_of(j) * kImgMix + 64 * hf, 32, 1, true, 16);
       });
-      if (hf == 0 && kEmb) {
-        tmem_ld8(lanes(tmem) + kW0 + 6 * h, w0[0]);
-        tmem_ld8(lanes(tmem) + kW0 + 24 + 6 * h, w0[1]);
-      }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int c = 8 * hf + 2 * h + e;
@@ -1375,7 +1310,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
         for (int g = 0; g < 9; ++g) tmem_wait4(t + 4 * g);
         float dT[TP2_NT];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) dT[q] = __uint_as_float(t[q]) + dsv[hf][e][q];
+        for (int q = 0; q < 3; ++q) dT[q] = __uint_as_float(t[q]) + dsv[hf][3 * e + q];
 #pragma unroll
         for (int mm1 = 0; mm1 < 3; ++mm1)
 #pragma unroll
@@ -1400,8 +1335,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
         for (int lm = 0; lm < NLM; ++lm) dG[lm] = dVp[lm] = 0.0f;
         tp2_bwd(V, G, dT, dVp, dG);
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
-        if (!kEmb) {                                 // dV^{k-1}: channel pairs (8 hf + 2h, + 1)
+        for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLH + (c - 8 * hf) * NLM + lm] = dG[lm];
+        if (!kEmb) {                                  // dV^{k-1}: channel pairs (8 hf + 2h, + 1)
           if (e == 0) {
 #pragma unroll
             for (int lm = 0; lm < NLM; ++lm) dVe[lm] = dVp[lm];
@@ -1413,43 +1348,47 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1t(BfW w, PassBufs b, int k) {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
             dw[hf][3 * e + l_of(lm)] = fmaf(dVp[lm], s_Y[r * NLM + lm], dw[hf][3 * e + l_of(lm)]);
-            dyl[lm] = fmaf(w0[hf][3 * e + l_of(lm)], dVp[lm], dyl[lm]);
+            dy[lm] = fmaf(w0[hf][3 * e + l_of(lm)], dVp[lm], dy[lm]);
           }
         }
       }
+      __syncthreads();
+      seg_store_cols(b.dgam[k], m, CL, 72 * hf, 72, [&](int p, int x) { return s_dg[p * CLH + x]; });
     }
-    if (kEmb) {
-      float* dxg = b.dX;
-      float dxo[32];                                  // columns 32h..32h+31, loaded ahead of the MMA wait
-#pragma unroll
-      for (int q = 0; q < 32; ++q) dxo[q] = valid ? dxg[sidx(tile, D, 32 * h + q, r)] : 0.0f;
+    if (kEmb) {                                       // the DVT operand is dead: dw0 takes its place
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
         for (int q = 0; q < 6; ++q) st1<Tin>(DW0, r, 3 * (8 * hf + 2 * h) + q, dw[hf][q]);
-      mm.run([&] { mma_k<Tin>(tmem + kDX, DW0, 0, Wemb, 128, 3, true, 48); }); // emb^T dw0
+      mm.run([&] { mma_k<Tin>(tmem + kDX, DW0, 0, Wemb, 128, 3, true, 48, true); });   // dx += emb^T dw0
+    } else {
+      __syncthreads();
+    }
+    float duo = 0.0f, dyo[NLM];
+    if (threadIdx.x < kT) {
+      duo = valid ? b.dU[sidx(tile, 1, 0, r)] : 0.0f;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
+    }
+    {
       float v[32];
       tmem_ld32(lanes(tmem) + kDX + 32 * h, v);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 32; ++q) dxg[sidx(tile, D, 32 * h + q, r)] = dxo[q] + v[q];
+        for (int q = 0; q < 32; ++q) b.dX[sidx(tile, D, 32 * h + q, r)] = v[q];
     }
-    b1t_loads(b, k, tile + (int)gridDim.x, P, r, h, dvw, dsv, xw);   // zeros past the last tile
+    ld_next(tile + (int)gridDim.x);                   // zeros past the last tile
     mq = meta_load(b, tile + (int)gridDim.x, P);
-    float dyo[NLM];
-    if (threadIdx.x < kT && kEmb)
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
-#pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dyl[lm];
+    for (int lm = 0; lm < NLM; ++lm) s_dy[(h * kT + r) * NLM + lm] = dy[lm];
     __syncthreads();
-    if (threadIdx.x < kT && valid && kEmb) {
+    if (threadIdx.x < kT && valid) {
+      b.dU[sidx(tile, 1, 0, r)] = duo + ((s_du[r] + s_du[kT + r]) + (s_du[2 * kT + r] + s_du[3 * kT + r]));
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
         b.dY[sidx(tile, NLM, lm, r)] = dyo[lm] + ((s_dy[r * NLM + lm] + s_dy[(kT + r) * NLM + lm]) +
                                                   (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]));
     }
-    seg_store(b.dgam[k], m, CL, [&](int p, int x) { return s_dg[p * CLP + x]; });
     __syncthreads();
   }
   BF_EPILOGUE
@@ -1662,10 +1601,8 @@ constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 
 constexpr size_t sm_c(bool split) {
   return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 + 4 * (10 * kT + kSegCap * CL);
 }
-constexpr size_t kSmB2T = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kOpH + kOp128 + kOp64 +
-                          4 * (kT + 5 * kT * NLM + 4 * kT + kSegCap * CL);
-constexpr size_t kSmB1T = 1024 + kImgEmb + 3 * kImgMix + kOpH + kOp128 + kOp64 +
-                          4 * (kT * NLM + kT * CLP + 4 * kT * NLM + kSegCap * CL);
+constexpr size_t kSmBT = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kImgEmb + 3 * kImgMix + kOpH + kRegA1 +
+                         4 * (kT + kT * NLM + 4 * kT + kSegCap * CL);
 constexpr size_t sm_at(bool split) {
   return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
          4 * (2 * kT * GP + 2 * kT * NLM + 4 * kT + kSegCap * CL);
@@ -1673,7 +1610,7 @@ constexpr size_t sm_at(bool split) {
 // 4 KB left for the static Meta, barriers and flags of every kernel
 constexpr size_t kSmLimit = 232448 - 4096;
 static_assert(sm_a(true) <= kSmLimit && kSmB1 <= kSmLimit && kSmB2 <= kSmLimit && sm_c(true) <= kSmLimit &&
-                  kSmB2T <= kSmLimit && kSmB1T <= kSmLimit && sm_at(true) <= kSmLimit,
+                  kSmBT <= kSmLimit && sm_at(true) <= kSmLimit,
               "shared memory per kernel");
 static_assert(kOpH + kOp128 >= 4 * kT * CLP, "pass C reuses HA + A1 for the dGamma contributions");
 static_assert(kOp128 >= 4 * 4 * kT * NLM, "pass A^T keeps the dY partials in X");
@@ -1689,9 +1626,8 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     cudaFuncSetAttribute(k_bf_b1<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1);
     cudaFuncSetAttribute(k_bf_b2<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
     cudaFuncSetAttribute(k_bf_c<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
-    cudaFuncSetAttribute(k_bf_b2t<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2T);
-    cudaFuncSetAttribute(k_bf_b1t<Tin, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
-    cudaFuncSetAttribute(k_bf_b1t<Tin, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1T);
+    cudaFuncSetAttribute(k_bf_bt<Tin, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBT);
+    cudaFuncSetAttribute(k_bf_bt<Tin, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBT);
     cudaFuncSetAttribute(k_bf_at<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1726,12 +1662,10 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
   sums(b.dgam[L], b.dgsum[L]);
   mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
-    k_bf_b2t<Tin><<<grid, kThr4, kSmB2T, s>>>(w, b, k);
-    mark(kPhBT);
-    if (k == 1) k_bf_b1t<Tin, true><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
-    else k_bf_b1t<Tin, false><<<grid, kThr4, kSmB1T, s>>>(w, b, k);
+    if (k == 1) k_bf_bt<Tin, true><<<grid, kThr4, kSmBT, s>>>(w, b, k);
+    else k_bf_bt<Tin, false><<<grid, kThr4, kSmBT, s>>>(w, b, k);
     sums(b.dgam[k], b.dgsum[k]);
-    mark(kPhBT2);
+    mark(kPhBT);
   }
   k_bf_at<Tin, kSplit><<<grid, kThr4, kSmAT, s>>>(w, b);
   mark(kPhAT);
