@@ -117,13 +117,14 @@ struct Meta {
 };
 
 // Neighbour-list entries of tile row t (threads t < 128), loaded one tile
-// ahead into registers: i, j, image code, and for the first lane of each warp
-// the centre atom of the row before it
+// ahead into registers: i, j, image code, optionally the species of i, and
+// for the first lane of each warp the centre atom of the row before it
 struct MetaPre {
-  int i, j, code, prev;
+  int i, j, code, prev, zi;
 };
+template <bool kSpecies = false>
 AL_DEV MetaPre meta_load(const PassBufs& b, int tile, int P) {
-  MetaPre q{-1, 0, 62, -1};
+  MetaPre q{-1, 0, 62, -1, 0};
   const int t = threadIdx.x;
   if (t < kT) {
     const int p0 = tile * kT;
@@ -132,6 +133,7 @@ AL_DEV MetaPre meta_load(const PassBufs& b, int tile, int P) {
       q.i = b.pi[p0 + t];
       q.j = b.pj[p0 + t];
       q.code = b.pcode[p0 + t];
+      if (kSpecies) q.zi = b.species[q.i];
     }
     if ((t & 31) == 0 && t > 0 && t - 1 < np) q.prev = b.pi[p0 + t - 1];
   }
@@ -391,6 +393,19 @@ struct Mma {
       phase ^= 1u;
     }
     tc_fence_after();
+  }
+  // all threads: publish smem operands, thread 0 issues without a commit; the
+  // next run() commits these MMAs together with its own and waits for all,
+  // so CUDA-core work between the two overlaps them
+  template <class F>
+  AL_DEV void issue(F&& f) {
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (*err == 0 && threadIdx.x == 0) {
+      tc_fence_after();
+      f();
+    }
   }
 };
 
@@ -921,7 +936,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   __half2 vw[2][NLM];
   uint32_t xw[16];
   c_loads(b, L, blockIdx.x, P, r, h, vw, xw);
-  MetaPre mq = meta_load(b, blockIdx.x, P);
+  MetaPre mq = meta_load<true>(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -937,10 +952,17 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
       if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
-      s_sig[r] = valid ? w.sigma[b.species[m.pi[r]]] : 0.0f;
+      s_sig[r] = valid ? w.sigma[mq.zi] : 0.0f;
     }
     stage_g(b.gsum[L], m, s_g);
-    __syncthreads();
+    // z1 = [x^{L-1}, S] W_0: the x^{L-1} K-steps run while the tensor product
+    // computes S
+    st_row<Tin, 32>(HA, r, 32 * h, xw);
+    if (h == 3) {
+      float z[16] = {};
+      st16<Tin>(HA, r, 176, z);
+    }
+    mm.issue([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, 8, false, 0); });
     {
       float S[4 * NS];                                 // columns D + 12 h .. D + 12 h + 11
 #pragma unroll
@@ -962,12 +984,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 #pragma unroll
       for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
     }
-    st_row<Tin, 32>(HA, r, 32 * h, xw);
-    if (h == 3) {
-      float z[16] = {};
-      st16<Tin>(HA, r, 176, z);
-    }
-    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, 3, false, 0, true); });
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
@@ -1079,7 +1096,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       }
     }
     c_loads(b, L, tile + (int)gridDim.x, P, r, h, vw, xw);
-    mq = meta_load(b, tile + (int)gridDim.x, P);
+    mq = meta_load<true>(b, tile + (int)gridDim.x, P);
     __syncthreads();
     {
       // energy partials in FP64, one warp per segment: lanes stride the
