@@ -97,38 +97,63 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
   const float lo = rc2 - g.band, hi = rc2 + g.band;
   const float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
   if (g.ncell[0] > 0) {
+    // lane o < 27 describes neighbour cell o (atom range, image shift); the
+    // lanes then stride over the concatenation of the 27 ranges, so that a
+    // warp visits ~10 candidates per cell in one pass instead of one pass per
+    // cell
     const int cell = atom_cell[i];
     const int cz = cell % g.ncell[2];
     const int cy = (cell / g.ncell[2]) % g.ncell[1];
     const int cx = cell / (g.ncell[2] * g.ncell[1]);
-    for (int o = 0; o < 27; ++o) {
-      const int ox = o / 9 - 1, oy = (o / 3) % 3 - 1, oz = o % 3 - 1;
+    int cb = 0, cn = 0, ccode = img_code(0, 0, 0);
+    if (lane < 27) {
+      const int ox = lane / 9 - 1, oy = (lane / 3) % 3 - 1, oz = lane % 3 - 1;
       int tx = cx + ox, ty = cy + oy, tz = cz + oz;
       int n[3] = {0, 0, 0};
       if (tx < 0) { tx += g.ncell[0]; n[0] = -1; } else if (tx >= g.ncell[0]) { tx -= g.ncell[0]; n[0] = 1; }
       if (ty < 0) { ty += g.ncell[1]; n[1] = -1; } else if (ty >= g.ncell[1]) { ty -= g.ncell[1]; n[1] = 1; }
       if (tz < 0) { tz += g.ncell[2]; n[2] = -1; } else if (tz >= g.ncell[2]) { tz -= g.ncell[2]; n[2] = 1; }
       const int other = (tx * g.ncell[1] + ty) * g.ncell[2] + tz;
-      const int b = cell_start[other], e = cell_start[other + 1];
-      const float sx = n[0] * Lf[0], sy = n[1] * Lf[1], sz = n[2] * Lf[2];
-      for (int k0 = b; k0 < e; k0 += 32) {
-        const int k = k0 + lane;
-        bool hit = false;
-        int j = -1;
-        if (k < e) {
-          j = cell_atoms[k];
-          const float dx = (w32[3 * j] - xi) + sx;
-          const float dy = (w32[3 * j + 1] - yi) + sy;
-          const float dz = (w32[3 * j + 2] - zi) + sz;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          const bool self = (j == i) && n[0] == 0 && n[1] == 0 && n[2] == 0;
-          if (!self) {
-            if (d2 < lo) hit = true;
-            else if (d2 <= hi) hit = exact_in(w64, i, j, n[0], n[1], n[2], g.L[0], g.L[1], g.L[2], g.rc);
-          }
-        }
-        f(hit, j, n);
+      cb = cell_start[other];
+      cn = cell_start[other + 1] - cb;
+      ccode = img_code(n[0], n[1], n[2]);
+    }
+    int incl = cn;                                    // inclusive scan of the range lengths
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int excl = incl - cn;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int k0 = 0; k0 < total; k0 += 32) {
+      const int k = k0 + lane;
+      int o = 0;                                      // last range starting at or before k
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int c = o + step;
+        const int ec = __shfl_sync(0xffffffffu, excl, c < 27 ? c : 26);
+        if (c < 27 && ec <= k) o = c;
       }
+      const int b = __shfl_sync(0xffffffffu, cb, o), e0 = __shfl_sync(0xffffffffu, excl, o);
+      const int code = __shfl_sync(0xffffffffu, ccode, o);
+      bool hit = false;
+      int j = -1;
+      int n[3];
+      img_decode(code, n[0], n[1], n[2]);
+      if (k < total) {
+        j = cell_atoms[b + (k - e0)];
+        const float dx = (w32[3 * j] - xi) + n[0] * Lf[0];
+        const float dy = (w32[3 * j + 1] - yi) + n[1] * Lf[1];
+        const float dz = (w32[3 * j + 2] - zi) + n[2] * Lf[2];
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        const bool self = (j == i) && n[0] == 0 && n[1] == 0 && n[2] == 0;
+        if (!self) {
+          if (d2 < lo) hit = true;
+          else if (d2 <= hi) hit = exact_in(w64, i, j, n[0], n[1], n[2], g.L[0], g.L[1], g.L[2], g.rc);
+        }
+      }
+      f(hit, j, n);
     }
   } else {
     const int nx = 2 * g.nimg[0] + 1, ny = 2 * g.nimg[1] + 1, nz = 2 * g.nimg[2] + 1;
