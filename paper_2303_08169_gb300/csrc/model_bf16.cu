@@ -764,10 +764,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       }
     }
     mm.run([&] {
-      for (int j = 0; j < 9; ++j) {
-        const int l3 = l_of(j), Pl = tp2_P(l3);
-        mma_k<Tin>(tmem + 64 + 16 * j, T, kSlice[j] / 16, Wmix + l3 * kImgMix, 16, C * Pl / 16, false, 0);
-      }
+      // K-step-major over the nine products: consecutive MMAs write different
+      // accumulators, so none waits for the one before it
+      for (int kk = 0; kk < 4; ++kk)
+        for (int j = 0; j < 9; ++j) {
+          const int l3 = l_of(j);
+          if (kk < C * tp2_P(l3) / 16)
+            mma_k<Tin>(tmem + 64 + 16 * j, T, kSlice[j] / 16 + kk, Wmix + l3 * kImgMix + 32 * kk, 16, 1, false, 0,
+                       kk > 0);
+        }
     });
     {
       const int nt = tile + (int)gridDim.x;
