@@ -355,7 +355,7 @@ class Runner:
         self.al.allegro_destroy(self.ctx)
 
 
-def sam_timing(al, torch, steps=5):
+def sam_timing(al, torch, steps=5, n_sharp=64):
     """SAM training step (Eq. 3) on 32 seeded ammonia structures of 64-512
     atoms; targets from a teacher model (weights seed 43) evaluated by the
     library's FP32 path.  Wall clock per allegro_sam_train_step."""
@@ -380,10 +380,30 @@ def sam_timing(al, torch, steps=5):
         losses.append(al.allegro_sam_train_step(ctx, b, 0.05, 2e-3, 1.0, 100.0))
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
+    # sharpness of the trained weights (Eq. 2, estimated as in Sec. 5.4 by the
+    # largest loss increase over random eps of norm rho = 0.05; 64 seeded
+    # samples here instead of the paper's 1,000) and its 1-D surface
+    n_par = al.allegro_query(ctx, al.ALLEGRO_Q_N_PARAMS)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    eps = torch.randn((n_sharp, n_par), generator=gen, device="cuda", dtype=torch.float32)
+    eps = eps * (0.05 / eps.norm(dim=1, keepdim=True))
+    eps = torch.cat([torch.zeros((1, n_par), device="cuda", dtype=torch.float32), eps])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ls = al.allegro_loss_scan(ctx, b, eps, np.ones(n_sharp + 1))
+    dt_scan = (time.perf_counter() - t1) / (n_sharp + 1)
+    kmax = int(np.argmax(ls[1:])) + 1
+    surface = al.allegro_loss_scan(ctx, b, eps[kmax], np.linspace(-1.0, 1.0, 9))
     al.allegro_destroy(ctx)
     n_atoms = int(sum(len(s["species"]) for s in structs))
     return {"structures": len(structs), "atoms": n_atoms, "ms_per_step": 1e3 * dt, "steps": steps,
             "rho": 0.05, "lr": 2e-3, "loss_first": losses[0], "loss_last": losses[-1],
+            "sharpness": {"value": float(ls[1:].max() - ls[0]), "samples": n_sharp, "loss_at_w": float(ls[0]),
+                          "ms_per_loss_evaluation": 1e3 * dt_scan,
+                          "surface_p": [-1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 0.75, 1.0],
+                          "surface_loss": [float(x) for x in surface],
+                          "note": "allegro_loss_scan after the SAM steps: loss at w + eps_k for random eps_k "
+                                  "of norm 0.05 (seeded), then L(w + p eps_max)"},
             "note": "FP32 passes with per-pair dumps over all 32 structures at once (one concatenated "
                     "pair list); two loss gradients (w, w + eps) per step, each one forward and three "
                     "training-mode pass sequences (energy seed, central difference along dL/dF)"}

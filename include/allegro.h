@@ -256,6 +256,25 @@ int allegro_loss_grad(allegro_ctx* ctx, const allegro_batch* batch, double w_ene
 int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double rho, double lr,
                            double w_energy, double w_force, double* loss_out);
 
+/*
+ * Loss landscape around the current weights w (the sharpness of Eq. 2 and its
+ * measurement in Sec. 5.4, Table 4 and Fig. 5): for k < n_points the loss of
+ * the batch (as allegro_loss_grad, weights w_energy, w_force) at
+ *   w_k = w + scales[k] d_k,   d_k = dirs + k dir_stride,
+ * into losses_out[k].  The sharpness estimate max_k L(w + eps_k) - L(w) over
+ * random eps_k of norm rho takes d_k = eps_k, scales 1 (and one point with
+ * scale 0 for L(w)); the one-dimensional surface L(w + p d), p in [-1, 1],
+ * takes dir_stride 0 and scales p.  The random directions are the caller's.
+ * dirs: device FP32, n_params per direction; dir_stride: elements between
+ * directions (0: the same direction for every point); scales, losses_out:
+ * host, n_points >= 1.  One forward energy+force evaluation of the batch per
+ * point (FP32 passes), no gradient.  The context's weights and Adam state
+ * are unchanged on return (the MD graph is re-captured at the next step).
+ * Models of at most two layers (E_UNSUPPORTED otherwise).
+ */
+int allegro_loss_scan(allegro_ctx* ctx, const allegro_batch* batch, const float* dirs, int64_t dir_stride,
+                      const double* scales, int32_t n_points, double w_energy, double w_force, double* losses_out);
+
 /* The trainable weights as one FP32 vector in blob order (every weight
  * matrix row-major, sigma/mu excluded); host or device, n = n_params. */
 int allegro_get_weights(allegro_ctx* ctx, float* out, int64_t n);

@@ -5,6 +5,8 @@ Base optimizer Adam with (beta1, beta2) = (0.9, 0.999) (Table 5), eps = 1e-8.
 Loss (Table 5 "per atom MSE", with the energy:force weights as arguments):
     L = (w_E / B) sum_b ((E_b - E*_b) / N_b)^2
         + (w_F / (3 sum_b N_b)) sum_b sum_i |F_bi - F*_bi|^2
+Sharpness (Eq. 2) and the loss landscape of Sec. 5.4 (Table 4, Fig. 5): the
+loss at w + eps for sampled eps of norm rho, and along one direction.
 Readings: the trainable vector is every weight matrix of the blob flattened
 row-major in blob order (sigma_Z, mu_Z fixed); ||.|| is the global L2 norm; if
 ||grad L|| = 0 the ascent step is zero.  The force term's weight gradient is a
@@ -59,9 +61,34 @@ def loss_and_grad(model, wvec, batch, w_energy=1.0, w_force=100.0, need_grad=Tru
         lf = lf + ((F - ft) ** 2).sum()
     loss = w_energy * le / B + w_force * lf / (3.0 * n_tot)
     if not need_grad:
-        return float(loss), None
+        return float(loss.detach()), None
     (gw,) = torch.autograd.grad(loss, vec)
     return float(loss.detach()), gw.numpy()
+
+
+def loss_scan(model, w, dirs, scales, batch, w_energy=1.0, w_force=100.0):
+    """L(w + scales[k] d_k) for every point k: the loss landscape around w that
+    the sharpness of Eq. 2 is defined on.  dirs: one row per point, or one row
+    shared by every point.  Returns an ndarray of losses."""
+    w = np.asarray(w, dtype=np.float64)
+    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+    scales = np.asarray(scales, dtype=np.float64).reshape(-1)
+    if dirs.shape[0] not in (1, scales.shape[0]):
+        raise ValueError("one direction per scale, or one direction for all")
+    out = []
+    for k, sk in enumerate(scales):
+        d = dirs[k] if dirs.shape[0] > 1 else dirs[0]
+        out.append(loss_and_grad(model, w + sk * d, batch, w_energy, w_force, need_grad=False)[0])
+    return np.array(out)
+
+
+def sharpness(model, w, eps, batch, w_energy=1.0, w_force=100.0):
+    """Eq. 2, max over ||eps|| <= rho of L(w + eps) - L(w), estimated as in
+    Sec. 5.4 (Table 4) by the largest value over the given samples eps_k
+    (rows of eps)."""
+    eps = np.atleast_2d(np.asarray(eps, dtype=np.float64))
+    base = loss_and_grad(model, w, batch, w_energy, w_force, need_grad=False)[0]
+    return float(np.max(loss_scan(model, w, eps, np.ones(eps.shape[0]), batch, w_energy, w_force)) - base)
 
 
 def adam_update(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -32,6 +32,7 @@ EXPORTED = [
     "allegro_query", "allegro_phase_times", "allegro_selftest_mma",
     "allegro_selftest_mma_mode", "allegro_outlier_count_noalloc",
     "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
+    "allegro_loss_scan",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -90,6 +91,7 @@ def lib():
         "allegro_outlier_count_noalloc": ([_i64, _vp, _f64, _vp, _vp], ctypes.c_int),
         "allegro_loss_grad": ([_vp, _vp, _f64, _f64, ctypes.POINTER(_f64), _vp], ctypes.c_int),
         "allegro_sam_train_step": ([_vp, _vp, _f64, _f64, _f64, _f64, ctypes.POINTER(_f64)], ctypes.c_int),
+        "allegro_loss_scan": ([_vp, _vp, _vp, _i64, _vp, _i32, _f64, _f64, _vp], ctypes.c_int),
         "allegro_get_weights": ([_vp, _vp, _i64], ctypes.c_int),
         "allegro_set_weights": ([_vp, _vp, _i64], ctypes.c_int),
     }
@@ -223,6 +225,20 @@ def allegro_sam_train_step(ctx, batch, rho, lr, w_energy=1.0, w_force=100.0):
     _check(ctx, lib().allegro_sam_train_step(ctx, ctypes.byref(batch), float(rho), float(lr), float(w_energy),
                                              float(w_force), ctypes.byref(loss)))
     return loss.value
+
+
+def allegro_loss_scan(ctx, batch, dirs, scales, w_energy=1.0, w_force=100.0):
+    """Loss at w + scales[k] * dirs[k] (dirs: device tensor, one row per
+    point, or one row shared by every point); returns a numpy array."""
+    scales = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).reshape(-1))
+    stride = 0 if dirs.dim() == 1 or dirs.shape[0] == 1 else int(dirs.shape[1])
+    if stride and dirs.shape[0] != scales.shape[0]:
+        raise ValueError("one direction per scale, or one direction for all")
+    out = np.zeros(scales.shape[0], dtype=np.float64)
+    d = dirs.contiguous()                             # kept alive across the call
+    _check(ctx, lib().allegro_loss_scan(ctx, ctypes.byref(batch), _ptr(d), stride, _ptr(scales),
+                                        int(scales.shape[0]), float(w_energy), float(w_force), _ptr(out)))
+    return out
 
 
 def allegro_get_weights(ctx, out):

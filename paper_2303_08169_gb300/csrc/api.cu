@@ -978,6 +978,27 @@ int batch_train_eval(allegro_ctx* c, const double* wpos, const float* seed) {
 // r +/- h v (h v at most 0.01 A; the pair list of r is kept, which differs
 // from the lists at r +/- h v only by pairs within 0.01 A of r_c, whose
 // energy vanishes there to third order).
+// Enqueue the forward evaluation of the built batch at the current weights:
+// forces, per-atom energies and the loss (Eq. 3's objective) into t.loss,
+// with the seeds of its weight gradient (dE, v, vmax).
+void batch_forward_loss(allegro_ctx* c, double w_energy, double w_force) {
+  const Blob& B = c->blob;
+  TrainBatch& t = c->bt;
+  cudaStream_t s = c->stream;
+  const int64_t N = t.n_atoms;
+  const double cf = w_force / (3.0 * (double)N);
+  fill_batch_passbufs(c, t.a.wpos);
+  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+  AtomArgs aa = atom_args(c);
+  aa.n = (int)N;
+  aa.species = t.a.species;
+  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk, c->d_stats,
+                c->nb.flags, s);
+  c->pb.atomL = nullptr;
+  launch_batch_loss((int)t.n_structs, N, t.atom_off, t.a.sid, c->d_Ei, t.e_target, c->d_F, t.f_target, w_energy,
+                    cf, t.dE, t.v, t.vmax, t.loss_blk, t.loss, s);
+}
+
 int loss_grad_impl(allegro_ctx* c, double w_energy, double w_force, double* loss_out) {
   const Blob& B = c->blob;
   if (B.L > 2) return c->fail(ALLEGRO_E_UNSUPPORTED, "training is built for models of at most two layers");
@@ -989,19 +1010,9 @@ int loss_grad_impl(allegro_ctx* c, double w_energy, double w_force, double* loss
   cudaMemsetAsync(c->nb.flags, 0, sizeof(int), s);
   const int nbk = (int)t.n_structs;
   const int64_t N = t.n_atoms;
-  const double cf = w_force / (3.0 * (double)N);
   const double delta = 1e-2;
-  // forward over the batch: forces and per-atom energies
-  fill_batch_passbufs(c, t.a.wpos);
-  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s);
-  AtomArgs aa = atom_args(c);
-  aa.n = (int)N;
-  aa.species = t.a.species;
-  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk, c->d_stats,
-                c->nb.flags, s);
-  c->pb.atomL = nullptr;
-  launch_batch_loss(nbk, N, t.atom_off, t.a.sid, c->d_Ei, t.e_target, c->d_F, t.f_target, w_energy, cf, t.dE, t.v,
-                    t.vmax, t.loss_blk, t.loss, s);
+  // forward over the batch: forces, per-atom energies, loss
+  batch_forward_loss(c, w_energy, w_force);
   // energy term at r, then the central difference along v
   launch_seed_energy(nbk, N, t.atom_off, t.a.sid, t.dE, w_energy, t.seed, s);
   rc = batch_train_eval(c, t.a.wpos, t.seed);
@@ -1447,6 +1458,40 @@ int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double 
     ctx->graph = nullptr;
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "sam step");
+  return ALLEGRO_OK;
+}
+
+int allegro_loss_scan(allegro_ctx* ctx, const allegro_batch* batch, const float* dirs, int64_t dir_stride,
+                      const double* scales, int32_t n_points, double w_energy, double w_force, double* losses_out) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  if (!dirs || !scales || !losses_out || n_points < 1 || dir_stride < 0)
+    return ctx->fail(ALLEGRO_E_INVALID_ARG, "loss_scan: dirs, scales, losses_out and n_points >= 1 are required");
+  if (!is_device_ptr(dirs)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "loss_scan: dirs must be device memory");
+  if (ctx->blob.L > 2) return ctx->fail(ALLEGRO_E_UNSUPPORTED, "training is built for models of at most two layers");
+  int rc = check_batch(ctx, batch);
+  if (!rc) rc = build_batch(ctx, batch);
+  if (!rc) rc = init_master(ctx);
+  if (rc) return rc;
+  const int n = (int)ctx->n_params;
+  cudaStream_t s = ctx->stream;
+  cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), s);
+  for (int k = 0; k < n_points && !rc; ++k) {
+    launch_axpy(ctx->d_master, dirs + (size_t)k * (size_t)dir_stride, scales[k], n, ctx->d_wtmp, s);
+    apply_flat(ctx, ctx->d_wtmp);
+    batch_forward_loss(ctx, w_energy, w_force);
+    cudaMemcpyAsync(&losses_out[k], ctx->bt.loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_check(ctx, "loss_scan");
+  }
+  apply_flat(ctx, ctx->d_master);                      // the context's weights are unchanged
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  int flags = 0;
+  cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return rc ? rc : cuda_check(ctx, "loss_scan");
+  if (rc) return rc;
+  if (flags & kFlagPairOverflow) return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "training batch exceeds the pair capacity");
   return ALLEGRO_OK;
 }
 

@@ -88,6 +88,14 @@ __global__ void k_ascent(const float* __restrict__ w, const float* __restrict__ 
   w_out[i] = nn > 0.0 ? (float)((double)w[i] + rho * (double)g[i] / sqrt(nn)) : w[i];
 }
 
+// w + s d (the weights of one point of a loss scan), rounded once from FP64
+__global__ void k_axpy(const float* __restrict__ w, const float* __restrict__ d, double s, int n,
+                       float* __restrict__ w_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  w_out[i] = (float)((double)w[i] + s * (double)d[i]);
+}
+
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, int n, double lr, double b1, double b2, double eps, int t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,6 +270,10 @@ void launch_sumsq(const float* g, int n, double* out, cudaStream_t s) { k_sumsq<
 void launch_ascent(const float* w, const float* g, int n, double rho, const double* norm2, float* w_out,
                    cudaStream_t s) {
   k_ascent<<<(n + 255) / 256, 256, 0, s>>>(w, g, n, rho, norm2, w_out);
+}
+
+void launch_axpy(const float* w, const float* d, double scale, int n, float* w_out, cudaStream_t s) {
+  k_axpy<<<(n + 255) / 256, 256, 0, s>>>(w, d, scale, n, w_out);
 }
 
 void launch_adam(float* w, const float* g, float* m, float* v, int n, double lr, int t, cudaStream_t s) {

@@ -14,6 +14,8 @@ void launch_sumsq(const float* g, int n, double* out, cudaStream_t s);
 void launch_ascent(const float* w, const float* g, int n, double rho, const double* norm2, float* w_out,
                    cudaStream_t s);
 void launch_adam(float* w, const float* g, float* m, float* v, int n, double lr, int t, cudaStream_t s);
+// w_out = w + scale d (FP64 arithmetic, one rounding)
+void launch_axpy(const float* w, const float* d, double scale, int n, float* w_out, cudaStream_t s);
 void launch_apply(const float* flat, int rows, int cols, float scale, float* t_out, float* n_out, cudaStream_t s);
 
 // ---- training batches: all structures in one pass sequence ----

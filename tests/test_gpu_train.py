@@ -15,7 +15,7 @@ import torch
 import synth
 import paper_2303_08169_gb300 as al
 from oracle.model import OracleModel
-from oracle.train import flat_params, loss_and_grad, sam_step
+from oracle.train import flat_params, loss_and_grad, loss_scan, sam_step
 from tests.conftest import GOLDEN
 
 pytestmark = pytest.mark.gpu
@@ -167,3 +167,27 @@ def test_uneven_batch_matches_oracle():
         al.allegro_destroy(ctx)
     assert abs(loss - lref) <= 1e-5 * lref
     assert np.linalg.norm(g - gref) <= 2e-3 * np.linalg.norm(gref)
+
+
+def test_loss_scan_matches_oracle(setup):
+    """Loss at w + eps_k (random eps_k of norm 0.05, the sharpness samples of
+    Eq. 2) and along one direction (the 1-D surface), against the oracle at
+    the same perturbed weights; the context's weights are unchanged after."""
+    ctx, stu, _, structs, w0 = setup
+    al.allegro_set_weights(ctx, w0)
+    b, keep = al.make_batch(structs)
+    rng = np.random.default_rng(7)
+    eps = rng.normal(size=(3, len(w0)))
+    eps *= 0.05 / np.linalg.norm(eps, axis=1, keepdims=True)
+    dirs = np.vstack([np.zeros(len(w0)), eps]).astype(np.float32)
+    got = al.allegro_loss_scan(ctx, b, torch.from_numpy(dirs).cuda(), [0.0, 1.0, 1.0, 1.0])
+    ref = loss_scan(stu, w0.astype(np.float64), dirs.astype(np.float64), [0.0, 1.0, 1.0, 1.0], structs, 1.0, 100.0)
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref))
+    p = np.array([-1.0, -0.5, 0.5, 1.0])
+    line = al.allegro_loss_scan(ctx, b, torch.from_numpy(dirs[1]).cuda(), p)
+    ref_line = loss_scan(stu, w0.astype(np.float64), dirs[1].astype(np.float64), p, structs, 1.0, 100.0)
+    assert np.all(np.abs(line - ref_line) <= 1e-5 * np.abs(ref_line))
+    back = np.zeros_like(w0)
+    al.allegro_get_weights(ctx, back)
+    assert np.array_equal(back, w0)
+    assert al.allegro_loss_grad(ctx, b, 1.0, 100.0) == pytest.approx(got[0], rel=1e-6)
