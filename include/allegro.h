@@ -282,6 +282,27 @@ int allegro_get_weights(allegro_ctx* ctx, float* out, int64_t n);
  * zero, step count 0): the next SAM step is the first of a new run. */
 int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n);
 
+/*
+ * NVT steps (the paper equilibrates at 200 K before its NVE runs, Sec. 3.2;
+ * its thermostat is not named: here Nose-Hoover): each step is a thermostat
+ * half step (dt/2), the velocity-Verlet step of allegro_md_step_nve, and a
+ * thermostat half step, in FP64, with g = 3N degrees of freedom, thermostat
+ * mass Q = g kB T tau^2 and the time-reversible half step
+ *   xi += (h/2) G;  v *= exp(-xi h);  eta += xi h;  xi += (h/2) G,
+ *   G = (2 K - g kB T) / Q,  h = dt / 2,
+ * K the kinetic energy at that point.  temperature_K > 0, tau_fs > 0 (the
+ * thermostat period).  outlier_counts: host or device int64[n_steps] or
+ * NULL; energies: host or device FP64[n_steps x 4] (E_pot, E_kin, E_tot, H)
+ * or NULL, H = E_pot + K + Q xi^2 / 2 + g kB T eta the conserved extended
+ * energy.  The thermostat state (xi, eta) persists across calls and is reset
+ * to zero by allegro_md_init.  Errors and pair-capacity growth as
+ * allegro_md_step_nve.
+ */
+int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double temperature_K, double tau_fs,
+                        int64_t* outlier_counts, double* energies);
+/* The thermostat state (xi in 1/fs, eta) into host or device xi_eta[2]. */
+int allegro_md_get_thermostat(allegro_ctx* ctx, double* xi_eta);
+
 /* Keys of allegro_query. */
 #define ALLEGRO_Q_N_PAIRS      0  /* ordered pairs of the last neighbour build   */
 #define ALLEGRO_Q_CAPACITY     1  /* pair capacity currently allocated           */

@@ -32,7 +32,7 @@ EXPORTED = [
     "allegro_query", "allegro_phase_times", "allegro_selftest_mma",
     "allegro_selftest_mma_mode", "allegro_outlier_count_noalloc",
     "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
-    "allegro_loss_scan",
+    "allegro_loss_scan", "allegro_md_step_nvt", "allegro_md_get_thermostat",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -83,6 +83,8 @@ def lib():
         "allegro_md_init": ([_vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "allegro_set_md_precision": ([_vp, _i32], ctypes.c_int),
         "allegro_md_step_nve": ([_vp, _f64, _i32, _vp, _vp], ctypes.c_int),
+        "allegro_md_step_nvt": ([_vp, _f64, _i32, _f64, _f64, _vp, _vp], ctypes.c_int),
+        "allegro_md_get_thermostat": ([_vp, _vp], ctypes.c_int),
         "allegro_md_get_state": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_i64)], ctypes.c_int),
         "allegro_query": ([_vp, _i32, ctypes.POINTER(_i64)], ctypes.c_int),
         "allegro_phase_times": ([_vp, _i32, _vp, _i32], ctypes.c_int),
@@ -255,6 +257,19 @@ def allegro_set_md_precision(ctx, precision):
 
 def allegro_md_step_nve(ctx, dt_fs, n_steps, outlier_counts=None, energies=None):
     _check(ctx, lib().allegro_md_step_nve(ctx, float(dt_fs), int(n_steps), _ptr(outlier_counts), _ptr(energies)))
+
+
+def allegro_md_step_nvt(ctx, dt_fs, n_steps, temperature_K, tau_fs, outlier_counts=None, energies=None):
+    """energies: (n_steps, 4) FP64 (E_pot, E_kin, E_tot, H) or None."""
+    _check(ctx, lib().allegro_md_step_nvt(ctx, float(dt_fs), int(n_steps), float(temperature_K), float(tau_fs),
+                                          _ptr(outlier_counts), _ptr(energies)))
+
+
+def allegro_md_get_thermostat(ctx):
+    """(xi, eta) of the Nose-Hoover thermostat."""
+    out = np.zeros(2, dtype=np.float64)
+    _check(ctx, lib().allegro_md_get_thermostat(ctx, _ptr(out)))
+    return float(out[0]), float(out[1])
 
 
 def allegro_md_get_state(ctx, positions=None, velocities=None, forces=None):

@@ -208,6 +208,11 @@ struct allegro_ctx {
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
   int64_t graph_kernels = 0;
+  // Nose-Hoover NVT: thermostat state (xi, eta, K, s) and its own step graph
+  double* d_nh = nullptr;
+  double* d_nh_snap = nullptr;
+  cudaGraphExec_t graph_nvt = nullptr;
+  double nvt_key[3] = {0.0, 0.0, 0.0};   // dt, T, tau of graph_nvt
   // rollback snapshot
   double* d_pos_snap = nullptr;
   double* d_v_snap = nullptr;
@@ -234,8 +239,17 @@ struct allegro_ctx {
     for (auto& a : allocs)
       if (a == p) { cudaFree(p); a = nullptr; }
   }
+  // the captured step graphs bake in buffers, weights and precision: every
+  // change of those drops them (they are re-captured at the next MD call)
+  void drop_graphs() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (graph_nvt) cudaGraphExecDestroy(graph_nvt);
+    graph = nullptr;
+    graph_nvt = nullptr;
+  }
   ~allegro_ctx() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph_nvt) cudaGraphExecDestroy(graph_nvt);
     for (void* p : allocs)
       if (p) cudaFree(p);
   }
@@ -463,7 +477,9 @@ int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
     c->nb.n_pairs = c->dalloc<int>(1);
     c->nb.flags = c->dalloc<int>(1);
     c->d_step = c->dalloc<long long>(1);
-    if (!c->d_stats || !c->d_count || !c->nb.n_pairs || !c->nb.flags || !c->d_step)
+    c->d_nh = c->dalloc<double>(4);
+    c->d_nh_snap = c->dalloc<double>(4);
+    if (!c->d_stats || !c->d_count || !c->nb.n_pairs || !c->nb.flags || !c->d_step || !c->d_nh || !c->d_nh_snap)
       return c->fail(ALLEGRO_E_OOM, "allocation failed");
     cudaMemset(c->nb.flags, 0, sizeof(int));
   }
@@ -566,10 +582,7 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   c->capacity = cap;
   c->nb.capacity = cap;
   c->part_rows = rows;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  c->drop_graphs();
   return ALLEGRO_OK;
 }
 
@@ -895,10 +908,7 @@ int build_batch(allegro_ctx* c, const allegro_batch* b) {
   const int64_t N = b->atom_offset[nb] - base;
   // a training batch replaces the single-system state
   c->md_ready = false;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  c->drop_graphs();
   int rc = bt_reserve(c, N, std::max<int64_t>(t.cap_pairs, 64 * N), nb, 0, 0);
   if (rc) return rc;
   int64_t P0 = 0;
@@ -1102,10 +1112,7 @@ void allegro_destroy(allegro_ctx* ctx) { delete ctx; }
 int allegro_set_stream(allegro_ctx* ctx, void* s) {
   if (!ctx) return ALLEGRO_E_INVALID_ARG;
   ctx->stream = (cudaStream_t)s;
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();
   return ALLEGRO_OK;
 }
 
@@ -1226,17 +1233,87 @@ int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions, 
   if (rc) return rc;
   // state positions are the wrapped ones
   cudaMemcpyAsync(ctx->d_pos, ctx->nb.wpos, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, ctx->stream);
+  cudaMemsetAsync(ctx->d_nh, 0, sizeof(double) * 4, ctx->stream);   // thermostat at rest (xi = eta = 0)
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "md_init");
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();
   ctx->step = 0;
   ctx->md_ready = true;
   return ALLEGRO_OK;
 }
 
 namespace {
+
+// per-step records (energies, 4 values a step, and outlier counts) for
+// n_steps steps; the step graphs bake the pointers in
+int ensure_records(allegro_ctx* c, int n_steps) {
+  if (n_steps <= c->rec_cap) return ALLEGRO_OK;
+  c->dfree(c->d_e_rec);
+  c->dfree(c->d_out_rec);
+  const int cap = std::max(n_steps, 1024);
+  c->d_e_rec = c->dalloc<double>(4 * (size_t)cap);
+  c->d_out_rec = c->dalloc<long long>(cap);
+  if (!c->d_e_rec || !c->d_out_rec) return c->fail(ALLEGRO_E_OOM, "record allocation failed");
+  c->rec_cap = cap;
+  c->drop_graphs();
+  return ALLEGRO_OK;
+}
+
+// end a capture on cs, count its kernels and instantiate it into *out
+int finish_capture(allegro_ctx* c, cudaStream_t cs, bool own, cudaGraphExec_t* out, int64_t* kernels) {
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (e != cudaSuccess) {
+    if (own) cudaStreamDestroy(cs);
+    return cuda_check(c, "end capture");
+  }
+  size_t n_nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &n_nodes);
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+  *kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++*kernels;
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (own) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_check(c, "graph instantiate");
+  return ALLEGRO_OK;
+}
+
+// one NVT step as a graph: thermostat half step, kick, drift, neighbour
+// list, energy and forces, kick, thermostat half step, record
+int capture_step_nvt(allegro_ctx* c, double dt, double temperature, double tau) {
+  if (c->graph_nvt) {
+    cudaGraphExecDestroy(c->graph_nvt);
+    c->graph_nvt = nullptr;
+  }
+  double L[3] = {c->grid.L[0], c->grid.L[1], c->grid.L[2]};
+  fill_passbufs(c, L);
+  cudaStream_t cs = c->stream;
+  bool own = false;
+  if (!cs) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_check(c, "stream");
+    own = true;
+  }
+  const double gkt = 3.0 * (double)c->n_atoms * kBoltzmannEv * temperature;
+  const double q = gkt * tau * tau;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_check(c, "capture");
+  const AtomArgs a = atom_args(c);
+  launch_nvt_first_half(a, c->d_pos, c->d_v, c->d_F, dt, L, gkt, q, c->d_blk_ke, c->d_nh, cs);
+  launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs);
+  launch_model(c, c->md_precision, cs, nullptr);
+  launch_nvt_second_half(a, c->d_v, c->d_F, dt, c->d_stats, 5.0, gkt, q, c->d_blk_ke, c->d_blku, c->d_nh,
+                         c->d_step, c->rec_cap, c->d_e_rec, c->d_out_rec, cs);
+  int64_t kernels = 0;
+  const int rc = finish_capture(c, cs, own, &c->graph_nvt, &kernels);
+  if (rc) return rc;
+  c->nvt_key[0] = dt;
+  c->nvt_key[1] = temperature;
+  c->nvt_key[2] = tau;
+  return ALLEGRO_OK;
+}
 
 int capture_step(allegro_ctx* c, double dt) {
   if (c->graph) {
@@ -1288,19 +1365,8 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
   if (!ctx || !ctx->md_ready) return ctx ? ctx->fail(ALLEGRO_E_INVALID_ARG, "md_init first") : ALLEGRO_E_INVALID_ARG;
   if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "bad dt or n_steps");
   if (n_steps == 0) return ALLEGRO_OK;
-  if (n_steps > ctx->rec_cap) {
-    ctx->dfree(ctx->d_e_rec);
-    ctx->dfree(ctx->d_out_rec);
-    const int cap = std::max(n_steps, 1024);
-    ctx->d_e_rec = ctx->dalloc<double>(3 * (size_t)cap);
-    ctx->d_out_rec = ctx->dalloc<long long>(cap);
-    if (!ctx->d_e_rec || !ctx->d_out_rec) return ctx->fail(ALLEGRO_E_OOM, "record allocation failed");
-    ctx->rec_cap = cap;
-    if (ctx->graph) {
-      cudaGraphExecDestroy(ctx->graph);
-      ctx->graph = nullptr;
-    }
-  }
+  int rc0 = ensure_records(ctx, n_steps);
+  if (rc0) return rc0;
   const size_t n3 = 3 * (size_t)ctx->n_atoms;
   for (int attempt = 0; attempt < 3; ++attempt) {
     if (!ctx->graph || ctx->graph_dt != dt_fs) {
@@ -1337,6 +1403,66 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
     return ALLEGRO_OK;
   }
   return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown during MD");
+}
+
+int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double temperature_K, double tau_fs,
+                        int64_t* outlier_counts, double* energies) {
+  if (!ctx || !ctx->md_ready) return ctx ? ctx->fail(ALLEGRO_E_INVALID_ARG, "md_init first") : ALLEGRO_E_INVALID_ARG;
+  if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "bad dt or n_steps");
+  if (!(temperature_K > 0.0) || !std::isfinite(temperature_K) || !(tau_fs > 0.0) || !std::isfinite(tau_fs))
+    return ctx->fail(ALLEGRO_E_INVALID_ARG, "temperature and tau must be positive");
+  if (n_steps == 0) return ALLEGRO_OK;
+  int rc = ensure_records(ctx, n_steps);
+  if (rc) return rc;
+  const size_t n3 = 3 * (size_t)ctx->n_atoms;
+  const AtomArgs a = atom_args(ctx);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    if (!ctx->graph_nvt || ctx->nvt_key[0] != dt_fs || ctx->nvt_key[1] != temperature_K || ctx->nvt_key[2] != tau_fs) {
+      rc = capture_step_nvt(ctx, dt_fs, temperature_K, tau_fs);
+      if (rc) return rc;
+    }
+    cudaMemcpyAsync(ctx->d_pos_snap, ctx->d_pos, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_v_snap, ctx->d_v, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_F_snap, ctx->d_F, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_nh_snap, ctx->d_nh, sizeof(double) * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream);
+    launch_nh_set_k(a, ctx->d_v, ctx->d_blk_ke, ctx->d_nh, ctx->stream);   // K of the current velocities
+    for (int s = 0; s < n_steps; ++s)
+      if (cudaGraphLaunch(ctx->graph_nvt, ctx->stream) != cudaSuccess) return cuda_check(ctx, "graph launch");
+    int flags = 0, np = 0;
+    cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "nvt steps");
+    if (flags & kFlagPairOverflow) {
+      cudaMemcpyAsync(ctx->d_pos, ctx->d_pos_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->d_v, ctx->d_v_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->d_F, ctx->d_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->d_nh, ctx->d_nh_snap, sizeof(double) * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+      const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024;
+      rc = ensure_pairs(ctx, grow);
+      if (rc) return rc;
+      continue;
+    }
+    if (flags & kFlagNonfinite) return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite energy or force during MD");
+    ctx->step += n_steps;
+    rc = copy_out(ctx, outlier_counts, ctx->d_out_rec, sizeof(long long) * n_steps);
+    if (!rc) rc = copy_out(ctx, energies, ctx->d_e_rec, sizeof(double) * 4 * n_steps);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "nvt record copy");
+    return ALLEGRO_OK;
+  }
+  return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown during MD");
+}
+
+int allegro_md_get_thermostat(allegro_ctx* ctx, double* xi_eta) {
+  if (!ctx || !xi_eta) return ALLEGRO_E_INVALID_ARG;
+  if (!ctx->md_ready) return ctx->fail(ALLEGRO_E_INVALID_ARG, "md_init first");
+  const int rc = copy_out(ctx, xi_eta, ctx->d_nh, sizeof(double) * 2);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "thermostat state");
+  return ALLEGRO_OK;
 }
 
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
@@ -1453,10 +1579,7 @@ int allegro_sam_train_step(allegro_ctx* ctx, const allegro_batch* batch, double 
   ctx->adam_t += 1;
   launch_adam(ctx->d_master, ctx->d_grad, ctx->d_adam_m, ctx->d_adam_v, n, lr, ctx->adam_t, ctx->stream);
   apply_flat(ctx, ctx->d_master);
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "sam step");
   return ALLEGRO_OK;
 }
@@ -1483,10 +1606,7 @@ int allegro_loss_scan(allegro_ctx* ctx, const allegro_batch* batch, const float*
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_check(ctx, "loss_scan");
   }
   apply_flat(ctx, ctx->d_master);                      // the context's weights are unchanged
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();
   int flags = 0;
   cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return rc ? rc : cuda_check(ctx, "loss_scan");
@@ -1515,10 +1635,7 @@ int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n) {
   cudaMemsetAsync(ctx->d_adam_v, 0, sizeof(float) * n, ctx->stream);
   ctx->adam_t = 0;
   apply_flat(ctx, ctx->d_master);
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "set_weights");
   return ALLEGRO_OK;
 }

@@ -175,9 +175,121 @@ __global__ void k_record(const double* __restrict__ stats, const double* __restr
   *step = s + 1;
 }
 
+// ---- Nose-Hoover thermostat (NVT); state nh = (xi, eta, K, s) in FP64 ----
+
+// K of the current velocities into nh[2] (per-block partials, then a
+// fixed-order sum by k_nh_set_k)
+__global__ void __launch_bounds__(kBlock)
+k_ke_partials(AtomArgs a, const double* __restrict__ v, double* __restrict__ blk_ke) {
+  __shared__ double sh[kBlock / 32];
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  double ke = 0.0;
+  if (i < a.n) {
+    const double m = a.mass[a.species[i]];
+    for (int k = 0; k < 3; ++k) ke += 0.5 * m * v[3 * i + k] * v[3 * i + k];
+  }
+  const double s = block_sum(ke, sh);
+  if (threadIdx.x == 0) blk_ke[blockIdx.x] = s / kKappa;
+}
+__global__ void k_nh_set_k(const double* __restrict__ blk_ke, int nblk, double* __restrict__ nh) {
+  if (threadIdx.x != 0) return;
+  double k = 0.0;
+  for (int b = 0; b < nblk; ++b) k += blk_ke[b];
+  nh[2] = k;
+}
+
+// thermostat half step of length h (one thread): K from the block partials of
+// the current velocities (use_partials) or nh[2]; xi by (h/2) G, G = (2K -
+// g kT) / Q; s = exp(-xi h) (the next kernel scales the velocities by it);
+// K by s^2; eta by xi h; xi by (h/2) G
+__global__ void k_nh_half(const double* __restrict__ blk_ke, int nblk, int use_partials, double h, double gkt,
+                          double q, double* __restrict__ nh) {
+  if (threadIdx.x != 0) return;
+  double k = 0.0;
+  if (use_partials) {
+    for (int b = 0; b < nblk; ++b) k += blk_ke[b];
+  } else {
+    k = nh[2];
+  }
+  double xi = nh[0] + 0.5 * h * (2.0 * k - gkt) / q;
+  const double s = exp(-xi * h);
+  k = k * s * s;
+  const double eta = nh[1] + xi * h;
+  xi = xi + 0.5 * h * (2.0 * k - gkt) / q;
+  nh[0] = xi;
+  nh[1] = eta;
+  nh[2] = k;
+  nh[3] = s;
+}
+
+// v = s v (thermostat) then the first half kick and the drift
+__global__ void __launch_bounds__(kBlock)
+k_kick_drift_nh(AtomArgs a, double* __restrict__ r, double* __restrict__ v, const float* __restrict__ F, double dt,
+                double L0, double L1, double L2, const double* __restrict__ nh) {
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  if (i >= a.n) return;
+  const double c = 0.5 * dt * kKappa / a.mass[a.species[i]];
+  const double s = nh[3];
+  const double L[3] = {L0, L1, L2};
+  for (int k = 0; k < 3; ++k) {
+    const double vs = v[3 * i + k] * s;
+    const double vv = vs + c * (double)F[3 * i + k];
+    v[3 * i + k] = vv;
+    r[3 * i + k] = wrap1(r[3 * i + k] + dt * vv, L[k]);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_scale_v(int n3, double* __restrict__ v, const double* __restrict__ nh) {
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  if (i < n3) v[i] *= nh[3];
+}
+
+// energies[step] = (E_pot, K, E_pot + K, H), H = E_pot + K + Q xi^2 / 2 + g kT eta
+__global__ void k_record_nh(const double* __restrict__ stats, const unsigned long long* __restrict__ blk_out,
+                            int nblk, const double* __restrict__ nh, double gkt, double q,
+                            long long* __restrict__ step, int max_steps, double* __restrict__ energies,
+                            long long* __restrict__ outliers) {
+  if (threadIdx.x != 0) return;
+  unsigned long long c = 0;
+  for (int b = 0; b < nblk; ++b) c += blk_out[b];
+  const long long s = *step;
+  if (s >= 0 && s < max_steps) {
+    const double e = stats[0], k = nh[2];
+    energies[4 * s] = e;
+    energies[4 * s + 1] = k;
+    energies[4 * s + 2] = e + k;
+    energies[4 * s + 3] = e + k + 0.5 * q * nh[0] * nh[0] + gkt * nh[1];
+    outliers[s] = (long long)c;
+  }
+  *step = s + 1;
+}
+
 }  // namespace
 
 int atom_blocks(int n) { return (n + kBlock - 1) / kBlock; }
+
+void launch_nh_set_k(const AtomArgs& a, const double* v, double* blk_ke, double* nh, cudaStream_t s) {
+  const int nb = atom_blocks(a.n);
+  k_ke_partials<<<nb, kBlock, 0, s>>>(a, v, blk_ke);
+  k_nh_set_k<<<1, 32, 0, s>>>(blk_ke, nb, nh);
+}
+
+void launch_nvt_first_half(const AtomArgs& a, double* r, double* v, const float* F, double dt, const double L[3],
+                           double gkt, double q, const double* blk_ke, double* nh, cudaStream_t s) {
+  k_nh_half<<<1, 32, 0, s>>>(blk_ke, 0, 0, 0.5 * dt, gkt, q, nh);
+  k_kick_drift_nh<<<atom_blocks(a.n), kBlock, 0, s>>>(a, r, v, F, dt, L[0], L[1], L[2], nh);
+}
+
+void launch_nvt_second_half(const AtomArgs& a, double* v, const float* F, double dt, const double* stats,
+                            double thr, double gkt, double q, double* blk_ke, unsigned long long* blk_out,
+                            double* nh, long long* step, int max_steps, double* energies, long long* outliers,
+                            cudaStream_t s) {
+  const int nb = atom_blocks(a.n);
+  k_kick_measure<<<nb, kBlock, 0, s>>>(a, v, F, dt, stats, thr, blk_ke, blk_out);
+  k_nh_half<<<1, 32, 0, s>>>(blk_ke, nb, 1, 0.5 * dt, gkt, q, nh);
+  k_scale_v<<<(3 * a.n + kBlock - 1) / kBlock, kBlock, 0, s>>>(3 * a.n, v, nh);
+  k_record_nh<<<1, 32, 0, s>>>(stats, blk_out, nb, nh, gkt, q, step, max_steps, energies, outliers);
+}
 
 void launch_forces(const AtomArgs& a, const int* row_ptr, const int* rev, const float* G,
                    const double* epart, int tile, float* F, double* Ei, double* blk,

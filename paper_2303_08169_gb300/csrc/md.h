@@ -5,6 +5,7 @@
 namespace al {
 
 constexpr double kKappa = 9.648533e-3;   // 1 eV/(A amu) in A/fs^2
+constexpr double kBoltzmannEv = 8.617333262e-5;   // eV/K
 
 struct AtomArgs {
   int n;
@@ -33,5 +34,18 @@ void launch_kick_measure(const AtomArgs& a, double* v, const float* F, double dt
                          const double* stats, double thr, double* blk_ke,
                          unsigned long long* blk_out, long long* step, int max_steps,
                          double* energies, long long* outliers, cudaStream_t s);
+
+// Nose-Hoover NVT (thermostat state nh = (xi, eta, K, s), FP64):
+// nh[2] = K of the velocities v
+void launch_nh_set_k(const AtomArgs& a, const double* v, double* blk_ke, double* nh, cudaStream_t s);
+// thermostat half step, then v = s v + dt/2 kappa F/m and r = wrap(r + dt v)
+void launch_nvt_first_half(const AtomArgs& a, double* r, double* v, const float* F, double dt, const double L[3],
+                           double gkt, double q, const double* blk_ke, double* nh, cudaStream_t s);
+// v += dt/2 kappa F/m, thermostat half step (K from v), v = s v, record
+// (E_pot, K, E_tot, H) and the outlier count of the step
+void launch_nvt_second_half(const AtomArgs& a, double* v, const float* F, double dt, const double* stats,
+                            double thr, double gkt, double q, double* blk_ke, unsigned long long* blk_out,
+                            double* nh, long long* step, int max_steps, double* energies, long long* outliers,
+                            cudaStream_t s);
 
 }  // namespace al

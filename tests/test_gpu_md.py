@@ -1,12 +1,12 @@
-"""GPU NVE velocity Verlet (Eq. 1, Sec. 3.2) and the >5 sigma outlier count
-(Fig. 1 caption) vs the oracle."""
+"""GPU NVE velocity Verlet (Eq. 1, Sec. 3.2), Nose-Hoover NVT and the >5 sigma
+outlier count (Fig. 1 caption) vs the oracle."""
 import numpy as np
 import pytest
 import torch
 
 import synth
 import paper_2303_08169_gb300 as al
-from oracle.md import kinetic_energy, outlier_count, velocity_verlet
+from oracle.md import kinetic_energy, nose_hoover, outlier_count, velocity_verlet
 from oracle.model import OracleModel
 from tests.conftest import energy_scale
 
@@ -82,4 +82,64 @@ def test_md_6912_energy_conservation_and_resume():
     e3 = np.zeros((25, 3))
     al.allegro_md_step_nve(ctx, 0.25, 25, None, e3)
     assert np.array_equal(np.concatenate([e2, e3]), e1)
+    al.allegro_destroy(ctx)
+
+
+def test_tiny_nvt_matches_oracle_trajectory():
+    """A hot start (400 K) thermostatted to 200 K with a 10 fs period: the
+    thermostat acts within the 20 steps, and positions, velocities, energies,
+    the extended energy H and the thermostat variable follow the oracle."""
+    cfg = synth.TINY
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("tiny"))
+    orc = OracleModel(blob)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(16, 0)
+    L = np.diag(cell)
+    v0 = synth.make_velocities(sp, 400.0, 1)
+    n, T, tau = 20, 200.0, 10.0
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    assert al.allegro_md_get_thermostat(ctx) == (0.0, 0.0)
+    out = torch.zeros(n, dtype=torch.int64, device="cuda")
+    en = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    al.allegro_md_step_nvt(ctx, 0.5, n, T, tau, out, en)
+    P = np.zeros((len(pos), 3))
+    V = np.zeros((len(pos), 3))
+    assert al.allegro_md_get_state(ctx, P, V) == n
+    xi, eta = al.allegro_md_get_thermostat(ctx)
+    ref = nose_hoover(lambda p: orc.energy_forces(p, sp, L)[:2], pos, v0, MASS[sp], L, 0.5, n, T, tau)
+    en = en.cpu().numpy()
+    d = P - ref["pos"]
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() < 1e-5
+    assert np.abs(V - ref["vel"]).max() < 1e-5
+    assert abs(ref["xi"]) > 1e-3 and abs(xi - ref["xi"]) <= 1e-4 * abs(ref["xi"])
+    assert abs(eta - ref["eta"]) <= 1e-4 * abs(ref["eta"])
+    np.testing.assert_allclose(en[:, 1], ref["ekin"], rtol=1e-5, atol=1e-7)
+    scale = abs(ref["epot"]).max()
+    np.testing.assert_allclose(en[:, 0], ref["epot"], rtol=0, atol=1e-4 * scale)
+    np.testing.assert_allclose(en[:, 3], ref["hext"], rtol=0, atol=1e-4 * scale)
+    assert abs(kinetic_energy(V, MASS[sp]) - en[-1, 1]) < 1e-9 * en[-1, 1]
+    al.allegro_destroy(ctx)
+
+
+def test_nvt_conserves_extended_energy_and_cools():
+    """200 steps from 400 K to 200 K: the total energy falls by far more than
+    the extended energy H moves, and the thermostat state carries over from
+    one call to the next (two calls of 100 steps equal one of 200)."""
+    cfg = synth.TINY
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("tiny"))
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(16, 0)
+    v0 = synth.make_velocities(sp, 400.0, 1)
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    e1 = np.zeros((200, 4))
+    al.allegro_md_step_nvt(ctx, 0.25, 200, 200.0, 10.0, None, e1)
+    al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+    a, b = np.zeros((100, 4)), np.zeros((100, 4))
+    al.allegro_md_step_nvt(ctx, 0.25, 100, 200.0, 10.0, None, a)
+    al.allegro_md_step_nvt(ctx, 0.25, 100, 200.0, 10.0, None, b)
+    assert np.array_equal(np.vstack([a, b]), e1)
+    dH = np.abs(e1[:, 3] - e1[0, 3]).max()
+    dE = e1[0, 2] - e1[:, 2].min()
+    assert dE > 0 and dH < 0.1 * dE
     al.allegro_destroy(ctx)

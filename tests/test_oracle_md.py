@@ -1,12 +1,12 @@
-"""Pins for the oracle's NVE velocity Verlet (Eq. 1, Sec. 3.2) and the
->5 sigma force-outlier count (Fig. 1 caption)."""
+"""Pins for the oracle's NVE velocity Verlet (Eq. 1, Sec. 3.2), its
+Nose-Hoover NVT and the >5 sigma force-outlier count (Fig. 1 caption)."""
 import math
 
 import numpy as np
 import pytest
 
 import synth
-from oracle.md import KAPPA, kinetic_energy, outlier_count, velocity_verlet
+from oracle.md import KAPPA, KB_EV, kinetic_energy, nose_hoover, outlier_count, velocity_verlet
 
 
 def test_verlet_harmonic_shadow_energy_exact():
@@ -83,3 +83,71 @@ def test_nve_drift_and_second_order(tiny_model):
     fb = np.abs(b["etot"] - b["etot"][0]).max()
     fc = np.abs(c["etot"] - c["etot"][0]).max()
     assert 2.5 < fb / fc < 6.0
+
+
+def _wells(n, seed=0):
+    """n particles in separate anharmonic wells (no pair forces): E = sum
+    k |x|^2 / 2 + a |x|^4 / 4 about fixed centres."""
+    rng = np.random.default_rng(seed)
+    ctr = 100.0 + 200.0 * rng.random((n, 3))
+    x0 = ctr + 0.3 * rng.normal(size=(n, 3))
+    v0 = 0.01 * rng.normal(size=(n, 3))
+    m = np.where(rng.random(n) < 0.5, 14.007, 1.008)
+    k, a = 2.0, 0.5
+
+    def ffn(p):
+        d = p - ctr
+        r2 = (d * d).sum(axis=1, keepdims=True)
+        return float((0.5 * k * r2 + 0.25 * a * r2 * r2).sum()), -(k + a * r2) * d
+
+    return ffn, x0, v0, m, np.array([1000.0, 1000.0, 1000.0])
+
+
+def test_nvt_without_coupling_is_verlet():
+    """An infinitely heavy thermostat (tau -> inf) leaves xi at zero: the
+    NVT steps are the velocity-Verlet steps."""
+    ffn, x0, v0, m, L = _wells(20)
+    a = nose_hoover(ffn, x0, v0, m, L, 0.5, 50, 300.0, 1e12)
+    b = velocity_verlet(ffn, x0, v0, m, L, 0.5, 50)
+    assert np.abs(a["pos"] - b["pos"]).max() < 1e-12 and np.abs(a["vel"] - b["vel"]).max() < 1e-13
+    assert abs(a["xi"]) < 1e-15
+
+
+def test_nvt_time_reversible():
+    """The splitting is symmetric: n steps, then n steps with v and xi
+    negated, return to the start."""
+    ffn, x0, v0, m, L = _wells(20, 1)
+    a = nose_hoover(ffn, x0, v0, m, L, 0.5, 200, 300.0, 20.0)
+    b = nose_hoover(ffn, a["pos"], -a["vel"], m, L, 0.5, 200, 300.0, 20.0, xi=-a["xi"], eta=a["eta"])
+    assert np.abs(b["pos"] - x0).max() < 1e-9
+    assert np.abs(-b["vel"] - v0).max() < 1e-11
+    assert abs(b["xi"]) < 1e-12
+
+
+def test_nvt_extended_energy_second_order():
+    """H = E_pot + K + Q xi^2 / 2 + g kT eta is conserved up to the splitting
+    error, which shrinks about 4x when dt halves."""
+    ffn, x0, v0, m, L = _wells(30, 2)
+    dev = []
+    for dt, n in ((0.4, 100), (0.2, 200)):
+        o = nose_hoover(ffn, x0, v0, m, L, dt, n, 300.0, 20.0)
+        dev.append(np.abs(o["hext"] - o["hext"][0]).max())
+    assert 3.0 < dev[0] / dev[1] < 5.0
+
+
+def test_nvt_free_particles_average_temperature():
+    """With no forces the thermostat variable oscillates; dxi/dt = (2K - g kT)/Q
+    integrates to zero over whole periods, so the time average of 2K/(g kB) is T."""
+    rng = np.random.default_rng(3)
+    n = 50
+    x0 = 500.0 + rng.random((n, 3))
+    m = np.full(n, 14.007)
+    v0 = rng.normal(size=(n, 3)) * np.sqrt(KAPPA * KB_EV * 600.0 / m[:, None])   # about 600 K
+
+    def ffn(p):
+        return 0.0, np.zeros_like(p)
+
+    T, tau = 200.0, 10.0
+    o = nose_hoover(ffn, x0, v0, m, np.array([1000.0] * 3), 0.25, 20000, T, tau)
+    t_inst = 2.0 * o["ekin"] / (3 * n * KB_EV)
+    assert abs(t_inst.mean() / T - 1.0) < 0.03
