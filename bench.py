@@ -315,6 +315,32 @@ class Runner:
                 "outliers_last": int(outl[-1].item()), "outliers_max": int(outl.max().item()),
                 "pos": pos, "sp": sp, "cell": cell}
 
+    def nvt(self, name, K, W, temperature=200.0, tau=100.0):
+        """K graph-captured Nose-Hoover NVT steps after W warm-up steps, from
+        the workload's 200 K start; returns ms, pairs and the drift of the
+        conserved extended energy."""
+        al, torch, dev = self.al, self.torch, self.dev
+        w = WORKLOADS[name]
+        pos, sp, cell, vel = _system(w["n_mol"])
+        al.allegro_set_md_precision(self.ctx, w["precision"])
+        al.allegro_md_init(self.ctx, torch.tensor(pos, device=dev), torch.tensor(vel, device=dev),
+                           torch.tensor(sp, device=dev, dtype=torch.int32), cell)
+        ener = torch.zeros((K, 4), dtype=torch.float64, device=dev)
+        al.allegro_md_step_nvt(self.ctx, w["dt"], W, temperature, tau)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(self.stream)
+        al.allegro_md_step_nvt(self.ctx, w["dt"], K, temperature, tau, None, ener)
+        ev1.record(self.stream)
+        torch.cuda.synchronize()
+        en = ener.cpu().numpy()
+        N = len(sp)
+        return {"ms": ev0.elapsed_time(ev1), "N": N, "K": K,
+                "n_pairs": al.allegro_query(self.ctx, al.ALLEGRO_Q_N_PAIRS),
+                "H_drift_over_NkT": float(np.abs(en[:, 3] - en[0, 3]).max() / (N * KB_T200)),
+                "T_end_K": float(2.0 * en[-1, 1] / (3 * N * 8.617333262e-5))}
+
     def phases(self, n_reps=20):
         """Per-kernel device times at the current MD state (CUDA events on
         the library stream) and the pair count of that state."""
@@ -490,6 +516,12 @@ def run_ours(args):
             r = head if name == args.config else run.md(name, K2, W)
             paths[name] = {"value": r["N"] * r["K"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / r["K"],
                            "atoms": r["N"], "pairs": r["n_pairs"], "steps": r["K"], "dtype": WORKLOADS[name]["dtype"]}
+        rn = run.nvt(args.config, min(K, 200), W)
+        nvt = {"workload": args.config, "value": rn["N"] * rn["K"] / (rn["ms"] * 1e-3), "unit": "atom-steps/s",
+               "ms_per_step": rn["ms"] / rn["K"], "steps": rn["K"], "pairs": rn["n_pairs"],
+               "temperature_K": 200.0, "tau_fs": 100.0, "H_drift_over_NkT": rn["H_drift_over_NkT"],
+               "T_end_K": rn["T_end_K"],
+               "note": "allegro_md_step_nvt: Nose-Hoover half steps around the same velocity-Verlet step"}
         sam = sam_timing(al, torch)
         if args.config != SCALE and not args.no_scale:
             big = Runner(al, torch, dev, blob, cfg)
@@ -512,6 +544,7 @@ def run_ours(args):
     else:
         e2e = None
         sam = None
+        nvt = None
     run.close()
     if rank != 0:
         if dist:
@@ -551,6 +584,8 @@ def run_ours(args):
             if args.config in accuracy else None, **accuracy}
     if sam:
         line["sam_train_step"] = sam
+    if nvt:
+        line["nvt"] = nvt
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
