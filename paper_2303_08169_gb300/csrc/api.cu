@@ -547,8 +547,6 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
     c->dfree(pb.S[k]);
     pb.S[k] = nullptr;
   }
-  c->dfree(pb.dS);
-  pb.dS = nullptr;
   c->dfree(pb.dR);
   pb.dR = nullptr;
   if (c->bf16_ok) {
@@ -557,8 +555,6 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
       pb.S[k] = c->dalloc<float>((size_t)capr * NSC);
       ok = ok && pb.S[k];
     }
-    pb.dS = c->dalloc<float>((size_t)capr * NSC);
-    ok = ok && pb.dS;
     pb.dR = c->dalloc<float>((size_t)capr * 3);
     ok = ok && pb.dR;
   }

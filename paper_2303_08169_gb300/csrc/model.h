@@ -81,7 +81,6 @@ struct PassBufs {
   float* G;               // P x 3  (dE/dDelta)
   float* S[kMaxLayers];   // BF16 path: tensor-product scalars of layer k (P x C P_0)
   float* dR = nullptr;    // tensor-core path: pair separation in FP32 (P x 3), written by pass A
-  float* dS;              // BF16 path: their gradient (P x C P_0)
   // per (tile, atom) partial sums, index (tile + atom)
   float* gam[kMaxLayers + 1];   // Gamma^k partials, k = 1..L
   float* dgam[kMaxLayers + 1];  // dGamma^k partials
