@@ -303,6 +303,45 @@ int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double 
 /* The thermostat state (xi in 1/fs, eta) into host or device xi_eta[2]. */
 int allegro_md_get_thermostat(allegro_ctx* ctx, double* xi_eta);
 
+/*
+ * Ring-polymer (path-integral) MD, the nuclear-quantum-effect workload of
+ * Sec. 6 (Fig. 6): every atom is P replicas (beads) coupled by harmonic
+ * springs along a closed ring, at P times the physical temperature,
+ *   H_P = sum_k [ sum_i m_i |v_ik|^2 / 2 + V(q_k) ]
+ *         + sum_i sum_k m_i omega_P^2 |q_ik - q_i,k+1|^2 / 2,
+ *   omega_P = P kB T / hbar,  replica P + 1 = replica 1.
+ * The paper states neither the equations nor the integrator; this is the
+ * standard form, integrated by velocity Verlet with the spring part solved
+ * exactly in the normal modes of the ring (frequencies 2 omega_P sin(k pi / P)).
+ * The energies and forces of all P replicas come from ONE pass sequence over
+ * the concatenated neighbour lists (each replica's list built with the common
+ * box), in the precision set by allegro_set_md_precision.
+ *
+ * allegro_pimd_init: n_beads in [1, 64], n_atoms >= 1; positions and
+ * velocities host or device FP64[n_beads x n_atoms x 3], replica-major
+ * (replica k's atom i at (k n_atoms + i) x 3), in A and A/fs; species host or
+ * device int32[n_atoms] (shared by the replicas); cell host FP64[9]
+ * (orthorhombic, as allegro_build_neighbors); temperature_K > 0.  Bead
+ * positions are not wrapped (each replica's neighbour build wraps them), so
+ * the springs are plain differences.  Evaluates the forces once; copies the
+ * inputs.  Replaces the single-system MD state (allegro_md_init again before
+ * allegro_md_step_*).
+ *
+ * allegro_pimd_step: n_steps >= 0 steps of dt_fs > 0:
+ *   v += dt/2 F/m;  free ring evolution for dt;  F <- F(q);  v += dt/2 F/m,
+ * energies: host or device FP64[n_steps x 3] or NULL: (mean replica energy
+ * sum_k V(q_k) / P, kinetic energy of all replicas, H_P) in eV after each
+ * step.  ALLEGRO_E_NONFINITE, ALLEGRO_E_PAIR_OVERFLOW as allegro_md_step_nve;
+ * after an error the ring state is undefined (allegro_pimd_init again).
+ *
+ * allegro_pimd_get_state: positions, velocities host or device
+ * FP64[n_beads x n_atoms x 3] (either may be NULL).
+ */
+int allegro_pimd_init(allegro_ctx* ctx, int32_t n_beads, int64_t n_atoms, const double* positions,
+                      const double* velocities, const int32_t* species, const double* cell, double temperature_K);
+int allegro_pimd_step(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double* energies);
+int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velocities);
+
 /* Keys of allegro_query. */
 #define ALLEGRO_Q_N_PAIRS      0  /* ordered pairs of the last neighbour build   */
 #define ALLEGRO_Q_CAPACITY     1  /* pair capacity currently allocated           */

@@ -33,6 +33,7 @@ EXPORTED = [
     "allegro_selftest_mma_mode", "allegro_outlier_count_noalloc",
     "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
     "allegro_loss_scan", "allegro_md_step_nvt", "allegro_md_get_thermostat",
+    "allegro_pimd_init", "allegro_pimd_step", "allegro_pimd_get_state",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -85,6 +86,9 @@ def lib():
         "allegro_md_step_nve": ([_vp, _f64, _i32, _vp, _vp], ctypes.c_int),
         "allegro_md_step_nvt": ([_vp, _f64, _i32, _f64, _f64, _vp, _vp], ctypes.c_int),
         "allegro_md_get_thermostat": ([_vp, _vp], ctypes.c_int),
+        "allegro_pimd_init": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _f64], ctypes.c_int),
+        "allegro_pimd_step": ([_vp, _f64, _i32, _vp], ctypes.c_int),
+        "allegro_pimd_get_state": ([_vp, _vp, _vp], ctypes.c_int),
         "allegro_md_get_state": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_i64)], ctypes.c_int),
         "allegro_query": ([_vp, _i32, ctypes.POINTER(_i64)], ctypes.c_int),
         "allegro_phase_times": ([_vp, _i32, _vp, _i32], ctypes.c_int),
@@ -270,6 +274,22 @@ def allegro_md_get_thermostat(ctx):
     out = np.zeros(2, dtype=np.float64)
     _check(ctx, lib().allegro_md_get_thermostat(ctx, _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def allegro_pimd_init(ctx, positions, velocities, species, cell, temperature_K):
+    """positions, velocities: (P, N, 3) FP64 (host or device); species (N,)."""
+    cell = _host(cell, np.float64)
+    _check(ctx, lib().allegro_pimd_init(ctx, int(positions.shape[0]), int(positions.shape[1]), _ptr(positions),
+                                        _ptr(velocities), _ptr(species), _ptr(cell), float(temperature_K)))
+
+
+def allegro_pimd_step(ctx, dt_fs, n_steps, energies=None):
+    """energies: (n_steps, 3) FP64 (mean replica energy, kinetic, H_P) or None."""
+    _check(ctx, lib().allegro_pimd_step(ctx, float(dt_fs), int(n_steps), _ptr(energies)))
+
+
+def allegro_pimd_get_state(ctx, positions=None, velocities=None):
+    _check(ctx, lib().allegro_pimd_get_state(ctx, _ptr(positions), _ptr(velocities)))
 
 
 def allegro_md_get_state(ctx, positions=None, velocities=None, forces=None):

@@ -213,6 +213,19 @@ struct allegro_ctx {
   double* d_nh_snap = nullptr;
   cudaGraphExec_t graph_nvt = nullptr;
   double nvt_key[3] = {0.0, 0.0, 0.0};   // dt, T, tau of graph_nvt
+  // ring-polymer MD: P replicas of rp_n atoms (bead-major positions and
+  // velocities, FP64), the normal-mode matrix and frequencies
+  int rp_P = 0;
+  int64_t rp_n = 0;
+  double rp_T = 0.0;
+  double rp_cell[9] = {};
+  bool rp_ready = false;
+  double* d_rp_q = nullptr;
+  double* d_rp_v = nullptr;
+  int* d_rp_species = nullptr;
+  double* d_rp_C = nullptr;
+  double* d_rp_w = nullptr;
+  double* d_rp_blk = nullptr;
   // rollback snapshot
   double* d_pos_snap = nullptr;
   double* d_v_snap = nullptr;
@@ -1459,6 +1472,181 @@ int allegro_md_get_thermostat(allegro_ctx* ctx, double* xi_eta) {
   if (rc) return rc;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "thermostat state");
   return ALLEGRO_OK;
+}
+
+namespace {
+
+// Energies and forces of every replica in one pass sequence: each replica's
+// neighbour list is built with the common box and appended (atom offset k n)
+// to one list, then the pair passes of the context's MD precision run once
+// over all replicas.  Leaves F (P n x 3) in d_F and stats[0] = sum of the
+// replica energies.
+int rp_forces(allegro_ctx* c) {
+  const int P = c->rp_P;
+  const int64_t n = c->rp_n, PN = (int64_t)P * n;
+  TrainBatch& t = c->bt;
+  int rc = bt_reserve(c, PN, std::max<int64_t>(t.cap_pairs, 64 * PN), P, 0, 0);
+  if (rc) return rc;
+  int64_t P0 = 0;
+  double L[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < P && !rc; ++k) {
+    rc = prepare(c, n, c->d_rp_q + 3 * n * k, c->d_rp_species, c->rp_cell, L);
+    int64_t np = 0;
+    if (!rc) rc = build_with_growth(c, c->d_pos, n, &np);
+    if (!rc) rc = bt_reserve(c, PN, P0 + np, P, PN, P0);
+    if (!rc)
+      launch_append(t.a, (int)n, (int)np, (int64_t)k * n, P0, k, c->nb.pi, c->nb.pj, c->nb.pcode, c->nb.rev,
+                    c->nb.row_ptr, c->nb.wpos, c->d_species, L, c->stream);
+    P0 += np;
+  }
+  if (rc) return rc;
+  if (P0 > 0x7ffffff0) return c->fail(ALLEGRO_E_UNSUPPORTED, "more than 2^31 pairs over the replicas");
+  t.n_structs = P;
+  t.n_atoms = PN;
+  t.n_pairs = P0;
+  const int np32 = (int)P0;
+  cudaMemcpyAsync(t.d_np, &np32, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  rc = ensure_pairs(c, std::max<int64_t>(P0, c->capacity));
+  if (rc) return rc;
+  const int prec = c->md_precision;
+  if (prec != ALLEGRO_FP32) {
+    rc = refresh_tc(c);
+    if (rc) return rc;
+  }
+  fill_batch_passbufs(c, t.a.wpos);
+  for (int a = 0; a < 3; ++a) c->pb.L[a] = L[a];      // one box for every replica
+  cudaStream_t s = c->stream;
+  int tile;
+  if (prec == ALLEGRO_FP32) {
+    fp32_energy_forces((int)c->blob.lmax, (int)c->blob.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+    tile = fp32_tile();
+  } else {
+    const TcMode mode = prec == ALLEGRO_BF16 ? TcMode::kBf16 : prec == ALLEGRO_FP16 ? TcMode::kFp16 : TcMode::kFp16Split;
+    bf16_energy_forces(prec == ALLEGRO_BF16 ? c->bw : prec == ALLEGRO_FP16 ? c->hw : c->sw, c->pb, c->capacity, s,
+                       nullptr, mode);
+    tile = bf16_tile();
+  }
+  AtomArgs aa = atom_args(c);
+  aa.n = (int)PN;
+  aa.species = t.a.species;
+  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, tile, c->d_F, c->d_Ei, c->d_blk, c->d_stats,
+                c->nb.flags, s);
+  c->pb.atomL = nullptr;
+  int flags = 0;
+  cudaMemcpyAsync(&flags, c->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "replica forces");
+  if (flags & kFlagPairOverflow) return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "replica pairs exceed the capacity");
+  if (flags & kFlagNonfinite) return c->fail(ALLEGRO_E_NONFINITE, "non-finite energy or force in a replica");
+  return ALLEGRO_OK;
+}
+
+AtomArgs rp_atom_args(allegro_ctx* c) {
+  AtomArgs a = atom_args(c);
+  a.n = (int)c->rp_n;
+  a.species = c->d_rp_species;
+  return a;
+}
+
+}  // namespace
+
+int allegro_pimd_init(allegro_ctx* ctx, int32_t n_beads, int64_t n_atoms, const double* positions,
+                      const double* velocities, const int32_t* species, const double* cell, double temperature_K) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  if (n_beads < 1 || n_beads > kMaxBeads) return ctx->fail(ALLEGRO_E_INVALID_ARG, "n_beads must be in [1, 64]");
+  if (n_atoms < 1 || (int64_t)n_beads * n_atoms > (1 << 30))
+    return ctx->fail(ALLEGRO_E_INVALID_ARG, "n_atoms out of range");
+  if (!positions || !velocities || !species || !cell)
+    return ctx->fail(ALLEGRO_E_INVALID_ARG, "positions, velocities, species and cell are required");
+  if (!(temperature_K > 0.0) || !std::isfinite(temperature_K))
+    return ctx->fail(ALLEGRO_E_INVALID_ARG, "temperature must be positive");
+  ctx->md_ready = false;
+  ctx->rp_ready = false;
+  ctx->drop_graphs();
+  const int P = n_beads;
+  const int64_t PN = (int64_t)P * n_atoms;
+  for (void* p : {(void*)ctx->d_rp_q, (void*)ctx->d_rp_v, (void*)ctx->d_rp_species, (void*)ctx->d_rp_C,
+                  (void*)ctx->d_rp_w, (void*)ctx->d_rp_blk})
+    ctx->dfree(p);
+  ctx->d_rp_q = ctx->dalloc<double>(3 * (size_t)PN);
+  ctx->d_rp_v = ctx->dalloc<double>(3 * (size_t)PN);
+  ctx->d_rp_species = ctx->dalloc<int>((size_t)n_atoms);
+  ctx->d_rp_C = ctx->dalloc<double>((size_t)P * P);
+  ctx->d_rp_w = ctx->dalloc<double>((size_t)P);
+  ctx->d_rp_blk = ctx->dalloc<double>(2 * ((size_t)PN / 256 + 2));
+  if (!ctx->d_rp_q || !ctx->d_rp_v || !ctx->d_rp_species || !ctx->d_rp_C || !ctx->d_rp_w || !ctx->d_rp_blk)
+    return ctx->fail(ALLEGRO_E_OOM, "replica allocation failed");
+  const cudaMemcpyKind kq = is_device_ptr(positions) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kv = is_device_ptr(velocities) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind ks = is_device_ptr(species) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(ctx->d_rp_q, positions, sizeof(double) * 3 * PN, kq, ctx->stream);
+  cudaMemcpyAsync(ctx->d_rp_v, velocities, sizeof(double) * 3 * PN, kv, ctx->stream);
+  cudaMemcpyAsync(ctx->d_rp_species, species, sizeof(int) * n_atoms, ks, ctx->stream);
+  // normal modes of the ring: C[j P + k], frequencies omega_k = 2 omega_P sin(k' pi / P)
+  const double wp = P * kBoltzmannEv * temperature_K / kHbarEvFs;
+  std::vector<double> C((size_t)P * P), w(P);
+  for (int k = 0; k < P; ++k) {
+    for (int j = 0; j < P; ++j) {
+      double c;
+      if (k == 0) c = 1.0 / std::sqrt((double)P);
+      else if (2 * k < P) c = std::sqrt(2.0 / P) * std::cos(2.0 * M_PI * j * k / P);
+      else if (2 * k == P) c = ((j & 1) ? -1.0 : 1.0) / std::sqrt((double)P);
+      else c = std::sqrt(2.0 / P) * std::sin(2.0 * M_PI * j * k / P);
+      C[(size_t)j * P + k] = c;
+    }
+    const int kk = 2 * k <= P ? k : P - k;
+    w[k] = 2.0 * wp * std::sin(kk * M_PI / P);
+  }
+  cudaMemcpyAsync(ctx->d_rp_C, C.data(), sizeof(double) * P * P, cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(ctx->d_rp_w, w.data(), sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream);
+  for (int i = 0; i < 9; ++i) ctx->rp_cell[i] = cell[i];
+  ctx->rp_P = P;
+  ctx->rp_n = n_atoms;
+  ctx->rp_T = temperature_K;
+  int rc = ensure_atoms(ctx, PN, 0);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "pimd_init");
+  if (!rc) rc = rp_forces(ctx);                      // checks the cell, species and capacity once
+  if (rc) return rc;
+  ctx->rp_ready = true;
+  return ALLEGRO_OK;
+}
+
+int allegro_pimd_step(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double* energies) {
+  if (!ctx || !ctx->rp_ready) return ctx ? ctx->fail(ALLEGRO_E_INVALID_ARG, "pimd_init first") : ALLEGRO_E_INVALID_ARG;
+  if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "bad dt or n_steps");
+  if (n_steps == 0) return ALLEGRO_OK;
+  int rc = ensure_records(ctx, n_steps);
+  if (rc) return rc;
+  const int P = ctx->rp_P;
+  const double wp = P * kBoltzmannEv * ctx->rp_T / kHbarEvFs;
+  rc = rp_forces(ctx);                               // forces of the current replicas
+  if (rc) return rc;
+  cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream);
+  for (int s = 0; s < n_steps && !rc; ++s) {
+    const AtomArgs a = rp_atom_args(ctx);
+    launch_rp_kick(P, a, ctx->d_rp_v, ctx->d_F, 0.5 * dt_fs, ctx->stream);
+    launch_rp_free(P, (int)ctx->rp_n, ctx->d_rp_q, ctx->d_rp_v, ctx->d_rp_C, ctx->d_rp_w, dt_fs, ctx->stream);
+    rc = rp_forces(ctx);
+    if (rc) break;
+    launch_rp_kick(P, a, ctx->d_rp_v, ctx->d_F, 0.5 * dt_fs, ctx->stream);
+    launch_rp_record(P, a, ctx->d_rp_q, ctx->d_rp_v, wp, ctx->d_rp_blk, ctx->d_stats, ctx->d_step, ctx->rec_cap,
+                     ctx->d_e_rec, ctx->stream);
+  }
+  if (rc) {
+    ctx->rp_ready = false;                           // the replicas are mid-step
+    return rc;
+  }
+  rc = copy_out(ctx, energies, ctx->d_e_rec, sizeof(double) * 3 * n_steps);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "pimd steps");
+  return rc;
+}
+
+int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velocities) {
+  if (!ctx || !ctx->rp_ready) return ctx ? ctx->fail(ALLEGRO_E_INVALID_ARG, "pimd_init first") : ALLEGRO_E_INVALID_ARG;
+  const size_t bytes = sizeof(double) * 3 * (size_t)ctx->rp_P * (size_t)ctx->rp_n;
+  int rc = copy_out(ctx, positions, ctx->d_rp_q, bytes);
+  if (!rc) rc = copy_out(ctx, velocities, ctx->d_rp_v, bytes);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "pimd state");
+  return rc;
 }
 
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {

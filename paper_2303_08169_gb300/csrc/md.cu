@@ -264,7 +264,122 @@ __global__ void k_record_nh(const double* __restrict__ stats, const unsigned lon
   *step = s + 1;
 }
 
+// ---- ring-polymer MD (Sec. 6): P replicas of n atoms, bead-major arrays
+// x[(k n + i) 3 + a]; C[j P + k] the orthogonal normal-mode matrix, w[k] the
+// mode frequencies (1/fs) ----
+
+// exact free ring-polymer evolution for dt, one thread per (atom, component)
+__global__ void __launch_bounds__(kBlock)
+k_rp_free(int P, int n, double* __restrict__ q, double* __restrict__ v, const double* __restrict__ C,
+          const double* __restrict__ w, double dt) {
+  const int t = blockIdx.x * kBlock + threadIdx.x;
+  if (t >= 3 * n) return;
+  double x[kMaxBeads], y[kMaxBeads], qm[kMaxBeads], vm[kMaxBeads];
+  for (int j = 0; j < P; ++j) {
+    x[j] = q[(size_t)j * 3 * n + t];
+    y[j] = v[(size_t)j * 3 * n + t];
+  }
+  for (int k = 0; k < P; ++k) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < P; ++j) {
+      a = fma(C[j * P + k], x[j], a);
+      b = fma(C[j * P + k], y[j], b);
+    }
+    const double om = w[k];
+    if (om == 0.0) {
+      qm[k] = a + dt * b;
+      vm[k] = b;
+    } else {
+      const double c = cos(om * dt), s = sin(om * dt);
+      qm[k] = c * a + (s / om) * b;
+      vm[k] = -om * s * a + c * b;
+    }
+  }
+  for (int j = 0; j < P; ++j) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < P; ++k) {
+      a = fma(C[j * P + k], qm[k], a);
+      b = fma(C[j * P + k], vm[k], b);
+    }
+    q[(size_t)j * 3 * n + t] = a;
+    v[(size_t)j * 3 * n + t] = b;
+  }
+}
+
+// v += h kappa F/m for every replica
+__global__ void __launch_bounds__(kBlock)
+k_rp_kick(int P, AtomArgs a, double* __restrict__ v, const float* __restrict__ F, double h) {
+  const int n = a.n;
+  const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;
+  if (t >= 3ll * P * n) return;
+  const int i = (int)((t / 3) % n);
+  v[t] += h * kKappa * (double)F[t] / a.mass[a.species[i]];
+}
+
+// block partials of sum m |v|^2 / 2 and sum m wp^2 |q_k - q_k+1|^2 / 2
+// (amu A^2/fs^2), one thread per (replica, atom)
+__global__ void __launch_bounds__(kBlock)
+k_rp_energy(int P, AtomArgs a, const double* __restrict__ q, const double* __restrict__ v, double wp,
+            double* __restrict__ blk) {
+  const int n = a.n;
+  __shared__ double sh[kBlock / 32];
+  const int t = blockIdx.x * kBlock + threadIdx.x;
+  double ke = 0.0, se = 0.0;
+  if (t < P * n) {
+    const int k = t / n, i = t % n, k1 = (k + 1) % P;
+    const double m = a.mass[a.species[i]];
+    for (int c = 0; c < 3; ++c) {
+      const double vv = v[(size_t)t * 3 + c];
+      const double d = q[(size_t)t * 3 + c] - q[((size_t)k1 * n + i) * 3 + c];
+      ke += 0.5 * m * vv * vv;
+      se += 0.5 * m * wp * wp * d * d;
+    }
+  }
+  const double sk = block_sum(ke, sh);
+  const double ss = block_sum(se, sh);
+  if (threadIdx.x == 0) {
+    blk[2 * blockIdx.x] = sk;
+    blk[2 * blockIdx.x + 1] = ss;
+  }
+}
+
+// energies[step] = (sum_k V_k / P, K, K + springs + sum_k V_k) in eV
+__global__ void k_rp_record(const double* __restrict__ blk, int nblk, const double* __restrict__ stats, int P,
+                            long long* __restrict__ step, int max_steps, double* __restrict__ energies) {
+  if (threadIdx.x != 0) return;
+  double k = 0.0, s = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    k += blk[2 * b];
+    s += blk[2 * b + 1];
+  }
+  k /= kKappa;
+  s /= kKappa;
+  const long long st = *step;
+  if (st >= 0 && st < max_steps) {
+    energies[3 * st] = stats[0] / P;
+    energies[3 * st + 1] = k;
+    energies[3 * st + 2] = k + s + stats[0];
+  }
+  *step = st + 1;
+}
+
 }  // namespace
+
+void launch_rp_free(int P, int n, double* q, double* v, const double* C, const double* w, double dt, cudaStream_t s) {
+  k_rp_free<<<(3 * n + kBlock - 1) / kBlock, kBlock, 0, s>>>(P, n, q, v, C, w, dt);
+}
+
+void launch_rp_kick(int P, const AtomArgs& a, double* v, const float* F, double h, cudaStream_t s) {
+  const long long tot = 3ll * P * a.n;
+  k_rp_kick<<<(unsigned)((tot + kBlock - 1) / kBlock), kBlock, 0, s>>>(P, a, v, F, h);
+}
+
+void launch_rp_record(int P, const AtomArgs& a, const double* q, const double* v, double wp, double* blk,
+                      const double* stats, long long* step, int max_steps, double* energies, cudaStream_t s) {
+  const int nb = (P * a.n + kBlock - 1) / kBlock;
+  k_rp_energy<<<nb, kBlock, 0, s>>>(P, a, q, v, wp, blk);
+  k_rp_record<<<1, 32, 0, s>>>(blk, nb, stats, P, step, max_steps, energies);
+}
 
 int atom_blocks(int n) { return (n + kBlock - 1) / kBlock; }
 

@@ -6,6 +6,8 @@ namespace al {
 
 constexpr double kKappa = 9.648533e-3;   // 1 eV/(A amu) in A/fs^2
 constexpr double kBoltzmannEv = 8.617333262e-5;   // eV/K
+constexpr double kHbarEvFs = 0.6582119569;         // reduced Planck constant, eV fs
+constexpr int kMaxBeads = 64;                      // replicas per atom in ring-polymer MD
 
 struct AtomArgs {
   int n;
@@ -47,5 +49,16 @@ void launch_nvt_second_half(const AtomArgs& a, double* v, const float* F, double
                             double thr, double gkt, double q, double* blk_ke, unsigned long long* blk_out,
                             double* nh, long long* step, int max_steps, double* energies, long long* outliers,
                             cudaStream_t s);
+
+// Ring-polymer MD (P replicas of n atoms, bead-major q, v, F):
+// exact free ring-polymer evolution for dt (C: P x P normal modes, w: mode
+// frequencies in 1/fs, both device)
+void launch_rp_free(int P, int n, double* q, double* v, const double* C, const double* w, double dt, cudaStream_t s);
+// v += h kappa F / m; a: one replica's atoms (n = a.n, species of one replica)
+void launch_rp_kick(int P, const AtomArgs& a, double* v, const float* F, double h, cudaStream_t s);
+// record (mean replica energy, kinetic energy, H_P) of the step from stats[0]
+// = sum of the replica energies; blk: 2 (P n / 256 + 1) doubles
+void launch_rp_record(int P, const AtomArgs& a, const double* q, const double* v, double wp, double* blk,
+                      const double* stats, long long* step, int max_steps, double* energies, cudaStream_t s);
 
 }  // namespace al
