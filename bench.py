@@ -411,6 +411,46 @@ class Runner:
         self.al.allegro_destroy(self.ctx)
 
 
+def lmax_sweep(al, torch, dev, K=10, W=3, n_mol=27648):
+    """Time per MD step (E+F, FP32 passes, graph-captured NVE step) of the
+    main model's widths at l_max 0, 1 and 2 on the 110,592-atom system: the
+    shape of the paper's Table 2 (395 : 916 : 2,580 ms for l = 0 : 1 : 2 on
+    its own platform and system)."""
+    import synth
+    pos, sp, cell, vel = _system(n_mol)
+    out = {"l_max": [], "ms_per_step": [], "pairs": [], "params": []}
+    for lmax in (0, 1, 2):
+        M = synth.MAIN
+        cfg = synth.ModelConfig(r_cut=M.r_cut, l_max=lmax, n_layers=M.n_layers, n_channels=M.n_channels,
+                                latent=M.latent, energy=M.energy, avg_num_neighbors=M.avg_num_neighbors)
+        blob = synth.make_blob(cfg, 42, sigma=_energy_scale("main"))
+        run = Runner(al, torch, dev, blob, cfg)
+        al.allegro_set_md_precision(run.ctx, 0)
+        al.allegro_md_init(run.ctx, torch.tensor(pos, device=dev), torch.tensor(vel, device=dev),
+                           torch.tensor(sp, device=dev, dtype=torch.int32), cell)
+        al.allegro_md_step_nve(run.ctx, 0.25, W)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(run.stream)
+        al.allegro_md_step_nve(run.ctx, 0.25, K)
+        ev1.record(run.stream)
+        torch.cuda.synchronize()
+        out["l_max"].append(lmax)
+        out["ms_per_step"].append(ev0.elapsed_time(ev1) / K)
+        out["pairs"].append(al.allegro_query(run.ctx, al.ALLEGRO_Q_N_PAIRS))
+        out["params"].append(al.allegro_query(run.ctx, al.ALLEGRO_Q_N_PARAMS))
+        run.close()
+    t0 = out["ms_per_step"][0]
+    out["ratio_to_l0"] = [t / t0 for t in out["ms_per_step"]]
+    out["paper_ratio_to_l0"] = [1.0, 916.0 / 395.0, 2580.0 / 395.0]
+    out["atoms"] = len(sp)
+    out["steps"] = K
+    out["note"] = ("FP32 pair passes (the tensor-core path is built for l_max 2 only); main model widths "
+                   "(16 channels, latent [128, 128]), 2 layers")
+    return out
+
+
 def sam_timing(al, torch, steps=5, n_sharp=64):
     """SAM training step (Eq. 3) on 32 seeded ammonia structures of 64-512
     atoms; targets from a teacher model (weights seed 43) evaluated by the
@@ -560,6 +600,7 @@ def run_ours(args):
                 "note": "allegro_pimd_step: all replicas' energies and forces in one pass sequence per step, "
                         "normal-mode spring propagation; the call's first force evaluation is inside the timing"}
         sam = sam_timing(al, torch)
+        lsweep = lmax_sweep(al, torch, dev)
         if args.config != SCALE and not args.no_scale:
             big = Runner(al, torch, dev, blob, cfg)
             r = big.md(SCALE, min(K, 200), W)
@@ -583,6 +624,7 @@ def run_ours(args):
         sam = None
         nvt = None
         pimd = None
+        lsweep = None
     run.close()
     if rank != 0:
         if dist:
@@ -626,6 +668,8 @@ def run_ours(args):
         line["nvt"] = nvt
     if pimd:
         line["pimd"] = pimd
+    if lsweep:
+        line["lmax_sweep"] = lsweep
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -75,7 +75,9 @@ const char* allegro_version(void);
  *  r_cut, l_max, n_layers   : must equal the blob header (else E_MISMATCH).
  * Supported model shapes (E_UNSUPPORTED otherwise): two species, 8 Bessel
  * functions, envelope p = 6, two latent hidden widths D = D, one energy
- * hidden width, and (l_max, C, D, E) in {(1, 8, 32, 32), (2, 16, 128, 32)}.
+ * hidden width, and (l_max, C, D, E) in {(1, 8, 32, 32), (0, 16, 128, 32),
+ * (1, 16, 128, 32), (2, 16, 128, 32)} (the last three: the l_max sweep of
+ * Table 2 at one width; the tensor-core precisions need l_max 2).
  * The paper defines only the pairwise-energy decomposition and equivariance
  * (Sec. 2.1); the layer structure follows the Allegro reading stated in the
  * oracle package.

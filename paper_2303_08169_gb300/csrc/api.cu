@@ -796,12 +796,18 @@ const WInfo* winfo(allegro_ctx* c, const std::string& name) {
   return nullptr;
 }
 
+// tensor-product table sizes of the model's l_max (0, 1 or 2)
+int tp_ns(int lmax) { return lmax == 0 ? TP0_NS : lmax == 1 ? TP1_NS : TP2_NS; }
+int tp_nt(int lmax) { return lmax == 0 ? TP0_NT : lmax == 1 ? TP1_NT : TP2_NT; }
+int tp_pl(int lmax, int l) { return lmax == 0 ? tp0_P(l) : lmax == 1 ? tp1_P(l) : tp2_P(l); }
+int tp_toff(int lmax, int l) { return lmax == 0 ? tp0_toff(l) : lmax == 1 ? tp1_toff(l) : tp2_toff(l); }
+
 int ensure_train(allegro_ctx* c) {
   const int64_t cap = c->capacity;
   if (cap <= c->tr_cap) return ALLEGRO_OK;
   const Blob& B = c->blob;
   const int D = c->D, C = (int)B.C, E = c->E, L = (int)B.L;
-  const int NS = B.lmax == 1 ? TP1_NS : TP2_NS, NT = B.lmax == 1 ? TP1_NT : TP2_NT;
+  const int NS = tp_ns((int)B.lmax), NT = tp_nt((int)B.lmax);
   const int NW0 = C * ((int)B.lmax + 1);
   TrainBufs& t = c->tr;
   auto re = [&](float*& p, size_t w) {
@@ -825,7 +831,7 @@ int ensure_train(allegro_ctx* c) {
 int reduce_wgrad(allegro_ctx* c, int P) {
   const Blob& B = c->blob;
   const int D = c->D, C = (int)B.C, E = c->E, Lz = (int)B.L;
-  const int NS = B.lmax == 1 ? TP1_NS : TP2_NS, NT = B.lmax == 1 ? TP1_NT : TP2_NT;
+  const int NS = tp_ns((int)B.lmax), NT = tp_nt((int)B.lmax);
   const int NLM = ((int)B.lmax + 1) * ((int)B.lmax + 1), NW0 = C * ((int)B.lmax + 1), KH = D + C * NS;
   const TrainBufs& t = c->tr;
   cudaStream_t s = c->stream;
@@ -846,7 +852,7 @@ int reduce_wgrad(allegro_ctx* c, int P) {
     launch_wgrad(t.dz2_l[k], D, t.a1_l[k], D, P, D, D, isD, g(pre + "latent.1"), D, 0, s);
     if (k < Lz)
       for (int l = 0; l <= (int)B.lmax; ++l) {
-        const int Pl = B.lmax == 1 ? tp1_P(l) : tp2_P(l), toff = B.lmax == 1 ? tp1_toff(l) : tp2_toff(l);
+        const int Pl = tp_pl((int)B.lmax, l), toff = tp_toff((int)B.lmax, l);
         launch_wgrad_mix(c->pb.dV, t.T[k], P, C, NLM, NT, l, Pl, toff, 1.0f / std::sqrt((float)(C * Pl)),
                          g(pre + "mix" + std::to_string(l)), s);
       }

@@ -241,6 +241,7 @@ int main(int argc, char** argv) {
   FILE* f = std::fopen(argv[1], "w");
   if (!f) return 1;
   std::fprintf(f, "// Generated by gen_tp.cpp at build time; do not edit.\n#pragma once\n");
+  emit(f, 0);
   emit(f, 1);
   emit(f, 2);
   std::fclose(f);

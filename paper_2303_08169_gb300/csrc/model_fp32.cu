@@ -67,6 +67,15 @@ AL_DEV void load_chunk(float* wbuf, const float* __restrict__ Wt, int ch) {
 
 
 template <int LMAX> struct TP;
+template <> struct TP<0> {
+  static constexpr int NT = TP0_NT, NS = TP0_NS;
+  static AL_DEV void fwd(const float* V, const float* G, float* T) { tp0_fwd(V, G, T); }
+  static AL_DEV void fwd_s(const float* V, const float* G, float* T) { tp0_fwd_scalar(V, G, T); }
+  static AL_DEV void bwd(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp0_bwd(V, G, dT, dV, dG); }
+  static AL_DEV void bwd_s(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp0_bwd_scalar(V, G, dT, dV, dG); }
+  static constexpr AL_DEV int P(int l) { return tp0_P(l); }
+  static constexpr AL_DEV int toff(int l) { return tp0_toff(l); }
+};
 template <> struct TP<1> {
   static constexpr int NT = TP1_NT, NS = TP1_NS;
   static AL_DEV void fwd(const float* V, const float* G, float* T) { tp1_fwd(V, G, T); }
@@ -99,7 +108,7 @@ struct Cfg {
   static constexpr int LDH = KH + 4;
   static constexpr int LDE = E + 4;
   static constexpr int WB = 2 * kKC * (KH > D ? KH : D);   // weight staging ring
-  static constexpr int MIXW = C * C * (LMAX == 1 ? 4 : 11); // all mixing matrices
+  static constexpr int MIXW = C * C * (TP<LMAX>::P(0) + TP<LMAX>::P(1) + TP<LMAX>::P(2));  // all mixing matrices
 };
 
 AL_DEV int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
@@ -1068,18 +1077,23 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
 
 using CfgTiny = Cfg<1, 8, 32, 32>;
 using CfgMain = Cfg<2, 16, 128, 32>;
+// the main model's widths at l_max 0 and 1 (the l_max sweep of Table 2)
+using CfgMainL0 = Cfg<0, 16, 128, 32>;
+using CfgMainL1 = Cfg<1, 16, 128, 32>;
 
 }  // namespace
 
 int fp32_tile() { return kTile; }
 
 bool fp32_supported(int lmax, int C, int D, int E) {
-  return (lmax == 1 && C == 8 && D == 32 && E == 32) || (lmax == 2 && C == 16 && D == 128 && E == 32);
+  return (lmax == 1 && C == 8 && D == 32 && E == 32) || (lmax <= 2 && C == 16 && D == 128 && E == 32);
 }
 
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
                         int64_t capacity, cudaStream_t s, KernelMarks* km) {
   if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s, km);
+  else if (lmax == 0) run<CfgMainL0>(w, b, capacity, s, km);
+  else if (lmax == 1) run<CfgMainL1>(w, b, capacity, s, km);
   else run<CfgMain>(w, b, capacity, s, km);
 }
 

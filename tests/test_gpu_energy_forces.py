@@ -82,6 +82,25 @@ def test_main_small_systems(main, n_mol, seed):
     _compare(E, F, Ei, Er, Fr, Eir)
 
 
+@pytest.mark.parametrize("l_max", [0, 1])
+@pytest.mark.parametrize("n_mol,seed", [(108, 5), (250, 9)])
+def test_lmax_sweep_models(l_max, n_mol, seed):
+    """The main model's widths at l_max 0 and 1 (Table 2's l_max sweep):
+    432 and 1,000 atoms against the oracle of the same model."""
+    cfg = synth.ModelConfig(r_cut=synth.MAIN.r_cut, l_max=l_max, n_layers=synth.MAIN.n_layers,
+                            n_channels=synth.MAIN.n_channels, latent=synth.MAIN.latent,
+                            energy=synth.MAIN.energy, avg_num_neighbors=synth.MAIN.avg_num_neighbors)
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(n_mol, seed)
+    E, F, Ei = _gpu(ctx, pos, sp, cell)
+    Er, Fr, Eir, _ = OracleModel(blob).energy_forces(pos, sp, np.diag(cell))
+    _compare(E, F, Ei, Er, Fr, Eir)
+    with pytest.raises(al.AllegroError):
+        al.allegro_set_md_precision(ctx, al.ALLEGRO_FP16_SPLIT)
+    al.allegro_destroy(ctx)
+
+
 def test_main_6912(main):
     ctx, orc = main
     pos, sp, cell = synth.make_ammonia(1728, 0)

@@ -76,7 +76,14 @@ def dimer_energy(cfg, W, d, sA, sB):
             + cfg.sigma[sB] * pair(sB, sA) + cfg.mu[sB])
 
 
-@pytest.mark.parametrize("cfg", [MINI, synth.TINY.with_sigma(1.7)], ids=["mini_l2_2layers", "tiny"])
+MINI_L0 = synth.ModelConfig(r_cut=4.5, l_max=0, n_layers=2, n_channels=4, latent=(8, 8), energy=(8,),
+                            avg_num_neighbors=7.0, sigma=(1.3, 0.7), mu=(0.25, -0.5))
+MINI_L1 = synth.ModelConfig(r_cut=4.5, l_max=1, n_layers=3, n_channels=4, latent=(8, 8), energy=(8,),
+                            avg_num_neighbors=7.0, sigma=(1.3, 0.7), mu=(0.25, -0.5))
+
+
+@pytest.mark.parametrize("cfg", [MINI, MINI_L0, MINI_L1, synth.TINY.with_sigma(1.7)],
+                         ids=["mini_l2_2layers", "mini_l0_2layers", "mini_l1_3layers", "tiny"])
 def test_dimer_closed_form(cfg):
     W = synth.make_weights(cfg, 11)
     model = OracleModel(synth.write_blob(cfg, W))
@@ -104,8 +111,9 @@ def _rot(rng):
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
 
 
-def test_o3_invariance_and_force_covariance():
-    model = OracleModel(synth.make_blob(MINI, 5))
+@pytest.mark.parametrize("cfg", [MINI, MINI_L1], ids=["l2", "l1"])
+def test_o3_invariance_and_force_covariance(cfg):
+    model = OracleModel(synth.make_blob(cfg, 5))
     pos, sp = _cluster()
     E0, F0, _, _ = model.energy_forces(pos, sp, BIG)
     rng = np.random.default_rng(1)
