@@ -369,6 +369,7 @@ class Runner:
         N = n_beads * len(sp)
         return {"ms": ev0.elapsed_time(ev1), "N": N, "K": K, "beads": n_beads, "atoms_per_replica": len(sp),
                 "n_pairs": al.allegro_query(self.ctx, al.ALLEGRO_Q_N_PAIRS),
+                "step_kernels": al.allegro_query(self.ctx, al.ALLEGRO_Q_RP_STEP_KERNELS),
                 "HP_drift_over_NkT": float(np.abs(en[:, 2] - en[0, 2]).max() / (N * KB_T200))}
 
     def phases(self, n_reps=20):
@@ -596,9 +597,11 @@ def run_ours(args):
         pimd = {"workload": f"{rp['beads']} replicas x {rp['atoms_per_replica']} atoms ({rp['N']} bead-atoms)",
                 "value": rp["N"] * rp["K"] / (rp["ms"] * 1e-3), "unit": "bead-atom-steps/s",
                 "ms_per_step": rp["ms"] / rp["K"], "steps": rp["K"], "temperature_K": 200.0,
-                "HP_drift_over_NkT": rp["HP_drift_over_NkT"],
-                "note": "allegro_pimd_step: all replicas' energies and forces in one pass sequence per step, "
-                        "normal-mode spring propagation; the call's first force evaluation is inside the timing"}
+                "HP_drift_over_NkT": rp["HP_drift_over_NkT"], "pairs": rp["n_pairs"],
+                "gpu_launches": int(rp["step_kernels"] * rp["K"]),
+                "note": "allegro_pimd_step: one CUDA graph per step (kicks, exact normal-mode spring "
+                        "propagation, one neighbour build over all replicas, one pass sequence over all "
+                        "replicas, record)"}
         sam = sam_timing(al, torch)
         lsweep = lmax_sweep(al, torch, dev)
         if args.config != SCALE and not args.no_scale:

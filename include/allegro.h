@@ -135,7 +135,9 @@ int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col,
  *                 unless l_max = 2, C = 16, D = 128, E = 32, at least two
  *                 layers).
  * On ALLEGRO_E_PAIR_OVERFLOW nothing is written; the context has grown and
- * the call may simply be repeated.
+ * the call may simply be repeated.  The call reuses the MD state's buffers:
+ * allegro_md_init again before the next allegro_md_step_* (which otherwise
+ * returns ALLEGRO_E_INVALID_ARG).  The ring-polymer state is kept.
  */
 int allegro_energy_forces(allegro_ctx* ctx, int64_t n_atoms,
                           const double* positions, const int32_t* species,
@@ -315,26 +317,31 @@ int allegro_md_get_thermostat(allegro_ctx* ctx, double* xi_eta);
  * The paper states neither the equations nor the integrator; this is the
  * standard form, integrated by velocity Verlet with the spring part solved
  * exactly in the normal modes of the ring (frequencies 2 omega_P sin(k pi / P)).
- * The energies and forces of all P replicas come from ONE pass sequence over
- * the concatenated neighbour lists (each replica's list built with the common
- * box), in the precision set by allegro_set_md_precision.
+ * The energies and forces of all P replicas come from ONE neighbour build and
+ * ONE pass sequence over all P n atoms, in the precision set by
+ * allegro_set_md_precision.
  *
  * allegro_pimd_init: n_beads in [1, 64], n_atoms >= 1; positions and
  * velocities host or device FP64[n_beads x n_atoms x 3], replica-major
  * (replica k's atom i at (k n_atoms + i) x 3), in A and A/fs; species host or
  * device int32[n_atoms] (shared by the replicas); cell host FP64[9]
  * (orthorhombic, as allegro_build_neighbors); temperature_K > 0.  Bead
- * positions are not wrapped (each replica's neighbour build wraps them), so
- * the springs are plain differences.  Evaluates the forces once; copies the
- * inputs.  Replaces the single-system MD state (allegro_md_init again before
- * allegro_md_step_*).
+ * positions are not wrapped (the neighbour build wraps them), so the springs
+ * are plain differences.  Evaluates the forces once; copies the inputs.  The
+ * ring state (positions, velocities, forces) lives in its own arrays and
+ * survives other calls; allegro_pimd_init and allegro_pimd_step end the
+ * single-system MD state (allegro_md_init again before allegro_md_step_*).
  *
- * allegro_pimd_step: n_steps >= 0 steps of dt_fs > 0:
+ * allegro_pimd_step: n_steps >= 0 steps of dt_fs > 0 (one captured CUDA
+ * graph per step: one neighbour build for all replicas, each replica its own
+ * system in the common box, then the pair passes over all replicas):
  *   v += dt/2 F/m;  free ring evolution for dt;  F <- F(q);  v += dt/2 F/m,
  * energies: host or device FP64[n_steps x 3] or NULL: (mean replica energy
  * sum_k V(q_k) / P, kinetic energy of all replicas, H_P) in eV after each
- * step.  ALLEGRO_E_NONFINITE, ALLEGRO_E_PAIR_OVERFLOW as allegro_md_step_nve;
- * after an error the ring state is undefined (allegro_pimd_init again).
+ * step.  Pair-capacity overflow rolls the ring back to the start of the
+ * call, grows the context and repeats (ALLEGRO_E_PAIR_OVERFLOW only if growth
+ * fails); after ALLEGRO_E_NONFINITE the ring state is undefined
+ * (allegro_pimd_init again).
  *
  * allegro_pimd_get_state: positions, velocities host or device
  * FP64[n_beads x n_atoms x 3] (either may be NULL).
@@ -350,6 +357,7 @@ int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velociti
 #define ALLEGRO_Q_STEP_KERNELS 2  /* kernel launches in one captured MD step     */
 #define ALLEGRO_Q_N_ATOMS      3  /* atoms of the current state                  */
 #define ALLEGRO_Q_N_PARAMS     4  /* trainable parameters (weights vector length) */
+#define ALLEGRO_Q_RP_STEP_KERNELS 5  /* kernel launches in one ring-polymer step */
 
 /* Read one integer property of the context into *value (host). */
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);

@@ -213,19 +213,30 @@ struct allegro_ctx {
   double* d_nh_snap = nullptr;
   cudaGraphExec_t graph_nvt = nullptr;
   double nvt_key[3] = {0.0, 0.0, 0.0};   // dt, T, tau of graph_nvt
-  // ring-polymer MD: P replicas of rp_n atoms (bead-major positions and
-  // velocities, FP64), the normal-mode matrix and frequencies
+  // ring-polymer MD: P replicas of rp_n atoms in one box (bead-major
+  // positions, velocities and forces, own arrays so that other calls leave
+  // the ring state intact), the normal-mode matrix and frequencies, species
+  // per replica and tiled over all replicas, and the ring's step graph
   int rp_P = 0;
   int64_t rp_n = 0;
   double rp_T = 0.0;
-  double rp_cell[9] = {};
+  double rp_L[3] = {0.0, 0.0, 0.0};
+  GridInfo rp_grid{};
   bool rp_ready = false;
   double* d_rp_q = nullptr;
   double* d_rp_v = nullptr;
+  float* d_rp_F = nullptr;
+  double* d_rp_q_snap = nullptr;
+  double* d_rp_v_snap = nullptr;
+  float* d_rp_F_snap = nullptr;
   int* d_rp_species = nullptr;
+  int* d_rp_species_all = nullptr;
   double* d_rp_C = nullptr;
   double* d_rp_w = nullptr;
   double* d_rp_blk = nullptr;
+  cudaGraphExec_t graph_rp = nullptr;
+  double rp_graph_dt = 0.0;
+  int64_t rp_graph_kernels = 0;
   // rollback snapshot
   double* d_pos_snap = nullptr;
   double* d_v_snap = nullptr;
@@ -257,12 +268,15 @@ struct allegro_ctx {
   void drop_graphs() {
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_nvt) cudaGraphExecDestroy(graph_nvt);
+    if (graph_rp) cudaGraphExecDestroy(graph_rp);
     graph = nullptr;
     graph_nvt = nullptr;
+    graph_rp = nullptr;
   }
   ~allegro_ctx() {
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_nvt) cudaGraphExecDestroy(graph_nvt);
+    if (graph_rp) cudaGraphExecDestroy(graph_rp);
     for (void* p : allocs)
       if (p) cudaFree(p);
   }
@@ -483,6 +497,7 @@ int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
       return c->fail(ALLEGRO_E_OOM, "per-atom allocation failed");
     c->n_atoms_alloc = na;
     c->part_rows = 0;   // partial buffers depend on N
+    c->drop_graphs();   // the step graphs hold the old per-atom buffers
   }
   if (!c->d_stats) {
     c->d_stats = c->dalloc<double>(8);
@@ -503,6 +518,7 @@ int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
     c->nb.cell_start = c->dalloc<int>(ncell + 2);
     if (!c->nb.cell_count || !c->nb.cell_start) return c->fail(ALLEGRO_E_OOM, "cell allocation failed");
     c->ncell_alloc = ncell + 2;
+    c->drop_graphs();
   }
   return ALLEGRO_OK;
 }
@@ -658,6 +674,7 @@ int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* s
   if (!positions) return c->fail(ALLEGRO_E_INVALID_ARG, "positions is NULL");
   int rc = check_cell(c, cell, L);
   if (rc) return rc;
+  c->md_ready = false;   // the per-atom buffers now hold this call's system
   c->grid = plan_grid(L, c->blob.rc);
   const int ncell = c->grid.ncell[0] > 0 ? c->grid.ncell[0] * c->grid.ncell[1] * c->grid.ncell[2] : 0;
   rc = ensure_atoms(c, n, ncell);
@@ -1216,10 +1233,7 @@ int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
   if (!ctx || !valid_precision(precision)) return ALLEGRO_E_INVALID_ARG;
   if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
     return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
-  if (precision != ctx->md_precision && ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  if (precision != ctx->md_precision) ctx->drop_graphs();
   ctx->md_precision = precision;
   return ALLEGRO_OK;
 }
@@ -1482,47 +1496,21 @@ int allegro_md_get_thermostat(allegro_ctx* ctx, double* xi_eta) {
 
 namespace {
 
-// Energies and forces of every replica in one pass sequence: each replica's
-// neighbour list is built with the common box and appended (atom offset k n)
-// to one list, then the pair passes of the context's MD precision run once
-// over all replicas.  Leaves F (P n x 3) in d_F and stats[0] = sum of the
-// replica energies.
-int rp_forces(allegro_ctx* c) {
-  const int P = c->rp_P;
-  const int64_t n = c->rp_n, PN = (int64_t)P * n;
-  TrainBatch& t = c->bt;
-  int rc = bt_reserve(c, PN, std::max<int64_t>(t.cap_pairs, 64 * PN), P, 0, 0);
-  if (rc) return rc;
-  int64_t P0 = 0;
-  double L[3] = {0.0, 0.0, 0.0};
-  for (int k = 0; k < P && !rc; ++k) {
-    rc = prepare(c, n, c->d_rp_q + 3 * n * k, c->d_rp_species, c->rp_cell, L);
-    int64_t np = 0;
-    if (!rc) rc = build_with_growth(c, c->d_pos, n, &np);
-    if (!rc) rc = bt_reserve(c, PN, P0 + np, P, PN, P0);
-    if (!rc)
-      launch_append(t.a, (int)n, (int)np, (int64_t)k * n, P0, k, c->nb.pi, c->nb.pj, c->nb.pcode, c->nb.rev,
-                    c->nb.row_ptr, c->nb.wpos, c->d_species, L, c->stream);
-    P0 += np;
-  }
-  if (rc) return rc;
-  if (P0 > 0x7ffffff0) return c->fail(ALLEGRO_E_UNSUPPORTED, "more than 2^31 pairs over the replicas");
-  t.n_structs = P;
-  t.n_atoms = PN;
-  t.n_pairs = P0;
-  const int np32 = (int)P0;
-  cudaMemcpyAsync(t.d_np, &np32, sizeof(int), cudaMemcpyHostToDevice, c->stream);
-  rc = ensure_pairs(c, std::max<int64_t>(P0, c->capacity));
-  if (rc) return rc;
-  const int prec = c->md_precision;
-  if (prec != ALLEGRO_FP32) {
-    rc = refresh_tc(c);
-    if (rc) return rc;
-  }
-  fill_batch_passbufs(c, t.a.wpos);
-  for (int a = 0; a < 3; ++a) c->pb.L[a] = L[a];      // one box for every replica
-  cudaStream_t s = c->stream;
+// Energies and forces of every replica at the current bead positions, into
+// d_rp_F, with stats[0] = the sum of the replica energies.  One neighbour
+// build covers all replicas (each replica its own system in the common box),
+// then one pass sequence of the MD precision runs over all P n atoms.  Only
+// launches: usable inside a stream capture; a pair-capacity overflow raises
+// the device flag and the pass kernels skip their work.
+void rp_launch_forces(allegro_ctx* c, cudaStream_t s) {
+  const int64_t PN = (int64_t)c->rp_P * c->rp_n;
+  c->grid = c->rp_grid;
+  c->n_atoms = (int)PN;
+  launch_build_neighbors(c->nb, c->rp_grid, c->d_rp_q, (int)PN, s, (int)c->rp_n);
+  fill_passbufs(c, c->rp_L);
+  c->pb.species = c->d_rp_species_all;
   int tile;
+  const int prec = c->md_precision;
   if (prec == ALLEGRO_FP32) {
     fp32_energy_forces((int)c->blob.lmax, (int)c->blob.C, c->D, c->E, c->w, c->pb, c->capacity, s);
     tile = fp32_tile();
@@ -1534,16 +1522,9 @@ int rp_forces(allegro_ctx* c) {
   }
   AtomArgs aa = atom_args(c);
   aa.n = (int)PN;
-  aa.species = t.a.species;
-  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, tile, c->d_F, c->d_Ei, c->d_blk, c->d_stats,
+  aa.species = c->d_rp_species_all;
+  launch_forces(aa, c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, tile, c->d_rp_F, c->d_Ei, c->d_blk, c->d_stats,
                 c->nb.flags, s);
-  c->pb.atomL = nullptr;
-  int flags = 0;
-  cudaMemcpyAsync(&flags, c->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "replica forces");
-  if (flags & kFlagPairOverflow) return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "replica pairs exceed the capacity");
-  if (flags & kFlagNonfinite) return c->fail(ALLEGRO_E_NONFINITE, "non-finite energy or force in a replica");
-  return ALLEGRO_OK;
 }
 
 AtomArgs rp_atom_args(allegro_ctx* c) {
@@ -1551,6 +1532,50 @@ AtomArgs rp_atom_args(allegro_ctx* c) {
   a.n = (int)c->rp_n;
   a.species = c->d_rp_species;
   return a;
+}
+
+// the per-atom, cell and pair buffers for P n atoms in the ring's box
+int rp_reserve(allegro_ctx* c) {
+  const int64_t PN = (int64_t)c->rp_P * c->rp_n;
+  const GridInfo& g = c->rp_grid;
+  const int64_t ncell = g.ncell[0] > 0 ? (int64_t)c->rp_P * g.ncell[0] * g.ncell[1] * g.ncell[2] : 0;
+  if (ncell > std::max<int64_t>(PN, 1 << 22)) return c->fail(ALLEGRO_E_UNSUPPORTED, "too many cells for the ring");
+  int rc = ensure_atoms(c, PN, (int)ncell);
+  if (rc) return rc;
+  const double vol = c->rp_L[0] * c->rp_L[1] * c->rp_L[2];
+  const double rc3 = c->blob.rc * c->blob.rc * c->blob.rc;
+  const double est = (double)PN * (4.18879 * rc3 * (double)c->rp_n / vol) * 1.3 + 4096.0;
+  if (c->capacity < (int64_t)std::min(est, 2.0e9)) return ensure_pairs(c, (int64_t)std::min(est, 2.0e9));
+  if (c->part_rows < c->capacity / fp32_tile() + 2 + c->n_atoms_alloc) return ensure_pairs(c, c->capacity);
+  return ALLEGRO_OK;
+}
+
+// one ring-polymer step as a graph: kick, free ring evolution, neighbour
+// list and forces of all replicas, kick, record
+int capture_step_rp(allegro_ctx* c, double dt) {
+  if (c->graph_rp) {
+    cudaGraphExecDestroy(c->graph_rp);
+    c->graph_rp = nullptr;
+  }
+  cudaStream_t cs = c->stream;
+  bool own = false;
+  if (!cs) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_check(c, "stream");
+    own = true;
+  }
+  const int P = c->rp_P;
+  const double wp = P * kBoltzmannEv * c->rp_T / kHbarEvFs;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_check(c, "capture");
+  const AtomArgs a = rp_atom_args(c);
+  launch_rp_kick(P, a, c->d_rp_v, c->d_rp_F, 0.5 * dt, cs);
+  launch_rp_free(P, (int)c->rp_n, c->d_rp_q, c->d_rp_v, c->d_rp_C, c->d_rp_w, dt, cs);
+  rp_launch_forces(c, cs);
+  launch_rp_kick(P, a, c->d_rp_v, c->d_rp_F, 0.5 * dt, cs);
+  launch_rp_record(P, a, c->d_rp_q, c->d_rp_v, wp, c->d_rp_blk, c->d_stats, c->d_step, c->rec_cap, c->d_e_rec, cs);
+  const int rc = finish_capture(c, cs, own, &c->graph_rp, &c->rp_graph_kernels);
+  if (rc) return rc;
+  c->rp_graph_dt = dt;
+  return ALLEGRO_OK;
 }
 
 }  // namespace
@@ -1565,85 +1590,140 @@ int allegro_pimd_init(allegro_ctx* ctx, int32_t n_beads, int64_t n_atoms, const 
     return ctx->fail(ALLEGRO_E_INVALID_ARG, "positions, velocities, species and cell are required");
   if (!(temperature_K > 0.0) || !std::isfinite(temperature_K))
     return ctx->fail(ALLEGRO_E_INVALID_ARG, "temperature must be positive");
-  ctx->md_ready = false;
+  double L[3];
+  int rc = check_cell(ctx, cell, L);
+  if (rc) return rc;
   ctx->rp_ready = false;
+  ctx->md_ready = false;
   ctx->drop_graphs();
   const int P = n_beads;
   const int64_t PN = (int64_t)P * n_atoms;
-  for (void* p : {(void*)ctx->d_rp_q, (void*)ctx->d_rp_v, (void*)ctx->d_rp_species, (void*)ctx->d_rp_C,
-                  (void*)ctx->d_rp_w, (void*)ctx->d_rp_blk})
+  for (void* p : {(void*)ctx->d_rp_q, (void*)ctx->d_rp_v, (void*)ctx->d_rp_F, (void*)ctx->d_rp_q_snap,
+                  (void*)ctx->d_rp_v_snap, (void*)ctx->d_rp_F_snap, (void*)ctx->d_rp_species,
+                  (void*)ctx->d_rp_species_all, (void*)ctx->d_rp_C, (void*)ctx->d_rp_w, (void*)ctx->d_rp_blk})
     ctx->dfree(p);
   ctx->d_rp_q = ctx->dalloc<double>(3 * (size_t)PN);
   ctx->d_rp_v = ctx->dalloc<double>(3 * (size_t)PN);
+  ctx->d_rp_F = ctx->dalloc<float>(3 * (size_t)PN);
+  ctx->d_rp_q_snap = ctx->dalloc<double>(3 * (size_t)PN);
+  ctx->d_rp_v_snap = ctx->dalloc<double>(3 * (size_t)PN);
+  ctx->d_rp_F_snap = ctx->dalloc<float>(3 * (size_t)PN);
   ctx->d_rp_species = ctx->dalloc<int>((size_t)n_atoms);
+  ctx->d_rp_species_all = ctx->dalloc<int>((size_t)PN);
   ctx->d_rp_C = ctx->dalloc<double>((size_t)P * P);
   ctx->d_rp_w = ctx->dalloc<double>((size_t)P);
   ctx->d_rp_blk = ctx->dalloc<double>(2 * ((size_t)PN / 256 + 2));
-  if (!ctx->d_rp_q || !ctx->d_rp_v || !ctx->d_rp_species || !ctx->d_rp_C || !ctx->d_rp_w || !ctx->d_rp_blk)
+  if (!ctx->d_rp_q || !ctx->d_rp_v || !ctx->d_rp_F || !ctx->d_rp_q_snap || !ctx->d_rp_v_snap ||
+      !ctx->d_rp_F_snap || !ctx->d_rp_species || !ctx->d_rp_species_all || !ctx->d_rp_C || !ctx->d_rp_w ||
+      !ctx->d_rp_blk)
     return ctx->fail(ALLEGRO_E_OOM, "replica allocation failed");
+  cudaStream_t s = ctx->stream;
   const cudaMemcpyKind kq = is_device_ptr(positions) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kv = is_device_ptr(velocities) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind ks = is_device_ptr(species) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaMemcpyAsync(ctx->d_rp_q, positions, sizeof(double) * 3 * PN, kq, ctx->stream);
-  cudaMemcpyAsync(ctx->d_rp_v, velocities, sizeof(double) * 3 * PN, kv, ctx->stream);
-  cudaMemcpyAsync(ctx->d_rp_species, species, sizeof(int) * n_atoms, ks, ctx->stream);
+  cudaMemcpyAsync(ctx->d_rp_q, positions, sizeof(double) * 3 * PN, kq, s);
+  cudaMemcpyAsync(ctx->d_rp_v, velocities, sizeof(double) * 3 * PN, kv, s);
+  cudaMemcpyAsync(ctx->d_rp_species, species, sizeof(int) * n_atoms, ks, s);
+  for (int k = 0; k < P; ++k)
+    cudaMemcpyAsync(ctx->d_rp_species_all + (size_t)k * n_atoms, ctx->d_rp_species, sizeof(int) * n_atoms,
+                    cudaMemcpyDeviceToDevice, s);
   // normal modes of the ring: C[j P + k], frequencies omega_k = 2 omega_P sin(k' pi / P)
   const double wp = P * kBoltzmannEv * temperature_K / kHbarEvFs;
   std::vector<double> C((size_t)P * P), w(P);
   for (int k = 0; k < P; ++k) {
     for (int j = 0; j < P; ++j) {
-      double c;
-      if (k == 0) c = 1.0 / std::sqrt((double)P);
-      else if (2 * k < P) c = std::sqrt(2.0 / P) * std::cos(2.0 * M_PI * j * k / P);
-      else if (2 * k == P) c = ((j & 1) ? -1.0 : 1.0) / std::sqrt((double)P);
-      else c = std::sqrt(2.0 / P) * std::sin(2.0 * M_PI * j * k / P);
-      C[(size_t)j * P + k] = c;
+      double cjk;
+      if (k == 0) cjk = 1.0 / std::sqrt((double)P);
+      else if (2 * k < P) cjk = std::sqrt(2.0 / P) * std::cos(2.0 * M_PI * j * k / P);
+      else if (2 * k == P) cjk = ((j & 1) ? -1.0 : 1.0) / std::sqrt((double)P);
+      else cjk = std::sqrt(2.0 / P) * std::sin(2.0 * M_PI * j * k / P);
+      C[(size_t)j * P + k] = cjk;
     }
     const int kk = 2 * k <= P ? k : P - k;
     w[k] = 2.0 * wp * std::sin(kk * M_PI / P);
   }
-  cudaMemcpyAsync(ctx->d_rp_C, C.data(), sizeof(double) * P * P, cudaMemcpyHostToDevice, ctx->stream);
-  cudaMemcpyAsync(ctx->d_rp_w, w.data(), sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream);
-  for (int i = 0; i < 9; ++i) ctx->rp_cell[i] = cell[i];
+  cudaMemcpyAsync(ctx->d_rp_C, C.data(), sizeof(double) * P * P, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(ctx->d_rp_w, w.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s);
+  for (int a = 0; a < 3; ++a) ctx->rp_L[a] = L[a];
+  ctx->rp_grid = plan_grid(L, ctx->blob.rc);
   ctx->rp_P = P;
   ctx->rp_n = n_atoms;
   ctx->rp_T = temperature_K;
-  int rc = ensure_atoms(ctx, PN, 0);
-  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "pimd_init");
-  if (!rc) rc = rp_forces(ctx);                      // checks the cell, species and capacity once
+  rc = rp_reserve(ctx);
   if (rc) return rc;
-  ctx->rp_ready = true;
-  return ALLEGRO_OK;
+  if (ctx->md_precision != ALLEGRO_FP32) {
+    rc = refresh_tc(ctx);
+    if (rc) return rc;
+  }
+  // species check, then the forces of the initial beads (growing the pair
+  // capacity if the estimate was short)
+  cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), s);
+  k_check_species<<<(int)((n_atoms + 255) / 256), 256, 0, s>>>((int)n_atoms, ctx->d_rp_species, (int)ctx->blob.S,
+                                                               ctx->nb.flags);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    rp_launch_forces(ctx, s);
+    int flags = 0, np = 0;
+    cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(ctx, "pimd_init");
+    if (flags & kFlagBadSpecies) return ctx->fail(ALLEGRO_E_INVALID_ARG, "species id out of range");
+    if (flags & kFlagNonfinite) return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite bead position or force");
+    if (!(flags & kFlagPairOverflow)) {
+      ctx->rp_ready = true;
+      return ALLEGRO_OK;
+    }
+    rc = ensure_pairs(ctx, std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024);
+    if (rc) return rc;
+    cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), s);
+  }
+  return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown for the ring");
 }
 
 int allegro_pimd_step(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double* energies) {
   if (!ctx || !ctx->rp_ready) return ctx ? ctx->fail(ALLEGRO_E_INVALID_ARG, "pimd_init first") : ALLEGRO_E_INVALID_ARG;
   if (n_steps < 0 || !(dt_fs > 0.0) || !std::isfinite(dt_fs)) return ctx->fail(ALLEGRO_E_INVALID_ARG, "bad dt or n_steps");
   if (n_steps == 0) return ALLEGRO_OK;
+  ctx->md_ready = false;                             // the shared buffers now hold the ring
   int rc = ensure_records(ctx, n_steps);
+  if (!rc) rc = rp_reserve(ctx);                     // other calls may have moved the shared buffers
+  if (!rc && ctx->md_precision != ALLEGRO_FP32) rc = refresh_tc(ctx);
   if (rc) return rc;
-  const int P = ctx->rp_P;
-  const double wp = P * kBoltzmannEv * ctx->rp_T / kHbarEvFs;
-  rc = rp_forces(ctx);                               // forces of the current replicas
-  if (rc) return rc;
-  cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream);
-  for (int s = 0; s < n_steps && !rc; ++s) {
-    const AtomArgs a = rp_atom_args(ctx);
-    launch_rp_kick(P, a, ctx->d_rp_v, ctx->d_F, 0.5 * dt_fs, ctx->stream);
-    launch_rp_free(P, (int)ctx->rp_n, ctx->d_rp_q, ctx->d_rp_v, ctx->d_rp_C, ctx->d_rp_w, dt_fs, ctx->stream);
-    rc = rp_forces(ctx);
-    if (rc) break;
-    launch_rp_kick(P, a, ctx->d_rp_v, ctx->d_F, 0.5 * dt_fs, ctx->stream);
-    launch_rp_record(P, a, ctx->d_rp_q, ctx->d_rp_v, wp, ctx->d_rp_blk, ctx->d_stats, ctx->d_step, ctx->rec_cap,
-                     ctx->d_e_rec, ctx->stream);
-  }
-  if (rc) {
-    ctx->rp_ready = false;                           // the replicas are mid-step
+  const size_t n3 = 3 * (size_t)ctx->rp_P * (size_t)ctx->rp_n;
+  cudaStream_t s = ctx->stream;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    if (!ctx->graph_rp || ctx->rp_graph_dt != dt_fs) {
+      rc = capture_step_rp(ctx, dt_fs);
+      if (rc) return rc;
+    }
+    cudaMemcpyAsync(ctx->d_rp_q_snap, ctx->d_rp_q, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ctx->d_rp_v_snap, ctx->d_rp_v, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ctx->d_rp_F_snap, ctx->d_rp_F, sizeof(float) * n3, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), s);
+    cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), s);
+    for (int k = 0; k < n_steps; ++k)
+      if (cudaGraphLaunch(ctx->graph_rp, s) != cudaSuccess) return cuda_check(ctx, "graph launch");
+    int flags = 0, np = 0;
+    cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(ctx, "pimd steps");
+    if (flags & kFlagPairOverflow) {
+      cudaMemcpyAsync(ctx->d_rp_q, ctx->d_rp_q_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(ctx->d_rp_v, ctx->d_rp_v_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(ctx->d_rp_F, ctx->d_rp_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, s);
+      cudaStreamSynchronize(s);
+      rc = ensure_pairs(ctx, std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024);
+      if (rc) return rc;
+      continue;
+    }
+    if (flags & kFlagNonfinite) {
+      ctx->rp_ready = false;                         // the ring state is no longer meaningful
+      return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite bead position or force");
+    }
+    rc = copy_out(ctx, energies, ctx->d_e_rec, sizeof(double) * 3 * n_steps);
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_check(ctx, "pimd records");
     return rc;
   }
-  rc = copy_out(ctx, energies, ctx->d_e_rec, sizeof(double) * 3 * n_steps);
-  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = cuda_check(ctx, "pimd steps");
-  return rc;
+  return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown during ring-polymer MD");
 }
 
 int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velocities) {
@@ -1669,6 +1749,7 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
     }
     case ALLEGRO_Q_CAPACITY: *value = ctx->capacity; return ALLEGRO_OK;
     case ALLEGRO_Q_STEP_KERNELS: *value = ctx->graph_kernels; return ALLEGRO_OK;
+    case ALLEGRO_Q_RP_STEP_KERNELS: *value = ctx->rp_graph_kernels; return ALLEGRO_OK;
     case ALLEGRO_Q_N_ATOMS: *value = ctx->n_atoms; return ALLEGRO_OK;
     case ALLEGRO_Q_N_PARAMS: *value = ctx->n_params; return ALLEGRO_OK;
     default: return ctx->fail(ALLEGRO_E_INVALID_ARG, "unknown query key");

@@ -51,8 +51,11 @@ GridInfo plan_grid(const double L[3], double rc);
 // Full rebuild: wrap, bin, count, scan, fill, sort, reverse.  Writes the pair
 // count to nb.n_pairs and raises kFlagPairOverflow if it exceeds capacity
 // (then the pair arrays are untouched beyond capacity and must not be used).
+// nps > 0: n_atoms / nps independent systems of nps atoms each in the same
+// box (atoms of system k at [k nps, (k + 1) nps)), paired only within their
+// system; the cell arrays then hold (n_atoms / nps) ncell + 1 entries.
 void launch_build_neighbors(const NeighborBuffers& nb, const GridInfo& g, const double* pos,
-                            int n_atoms, cudaStream_t s);
+                            int n_atoms, cudaStream_t s, int nps = 0);
 
 // Exclusive scan of n ints (in -> out), out[n] = total; total also copied to
 // *total_dev when non-null.

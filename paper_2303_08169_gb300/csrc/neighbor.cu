@@ -16,6 +16,11 @@
 // One warp per centre atom enumerates candidates, counts with ballots, fills
 // keys, rank-sorts its row and decodes it.  Deterministic: the cell-filling
 // order does not matter because every row is sorted by a unique key.
+//
+// Several systems in one build: atoms [k nps, (k + 1) nps) form system k
+// (same box); each system has its own cells (cell index k ncell + c) and its
+// atoms pair only among themselves, so the result is the concatenation of
+// the systems' own lists with atom indices offset by k nps.
 #include <cmath>
 #include <cstdio>
 
@@ -28,7 +33,7 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 
-__global__ void k_wrap_bin(const double* __restrict__ pos, int n, GridInfo g,
+__global__ void k_wrap_bin(const double* __restrict__ pos, int n, int nps, GridInfo g,
                            double* __restrict__ wpos, float* __restrict__ wpos32,
                            int* __restrict__ atom_cell, int* __restrict__ cell_count,
                            int* __restrict__ flags) {
@@ -55,7 +60,8 @@ __global__ void k_wrap_bin(const double* __restrict__ pos, int n, GridInfo g,
   }
   if (!finite) atomicOr(flags, kFlagNonfinite);
   if (g.ncell[0] > 0) {
-    int cell = (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
+    const int ncl = g.ncell[0] * g.ncell[1] * g.ncell[2];
+    const int cell = (i / nps) * ncl + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
     atom_cell[i] = cell;
     atomicAdd(&cell_count[cell], 1);
   }
@@ -83,14 +89,15 @@ __device__ __noinline__ bool exact_in(const double* __restrict__ w, int i, int j
   return d2 < __dmul_rn(rc, rc);
 }
 
-// Visit every candidate (j, n) of centre i, lanes striding over candidates.
-// f(j, n[3]) is called by the lane owning a candidate that is inside the
-// cutoff; returns nothing, the caller ballots.
+// Visit every candidate (j, n) of centre i, lanes striding over candidates
+// of i's own system (nps atoms per system).  f(j, n[3]) is called by the
+// lane owning a candidate that is inside the cutoff; returns nothing, the
+// caller ballots.
 template <class F>
 AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict__ w32,
                                const double* __restrict__ w64, const int* __restrict__ atom_cell,
                                const int* __restrict__ cell_start,
-                               const int* __restrict__ cell_atoms, int n_atoms, F f) {
+                               const int* __restrict__ cell_atoms, int nps, F f) {
   const int lane = threadIdx.x & 31;
   const float xi = w32[3 * i], yi = w32[3 * i + 1], zi = w32[3 * i + 2];
   const float rc2 = (float)(g.rc * g.rc);
@@ -101,7 +108,9 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
     // lanes then stride over the concatenation of the 27 ranges, so that a
     // warp visits ~10 candidates per cell in one pass instead of one pass per
     // cell
-    const int cell = atom_cell[i];
+    const int ncl = g.ncell[0] * g.ncell[1] * g.ncell[2];
+    const int sys_cell = (atom_cell[i] / ncl) * ncl;  // first cell of i's system
+    const int cell = atom_cell[i] - sys_cell;
     const int cz = cell % g.ncell[2];
     const int cy = (cell / g.ncell[2]) % g.ncell[1];
     const int cx = cell / (g.ncell[2] * g.ncell[1]);
@@ -113,7 +122,7 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
       if (tx < 0) { tx += g.ncell[0]; n[0] = -1; } else if (tx >= g.ncell[0]) { tx -= g.ncell[0]; n[0] = 1; }
       if (ty < 0) { ty += g.ncell[1]; n[1] = -1; } else if (ty >= g.ncell[1]) { ty -= g.ncell[1]; n[1] = 1; }
       if (tz < 0) { tz += g.ncell[2]; n[2] = -1; } else if (tz >= g.ncell[2]) { tz -= g.ncell[2]; n[2] = 1; }
-      const int other = (tx * g.ncell[1] + ty) * g.ncell[2] + tz;
+      const int other = sys_cell + (tx * g.ncell[1] + ty) * g.ncell[2] + tz;
       cb = cell_start[other];
       cn = cell_start[other + 1] - cb;
       ccode = img_code(n[0], n[1], n[2]);
@@ -158,14 +167,15 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
   } else {
     const int nx = 2 * g.nimg[0] + 1, ny = 2 * g.nimg[1] + 1, nz = 2 * g.nimg[2] + 1;
     const int nimg = nx * ny * nz;
-    const int total = n_atoms * nimg;
+    const int total = nps * nimg;
+    const int j0 = (i / nps) * nps;                   // first atom of i's system
     for (int k0 = 0; k0 < total; k0 += 32) {
       const int k = k0 + lane;
       bool hit = false;
       int j = -1;
       int n[3] = {0, 0, 0};
       if (k < total) {
-        j = k / nimg;
+        j = j0 + k / nimg;
         const int m = k % nimg;
         n[0] = m / (ny * nz) - g.nimg[0];
         n[1] = (m / nz) % ny - g.nimg[1];
@@ -186,13 +196,13 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_count(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __restrict__ w64,
+k_count(int n_atoms, int nps, GridInfo g, const float* __restrict__ w32, const double* __restrict__ w64,
         const int* __restrict__ atom_cell, const int* __restrict__ cell_start,
         const int* __restrict__ cell_atoms, int* __restrict__ row_cnt) {
   const int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (i >= n_atoms) return;
   int cnt = 0;
-  for_each_candidate(i, g, w32, w64, atom_cell, cell_start, cell_atoms, n_atoms,
+  for_each_candidate(i, g, w32, w64, atom_cell, cell_start, cell_atoms, nps,
                      [&](bool hit, int, const int*) { cnt += __popc(__ballot_sync(0xffffffffu, hit)); });
   if ((threadIdx.x & 31) == 0) row_cnt[i] = cnt;
 }
@@ -202,7 +212,7 @@ k_count(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __
 constexpr int kRowCap = 192;
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_fill(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __restrict__ w64,
+k_fill(int n_atoms, int nps, GridInfo g, const float* __restrict__ w32, const double* __restrict__ w64,
        const int* __restrict__ atom_cell, const int* __restrict__ cell_start,
        const int* __restrict__ cell_atoms, const int* __restrict__ row_ptr,
        const int* __restrict__ n_pairs, int64_t capacity, unsigned long long* __restrict__ keys,
@@ -220,7 +230,7 @@ k_fill(int n_atoms, GridInfo g, const float* __restrict__ w32, const double* __r
   const int len = row_ptr[i + 1] - base;
   unsigned long long* kb = len <= kRowCap ? s_keys[threadIdx.x >> 5] : keys + base;
   int cnt = 0;
-  for_each_candidate(i, g, w32, w64, atom_cell, cell_start, cell_atoms, n_atoms,
+  for_each_candidate(i, g, w32, w64, atom_cell, cell_start, cell_atoms, nps,
                      [&](bool hit, int j, const int* n) {
                        const unsigned m = __ballot_sync(0xffffffffu, hit);
                        if (hit) {
@@ -381,11 +391,13 @@ GridInfo plan_grid(const double L[3], double rc) {
 }
 
 void launch_build_neighbors(const NeighborBuffers& nb, const GridInfo& g, const double* pos,
-                            int n_atoms, cudaStream_t s) {
-  const int ncell = g.ncell[0] > 0 ? g.ncell[0] * g.ncell[1] * g.ncell[2] : 0;
+                            int n_atoms, cudaStream_t s, int nps) {
+  if (nps <= 0) nps = n_atoms > 0 ? n_atoms : 1;
+  const int n_sys = n_atoms / nps;
+  const int ncell = g.ncell[0] > 0 ? n_sys * g.ncell[0] * g.ncell[1] * g.ncell[2] : 0;
   if (ncell > 0) cudaMemsetAsync(nb.cell_count, 0, sizeof(int) * (ncell + 1), s);
   const int tb = 256;
-  k_wrap_bin<<<(n_atoms + tb - 1) / tb, tb, 0, s>>>(pos, n_atoms, g, nb.wpos, nb.wpos32,
+  k_wrap_bin<<<(n_atoms + tb - 1) / tb, tb, 0, s>>>(pos, n_atoms, nps, g, nb.wpos, nb.wpos32,
                                                    nb.atom_cell, nb.cell_count, nb.flags);
   if (ncell > 0) {
     launch_scan(nb.cell_count, nb.cell_start, ncell, nb.scan_blocks, nullptr, s);
@@ -395,10 +407,10 @@ void launch_build_neighbors(const NeighborBuffers& nb, const GridInfo& g, const 
                                                       nb.cell_count, nb.cell_atoms);
   }
   const int wb = (n_atoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  k_count<<<wb, kWarpsPerBlock * 32, 0, s>>>(n_atoms, g, nb.wpos32, nb.wpos, nb.atom_cell,
+  k_count<<<wb, kWarpsPerBlock * 32, 0, s>>>(n_atoms, nps, g, nb.wpos32, nb.wpos, nb.atom_cell,
                                              nb.cell_start, nb.cell_atoms, nb.row_cnt);
   launch_scan(nb.row_cnt, nb.row_ptr, n_atoms, nb.scan_blocks, nb.n_pairs, s);
-  k_fill<<<wb, kWarpsPerBlock * 32, 0, s>>>(n_atoms, g, nb.wpos32, nb.wpos, nb.atom_cell,
+  k_fill<<<wb, kWarpsPerBlock * 32, 0, s>>>(n_atoms, nps, g, nb.wpos32, nb.wpos, nb.atom_cell,
                                             nb.cell_start, nb.cell_atoms, nb.row_ptr, nb.n_pairs,
                                             nb.capacity, nb.keys, nb.skeys, nb.pi, nb.pj,
                                             nb.pcode, nb.flags);

@@ -123,7 +123,9 @@ def test_batched_replicas_match_single_evaluations(precision):
 def test_pimd_conserves_hp_and_resumes():
     """200 steps: H_P stays within a small fraction of the kinetic-energy
     swing, and two calls of 100 steps equal one call of 200 (bitwise: the
-    pass sequence is deterministic)."""
+    pass sequence is deterministic), also with an energy evaluation of a
+    larger system in between (the ring state lives in its own arrays; the
+    shared buffers grow and the step graph is captured again)."""
     cfg = synth.TINY
     blob = synth.make_blob(cfg, 42, sigma=energy_scale("tiny"))
     ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
@@ -137,9 +139,37 @@ def test_pimd_conserves_hp_and_resumes():
     al.allegro_pimd_init(ctx, q0, v0, sp32, cell, T)
     a, b = np.zeros((100, 3)), np.zeros((100, 3))
     al.allegro_pimd_step(ctx, 0.25, 100, a)
+    big, sbig, cbig = synth.make_ammonia(250, 4)
+    al.allegro_energy_forces(ctx, big, sbig.astype(np.int32), cbig)
     al.allegro_pimd_step(ctx, 0.25, 100, b)
     assert np.array_equal(np.vstack([a, b]), e1)
     dH = np.abs(e1[:, 2] - e1[0, 2]).max()
     dK = np.ptp(e1[:, 1])
     assert dK > 0 and dH < 0.05 * dK
+    al.allegro_destroy(ctx)
+
+
+def test_shared_buffer_calls_end_the_md_state():
+    """allegro_energy_forces and the ring-polymer calls reuse the MD state's
+    buffers: the next NVE step asks for allegro_md_init instead of stepping
+    a clobbered state."""
+    cfg = synth.TINY
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("tiny"))
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(16, 0)
+    sp32 = sp.astype(np.int32)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    al.allegro_md_init(ctx, pos, v0, sp32, cell)
+    al.allegro_md_step_nve(ctx, 0.5, 2)
+    al.allegro_energy_forces(ctx, pos, sp32, cell)
+    with pytest.raises(al.AllegroError):
+        al.allegro_md_step_nve(ctx, 0.5, 2)
+    al.allegro_md_init(ctx, pos, v0, sp32, cell)
+    al.allegro_md_step_nve(ctx, 0.5, 2)
+    q0, v = _ring(pos, sp, 2, 200.0, 9)
+    al.allegro_pimd_init(ctx, q0, v, sp32, cell, 200.0)
+    with pytest.raises(al.AllegroError):
+        al.allegro_md_step_nvt(ctx, 0.5, 2, 200.0, 10.0)
+    al.allegro_pimd_step(ctx, 0.5, 2)
+    assert al.allegro_query(ctx, al.ALLEGRO_Q_RP_STEP_KERNELS) > 10
     al.allegro_destroy(ctx)
