@@ -12,21 +12,31 @@
 namespace al {
 namespace {
 
-constexpr int kWT = 32;       // output tile (rows n, cols k) of the reduction
-constexpr int kWP = 64;       // pairs staged per step
+constexpr int kWT = 64;       // output tile (rows n, cols k) of the reduction
+constexpr int kWP = 32;       // pairs staged per step
 
 // dW[n * ldw + k0 + k] += scale * sum_{p in chunk} dz[p * ldz + n] * x[p * ldx + k]
+// A 64 x 64 output tile per block over one chunk of pairs: 256 threads, each
+// a 4 x 4 register tile fed by two 16-byte shared-memory reads per pair (the
+// dz read is a broadcast within each half warp), one atomic add per output
+// at the end of the chunk.
 __global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int ldz, const float* __restrict__ x,
                                                int ldx, int P, int N, int K, float scale, float* __restrict__ dW,
                                                int ldw, int k0, int chunk) {
-  __shared__ float sz[kWP][kWT + 1];
-  __shared__ float sx[kWP][kWT + 1];
+  __shared__ __align__(16) float sz[kWP][kWT];
+  __shared__ __align__(16) float sx[kWP][kWT];
   const int n0 = blockIdx.x * kWT, kb = blockIdx.y * kWT;
   const int pb = blockIdx.z * chunk, pe = min(P, pb + chunk);
-  const int tn = threadIdx.x >> 3, tk = (threadIdx.x & 7) * 4;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int tn = (threadIdx.x >> 4) * 4, tk = (threadIdx.x & 15) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
   for (int p0 = pb; p0 < pe; p0 += kWP) {
-    for (int idx = threadIdx.x; idx < kWP * kWT; idx += blockDim.x) {
+#pragma unroll
+    for (int r = 0; r < kWP * kWT / 256; ++r) {
+      const int idx = r * 256 + threadIdx.x;
       const int pp = idx / kWT, c = idx % kWT;
       const int p = p0 + pp;
       sz[pp][c] = (p < pe && n0 + c < N) ? dz[(size_t)p * ldz + n0 + c] : 0.0f;
@@ -35,17 +45,24 @@ __global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int
     __syncthreads();
 #pragma unroll 8
     for (int pp = 0; pp < kWP; ++pp) {
-      const float a = sz[pp][tn];
+      const float4 a = *reinterpret_cast<const float4*>(&sz[pp][tn]);
+      const float4 b = *reinterpret_cast<const float4*>(&sx[pp][tk]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fmaf(a, sx[pp][tk + j], acc[j]);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
-  const int n = n0 + tn;
-  if (n < N)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = n0 + tn + i;
+    if (n >= N) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (kb + tk + j < K) atomicAdd(&dW[(size_t)n * ldw + k0 + kb + tk + j], scale * acc[j]);
+      if (kb + tk + j < K) atomicAdd(&dW[(size_t)n * ldw + k0 + kb + tk + j], scale * acc[i][j]);
+  }
 }
 
 // Mixing of order l: dW[c'][c Pl + q] += scale sum_p sum_m dV[p][c' NLM + l l + m] T[p][c NT + toff + q (2l+1) + m]
@@ -252,7 +269,12 @@ void launch_displace(int64_t N, const int* sid, const double* wpos, const float*
 void launch_wgrad(const float* dz, int ldz, const float* x, int ldx, int P, int N, int K, float scale, float* dW,
                   int ldw, int k0, cudaStream_t s) {
   if (P <= 0) return;
-  const int chunk = 2048;
+  // about four blocks per SM over all output tiles, chunks a multiple of the
+  // staging depth
+  const int tiles = ((N + kWT - 1) / kWT) * ((K + kWT - 1) / kWT);
+  const int want = std::max(1, 152 * 4 / tiles);
+  int chunk = (P + want - 1) / want;
+  chunk = std::max(kWP * 8, (chunk + kWP - 1) / kWP * kWP);
   dim3 grid((N + kWT - 1) / kWT, (K + kWT - 1) / kWT, (P + chunk - 1) / chunk);
   k_wgrad<<<grid, 256, 0, s>>>(dz, ldz, x, ldx, P, N, K, scale, dW, ldw, k0, chunk);
 }
