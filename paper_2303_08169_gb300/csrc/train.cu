@@ -66,21 +66,60 @@ __global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int
 }
 
 // Mixing of order l: dW[c'][c Pl + q] += scale sum_p sum_m dV[p][c' NLM + l l + m] T[p][c NT + toff + q (2l+1) + m]
+// One block per chunk of pairs: the order-l parts of kMixG pairs' dV and T
+// rows are staged in shared memory with contiguous loads, then every thread
+// accumulates up to kMixR outputs (a pass over the chunk per kMixR x 256
+// outputs), one atomic add per output at the end.
+constexpr int kMixG = 16;
+constexpr int kMixR = 4;
+
 __global__ void __launch_bounds__(256) k_wgrad_mix(const float* __restrict__ dV, const float* __restrict__ T, int P,
                                                    int C, int NLM, int NT, int l, int Pl, int toff, float scale,
                                                    float* __restrict__ dW, int chunk) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= C * C * Pl) return;
-  const int co = o / (C * Pl), rem = o % (C * Pl), c = rem / Pl, q = rem % Pl;
+  extern __shared__ float mix_s[];
   const int nm = 2 * l + 1;
-  const int pb = blockIdx.y * chunk, pe = min(P, pb + chunk);
-  float acc = 0.0f;
-  for (int p = pb; p < pe; ++p) {
-    const float* dv = dV + (size_t)p * C * NLM + co * NLM + l * l;
-    const float* t = T + (size_t)p * C * NT + c * NT + toff + q * nm;
-    for (int m = 0; m < nm; ++m) acc = fmaf(dv[m], t[m], acc);
+  const int wv = C * nm, wt = C * Pl * nm;            // staged floats per pair
+  float* dv_s = mix_s;                                // [kMixG][wv]
+  float* t_s = mix_s + kMixG * wv;                    // [kMixG][wt]
+  const int n_out = C * C * Pl;
+  const int pb = blockIdx.x * chunk, pe = min(P, pb + chunk);
+  for (int ob = 0; ob < n_out; ob += kMixR * 256) {
+    float acc[kMixR];
+    int dvo[kMixR], to[kMixR];
+#pragma unroll
+    for (int r = 0; r < kMixR; ++r) {
+      acc[r] = 0.0f;
+      const int o = min(ob + r * 256 + (int)threadIdx.x, n_out - 1);
+      const int co = o / (C * Pl), c = (o / Pl) % C, q = o % Pl;
+      dvo[r] = co * nm;
+      to[r] = c * Pl * nm + q * nm;
+    }
+    for (int p0 = pb; p0 < pe; p0 += kMixG) {
+      const int gn = min(kMixG, pe - p0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < gn * wv; idx += blockDim.x) {
+        const int g = idx / wv, e = idx % wv, co = e / nm, m = e % nm;
+        dv_s[g * wv + e] = dV[(size_t)(p0 + g) * C * NLM + co * NLM + l * l + m];
+      }
+      for (int idx = threadIdx.x; idx < gn * wt; idx += blockDim.x) {
+        const int g = idx / wt, e = idx % wt, c = e / (Pl * nm), j = e % (Pl * nm);
+        t_s[g * wt + e] = T[(size_t)(p0 + g) * C * NT + c * NT + toff + j];
+      }
+      __syncthreads();
+      for (int g = 0; g < gn; ++g) {
+        const float* dv = dv_s + g * wv;
+        const float* tt = t_s + g * wt;
+#pragma unroll
+        for (int r = 0; r < kMixR; ++r)
+          for (int m = 0; m < nm; ++m) acc[r] = fmaf(dv[dvo[r] + m], tt[to[r] + m], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kMixR; ++r) {
+      const int o = ob + r * 256 + (int)threadIdx.x;
+      if (o < n_out) atomicAdd(&dW[o], scale * acc[r]);
+    }
   }
-  atomicAdd(&dW[o], scale * acc);
 }
 
 __global__ void k_sumsq(const float* __restrict__ g, int n, double* __restrict__ out) {
@@ -282,9 +321,11 @@ void launch_wgrad(const float* dz, int ldz, const float* x, int ldx, int P, int 
 void launch_wgrad_mix(const float* dV, const float* T, int P, int C, int NLM, int NT, int l, int Pl, int toff,
                       float scale, float* dW, cudaStream_t s) {
   if (P <= 0) return;
-  const int chunk = 1024;
-  dim3 grid((C * C * Pl + 255) / 256, (P + chunk - 1) / chunk);
-  k_wgrad_mix<<<grid, 256, 0, s>>>(dV, T, P, C, NLM, NT, l, Pl, toff, scale, dW, chunk);
+  // about four blocks per SM
+  const int chunk = std::max(kMixG, (P + 152 * 4 - 1) / (152 * 4));
+  const int nm = 2 * l + 1;
+  const size_t smem = sizeof(float) * kMixG * (size_t)(C * nm + C * Pl * nm);
+  k_wgrad_mix<<<(P + chunk - 1) / chunk, 256, smem, s>>>(dV, T, P, C, NLM, NT, l, Pl, toff, scale, dW, chunk);
 }
 
 void launch_sumsq(const float* g, int n, double* out, cudaStream_t s) { k_sumsq<<<1, 1024, 0, s>>>(g, n, out); }

@@ -173,3 +173,43 @@ def test_shared_buffer_calls_end_the_md_state():
     al.allegro_pimd_step(ctx, 0.5, 2)
     assert al.allegro_query(ctx, al.ALLEGRO_Q_RP_STEP_KERNELS) > 10
     al.allegro_destroy(ctx)
+
+
+@pytest.mark.parametrize("cfg_name,n_mol,P", [("tiny", 16, 3), ("main", 108, 4)])
+def test_ring_neighbour_list_is_each_replicas_list(cfg_name, n_mol, P):
+    """The ring's one neighbour build (small-box mode at 64 atoms, cell mode at
+    432) is, bit for bit, each replica's own pair list (the oracle's canonical
+    order) with atom indices offset by k n, and its reverse index maps every
+    pair to (j, i, -n) inside the same replica."""
+    from oracle.neighbors import pairs_bruteforce, reverse_index
+    cfg = synth.TINY if cfg_name == "tiny" else synth.MAIN
+    ctx = al.allegro_create(synth.make_blob(cfg, 42, sigma=energy_scale(cfg_name)), MASS, cfg.r_cut, cfg.l_max,
+                            cfg.n_layers)
+    pos, sp, cell = synth.make_ammonia(n_mol, 2)
+    L = np.diag(cell)
+    n = len(pos)
+    q0, v0 = _ring(pos, sp, P, 200.0, 13)
+    q0[1] += L                                          # a replica shifted by a whole box: same list
+    al.allegro_pimd_init(ctx, q0, v0, sp.astype(np.int32), cell, 200.0)
+    n_pairs = al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS)
+    row = np.zeros(P * n + 1, np.int32)
+    col = np.zeros(n_pairs, np.int32)
+    img = np.zeros((n_pairs, 3), np.int8)
+    rev = np.zeros(n_pairs, np.int32)
+    al.allegro_get_neighbors(ctx, row, col, img, rev)
+    gi = np.repeat(np.arange(P * n), np.diff(row.astype(np.int64)))
+    RI, RJ, RN, RR = [], [], [], []
+    off = 0
+    for k in range(P):
+        ri, rj, rn = pairs_bruteforce(q0[k], L, cfg.r_cut)
+        RI.append(ri + k * n)
+        RJ.append(rj + k * n)
+        RN.append(rn)
+        RR.append(reverse_index(ri, rj, rn, n) + off)
+        off += len(ri)
+    assert n_pairs == off
+    assert np.array_equal(gi, np.concatenate(RI))
+    assert np.array_equal(col.astype(np.int64), np.concatenate(RJ))
+    assert np.array_equal(img.astype(np.int64), np.concatenate(RN))
+    assert np.array_equal(rev.astype(np.int64), np.concatenate(RR))
+    al.allegro_destroy(ctx)
