@@ -692,12 +692,36 @@ def main():
     ap.add_argument("--no-scale", action="store_true", help="skip the 10^6-atom path")
     ap.add_argument("--only-headline", action="store_true",
                     help="time the headline workload only (no other paths, e2e, accuracy or CPU baseline)")
+    ap.add_argument("--only", choices=["pimd", "sam", "lmax"],
+                    help="run one secondary block alone (for profiling) and print its result as JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_block(args)
     return run_ours(args)
+
+
+def run_block(args):
+    """One secondary block on GPU 0 with --steps / --warmup steps where it
+    steps (ring-polymer MD) or SAM steps (sam), printed as one JSON line."""
+    import torch
+    import paper_2303_08169_gb300 as al
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.only == "pimd":
+        cfg, blob = _model()
+        run = Runner(al, torch, dev, blob, cfg)
+        out = run.pimd(args.config, args.steps, args.warmup)
+        run.close()
+    elif args.only == "sam":
+        out = sam_timing(al, torch, steps=args.steps, n_sharp=2)
+    else:
+        out = lmax_sweep(al, torch, dev, K=args.steps, W=args.warmup)
+    print(json.dumps({"block": args.only, **out}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
