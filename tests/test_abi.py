@@ -69,3 +69,16 @@ def test_null_arguments(built):
     assert rc == 1
     assert built.allegro_set_stream(None, None) == 1
     assert built.allegro_md_step_nve(None, 1.0, 1, None, None) == 1
+    assert built.allegro_pimd_step(None, 1.0, 1, None) == 1
+    assert built.allegro_pimd_get_state(None, None, None) == 1
+    assert built.allegro_pimd_init(None, 4, 10, None, None, None, None, 200.0) == 1
+
+
+def test_torch_glue_is_autograd_functions():
+    """The torch glue is two autograd Functions over the library calls (no
+    compute of its own)."""
+    import torch
+    from paper_2303_08169_gb300 import torch_ops
+    assert issubclass(torch_ops.EnergyFunction, torch.autograd.Function)
+    assert issubclass(torch_ops.BatchLossFunction, torch.autograd.Function)
+    assert callable(torch_ops.energy) and callable(torch_ops.batch_loss)
