@@ -85,3 +85,40 @@ def test_ring_polymer_energy_second_order():
         o = rpmd(ffn, q0, v0, m, dt, n, 300.0)
         dev.append(np.abs(o["hp"] - o["hp"][0]).max())
     assert 3.0 < dev[0] / dev[1] < 5.0
+
+
+def test_harmonic_ring_against_matrix_exponential():
+    """Beads of atoms in harmonic wells (V = k |q - c|^2 / 2 per replica):
+    the ring-polymer equations are linear, q'' = -(kappa k / m + omega_P^2 K) q
+    with K the cyclic spring matrix, and their exact flow is the matrix
+    exponential of the first-order system (no normal modes involved).  The
+    integrator follows it with a second-order error."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(5)
+    P, N, T, t_end = 5, 3, 300.0, 12.0
+    m = np.array([14.007, 1.008, 1.008])
+    kk = np.array([2.0, 0.5, 0.8])                   # eV / A^2
+    c = 50.0 + 5.0 * rng.random((N, 3))
+    q0 = c[None] + 0.1 * rng.normal(size=(P, N, 3))
+    v0 = 0.01 * rng.normal(size=(P, N, 3))
+    wp = omega_p(P, T)
+    K = 2.0 * np.eye(P) - np.roll(np.eye(P), 1, axis=1) - np.roll(np.eye(P), -1, axis=1)
+
+    def ffn(p):
+        d = p - c
+        return 0.5 * float((kk[:, None] * d * d).sum()), -kk[:, None] * d
+
+    exact = np.zeros_like(q0)
+    for i in range(N):
+        A = KAPPA * kk[i] / m[i] * np.eye(P) + wp * wp * K
+        M = np.block([[np.zeros((P, P)), np.eye(P)], [-A, np.zeros((P, P))]])
+        E = expm(M * t_end)
+        for a in range(3):
+            y = E @ np.concatenate([q0[:, i, a] - c[i, a], v0[:, i, a]])
+            exact[:, i, a] = y[:P] + c[i, a]
+    err = []
+    for dt in (0.1, 0.05):
+        o = rpmd(ffn, q0, v0, m, dt, int(round(t_end / dt)), T)
+        err.append(np.abs(o["q"] - exact).max())
+    assert err[1] < 1e-4
+    assert 3.5 < err[0] / err[1] < 4.5
