@@ -88,3 +88,12 @@ def test_step_roofline_sums_the_seven_pass_kernels(tmp_path, monkeypatch):
     r = bench.roofline_step(phases, 1_000_000, {"bf16_tflops": 2000.0, "hbm_gbs": 5000.0})
     assert r["traffic"] == pytest.approx(100.0 * len(bench.GEMM_MAC_PER_PAIR) * 1_000_000)
     assert r["frac_hbm"] == pytest.approx(r["traffic"] / (r["kernels_ms"] * 1e-3) / 1e9 / 5000.0)
+
+
+def test_extra_blocks_cannot_take_the_headline_down():
+    """A block beside the headline that raises is reported in its place."""
+    assert bench._guarded(lambda: {"value": 1.0}) == {"value": 1.0}
+
+    def bad():
+        raise RuntimeError("capacity")
+    assert bench._guarded(bad) == {"error": "RuntimeError: capacity"}
