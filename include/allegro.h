@@ -194,11 +194,11 @@ int allegro_md_get_state(allegro_ctx* ctx, double* positions,
 
 /*
  * The outlier count of allegro_outlier_count without allocating device
- * memory, for callers that cannot allocate: code running while a CUDA graph
- * is being captured (cudaMalloc is not allowed there), applications whose own
- * allocator holds all device memory, and latency-bound loops where
- * cudaMalloc/cudaFree would synchronise the device.  The paper has no
- * counterpart; this is a deployment convenience.
+ * memory, for callers that cannot allocate: applications whose own allocator
+ * holds all device memory (a foreign cudaMalloc fails or fragments their
+ * pool), and latency-bound loops where cudaMalloc/cudaFree would synchronise
+ * the device.  The paper has no counterpart; this is a deployment
+ * convenience.
  *  n_atoms   : 1 .. 4,194,304 (the fixed scratch size), else
  *              ALLEGRO_E_INVALID_ARG with a message in allegro_last_error(NULL).
  *  forces    : device, N x 3 FP32.
@@ -212,8 +212,11 @@ int allegro_md_get_state(allegro_ctx* ctx, double* positions,
  * slots it later reads, so nothing needs clearing, but calls that overlap on
  * the GPU (different streams, or different host threads on one device) race
  * on it and must be serialised by the caller.  The first call on each device
- * looks the array's device address up (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.
+ * (and again after the device's CUDA context changed, e.g. after
+ * cudaDeviceReset) looks the array's device address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * A CUDA error left pending by the caller's earlier work is reported as
+ * ALLEGRO_E_CUDA without being cleared, and nothing is launched.
  */
 int allegro_outlier_count_noalloc(int64_t n_atoms, const float* forces, double threshold,
                                   int64_t* count_out, void* cuda_stream);
@@ -401,6 +404,22 @@ int allegro_selftest_mma(int32_t n, int32_t k, const float* a, const float* b, f
  * the descriptor the hardware follows).
  */
 int allegro_selftest_mma_mode(int32_t n, int32_t k, const float* a, const float* b, float* d, int32_t mode);
+
+/*
+ * Failure injection for the failure-detection tests (not part of the paper's
+ * method).  Every wait of the tensor-core passes on an mbarrier is bounded;
+ * when one gives up, the pass skips its remaining MMAs, frees its tensor
+ * memory, returns, and the calling entry point reports ALLEGRO_E_TIMEOUT
+ * (MD and ring-polymer steps first restore the state they started from).
+ * enable != 0 makes the passes on the current device issue no weight copies
+ * and wait at most 2^20 clock cycles for them, so that every tensor-core call
+ * ends in ALLEGRO_E_TIMEOUT with no copy or MMA in flight; enable == 0
+ * restores normal operation (copies issued, 2^31-cycle limit).  Process-wide
+ * for the current device; synchronises the device before and after, so call
+ * it between calls, never while another thread uses the library.
+ * ALLEGRO_E_CUDA if the device could not be updated.
+ */
+int allegro_debug_inject_wait_timeout(int32_t enable);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ EXPORTED = [
     "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
     "allegro_loss_scan", "allegro_md_step_nvt", "allegro_md_get_thermostat",
     "allegro_pimd_init", "allegro_pimd_step", "allegro_pimd_get_state",
+    "allegro_debug_inject_wait_timeout",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -101,6 +102,7 @@ def lib():
         "allegro_loss_scan": ([_vp, _vp, _vp, _i64, _vp, _i32, _f64, _f64, _vp], ctypes.c_int),
         "allegro_get_weights": ([_vp, _vp, _i64], ctypes.c_int),
         "allegro_set_weights": ([_vp, _vp, _i64], ctypes.c_int),
+        "allegro_debug_inject_wait_timeout": ([_i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -324,3 +326,9 @@ def allegro_selftest_mma_mode(a, b, d, mode):
 
 
 __all__ = ["ALLEGRO_FP32", "ALLEGRO_BF16", "ALLEGRO_FP16", "ALLEGRO_FP16_SPLIT", "AllegroError", "EXPORTED", "build", "lib"] + EXPORTED
+
+
+def allegro_debug_inject_wait_timeout(enable):
+    """Failure injection for tests: the tensor-core passes skip their weight
+    copies and their bounded waits run out (ALLEGRO_E_TIMEOUT)."""
+    _check(None, lib().allegro_debug_inject_wait_timeout(int(bool(enable))))

@@ -662,8 +662,9 @@ int build_with_growth(allegro_ctx* c, const double* d_positions, int64_t n, int6
     }
     const int rc = ensure_pairs(c, (int64_t)np + np / 4 + 1024);
     if (rc) return rc;
-    const int cleared = flags & ~kFlagPairOverflow;
-    cudaMemcpy(c->nb.flags, &cleared, sizeof(int), cudaMemcpyHostToDevice);
+    // every other bit returned above, so clearing the word on the library
+    // stream orders the clear before the rebuild's atomicOr
+    cudaMemsetAsync(c->nb.flags, 0, sizeof(int), c->stream);
   }
   return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown");
 }
@@ -1068,6 +1069,7 @@ int loss_grad_impl(allegro_ctx* c, double w_energy, double w_force, double* loss
   cudaMemcpyAsync(&loss, t.loss, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&flags, c->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "loss gradient");
+  if (flags & kFlagTimeout) return c->fail(ALLEGRO_E_TIMEOUT, "a pass gave up a bounded wait");
   if (flags & kFlagPairOverflow) return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "training batch exceeds the pair capacity");
   if (loss_out) *loss_out = loss;
   return ALLEGRO_OK;
@@ -1207,6 +1209,7 @@ int allegro_energy_forces(allegro_ctx* ctx, int64_t n_atoms, const double* posit
   if (!rc) rc = copy_out(ctx, atom_energy, ctx->d_Ei, sizeof(double) * n_atoms);
   if (rc) return rc;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "energy_forces");
+  if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait");
   if (flags & kFlagNonfinite) return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite energy or force");
   *energy_out = stats[0];
   return ALLEGRO_OK;
@@ -1413,11 +1416,12 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
     cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "md steps");
-    if (flags & kFlagPairOverflow) {
+    if (flags & (kFlagPairOverflow | kFlagTimeout)) {
       cudaMemcpyAsync(ctx->d_pos, ctx->d_pos_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->d_v, ctx->d_v_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->d_F, ctx->d_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaStreamSynchronize(ctx->stream);
+      if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait (state rolled back)");
       const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024;
       int rc = ensure_pairs(ctx, grow);
       if (rc) return rc;
@@ -1463,12 +1467,13 @@ int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double 
     cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "nvt steps");
-    if (flags & kFlagPairOverflow) {
+    if (flags & (kFlagPairOverflow | kFlagTimeout)) {
       cudaMemcpyAsync(ctx->d_pos, ctx->d_pos_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->d_v, ctx->d_v_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->d_F, ctx->d_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->d_nh, ctx->d_nh_snap, sizeof(double) * 4, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaStreamSynchronize(ctx->stream);
+      if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait (state rolled back)");
       const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024;
       rc = ensure_pairs(ctx, grow);
       if (rc) return rc;
@@ -1666,6 +1671,7 @@ int allegro_pimd_init(allegro_ctx* ctx, int32_t n_beads, int64_t n_atoms, const 
     cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(ctx, "pimd_init");
+    if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait");
     if (flags & kFlagBadSpecies) return ctx->fail(ALLEGRO_E_INVALID_ARG, "species id out of range");
     if (flags & kFlagNonfinite) return ctx->fail(ALLEGRO_E_NONFINITE, "non-finite bead position or force");
     if (!(flags & kFlagPairOverflow)) {
@@ -1706,11 +1712,12 @@ int allegro_pimd_step(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double* e
     cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&np, ctx->nb.n_pairs, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(ctx, "pimd steps");
-    if (flags & kFlagPairOverflow) {
+    if (flags & (kFlagPairOverflow | kFlagTimeout)) {
       cudaMemcpyAsync(ctx->d_rp_q, ctx->d_rp_q_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(ctx->d_rp_v, ctx->d_rp_v_snap, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(ctx->d_rp_F, ctx->d_rp_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, s);
       cudaStreamSynchronize(s);
+      if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait (state rolled back)");
       rc = ensure_pairs(ctx, std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024);
       if (rc) return rc;
       continue;
@@ -1882,6 +1889,7 @@ int allegro_loss_scan(allegro_ctx* ctx, const allegro_batch* batch, const float*
   cudaMemcpyAsync(&flags, ctx->nb.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return rc ? rc : cuda_check(ctx, "loss_scan");
   if (rc) return rc;
+  if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a pass gave up a bounded wait");
   if (flags & kFlagPairOverflow) return ctx->fail(ALLEGRO_E_PAIR_OVERFLOW, "training batch exceeds the pair capacity");
   return ALLEGRO_OK;
 }
@@ -1909,6 +1917,10 @@ int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n) {
   ctx->drop_graphs();
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "set_weights");
   return ALLEGRO_OK;
+}
+
+int allegro_debug_inject_wait_timeout(int32_t enable) {
+  return al::bf16_inject_wait_timeout(enable) == 0 ? ALLEGRO_OK : ALLEGRO_E_CUDA;
 }
 
 }  // extern "C"

@@ -116,6 +116,11 @@ struct BfW {
 
 bool bf16_supported(int lmax, int C, int D, int E, int L);
 int bf16_tile();
+// Failure injection for tests (current device): enable != 0 makes every
+// tensor-core pass skip its weight copies and wait at most 2^20 cycles for
+// them, so each pass raises the timeout flag with nothing in flight;
+// enable == 0 restores the copies and the 2^31-cycle limit.  0 on success.
+int bf16_inject_wait_timeout(int enable);
 // Optional launch timing: mark(kind) records an event on the stream after a
 // pass kernel, tagged with its kind; interval i lies between event i and
 // event i + 1 and belongs to kind[i + 1].

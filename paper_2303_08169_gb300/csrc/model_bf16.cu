@@ -35,6 +35,14 @@ namespace {
 
 using namespace umma;
 
+// Limit of every bounded mbarrier wait (clock cycles) and the failure
+// injection of the failure-detection tests: when c_no_weight_copies is set,
+// no kernel issues its weight copies, so the weight barrier's wait runs out
+// (nothing is in flight), the kernel skips its MMAs and raises the timeout
+// flag that the host turns into ALLEGRO_E_TIMEOUT.
+__constant__ long long c_wait_cycles = 1ll << 31;
+__constant__ int c_no_weight_copies = 0;
+
 constexpr int kT = 128;
 // threads of a CTA: thread t owns tile row r = t % 128 (its TMEM lane) and
 // column quarter h = t / 128 of every epilogue (16 warps per SM)
@@ -389,7 +397,7 @@ struct Mma {
         issue();
         mma_commit(bar);
       }
-      if (!mbar_wait(bar, phase)) *err = 1;
+      if (!mbar_wait(bar, phase, c_wait_cycles)) *err = 1;
       phase ^= 1u;
     }
     tc_fence_after();
@@ -537,11 +545,11 @@ AL_DEV uint8_t* align1024(uint8_t* p) {
   __syncthreads();                                                                \
   tc_fence_after();                                                               \
   const uint32_t tmem = tslot;                                                    \
-  if (threadIdx.x == 0) {                                                         \
+  if (threadIdx.x == 0 && !c_no_weight_copies) {                                 \
     mbar_expect_tx(&bars[1], (WBYTES));                                           \
     LOADS;                                                                        \
   }                                                                               \
-  if (!mbar_wait(&bars[1], 0)) err = 1;                                           \
+  if (!mbar_wait(&bars[1], 0, c_wait_cycles)) err = 1;                            \
   __syncthreads();                                                                \
   Mma mm{&bars[0], 0u, &err};                                                     \
   const int P = (int)min((int64_t)*b.n_pairs, b.capacity);                        \
@@ -1700,6 +1708,15 @@ bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
 }
 
 int bf16_tile() { return kT; }
+
+int bf16_inject_wait_timeout(int enable) {
+  const long long cycles = enable ? (1ll << 20) : (1ll << 31);
+  const int skip = enable ? 1 : 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;   // no pass kernel in flight
+  if (cudaMemcpyToSymbol(c_wait_cycles, &cycles, sizeof(cycles)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_no_weight_copies, &skip, sizeof(skip)) != cudaSuccess) return -1;
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
+}
 
 void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km,
                         TcMode mode) {

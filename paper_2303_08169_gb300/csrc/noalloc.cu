@@ -1,7 +1,5 @@
 // noalloc.cu - the >5 sigma force-outlier count without any device
 // allocation, for callers that cannot allocate device memory:
-//   * code that runs while a CUDA graph is being captured on its stream
-//     (cudaMalloc is not a stream operation and is rejected in capture);
 //   * applications whose own allocator owns all device memory (a framework
 //     pool or a fixed memory budget), where a foreign cudaMalloc fails or
 //     fragments their pool;
@@ -33,7 +31,33 @@ constexpr size_t kNaScratchBytes = (size_t)kNaMaxBlocks * 8 * 2 + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
 
 std::mutex g_mu;
+// per device: the scratch address and the CUDA context it was looked up in
+// (a reset device or another context on the same ordinal loads the module
+// again, possibly at another address)
 void* g_scratch_ptr[kNaMaxDevices] = {};
+void* g_scratch_ctx[kNaMaxDevices] = {};
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link-time
+// dependency on the driver library); null if unavailable.
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static const CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
+void* current_context() {
+  void* c = nullptr;
+  const CtxGetCurrentFn fn = ctx_get_current();
+  if (!fn || fn(&c) != 0) return nullptr;
+  return c;
+}
 
 __global__ void k_na_sumsq(int n, const float* __restrict__ F, double* __restrict__ part) {
   __shared__ double sh[kNaBlock / 32];
@@ -97,7 +121,8 @@ __global__ void k_na_final(const unsigned long long* __restrict__ cnt, int nblk,
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device (host code may not use the symbol itself as a device pointer).
+// per device and context (host code may not use the symbol itself as a
+// device pointer).
 int scratch_ptr(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -109,7 +134,8 @@ int scratch_ptr(unsigned char** out) {
     return ALLEGRO_E_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  void* ctx = current_context();
+  if (!g_scratch_ptr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -118,6 +144,7 @@ int scratch_ptr(unsigned char** out) {
       return ALLEGRO_E_CUDA;
     }
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = current_context();   // the lookup made the context current if it was not
   }
   *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
   return ALLEGRO_OK;
@@ -135,6 +162,14 @@ extern "C" int allegro_outlier_count_noalloc(int64_t n_atoms, const float* force
     al::set_global_error("outlier_count_noalloc: n_atoms must be in [1, 4194304] (fixed scratch size)");
     return ALLEGRO_E_INVALID_ARG;
   }
+  // an error left by the caller's own earlier work stays the caller's: report
+  // it without clearing it, and launch nothing
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    al::set_global_error(std::string("outlier_count_noalloc: a CUDA error from earlier work is pending: ") +
+                         cudaGetErrorString(pending));
+    return ALLEGRO_E_CUDA;
+  }
   unsigned char* base = nullptr;
   const int rc = scratch_ptr(&base);
   if (rc) return rc;
@@ -148,7 +183,7 @@ extern "C" int allegro_outlier_count_noalloc(int64_t n_atoms, const float* force
   k_na_total<<<1, kNaBlock, 0, s>>>(part, nblk, total);
   k_na_count<<<nblk, kNaBlock, 0, s>>>(n, forces, threshold, total, cnt);
   k_na_final<<<1, kNaBlock, 0, s>>>(cnt, nblk, reinterpret_cast<long long*>(count_out));
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();   // no error was pending before the launches: this one is ours
   if (e != cudaSuccess) {
     al::set_global_error(std::string("outlier_count_noalloc: ") + cudaGetErrorString(e));
     return ALLEGRO_E_CUDA;

@@ -113,12 +113,13 @@ UM_DEV bool mbar_try_wait(uint64_t* m, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait (about 2^31 clock cycles, ~1 s): returns false and leaves the
-// barrier alone if the phase never completes; the caller records an error.
-UM_DEV bool mbar_wait(uint64_t* m, uint32_t phase) {
+// Bounded wait (by default about 2^31 clock cycles, ~1 s): returns false and
+// leaves the barrier alone if the phase never completes; the caller records
+// an error.
+UM_DEV bool mbar_wait(uint64_t* m, uint32_t phase, long long limit = 1ll << 31) {
   const long long t0 = clock64();
   while (!mbar_try_wait(m, phase)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }

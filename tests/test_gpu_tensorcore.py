@@ -134,3 +134,39 @@ def test_tensorcore_three_layers(mode):
     d = F - Fe
     assert np.abs(d).max() <= tol["fmax"] and np.sqrt(np.mean(d * d)) <= tol["frms"]
     assert np.abs(F - Fr).max() <= 2 * tol["fmax"]     # one more layer of operand rounding
+
+
+def test_tensorcore_wait_timeout_is_reported(main):
+    """Failure detection without a GPU fault: with the weight copies of the
+    tensor-core passes withheld (nothing in flight), their bounded mbarrier
+    waits run out; the entry points must report ALLEGRO_E_TIMEOUT instead of
+    returning stale energies, the MD step must restore its starting state, and
+    the context must work normally once the injection is lifted."""
+    ctx, blob = main
+    pos, sp, cell = synth.make_ammonia(108, 0)
+    E0, F0, _ = _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP16_SPLIT)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    try:
+        al.allegro_debug_inject_wait_timeout(True)
+        with pytest.raises(al.AllegroError) as err:
+            _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP16_SPLIT)
+        assert err.value.code == 8
+        al.allegro_debug_inject_wait_timeout(False)
+        al.allegro_set_md_precision(ctx, al.ALLEGRO_FP16_SPLIT)
+        al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+        al.allegro_md_step_nve(ctx, 0.25, 2)
+        r1, v1 = np.zeros_like(pos), np.zeros_like(pos)
+        step1 = al.allegro_md_get_state(ctx, r1, v1)
+        al.allegro_debug_inject_wait_timeout(True)
+        with pytest.raises(al.AllegroError) as err:
+            al.allegro_md_step_nve(ctx, 0.25, 3)
+        assert err.value.code == 8
+    finally:
+        al.allegro_debug_inject_wait_timeout(False)
+    r2, v2 = np.zeros_like(pos), np.zeros_like(pos)
+    step2 = al.allegro_md_get_state(ctx, r2, v2)
+    assert step2 == step1 and np.array_equal(r1, r2) and np.array_equal(v1, v2)
+    al.allegro_md_step_nve(ctx, 0.25, 1)                  # the MD state still steps
+    al.allegro_set_md_precision(ctx, al.ALLEGRO_FP32)
+    E1, F1, _ = _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP16_SPLIT)
+    assert E1 == E0 and np.array_equal(F1, F0)

@@ -1,6 +1,6 @@
 """The allocation-free outlier count (allegro_outlier_count_noalloc), for
-callers that cannot allocate device memory (graph capture, a foreign
-allocator owning the device, latency-bound loops), against the context-based
+callers that cannot allocate device memory (a foreign allocator owning the
+device, latency-bound loops), against the context-based
 allegro_outlier_count on the same forces.  Integer counts must agree exactly,
 on two calls in a row (the shared scratch keeps the previous call's contents
 and must not leak into the next result).  Collected last on purpose."""
