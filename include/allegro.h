@@ -406,6 +406,17 @@ int allegro_selftest_mma(int32_t n, int32_t k, const float* a, const float* b, f
 int allegro_selftest_mma_mode(int32_t n, int32_t k, const float* a, const float* b, float* d, int32_t mode);
 
 /*
+ * Diagnostic (not part of the paper's method): SiLU(x) = x sigmoid(x) and its
+ * derivative as the tensor-core passes compute them, sigmoid(x) =
+ * 1/2 + tanh(x/2)/2 with the tanh.approx.f32 instruction, for checking their
+ * error against a host reference (the error model of the tensor-core tests
+ * rests on it).  x: device, n FP32; y: device, 2n FP32, y[2i] = SiLU(x[i]),
+ * y[2i+1] = SiLU'(x[i]).  0 <= n <= 2^30, else ALLEGRO_E_INVALID_ARG.  Runs on
+ * the legacy default stream and synchronises.
+ */
+int allegro_selftest_silu(int64_t n, const float* x, float* y);
+
+/*
  * Failure injection for the failure-detection tests (not part of the paper's
  * method).  Every wait of the tensor-core passes on an mbarrier is bounded;
  * when one gives up, the pass skips its remaining MMAs, frees its tensor

@@ -56,21 +56,64 @@ def envelope(d, r_cut, p=6):
     return 1.0 - a * x ** p + b * x ** (p + 1) - c * x ** (p + 2)
 
 
+def round_to(x, dtype):
+    """x rounded to the floating-point type dtype (round to nearest, ties to
+    even, as every conversion here does), returned in float64."""
+    return x.to(dtype).to(F64)
+
+
+class RoundedLinear(torch.autograd.Function):
+    """Emulated tensor-core GEMM y = q(x) q(Ws)^T, accumulated in float64, with
+    q(.) the operand rounding and Ws the weight matrix with its scale folded
+    in.  Its adjoint (the input-gradient GEMM) rounds its operands the same
+    way: dx = q(dy) q(Ws).  The weight gradient is left exact."""
+
+    @staticmethod
+    def forward(ctx, x, Ws, q_x, q_w, q_adj):
+        xq, Wq = q_x(x), q_w(Ws)
+        ctx.save_for_backward(xq, Wq)
+        ctx.q_adj = q_adj
+        return xq @ Wq.T
+
+    @staticmethod
+    def backward(ctx, g):
+        xq, Wq = ctx.saved_tensors
+        return ctx.q_adj(g) @ Wq, g.T @ xq, None, None, None
+
+
 class OracleModel:
-    """emulate: None (exact FP64), "bf16", "fp16" or "fp16split".  With
-    emulation, every per-pair GEMM (two-body, embedding, env, mixing, latent
-    and energy hidden layers) rounds its input and its pre-scaled weight
-    matrix (1/sqrt(fan_in), and 1/sqrt(nu) for env, folded in first) to that
-    type and accumulates in FP64: the operand precision of the tensor-core
-    path, used to check that path separately from the sensitivity of the
-    model to rounding.  "fp16split" is "fp16" with the two-body MLP and the
-    energy hidden layer left unrounded (the tensor-core path splits their
-    operands into two FP16 parts, which carry about 22 bits).  In every
-    emulation mode the per-pair values that the tensor-core path keeps in
-    FP16 between its passes (x^k and the tensor-product scalars of layers
-    k < L, V^k) are rounded to FP16 in the forward direction only (their
-    gradients stay FP32 there).  The energy output layer, tensor products and
-    all elementwise steps stay FP64."""
+    """emulate: None (exact FP64), "bf16", "fp16" or "fp16split".
+
+    Emulation models the operand precision of the tensor-core path, so that
+    the kernels can be checked separately from the sensitivity of the model to
+    rounding:
+      * every per-pair GEMM (two-body, embedding, env, mixing, latent and
+        energy hidden layers) is a RoundedLinear: its input and its pre-scaled
+        weight matrix (1/sqrt(fan_in), and 1/sqrt(nu) for env, folded in
+        first) are rounded to op_dtype and accumulated in FP64, and its
+        adjoint GEMM rounds the incoming gradient to op_dtype as well;
+      * "fp16split" is "fp16" with the GEMMs of the groups in exact_groups
+        (the two-body MLP and the energy hidden layer) left unrounded: the
+        tensor-core path splits their operands into two FP16 parts, which
+        carry about 22 bits;
+      * the per-pair values that the tensor-core path keeps between its passes
+        (x^k and the tensor-product scalars of layers k < L, and V^k) are
+        rounded to store_dtype (FP16) in the forward direction only: the
+        gradient passes through unchanged (straight-through), as the path keeps
+        gradients in FP32;
+      * the energy output layer, the tensor products and every elementwise
+        step stay FP64.
+    op_dtype, adj_dtype, store_dtype and exact_groups are plain attributes, so
+    that tests can substitute them (float64 makes every rounding an identity).
+    perturb_silu(z), perturb_value(x), perturb_grad(g) and perturb_split(a),
+    None by default, are hooks for a perturbation analysis: the first returns
+    an additive perturbation of SiLU(z), the second a perturbed copy of a
+    forward value about to be rounded (a GEMM input or a stored value), the
+    third a perturbed copy of an adjoint-GEMM gradient operand about to be
+    rounded, the fourth a perturbed copy of an operand (input or pre-scaled
+    weight) of a GEMM of the exact groups.  Rounded weights are never
+    perturbed; the hooks change forward values only (gradients pass
+    through)."""
 
     def __init__(self, blob, emulate=None):
         cfg, w, names = read_blob(blob)
@@ -90,24 +133,62 @@ class OracleModel:
         if emulate not in (None, "bf16", "fp16", "fp16split"):
             raise ValueError("emulate must be None, 'bf16', 'fp16' or 'fp16split'")
         self.emulate = emulate
-        self._qdt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp16split": torch.float16}.get(emulate)
-        self._split = emulate == "fp16split"
+        self.op_dtype = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp16split": torch.float16}.get(emulate)
+        self.adj_dtype = self.op_dtype
+        self.store_dtype = torch.float16 if emulate else None
+        self.exact_groups = {"twobody", "energy"} if emulate == "fp16split" else set()
+        self.perturb_silu = None
+        self.perturb_value = None
+        self.perturb_grad = None
+        self.perturb_split = None
 
-    def _q(self, x):
-        return x if self._qdt is None else x.to(self._qdt).to(F64)
+    def _pre(self, x, hook=None):
+        """A value about to be rounded, with a perturbation hook applied."""
+        hook = self.perturb_value if hook is None else hook
+        if hook is None:
+            return x
+        with torch.no_grad():
+            return hook(x.detach())
+
+    def _q_op(self, x):
+        return round_to(self._pre(x), self.op_dtype)
+
+    def _q_w(self, W):
+        return round_to(W, self.op_dtype)
+
+    def _q_adj(self, g):
+        if self.perturb_grad is not None:
+            g = self._pre(g, self.perturb_grad)
+        return round_to(g, self.adj_dtype)
 
     def _qs(self, x):
-        """Emulation: FP16 storage of a forward value (gradient unchanged)."""
-        if self._qdt is None:
+        """Emulation: storage of a forward value in store_dtype (gradient
+        passes through unchanged)."""
+        if self.store_dtype is None:
             return x
-        return x + (x.to(torch.float16).to(F64) - x).detach()
+        return x + (round_to(self._pre(x), self.store_dtype) - x).detach()
 
-    def _qlin(self, x, W, extra=1.0):
-        """Linear layer; in emulation mode the GEMM operands are rounded."""
-        if self._qdt is None:
-            return self._lin(x, W)
+    def _act(self, z):
+        a = silu(z)
+        if self.perturb_silu is not None:
+            with torch.no_grad():
+                d = self.perturb_silu(z.detach())
+            a = a + d
+        return a
+
+    def _qlin(self, x, W, extra=1.0, group=None):
+        """Linear layer; emulated as a RoundedLinear unless exact."""
+        if self.op_dtype is None or group in self.exact_groups:
+            if self.perturb_split is not None and group in self.exact_groups:
+                s = extra / math.sqrt(W.shape[1])
+                with torch.no_grad():
+                    dx = self.perturb_split(x.detach()) - x.detach()
+                    Ws = W.detach() * s
+                    dW = self.perturb_split(Ws) - Ws
+                return (x + dx) @ (W * s + dW).T
+            return self._lin(x, W) if extra == 1.0 else self._lin(x, W) * extra
         s = extra / math.sqrt(W.shape[1])
-        return self._q(x) @ self._q(W * s).T
+        return RoundedLinear.apply(x, W * s, self._q_op, self._q_w, self._q_adj)
 
     # ------------------------------------------------------------------ helpers
     def params(self):
@@ -118,11 +199,11 @@ class OracleModel:
     def _lin(x, W):
         return x @ W.T / math.sqrt(W.shape[1])
 
-    def _mlp(self, x, Ws, last_act=True, exact=False):
+    def _mlp(self, x, Ws, last_act=True, group=None):
         for k, W in enumerate(Ws):
-            x = self._lin(x, W) if exact else self._qlin(x, W)
+            x = self._qlin(x, W, group=group)
             if last_act or k + 1 < len(Ws):
-                x = silu(x)
+                x = self._act(x)
         return x
 
     # ------------------------------------------------------------------ model
@@ -160,15 +241,15 @@ class OracleModel:
         onehot = torch.eye(S, dtype=F64)
         h = torch.cat([onehot[Z[i]], onehot[Z[j]], B], dim=1)
         nlat = len(cfg["latent"])
-        x = self._qs(fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)], exact=self._split))
-        w0 = self._qlin(x, w["embed"]).view(P, C, lmax + 1)
+        x = self._qs(fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)], group="twobody"))
+        w0 = self._qlin(x, w["embed"], group="embed").view(P, C, lmax + 1)
         V = [w0[:, :, l, None] * Y[l][:, None, :] for l in range(lmax + 1)]
         for layer in range(1, self.L + 1):
             last = layer == self.L
-            if self._qdt is None:
+            if self.op_dtype is None:
                 e = self._lin(x, w[f"layer{layer}.env"]) / math.sqrt(self.nu)   # (P, C)
             else:
-                e = self._qlin(x, w[f"layer{layer}.env"], 1.0 / math.sqrt(self.nu))
+                e = self._qlin(x, w[f"layer{layer}.env"], 1.0 / math.sqrt(self.nu), group="env")
             G = []
             for l in range(lmax + 1):
                 contrib = e[:, :, None] * Y[l][:, None, :]
@@ -189,21 +270,24 @@ class OracleModel:
                     Tl = torch.stack([T[p] for p in ps], dim=2)        # (P, C, Pl, 2l3+1)
                     Tl = Tl.reshape(P, C * len(ps), 2 * l3 + 1)
                     Wm = w[f"layer{layer}.mix{l3}"]
-                    if self._qdt is None:
+                    if self.op_dtype is None:
                         newV.append(torch.einsum("oi,pim->pom", Wm, Tl) / math.sqrt(C * len(ps)))
                     else:
-                        Wq = self._q(Wm / math.sqrt(C * len(ps)))
-                        newV.append(torch.einsum("oi,pim->pom", Wq, self._q(Tl)))
+                        # one GEMM over the (pair, m) rows of the K = C P_l3 inputs
+                        nm = 2 * l3 + 1
+                        rows = Tl.permute(0, 2, 1).reshape(P * nm, C * len(ps))
+                        out = self._qlin(rows, Wm, group="mix")
+                        newV.append(out.reshape(P, nm, C).permute(0, 2, 1))
                 V = [self._qs(v) for v in newV]
             if not last:
                 s = self._qs(s)
             m = self._mlp(torch.cat([x, s], dim=1),
-                          [w[f"layer{layer}.latent.{k}"] for k in range(nlat)])
+                          [w[f"layer{layer}.latent.{k}"] for k in range(nlat)], group="latent")
             x = (x + fc[:, None] * m) / math.sqrt(2.0)
             if not last:
                 x = self._qs(x)
         ne = len(cfg["energy"])
-        hdn = self._mlp(x, [w[f"energy.{k}"] for k in range(ne)], exact=self._split)
+        hdn = self._mlp(x, [w[f"energy.{k}"] for k in range(ne)], group="energy")
         Eij = self._lin(hdn, w["energy.out"])[:, 0]
         Esum = torch.zeros(N, dtype=F64).index_add(0, i, Eij)
         return sig * Esum + mu

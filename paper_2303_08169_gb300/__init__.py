@@ -34,7 +34,7 @@ EXPORTED = [
     "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
     "allegro_loss_scan", "allegro_md_step_nvt", "allegro_md_get_thermostat",
     "allegro_pimd_init", "allegro_pimd_step", "allegro_pimd_get_state",
-    "allegro_debug_inject_wait_timeout",
+    "allegro_debug_inject_wait_timeout", "allegro_selftest_silu",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -103,6 +103,7 @@ def lib():
         "allegro_get_weights": ([_vp, _vp, _i64], ctypes.c_int),
         "allegro_set_weights": ([_vp, _vp, _i64], ctypes.c_int),
         "allegro_debug_inject_wait_timeout": ([_i32], ctypes.c_int),
+        "allegro_selftest_silu": ([_i64, _vp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -332,3 +333,9 @@ def allegro_debug_inject_wait_timeout(enable):
     """Failure injection for tests: the tensor-core passes skip their weight
     copies and their bounded waits run out (ALLEGRO_E_TIMEOUT)."""
     _check(None, lib().allegro_debug_inject_wait_timeout(int(bool(enable))))
+
+
+def allegro_selftest_silu(x, y):
+    """y[2i], y[2i+1] = SiLU(x[i]), SiLU'(x[i]) as the tensor-core passes
+    compute them (device tensors: x n FP32, y 2n FP32)."""
+    _check(None, lib().allegro_selftest_silu(int(x.numel()), _ptr(x), _ptr(y)))

@@ -136,14 +136,12 @@ struct TrainBatch {
   int64_t cap_atoms = 0, cap_pairs = 0;
   int cap_structs = 0;
   int* d_np = nullptr;          // device copy of n_pairs
-  double* wdisp = nullptr;      // displaced positions (N x 3)
-  float* v = nullptr;           // dL/dF (N x 3)
-  float* seed = nullptr;        // dL/dE_i of the current evaluation (N)
+  float* v = nullptr;           // dL/dF (N x 3): the position direction of the tangent passes
+  float* seed = nullptr;        // energy-loss seeds dL/dE_i (N)
   float* f_target = nullptr;    // N x 3
   int64_t* atom_off = nullptr;  // n_structs + 1
   double* e_target = nullptr;
   double* dE = nullptr;         // E_b - E*_b
-  unsigned* vmax = nullptr;     // max |v| per structure (float bits)
   double* loss_blk = nullptr;
   double* loss = nullptr;
 };
@@ -162,6 +160,18 @@ struct allegro_ctx {
   bool tc_dirty = false;       // tensor-core images lag behind d_master
   TrainBufs tr{};
   int64_t tr_cap = 0;
+  // second-order adjoint: tangent dumps (trt), the tangent passes' per-pair
+  // and per-(tile, atom) arrays of Dual values, and the per-chunk partials of
+  // the weight-gradient reductions
+  TrainBufs trt{};
+  float* tX[kMaxLayers] = {};
+  float* tV[kMaxLayers] = {};
+  float *tdX = nullptr, *tdV = nullptr, *tdU = nullptr, *tdY = nullptr, *tG = nullptr;
+  float* tgam[kMaxLayers + 1] = {};
+  float* tdgam[kMaxLayers + 1] = {};
+  double* tepart = nullptr;
+  float* wpart = nullptr;
+  int64_t tr_rows = 0;
   cudaStream_t stream = nullptr;
   Blob blob;
   double mass[2] = {14.007, 1.008};
@@ -182,6 +192,14 @@ struct allegro_ctx {
   int ncell_alloc = 0;
   int64_t capacity = 0;
   int64_t part_rows = 0;
+  // Per-pair arrays at the width of the FP32 passes (FP32 x^k, V^k, dV,
+  // 32-pair tiles of per-atom partials) or of the tensor-core passes only
+  // (FP16 pairs: half the words, 128-pair tiles): want_fp32 is set for good
+  // by the first call that may run the FP32 passes, pb_fp32 says what is
+  // allocated, and fp32_bad records an FP32 launch refused on narrow arrays.
+  bool want_fp32 = false;
+  bool pb_fp32 = false;
+  bool fp32_bad = false;
   NeighborBuffers nb{};
   GridInfo grid{};
   PassBufs pb{};
@@ -287,6 +305,10 @@ namespace {
 int cuda_check(allegro_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return c->fail(ALLEGRO_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  if (c->fp32_bad) {
+    c->fp32_bad = false;
+    return c->fail(ALLEGRO_E_CUDA, std::string(where) + ": internal error, FP32 passes on tensor-core-width buffers");
+  }
   return ALLEGRO_OK;
 }
 
@@ -527,9 +549,10 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   const Blob& B = c->blob;
   const int NLM = (B.lmax + 1) * (B.lmax + 1);
   const int CL = B.C * NLM;
-  const int tile = fp32_tile();
+  const bool full = c->want_fp32 || !c->bf16_ok;
+  const int tile = full ? fp32_tile() : bf16_tile();
   const int64_t rows_needed = cap / tile + 2 + c->n_atoms_alloc;
-  if (cap <= c->capacity && rows_needed <= c->part_rows) return ALLEGRO_OK;
+  if (cap <= c->capacity && rows_needed <= c->part_rows && (c->pb_fp32 || !full)) return ALLEGRO_OK;
   if (cap > (int64_t)0x7fffffff - 1024) return c->fail(ALLEGRO_E_UNSUPPORTED, "more than 2^31 pairs");
   PassBufs& pb = c->pb;
   for (void* p : {(void*)c->nb.pi, (void*)c->nb.pj, (void*)c->nb.pcode, (void*)c->nb.rev, (void*)c->nb.keys,
@@ -559,16 +582,20 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   c->nb.keys = c->dalloc<unsigned long long>(capr);
   c->nb.skeys = c->dalloc<unsigned long long>(capr);
   bool ok = c->nb.pi && c->nb.pj && c->nb.pcode && c->nb.rev && c->nb.keys && c->nb.skeys;
+  // x^k, V^k and dV: FP32 rows for the FP32 passes, FP16 (or 16-bit operand)
+  // pairs, half the words, for the tensor-core passes
+  const size_t xw = full ? (size_t)c->D : (size_t)c->D / 2;
+  const size_t vw = full ? (size_t)CL : (size_t)CL / 2;
   for (uint32_t k = 0; k < B.L && ok; ++k) {
-    pb.X[k] = c->dalloc<float>((size_t)capr * c->D);
+    pb.X[k] = c->dalloc<float>((size_t)capr * xw);
     ok = ok && pb.X[k];
     if (k >= 1) {
-      pb.V[k] = c->dalloc<float>((size_t)capr * CL);
+      pb.V[k] = c->dalloc<float>((size_t)capr * vw);
       ok = ok && pb.V[k];
     }
   }
   pb.dX = c->dalloc<float>((size_t)capr * c->D);
-  pb.dV = c->dalloc<float>((size_t)capr * CL);
+  pb.dV = c->dalloc<float>((size_t)capr * vw);
   pb.dU = c->dalloc<float>(capr);
   pb.dY = c->dalloc<float>((size_t)capr * NLM);
   pb.G = c->dalloc<float>((size_t)capr * 3);
@@ -579,9 +606,9 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   c->dfree(pb.dR);
   pb.dR = nullptr;
   if (c->bf16_ok) {
-    const int NSC = B.C * 3;
+    const int NSC = B.C * 3;                          // layer scalars, FP16 pairs
     for (uint32_t k = 1; k < B.L && ok; ++k) {
-      pb.S[k] = c->dalloc<float>((size_t)capr * NSC);
+      pb.S[k] = c->dalloc<float>((size_t)capr * (NSC / 2));
       ok = ok && pb.S[k];
     }
     pb.dR = c->dalloc<float>((size_t)capr * 3);
@@ -607,7 +634,17 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   c->capacity = cap;
   c->nb.capacity = cap;
   c->part_rows = rows;
+  c->pb_fp32 = full;
   c->drop_graphs();
+  return ALLEGRO_OK;
+}
+
+// Called by every entry point that may run the FP32 passes, before it
+// allocates: from now on the per-pair arrays are allocated at FP32 width
+// (reallocated now if they exist at tensor-core width).
+int require_fp32(allegro_ctx* c) {
+  c->want_fp32 = true;
+  if (c->capacity > 0 && !c->pb_fp32) return ensure_pairs(c, c->capacity);
   return ALLEGRO_OK;
 }
 
@@ -696,8 +733,8 @@ int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* s
     const double est = (double)n * (4.18879 * rc3 * (double)n / vol) * 1.3 + 4096.0;
     rc = ensure_pairs(c, (int64_t)std::min(est, 2.0e9));
     if (rc) return rc;
-  } else if (c->part_rows < c->capacity / fp32_tile() + 2 + c->n_atoms_alloc) {
-    rc = ensure_pairs(c, c->capacity);
+  } else {
+    rc = ensure_pairs(c, c->capacity);               // partial rows follow N (no-op when nothing changed)
     if (rc) return rc;
   }
   return cuda_check(c, "prepare");
@@ -721,7 +758,8 @@ void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, KernelMarks
     bf16_energy_forces(c->sw, c->pb, c->capacity, s, km, TcMode::kFp16Split);
     tile = bf16_tile();
   } else {
-    fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km);
+    if (c->pb_fp32) fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km);
+    else c->fp32_bad = true;
     tile = fp32_tile();
   }
   launch_forces(atom_args(c), c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, tile, c->d_F, c->d_Ei, c->d_blk,
@@ -822,61 +860,105 @@ int tp_toff(int lmax, int l) { return lmax == 0 ? tp0_toff(l) : lmax == 1 ? tp1_
 
 int ensure_train(allegro_ctx* c) {
   const int64_t cap = c->capacity;
-  if (cap <= c->tr_cap) return ALLEGRO_OK;
+  const int64_t rows = cap / fp32_tangent_tile() + 2 + c->n_atoms_alloc;
+  if (cap <= c->tr_cap && rows <= c->tr_rows) return ALLEGRO_OK;
   const Blob& B = c->blob;
   const int D = c->D, C = (int)B.C, E = c->E, L = (int)B.L;
   const int NS = tp_ns((int)B.lmax), NT = tp_nt((int)B.lmax);
   const int NW0 = C * ((int)B.lmax + 1);
-  TrainBufs& t = c->tr;
-  auto re = [&](float*& p, size_t w) {
+  const int NLM = ((int)B.lmax + 1) * ((int)B.lmax + 1), CL = C * NLM;
+  auto re = [&](float*& p, size_t n) {
     c->dfree(p);
-    p = c->dalloc<float>((size_t)cap * w);
+    p = c->dalloc<float>(n);
     return p != nullptr;
   };
-  bool ok = re(t.h0, 16) && re(t.a1_tb, D) && re(t.dz1_tb, D) && re(t.dz2_tb, D) && re(t.dw0, NW0) &&
-            re(t.xL, D) && re(t.ae, E) && re(t.dze, E) && re(t.dEij, 1);
-  for (int j = 0; j < L && ok; ++j) ok = re(t.de[j], C);
-  for (int k = 1; k <= L && ok; ++k)
-    ok = re(t.s[k], C * NS) && re(t.a1_l[k], D) && re(t.dz1_l[k], D) && re(t.dz2_l[k], D) &&
-         (k == L || re(t.T[k], C * NT));
-  if (!ok) return c->fail(ALLEGRO_E_OOM, "training dump allocation failed");
+  bool ok = true;
+  for (TrainBufs* t : {&c->tr, &c->trt}) {          // values and tangents of the dumps
+    ok = ok && re(t->h0, cap * 16) && re(t->a1_tb, cap * D) && re(t->dz1_tb, cap * D) && re(t->dz2_tb, cap * D) &&
+         re(t->dw0, cap * NW0) && re(t->xL, cap * D) && re(t->ae, cap * E) && re(t->dze, cap * E) &&
+         re(t->dEij, cap);
+    for (int j = 0; j < L && ok; ++j) ok = re(t->de[j], cap * C);
+    for (int k = 1; k <= L && ok; ++k)
+      ok = re(t->s[k], cap * C * NS) && re(t->a1_l[k], cap * D) && re(t->dz1_l[k], cap * D) &&
+           re(t->dz2_l[k], cap * D) && (k == L || re(t->T[k], cap * C * NT));
+  }
+  // tangent passes: every array holds Dual values (two floats each)
+  for (int k = 0; k < L && ok; ++k) ok = re(c->tX[k], 2 * cap * D) && (k == 0 || re(c->tV[k], 2 * cap * CL));
+  ok = ok && re(c->tdX, 2 * cap * D) && re(c->tdV, 2 * cap * CL) && re(c->tdU, 2 * cap) &&
+       re(c->tdY, 2 * cap * NLM) && re(c->tG, 2 * cap * 3);
+  for (int k = 1; k <= L && ok; ++k) ok = re(c->tgam[k], 2 * rows * CL) && re(c->tdgam[k], 2 * rows * CL);
+  if (ok) {
+    c->dfree(c->tepart);
+    c->tepart = c->dalloc<double>((size_t)rows);
+    ok = c->tepart != nullptr;
+  }
+  ok = ok && (c->wpart || re(c->wpart, wgrad_part_floats()));
+  if (!ok) {
+    c->tr_cap = c->tr_rows = 0;
+    return c->fail(ALLEGRO_E_OOM, "training buffer allocation failed");
+  }
   c->tr_cap = cap;
+  c->tr_rows = rows;
   return ALLEGRO_OK;
 }
 
-// Weight gradients of the per-pair dumps of the last training-mode pass
-// sequence (P pairs), added into d_grad.
-int reduce_wgrad(allegro_ctx* c, int P) {
+// Weight gradient of the last tangent pass sequence (P pairs), added into
+// d_grad.  For every linear layer z = (W s) x the passes dumped the value and
+// the tangent of its pre-activation gradient dz and of its input x (from
+// per-pair Dual arrays: element stride 2, tangent at offset 1); with the
+// tangent passes seeded by (-1, dL/dE_i) and directed along v = dL/dF,
+//     tangent of s sum_p dz (x) x = s sum_p (dz.t (x) x.v + dz.v (x) x.t)
+// is the loss gradient: the energy term sum_i dL/dE_i dE_i/dw plus the force
+// term -d/dw (v . dE/dr).
+int reduce_wgrad_tangent(allegro_ctx* c, int P) {
   const Blob& B = c->blob;
   const int D = c->D, C = (int)B.C, E = c->E, Lz = (int)B.L;
   const int NS = tp_ns((int)B.lmax), NT = tp_nt((int)B.lmax);
   const int NLM = ((int)B.lmax + 1) * ((int)B.lmax + 1), NW0 = C * ((int)B.lmax + 1), KH = D + C * NS;
-  const TrainBufs& t = c->tr;
+  const TrainBufs& v = c->tr;
+  const TrainBufs& t = c->trt;
   cudaStream_t s = c->stream;
+  float* part = c->wpart;
   auto g = [&](const std::string& name) { return c->d_grad + winfo(c, name)->flat_off; };
+  // a per-pair input: value and tangent views (plane arrays: stride 1;
+  // Dual arrays: stride 2, tangent at offset 1)
+  struct In {
+    const float* v;
+    const float* t;
+    int es;
+  };
+  auto plane = [](const float* pv, const float* pt) { return In{pv, pt, 1}; };
+  auto dual = [](const float* p) { return In{p, p + 1, 2}; };
+  auto wg = [&](const float* dzv, const float* dzt, int ldz, In x, int ldx, int N, int K, float scale, float* dW,
+                int ldw, int k0) {
+    launch_wgrad(dzt, ldz, 1, x.v, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, s);
+    launch_wgrad(dzv, ldz, 1, x.t, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, s);
+  };
   const float isD = 1.0f / std::sqrt((float)D);
-  launch_wgrad(t.dz1_tb, D, t.h0, 16, P, D, 2 * (int)B.S + 8, 1.0f / std::sqrt((float)(2 * B.S + 8)),
-               g("twobody.0"), 2 * (int)B.S + 8, 0, s);
-  launch_wgrad(t.dz2_tb, D, t.a1_tb, D, P, D, D, isD, g("twobody.1"), D, 0, s);
-  launch_wgrad(t.dw0, NW0, c->pb.X[0], D, P, NW0, D, isD, g("embed"), D, 0, s);
+  const int H0 = 2 * (int)B.S + 8;
+  wg(v.dz1_tb, t.dz1_tb, D, plane(v.h0, t.h0), 16, D, H0, 1.0f / std::sqrt((float)H0), g("twobody.0"), H0, 0);
+  wg(v.dz2_tb, t.dz2_tb, D, plane(v.a1_tb, t.a1_tb), D, D, D, isD, g("twobody.1"), D, 0);
+  wg(v.dw0, t.dw0, NW0, dual(c->tX[0]), D, NW0, D, isD, g("embed"), D, 0);
   for (int j = 0; j < Lz; ++j)
-    launch_wgrad(t.de[j], C, c->pb.X[j], D, P, C, D, isD / (float)std::sqrt(B.nu),
-                 g("layer" + std::to_string(j + 1) + ".env"), D, 0, s);
+    wg(v.de[j], t.de[j], C, dual(c->tX[j]), D, C, D, isD / (float)std::sqrt(B.nu),
+       g("layer" + std::to_string(j + 1) + ".env"), D, 0);
   for (int k = 1; k <= Lz; ++k) {
     const std::string pre = "layer" + std::to_string(k) + ".";
     const float sh = 1.0f / std::sqrt((float)KH);
-    launch_wgrad(t.dz1_l[k], D, c->pb.X[k - 1], D, P, D, D, sh, g(pre + "latent.0"), KH, 0, s);
-    launch_wgrad(t.dz1_l[k], D, t.s[k], C * NS, P, D, C * NS, sh, g(pre + "latent.0"), KH, D, s);
-    launch_wgrad(t.dz2_l[k], D, t.a1_l[k], D, P, D, D, isD, g(pre + "latent.1"), D, 0, s);
+    wg(v.dz1_l[k], t.dz1_l[k], D, dual(c->tX[k - 1]), D, D, D, sh, g(pre + "latent.0"), KH, 0);
+    wg(v.dz1_l[k], t.dz1_l[k], D, plane(v.s[k], t.s[k]), C * NS, D, C * NS, sh, g(pre + "latent.0"), KH, D);
+    wg(v.dz2_l[k], t.dz2_l[k], D, plane(v.a1_l[k], t.a1_l[k]), D, D, D, isD, g(pre + "latent.1"), D, 0);
     if (k < Lz)
       for (int l = 0; l <= (int)B.lmax; ++l) {
         const int Pl = tp_pl((int)B.lmax, l), toff = tp_toff((int)B.lmax, l);
-        launch_wgrad_mix(c->pb.dV, t.T[k], P, C, NLM, NT, l, Pl, toff, 1.0f / std::sqrt((float)(C * Pl)),
-                         g(pre + "mix" + std::to_string(l)), s);
+        const float sc = 1.0f / std::sqrt((float)(C * Pl));
+        float* dW = g(pre + "mix" + std::to_string(l));
+        launch_wgrad_mix(c->tdV + 1, 2, v.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part, s);   // dV.t (x) T.v
+        launch_wgrad_mix(c->tdV, 2, t.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part, s);       // dV.v (x) T.t
       }
   }
-  launch_wgrad(t.dze, E, t.xL, D, P, E, D, isD, g("energy.0"), D, 0, s);
-  launch_wgrad(t.dEij, 1, t.ae, E, P, 1, E, 1.0f / std::sqrt((float)E), g("energy.out"), E, 0, s);
+  wg(v.dze, t.dze, E, plane(v.xL, t.xL), D, E, D, isD, g("energy.0"), D, 0);
+  wg(v.dEij, t.dEij, 1, plane(v.ae, t.ae), E, 1, E, 1.0f / std::sqrt((float)E), g("energy.out"), E, 0);
   return cuda_check(c, "weight gradient");
 }
 
@@ -904,7 +986,6 @@ int bt_reserve(allegro_ctx* c, int64_t atoms, int64_t pairs, int structs, int64_
     if (!rc) rc = bt_grow(c, t.a.atomL, 3 * na, 3 * keep_atoms);
     if (!rc) rc = bt_grow(c, t.a.species, na, keep_atoms);
     if (!rc) rc = bt_grow(c, t.a.sid, na, keep_atoms);
-    if (!rc) rc = bt_grow(c, t.wdisp, 3 * na, 0);
     if (!rc) rc = bt_grow(c, t.v, 3 * na, 0);
     if (!rc) rc = bt_grow(c, t.seed, na, 0);
     if (!rc) rc = bt_grow(c, t.f_target, 3 * na, 0);
@@ -925,7 +1006,6 @@ int bt_reserve(allegro_ctx* c, int64_t atoms, int64_t pairs, int structs, int64_
     rc = bt_grow(c, t.atom_off, structs + 1, 0);
     if (!rc) rc = bt_grow(c, t.e_target, structs, 0);
     if (!rc) rc = bt_grow(c, t.dE, structs, 0);
-    if (!rc) rc = bt_grow(c, t.vmax, structs, 0);
     if (!rc && !t.d_np) t.d_np = c->dalloc<int>(1);
     if (!rc && !t.loss) t.loss = c->dalloc<double>(1);
     if (rc || !t.d_np || !t.loss) return rc ? rc : c->fail(ALLEGRO_E_OOM, "training batch allocation failed");
@@ -935,6 +1015,8 @@ int bt_reserve(allegro_ctx* c, int64_t atoms, int64_t pairs, int structs, int64_
 }
 
 int build_batch(allegro_ctx* c, const allegro_batch* b) {
+  int rc0 = require_fp32(c);                           // training runs the FP32 passes
+  if (rc0) return rc0;
   TrainBatch& t = c->bt;
   const int nb = b->n_structs;
   const int64_t base = b->atom_offset[0];
@@ -997,33 +1079,43 @@ void fill_batch_passbufs(allegro_ctx* c, const double* wpos) {
   pb.tile = fp32_tile();
 }
 
-// training-mode pass sequence over the batch at positions wpos with per-atom
-// seeds dL/dE_i, then the weight-gradient reductions into d_grad
-int batch_train_eval(allegro_ctx* c, const double* wpos, const float* seed) {
+// Tangent pass sequence over the batch (positions moving along v = dL/dF,
+// seeds (-1, dL/dE_i)), then the weight-gradient reductions into d_grad.
+int batch_tangent_eval(allegro_ctx* c) {
   const Blob& B = c->blob;
-  fill_batch_passbufs(c, wpos);
-  c->pb.tr = c->tr;
-  c->pb.tr.seed_atom = seed;
-  c->pb.train = 1;
-  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream);
-  c->pb.train = 0;
-  c->pb.tr.seed_atom = nullptr;
-  const int rc = reduce_wgrad(c, (int)c->bt.n_pairs);
+  TrainBatch& t = c->bt;
+  fill_batch_passbufs(c, t.a.wpos);
+  PassBufs pb = c->pb;
+  for (int k = 0; k < kMaxLayers; ++k) {
+    pb.X[k] = c->tX[k];
+    pb.V[k] = c->tV[k];
+  }
+  pb.dX = c->tdX;
+  pb.dV = c->tdV;
+  pb.dU = c->tdU;
+  pb.dY = c->tdY;
+  pb.G = c->tG;
+  for (int k = 0; k <= kMaxLayers; ++k) {
+    pb.gam[k] = c->tgam[k];
+    pb.dgam[k] = c->tdgam[k];
+  }
+  pb.epart = c->tepart;
+  pb.tile = fp32_tangent_tile();
+  pb.tr = c->tr;
+  pb.tr.seed = -1.0f;
+  pb.tr.seed_atom = nullptr;
+  pb.tr.seed_atom_t = t.seed;
+  pb.trt = c->trt;
+  pb.train = 1;
+  pb.vdir = t.v;
+  fp32_tangent_passes((int)B.lmax, (int)B.C, c->D, c->E, c->w, pb, c->capacity, c->stream);
   c->pb.atomL = nullptr;
-  return rc;
+  return reduce_wgrad_tangent(c, (int)t.n_pairs);
 }
 
-// Loss (per-atom MSE, energy:force weights) of the built batch and its weight
-// gradient into d_grad, all structures at once.  The force term's gradient
-// -d/dw sum_i v_i . dE/dr_i (v = 2 c (F - F*), c = w_force / (3 N)) is the
-// weight gradient of the directional derivative of E along v, taken per
-// structure as a central difference of the hand-written weight adjoint at
-// r +/- h v (h v at most 0.01 A; the pair list of r is kept, which differs
-// from the lists at r +/- h v only by pairs within 0.01 A of r_c, whose
-// energy vanishes there to third order).
 // Enqueue the forward evaluation of the built batch at the current weights:
 // forces, per-atom energies and the loss (Eq. 3's objective) into t.loss,
-// with the seeds of its weight gradient (dE, v, vmax).
+// with the seeds of its weight gradient (dE, v).
 void batch_forward_loss(allegro_ctx* c, double w_energy, double w_force) {
   const Blob& B = c->blob;
   TrainBatch& t = c->bt;
@@ -1031,17 +1123,23 @@ void batch_forward_loss(allegro_ctx* c, double w_energy, double w_force) {
   const int64_t N = t.n_atoms;
   const double cf = w_force / (3.0 * (double)N);
   fill_batch_passbufs(c, t.a.wpos);
-  fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+  if (c->pb_fp32) fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+  else c->fp32_bad = true;
   AtomArgs aa = atom_args(c);
   aa.n = (int)N;
   aa.species = t.a.species;
   launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk, c->d_stats,
                 c->nb.flags, s);
   c->pb.atomL = nullptr;
-  launch_batch_loss((int)t.n_structs, N, t.atom_off, t.a.sid, c->d_Ei, t.e_target, c->d_F, t.f_target, w_energy,
-                    cf, t.dE, t.v, t.vmax, t.loss_blk, t.loss, s);
+  launch_batch_loss((int)t.n_structs, N, t.atom_off, c->d_Ei, t.e_target, c->d_F, t.f_target, w_energy, cf, t.dE,
+                    t.v, t.loss_blk, t.loss, s);
 }
 
+// Loss (per-atom MSE, energy:force weights) of the built batch and its weight
+// gradient into d_grad, all structures at once.  The force term's gradient
+// -d/dw sum_i v_i . dE/dr_i (v = 2 c (F - F*), c = w_force / (3 N)) is the
+// derivative along v of the hand-written weight adjoint, taken exactly by the
+// tangent passes (forward-mode differentiation of the FP32 pass kernels).
 int loss_grad_impl(allegro_ctx* c, double w_energy, double w_force, double* loss_out) {
   const Blob& B = c->blob;
   if (B.L > 2) return c->fail(ALLEGRO_E_UNSUPPORTED, "training is built for models of at most two layers");
@@ -1053,16 +1151,12 @@ int loss_grad_impl(allegro_ctx* c, double w_energy, double w_force, double* loss
   cudaMemsetAsync(c->nb.flags, 0, sizeof(int), s);
   const int nbk = (int)t.n_structs;
   const int64_t N = t.n_atoms;
-  const double delta = 1e-2;
-  // forward over the batch: forces, per-atom energies, loss
+  // forward over the batch: forces, per-atom energies, loss, v = dL/dF
   batch_forward_loss(c, w_energy, w_force);
-  // energy term at r, then the central difference along v
+  // energy-loss seeds, then one tangent pass sequence along v: the energy
+  // term and the force term's -d/dw (v . dE/dr) of Eq. 3's loss at once
   launch_seed_energy(nbk, N, t.atom_off, t.a.sid, t.dE, w_energy, t.seed, s);
-  rc = batch_train_eval(c, t.a.wpos, t.seed);
-  for (int sg = 0; sg < 2 && !rc; ++sg) {
-    launch_displace(N, t.a.sid, t.a.wpos, t.v, t.vmax, delta, sg == 0 ? 1.0 : -1.0, t.wdisp, t.seed, s);
-    rc = batch_train_eval(c, t.wdisp, t.seed);
-  }
+  rc = batch_tangent_eval(c);
   if (rc) return rc;
   double loss = 0.0;
   int flags = 0;
@@ -1194,7 +1288,8 @@ int allegro_energy_forces(allegro_ctx* ctx, int64_t n_atoms, const double* posit
   if (!ctx) return ALLEGRO_E_INVALID_ARG;
   if (!species || !energy_out) return ctx->fail(ALLEGRO_E_INVALID_ARG, "species and energy_out are required");
   double L[3];
-  int rc = prepare(ctx, n_atoms, positions, species, cell, L);
+  int rc = precision == ALLEGRO_FP32 ? require_fp32(ctx) : ALLEGRO_OK;
+  if (!rc) rc = prepare(ctx, n_atoms, positions, species, cell, L);
   if (rc) return rc;
   int64_t np = 0;
   rc = build_with_growth(ctx, ctx->d_pos, n_atoms, &np);
@@ -1236,6 +1331,10 @@ int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
   if (!ctx || !valid_precision(precision)) return ALLEGRO_E_INVALID_ARG;
   if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
     return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
+  if (precision == ALLEGRO_FP32) {
+    const int rc = require_fp32(ctx);
+    if (rc) return rc;
+  }
   if (precision != ctx->md_precision) ctx->drop_graphs();
   ctx->md_precision = precision;
   return ALLEGRO_OK;
@@ -1247,7 +1346,8 @@ int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions, 
   if (!velocities || !species) return ctx->fail(ALLEGRO_E_INVALID_ARG, "velocities and species are required");
   double L[3];
   ctx->md_ready = false;
-  int rc = prepare(ctx, n_atoms, positions, species, cell, L);
+  int rc = ctx->md_precision == ALLEGRO_FP32 ? require_fp32(ctx) : ALLEGRO_OK;
+  if (!rc) rc = prepare(ctx, n_atoms, positions, species, cell, L);
   if (rc) return rc;
   const cudaMemcpyKind kv = is_device_ptr(velocities) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaMemcpyAsync(ctx->d_v, velocities, sizeof(double) * 3 * n_atoms, kv, ctx->stream);
@@ -1517,7 +1617,8 @@ void rp_launch_forces(allegro_ctx* c, cudaStream_t s) {
   int tile;
   const int prec = c->md_precision;
   if (prec == ALLEGRO_FP32) {
-    fp32_energy_forces((int)c->blob.lmax, (int)c->blob.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+    if (c->pb_fp32) fp32_energy_forces((int)c->blob.lmax, (int)c->blob.C, c->D, c->E, c->w, c->pb, c->capacity, s);
+    else c->fp32_bad = true;
     tile = fp32_tile();
   } else {
     const TcMode mode = prec == ALLEGRO_BF16 ? TcMode::kBf16 : prec == ALLEGRO_FP16 ? TcMode::kFp16 : TcMode::kFp16Split;
@@ -1551,8 +1652,7 @@ int rp_reserve(allegro_ctx* c) {
   const double rc3 = c->blob.rc * c->blob.rc * c->blob.rc;
   const double est = (double)PN * (4.18879 * rc3 * (double)c->rp_n / vol) * 1.3 + 4096.0;
   if (c->capacity < (int64_t)std::min(est, 2.0e9)) return ensure_pairs(c, (int64_t)std::min(est, 2.0e9));
-  if (c->part_rows < c->capacity / fp32_tile() + 2 + c->n_atoms_alloc) return ensure_pairs(c, c->capacity);
-  return ALLEGRO_OK;
+  return ensure_pairs(c, c->capacity);
 }
 
 // one ring-polymer step as a graph: kick, free ring evolution, neighbour
@@ -1597,6 +1697,7 @@ int allegro_pimd_init(allegro_ctx* ctx, int32_t n_beads, int64_t n_atoms, const 
     return ctx->fail(ALLEGRO_E_INVALID_ARG, "temperature must be positive");
   double L[3];
   int rc = check_cell(ctx, cell, L);
+  if (!rc && ctx->md_precision == ALLEGRO_FP32) rc = require_fp32(ctx);
   if (rc) return rc;
   ctx->rp_ready = false;
   ctx->md_ready = false;
@@ -1917,6 +2018,11 @@ int allegro_set_weights(allegro_ctx* ctx, const float* in, int64_t n) {
   ctx->drop_graphs();
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "set_weights");
   return ALLEGRO_OK;
+}
+
+int allegro_selftest_silu(int64_t n, const float* x, float* y) {
+  if (n < 0 || n > (int64_t)1 << 30 || (n > 0 && (!x || !y))) return ALLEGRO_E_INVALID_ARG;
+  return al::bf16_silu_probe((int)n, x, y) == 0 ? ALLEGRO_OK : ALLEGRO_E_CUDA;
 }
 
 int allegro_debug_inject_wait_timeout(int32_t enable) {

@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
-#define AL_DEV __device__ __forceinline__
+#include "dual.cuh"
 
 namespace al {
 
@@ -46,8 +46,9 @@ AL_DEV void pair_delta(const double* __restrict__ w, int i, int j, int code, con
 // index l*l + m + l, for a unit vector (x, y, z):
 //   Y_0 = 1; Y_1 = sqrt3 (y, z, x);
 //   Y_2 = (sqrt15 xy, sqrt15 yz, sqrt5/2 (3z^2 - 1), sqrt15 xz, sqrt15/2 (x^2 - y^2)).
-template <int LMAX>
-AL_DEV void sph_harm(float x, float y, float z, float* Y) {
+// (T is float, or Dual for the tangent passes of the second-order adjoint.)
+template <int LMAX, class T>
+AL_DEV void sph_harm(T x, T y, T z, T* Y) {
   Y[0] = 1.0f;
   if (LMAX >= 1) {
     Y[1] = kSqrt3 * y;
@@ -65,9 +66,9 @@ AL_DEV void sph_harm(float x, float y, float z, float* Y) {
 
 // g_u = sum_lm dY[lm] * dY_lm/du (gradient of the polynomial forms w.r.t. the
 // unit-vector components, before projection onto the sphere's tangent).
-template <int LMAX>
-AL_DEV void sph_harm_vjp(float x, float y, float z, const float* dY, float g[3]) {
-  g[0] = g[1] = g[2] = 0.0f;
+template <int LMAX, class T>
+AL_DEV void sph_harm_vjp(T x, T y, T z, const T* dY, T g[3]) {
+  g[0] = g[1] = g[2] = T(0.0f);
   if (LMAX >= 1) {
     g[1] += kSqrt3 * dY[1];
     g[2] += kSqrt3 * dY[2];
@@ -82,20 +83,20 @@ AL_DEV void sph_harm_vjp(float x, float y, float z, const float* dY, float g[3])
 
 // Bessel radial basis B_n(d) = sqrt(2/rc) sin(n pi d / rc) / d, n = 1..NB, and
 // dB_n/dd, through the angle-addition recurrence from sincospi(d/rc).
-template <int NB>
-AL_DEV void bessel(float d, float rc, float* B, float* dB) {
+template <int NB, class T>
+AL_DEV void bessel(T d, float rc, T* B, typename nodeduce<T>::type* dB) {
   const float c = sqrtf(2.0f / rc);
-  const float t = d / rc;
-  float s1, c1;
-  sincospif(t, &s1, &c1);
-  float sn = s1, cn = c1;
-  const float inv_d = 1.0f / d;
+  const T t = d / rc;
+  T s1, c1;
+  fsincospi(t, &s1, &c1);
+  T sn = s1, cn = c1;
+  const T inv_d = 1.0f / d;
 #pragma unroll
   for (int n = 1; n <= NB; ++n) {
     B[n - 1] = c * sn * inv_d;
     if (dB) dB[n - 1] = c * ((float)n * kPi / rc * cn - sn * inv_d) * inv_d;
-    const float s2 = sn * c1 + cn * s1;
-    const float c2 = cn * c1 - sn * s1;
+    const T s2 = sn * c1 + cn * s1;
+    const T c2 = cn * c1 - sn * s1;
     sn = s2;
     cn = c2;
   }
@@ -104,23 +105,27 @@ AL_DEV void bessel(float d, float rc, float* B, float* dB) {
 // Polynomial envelope (p = 6): u(x) = 1 - 28 x^6 + 48 x^7 - 21 x^8, x = d/rc,
 // and du/dd = (-168 x^5 + 336 x^6 - 168 x^7) / rc.
 // (zero at and beyond r_c, where a pair contributes nothing: C^2 continuous)
-AL_DEV void envelope(float d, float rc, float& u, float& du) {
+template <class T>
+AL_DEV void envelope(T d, float rc, T& u, T& du) {
   if (d >= rc) {
-    u = 0.0f;
-    du = 0.0f;
+    u = T(0.0f);
+    du = T(0.0f);
     return;
   }
-  const float x = d / rc;
-  const float x2 = x * x, x5 = x2 * x2 * x, x6 = x5 * x;
+  const T x = d / rc;
+  const T x2 = x * x, x5 = x2 * x2 * x, x6 = x5 * x;
   u = 1.0f + x6 * (-28.0f + x * (48.0f - 21.0f * x));
   du = x5 * (-168.0f + x * (336.0f - 168.0f * x)) / rc;
 }
 
-AL_DEV float sigmoidf_(float z) { return __frcp_rn(1.0f + __expf(-z)); }
-AL_DEV float silu(float z) { return z * sigmoidf_(z); }
+template <class T>
+AL_DEV T sigmoidf_(T z) { return frcp(1.0f + fexp(-z)); }
+template <class T>
+AL_DEV T silu(T z) { return z * sigmoidf_(z); }
 // d silu / dz = s (1 + z (1 - s)), s = sigmoid(z)
-AL_DEV float silu_grad(float z) {
-  const float s = sigmoidf_(z);
+template <class T>
+AL_DEV T silu_grad(T z) {
+  const T s = sigmoidf_(z);
   return s * (1.0f + z * (1.0f - s));
 }
 

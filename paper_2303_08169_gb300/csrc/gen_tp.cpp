@@ -13,7 +13,9 @@
 // product rule with 8 Gauss-Legendre nodes in cos(theta) and 16 equispaced
 // nodes in phi integrates it exactly.  G is then normalised and sign-fixed.
 //
-// Output: a header with, per l_max in {1, 2}, straight-line device functions
+// Output: a header with, per l_max in {0, 1, 2}, straight-line device
+// function templates over the scalar type S (float, or the tangent numbers of
+// the second-order adjoint)
 //   tpL_fwd(V, G, T)          all paths            T[c-local layout below]
 //   tpL_fwd_scalar(V, G, S)   l3 = 0 paths only
 //   tpL_bwd(V, G, dT, dV, dG) adjoint of tpL_fwd (accumulates into dV, dG)
@@ -178,8 +180,8 @@ void emit(FILE* f, int lmax) {
   }
   std::fprintf(f, "#define TP%d_NNZ %zu\n", lmax, terms.size());
   auto fwd = [&](const char* name, const std::vector<Term>& ts, int nout) {
-    std::fprintf(f, "__device__ __forceinline__ void tp%s_%s(const float* __restrict__ V, "
-                 "const float* __restrict__ G, float* __restrict__ T) {\n", L.c_str(), name);
+    std::fprintf(f, "template <class S>\n__device__ __forceinline__ void tp%s_%s(const S* __restrict__ V, "
+                 "const S* __restrict__ G, S* __restrict__ T) {\n", L.c_str(), name);
     for (int o = 0; o < nout; ++o) {
       std::string e;
       for (auto& t : ts)
@@ -188,14 +190,14 @@ void emit(FILE* f, int lmax) {
                              std::to_string(t.b) + "]";
           e = e.empty() ? term : e + " + " + term;
         }
-      std::fprintf(f, "  T[%d] = %s;\n", o, e.empty() ? "0.0f" : e.c_str());
+      std::fprintf(f, "  T[%d] = %s;\n", o, e.empty() ? "S(0.0f)" : e.c_str());
     }
     std::fprintf(f, "}\n");
   };
   auto bwd = [&](const char* name, const std::vector<Term>& ts) {
-    std::fprintf(f, "__device__ __forceinline__ void tp%s_%s(const float* __restrict__ V, "
-                 "const float* __restrict__ G, const float* __restrict__ dT, "
-                 "float* __restrict__ dV, float* __restrict__ dG) {\n", L.c_str(), name);
+    std::fprintf(f, "template <class S>\n__device__ __forceinline__ void tp%s_%s(const S* __restrict__ V, "
+                 "const S* __restrict__ G, const S* __restrict__ dT, "
+                 "S* __restrict__ dV, S* __restrict__ dG) {\n", L.c_str(), name);
     const int nc = (lmax + 1) * (lmax + 1);
     for (int a = 0; a < nc; ++a) {
       std::string e;

@@ -39,6 +39,7 @@ struct ModelW {
 struct TrainBufs {
   float seed = 1.0f;                  // dL/dE of this evaluation (scales sigma_Z)
   const float* seed_atom = nullptr;   // [N] per-atom dL/dE_i instead of seed (training batches)
+  const float* seed_atom_t = nullptr; // [N] tangent of seed_atom (tangent passes)
   float* h0 = nullptr;                // [P][16] two-body input (12 used)
   float* a1_tb = nullptr;             // [P][D]  SiLU of the first two-body layer
   float* dz1_tb = nullptr;            // [P][D]
@@ -89,8 +90,10 @@ struct PassBufs {
   float* dgsum[kMaxLayers + 1] = {};
   double* epart;                // sum_j E_ij partials
   int tile;                     // pairs per tile (all passes)
-  TrainBufs tr;                 // training dumps (FP32 path)
+  TrainBufs tr;                 // training dumps (FP32 path; tangent passes: the values)
+  TrainBufs trt;                // tangent passes: the tangents of the same dumps
   int train;                    // nonzero: write the TrainBufs dumps
+  const float* vdir = nullptr;  // tangent passes: N x 3 position direction v
 };
 
 // BF16 path weights: pre-scaled BF16 images in the 128-byte-swizzled K-major
@@ -121,6 +124,10 @@ int bf16_tile();
 // them, so each pass raises the timeout flag with nothing in flight;
 // enable == 0 restores the copies and the 2^31-cycle limit.  0 on success.
 int bf16_inject_wait_timeout(int enable);
+// SiLU and its derivative as the tensor-core passes evaluate them (sigmoid
+// through tanh.approx.f32): y[2i], y[2i+1] for x[i]; device arrays; legacy
+// stream, synchronises.  0 on success.
+int bf16_silu_probe(int n, const float* x, float* y);
 // Optional launch timing: mark(kind) records an event on the stream after a
 // pass kernel, tagged with its kind; interval i lies between event i and
 // event i + 1 and belongs to kind[i + 1].
@@ -152,5 +159,14 @@ bool fp32_supported(int lmax, int C, int D, int E);
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
                         int64_t capacity, cudaStream_t s, KernelMarks* km = nullptr);
 int fp32_tile();
+// Tangent passes of the second-order adjoint: the FP32 pass sequence in
+// tangent numbers (value and derivative along the position direction b.vdir),
+// tiles of fp32_tangent_tile() pairs.  Every per-pair and per-(tile, atom)
+// array of b holds Dual values (twice the floats of the FP32 passes); the
+// training dumps write values to b.tr and tangents to b.trt.  Models: the
+// 1-layer tiny model and the 2-layer main model.
+int fp32_tangent_tile();
+void fp32_tangent_passes(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b, int64_t capacity,
+                         cudaStream_t s);
 
 }  // namespace al

@@ -117,6 +117,14 @@ AL_DEV float dsilu_b(float z) {
   return s * (1.0f + z * (1.0f - s));
 }
 
+// y = (SiLU(x), dSiLU/dx(x)) with the tensor-core passes' own arithmetic
+__global__ void k_silu_probe(int n, const float* __restrict__ x, float* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[2 * i] = silu_b(x[i]);
+  y[2 * i + 1] = dsilu_b(x[i]);
+}
+
 // ---------------------------------------------------------------------------
 struct Meta {
   int pi[kT], pj[kT], code[kT], seg[kT], atom[kT], sstart[kT + 1];
@@ -1708,6 +1716,12 @@ bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
 }
 
 int bf16_tile() { return kT; }
+
+int bf16_silu_probe(int n, const float* x, float* y) {
+  if (n <= 0) return 0;
+  k_silu_probe<<<(n + 255) / 256, 256>>>(n, x, y);
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
+}
 
 int bf16_inject_wait_timeout(int enable) {
   const long long cycles = enable ? (1ll << 20) : (1ll << 31);

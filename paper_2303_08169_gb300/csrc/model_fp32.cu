@@ -33,9 +33,9 @@
 namespace al {
 namespace {
 
-constexpr int kTile = 32;       // pairs per tile
-constexpr int kThreads = 256;   // 8 threads per pair in per-pair phases
-constexpr int kSub = kThreads / kTile;
+constexpr int kTile = 32;       // pairs per tile (FP32 passes)
+constexpr int kTileDual = 16;   // pairs per tile (tangent passes: two floats per value)
+constexpr int kThreads = 256;   // 8 (16) threads per pair in per-pair phases
 constexpr float kRsqrt2 = 0.70710678118654752f;
 
 // ----------------------------------------------------------------------------
@@ -69,28 +69,34 @@ AL_DEV void load_chunk(float* wbuf, const float* __restrict__ Wt, int ch) {
 template <int LMAX> struct TP;
 template <> struct TP<0> {
   static constexpr int NT = TP0_NT, NS = TP0_NS;
-  static AL_DEV void fwd(const float* V, const float* G, float* T) { tp0_fwd(V, G, T); }
-  static AL_DEV void fwd_s(const float* V, const float* G, float* T) { tp0_fwd_scalar(V, G, T); }
-  static AL_DEV void bwd(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp0_bwd(V, G, dT, dV, dG); }
-  static AL_DEV void bwd_s(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp0_bwd_scalar(V, G, dT, dV, dG); }
+  template <class S> static AL_DEV void fwd(const S* V, const S* G, S* T) { tp0_fwd(V, G, T); }
+  template <class S> static AL_DEV void fwd_s(const S* V, const S* G, S* T) { tp0_fwd_scalar(V, G, T); }
+  template <class S>
+  static AL_DEV void bwd(const S* V, const S* G, const S* dT, S* dV, S* dG) { tp0_bwd(V, G, dT, dV, dG); }
+  template <class S>
+  static AL_DEV void bwd_s(const S* V, const S* G, const S* dT, S* dV, S* dG) { tp0_bwd_scalar(V, G, dT, dV, dG); }
   static constexpr AL_DEV int P(int l) { return tp0_P(l); }
   static constexpr AL_DEV int toff(int l) { return tp0_toff(l); }
 };
 template <> struct TP<1> {
   static constexpr int NT = TP1_NT, NS = TP1_NS;
-  static AL_DEV void fwd(const float* V, const float* G, float* T) { tp1_fwd(V, G, T); }
-  static AL_DEV void fwd_s(const float* V, const float* G, float* T) { tp1_fwd_scalar(V, G, T); }
-  static AL_DEV void bwd(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp1_bwd(V, G, dT, dV, dG); }
-  static AL_DEV void bwd_s(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp1_bwd_scalar(V, G, dT, dV, dG); }
+  template <class S> static AL_DEV void fwd(const S* V, const S* G, S* T) { tp1_fwd(V, G, T); }
+  template <class S> static AL_DEV void fwd_s(const S* V, const S* G, S* T) { tp1_fwd_scalar(V, G, T); }
+  template <class S>
+  static AL_DEV void bwd(const S* V, const S* G, const S* dT, S* dV, S* dG) { tp1_bwd(V, G, dT, dV, dG); }
+  template <class S>
+  static AL_DEV void bwd_s(const S* V, const S* G, const S* dT, S* dV, S* dG) { tp1_bwd_scalar(V, G, dT, dV, dG); }
   static constexpr AL_DEV int P(int l) { return tp1_P(l); }
   static constexpr AL_DEV int toff(int l) { return tp1_toff(l); }
 };
 template <> struct TP<2> {
   static constexpr int NT = TP2_NT, NS = TP2_NS;
-  static AL_DEV void fwd(const float* V, const float* G, float* T) { tp2_fwd(V, G, T); }
-  static AL_DEV void fwd_s(const float* V, const float* G, float* T) { tp2_fwd_scalar(V, G, T); }
-  static AL_DEV void bwd(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp2_bwd(V, G, dT, dV, dG); }
-  static AL_DEV void bwd_s(const float* V, const float* G, const float* dT, float* dV, float* dG) { tp2_bwd_scalar(V, G, dT, dV, dG); }
+  template <class S> static AL_DEV void fwd(const S* V, const S* G, S* T) { tp2_fwd(V, G, T); }
+  template <class S> static AL_DEV void fwd_s(const S* V, const S* G, S* T) { tp2_fwd_scalar(V, G, T); }
+  template <class S>
+  static AL_DEV void bwd(const S* V, const S* G, const S* dT, S* dV, S* dG) { tp2_bwd(V, G, dT, dV, dG); }
+  template <class S>
+  static AL_DEV void bwd_s(const S* V, const S* G, const S* dT, S* dV, S* dG) { tp2_bwd_scalar(V, G, dT, dV, dG); }
   static constexpr AL_DEV int P(int l) { return tp2_P(l); }
   static constexpr AL_DEV int toff(int l) { return tp2_toff(l); }
 };
@@ -129,22 +135,22 @@ AL_DEV void stage_mix(const LayerW& LW, float* s_mix) {
   cp_async_commit();
 }
 
-// Tile GEMM: out[m][n] = sum_k A[m*lda + k] * Wt[k*N + n] for m < kTile, n < N.
+// Tile GEMM: out[m][n] = sum_k A[m*lda + k] * Wt[k*N + n] for m < TT, n < N.
 // A in shared memory, Wt ([K][N], 16-byte aligned) staged through wbuf
 // (>= 2 kKC N floats of shared memory); 256 threads with a TM x TN register
 // tile each; epi(m, n, value) consumes every output once.  All threads of the
 // block must call it; it begins and ends with a block barrier.
-template <int N, int K, class Epi>
-AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__ Wt, float* wbuf,
+template <int N, int K, int TT, class T, class Epi>
+AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt, float* wbuf,
                  Epi&& epi) {
-  constexpr int M = kTile;
+  constexpr int M = TT;
   constexpr int NCH = (K + kKC - 1) / kKC;
   static_assert(N % 4 == 0, "weights are staged in 16-byte units");
   __syncthreads();
   load_chunk<N, K>(wbuf, Wt, 0);
   if constexpr ((M * N) % kThreads != 0) {
     constexpr int R = (M * N + kThreads - 1) / kThreads;
-    float acc[R];
+    T acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0f;
     for (int ch = 0; ch < NCH; ++ch) {
@@ -181,7 +187,7 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
     constexpr int TY = kThreads / TX;
     static_assert(TY * TM == M, "tile shape");
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    float acc[TM][TN];
+    T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -198,9 +204,10 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
       // that the 16-byte loads of a warp are contiguous (no bank conflicts)
       const float* wc = wbuf + (ch & 1) * kKC * N + (TN % 4 == 0 ? tx * 4 : tx * TN);
       const int k0 = ch * kKC;
-      const float* a0 = A + ty * lda + k0;
+      const T* a0 = A + ty * lda + k0;
       auto step = [&](int k) {
-        float a[TM], b[TN];
+        T a[TM];
+        float b[TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i) a[i] = a0[i * TY * lda + k];
         if constexpr (TN % 4 == 0) {
@@ -242,17 +249,20 @@ AL_DEV void gemm(const float* __restrict__ A, int lda, const float* __restrict__
 
 // ----------------------------------------------------------------------------
 // Tile bookkeeping: pair meta data and segments (runs of equal centre atom).
+template <int TT>
 struct TileMeta {
-  int pi[kTile], pj[kTile], code[kTile], seg[kTile], atom[kTile];
+  int pi[TT], pj[TT], code[TT], seg[TT], atom[TT];
   int nseg, np, p0;
 };
 
-AL_DEV bool tile_setup(const PassBufs& b, TileMeta& t) {
+template <int TT>
+AL_DEV bool tile_setup(const PassBufs& b, TileMeta<TT>& t) {
+  static_assert(TT <= 32, "one warp sets a tile up");
   if (*b.flags & 1) return false;   // pair overflow: the list is incomplete
   const int P = (int)min((int64_t)*b.n_pairs, b.capacity);
-  const int p0 = blockIdx.x * kTile;
+  const int p0 = blockIdx.x * TT;
   if (p0 >= P) return false;
-  const int np = min(kTile, P - p0);
+  const int np = min(TT, P - p0);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int i = -1;
@@ -261,7 +271,7 @@ AL_DEV bool tile_setup(const PassBufs& b, TileMeta& t) {
       t.pi[lane] = i;
       t.pj[lane] = b.pj[p0 + lane];
       t.code[lane] = b.pcode[p0 + lane];
-    } else {
+    } else if (lane < TT) {
       t.pi[lane] = 0;
       t.pj[lane] = 0;
       t.code[lane] = 62;  // n = 0
@@ -270,7 +280,7 @@ AL_DEV bool tile_setup(const PassBufs& b, TileMeta& t) {
     const bool head = lane < np && (lane == 0 || i != prev);
     const unsigned m = __ballot_sync(0xffffffffu, head);
     const unsigned below = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-    t.seg[lane] = lane < np ? __popc(m & below) - 1 : 0;
+    if (lane < TT) t.seg[lane] = lane < np ? __popc(m & below) - 1 : 0;
     if (head) t.atom[__popc(m & below) - 1] = i;
     if (lane == 0) {
       t.nseg = __popc(m);
@@ -283,25 +293,25 @@ AL_DEV bool tile_setup(const PassBufs& b, TileMeta& t) {
 }
 
 // Sum of per-(tile, atom) partials of every segment's atom: out[s][x].
-template <int W>
-AL_DEV void load_segments(const float* __restrict__ part, const int* __restrict__ row_ptr,
-                          const TileMeta& t, float* out) {
+template <int W, int TT, class T>
+AL_DEV void load_segments(const T* __restrict__ part, const int* __restrict__ row_ptr,
+                          const TileMeta<TT>& t, T* out) {
   for (int idx = threadIdx.x; idx < t.nseg * W; idx += kThreads) {
     const int s = idx / W, x = idx % W;
     const int i = t.atom[s];
-    const int t0 = row_ptr[i] / kTile, t1 = (row_ptr[i + 1] - 1) / kTile;
-    float acc = 0.0f;
+    const int t0 = row_ptr[i] / TT, t1 = (row_ptr[i + 1] - 1) / TT;
+    T acc = 0.0f;
     for (int tt = t0; tt <= t1; ++tt) acc += part[(size_t)(tt + i) * W + x];
     out[s * W + x] = acc;
   }
 }
 
 // part[(tile + atom) * W + x] = sum over the segment's pairs of f(p, x).
-template <int W, class F>
-AL_DEV void store_segments(float* __restrict__ part, const TileMeta& t, F&& f) {
+template <int W, int TT, class T, class F>
+AL_DEV void store_segments(T* __restrict__ part, const TileMeta<TT>& t, F&& f) {
   for (int idx = threadIdx.x; idx < t.nseg * W; idx += kThreads) {
     const int s = idx / W, x = idx % W;
-    float acc = 0.0f;
+    T acc = 0.0f;
     for (int p = 0; p < t.np; ++p)
       if (t.seg[p] == s) acc += f(p, x);
     part[(size_t)(blockIdx.x + t.atom[s]) * W + x] = acc;
@@ -310,25 +320,32 @@ AL_DEV void store_segments(float* __restrict__ part, const TileMeta& t, F&& f) {
 
 // Copy a kTile x W block of a pair-major global array into shared memory
 // (zero rows past the end of the list).
-template <int W>
-AL_DEV void load_rows(const float* __restrict__ g, const TileMeta& t, float* s, int lds) {
-  for (int idx = threadIdx.x; idx < kTile * W; idx += kThreads) {
+template <int W, int TT, class T>
+AL_DEV void load_rows(const T* __restrict__ g, const TileMeta<TT>& t, T* s, int lds) {
+  for (int idx = threadIdx.x; idx < TT * W; idx += kThreads) {
     const int m = idx / W, n = idx % W;
-    s[m * lds + n] = m < t.np ? g[(size_t)(t.p0 + m) * W + n] : 0.0f;
+    s[m * lds + n] = m < t.np ? g[(size_t)(t.p0 + m) * W + n] : T(0.0f);
   }
 }
 
-// Geometry of one pair: unit vector, distance, envelope and SH.
-template <class Cf>
-AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float u[3], float& d,
-                     float& fc, float& dfc, float* Y) {
+// Geometry of one pair: unit vector, distance, envelope and SH.  Tangent
+// passes: the separation moves along v_j - v_i (b.vdir, the position
+// direction of the second-order adjoint).
+template <class Cf, class T>
+AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, T u[3], T& d,
+                     T& fc, T& dfc, T* Y) {
   Box box{{b.L[0], b.L[1], b.L[2]}};
   if (b.atomL) box = Box{{b.atomL[3 * i], b.atomL[3 * i + 1], b.atomL[3 * i + 2]}};
   double dd[3];
   pair_delta(b.wpos, i, j, code, box, dd);
-  const float dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
+  T dx = (float)dd[0], dy = (float)dd[1], dz = (float)dd[2];
+  if constexpr (is_dual<T>::value) {
+    dx.t = b.vdir[3 * j] - b.vdir[3 * i];
+    dy.t = b.vdir[3 * j + 1] - b.vdir[3 * i + 1];
+    dz.t = b.vdir[3 * j + 2] - b.vdir[3 * i + 2];
+  }
   d = sqrtf(dx * dx + dy * dy + dz * dz);
-  const float inv = 1.0f / d;
+  const T inv = 1.0f / d;
   u[0] = dx * inv;
   u[1] = dy * inv;
   u[2] = dz * inv;
@@ -336,50 +353,59 @@ AL_DEV void geometry(const PassBufs& b, float rc, int i, int j, int code, float 
   sph_harm<Cf::LMAX>(u[0], u[1], u[2], Y);
 }
 
-// Training dumps: copy a kTile x W block of shared memory (row stride lds)
-// into a per-pair array (row-major [P][W]); no-op for a null array.
-template <int W>
-AL_DEV void dump_rows(float* g, const TileMeta& t, const float* s, int lds) {
+// Training dumps: copy a tile x W block of shared memory (row stride lds)
+// into a per-pair array (row-major [P][W]); no-op for a null array.  Tangent
+// passes write the values to g and the tangents to gt.
+template <int W, int TT, class T>
+AL_DEV void dump_rows(float* g, float* gt, const TileMeta<TT>& t, const T* s, int lds) {
   if (!g) return;
   for (int idx = threadIdx.x; idx < t.np * W; idx += kThreads) {
     const int m = idx / W, n = idx % W;
-    g[(size_t)(t.p0 + m) * W + n] = s[m * lds + n];
+    g[(size_t)(t.p0 + m) * W + n] = val(s[m * lds + n]);
+    if constexpr (is_dual<T>::value) gt[(size_t)(t.p0 + m) * W + n] = s[m * lds + n].t;
   }
 }
 
-// Shared-memory carve-up helper.
+// A per-pair or per-(tile, atom) array of the pass buffers viewed as T
+// (tangent passes: arrays of Dual, allocated at twice the floats).
+template <class T>
+AL_DEV T* as(float* p) { return reinterpret_cast<T*>(p); }
+
+// Shared-memory carve-up helper (n elements of X, 16-byte aligned).
 struct Carve {
   float* p;
-  AL_DEV float* take(int n) {
-    float* r = p;
-    p += (n + 3) & ~3;
+  template <class X = float>
+  AL_DEV X* take(int n) {
+    X* r = reinterpret_cast<X*>(p);
+    p += ((int)(n * sizeof(X) / 4) + 3) & ~3;
     return r;
   }
 };
 
 // ============================================================================
 // Pass A: geometry, two-body MLP, x0, e^1 -> Gamma^1 partials.
-template <class Cf>
+template <class Cf, class T, int TT>
 __global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, LDD = Cf::LDD;
-  __shared__ TileMeta t;
+  __shared__ TileMeta<TT> t;
+  constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
-  float* s_h0 = cv.take(kTile * Cf::LDH0);
-  float* s_fc = cv.take(kTile);
-  float* s_Y = cv.take(kTile * NLM);
-  float* s_z1 = cv.take(kTile * LDD);
-  float* s_x = cv.take(kTile * LDD);
-  float* s_e = cv.take(kTile * C);
-  if (threadIdx.x < kTile) {
+  T* s_h0 = cv.take<T>(TT * Cf::LDH0);
+  T* s_fc = cv.take<T>(TT);
+  T* s_Y = cv.take<T>(TT * NLM);
+  T* s_z1 = cv.take<T>(TT * LDD);
+  T* s_x = cv.take<T>(TT * LDD);
+  T* s_e = cv.take<T>(TT * C);
+  if (threadIdx.x < TT) {
     const int p = threadIdx.x;
-    float* h = s_h0 + p * Cf::LDH0;
+    T* h = s_h0 + p * Cf::LDH0;
     for (int k = 0; k < Cf::LDH0; ++k) h[k] = 0.0f;
     if (p < t.np) {
-      float u[3], d, fc, dfc, Y[NLM], B[Cf::NB];
-      geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+      T u[3], d, fc, dfc, Y[NLM], B[Cf::NB];
+      geometry<Cf, T>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
       bessel<Cf::NB>(d, w.rc, B, nullptr);
       h[b.species[t.pi[p]]] = 1.0f;
       h[Cf::S + b.species[t.pj[p]]] = 1.0f;
@@ -392,34 +418,34 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
     }
   }
   __syncthreads();
-  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
+  gemm<D, Cf::H0, TT>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, T v) { s_z1[m * LDD + n] = silu(v); });
   __syncthreads();
-  float* X0 = b.X[0];
-  gemm<D, D>(s_z1, LDD, w.tb1.t, s_wb, [&](int m, int n, float v) {
-    const float x = s_fc[m] * silu(v);
+  T* X0 = as<T>(b.X[0]);
+  gemm<D, D, TT>(s_z1, LDD, w.tb1.t, s_wb, [&](int m, int n, T v) {
+    const T x = s_fc[m] * silu(v);
     s_x[m * LDD + n] = x;
     if (m < t.np) X0[(size_t)(t.p0 + m) * D + n] = x;
   });
   __syncthreads();
-  gemm<C, D>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  gemm<C, D, TT>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
   __syncthreads();
-  store_segments<Cf::CL>(b.gam[1], t, [&](int p, int x) {
+  store_segments<Cf::CL>(as<T>(b.gam[1]), t, [&](int p, int x) {
     return s_e[p * C + x / NLM] * s_Y[p * NLM + x % NLM];
   });
 }
 
 // V^{k-1}_c for one pair and channel: from the stored array, or for k = 1 from
 // w0 (x) Y.
-template <class Cf>
-AL_DEV void load_v(int k, const PassBufs& b, const TileMeta& t, int p, int c, const float* s_w0,
-                   const float* s_Y, float* V) {
+template <class Cf, int TT, class T>
+AL_DEV void load_v(int k, const PassBufs& b, const TileMeta<TT>& t, int p, int c, const T* s_w0,
+                   const T* s_Y, T* V) {
   constexpr int NLM = Cf::NLM;
   if (k == 1) {
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
       V[lm] = s_w0[p * Cf::NW0 + c * (Cf::LMAX + 1) + l_of(lm)] * s_Y[p * NLM + lm];
   } else {
-    const float* g = b.V[k - 1] + (size_t)(t.p0 + p) * Cf::CL + c * NLM;
+    const T* g = as<T>(b.V[k - 1]) + (size_t)(t.p0 + p) * Cf::CL + c * NLM;
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) V[lm] = p < t.np ? g[lm] : 0.0f;
   }
@@ -427,59 +453,60 @@ AL_DEV void load_v(int k, const PassBufs& b, const TileMeta& t, int p, int c, co
 
 // ============================================================================
 // Pass B_k (1 <= k < L): tensor product, mixing, latent MLP, e^{k+1} scatter.
-template <class Cf>
+template <class Cf, class T, int TT>
 __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, NT = Cf::NT, NS = Cf::NS, CL = Cf::CL;
   constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LMAX = Cf::LMAX;
   using Tp = TP<LMAX>;
-  __shared__ TileMeta t;
+  __shared__ TileMeta<TT> t;
+  constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
-  float* s_h = cv.take(kTile * LDH);
-  float* s_z1 = cv.take(kTile * LDD);
-  float* s_w0 = cv.take(kTile * Cf::NW0);
-  float* s_G = cv.take(kTile * CL);
-  float* s_T = cv.take(kTile * C * NT);
-  float* s_fc = cv.take(kTile);
-  float* s_Y = cv.take(kTile * NLM);
-  float* s_e = cv.take(kTile * C);
+  T* s_h = cv.take<T>(TT * LDH);
+  T* s_z1 = cv.take<T>(TT * LDD);
+  T* s_w0 = cv.take<T>(TT * Cf::NW0);
+  T* s_G = cv.take<T>(TT * CL);
+  T* s_T = cv.take<T>(TT * C * NT);
+  T* s_fc = cv.take<T>(TT);
+  T* s_Y = cv.take<T>(TT * NLM);
+  T* s_e = cv.take<T>(TT * C);
   float* s_mix = cv.take(Cf::MIXW);
   const LayerW& LW = w.layer[k - 1];
   stage_mix<Cf>(LW, s_mix);
-  if (threadIdx.x < kTile) {
+  if (threadIdx.x < TT) {
     const int p = threadIdx.x;
-    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    T u[3], d, fc = 0.0f, dfc, Y[NLM];
     for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-    if (p < t.np) geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+    if (p < t.np) geometry<Cf, T>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
     s_fc[p] = fc;
     for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
   }
-  load_rows<D>(b.X[k - 1], t, s_h, LDH);
-  load_segments<CL>(b.gam[k], b.row_ptr, t, s_G);
+  load_rows<D>(as<T>(b.X[k - 1]), t, s_h, LDH);
+  load_segments<CL>(as<T>(b.gam[k]), b.row_ptr, t, s_G);
   __syncthreads();
   if (k == 1) {
-    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D, TT>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   for (int c = sub; c < C; c += kSub) {
-    float V[NLM], G[NLM], T[NT];
-    load_v<Cf>(k, b, t, p, c, s_w0, s_Y, V);
+    T V[NLM], G[NLM], To[NT];
+    load_v<Cf, TT>(k, b, t, p, c, s_w0, s_Y, V);
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
-    Tp::fwd(V, G, T);
+    Tp::fwd(V, G, To);
 #pragma unroll
-    for (int o = 0; o < NT; ++o) s_T[(p * C + c) * NT + o] = T[o];
+    for (int o = 0; o < NT; ++o) s_T[(p * C + c) * NT + o] = To[o];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = T[q];
+    for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = To[q];
   }
   cp_async_wait<0>();
   __syncthreads();
   if (b.train) {
-    dump_rows<C * NS>(b.tr.s[k], t, s_h + D, LDH);
-    dump_rows<C * NT>(b.tr.T[k], t, s_T, C * NT);
+    dump_rows<C * NS>(b.tr.s[k], b.trt.s[k], t, s_h + D, LDH);
+    dump_rows<C * NT>(b.tr.T[k], b.trt.T[k], t, s_T, C * NT);
   }
   // channel mixing: V^k[c'][l3 m] = sum_{c, q} mix_l3[c'][c P + q] T[c][l3 block q m]
   for (int co = sub; co < C; co += kSub) {
@@ -488,91 +515,99 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
       const int Pl = Tp::P(l3), off = Tp::toff(l3), nm = 2 * l3 + 1;
       const float* Wm = s_mix + mix_off<Cf>(l3) + co * (C * Pl);
       for (int m = 0; m < nm; ++m) {
-        float acc = 0.0f;
+        T acc = 0.0f;
         for (int c = 0; c < C; ++c)
           for (int q = 0; q < Pl; ++q)
             acc = fmaf(Wm[c * Pl + q], s_T[(p * C + c) * NT + off + q * nm + m], acc);
-        if (p < t.np) b.V[k][(size_t)(t.p0 + p) * CL + co * NLM + l3 * l3 + m] = acc;
+        if (p < t.np) as<T>(b.V[k])[(size_t)(t.p0 + p) * CL + co * NLM + l3 * l3 + m] = acc;
       }
     }
   }
-  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) { s_z1[m * LDD + n] = silu(v); });
+  gemm<D, Cf::KH, TT>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, T v) { s_z1[m * LDD + n] = silu(v); });
   __syncthreads();
-  float* Xk = b.X[k];
-  gemm<D, D>(s_z1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) {
-    const float x = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;
+  T* Xk = as<T>(b.X[k]);
+  gemm<D, D, TT>(s_z1, LDD, LW.lat1.t, s_wb, [&](int m, int n, T v) {
+    const T x = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;
     s_h[m * LDH + n] = x;
     if (m < t.np) Xk[(size_t)(t.p0 + m) * D + n] = x;
   });
   __syncthreads();
-  gemm<C, D>(s_h, LDH, w.layer[k].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  gemm<C, D, TT>(s_h, LDH, w.layer[k].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
   __syncthreads();
-  store_segments<CL>(b.gam[k + 1], t, [&](int pp, int x) {
+  store_segments<CL>(as<T>(b.gam[k + 1]), t, [&](int pp, int x) {
     return s_e[pp * C + x / NLM] * s_Y[pp * NLM + x % NLM];
   });
 }
 
 // Reduce a per-thread value over the kSub consecutive lanes of one pair.
-AL_DEV float sub_sum(float v) {
+template <int kSub, class T>
+AL_DEV T sub_sum_(T v) {
 #pragma unroll
-  for (int o = kSub / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = kSub / 2; o > 0; o >>= 1) v += shfl_xor(0xffffffffu, v, o);
   return v;
 }
 
 // ============================================================================
 // Pass C: last layer L and energy MLP forward, then their adjoint.
-template <class Cf>
+template <class Cf, class T, int TT>
 __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   constexpr int D = Cf::D, C = Cf::C, E = Cf::E, NLM = Cf::NLM, NS = Cf::NS, CL = Cf::CL;
   constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LDE = Cf::LDE, LMAX = Cf::LMAX;
   using Tp = TP<LMAX>;
-  __shared__ TileMeta t;
-  __shared__ float s_eij[kTile];
-  __shared__ float s_sig[kTile];
+  __shared__ TileMeta<TT> t;
+  constexpr int kSub = kThreads / TT;
+  __shared__ T s_eij[TT];
+  __shared__ T s_sig[TT];
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   const int L = w.n_layers;
   const LayerW& LW = w.layer[L - 1];
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
-  float* s_h = cv.take(kTile * LDH);
-  float* s_z1 = cv.take(kTile * LDD);
-  float* s_a1 = cv.take(kTile * LDD);
-  float* s_z2 = cv.take(kTile * LDD);
-  float* s_ze = cv.take(kTile * LDE);
-  float* s_ae = cv.take(kTile * LDE);
-  float* s_G = cv.take(kTile * CL);
-  float* s_dg = cv.take(kTile * CL);
-  float* s_w0 = cv.take(kTile * Cf::NW0);
-  float* s_dw0 = cv.take(kTile * Cf::NW0);
-  float* s_fc = cv.take(kTile);
-  float* s_Y = cv.take(kTile * NLM);
-  float* s_dy = cv.take(kTile * NLM);
-  float* s_du = cv.take(kTile);
-  if (threadIdx.x < kTile) {
+  T* s_h = cv.take<T>(TT * LDH);
+  T* s_z1 = cv.take<T>(TT * LDD);
+  T* s_a1 = cv.take<T>(TT * LDD);
+  T* s_z2 = cv.take<T>(TT * LDD);
+  T* s_ze = cv.take<T>(TT * LDE);
+  T* s_ae = cv.take<T>(TT * LDE);
+  T* s_G = cv.take<T>(TT * CL);
+  T* s_dg = cv.take<T>(TT * CL);
+  T* s_w0 = cv.take<T>(TT * Cf::NW0);
+  T* s_dw0 = cv.take<T>(TT * Cf::NW0);
+  T* s_fc = cv.take<T>(TT);
+  T* s_Y = cv.take<T>(TT * NLM);
+  T* s_dy = cv.take<T>(TT * NLM);
+  T* s_du = cv.take<T>(TT);
+  if (threadIdx.x < TT) {
     const int p = threadIdx.x;
-    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    T u[3], d, fc = 0.0f, dfc, Y[NLM];
     for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-    if (p < t.np) geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+    if (p < t.np) geometry<Cf, T>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
     s_fc[p] = fc;
     for (int q = 0; q < NLM; ++q) {
       s_Y[p * NLM + q] = Y[q];
       s_dy[p * NLM + q] = 0.0f;
     }
-    s_sig[p] = p < t.np ? (b.tr.seed_atom ? b.tr.seed_atom[t.pi[p]] : b.tr.seed) * w.sigma[b.species[t.pi[p]]]
-                        : 0.0f;
+    // dL/dE_ij = seed * sigma_Z; tangent passes take the seed's tangent too
+    T sd = 0.0f;
+    if (p < t.np) {
+      sd = b.tr.seed_atom ? b.tr.seed_atom[t.pi[p]] : b.tr.seed;
+      if constexpr (is_dual<T>::value) sd.t = b.tr.seed_atom_t ? b.tr.seed_atom_t[t.pi[p]] : 0.0f;
+      sd = sd * w.sigma[b.species[t.pi[p]]];
+    }
+    s_sig[p] = sd;
   }
-  load_rows<D>(b.X[L - 1], t, s_h, LDH);
-  load_segments<CL>(b.gam[L], b.row_ptr, t, s_G);
+  load_rows<D>(as<T>(b.X[L - 1]), t, s_h, LDH);
+  load_segments<CL>(as<T>(b.gam[L]), b.row_ptr, t, s_G);
   __syncthreads();
   if (L == 1) {
-    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D, TT>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   for (int c = sub; c < C; c += kSub) {
-    float V[NLM], G[NLM], S[NS];
-    load_v<Cf>(L, b, t, p, c, s_w0, s_Y, V);
+    T V[NLM], G[NLM], S[NS];
+    load_v<Cf, TT>(L, b, t, p, c, s_w0, s_Y, V);
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
     Tp::fwd_s(V, G, S);
@@ -580,36 +615,36 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
   }
   __syncthreads();
-  if (b.train) dump_rows<C * NS>(b.tr.s[L], t, s_h + D, LDH);
-  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<C * NS>(b.tr.s[L], b.trt.s[L], t, s_h + D, LDH);
+  gemm<D, Cf::KH, TT>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) {
+  gemm<D, D, TT>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, T v) {
     s_z2[m * LDD + n] = v;
     s_h[m * LDH + n] = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;   // x^L
   });
   __syncthreads();
-  gemm<E, D>(s_h, LDH, w.e0.t, s_wb, [&](int m, int n, float v) {
+  gemm<E, D, TT>(s_h, LDH, w.e0.t, s_wb, [&](int m, int n, T v) {
     s_ze[m * LDE + n] = v;
     s_ae[m * LDE + n] = silu(v);
   });
   __syncthreads();
   if (b.train) {
-    dump_rows<D>(b.tr.a1_l[L], t, s_a1, LDD);
-    dump_rows<D>(b.tr.xL, t, s_h, LDH);
-    dump_rows<E>(b.tr.ae, t, s_ae, LDE);
-    dump_rows<1>(b.tr.dEij, t, s_sig, 1);
+    dump_rows<D>(b.tr.a1_l[L], b.trt.a1_l[L], t, s_a1, LDD);
+    dump_rows<D>(b.tr.xL, b.trt.xL, t, s_h, LDH);
+    dump_rows<E>(b.tr.ae, b.trt.ae, t, s_ae, LDE);
+    dump_rows<1>(b.tr.dEij, b.trt.dEij, t, s_sig, 1);
   }
-  if (threadIdx.x < kTile) {
+  if (threadIdx.x < TT) {
     const int q = threadIdx.x;
-    float acc = 0.0f;
+    T acc = 0.0f;
     for (int n = 0; n < E; ++n) acc = fmaf(__ldg(w.eout + n), s_ae[q * LDE + n], acc);
     s_eij[q] = q < t.np ? acc : 0.0f;
   }
   // adjoint of the energy MLP: dE/dE_ij = sigma_{Z_i}
-  for (int idx = threadIdx.x; idx < kTile * E; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < TT * E; idx += kThreads) {
     const int m = idx / E, n = idx % E;
     s_ze[m * LDE + n] = s_sig[m] * __ldg(w.eout + n) * silu_grad(s_ze[m * LDE + n]);
   }
@@ -618,43 +653,43 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     const int s = threadIdx.x;
     double acc = 0.0;
     for (int q = 0; q < t.np; ++q)
-      if (t.seg[q] == s) acc += (double)s_eij[q];
+      if (t.seg[q] == s) acc += (double)val(s_eij[q]);
     b.epart[blockIdx.x + t.atom[s]] = acc;
   }
-  if (b.train) dump_rows<E>(b.tr.dze, t, s_ze, LDE);
-  gemm<D, E>(s_ze, LDE, w.e0.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] = v; });  // dx^L
+  if (b.train) dump_rows<E>(b.tr.dze, b.trt.dze, t, s_ze, LDE);
+  gemm<D, E, TT>(s_ze, LDE, w.e0.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] = v; });  // dx^L
   __syncthreads();
   {
-    float du = 0.0f;
-    const float fc = s_fc[p];
+    T du = 0.0f;
+    const T fc = s_fc[p];
     for (int n = sub; n < D; n += kSub) {
-      const float dx = s_h[p * LDH + n];
-      const float z2 = s_z2[p * LDD + n];
+      const T dx = s_h[p * LDH + n];
+      const T z2 = s_z2[p * LDD + n];
       du = fmaf(dx, silu(z2), du);
       s_z2[p * LDD + n] = dx * fc * kRsqrt2 * silu_grad(z2);
     }
-    du = sub_sum(du);
+    du = sub_sum_<kSub>(du);
     if (sub == 0) s_du[p] = du * kRsqrt2;
   }
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.dz2_l[L], t, s_z2, LDD);
-  gemm<D, D>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<D>(b.tr.dz2_l[L], b.trt.dz2_l[L], t, s_z2, LDD);
+  gemm<D, D, TT>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.dz1_l[L], t, s_z1, LDD);
-  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<D>(b.tr.dz1_l[L], b.trt.dz1_l[L], t, s_z1, LDD);
+  gemm<Cf::KH, D, TT>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, T v) {
     if (n < D) s_h[m * LDH + n] = v + s_h[m * LDH + n] * kRsqrt2;   // dx^{L-1}
     else s_h[m * LDH + n] = v;                                      // d(scalars)
   });
   __syncthreads();
   {
-    float dyl[NLM];
+    T dyl[NLM];
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
     for (int c = sub; c < C; c += kSub) {
-      float V[NLM], G[NLM], dS[NS], dV[NLM], dG[NLM];
-      load_v<Cf>(L, b, t, p, c, s_w0, s_Y, V);
+      T V[NLM], G[NLM], dS[NS], dV[NLM], dG[NLM];
+      load_v<Cf, TT>(L, b, t, p, c, s_w0, s_Y, V);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) {
         G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
@@ -668,12 +703,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
       for (int lm = 0; lm < NLM; ++lm) s_dg[p * CL + c * NLM + lm] = dG[lm];
       if (L >= 2) {
         if (p < t.np) {
-          float* g = b.dV + (size_t)(t.p0 + p) * CL + c * NLM;
+          T* g = as<T>(b.dV) + (size_t)(t.p0 + p) * CL + c * NLM;
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) g[lm] = dV[lm];
         }
       } else {
-        float dw[LMAX + 1];
+        T dw[LMAX + 1];
 #pragma unroll
         for (int l = 0; l <= LMAX; ++l) dw[l] = 0.0f;
 #pragma unroll
@@ -688,104 +723,105 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     if (L == 1) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) {
-        const float v = sub_sum(dyl[lm]);
+        const T v = sub_sum_<kSub>(dyl[lm]);
         if (sub == 0) s_dy[p * NLM + lm] = v;
       }
     }
   }
   __syncthreads();
   if (L == 1) {
-    if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, t, s_dw0, Cf::NW0);
-    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
+    if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, b.trt.dw0, t, s_dw0, Cf::NW0);
+    gemm<D, Cf::NW0, TT>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
     const int m = idx / D, n = idx % D;
-    b.dX[(size_t)(t.p0 + m) * D + n] = s_h[m * LDH + n];
+    as<T>(b.dX)[(size_t)(t.p0 + m) * D + n] = s_h[m * LDH + n];
   }
   for (int idx = threadIdx.x; idx < t.np * NLM; idx += kThreads)
-    b.dY[(size_t)t.p0 * NLM + idx] = s_dy[idx];
-  if (threadIdx.x < t.np) b.dU[t.p0 + threadIdx.x] = s_du[threadIdx.x];
-  store_segments<CL>(b.dgam[L], t, [&](int pp, int x) { return s_dg[pp * CL + x]; });
+    as<T>(b.dY)[(size_t)t.p0 * NLM + idx] = s_dy[idx];
+  if (threadIdx.x < t.np) as<T>(b.dU)[t.p0 + threadIdx.x] = s_du[threadIdx.x];
+  store_segments<CL>(as<T>(b.dgam[L]), t, [&](int pp, int x) { return s_dg[pp * CL + x]; });
 }
 
 // ============================================================================
 // Pass B_k^T (k = L-1 .. 1): adjoint of the Gamma^{k+1} scatter and of layer k.
-template <class Cf>
+template <class Cf, class T, int TT>
 __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, int k) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, NT = Cf::NT, NS = Cf::NS, CL = Cf::CL;
   constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LMAX = Cf::LMAX;
   using Tp = TP<LMAX>;
-  __shared__ TileMeta t;
+  __shared__ TileMeta<TT> t;
+  constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   const LayerW& LW = w.layer[k - 1];
   const LayerW& LN = w.layer[k];
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
-  float* s_h = cv.take(kTile * LDH);
-  float* s_z1 = cv.take(kTile * LDD);
-  float* s_a1 = cv.take(kTile * LDD);
-  float* s_z2 = cv.take(kTile * LDD);
-  float* s_tmp = cv.take(kTile * (CL > LDD ? CL : LDD));
-  float* s_G = cv.take(kTile * CL);
-  float* s_dG = cv.take(kTile * CL);
-  float* s_w0 = cv.take(kTile * Cf::NW0);
-  float* s_dw0 = cv.take(kTile * Cf::NW0);
-  float* s_e = cv.take(kTile * C);
-  float* s_de = cv.take(kTile * C);
-  float* s_fc = cv.take(kTile);
-  float* s_Y = cv.take(kTile * NLM);
-  float* s_dy = cv.take(kTile * NLM);
-  float* s_du = cv.take(kTile);
+  T* s_h = cv.take<T>(TT * LDH);
+  T* s_z1 = cv.take<T>(TT * LDD);
+  T* s_a1 = cv.take<T>(TT * LDD);
+  T* s_z2 = cv.take<T>(TT * LDD);
+  T* s_tmp = cv.take<T>(TT * (CL > LDD ? CL : LDD));
+  T* s_G = cv.take<T>(TT * CL);
+  T* s_dG = cv.take<T>(TT * CL);
+  T* s_w0 = cv.take<T>(TT * Cf::NW0);
+  T* s_dw0 = cv.take<T>(TT * Cf::NW0);
+  T* s_e = cv.take<T>(TT * C);
+  T* s_de = cv.take<T>(TT * C);
+  T* s_fc = cv.take<T>(TT);
+  T* s_Y = cv.take<T>(TT * NLM);
+  T* s_dy = cv.take<T>(TT * NLM);
+  T* s_du = cv.take<T>(TT);
   float* s_mix = cv.take(Cf::MIXW);
   stage_mix<Cf>(LW, s_mix);
-  if (threadIdx.x < kTile) {
+  if (threadIdx.x < TT) {
     const int p = threadIdx.x;
-    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    T u[3], d, fc = 0.0f, dfc, Y[NLM];
     for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-    if (p < t.np) geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+    if (p < t.np) geometry<Cf, T>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
     s_fc[p] = fc;
     for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
   }
   cp_async_wait<0>();
-  load_rows<D>(b.X[k], t, s_z2, LDD);          // x^k (temporarily)
-  load_rows<D>(b.X[k - 1], t, s_h, LDH);       // x^{k-1}
-  load_segments<CL>(b.gam[k], b.row_ptr, t, s_G);
-  load_segments<CL>(b.dgam[k + 1], b.row_ptr, t, s_dG);
+  load_rows<D>(as<T>(b.X[k]), t, s_z2, LDD);          // x^k (temporarily)
+  load_rows<D>(as<T>(b.X[k - 1]), t, s_h, LDH);       // x^{k-1}
+  load_segments<CL>(as<T>(b.gam[k]), b.row_ptr, t, s_G);
+  load_segments<CL>(as<T>(b.dgam[k + 1]), b.row_ptr, t, s_dG);
   __syncthreads();
-  gemm<C, D>(s_z2, LDD, LN.env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });  // e^{k+1}
+  gemm<C, D, TT>(s_z2, LDD, LN.env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });  // e^{k+1}
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   {
-    const float* dg = s_dG + (p < t.np ? t.seg[p] : 0) * CL;
+    const T* dg = s_dG + (p < t.np ? t.seg[p] : 0) * CL;
     for (int c = sub; c < C; c += kSub) {
-      float acc = 0.0f;
+      T acc = 0.0f;
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) acc = fmaf(dg[c * NLM + lm], s_Y[p * NLM + lm], acc);
       s_de[p * C + c] = p < t.np ? acc : 0.0f;
     }
     for (int lm = sub; lm < NLM; lm += kSub) {
-      float acc = 0.0f;
+      T acc = 0.0f;
       for (int c = 0; c < C; ++c) acc = fmaf(dg[c * NLM + lm], s_e[p * C + c], acc);
       s_dy[p * NLM + lm] = p < t.np ? acc : 0.0f;
     }
   }
   __syncthreads();
-  if (b.train) dump_rows<C>(b.tr.de[k], t, s_de, C);
-  const float* dXg = b.dX;
-  gemm<D, C>(s_de, C, LN.env.n, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<C>(b.tr.de[k], b.trt.de[k], t, s_de, C);
+  const T* dXg = as<T>(b.dX);
+  gemm<D, C, TT>(s_de, C, LN.env.n, s_wb, [&](int m, int n, T v) {
     s_z2[m * LDD + n] = v + (m < t.np ? dXg[(size_t)(t.p0 + m) * D + n] : 0.0f);   // dx^k
   });
   __syncthreads();
   // recompute layer k forward (scalars, latent MLP)
   if (k == 1) {
-    gemm<Cf::NW0, D>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, float v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D, TT>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   for (int c = sub; c < C; c += kSub) {
-    float V[NLM], G[NLM], S[NS];
-    load_v<Cf>(k, b, t, p, c, s_w0, s_Y, V);
+    T V[NLM], G[NLM], S[NS];
+    load_v<Cf, TT>(k, b, t, p, c, s_w0, s_Y, V);
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
     Tp::fwd_s(V, G, S);
@@ -793,61 +829,61 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
   }
   __syncthreads();
-  gemm<D, Cf::KH>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, float v) {
+  gemm<D, Cf::KH, TT>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, float v) { s_tmp[m * LDD + n] = v; });  // z2
+  gemm<D, D, TT>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, T v) { s_tmp[m * LDD + n] = v; });  // z2
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.a1_l[k], t, s_a1, LDD);
+  if (b.train) dump_rows<D>(b.tr.a1_l[k], b.trt.a1_l[k], t, s_a1, LDD);
   {
-    float du = 0.0f;
-    const float fc = s_fc[p];
+    T du = 0.0f;
+    const T fc = s_fc[p];
     for (int n = sub; n < D; n += kSub) {
-      const float dx = s_z2[p * LDD + n];
-      const float z2 = s_tmp[p * LDD + n];
+      const T dx = s_z2[p * LDD + n];
+      const T z2 = s_tmp[p * LDD + n];
       du = fmaf(dx, silu(z2), du);
       s_z2[p * LDD + n] = dx * fc * kRsqrt2 * silu_grad(z2);   // dz2
       s_h[p * LDH + n] = dx * kRsqrt2;                          // residual part of dx^{k-1}
     }
-    du = sub_sum(du);
+    du = sub_sum_<kSub>(du);
     if (sub == 0) s_du[p] = du * kRsqrt2;
   }
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.dz2_l[k], t, s_z2, LDD);
-  load_rows<CL>(b.dV, t, s_tmp, CL);            // dV^k
-  gemm<D, D>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<D>(b.tr.dz2_l[k], b.trt.dz2_l[k], t, s_z2, LDD);
+  load_rows<CL>(as<T>(b.dV), t, s_tmp, CL);            // dV^k
+  gemm<D, D, TT>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);     // dz1
   });
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.dz1_l[k], t, s_z1, LDD);
-  gemm<Cf::KH, D>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<D>(b.tr.dz1_l[k], b.trt.dz1_l[k], t, s_z1, LDD);
+  gemm<Cf::KH, D, TT>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, T v) {
     if (n < D) s_h[m * LDH + n] += v;
     else s_h[m * LDH + n] = v;
   });
   __syncthreads();
   // adjoint of mixing and of the full tensor product of layer k
   {
-    float dyl[NLM];
+    T dyl[NLM];
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) dyl[lm] = 0.0f;
     for (int c = sub; c < C; c += kSub) {
-      float dT[NT];
+      T dT[NT];
 #pragma unroll
       for (int l3 = 0; l3 <= LMAX; ++l3) {
         const int Pl = Tp::P(l3), off = Tp::toff(l3), nm = 2 * l3 + 1;
         for (int q = 0; q < Pl; ++q)
           for (int m = 0; m < nm; ++m) {
-            float acc = l3 == 0 ? s_h[p * LDH + D + c * NS + q] : 0.0f;
+            T acc = l3 == 0 ? s_h[p * LDH + D + c * NS + q] : 0.0f;
             for (int co = 0; co < C; ++co)
               acc = fmaf(s_mix[mix_off<Cf>(l3) + co * (C * Pl) + c * Pl + q],
                          s_tmp[p * CL + co * NLM + l3 * l3 + m], acc);
             dT[off + q * nm + m] = acc;
           }
       }
-      float V[NLM], G[NLM], dV[NLM], dG[NLM];
-      load_v<Cf>(k, b, t, p, c, s_w0, s_Y, V);
+      T V[NLM], G[NLM], dV[NLM], dG[NLM];
+      load_v<Cf, TT>(k, b, t, p, c, s_w0, s_Y, V);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) {
         G[lm] = p < t.np ? s_G[t.seg[p] * CL + c * NLM + lm] : 0.0f;
@@ -859,12 +895,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
       for (int lm = 0; lm < NLM; ++lm) s_dG[p * CL + c * NLM + lm] = dG[lm];   // reuse
       if (k >= 2) {
         if (p < t.np) {
-          float* g = b.dV + (size_t)(t.p0 + p) * CL + c * NLM;
+          T* g = as<T>(b.dV) + (size_t)(t.p0 + p) * CL + c * NLM;
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) g[lm] = dV[lm];
         }
       } else {
-        float dw[LMAX + 1];
+        T dw[LMAX + 1];
 #pragma unroll
         for (int l = 0; l <= LMAX; ++l) dw[l] = 0.0f;
 #pragma unroll
@@ -879,199 +915,206 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     if (k == 1) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) {
-        const float v = sub_sum(dyl[lm]);
+        const T v = sub_sum_<kSub>(dyl[lm]);
         if (sub == 0) s_dy[p * NLM + lm] += v;
       }
     }
   }
   __syncthreads();
   if (k == 1) {
-    if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, t, s_dw0, Cf::NW0);
-    gemm<D, Cf::NW0>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, float v) { s_h[m * LDH + n] += v; });
+    if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, b.trt.dw0, t, s_dw0, Cf::NW0);
+    gemm<D, Cf::NW0, TT>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
     const int m = idx / D, n = idx % D;
-    b.dX[(size_t)(t.p0 + m) * D + n] = s_h[m * LDH + n];
+    as<T>(b.dX)[(size_t)(t.p0 + m) * D + n] = s_h[m * LDH + n];
   }
   for (int idx = threadIdx.x; idx < t.np * NLM; idx += kThreads)
-    b.dY[(size_t)t.p0 * NLM + idx] += s_dy[idx];
-  if (threadIdx.x < t.np) b.dU[t.p0 + threadIdx.x] += s_du[threadIdx.x];
-  store_segments<CL>(b.dgam[k], t, [&](int pp, int x) { return s_dG[pp * CL + x]; });
+    as<T>(b.dY)[(size_t)t.p0 * NLM + idx] += s_dy[idx];
+  if (threadIdx.x < t.np) as<T>(b.dU)[t.p0 + threadIdx.x] += s_du[threadIdx.x];
+  store_segments<CL>(as<T>(b.dgam[k]), t, [&](int pp, int x) { return s_dG[pp * CL + x]; });
 }
 
 // ============================================================================
 // Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP and of the
 // geometry; writes g_ij = dE/dDelta_ij.
-template <class Cf>
+template <class Cf, class T, int TT>
 __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, CL = Cf::CL, LDD = Cf::LDD, NB = Cf::NB;
-  __shared__ TileMeta t;
+  __shared__ TileMeta<TT> t;
+  constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
   if (!tile_setup(b, t)) return;
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
-  float* s_h0 = cv.take(kTile * Cf::LDH0);
-  float* s_z1 = cv.take(kTile * LDD);
-  float* s_a1 = cv.take(kTile * LDD);
-  float* s_z2 = cv.take(kTile * LDD);
-  float* s_x = cv.take(kTile * LDD);
-  float* s_dx = cv.take(kTile * LDD);
-  float* s_dG = cv.take(kTile * CL);
-  float* s_e = cv.take(kTile * C);
-  float* s_de = cv.take(kTile * C);
-  float* s_dh0 = cv.take(kTile * Cf::LDH0);
-  float* s_geo = cv.take(kTile * 8);        // u[3], d, fc, dfc
-  float* s_dB = cv.take(kTile * NB);
-  float* s_Y = cv.take(kTile * NLM);
-  float* s_dy = cv.take(kTile * NLM);
-  float* s_du = cv.take(kTile);
-  if (threadIdx.x < kTile) {
+  T* s_h0 = cv.take<T>(TT * Cf::LDH0);
+  T* s_z1 = cv.take<T>(TT * LDD);
+  T* s_a1 = cv.take<T>(TT * LDD);
+  T* s_z2 = cv.take<T>(TT * LDD);
+  T* s_x = cv.take<T>(TT * LDD);
+  T* s_dx = cv.take<T>(TT * LDD);
+  T* s_dG = cv.take<T>(TT * CL);
+  T* s_e = cv.take<T>(TT * C);
+  T* s_de = cv.take<T>(TT * C);
+  T* s_dh0 = cv.take<T>(TT * Cf::LDH0);
+  T* s_geo = cv.take<T>(TT * 8);        // u[3], d, fc, dfc
+  T* s_dB = cv.take<T>(TT * NB);
+  T* s_Y = cv.take<T>(TT * NLM);
+  T* s_dy = cv.take<T>(TT * NLM);
+  T* s_du = cv.take<T>(TT);
+  if (threadIdx.x < TT) {
     const int p = threadIdx.x;
-    float* h = s_h0 + p * Cf::LDH0;
+    T* h = s_h0 + p * Cf::LDH0;
     for (int q = 0; q < Cf::LDH0; ++q) h[q] = 0.0f;
-    float u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f, Y[NLM], B[NB], dB[NB];
+    T u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f, Y[NLM], B[NB], dB[NB];
     for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
     for (int q = 0; q < NB; ++q) dB[q] = 0.0f;
     if (p < t.np) {
-      geometry<Cf>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
+      geometry<Cf, T>(b, w.rc, t.pi[p], t.pj[p], t.code[p], u, d, fc, dfc, Y);
       bessel<NB>(d, w.rc, B, dB);
       h[b.species[t.pi[p]]] = 1.0f;
       h[Cf::S + b.species[t.pj[p]]] = 1.0f;
       for (int q = 0; q < NB; ++q) h[2 * Cf::S + q] = B[q];
     }
-    float* g = s_geo + p * 8;
+    T* g = s_geo + p * 8;
     g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
     for (int q = 0; q < NB; ++q) s_dB[p * NB + q] = dB[q];
     for (int q = 0; q < NLM; ++q) s_Y[p * NLM + q] = Y[q];
   }
-  load_rows<D>(b.dX, t, s_dx, LDD);
-  load_segments<CL>(b.dgam[1], b.row_ptr, t, s_dG);
+  load_rows<D>(as<T>(b.dX), t, s_dx, LDD);
+  load_segments<CL>(as<T>(b.dgam[1]), b.row_ptr, t, s_dG);
   __syncthreads();
-  gemm<D, Cf::H0>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, float v) {
+  gemm<D, Cf::H0, TT>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D>(s_a1, LDD, w.tb1.t, s_wb, [&](int m, int n, float v) {
+  gemm<D, D, TT>(s_a1, LDD, w.tb1.t, s_wb, [&](int m, int n, T v) {
     s_z2[m * LDD + n] = v;
     s_x[m * LDD + n] = s_geo[m * 8 + 4] * silu(v);
   });
   __syncthreads();
   if (b.train) {
-    dump_rows<Cf::LDH0>(b.tr.h0, t, s_h0, Cf::LDH0);
-    dump_rows<D>(b.tr.a1_tb, t, s_a1, LDD);
+    dump_rows<Cf::LDH0>(b.tr.h0, b.trt.h0, t, s_h0, Cf::LDH0);
+    dump_rows<D>(b.tr.a1_tb, b.trt.a1_tb, t, s_a1, LDD);
   }
-  gemm<C, D>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, float v) { s_e[m * C + n] = v; });
+  gemm<C, D, TT>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   {
-    const float* dg = s_dG + (p < t.np ? t.seg[p] : 0) * CL;
+    const T* dg = s_dG + (p < t.np ? t.seg[p] : 0) * CL;
     for (int c = sub; c < C; c += kSub) {
-      float acc = 0.0f;
+      T acc = 0.0f;
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) acc = fmaf(dg[c * NLM + lm], s_Y[p * NLM + lm], acc);
       s_de[p * C + c] = p < t.np ? acc : 0.0f;
     }
     for (int lm = sub; lm < NLM; lm += kSub) {
-      float acc = 0.0f;
+      T acc = 0.0f;
       for (int c = 0; c < C; ++c) acc = fmaf(dg[c * NLM + lm], s_e[p * C + c], acc);
       s_dy[p * NLM + lm] = p < t.np ? acc : 0.0f;
     }
   }
   __syncthreads();
-  if (b.train) dump_rows<C>(b.tr.de[0], t, s_de, C);
-  gemm<D, C>(s_de, C, w.layer[0].env.n, s_wb, [&](int m, int n, float v) { s_dx[m * LDD + n] += v; });
+  if (b.train) dump_rows<C>(b.tr.de[0], b.trt.de[0], t, s_de, C);
+  gemm<D, C, TT>(s_de, C, w.layer[0].env.n, s_wb, [&](int m, int n, T v) { s_dx[m * LDD + n] += v; });
   __syncthreads();
   {
-    float du = 0.0f;
-    const float fc = s_geo[p * 8 + 4];
+    T du = 0.0f;
+    const T fc = s_geo[p * 8 + 4];
     for (int n = sub; n < D; n += kSub) {
-      const float dx = s_dx[p * LDD + n];
-      const float z2 = s_z2[p * LDD + n];
+      const T dx = s_dx[p * LDD + n];
+      const T z2 = s_z2[p * LDD + n];
       du = fmaf(dx, silu(z2), du);
       s_z2[p * LDD + n] = dx * fc * silu_grad(z2);
     }
-    du = sub_sum(du);
+    du = sub_sum_<kSub>(du);
     if (sub == 0) s_du[p] = du;
   }
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.dz2_tb, t, s_z2, LDD);
-  gemm<D, D>(s_z2, LDD, w.tb1.n, s_wb, [&](int m, int n, float v) {
+  if (b.train) dump_rows<D>(b.tr.dz2_tb, b.trt.dz2_tb, t, s_z2, LDD);
+  gemm<D, D, TT>(s_z2, LDD, w.tb1.n, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
-  if (b.train) dump_rows<D>(b.tr.dz1_tb, t, s_z1, LDD);
-  gemm<Cf::H0, D>(s_z1, LDD, w.tb0.n, s_wb, [&](int m, int n, float v) { s_dh0[m * Cf::LDH0 + n] = v; });
+  if (b.train) dump_rows<D>(b.tr.dz1_tb, b.trt.dz1_tb, t, s_z1, LDD);
+  gemm<Cf::H0, D, TT>(s_z1, LDD, w.tb0.n, s_wb, [&](int m, int n, T v) { s_dh0[m * Cf::LDH0 + n] = v; });
   __syncthreads();
   if (threadIdx.x < t.np) {
     const int q = threadIdx.x;
-    const float* g = s_geo + q * 8;
-    const float u[3] = {g[0], g[1], g[2]};
-    const float d = g[3], dfc = g[5];
+    const T* g = s_geo + q * 8;
+    const T u[3] = {g[0], g[1], g[2]};
+    const T d = g[3], dfc = g[5];
     const size_t pp = (size_t)(t.p0 + q);
-    float gd = (s_du[q] + b.dU[pp]) * dfc;
+    T gd = (s_du[q] + as<T>(b.dU)[pp]) * dfc;
     for (int n = 0; n < NB; ++n) gd = fmaf(s_dh0[q * Cf::LDH0 + 2 * Cf::S + n], s_dB[q * NB + n], gd);
-    float dY[NLM];
-    for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[q * NLM + lm] + b.dY[pp * NLM + lm];
-    float gu[3];
+    T dY[NLM];
+    for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[q * NLM + lm] + as<T>(b.dY)[pp * NLM + lm];
+    T gu[3];
     sph_harm_vjp<Cf::LMAX>(u[0], u[1], u[2], dY, gu);
-    const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
-    const float inv = 1.0f / d;
-    for (int a = 0; a < 3; ++a) b.G[pp * 3 + a] = gd * u[a] + (gu[a] - ud * u[a]) * inv;
+    const T ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
+    const T inv = 1.0f / d;
+    for (int a = 0; a < 3; ++a) as<T>(b.G)[pp * 3 + a] = gd * u[a] + (gu[a] - ud * u[a]) * inv;
   }
 }
 
 // ----------------------------------------------------------------------------
-template <class Cf>
+// Dynamic shared memory of each pass for scalar type X and tile TT (in the
+// order of the kernels' carve-up; weight staging stays FP32).
+template <class Cf, class X, int TT>
 struct Smem {
+  static constexpr int K = (int)(sizeof(X) / 4);
   static constexpr int r(int n) { return (n + 3) & ~3; }
-  static constexpr int T = kTile;
-  static constexpr size_t a = 4 * (r(Cf::WB) + r(T * Cf::LDH0) + r(T) + r(T * Cf::NLM) + 2 * r(T * Cf::LDD) + r(T * Cf::C));
-  static constexpr size_t b = 4 * (r(Cf::WB) + r(T * Cf::LDH) + r(T * Cf::LDD) + r(T * Cf::NW0) +
-                                   r(T * Cf::CL) + r(T * Cf::C * Cf::NT) + r(T) + r(T * Cf::NLM) +
-                                   r(T * Cf::C) + r(Cf::MIXW));
-  static constexpr size_t c = 4 * (r(Cf::WB) + r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + 2 * r(T * Cf::LDE) + 2 * r(T * Cf::CL) +
-                                   2 * r(T * Cf::NW0) + r(T) + 2 * r(T * Cf::NLM) + r(T));
+  static constexpr int q(int n) { return r(K * n); }
+  static constexpr int T = TT;
+  static constexpr size_t a = 4 * (r(Cf::WB) + q(T * Cf::LDH0) + q(T) + q(T * Cf::NLM) + 2 * q(T * Cf::LDD) + q(T * Cf::C));
+  static constexpr size_t b = 4 * (r(Cf::WB) + q(T * Cf::LDH) + q(T * Cf::LDD) + q(T * Cf::NW0) +
+                                   q(T * Cf::CL) + q(T * Cf::C * Cf::NT) + q(T) + q(T * Cf::NLM) +
+                                   q(T * Cf::C) + r(Cf::MIXW));
+  static constexpr size_t c = 4 * (r(Cf::WB) + q(T * Cf::LDH) + 3 * q(T * Cf::LDD) + 2 * q(T * Cf::LDE) + 2 * q(T * Cf::CL) +
+                                   2 * q(T * Cf::NW0) + q(T) + 2 * q(T * Cf::NLM) + q(T));
   static constexpr int tmpw = Cf::CL > Cf::LDD ? Cf::CL : Cf::LDD;
-  static constexpr size_t bb = 4 * (r(Cf::WB) + r(T * Cf::LDH) + 3 * r(T * Cf::LDD) + r(T * tmpw) +
-                                    2 * r(T * Cf::CL) + 2 * r(T * Cf::NW0) + 2 * r(T * Cf::C) + r(T) +
-                                    2 * r(T * Cf::NLM) + r(T) + r(Cf::MIXW));
-  static constexpr size_t ab = 4 * (r(Cf::WB) + r(T * Cf::LDH0) + 5 * r(T * Cf::LDD) + r(T * Cf::CL) + 2 * r(T * Cf::C) +
-                                    r(T * Cf::LDH0) + r(T * 8) + r(T * Cf::NB) + 2 * r(T * Cf::NLM) + r(T));
+  static constexpr size_t bb = 4 * (r(Cf::WB) + q(T * Cf::LDH) + 3 * q(T * Cf::LDD) + q(T * tmpw) +
+                                    2 * q(T * Cf::CL) + 2 * q(T * Cf::NW0) + 2 * q(T * Cf::C) + q(T) +
+                                    2 * q(T * Cf::NLM) + q(T) + r(Cf::MIXW));
+  static constexpr size_t ab = 4 * (r(Cf::WB) + q(T * Cf::LDH0) + 5 * q(T * Cf::LDD) + q(T * Cf::CL) + 2 * q(T * Cf::C) +
+                                    q(T * Cf::LDH0) + q(T * 8) + q(T * Cf::NB) + 2 * q(T * Cf::NLM) + q(T));
+  static_assert(a <= 227 * 1024 && b <= 227 * 1024 && c <= 227 * 1024 && bb <= 227 * 1024 && ab <= 227 * 1024,
+                "shared memory per block");
 };
 
-template <class Cf>
+template <class Cf, class X, int TT>
 void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km) {
-  using Sm = Smem<Cf>;
+  using Sm = Smem<Cf, X, TT>;
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_pass_a<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::a);
-    cudaFuncSetAttribute(k_pass_b<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::b);
-    cudaFuncSetAttribute(k_pass_c<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::c);
-    cudaFuncSetAttribute(k_pass_b_bwd<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::bb);
-    cudaFuncSetAttribute(k_pass_a_bwd<Cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::ab);
+    cudaFuncSetAttribute(k_pass_a<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::a);
+    cudaFuncSetAttribute(k_pass_b<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::b);
+    cudaFuncSetAttribute(k_pass_c<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::c);
+    cudaFuncSetAttribute(k_pass_b_bwd<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::bb);
+    cudaFuncSetAttribute(k_pass_a_bwd<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::ab);
     init = true;
   }
-  const int grid = (int)((capacity + kTile - 1) / kTile);
+  const int grid = (int)((capacity + TT - 1) / TT);
   const int L = w.n_layers;
   auto mark = [&](int k) {
     if (km) km->mark(k, s);
   };
   mark(kPhStart);
-  k_pass_a<Cf><<<grid, kThreads, Sm::a, s>>>(w, b);
+  k_pass_a<Cf, X, TT><<<grid, kThreads, Sm::a, s>>>(w, b);
   mark(kPhA);
   for (int k = 1; k < L; ++k) {
-    k_pass_b<Cf><<<grid, kThreads, Sm::b, s>>>(w, b, k);
+    k_pass_b<Cf, X, TT><<<grid, kThreads, Sm::b, s>>>(w, b, k);
     mark(kPhB);
   }
-  k_pass_c<Cf><<<grid, kThreads, Sm::c, s>>>(w, b);
+  k_pass_c<Cf, X, TT><<<grid, kThreads, Sm::c, s>>>(w, b);
   mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
-    k_pass_b_bwd<Cf><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
+    k_pass_b_bwd<Cf, X, TT><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
     mark(kPhBT);
   }
-  k_pass_a_bwd<Cf><<<grid, kThreads, Sm::ab, s>>>(w, b);
+  k_pass_a_bwd<Cf, X, TT><<<grid, kThreads, Sm::ab, s>>>(w, b);
   mark(kPhAT);
 }
 
@@ -1091,10 +1134,18 @@ bool fp32_supported(int lmax, int C, int D, int E) {
 
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
                         int64_t capacity, cudaStream_t s, KernelMarks* km) {
-  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny>(w, b, capacity, s, km);
-  else if (lmax == 0) run<CfgMainL0>(w, b, capacity, s, km);
-  else if (lmax == 1) run<CfgMainL1>(w, b, capacity, s, km);
-  else run<CfgMain>(w, b, capacity, s, km);
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny, float, kTile>(w, b, capacity, s, km);
+  else if (lmax == 0) run<CfgMainL0, float, kTile>(w, b, capacity, s, km);
+  else if (lmax == 1) run<CfgMainL1, float, kTile>(w, b, capacity, s, km);
+  else run<CfgMain, float, kTile>(w, b, capacity, s, km);
+}
+
+int fp32_tangent_tile() { return kTileDual; }
+
+void fp32_tangent_passes(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b, int64_t capacity,
+                         cudaStream_t s) {
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny, Dual, kTileDual>(w, b, capacity, s, nullptr);
+  else if (lmax == 2 && C == 16 && D == 128 && E == 32) run<CfgMain, Dual, kTileDual>(w, b, capacity, s, nullptr);
 }
 
 }  // namespace al

@@ -15,14 +15,16 @@ namespace {
 constexpr int kWT = 64;       // output tile (rows n, cols k) of the reduction
 constexpr int kWP = 32;       // pairs staged per step
 
-// dW[n * ldw + k0 + k] += scale * sum_{p in chunk} dz[p * ldz + n] * x[p * ldx + k]
-// A 64 x 64 output tile per block over one chunk of pairs: 256 threads, each
-// a 4 x 4 register tile fed by two 16-byte shared-memory reads per pair (the
-// dz read is a broadcast within each half warp), one atomic add per output
-// at the end of the chunk.
-__global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int ldz, const float* __restrict__ x,
-                                               int ldx, int P, int N, int K, float scale, float* __restrict__ dW,
-                                               int ldw, int k0, int chunk) {
+// part[z][n][k] = scale * sum_{p in chunk z} dz[p * ldz + n * esz] * x[p * ldx + k * esx]
+// (element strides esz, esx: 1 for plain arrays, 2 for one part of an array
+// of tangent numbers).  A 64 x 64 output tile per block over one chunk of
+// pairs: 256 threads, each a 4 x 4 register tile fed by two 16-byte
+// shared-memory reads per pair (the dz read is a broadcast within each half
+// warp); every chunk writes its own partial, which k_chunk_sum adds in chunk
+// order, so the gradient is the same bits on every run (no atomics).
+__global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int ldz, int esz,
+                                               const float* __restrict__ x, int ldx, int esx, int P, int N, int K,
+                                               float scale, float* __restrict__ part, int chunk) {
   __shared__ __align__(16) float sz[kWP][kWT];
   __shared__ __align__(16) float sx[kWP][kWT];
   const int n0 = blockIdx.x * kWT, kb = blockIdx.y * kWT;
@@ -39,8 +41,8 @@ __global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int
       const int idx = r * 256 + threadIdx.x;
       const int pp = idx / kWT, c = idx % kWT;
       const int p = p0 + pp;
-      sz[pp][c] = (p < pe && n0 + c < N) ? dz[(size_t)p * ldz + n0 + c] : 0.0f;
-      sx[pp][c] = (p < pe && kb + c < K) ? x[(size_t)p * ldx + kb + c] : 0.0f;
+      sz[pp][c] = (p < pe && n0 + c < N) ? dz[(size_t)p * ldz + (size_t)(n0 + c) * esz] : 0.0f;
+      sx[pp][c] = (p < pe && kb + c < K) ? x[(size_t)p * ldx + (size_t)(kb + c) * esx] : 0.0f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -55,27 +57,39 @@ __global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dz, int
     }
     __syncthreads();
   }
+  float* out = part + (size_t)blockIdx.z * N * K;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int n = n0 + tn + i;
     if (n >= N) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (kb + tk + j < K) atomicAdd(&dW[(size_t)n * ldw + k0 + kb + tk + j], scale * acc[i][j]);
+      if (kb + tk + j < K) out[(size_t)n * K + kb + tk + j] = scale * acc[i][j];
   }
 }
 
-// Mixing of order l: dW[c'][c Pl + q] += scale sum_p sum_m dV[p][c' NLM + l l + m] T[p][c NT + toff + q (2l+1) + m]
+// dW[(o / K) * ldw + k0 + o % K] += sum over z of part[z][o], z in order
+__global__ void k_chunk_sum(const float* __restrict__ part, int nz, int N, int K, float* __restrict__ dW, int ldw,
+                            int k0) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= N * K) return;
+  float acc = 0.0f;
+  for (int z = 0; z < nz; ++z) acc += part[(size_t)z * N * K + o];
+  dW[(size_t)(o / K) * ldw + k0 + o % K] += acc;
+}
+
+// Mixing of order l: part[blk][c' C Pl + c Pl + q] = scale sum_{p in chunk}
+// sum_m dV[p][(c' NLM + l l + m) esv] T[p][c NT + toff + q (2l+1) + m]
 // One block per chunk of pairs: the order-l parts of kMixG pairs' dV and T
 // rows are staged in shared memory with contiguous loads, then every thread
 // accumulates up to kMixR outputs (a pass over the chunk per kMixR x 256
-// outputs), one atomic add per output at the end.
+// outputs) and writes the chunk's partial; k_chunk_sum adds them in order.
 constexpr int kMixG = 16;
 constexpr int kMixR = 4;
 
-__global__ void __launch_bounds__(256) k_wgrad_mix(const float* __restrict__ dV, const float* __restrict__ T, int P,
-                                                   int C, int NLM, int NT, int l, int Pl, int toff, float scale,
-                                                   float* __restrict__ dW, int chunk) {
+__global__ void __launch_bounds__(256) k_wgrad_mix(const float* __restrict__ dV, int esv,
+                                                   const float* __restrict__ T, int P, int C, int NLM, int NT, int l,
+                                                   int Pl, int toff, float scale, float* __restrict__ part, int chunk) {
   extern __shared__ float mix_s[];
   const int nm = 2 * l + 1;
   const int wv = C * nm, wt = C * Pl * nm;            // staged floats per pair
@@ -99,7 +113,7 @@ __global__ void __launch_bounds__(256) k_wgrad_mix(const float* __restrict__ dV,
       __syncthreads();
       for (int idx = threadIdx.x; idx < gn * wv; idx += blockDim.x) {
         const int g = idx / wv, e = idx % wv, co = e / nm, m = e % nm;
-        dv_s[g * wv + e] = dV[(size_t)(p0 + g) * C * NLM + co * NLM + l * l + m];
+        dv_s[g * wv + e] = dV[((size_t)(p0 + g) * C * NLM + co * NLM + l * l + m) * esv];
       }
       for (int idx = threadIdx.x; idx < gn * wt; idx += blockDim.x) {
         const int g = idx / wt, e = idx % wt, c = e / (Pl * nm), j = e % (Pl * nm);
@@ -117,7 +131,7 @@ __global__ void __launch_bounds__(256) k_wgrad_mix(const float* __restrict__ dV,
 #pragma unroll
     for (int r = 0; r < kMixR; ++r) {
       const int o = ob + r * 256 + (int)threadIdx.x;
-      if (o < n_out) atomicAdd(&dW[o], scale * acc[r]);
+      if (o < n_out) part[(size_t)blockIdx.x * n_out + o] = scale * acc[r];
     }
   }
 }
@@ -217,22 +231,17 @@ __global__ void k_struct_dE(const int64_t* __restrict__ off, const double* __res
   }
 }
 
-__global__ void k_force_resid(int64_t N, const int* __restrict__ sid, const float* __restrict__ F,
-                              const float* __restrict__ ft, double cf, float* __restrict__ v,
-                              unsigned* __restrict__ vmax, double* __restrict__ blk) {
+__global__ void k_force_resid(int64_t N, const float* __restrict__ F, const float* __restrict__ ft, double cf,
+                              float* __restrict__ v, double* __restrict__ blk) {
   __shared__ double sh[256];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double l = 0.0;
   if (i < N) {
-    float m = 0.0f;
     for (int d = 0; d < 3; ++d) {
       const double r = (double)F[3 * i + d] - (double)ft[3 * i + d];
       l += cf * r * r;
-      const float vv = (float)(2.0 * cf * r);
-      v[3 * i + d] = vv;
-      m = fmaxf(m, fabsf(vv));
+      v[3 * i + d] = (float)(2.0 * cf * r);
     }
-    atomicMax(&vmax[sid[i]], __float_as_uint(m));   // non-negative floats order like their bits
   }
   sh[threadIdx.x] = l;
   __syncthreads();
@@ -264,17 +273,6 @@ __global__ void k_seed_energy(int B, int64_t N, const int64_t* __restrict__ off,
   seed[i] = (float)(2.0 * wE * dE[b] / ((double)B * n * n));
 }
 
-__global__ void k_displace(int64_t N, const int* __restrict__ sid, const double* __restrict__ wpos,
-                           const float* __restrict__ v, const unsigned* __restrict__ vmax, double delta, double sign,
-                           double* __restrict__ wdisp, float* __restrict__ seed) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const double vm = (double)__uint_as_float(vmax[sid[i]]);
-  const double h = vm > 0.0 ? delta / vm : 0.0;
-  for (int d = 0; d < 3; ++d) wdisp[3 * i + d] = wpos[3 * i + d] + sign * h * (double)v[3 * i + d];
-  seed[i] = h > 0.0 ? (float)(-sign * 0.5 / h) : 0.0f;
-}
-
 }  // namespace
 
 void launch_append(const BatchArrays& bt, int n, int np, int64_t A0, int64_t P0, int b, const int* pi, const int* pj,
@@ -285,13 +283,12 @@ void launch_append(const BatchArrays& bt, int n, int np, int64_t A0, int64_t P0,
                                            L[1], L[2]);
 }
 
-void launch_batch_loss(int B, int64_t N, const int64_t* off, const int* sid, const double* Ei, const double* e_target,
+void launch_batch_loss(int B, int64_t N, const int64_t* off, const double* Ei, const double* e_target,
                        const float* F, const float* f_target, double w_energy, double cf, double* dE, float* v,
-                       unsigned* vmax, double* blk, double* loss, cudaStream_t s) {
+                       double* blk, double* loss, cudaStream_t s) {
   const int nblk = (int)((N + 255) / 256);
-  cudaMemsetAsync(vmax, 0, sizeof(unsigned) * B, s);
   k_struct_dE<<<B, 256, 0, s>>>(off, Ei, e_target, dE);
-  k_force_resid<<<nblk, 256, 0, s>>>(N, sid, F, f_target, cf, v, vmax, blk);
+  k_force_resid<<<nblk, 256, 0, s>>>(N, F, f_target, cf, v, blk);
   k_loss_total<<<1, 32, 0, s>>>(B, off, dE, w_energy, blk, nblk, loss);
 }
 
@@ -300,32 +297,43 @@ void launch_seed_energy(int B, int64_t N, const int64_t* off, const int* sid, co
   k_seed_energy<<<(int)((N + 255) / 256), 256, 0, s>>>(B, N, off, sid, dE, w_energy, seed);
 }
 
-void launch_displace(int64_t N, const int* sid, const double* wpos, const float* v, const unsigned* vmax, double delta,
-                     double sign, double* wdisp, float* seed, cudaStream_t s) {
-  k_displace<<<(int)((N + 255) / 256), 256, 0, s>>>(N, sid, wpos, v, vmax, delta, sign, wdisp, seed);
-}
-
-void launch_wgrad(const float* dz, int ldz, const float* x, int ldx, int P, int N, int K, float scale, float* dW,
-                  int ldw, int k0, cudaStream_t s) {
-  if (P <= 0) return;
+int wgrad_chunks(int P, int N, int K) {
   // about four blocks per SM over all output tiles, chunks a multiple of the
   // staging depth
   const int tiles = ((N + kWT - 1) / kWT) * ((K + kWT - 1) / kWT);
   const int want = std::max(1, 152 * 4 / tiles);
   int chunk = (P + want - 1) / want;
   chunk = std::max(kWP * 8, (chunk + kWP - 1) / kWP * kWP);
-  dim3 grid((N + kWT - 1) / kWT, (K + kWT - 1) / kWT, (P + chunk - 1) / chunk);
-  k_wgrad<<<grid, 256, 0, s>>>(dz, ldz, x, ldx, P, N, K, scale, dW, ldw, k0, chunk);
+  return chunk;
 }
 
-void launch_wgrad_mix(const float* dV, const float* T, int P, int C, int NLM, int NT, int l, int Pl, int toff,
-                      float scale, float* dW, cudaStream_t s) {
+void launch_wgrad(const float* dz, int ldz, int esz, const float* x, int ldx, int esx, int P, int N, int K,
+                  float scale, float* dW, int ldw, int k0, float* part, cudaStream_t s) {
+  if (P <= 0) return;
+  const int chunk = wgrad_chunks(P, N, K);
+  const int nz = (P + chunk - 1) / chunk;
+  dim3 grid((N + kWT - 1) / kWT, (K + kWT - 1) / kWT, nz);
+  k_wgrad<<<grid, 256, 0, s>>>(dz, ldz, esz, x, ldx, esx, P, N, K, scale, part, chunk);
+  k_chunk_sum<<<(N * K + 255) / 256, 256, 0, s>>>(part, nz, N, K, dW, ldw, k0);
+}
+
+void launch_wgrad_mix(const float* dV, int esv, const float* T, int P, int C, int NLM, int NT, int l, int Pl,
+                      int toff, float scale, float* dW, float* part, cudaStream_t s) {
   if (P <= 0) return;
   // about four blocks per SM
   const int chunk = std::max(kMixG, (P + 152 * 4 - 1) / (152 * 4));
+  const int nblk = (P + chunk - 1) / chunk;
   const int nm = 2 * l + 1;
   const size_t smem = sizeof(float) * kMixG * (size_t)(C * nm + C * Pl * nm);
-  k_wgrad_mix<<<(P + chunk - 1) / chunk, 256, smem, s>>>(dV, T, P, C, NLM, NT, l, Pl, toff, scale, dW, chunk);
+  k_wgrad_mix<<<nblk, 256, smem, s>>>(dV, esv, T, P, C, NLM, NT, l, Pl, toff, scale, part, chunk);
+  const int n_out = C * C * Pl;
+  k_chunk_sum<<<(n_out + 255) / 256, 256, 0, s>>>(part, nblk, 1, n_out, dW, n_out, 0);
+}
+
+size_t wgrad_part_floats() {
+  // k_wgrad: chunks x N x K <= (608 / tiles + 1) x tiles 64 x 64; k_wgrad_mix:
+  // at most 608 blocks of C C P_l <= 16 x 16 x 4 outputs
+  return std::max<size_t>((size_t)(152 * 4 + 8) * kWT * kWT, (size_t)(152 * 4 + 8) * 1024);
 }
 
 void launch_sumsq(const float* g, int n, double* out, cudaStream_t s) { k_sumsq<<<1, 1024, 0, s>>>(g, n, out); }

@@ -4,12 +4,16 @@
 
 namespace al {
 
-// dW[n * ldw + k0 + k] += scale * sum_p dz[p * ldz + n] * x[p * ldx + k]
-void launch_wgrad(const float* dz, int ldz, const float* x, int ldx, int P, int N, int K, float scale, float* dW,
-                  int ldw, int k0, cudaStream_t s);
-// mixing matrix of order l (see train.cu)
-void launch_wgrad_mix(const float* dV, const float* T, int P, int C, int NLM, int NT, int l, int Pl, int toff,
-                      float scale, float* dW, cudaStream_t s);
+// dW[n * ldw + k0 + k] += scale * sum_p dz[p * ldz + n esz] * x[p * ldx + k esx]
+// (element strides 1, or 2 for one part of an array of tangent numbers),
+// per-chunk partials in part (wgrad_part_floats() floats) added in a fixed
+// order: bitwise reproducible
+void launch_wgrad(const float* dz, int ldz, int esz, const float* x, int ldx, int esx, int P, int N, int K,
+                  float scale, float* dW, int ldw, int k0, float* part, cudaStream_t s);
+// mixing matrix of order l (see train.cu); dV element stride esv
+void launch_wgrad_mix(const float* dV, int esv, const float* T, int P, int C, int NLM, int NT, int l, int Pl,
+                      int toff, float scale, float* dW, float* part, cudaStream_t s);
+size_t wgrad_part_floats();
 void launch_sumsq(const float* g, int n, double* out, cudaStream_t s);
 void launch_ascent(const float* w, const float* g, int n, double rho, const double* norm2, float* w_out,
                    cudaStream_t s);
@@ -37,15 +41,11 @@ void launch_append(const BatchArrays& bt, int n, int np, int64_t A0, int64_t P0,
                    const double L[3], cudaStream_t s);
 // Loss of Eq. 3's objective (per-atom energy MSE + force MSE) on the batch and
 // the seeds of its weight gradient: dE[b] = E_b - E*_b; v = 2 cf (F - F*);
-// vmax[b] = max |v| over structure b (float bits); *loss.
-void launch_batch_loss(int B, int64_t N, const int64_t* off, const int* sid, const double* Ei, const double* e_target,
+// *loss.
+void launch_batch_loss(int B, int64_t N, const int64_t* off, const double* Ei, const double* e_target,
                        const float* F, const float* f_target, double w_energy, double cf, double* dE, float* v,
-                       unsigned* vmax, double* blk, double* loss, cudaStream_t s);
+                       double* blk, double* loss, cudaStream_t s);
 // seed_i = 2 w_E dE_b / (B N_b^2) for atom i of structure b
 void launch_seed_energy(int B, int64_t N, const int64_t* off, const int* sid, const double* dE, double w_energy,
                         float* seed, cudaStream_t s);
-// r_i + sign h_b v_i with h_b = delta / vmax_b, seed_i = -sign / (2 h_b) (0 where vmax_b = 0)
-void launch_displace(int64_t N, const int* sid, const double* wpos, const float* v, const unsigned* vmax, double delta,
-                     double sign, double* wdisp, float* seed, cudaStream_t s);
-
 }  // namespace al

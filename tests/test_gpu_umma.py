@@ -53,3 +53,23 @@ def test_mn_major_b_operand(N, K):
     torch.cuda.synchronize()
     err = (D.double() - ref).abs().max().item()
     assert err <= 1e-5 * ref.abs().max().item() + 1e-5, err
+
+
+def test_silu_error_bound():
+    """The error model of the tensor-core tests (tests/emulation_bounds.py)
+    rests on this: the passes' SiLU, z sigmoid(z) with sigmoid through
+    tanh.approx.f32, is within |z| 2^-17.5 of the exact value, and its
+    derivative within (1 + |z|) 2^-17.5, on a dense grid over [-30, 30]
+    (FP32 rounding of the final products added)."""
+    x = torch.linspace(-30.0, 30.0, 1 << 22, device="cuda", dtype=torch.float32)
+    y = torch.empty(2 * x.numel(), device="cuda", dtype=torch.float32)
+    al.allegro_selftest_silu(x, y)
+    z = x.double().cpu()
+    s = torch.sigmoid(z)
+    silu, dsilu = z * s, s * (1.0 + z * (1.0 - s))
+    got = y.double().cpu().view(-1, 2)
+    e1 = (got[:, 0] - silu).abs()
+    e2 = (got[:, 1] - dsilu).abs()
+    b = 2.0 ** -17.5
+    assert bool((e1 <= z.abs() * b + 2.0 ** -23 * silu.abs()).all()), float((e1 / (z.abs() * b + 1e-30)).max())
+    assert bool((e2 <= (1.0 + z.abs()) * b + 2.0 ** -23 * (1.0 + z.abs())).all())
