@@ -93,17 +93,24 @@ def test_sam_step_matches_oracle(setup):
     ctx, stu, _, structs, w0 = setup
     al.allegro_set_weights(ctx, w0)
     z = np.zeros(len(w0))
-    wref, _, lref, _, _ = sam_step(stu, w0.astype(np.float64), structs, 0.05, 2e-3, (z, z, 0))
+    wref, (mref, _, _), lref, _, _ = sam_step(stu, w0.astype(np.float64), structs, 0.05, 2e-3, (z, z, 0))
     b, keep = al.make_batch(structs)
     loss = al.allegro_sam_train_step(ctx, b, 0.05, 2e-3, 1.0, 100.0)
     w1 = np.zeros_like(w0)
     al.allegro_get_weights(ctx, w1)
     assert abs(loss - lref) <= 1e-5 * lref
-    # the first Adam step moves each weight by about lr * sign(g'): agreement
-    # within 1% of lr on every weight
-    agree = np.mean(np.abs((w1 - w0) - (wref - w0)) <= 2e-5)
-    print(f"SAM update agreement {agree:.6f}")
-    assert agree == 1.0
+    # The first Adam step moves weight i by u(g'_i) = -lr g'/(|g'| + 1e-8).
+    # A gradient error dg changes it by at most lr 1e-8 |dg| / (|g'| + 1e-8)^2;
+    # with |dg| <= 1e-5 ||g'|| (the gradient bound above) that is within 1% of
+    # lr (2e-5) wherever lr 1e-8 1e-5 ||g'|| / (|g'_i| + 1e-8)^2 <= 2e-5.
+    # Every such weight must agree to 2e-5; the rest (Adam's first step is
+    # ill-conditioned there) must be a tiny fraction.
+    gp = mref / 0.1                              # the oracle's g' (m = (1 - beta1) g' after one step)
+    cond = 2e-3 * 1e-8 * 1e-5 * np.linalg.norm(gp) / (np.abs(gp) + 1e-8) ** 2 <= 2e-5
+    ok = np.abs((w1 - w0) - (wref - w0)) <= 2e-5
+    print(f"SAM update agreement {ok.mean():.6f}, well-conditioned weights {cond.mean():.6f}")
+    assert ok[cond].all()
+    assert cond.mean() >= 0.999
     al.allegro_set_weights(ctx, w0)
 
 
