@@ -67,6 +67,12 @@ ALL_MAC_PER_PAIR = {
     "pass_b_adjoint": 288 + 2048 + 16384 + 22528 + 8960 + 2656 + 6144 + 288,
     "pass_a_adjoint": 288 + 2048 + 16384 + 1536,
 }
+# one E + F of the FP32 path (all of the above), and the multiply-adds of the
+# per-pair weight layers (two-body, embedding, env, mixing, latent, energy
+# hidden and output): one outer product dz (x) x per layer and pair in a
+# weight-gradient reduction
+FP32_MAC_PER_PAIR = sum(ALL_MAC_PER_PAIR.values())
+WEIGHT_MAC_PER_PAIR = 1536 + 16384 + 6144 + 2 * 2048 + 8960 + 2 * (22528 + 16384) + 4096 + 32
 TC_KERNELS = {"pass_a": "k_bf_a", "pass_b1": "k_bf_b1", "pass_b2": "k_bf_b2", "pass_c": "k_bf_c",
               "pass_b_adjoint": "k_bf_bt", "pass_a_adjoint": "k_bf_at"}
 FP32_KERNELS = {"pass_a": "k_pass_a", "pass_b": "k_pass_b", "pass_c": "k_pass_c",
@@ -504,9 +510,20 @@ def sam_timing(al, torch, steps=5, n_sharp=64):
     dt_scan = (time.perf_counter() - t1) / (n_sharp + 1)
     kmax = int(np.argmax(ls[1:])) + 1
     surface = al.allegro_loss_scan(ctx, b, eps[kmax], np.linspace(-1.0, 1.0, 9))
+    n_pairs = al.allegro_query(ctx, al.ALLEGRO_Q_BATCH_PAIRS)
     al.allegro_destroy(ctx)
     n_atoms = int(sum(len(s["species"]) for s in structs))
-    return {"structures": len(structs), "atoms": n_atoms, "ms_per_step": 1e3 * dt, "steps": steps,
+    # algorithmic work of one SAM step: two loss gradients, each the forward
+    # E + F (forward and force adjoint), the tangent of both along dL/dF
+    # (twice their multiply-adds: value and tangent) and the weight-gradient
+    # reductions (two outer products per linear layer and pair)
+    flops = 2 * n_pairs * 2 * (3 * FP32_MAC_PER_PAIR + 2 * WEIGHT_MAC_PER_PAIR)
+    peak = FP32_PEAK_TFLOPS
+    sam_roof = {"bound": "alu", "achieved": flops / dt * 1e-12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / dt * 1e-12 / peak, "algorithmic_flops": flops, "pairs": n_pairs,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"}
+    return {"structures": len(structs), "atoms": n_atoms, "pairs": n_pairs, "ms_per_step": 1e3 * dt,
+            "steps": steps, "roofline": sam_roof,
             "rho": 0.05, "lr": 2e-3, "loss_first": losses[0], "loss_last": losses[-1],
             "sharpness": {"value": float(ls[1:].max() - ls[0]), "samples": n_sharp, "loss_at_w": float(ls[0]),
                           "ms_per_loss_evaluation": 1e3 * dt_scan,
@@ -514,9 +531,10 @@ def sam_timing(al, torch, steps=5, n_sharp=64):
                           "surface_loss": [float(x) for x in surface],
                           "note": "allegro_loss_scan after the SAM steps: loss at w + eps_k for random eps_k "
                                   "of norm 0.05 (seeded), then L(w + p eps_max)"},
-            "note": "FP32 passes with per-pair dumps over all 32 structures at once (one concatenated "
-                    "pair list); two loss gradients (w, w + eps) per step, each one forward and three "
-                    "training-mode pass sequences (energy seed, central difference along dL/dF)"}
+            "note": "all 32 structures in one concatenated pair list; two loss gradients (w, w + eps) "
+                    "per step, each one FP32 forward pass sequence and one tangent pass sequence (the "
+                    "hand-written adjoint differentiated along dL/dF: the exact force-term gradient) "
+                    "with per-pair dumps, then deterministic weight-gradient reductions"}
 
 
 def roofline(phases, n_pairs, tensor_path, peaks):

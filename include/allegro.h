@@ -361,6 +361,7 @@ int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velociti
 #define ALLEGRO_Q_N_ATOMS      3  /* atoms of the current state                  */
 #define ALLEGRO_Q_N_PARAMS     4  /* trainable parameters (weights vector length) */
 #define ALLEGRO_Q_RP_STEP_KERNELS 5  /* kernel launches in one ring-polymer step */
+#define ALLEGRO_Q_BATCH_PAIRS  6  /* ordered pairs of the last training batch     */
 
 /* Read one integer property of the context into *value (host). */
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);

@@ -43,6 +43,7 @@ ALLEGRO_Q_STEP_KERNELS = 2
 ALLEGRO_Q_N_ATOMS = 3
 ALLEGRO_Q_N_PARAMS = 4
 ALLEGRO_Q_RP_STEP_KERNELS = 5
+ALLEGRO_Q_BATCH_PAIRS = 6
 
 
 class _Batch(ctypes.Structure):

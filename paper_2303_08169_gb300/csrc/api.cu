@@ -1860,6 +1860,7 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
     case ALLEGRO_Q_RP_STEP_KERNELS: *value = ctx->rp_graph_kernels; return ALLEGRO_OK;
     case ALLEGRO_Q_N_ATOMS: *value = ctx->n_atoms; return ALLEGRO_OK;
     case ALLEGRO_Q_N_PARAMS: *value = ctx->n_params; return ALLEGRO_OK;
+    case ALLEGRO_Q_BATCH_PAIRS: *value = ctx->bt.n_pairs; return ALLEGRO_OK;
     default: return ctx->fail(ALLEGRO_E_INVALID_ARG, "unknown query key");
   }
 }
