@@ -92,6 +92,7 @@ WORKLOADS = {
 SECONDARY = ["bf16_110592", "fp16_110592", "fp32_6912"]
 SCALE = "tc_1000000"   # own context, run after the others
 SCALE_SAMPLES = 16      # atoms of the 10^6-atom frame checked against the oracle
+SKIN = 0.3              # A, the Verlet-skin block
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tc_110592_kernels.md")
 
 
@@ -297,12 +298,13 @@ class Runner:
         self.stream = torch.cuda.Stream(device=dev)
         al.allegro_set_stream(self.ctx, self.stream)
 
-    def md(self, name, K, W, clocks=None, barrier=None):
+    def md(self, name, K, W, clocks=None, barrier=None, skin=0.0):
         """K graph-captured MD steps after W warm-up steps; returns a dict."""
         al, torch, dev = self.al, self.torch, self.dev
         w = WORKLOADS[name]
         pos, sp, cell, vel = _system(w["n_mol"])
         al.allegro_set_md_precision(self.ctx, w["precision"])
+        al.allegro_set_skin(self.ctx, skin)
         al.allegro_md_init(self.ctx, torch.tensor(pos, device=dev), torch.tensor(vel, device=dev),
                            torch.tensor(sp, device=dev, dtype=torch.int32), cell)
         outl = torch.zeros(K, dtype=torch.int64, device=dev)
@@ -328,6 +330,7 @@ class Runner:
         en = ener.cpu().numpy()
         N = len(sp)
         return {"ms": ms, "N": N, "K": K, "clocks": clk, "n_pairs_start": n_pairs_start,
+                "rebuilds": al.allegro_query(self.ctx, al.ALLEGRO_Q_REBUILDS),
                 "n_pairs": al.allegro_query(self.ctx, al.ALLEGRO_Q_N_PAIRS),
                 "step_kernels": al.allegro_query(self.ctx, al.ALLEGRO_Q_STEP_KERNELS),
                 "drift": float(np.abs(en[:, 2] - en[0, 2]).max() / (N * KB_T200)),
@@ -647,7 +650,19 @@ def run_ours(args):
                             "propagation, one neighbour build over all replicas, one pass sequence over all "
                             "replicas, record)"}
 
+        def skin_block():
+            rs = run.md(args.config, min(K, 200), W, skin=SKIN)
+            run.md(args.config, 1, 1)                     # back to per-step rebuilds for the blocks below
+            rn = run.md(args.config, min(K, 200), W)
+            return {"workload": args.config, "skin_A": SKIN, "steps": rs["K"],
+                    "ms_per_step": rs["ms"] / rs["K"], "value": rs["N"] * rs["K"] / (rs["ms"] * 1e-3),
+                    "rebuilds": rs["rebuilds"], "pairs": rs["n_pairs"],
+                    "ms_per_step_rebuild_every_step": rn["ms"] / rn["K"], "pairs_rebuild_every_step": rn["n_pairs"],
+                    "note": "allegro_set_skin: list of r_cut + skin kept until an atom moved skin/2; the skin's "
+                            "extra pairs (zero contribution) against the builds it saves"}
+
         nvt = _guarded(nvt_block)
+        skin = _guarded(skin_block)
         pimd = _guarded(pimd_block)
         sam = _guarded(lambda: sam_timing(al, torch))
         lsweep = _guarded(lambda: lmax_sweep(al, torch, dev))
@@ -693,6 +708,7 @@ def run_ours(args):
         e2e = None
         sam = None
         nvt = None
+        skin = None
         pimd = None
         lsweep = None
     run.close()
@@ -740,6 +756,8 @@ def run_ours(args):
         line["sam_train_step"] = sam
     if nvt:
         line["nvt"] = nvt
+    if skin:
+        line["verlet_skin"] = skin
     if pimd:
         line["pimd"] = pimd
     if lsweep:

@@ -170,6 +170,23 @@ int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions,
 int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision);
 
 /*
+ * Verlet-skin reuse of the neighbour list in the MD steps (Sec. 3.2 runs
+ * long NVT and NVE trajectories; reusing the list between rebuilds is the
+ * classical way to amortise its cost).  skin_A in [0, r_cut] A, 0 (the
+ * default) rebuilding every step.  With skin_A > 0 the list of the MD state
+ * holds every pair within r_cut + skin_A; each step of allegro_md_step_nve /
+ * _nvt rebuilds it only when some atom has moved by more than skin_A / 2
+ * (minimum image) since the last build, and at the first step of every call.
+ * Pairs beyond r_cut contribute exactly zero (the envelope vanishes there),
+ * so results equal those of per-step rebuilds up to FP32 summation order.
+ * Takes effect at the next allegro_md_init; ring-polymer steps always
+ * rebuild.  ALLEGRO_E_INVALID_ARG outside the range; allegro_md_init returns
+ * ALLEGRO_E_CUTOFF_TOO_LARGE when r_cut + skin exceeds twice a cell length.
+ * The builds since allegro_md_init: allegro_query(ALLEGRO_Q_REBUILDS).
+ */
+int allegro_set_skin(allegro_ctx* ctx, double skin_A);
+
+/*
  * n_steps microcanonical velocity-Verlet steps of dt_fs each (Eq. 1,
  * Sec. 3.2): v += dt/2 a; r += dt v; wrap; F = F(r); v += dt/2 a with
  * a = kappa F / m, kappa = 9.648533e-3 A/fs^2 per eV/(A amu), in FP64.
@@ -362,6 +379,7 @@ int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velociti
 #define ALLEGRO_Q_N_PARAMS     4  /* trainable parameters (weights vector length) */
 #define ALLEGRO_Q_RP_STEP_KERNELS 5  /* kernel launches in one ring-polymer step */
 #define ALLEGRO_Q_BATCH_PAIRS  6  /* ordered pairs of the last training batch     */
+#define ALLEGRO_Q_REBUILDS     7  /* skin: neighbour builds since allegro_md_init  */
 
 /* Read one integer property of the context into *value (host). */
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);

@@ -34,7 +34,7 @@ EXPORTED = [
     "allegro_loss_grad", "allegro_sam_train_step", "allegro_get_weights", "allegro_set_weights",
     "allegro_loss_scan", "allegro_md_step_nvt", "allegro_md_get_thermostat",
     "allegro_pimd_init", "allegro_pimd_step", "allegro_pimd_get_state",
-    "allegro_debug_inject_wait_timeout", "allegro_selftest_silu",
+    "allegro_debug_inject_wait_timeout", "allegro_selftest_silu", "allegro_set_skin",
 ]
 
 ALLEGRO_Q_N_PAIRS = 0
@@ -44,6 +44,7 @@ ALLEGRO_Q_N_ATOMS = 3
 ALLEGRO_Q_N_PARAMS = 4
 ALLEGRO_Q_RP_STEP_KERNELS = 5
 ALLEGRO_Q_BATCH_PAIRS = 6
+ALLEGRO_Q_REBUILDS = 7
 
 
 class _Batch(ctypes.Structure):
@@ -105,6 +106,7 @@ def lib():
         "allegro_set_weights": ([_vp, _vp, _i64], ctypes.c_int),
         "allegro_debug_inject_wait_timeout": ([_i32], ctypes.c_int),
         "allegro_selftest_silu": ([_i64, _vp, _vp], ctypes.c_int),
+        "allegro_set_skin": ([_vp, _f64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -340,3 +342,9 @@ def allegro_selftest_silu(x, y):
     """y[2i], y[2i+1] = SiLU(x[i]), SiLU'(x[i]) as the tensor-core passes
     compute them (device tensors: x n FP32, y 2n FP32)."""
     _check(None, lib().allegro_selftest_silu(int(x.numel()), _ptr(x), _ptr(y)))
+
+
+def allegro_set_skin(ctx, skin_A):
+    """Verlet-skin reuse of the MD neighbour list (0 = rebuild every step);
+    takes effect at the next allegro_md_init."""
+    _check(ctx, lib().allegro_set_skin(ctx, float(skin_A)))

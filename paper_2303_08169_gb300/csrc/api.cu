@@ -255,6 +255,14 @@ struct allegro_ctx {
   cudaGraphExec_t graph_rp = nullptr;
   double rp_graph_dt = 0.0;
   int64_t rp_graph_kernels = 0;
+  // Verlet skin of the MD state (NVE, NVT): skin requested, skin of the
+  // current MD state's list (set by allegro_md_init), reference positions and
+  // their wrap at the last build, and [rebuild now, forced rebuild, rebuilds]
+  double skin = 0.0;
+  double md_skin = 0.0;
+  double* d_pos_ref = nullptr;
+  double* d_wpos_ref = nullptr;
+  int* d_skin_flag = nullptr;
   // rollback snapshot
   double* d_pos_snap = nullptr;
   double* d_v_snap = nullptr;
@@ -493,7 +501,7 @@ int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
                     (void*)c->d_blku, (void*)c->nb.wpos, (void*)c->nb.wpos32, (void*)c->nb.atom_cell,
                     (void*)c->nb.cell_atoms, (void*)c->nb.row_cnt, (void*)c->nb.row_ptr, (void*)c->nb.scan_blocks,
                     (void*)c->d_v, (void*)c->d_blk_ke, (void*)c->d_pos_snap, (void*)c->d_v_snap,
-                    (void*)c->d_F_snap})
+                    (void*)c->d_F_snap, (void*)c->d_pos_ref, (void*)c->d_wpos_ref})
       c->dfree(p);
     c->d_pos = c->dalloc<double>(3 * na);
     c->d_species = c->dalloc<int>(na);
@@ -513,9 +521,12 @@ int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
     c->d_pos_snap = c->dalloc<double>(3 * na);
     c->d_v_snap = c->dalloc<double>(3 * na);
     c->d_F_snap = c->dalloc<float>(3 * na);
+    c->d_pos_ref = c->dalloc<double>(3 * na);
+    c->d_wpos_ref = c->dalloc<double>(3 * na);
     if (!c->d_pos || !c->d_species || !c->d_F || !c->d_Ei || !c->d_blk || !c->d_blku || !c->nb.wpos ||
         !c->nb.wpos32 || !c->nb.atom_cell || !c->nb.cell_atoms || !c->nb.row_cnt || !c->nb.row_ptr ||
-        !c->nb.scan_blocks || !c->d_v || !c->d_blk_ke || !c->d_pos_snap || !c->d_v_snap || !c->d_F_snap)
+        !c->nb.scan_blocks || !c->d_v || !c->d_blk_ke || !c->d_pos_snap || !c->d_v_snap || !c->d_F_snap ||
+        !c->d_pos_ref || !c->d_wpos_ref)
       return c->fail(ALLEGRO_E_OOM, "per-atom allocation failed");
     c->n_atoms_alloc = na;
     c->part_rows = 0;   // partial buffers depend on N
@@ -527,6 +538,7 @@ int ensure_atoms(allegro_ctx* c, int64_t n, int ncell) {
     c->nb.n_pairs = c->dalloc<int>(1);
     c->nb.flags = c->dalloc<int>(1);
     c->d_step = c->dalloc<long long>(1);
+    c->d_skin_flag = c->dalloc<int>(4);
     c->d_nh = c->dalloc<double>(4);
     c->d_nh_snap = c->dalloc<double>(4);
     if (!c->d_stats || !c->d_count || !c->nb.n_pairs || !c->nb.flags || !c->d_step || !c->d_nh || !c->d_nh_snap)
@@ -706,14 +718,19 @@ int build_with_growth(allegro_ctx* c, const double* d_positions, int64_t n, int6
   return c->fail(ALLEGRO_E_PAIR_OVERFLOW, "pair capacity could not be grown");
 }
 
+// skin > 0 (MD with Verlet-skin reuse): the list holds every pair within
+// r_cut + skin.
 int prepare(allegro_ctx* c, int64_t n, const double* positions, const int32_t* species,
-            const double* cell, double L[3]) {
+            const double* cell, double L[3], double skin = 0.0) {
   if (n <= 0 || n > (1 << 30)) return c->fail(ALLEGRO_E_INVALID_ARG, "n_atoms out of range");
   if (!positions) return c->fail(ALLEGRO_E_INVALID_ARG, "positions is NULL");
   int rc = check_cell(c, cell, L);
   if (rc) return rc;
+  for (int a = 0; a < 3; ++a)
+    if (c->blob.rc + skin > 2.0 * L[a])
+      return c->fail(ALLEGRO_E_CUTOFF_TOO_LARGE, "r_cut + skin exceeds twice the cell length");
   c->md_ready = false;   // the per-atom buffers now hold this call's system
-  c->grid = plan_grid(L, c->blob.rc);
+  c->grid = plan_grid(L, c->blob.rc + skin);
   const int ncell = c->grid.ncell[0] > 0 ? c->grid.ncell[0] * c->grid.ncell[1] * c->grid.ncell[2] : 0;
   rc = ensure_atoms(c, n, ncell);
   if (rc) return rc;
@@ -1327,6 +1344,14 @@ int allegro_outlier_count(allegro_ctx* ctx, int64_t n_atoms, const float* forces
   return ALLEGRO_OK;
 }
 
+int allegro_set_skin(allegro_ctx* ctx, double skin_A) {
+  if (!ctx) return ALLEGRO_E_INVALID_ARG;
+  if (!(skin_A >= 0.0) || !std::isfinite(skin_A) || skin_A > ctx->blob.rc)
+    return ctx->fail(ALLEGRO_E_INVALID_ARG, "skin must be in [0, r_cut]");
+  ctx->skin = skin_A;
+  return ALLEGRO_OK;
+}
+
 int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
   if (!ctx || !valid_precision(precision)) return ALLEGRO_E_INVALID_ARG;
   if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
@@ -1347,7 +1372,8 @@ int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions, 
   double L[3];
   ctx->md_ready = false;
   int rc = ctx->md_precision == ALLEGRO_FP32 ? require_fp32(ctx) : ALLEGRO_OK;
-  if (!rc) rc = prepare(ctx, n_atoms, positions, species, cell, L);
+  if (!rc) rc = prepare(ctx, n_atoms, positions, species, cell, L, ctx->skin);
+  ctx->md_skin = ctx->skin;
   if (rc) return rc;
   const cudaMemcpyKind kv = is_device_ptr(velocities) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaMemcpyAsync(ctx->d_v, velocities, sizeof(double) * 3 * n_atoms, kv, ctx->stream);
@@ -1363,8 +1389,12 @@ int allegro_md_init(allegro_ctx* ctx, int64_t n_atoms, const double* positions, 
   }
   rc = run_model(ctx, ctx->md_precision, L);
   if (rc) return rc;
-  // state positions are the wrapped ones
+  // state positions are the wrapped ones; they are also the skin's reference
   cudaMemcpyAsync(ctx->d_pos, ctx->nb.wpos, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, ctx->stream);
+  cudaMemcpyAsync(ctx->d_pos_ref, ctx->nb.wpos, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, ctx->stream);
+  cudaMemcpyAsync(ctx->d_wpos_ref, ctx->nb.wpos, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice,
+                  ctx->stream);
+  cudaMemsetAsync(ctx->d_skin_flag, 0, sizeof(int) * 4, ctx->stream);
   cudaMemsetAsync(ctx->d_nh, 0, sizeof(double) * 4, ctx->stream);   // thermostat at rest (xi = eta = 0)
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "md_init");
   ctx->drop_graphs();
@@ -1414,6 +1444,20 @@ int finish_capture(allegro_ctx* c, cudaStream_t cs, bool own, cudaGraphExec_t* o
   return ALLEGRO_OK;
 }
 
+// Neighbour list of one MD step: rebuilt every step without a skin; with a
+// skin, the build runs only when an atom has moved by more than skin/2 since
+// the last one (or a rebuild was forced), otherwise the list stays and the
+// wrapped positions follow the atoms from the reference wrap.
+void launch_md_neighbors(allegro_ctx* c, const double L[3], cudaStream_t cs) {
+  if (c->md_skin <= 0.0) {
+    launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs);
+    return;
+  }
+  launch_skin_check(c->n_atoms, c->d_pos, c->d_pos_ref, L, c->md_skin, c->d_skin_flag, cs);
+  launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs, 0, c->d_skin_flag);
+  launch_skin_commit(c->n_atoms, c->d_pos, c->d_pos_ref, c->nb.wpos, c->d_wpos_ref, L, c->d_skin_flag, cs);
+}
+
 // one NVT step as a graph: thermostat half step, kick, drift, neighbour
 // list, energy and forces, kick, thermostat half step, record
 int capture_step_nvt(allegro_ctx* c, double dt, double temperature, double tau) {
@@ -1434,7 +1478,7 @@ int capture_step_nvt(allegro_ctx* c, double dt, double temperature, double tau) 
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_check(c, "capture");
   const AtomArgs a = atom_args(c);
   launch_nvt_first_half(a, c->d_pos, c->d_v, c->d_F, dt, L, gkt, q, c->d_blk_ke, c->d_nh, cs);
-  launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs);
+  launch_md_neighbors(c, L, cs);
   launch_model(c, c->md_precision, cs, nullptr);
   launch_nvt_second_half(a, c->d_v, c->d_F, dt, c->d_stats, 5.0, gkt, q, c->d_blk_ke, c->d_blku, c->d_nh,
                          c->d_step, c->rec_cap, c->d_e_rec, c->d_out_rec, cs);
@@ -1464,7 +1508,7 @@ int capture_step(allegro_ctx* c, double dt) {
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_check(c, "capture");
   const AtomArgs a = atom_args(c);
   launch_kick_drift(a, c->d_pos, c->d_v, c->d_F, dt, L, cs);
-  launch_build_neighbors(c->nb, c->grid, c->d_pos, c->n_atoms, cs);
+  launch_md_neighbors(c, L, cs);
   launch_model(c, c->md_precision, cs, nullptr);
   launch_kick_measure(a, c->d_v, c->d_F, dt, c->d_stats, 5.0, c->d_blk_ke, c->d_blku, c->d_step, c->rec_cap,
                       c->d_e_rec, c->d_out_rec, cs);
@@ -1510,6 +1554,7 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
     cudaMemcpyAsync(ctx->d_F_snap, ctx->d_F, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
     cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream);
+    cudaMemsetAsync(ctx->d_skin_flag + 1, 1, sizeof(int), ctx->stream);   // skin: rebuild at the first step
     for (int s = 0; s < n_steps; ++s)
       if (cudaGraphLaunch(ctx->graph, ctx->stream) != cudaSuccess) return cuda_check(ctx, "graph launch");
     int flags = 0, np = 0;
@@ -1560,6 +1605,7 @@ int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double 
     cudaMemcpyAsync(ctx->d_nh_snap, ctx->d_nh, sizeof(double) * 4, cudaMemcpyDeviceToDevice, ctx->stream);
     cudaMemsetAsync(ctx->nb.flags, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream);
+    cudaMemsetAsync(ctx->d_skin_flag + 1, 1, sizeof(int), ctx->stream);   // skin: rebuild at the first step
     launch_nh_set_k(a, ctx->d_v, ctx->d_blk_ke, ctx->d_nh, ctx->stream);   // K of the current velocities
     for (int s = 0; s < n_steps; ++s)
       if (cudaGraphLaunch(ctx->graph_nvt, ctx->stream) != cudaSuccess) return cuda_check(ctx, "graph launch");
@@ -1861,6 +1907,15 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
     case ALLEGRO_Q_N_ATOMS: *value = ctx->n_atoms; return ALLEGRO_OK;
     case ALLEGRO_Q_N_PARAMS: *value = ctx->n_params; return ALLEGRO_OK;
     case ALLEGRO_Q_BATCH_PAIRS: *value = ctx->bt.n_pairs; return ALLEGRO_OK;
+    case ALLEGRO_Q_REBUILDS: {
+      int f[4] = {0, 0, 0, 0};
+      if (ctx->d_skin_flag) {
+        cudaMemcpyAsync(f, ctx->d_skin_flag, sizeof(f), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check(ctx, "query");
+      }
+      *value = f[2];
+      return ALLEGRO_OK;
+    }
     default: return ctx->fail(ALLEGRO_E_INVALID_ARG, "unknown query key");
   }
 }

@@ -54,12 +54,23 @@ GridInfo plan_grid(const double L[3], double rc);
 // nps > 0: n_atoms / nps independent systems of nps atoms each in the same
 // box (atoms of system k at [k nps, (k + 1) nps)), paired only within their
 // system; the cell arrays then hold (n_atoms / nps) ncell + 1 entries.
+// gate (optional, device): when *gate == 0 every kernel of the build returns
+// at once and the previous list stays (Verlet-skin reuse).
 void launch_build_neighbors(const NeighborBuffers& nb, const GridInfo& g, const double* pos,
-                            int n_atoms, cudaStream_t s, int nps = 0);
+                            int n_atoms, cudaStream_t s, int nps = 0, const int* gate = nullptr);
 
 // Exclusive scan of n ints (in -> out), out[n] = total; total also copied to
 // *total_dev when non-null.
 void launch_scan(const int* in, int* out, int n, int* block_scratch, int* total_dev,
-                 cudaStream_t s);
+                 cudaStream_t s, const int* gate = nullptr);
+
+// Verlet skin: flag[0] = rebuild needed (flag[1] forced, or an atom moved by
+// more than skin/2 since pos_ref), flag[1] cleared (one block); then, after
+// the gated build, pos_ref/wpos_ref recorded on a rebuild, else wpos set to
+// wpos_ref + the minimum-image displacement; flag[2] counts rebuilds.
+void launch_skin_check(int n, const double* pos, const double* pos_ref, const double L[3], double skin, int* flag,
+                       cudaStream_t s);
+void launch_skin_commit(int n, const double* pos, double* pos_ref, double* wpos, double* wpos_ref, const double L[3],
+                        int* flag, cudaStream_t s);
 
 }  // namespace al

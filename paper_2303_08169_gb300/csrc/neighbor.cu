@@ -33,10 +33,16 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 
+// Verlet-skin reuse: every kernel of a build returns at once when the gate
+// word says that the current list is still valid (uniform over the grid).
+#define NB_GATED(gate) \
+  if ((gate) && *(gate) == 0) return;
+
 __global__ void k_wrap_bin(const double* __restrict__ pos, int n, int nps, GridInfo g,
                            double* __restrict__ wpos, float* __restrict__ wpos32,
                            int* __restrict__ atom_cell, int* __restrict__ cell_count,
-                           int* __restrict__ flags) {
+                           int* __restrict__ flags, const int* __restrict__ gate) {
+  NB_GATED(gate)
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c[3];
@@ -69,7 +75,8 @@ __global__ void k_wrap_bin(const double* __restrict__ pos, int n, int nps, GridI
 
 __global__ void k_cell_fill(int n, const int* __restrict__ atom_cell,
                             const int* __restrict__ cell_start, int* __restrict__ cursor,
-                            int* __restrict__ cell_atoms) {
+                            int* __restrict__ cell_atoms, const int* __restrict__ gate) {
+  NB_GATED(gate)
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = atom_cell[i];
@@ -198,7 +205,8 @@ AL_DEV void for_each_candidate(int i, const GridInfo& g, const float* __restrict
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_count(int n_atoms, int nps, GridInfo g, const float* __restrict__ w32, const double* __restrict__ w64,
         const int* __restrict__ atom_cell, const int* __restrict__ cell_start,
-        const int* __restrict__ cell_atoms, int* __restrict__ row_cnt) {
+        const int* __restrict__ cell_atoms, int* __restrict__ row_cnt, const int* __restrict__ gate) {
+  NB_GATED(gate)
   const int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (i >= n_atoms) return;
   int cnt = 0;
@@ -217,7 +225,8 @@ k_fill(int n_atoms, int nps, GridInfo g, const float* __restrict__ w32, const do
        const int* __restrict__ cell_atoms, const int* __restrict__ row_ptr,
        const int* __restrict__ n_pairs, int64_t capacity, unsigned long long* __restrict__ keys,
        unsigned long long* __restrict__ skeys, int* __restrict__ pi, int* __restrict__ pj,
-       int* __restrict__ pcode, int* __restrict__ flags) {
+       int* __restrict__ pcode, int* __restrict__ flags, const int* __restrict__ gate) {
+  NB_GATED(gate)
   __shared__ unsigned long long s_keys[kWarpsPerBlock][kRowCap];
   if ((int64_t)(*n_pairs) > capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, kFlagPairOverflow);
@@ -258,7 +267,8 @@ __global__ void k_reverse(const int* __restrict__ n_pairs, int64_t capacity,
                           const int* __restrict__ row_ptr, const int* __restrict__ pi,
                           const int* __restrict__ pj, const int* __restrict__ pcode,
                           const unsigned long long* __restrict__ skeys, int* __restrict__ rev,
-                          int* __restrict__ flags) {
+                          int* __restrict__ flags, const int* __restrict__ gate) {
+  NB_GATED(gate)
   const int P = *n_pairs;
   if ((int64_t)P > capacity) return;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -285,7 +295,9 @@ __global__ void k_reverse(const int* __restrict__ n_pairs, int64_t capacity,
 // ---- exclusive scan (three phases, 1024 elements per block) ----
 constexpr int kScanBlock = 1024;
 
-__global__ void k_scan_reduce(const int* __restrict__ in, int n, int* __restrict__ bsum) {
+__global__ void k_scan_reduce(const int* __restrict__ in, int n, int* __restrict__ bsum,
+                              const int* __restrict__ gate) {
+  NB_GATED(gate)
   __shared__ int sh[32];
   const int b = blockIdx.x;
   int v = 0;
@@ -303,7 +315,8 @@ __global__ void k_scan_reduce(const int* __restrict__ in, int n, int* __restrict
   }
 }
 
-__global__ void k_scan_blocks(int* __restrict__ bsum, int nb) {
+__global__ void k_scan_blocks(int* __restrict__ bsum, int nb, const int* __restrict__ gate) {
+  NB_GATED(gate)
   // single thread block, sequential over chunks of 1024
   __shared__ int sh[1024];
   __shared__ int carry;
@@ -329,7 +342,9 @@ __global__ void k_scan_blocks(int* __restrict__ bsum, int nb) {
 }
 
 __global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n,
-                             const int* __restrict__ bsum, int nb, int* __restrict__ total) {
+                             const int* __restrict__ bsum, int nb, int* __restrict__ total,
+                             const int* __restrict__ gate) {
+  NB_GATED(gate)
   __shared__ int sh[kScanBlock];
   const int b = blockIdx.x;
   for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x) {
@@ -359,12 +374,12 @@ __global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, 
 }  // namespace
 
 void launch_scan(const int* in, int* out, int n, int* block_scratch, int* total_dev,
-                 cudaStream_t s) {
+                 cudaStream_t s, const int* gate) {
   const int nb = (n + kScanBlock - 1) / kScanBlock;
   const int nbb = nb > 0 ? nb : 1;
-  k_scan_reduce<<<nbb, 256, 0, s>>>(in, n, block_scratch);
-  k_scan_blocks<<<1, 1024, 0, s>>>(block_scratch, nbb);
-  k_scan_apply<<<nbb, 256, 0, s>>>(in, out, n, block_scratch, nbb, total_dev);
+  k_scan_reduce<<<nbb, 256, 0, s>>>(in, n, block_scratch, gate);
+  k_scan_blocks<<<1, 1024, 0, s>>>(block_scratch, nbb, gate);
+  k_scan_apply<<<nbb, 256, 0, s>>>(in, out, n, block_scratch, nbb, total_dev, gate);
 }
 
 GridInfo plan_grid(const double L[3], double rc) {
@@ -391,31 +406,92 @@ GridInfo plan_grid(const double L[3], double rc) {
 }
 
 void launch_build_neighbors(const NeighborBuffers& nb, const GridInfo& g, const double* pos,
-                            int n_atoms, cudaStream_t s, int nps) {
+                            int n_atoms, cudaStream_t s, int nps, const int* gate) {
   if (nps <= 0) nps = n_atoms > 0 ? n_atoms : 1;
   const int n_sys = n_atoms / nps;
   const int ncell = g.ncell[0] > 0 ? n_sys * g.ncell[0] * g.ncell[1] * g.ncell[2] : 0;
   if (ncell > 0) cudaMemsetAsync(nb.cell_count, 0, sizeof(int) * (ncell + 1), s);
   const int tb = 256;
   k_wrap_bin<<<(n_atoms + tb - 1) / tb, tb, 0, s>>>(pos, n_atoms, nps, g, nb.wpos, nb.wpos32,
-                                                   nb.atom_cell, nb.cell_count, nb.flags);
+                                                   nb.atom_cell, nb.cell_count, nb.flags, gate);
   if (ncell > 0) {
-    launch_scan(nb.cell_count, nb.cell_start, ncell, nb.scan_blocks, nullptr, s);
+    launch_scan(nb.cell_count, nb.cell_start, ncell, nb.scan_blocks, nullptr, s, gate);
     // reuse cell_count as the fill cursor
     cudaMemsetAsync(nb.cell_count, 0, sizeof(int) * (ncell + 1), s);
     k_cell_fill<<<(n_atoms + tb - 1) / tb, tb, 0, s>>>(n_atoms, nb.atom_cell, nb.cell_start,
-                                                      nb.cell_count, nb.cell_atoms);
+                                                      nb.cell_count, nb.cell_atoms, gate);
   }
   const int wb = (n_atoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
   k_count<<<wb, kWarpsPerBlock * 32, 0, s>>>(n_atoms, nps, g, nb.wpos32, nb.wpos, nb.atom_cell,
-                                             nb.cell_start, nb.cell_atoms, nb.row_cnt);
-  launch_scan(nb.row_cnt, nb.row_ptr, n_atoms, nb.scan_blocks, nb.n_pairs, s);
+                                             nb.cell_start, nb.cell_atoms, nb.row_cnt, gate);
+  launch_scan(nb.row_cnt, nb.row_ptr, n_atoms, nb.scan_blocks, nb.n_pairs, s, gate);
   k_fill<<<wb, kWarpsPerBlock * 32, 0, s>>>(n_atoms, nps, g, nb.wpos32, nb.wpos, nb.atom_cell,
                                             nb.cell_start, nb.cell_atoms, nb.row_ptr, nb.n_pairs,
                                             nb.capacity, nb.keys, nb.skeys, nb.pi, nb.pj,
-                                            nb.pcode, nb.flags);
+                                            nb.pcode, nb.flags, gate);
   k_reverse<<<152 * 8, 256, 0, s>>>(nb.n_pairs, nb.capacity, nb.row_ptr, nb.pi, nb.pj, nb.pcode,
-                                    nb.skeys, nb.rev, nb.flags);
+                                    nb.skeys, nb.rev, nb.flags, gate);
+}
+
+// ---- Verlet skin (reuse of a list built with r_c + skin) ----
+namespace {
+
+// One block: flag[0] = flag[1] (a forced rebuild) or some atom moved more
+// than skin/2 (minimum image) since the last build; flag[1] cleared.
+__global__ void k_skin_check(int n, const double* __restrict__ pos, const double* __restrict__ pos_ref, double L0,
+                             double L1, double L2, double half_skin2, int* __restrict__ flag) {
+  const double L[3] = {L0, L1, L2};
+  int far = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double d = pos[3 * i + a] - pos_ref[3 * i + a];
+      d -= L[a] * rint(d / L[a]);
+      d2 += d * d;
+    }
+    far |= d2 > half_skin2 ? 1 : 0;
+  }
+  const int any = __syncthreads_or(far);
+  if (threadIdx.x == 0) {
+    flag[0] = (any || flag[1]) ? 1 : 0;
+    flag[1] = 0;
+  }
+}
+
+// After the (possibly skipped) build: a rebuild records the reference
+// positions (the state and its wrap); otherwise the build's wrapped positions
+// are the reference wrap plus the minimum-image displacement, which keeps
+// every pair's image code valid.  Counts rebuilds in flag[2].
+__global__ void k_skin_commit(int n, const double* __restrict__ pos, double* __restrict__ pos_ref,
+                              double* __restrict__ wpos, double* __restrict__ wpos_ref, double L0, double L1, double L2,
+                              int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool rebuilt = flag[0] != 0;
+  if (rebuilt && i == 0) flag[2] += 1;
+  if (i >= n) return;
+  const double L[3] = {L0, L1, L2};
+  for (int a = 0; a < 3; ++a) {
+    if (rebuilt) {
+      pos_ref[3 * i + a] = pos[3 * i + a];
+      wpos_ref[3 * i + a] = wpos[3 * i + a];
+    } else {
+      double d = pos[3 * i + a] - pos_ref[3 * i + a];
+      d -= L[a] * rint(d / L[a]);
+      wpos[3 * i + a] = wpos_ref[3 * i + a] + d;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_skin_check(int n, const double* pos, const double* pos_ref, const double L[3], double skin, int* flag,
+                       cudaStream_t s) {
+  k_skin_check<<<1, 1024, 0, s>>>(n, pos, pos_ref, L[0], L[1], L[2], 0.25 * skin * skin, flag);
+}
+
+void launch_skin_commit(int n, const double* pos, double* pos_ref, double* wpos, double* wpos_ref, const double L[3],
+                        int* flag, cudaStream_t s) {
+  k_skin_commit<<<(n + 255) / 256, 256, 0, s>>>(n, pos, pos_ref, wpos, wpos_ref, L[0], L[1], L[2], flag);
 }
 
 }  // namespace al

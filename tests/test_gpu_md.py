@@ -143,3 +143,57 @@ def test_nvt_conserves_extended_energy_and_cools():
     dE = e1[0, 2] - e1[:, 2].min()
     assert dE > 0 and dH < 0.1 * dE
     al.allegro_destroy(ctx)
+
+
+# force difference between the two runs: FP32, the summation order of the
+# per-atom sums (up to 100 terms, 2^-24 each: 1e-6 of max |F| ~ 5 eV/A);
+# split mode, each run within the method's 2e-3 eV/A of the exact forces
+@pytest.mark.parametrize("prec,dF", [(al.ALLEGRO_FP32, 5e-6), (al.ALLEGRO_FP16_SPLIT, 4e-3)], ids=["fp32", "fp16split"])
+def test_verlet_skin_matches_rebuild_every_step(prec, dF):
+    """Verlet-skin reuse (allegro_set_skin): the list built with r_cut + skin
+    is kept until an atom has moved by more than skin/2.  Pairs beyond r_cut
+    contribute exactly zero, so the trajectory equals the one with a rebuild at
+    every step up to the summation order of the per-atom sums (the extra pairs
+    shift tile boundaries).  A force difference dF moves the lightest atom
+    (1.008 amu) by at most kappa dF t^2 / (2 m) over t = 40 x 0.25 fs, times
+    4 for the divergence of neighbouring trajectories (as in the NVE
+    trajectory test), and changes its velocity by kappa dF t / m times 4.
+    A large skin rebuilds only at the first step, a small one several times;
+    a missed pair or a stale image code would move atoms by far more."""
+    kappa, t, m = 9.648533e-3, 10.0, 1.008
+    tol, tolv = 4 * kappa * dF * t * t / (2 * m), 4 * kappa * dF * t / m
+    cfg = synth.MAIN
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    pos, sp, cell = synth.make_ammonia(108, 0)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    n = 40
+    out = {}
+    for skin in (0.0, 0.6, 0.02):
+        ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+        try:
+            al.allegro_set_md_precision(ctx, prec)
+            al.allegro_set_skin(ctx, skin)
+            al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+            np0 = al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS)
+            e = np.zeros((n, 3))
+            al.allegro_md_step_nve(ctx, 0.25, n, None, e)
+            P, V = np.zeros_like(pos), np.zeros_like(pos)
+            al.allegro_md_get_state(ctx, P, V)
+            out[skin] = (P, V, e, np0, al.allegro_query(ctx, al.ALLEGRO_Q_REBUILDS))
+        finally:
+            al.allegro_destroy(ctx)
+    L = np.diag(cell)
+    for skin in (0.6, 0.02):
+        d = out[skin][0] - out[0.0][0]
+        d -= np.round(d / L) * L
+        assert np.abs(d).max() <= tol, (skin, np.abs(d).max())
+        assert np.abs(out[skin][1] - out[0.0][1]).max() <= tolv
+    assert out[0.6][3] > out[0.0][3]                 # the skin list holds more pairs
+    assert out[0.6][4] == 1                          # built once, at the first step
+    assert 2 <= out[0.02][4] < n                     # rebuilt whenever an atom moved 0.01 A
+    with pytest.raises(al.AllegroError):
+        ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+        try:
+            al.allegro_set_skin(ctx, -1.0)
+        finally:
+            al.allegro_destroy(ctx)
