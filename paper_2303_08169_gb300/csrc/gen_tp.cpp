@@ -194,30 +194,39 @@ void emit(FILE* f, int lmax) {
     }
     std::fprintf(f, "}\n");
   };
+  // Adjoint: with M[a][b] = sum_o c_abo dT[o] (one entry per (a, b) that has
+  // terms), dV[a] += sum_b M[a][b] G[b] and dG[b] += sum_a M[a][b] V[a]: each
+  // CG term costs one multiply-add in M instead of one in each of dV and dG.
+  // Emitted row by row (a), so that only one row of M is live at a time.
   auto bwd = [&](const char* name, const std::vector<Term>& ts) {
     std::fprintf(f, "template <class S>\n__device__ __forceinline__ void tp%s_%s(const S* __restrict__ V, "
                  "const S* __restrict__ G, const S* __restrict__ dT, "
                  "S* __restrict__ dV, S* __restrict__ dG) {\n", L.c_str(), name);
     const int nc = (lmax + 1) * (lmax + 1);
     for (int a = 0; a < nc; ++a) {
-      std::string e;
-      for (auto& t : ts)
-        if (t.a == a) {
-          std::string term = lit(t.c) + " * dT[" + std::to_string(t.o) + "] * G[" +
-                             std::to_string(t.b) + "]";
-          e = e.empty() ? term : e + " + " + term;
-        }
-      if (!e.empty()) std::fprintf(f, "  dV[%d] += %s;\n", a, e.c_str());
-    }
-    for (int b = 0; b < nc; ++b) {
-      std::string e;
-      for (auto& t : ts)
-        if (t.b == b) {
-          std::string term = lit(t.c) + " * dT[" + std::to_string(t.o) + "] * V[" +
-                             std::to_string(t.a) + "]";
-          e = e.empty() ? term : e + " + " + term;
-        }
-      if (!e.empty()) std::fprintf(f, "  dG[%d] += %s;\n", b, e.c_str());
+      std::vector<int> bs;
+      std::string block;
+      for (int b = 0; b < nc; ++b) {
+        std::string e;
+        for (auto& t : ts)
+          if (t.a == a && t.b == b) {
+            const std::string term = lit(t.c) + " * dT[" + std::to_string(t.o) + "]";
+            e = e.empty() ? term : e + " + " + term;
+          }
+        if (e.empty()) continue;
+        bs.push_back(b);
+        block += "    const S m" + std::to_string(b) + " = " + e + ";\n";
+      }
+      if (bs.empty()) continue;
+      std::string dv;
+      for (int b : bs) {
+        const std::string term = "m" + std::to_string(b) + " * G[" + std::to_string(b) + "]";
+        dv = dv.empty() ? term : dv + " + " + term;
+      }
+      block += "    dV[" + std::to_string(a) + "] += " + dv + ";\n";
+      for (int b : bs)
+        block += "    dG[" + std::to_string(b) + "] += m" + std::to_string(b) + " * V[" + std::to_string(a) + "];\n";
+      std::fprintf(f, "  {\n%s  }\n", block.c_str());
     }
     std::fprintf(f, "}\n");
   };

@@ -427,6 +427,31 @@ struct Mma {
 
 AL_DEV uint32_t lanes(uint32_t tmem) { return tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16); }
 
+// SiLU epilogue of a 128-column pre-activation z at TMEM column col0 whose
+// adjoint needs SiLU'(z) later: thread (r, h) turns its 32 columns into
+// SiLU(z), handed to st(r, n0, v[16]) 16 at a time, and writes SiLU'(z) back
+// over z (one sigmoid for both); the adjoint epilogue reads SiLU' directly.
+// The store is waited for before returning.
+template <class St>
+AL_DEV void epi_silu_keep_grad(uint32_t tmem, int col0, St&& st) {
+  const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  const uint32_t base = lanes(tmem) + (uint32_t)(col0 + 32 * h);
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    float v[16], o[16];
+    tmem_ld16(base + 16 * hf, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float z = v[q], sg = sgm(z);
+      o[q] = z * sg;                                 // silu_b(z)
+      v[q] = sg * (1.0f + z * (1.0f - sg));          // dsilu_b(z)
+    }
+    st(r, 32 * h + 16 * hf, o);
+    tmem_st16(base + 16 * hf, v);
+  }
+  tmem_wait_st();
+}
+
 // thread (r, h) of a CTA with nq = blockDim / 128 column groups visits
 // columns [h N/nq, (h+1) N/nq) of an N-wide accumulator at TMEM column col0,
 // 16 at a time: f(r, n0, v[16])
@@ -1006,12 +1031,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
     }
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, 3, false, 0, true); });
-    epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
-      float o[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16<Tin>(A1, rr, n0, o);
-    });
+    epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16];
@@ -1067,10 +1087,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     }
     mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, true, 128); });    // da1
     epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
-      float z1[16], o[16];
-      tmem_ld16(lanes(tmem) + n0, z1);
+      float g1[16], o[16];                             // SiLU'(z1), left in TMEM by the z1 epilogue
+      tmem_ld16(lanes(tmem) + n0, g1);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
+      for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16<Tin>(HA, rr, n0, o);
     });
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 176, 8, true, 128); });      // [dx^{L-1}, ds]
@@ -1270,12 +1290,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       mma_k<Tin>(tmem + kZ1, HA, 0, Wl0, 128, 11, false, 0);                    // z1
       if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, 48, 8, false, 0);           // w0 = emb x^0
     });
-    epi(tmem, kZ1, 128, [&](int rr, int n0, const float* v) {
-      float o[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16<Tin>(A1, rr, n0, o);
-    });
+    epi_silu_keep_grad(tmem, kZ1, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.run([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, false, 0); });     // z2
     {
       // dx = dx^k + env^T de; its residual part dx / sqrt 2 goes back into
@@ -1306,10 +1321,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
     }
     mm.run([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, true, 128); });    // da1
     epi(tmem, kZ2, 128, [&](int rr, int n0, const float* da) {
-      float z1[16], o[16];
-      tmem_ld16(lanes(tmem) + kZ1 + n0, z1);
+      float g1[16], o[16];                             // SiLU'(z1), left in TMEM by the z1 epilogue
+      tmem_ld16(lanes(tmem) + kZ1 + n0, g1);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
+      for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16<Tin>(HA, rr, n0, o);
     });
     mm.run([&] { mma_k<Tin>(tmem + kDX, HA, 0, Wl0, 176, 8, true, 128, true); });  // [dx, ds] += dz1 W
@@ -1514,12 +1529,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
     }
     stage_g(b.dgsum[1], m, s_g);
     mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });   // z1
-    epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
-      float o[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
-      st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o);
-    });
+    epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o); });
     mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });   // z2
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16];
@@ -1579,10 +1589,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
     }
     mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, true, 128); });   // da1
     epi(tmem, 128, 128, [&](int rr, int n0, const float* da) {
-      float z1[16], o[16];
-      tmem_ld16(lanes(tmem) + n0, z1);
+      float g1[16], o[16];                             // SiLU'(z1), left in TMEM by the z1 epilogue
+      tmem_ld16(lanes(tmem) + n0, g1);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = da[q] * dsilu_b(z1[q]);
+      for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16_op<Tin, kSplit>(X, A1lo, rr, n0, o);
     });
     float duo = 0.0f, dyo[NLM];                       // loaded ahead of the MMA wait
