@@ -1491,6 +1491,11 @@ int capture_step_nvt(allegro_ctx* c, double dt, double temperature, double tau) 
   return ALLEGRO_OK;
 }
 
+// MD calls that overflow the pair capacity roll back to their first step,
+// grow the capacity by half and run again, up to this many times (a long call
+// on a heating system may outgrow several capacities).
+constexpr int kMdAttempts = 6;
+
 int capture_step(allegro_ctx* c, double dt) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -1544,7 +1549,7 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
   int rc0 = ensure_records(ctx, n_steps);
   if (rc0) return rc0;
   const size_t n3 = 3 * (size_t)ctx->n_atoms;
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  for (int attempt = 0; attempt < kMdAttempts; ++attempt) {
     if (!ctx->graph || ctx->graph_dt != dt_fs) {
       int rc = capture_step(ctx, dt_fs);
       if (rc) return rc;
@@ -1567,7 +1572,7 @@ int allegro_md_step_nve(allegro_ctx* ctx, double dt_fs, int32_t n_steps, int64_t
       cudaMemcpyAsync(ctx->d_F, ctx->d_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaStreamSynchronize(ctx->stream);
       if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait (state rolled back)");
-      const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024;
+      const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 3 / 2 + 1024;
       int rc = ensure_pairs(ctx, grow);
       if (rc) return rc;
       continue;
@@ -1594,7 +1599,7 @@ int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double 
   if (rc) return rc;
   const size_t n3 = 3 * (size_t)ctx->n_atoms;
   const AtomArgs a = atom_args(ctx);
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  for (int attempt = 0; attempt < kMdAttempts; ++attempt) {
     if (!ctx->graph_nvt || ctx->nvt_key[0] != dt_fs || ctx->nvt_key[1] != temperature_K || ctx->nvt_key[2] != tau_fs) {
       rc = capture_step_nvt(ctx, dt_fs, temperature_K, tau_fs);
       if (rc) return rc;
@@ -1620,7 +1625,7 @@ int allegro_md_step_nvt(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double 
       cudaMemcpyAsync(ctx->d_nh, ctx->d_nh_snap, sizeof(double) * 4, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaStreamSynchronize(ctx->stream);
       if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait (state rolled back)");
-      const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024;
+      const int64_t grow = std::max<int64_t>((int64_t)np, ctx->capacity) * 3 / 2 + 1024;
       rc = ensure_pairs(ctx, grow);
       if (rc) return rc;
       continue;
@@ -1843,7 +1848,7 @@ int allegro_pimd_step(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double* e
   if (rc) return rc;
   const size_t n3 = 3 * (size_t)ctx->rp_P * (size_t)ctx->rp_n;
   cudaStream_t s = ctx->stream;
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  for (int attempt = 0; attempt < kMdAttempts; ++attempt) {
     if (!ctx->graph_rp || ctx->rp_graph_dt != dt_fs) {
       rc = capture_step_rp(ctx, dt_fs);
       if (rc) return rc;
@@ -1865,7 +1870,7 @@ int allegro_pimd_step(allegro_ctx* ctx, double dt_fs, int32_t n_steps, double* e
       cudaMemcpyAsync(ctx->d_rp_F, ctx->d_rp_F_snap, sizeof(float) * n3, cudaMemcpyDeviceToDevice, s);
       cudaStreamSynchronize(s);
       if (flags & kFlagTimeout) return ctx->fail(ALLEGRO_E_TIMEOUT, "a tensor-core pass gave up a bounded wait (state rolled back)");
-      rc = ensure_pairs(ctx, std::max<int64_t>((int64_t)np, ctx->capacity) * 5 / 4 + 1024);
+      rc = ensure_pairs(ctx, std::max<int64_t>((int64_t)np, ctx->capacity) * 3 / 2 + 1024);
       if (rc) return rc;
       continue;
     }

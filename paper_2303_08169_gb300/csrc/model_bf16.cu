@@ -499,6 +499,24 @@ AL_DEV void st16(uint8_t* A, int r, int c0, const float* v) {
   st8<Tin>(A, sw128_off(r, c0, 128), v);
   st8<Tin>(A, sw128_off(r, c0 + 8, 128), v + 8);
 }
+// 16 FP16 operand values of row r from column c0 (c0 % 8 == 0) of a 128-row
+// swizzled tile, as floats (the inverse of st16 for FP16 operands)
+AL_DEV void ld16_h(const uint8_t* A, int r, int c0, float* x) {
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const uint4 u = *reinterpret_cast<const uint4*>(A + sw128_off(r, c0 + 8 * g, 128));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __half2 h2;
+      memcpy(&h2, &w[q], 4);
+      const float2 f = __half22float2(h2);
+      x[8 * g + 2 * q] = f.x;
+      x[8 * g + 2 * q + 1] = f.y;
+    }
+  }
+}
+
 template <class Tin>
 AL_DEV void st4(uint8_t* A, uint32_t off, const float* v) {
   const uint32_t w0 = Op<Tin>::pack2(v[0], v[1]);
@@ -897,11 +915,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     });
     mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
-      float o[16];
+      float o[16], xs[16];
       const float fc = s_fc[rr];
+      // FP16 operands: the operand tile holds the stored x^{k-1} itself
+      if constexpr (Op<Tin>::fmt == 0) ld16_h(HA, rr, n0, xs);
 #pragma unroll
       for (int q = 0; q < 16; q += 2) {
-        const float2 x = valid ? ldh2(xg, hidx(tile, D, n0 + q, rr)) : make_float2(0.f, 0.f);
+        float2 x;
+        if constexpr (Op<Tin>::fmt == 0) x = make_float2(xs[q], xs[q + 1]);
+        else x = valid ? ldh2(xg, hidx(tile, D, n0 + q, rr)) : make_float2(0.f, 0.f);
         o[q] = r16((x.x + fc * silu_b(v[q])) * kR2);
         o[q + 1] = r16((x.y + fc * silu_b(v[q + 1])) * kR2);
       }
@@ -1034,11 +1056,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
-      float o[16];
+      float o[16], xs[16];
       const float fc = s_fc[rr];
+      // FP16 operands: the operand tile holds the stored x^{L-1} itself
+      if constexpr (Op<Tin>::fmt == 0) ld16_h(HA, rr, n0, xs);
 #pragma unroll
       for (int q = 0; q < 16; q += 2) {
-        const float2 x = valid ? ldh2(xg, hidx(tile, D, n0 + q, rr)) : make_float2(0.f, 0.f);
+        float2 x;
+        if constexpr (Op<Tin>::fmt == 0) x = make_float2(xs[q], xs[q + 1]);
+        else x = valid ? ldh2(xg, hidx(tile, D, n0 + q, rr)) : make_float2(0.f, 0.f);
         o[q] = (x.x + fc * silu_b(v[q])) * kR2;
         o[q + 1] = (x.y + fc * silu_b(v[q + 1])) * kR2;
       }

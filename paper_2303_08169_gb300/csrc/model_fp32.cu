@@ -24,6 +24,7 @@
 // Per-atom sums (Gamma, dGamma, sum_j E_ij) are written as per-(tile, atom)
 // partials at index tile + atom and summed in tile order by the consumer, so
 // every result is bitwise deterministic without atomics.
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -257,16 +258,23 @@ AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt,
 template <int TT>
 struct TileMeta {
   int pi[TT], pj[TT], code[TT], seg[TT], atom[TT];
-  int nseg, np, p0;
+  int nseg, np, p0, tile;
 };
 
+// Tiles of the current list (0 on pair overflow: the list is incomplete).
+// Every pass kernel loops over tiles tile = blockIdx.x, + gridDim.x, ...
 template <int TT>
-AL_DEV bool tile_setup(const PassBufs& b, TileMeta<TT>& t) {
-  static_assert(TT <= 32, "one warp sets a tile up");
-  if (*b.flags & 1) return false;   // pair overflow: the list is incomplete
+AL_DEV int num_tiles(const PassBufs& b) {
+  if (*b.flags & 1) return 0;
   const int P = (int)min((int64_t)*b.n_pairs, b.capacity);
-  const int p0 = blockIdx.x * TT;
-  if (p0 >= P) return false;
+  return (P + TT - 1) / TT;
+}
+
+template <int TT>
+AL_DEV void tile_setup(const PassBufs& b, TileMeta<TT>& t, int tile) {
+  static_assert(TT <= 32, "one warp sets a tile up");
+  const int P = (int)min((int64_t)*b.n_pairs, b.capacity);
+  const int p0 = tile * TT;
   const int np = min(TT, P - p0);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -291,10 +299,10 @@ AL_DEV bool tile_setup(const PassBufs& b, TileMeta<TT>& t) {
       t.nseg = __popc(m);
       t.np = np;
       t.p0 = p0;
+      t.tile = tile;
     }
   }
   __syncthreads();
-  return true;
 }
 
 // Sum of per-(tile, atom) partials of every segment's atom: out[s][x].
@@ -319,7 +327,7 @@ AL_DEV void store_segments(T* __restrict__ part, const TileMeta<TT>& t, F&& f) {
     T acc = 0.0f;
     for (int p = 0; p < t.np; ++p)
       if (t.seg[p] == s) acc += f(p, x);
-    part[(size_t)(blockIdx.x + t.atom[s]) * W + x] = acc;
+    part[(size_t)(t.tile + t.atom[s]) * W + x] = acc;
   }
 }
 
@@ -395,7 +403,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_a(ModelW w, Pa
   __shared__ TileMeta<TT> t;
   constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
-  if (!tile_setup(b, t)) return;
+  const int ntiles = num_tiles<TT>(b);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  tile_setup(b, t, tile);
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
   T* s_h0 = cv.take<T>(TT * Cf::LDH0);
@@ -437,6 +447,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_a(ModelW w, Pa
   store_segments<Cf::CL>(as<T>(b.gam[1]), t, [&](int p, int x) {
     return s_e[p * C + x / NLM] * s_Y[p * NLM + x % NLM];
   });
+  __syncthreads();   // the next tile reuses the shared arrays
+  }
 }
 
 // V^{k-1}_c for one pair and channel: from the stored array, or for k = 1 from
@@ -466,7 +478,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b(ModelW w, Pa
   __shared__ TileMeta<TT> t;
   constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
-  if (!tile_setup(b, t)) return;
+  const int ntiles = num_tiles<TT>(b);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  tile_setup(b, t, tile);
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
   T* s_h = cv.take<T>(TT * LDH);
@@ -542,6 +556,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b(ModelW w, Pa
   store_segments<CL>(as<T>(b.gam[k + 1]), t, [&](int pp, int x) {
     return s_e[pp * C + x / NLM] * s_Y[pp * NLM + x % NLM];
   });
+  __syncthreads();   // the next tile reuses the shared arrays
+  }
 }
 
 // Reduce a per-thread value over the kSub consecutive lanes of one pair.
@@ -564,7 +580,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_c(ModelW w, Pa
   __shared__ T s_eij[TT];
   __shared__ T s_sig[TT];
   extern __shared__ float4 smem4[];
-  if (!tile_setup(b, t)) return;
+  const int ntiles = num_tiles<TT>(b);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  tile_setup(b, t, tile);
   const int L = w.n_layers;
   const LayerW& LW = w.layer[L - 1];
   Carve cv{reinterpret_cast<float*>(smem4)};
@@ -659,7 +677,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_c(ModelW w, Pa
     double acc = 0.0;
     for (int q = 0; q < t.np; ++q)
       if (t.seg[q] == s) acc += (double)val(s_eij[q]);
-    b.epart[blockIdx.x + t.atom[s]] = acc;
+    b.epart[t.tile + t.atom[s]] = acc;
   }
   if (b.train) dump_rows<E>(b.tr.dze, b.trt.dze, t, s_ze, LDE);
   gemm<D, E, TT>(s_ze, LDE, w.e0.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] = v; });  // dx^L
@@ -747,6 +765,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_c(ModelW w, Pa
     as<T>(b.dY)[(size_t)t.p0 * NLM + idx] = s_dy[idx];
   if (threadIdx.x < t.np) as<T>(b.dU)[t.p0 + threadIdx.x] = s_du[threadIdx.x];
   store_segments<CL>(as<T>(b.dgam[L]), t, [&](int pp, int x) { return s_dg[pp * CL + x]; });
+  __syncthreads();   // the next tile reuses the shared arrays
+  }
 }
 
 // ============================================================================
@@ -759,7 +779,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b_bwd(ModelW w
   __shared__ TileMeta<TT> t;
   constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
-  if (!tile_setup(b, t)) return;
+  const int ntiles = num_tiles<TT>(b);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  tile_setup(b, t, tile);
   const LayerW& LW = w.layer[k - 1];
   const LayerW& LN = w.layer[k];
   Carve cv{reinterpret_cast<float*>(smem4)};
@@ -939,6 +961,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b_bwd(ModelW w
     as<T>(b.dY)[(size_t)t.p0 * NLM + idx] += s_dy[idx];
   if (threadIdx.x < t.np) as<T>(b.dU)[t.p0 + threadIdx.x] += s_du[threadIdx.x];
   store_segments<CL>(as<T>(b.dgam[k]), t, [&](int pp, int x) { return s_dG[pp * CL + x]; });
+  __syncthreads();   // the next tile reuses the shared arrays
+  }
 }
 
 // ============================================================================
@@ -950,7 +974,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_a_bwd(ModelW w
   __shared__ TileMeta<TT> t;
   constexpr int kSub = kThreads / TT;
   extern __shared__ float4 smem4[];
-  if (!tile_setup(b, t)) return;
+  const int ntiles = num_tiles<TT>(b);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  tile_setup(b, t, tile);
   Carve cv{reinterpret_cast<float*>(smem4)};
   float* s_wb = cv.take(Cf::WB);
   T* s_h0 = cv.take<T>(TT * Cf::LDH0);
@@ -1062,6 +1088,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_a_bwd(ModelW w
     const T inv = 1.0f / d;
     for (int a = 0; a < 3; ++a) as<T>(b.G)[pp * 3 + a] = gd * u[a] + (gu[a] - ud * u[a]) * inv;
   }
+  __syncthreads();   // the next tile reuses the shared arrays
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -1101,7 +1129,10 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     cudaFuncSetAttribute(k_pass_a_bwd<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::ab);
     init = true;
   }
-  const int grid = (int)((capacity + TT - 1) / TT);
+  // blocks loop over the tiles of the list (the pair count is known on the
+  // device only): eight waves of resident blocks, or one block per tile of
+  // the capacity if that is fewer
+  const int grid = (int)std::min<int64_t>((capacity + TT - 1) / TT, 152 * kMinBlocks<X> * 8);
   const int L = w.n_layers;
   auto mark = [&](int k) {
     if (km) km->mark(k, s);

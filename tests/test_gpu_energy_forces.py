@@ -160,3 +160,23 @@ def test_invalid_inputs(main):
     # the context stays usable after each rejected call
     E, F, Ei = _gpu(ctx, pos, sp, cell)
     assert np.isfinite(E)
+
+
+@pytest.mark.parametrize("precision", [al.ALLEGRO_FP32, al.ALLEGRO_FP16_SPLIT], ids=["fp32", "fp16split"])
+def test_no_pairs_and_single_atom(main, precision):
+    """Degenerate inputs: atoms farther apart than r_cut (an empty pair list)
+    and a single atom.  E_i = mu_Z (0 here) and every force is zero, exactly,
+    on both paths; a following ordinary call is unaffected."""
+    ctx, orc = main
+    cell = np.diag([30.0, 30.0, 30.0])
+    pos = np.array([[1.0, 1.0, 1.0], [8.0, 1.0, 1.0], [1.0, 9.5, 20.0]])
+    sp = np.array([0, 1, 1])
+    for p, s in ((pos, sp), (pos[:1], sp[:1])):
+        E, F, Ei = _gpu(ctx, p, s, cell, precision)
+        Er, Fr, Eir, pairs = orc.energy_forces(p, s, np.diag(cell))
+        assert len(pairs[0]) == 0 and al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS) == 0
+        assert E == Er and np.array_equal(Ei, Eir) and not np.any(F) and not np.any(Fr)
+    p2, s2, c2 = synth.make_ammonia(16, 3)
+    E, F, Ei = _gpu(ctx, p2, s2, c2)
+    Er, Fr, Eir, _ = orc.energy_forces(p2, s2, np.diag(c2))
+    _compare(E, F, Ei, Er, Fr, Eir)
