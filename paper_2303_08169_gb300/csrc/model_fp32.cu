@@ -34,14 +34,9 @@
 namespace al {
 namespace {
 
-constexpr int kTile = 16;       // pairs per tile (FP32 passes)
+constexpr int kTile = 32;       // pairs per tile (FP32 passes)
 constexpr int kTileDual = 16;   // pairs per tile (tangent passes: two floats per value)
-constexpr int kThreads = 256;   // 16 threads per pair in per-pair phases
-// resident blocks per SM the kernels are compiled for: two for the FP32
-// passes (16-pair tiles fit twice into shared memory and the register file),
-// one for the tangent passes
-template <class T>
-constexpr int kMinBlocks = is_dual<T>::value ? 1 : 2;
+constexpr int kThreads = 256;   // 8 (16) threads per pair in per-pair phases
 constexpr float kRsqrt2 = 0.70710678118654752f;
 
 // ----------------------------------------------------------------------------
@@ -398,7 +393,7 @@ struct Carve {
 // ============================================================================
 // Pass A: geometry, two-body MLP, x0, e^1 -> Gamma^1 partials.
 template <class Cf, class T, int TT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_a(ModelW w, PassBufs b) {
+__global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, LDD = Cf::LDD;
   __shared__ TileMeta<TT> t;
   constexpr int kSub = kThreads / TT;
@@ -471,7 +466,7 @@ AL_DEV void load_v(int k, const PassBufs& b, const TileMeta<TT>& t, int p, int c
 // ============================================================================
 // Pass B_k (1 <= k < L): tensor product, mixing, latent MLP, e^{k+1} scatter.
 template <class Cf, class T, int TT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b(ModelW w, PassBufs b, int k) {
+__global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, NT = Cf::NT, NS = Cf::NS, CL = Cf::CL;
   constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LMAX = Cf::LMAX;
   using Tp = TP<LMAX>;
@@ -571,7 +566,7 @@ AL_DEV T sub_sum_(T v) {
 // ============================================================================
 // Pass C: last layer L and energy MLP forward, then their adjoint.
 template <class Cf, class T, int TT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_c(ModelW w, PassBufs b) {
+__global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   constexpr int D = Cf::D, C = Cf::C, E = Cf::E, NLM = Cf::NLM, NS = Cf::NS, CL = Cf::CL;
   constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LDE = Cf::LDE, LMAX = Cf::LMAX;
   using Tp = TP<LMAX>;
@@ -772,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_c(ModelW w, Pa
 // ============================================================================
 // Pass B_k^T (k = L-1 .. 1): adjoint of the Gamma^{k+1} scatter and of layer k.
 template <class Cf, class T, int TT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b_bwd(ModelW w, PassBufs b, int k) {
+__global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, int k) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, NT = Cf::NT, NS = Cf::NS, CL = Cf::CL;
   constexpr int LDD = Cf::LDD, LDH = Cf::LDH, LMAX = Cf::LMAX;
   using Tp = TP<LMAX>;
@@ -969,7 +964,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_b_bwd(ModelW w
 // Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP and of the
 // geometry; writes g_ij = dE/dDelta_ij.
 template <class Cf, class T, int TT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>) k_pass_a_bwd(ModelW w, PassBufs b) {
+__global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   constexpr int D = Cf::D, C = Cf::C, NLM = Cf::NLM, CL = Cf::CL, LDD = Cf::LDD, NB = Cf::NB;
   __shared__ TileMeta<TT> t;
   constexpr int kSub = kThreads / TT;
@@ -1130,9 +1125,9 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     init = true;
   }
   // blocks loop over the tiles of the list (the pair count is known on the
-  // device only): eight waves of resident blocks, or one block per tile of
-  // the capacity if that is fewer
-  const int grid = (int)std::min<int64_t>((capacity + TT - 1) / TT, 152 * kMinBlocks<X> * 8);
+  // device only): eight waves of one resident block per SM, or one block per
+  // tile of the capacity if that is fewer
+  const int grid = (int)std::min<int64_t>((capacity + TT - 1) / TT, 152 * 8);
   const int L = w.n_layers;
   auto mark = [&](int k) {
     if (km) km->mark(k, s);
