@@ -435,42 +435,49 @@ class Runner:
 
 
 def lmax_sweep(al, torch, dev, K=10, W=3, n_mol=27648):
-    """Time per MD step (E+F, FP32 passes, graph-captured NVE step) of the
-    main model's widths at l_max 0, 1 and 2 on the 110,592-atom system: the
+    """Time per MD step (E+F, graph-captured NVE step) of the main model's
+    widths at l_max 0, 1 and 2 on the 110,592-atom system, in the split
+    tensor-core mode (the headline precision) and on the FP32 passes: the
     shape of the paper's Table 2 (395 : 916 : 2,580 ms for l = 0 : 1 : 2 on
     its own platform and system)."""
     import synth
     pos, sp, cell, vel = _system(n_mol)
-    out = {"l_max": [], "ms_per_step": [], "pairs": [], "params": []}
+    out = {"l_max": [], "ms_per_step": [], "ms_per_step_fp32": [], "pairs": [], "params": []}
     for lmax in (0, 1, 2):
         M = synth.MAIN
         cfg = synth.ModelConfig(r_cut=M.r_cut, l_max=lmax, n_layers=M.n_layers, n_channels=M.n_channels,
                                 latent=M.latent, energy=M.energy, avg_num_neighbors=M.avg_num_neighbors)
         blob = synth.make_blob(cfg, 42, sigma=_energy_scale("main"))
         run = Runner(al, torch, dev, blob, cfg)
-        al.allegro_set_md_precision(run.ctx, 0)
-        al.allegro_md_init(run.ctx, torch.tensor(pos, device=dev), torch.tensor(vel, device=dev),
-                           torch.tensor(sp, device=dev, dtype=torch.int32), cell)
-        al.allegro_md_step_nve(run.ctx, 0.25, W)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(run.stream)
-        al.allegro_md_step_nve(run.ctx, 0.25, K)
-        ev1.record(run.stream)
-        torch.cuda.synchronize()
+        times = {}
+        for prec in (al.ALLEGRO_FP16_SPLIT, al.ALLEGRO_FP32):
+            al.allegro_set_md_precision(run.ctx, prec)
+            al.allegro_md_init(run.ctx, torch.tensor(pos, device=dev), torch.tensor(vel, device=dev),
+                               torch.tensor(sp, device=dev, dtype=torch.int32), cell)
+            al.allegro_md_step_nve(run.ctx, 0.25, W)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(run.stream)
+            al.allegro_md_step_nve(run.ctx, 0.25, K)
+            ev1.record(run.stream)
+            torch.cuda.synchronize()
+            times[prec] = ev0.elapsed_time(ev1) / K
+            if prec == al.ALLEGRO_FP16_SPLIT:
+                out["pairs"].append(al.allegro_query(run.ctx, al.ALLEGRO_Q_N_PAIRS))
         out["l_max"].append(lmax)
-        out["ms_per_step"].append(ev0.elapsed_time(ev1) / K)
-        out["pairs"].append(al.allegro_query(run.ctx, al.ALLEGRO_Q_N_PAIRS))
+        out["ms_per_step"].append(times[al.ALLEGRO_FP16_SPLIT])
+        out["ms_per_step_fp32"].append(times[al.ALLEGRO_FP32])
         out["params"].append(al.allegro_query(run.ctx, al.ALLEGRO_Q_N_PARAMS))
         run.close()
     t0 = out["ms_per_step"][0]
     out["ratio_to_l0"] = [t / t0 for t in out["ms_per_step"]]
+    out["ratio_to_l0_fp32"] = [t / out["ms_per_step_fp32"][0] for t in out["ms_per_step_fp32"]]
     out["paper_ratio_to_l0"] = [1.0, 916.0 / 395.0, 2580.0 / 395.0]
     out["atoms"] = len(sp)
     out["steps"] = K
-    out["note"] = ("FP32 pair passes (the tensor-core path is built for l_max 2 only); main model widths "
-                   "(16 channels, latent [128, 128]), 2 layers")
+    out["note"] = ("ms_per_step: FP16_SPLIT tensor-core passes; ms_per_step_fp32: FP32 pair passes; main model "
+                   "widths (16 channels, latent [128, 128]), 2 layers; pairs at the start of the split-mode run")
     return out
 
 

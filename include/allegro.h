@@ -55,7 +55,7 @@ extern "C" {
 
 #define ALLEGRO_FP32 0   /* every per-pair GEMM in FP32 on CUDA cores           */
 #define ALLEGRO_BF16 1   /* per-pair GEMMs on tensor cores, BF16 operands,      */
-                         /* FP32 accumulation (2-layer l_max 2 model)           */
+                         /* FP32 accumulation (C 16, D 128, E 32, 2+ layers)    */
 #define ALLEGRO_FP16 2   /* same tensor-core path with FP16 operands            */
 #define ALLEGRO_FP16_SPLIT 3  /* FP16 operands; the two-body MLP and the energy   */
                          /* hidden layer with split operands x = hi + lo, three */
@@ -77,7 +77,8 @@ const char* allegro_version(void);
  * functions, envelope p = 6, two latent hidden widths D = D, one energy
  * hidden width, and (l_max, C, D, E) in {(1, 8, 32, 32), (0, 16, 128, 32),
  * (1, 16, 128, 32), (2, 16, 128, 32)} (the last three: the l_max sweep of
- * Table 2 at one width; the tensor-core precisions need l_max 2).
+ * Table 2 at one width, in every precision; the tensor-core precisions need
+ * at least two layers).
  * The paper defines only the pairwise-energy decomposition and equivariance
  * (Sec. 2.1); the layer structure follows the Allegro reading stated in the
  * oracle package.
@@ -132,7 +133,7 @@ int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col,
  *  atom_energy  : host or device, N FP64 per-atom energies E_i (may be NULL).
  *  precision    : ALLEGRO_FP32, ALLEGRO_BF16, ALLEGRO_FP16 or
  *                 ALLEGRO_FP16_SPLIT (the tensor-core modes: E_UNSUPPORTED
- *                 unless l_max = 2, C = 16, D = 128, E = 32, at least two
+ *                 unless l_max <= 2, C = 16, D = 128, E = 32, at least two
  *                 layers).
  * On ALLEGRO_E_PAIR_OVERFLOW nothing is written; the context has grown and
  * the call may simply be repeated.  The call reuses the MD state's buffers:

@@ -439,7 +439,7 @@ int upload_weights_bf16(allegro_ctx* c, TcMode mode) {
   size_t o_tb0 = split ? add_parts(B.find("twobody.0"), 1.0, 128, 64, {0, 0, 1}, {0, 16, 32})
                        : add(B.find("twobody.0"), 1.0, 128, 64);
   size_t o_tb1 = add(B.find("twobody.1"), 1.0, 128, 128);
-  size_t o_emb = add(B.find("embed"), 1.0, 48, 128);
+  size_t o_emb = add(B.find("embed"), 1.0, (int)(B.C * (B.lmax + 1)), 128);
   size_t o_e0 = add(B.find("energy.0"), 1.0, 32, 128);
   size_t o_tb1_lo = 0, o_e0_lo = 0;
   if (split) {
@@ -453,7 +453,7 @@ int upload_weights_bf16(allegro_ctx* c, TcMode mode) {
     o_l0[k - 1] = add(B.find(pre + "latent.0"), 1.0, 128, 192);
     o_l1[k - 1] = add(B.find(pre + "latent.1"), 1.0, 128, 128);
     if (k < B.L)
-      for (int l = 0; l < 3; ++l) o_mix[k - 1][l] = add(B.find(pre + "mix" + std::to_string(l)), 1.0, 16, 64);
+      for (uint32_t l = 0; l <= B.lmax; ++l) o_mix[k - 1][l] = add(B.find(pre + "mix" + std::to_string(l)), 1.0, 16, 64);
   }
   uint8_t* dev = c->dalloc<uint8_t>(img.size());
   if (!dev) return c->fail(ALLEGRO_E_OOM, "tensor-core weights allocation failed");
@@ -472,12 +472,13 @@ int upload_weights_bf16(allegro_ctx* c, TcMode mode) {
     w.lat0[k - 1] = dev + o_l0[k - 1];
     w.lat1[k - 1] = dev + o_l1[k - 1];
     if (k < B.L)
-      for (int l = 0; l < 3; ++l) w.mix[k - 1][l] = dev + o_mix[k - 1][l];
+      for (uint32_t l = 0; l <= B.lmax; ++l) w.mix[k - 1][l] = dev + o_mix[k - 1][l];
   }
   w.eout = c->w.eout;
   for (int s = 0; s < 2; ++s) w.sigma[s] = (float)B.sigma[s];
   w.rc = (float)B.rc;
   w.n_layers = (int)B.L;
+  w.lmax = (int)B.lmax;
   return ALLEGRO_OK;
 }
 
@@ -618,7 +619,7 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   c->dfree(pb.dR);
   pb.dR = nullptr;
   if (c->bf16_ok) {
-    const int NSC = B.C * 3;                          // layer scalars, FP16 pairs
+    const int NSC = B.C * (B.lmax + 1);               // layer scalars (P_0 = l_max + 1 per channel), FP16 pairs
     for (uint32_t k = 1; k < B.L && ok; ++k) {
       pb.S[k] = c->dalloc<float>((size_t)capr * (NSC / 2));
       ok = ok && pb.S[k];
@@ -790,7 +791,7 @@ int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
     return c->fail(ALLEGRO_E_INVALID_ARG,
                    "precision must be ALLEGRO_FP32, ALLEGRO_BF16, ALLEGRO_FP16 or ALLEGRO_FP16_SPLIT");
   if (precision != ALLEGRO_FP32 && !c->bf16_ok)
-    return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
+    return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 16-channel, latent-128 model with 2+ layers and l_max <= 2 only");
   if (precision != ALLEGRO_FP32) {
     const int rc = refresh_tc(c);
     if (rc) return rc;
@@ -1355,7 +1356,7 @@ int allegro_set_skin(allegro_ctx* ctx, double skin_A) {
 int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
   if (!ctx || !valid_precision(precision)) return ALLEGRO_E_INVALID_ARG;
   if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
-    return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 2+-layer l_max 2 model only");
+    return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 16-channel, latent-128 model with 2+ layers and l_max <= 2 only");
   if (precision == ALLEGRO_FP32) {
     const int rc = require_fp32(ctx);
     if (rc) return rc;

@@ -101,12 +101,12 @@ struct PassBufs {
 struct BfW {
   const uint8_t* tb0 = nullptr;   // [128 x 64]  (12 inputs used)
   const uint8_t* tb1 = nullptr;   // [128 x 128]
-  const uint8_t* emb = nullptr;   // [48 x 128]
+  const uint8_t* emb = nullptr;   // [C (l_max + 1) x 128]
   const uint8_t* e0 = nullptr;    // [32 x 128]
   const uint8_t* env[kMaxLayers] = {};
   const uint8_t* lat0[kMaxLayers] = {};   // [128 x 192] (176 inputs used)
   const uint8_t* lat1[kMaxLayers] = {};
-  const uint8_t* mix[kMaxLayers][3] = {}; // [16 x 64] (C P_l inputs used)
+  const uint8_t* mix[kMaxLayers][3] = {}; // [16 x 64] (C P_l inputs used), l <= l_max
   // split mode: tb0 holds [W_hi | W_hi | W_lo] in columns 0, 16, 32; lo images
   // of twobody.1 and energy.0
   const uint8_t* tb1_lo = nullptr;
@@ -115,6 +115,7 @@ struct BfW {
   float sigma[2];
   float rc;
   int n_layers;
+  int lmax;
 };
 
 bool bf16_supported(int lmax, int C, int D, int E, int L);

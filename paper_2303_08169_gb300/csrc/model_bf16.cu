@@ -1,5 +1,6 @@
 // model_bf16.cu - BF16 tensor-core pair passes (tcgen05.mma, FP32 accumulation
-// in TMEM) for the 2-layer, l_max 2, 16-channel, latent-128, energy-32 model.
+// in TMEM) for the 16-channel, latent-128, energy-32 model with two or more
+// layers at l_max 0, 1 or 2 (every kernel is instantiated per l_max).
 //
 // Same model and same pass order as the FP32 path (model_fp32.cu): forward
 // passes, a fused last-layer forward + adjoint, then the adjoint passes
@@ -11,8 +12,8 @@
 //    128-byte-swizzled shared memory and FP32 accumulators in TMEM; the
 //    adjoint GEMMs read the forward weight images as MN-major operands;
 //  * pre-activations stay in TMEM between a GEMM and its adjoint;
-//  * channel mixing is 9 MMAs, one per output component (l3, m), over
-//    K-slices of one tile holding the tensor-product outputs;
+//  * channel mixing is (l_max + 1)^2 MMAs, one per output component (l3, m),
+//    over K-slices of one tile holding the tensor-product outputs;
 //  * the forward layer-k pass is split in two (TP + mixing; latent MLP) so
 //    that the weights of every kernel stay resident in shared memory; its
 //    adjoint is one kernel (no per-atom sum lies between its two halves);
@@ -22,6 +23,7 @@
 // between passes, dV in the operand type, the other gradients in FP32.
 // Per-atom sums use the per-(tile, atom) partials of the FP32 path with
 // 128-pair tiles, reduced per atom once per producing pass.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -47,28 +49,76 @@ constexpr int kT = 128;
 // threads of a CTA: thread t owns tile row r = t % 128 (its TMEM lane) and
 // column quarter h = t / 128 of every epilogue (16 warps per SM)
 constexpr int kThr4 = 512;
-constexpr int D = 128, C = 16, E = 32, NLM = 9, NS = 3, KH = 176, NW0 = 48, CL = 144, NB = 8;
+constexpr int D = 128, C = 16, E = 32, NB = 8;
 constexpr float kR2 = 0.70710678118654752f;
 // odd row strides of per-row shared arrays (32 consecutive rows hit 32 banks)
-constexpr int CLP = CL + 1, EP = C + 1, GP = 9;
+constexpr int EP = C + 1, GP = 9;
+
+__host__ __device__ constexpr int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
+
+// Shapes of the passes at l_max = LM: NLM spherical components, NS = P_0
+// scalar paths per channel, CL = C NLM features of V^k and Gamma, KH = D + C NS
+// inputs of the first latent layer, NW0 = C (LM + 1) embedding outputs, NT
+// tensor-product outputs per channel (the tables generated by gen_tp.cpp:
+// path-major within each output order l, offset toff(l), P(l) paths).  The
+// mixing operand holds output component j's K-slice (C P_l columns, channel
+// c's paths at c P_l + p) from column slice(j).
+template <int LM>
+struct Tc {
+  static_assert(LM >= 0 && LM <= 2, "l_max 0, 1 or 2");
+  static constexpr int NLM = (LM + 1) * (LM + 1), NS = LM + 1, CL = C * NLM, KH = D + C * NS, NW0 = C * (LM + 1);
+  static constexpr int NT = LM == 0 ? TP0_NT : LM == 1 ? TP1_NT : TP2_NT;
+  static constexpr int CLP = CL + 1;                 // odd stride of per-row dGamma staging
+  __host__ __device__ static constexpr int P(int l) { return LM == 0 ? tp0_P(l) : LM == 1 ? tp1_P(l) : tp2_P(l); }
+  __host__ __device__ static constexpr int toff(int l) {
+    return LM == 0 ? tp0_toff(l) : LM == 1 ? tp1_toff(l) : tp2_toff(l);
+  }
+  __host__ __device__ static constexpr int slice(int j) {
+    int s = 0;
+    for (int q = 0; q < j; ++q) s += C * P(l_of(q));
+    return s;
+  }
+  template <class S>
+  static AL_DEV void fwd(const S* V, const S* G, S* T) {
+    if constexpr (LM == 0) tp0_fwd(V, G, T);
+    else if constexpr (LM == 1) tp1_fwd(V, G, T);
+    else tp2_fwd(V, G, T);
+  }
+  template <class S>
+  static AL_DEV void fwd_scalar(const S* V, const S* G, S* T) {
+    if constexpr (LM == 0) tp0_fwd_scalar(V, G, T);
+    else if constexpr (LM == 1) tp1_fwd_scalar(V, G, T);
+    else tp2_fwd_scalar(V, G, T);
+  }
+  template <class S>
+  static AL_DEV void bwd(const S* V, const S* G, const S* dT, S* dV, S* dG) {
+    if constexpr (LM == 0) tp0_bwd(V, G, dT, dV, dG);
+    else if constexpr (LM == 1) tp1_bwd(V, G, dT, dV, dG);
+    else tp2_bwd(V, G, dT, dV, dG);
+  }
+  template <class S>
+  static AL_DEV void bwd_scalar(const S* V, const S* G, const S* dT, S* dV, S* dG) {
+    if constexpr (LM == 0) tp0_bwd_scalar(V, G, dT, dV, dG);
+    else if constexpr (LM == 1) tp1_bwd_scalar(V, G, dT, dV, dG);
+    else tp2_bwd_scalar(V, G, dT, dV, dG);
+  }
+  static constexpr uint32_t kImgEmb = sw128_bytes(NW0, 128);
+  static constexpr uint32_t kOpT = sw128_bytes(128, (C * NT + 63) / 64 * 64);
+};
+static_assert(Tc<2>::slice(1) == 48 && Tc<2>::slice(4) == 240 && Tc<2>::slice(9) == C * TP2_NT, "l_max 2 slices");
+static_assert(Tc<1>::slice(1) == 32 && Tc<1>::slice(4) == C * TP1_NT && Tc<0>::slice(1) == C * TP0_NT,
+              "l_max 0 / 1 slices");
 
 constexpr uint32_t kImgTb0 = sw128_bytes(128, 64);
 constexpr uint32_t kImgTb1 = sw128_bytes(128, 128);
-constexpr uint32_t kImgEmb = sw128_bytes(48, 128);
 constexpr uint32_t kImgE0 = sw128_bytes(32, 128);
 constexpr uint32_t kImgEnv = sw128_bytes(16, 128);
-constexpr uint32_t kImgLat0 = sw128_bytes(128, 192);
+constexpr uint32_t kImgLat0 = sw128_bytes(128, 192);   // KH <= 176 inputs used
 constexpr uint32_t kImgLat1 = sw128_bytes(128, 128);
-constexpr uint32_t kImgMix = sw128_bytes(16, 64);
+constexpr uint32_t kImgMix = sw128_bytes(16, 64);      // C P_l <= 64 inputs used
 constexpr uint32_t kOp128 = sw128_bytes(128, 128);
 constexpr uint32_t kOp64 = sw128_bytes(128, 64);
 constexpr uint32_t kOpH = sw128_bytes(128, 192);
-constexpr uint32_t kOpT = sw128_bytes(128, 576);
-
-// mixing: output component j = l*l + m (0..8) reads the K-slice of the
-// tensor-product tile starting at column kSlice[j] (width C P_l)
-__device__ __constant__ int kSlice[9] = {0, 48, 112, 176, 240, 304, 368, 432, 496};
-AL_DEV int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
 
 // Operand type of the tensor-core GEMMs: BF16 (the precision the method
 // names for per-pair GEMMs) or FP16 (same tensor-core rate, 3 more mantissa
@@ -295,6 +345,7 @@ AL_DEV void seg_store_cols(float* __restrict__ part, const Meta& m, int W, int x
 // consumers copy the rows of the tile's first kSegCap centre atoms into
 // shared memory, and rows of later segments read gsum directly.
 constexpr int kSegCap = 8;
+template <int CL>
 AL_DEV void stage_g(const float* __restrict__ gsum, const Meta& m, float* s) {
   const int ns = min(m.nseg, kSegCap);
   for (int idx = threadIdx.x; idx < ns * (CL / 4); idx += blockDim.x) {
@@ -302,7 +353,9 @@ AL_DEV void stage_g(const float* __restrict__ gsum, const Meta& m, float* s) {
     reinterpret_cast<float4*>(s + sg * CL)[x] = reinterpret_cast<const float4*>(gsum + (size_t)m.atom[sg] * CL)[x];
   }
 }
+template <int NLM>
 AL_DEV void get_g(const float* s, const float* __restrict__ gsum, const Meta& m, int r, bool valid, int c, float* G) {
+  constexpr int CL = C * NLM;
   if (!valid) {
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) G[lm] = 0.0f;
@@ -316,6 +369,7 @@ AL_DEV void get_g(const float* s, const float* __restrict__ gsum, const Meta& m,
 
 // gsum[i][x] = sum over the tiles t0..t1 that hold atom i's pairs of the
 // partial row (t + i), in tile order (zero for an atom without pairs)
+template <int CL>
 __global__ void k_atom_sums(const float* __restrict__ part, const int* __restrict__ row_ptr, int n,
                             const int* __restrict__ flags, float* __restrict__ gsum) {
   if (*flags & 1) return;
@@ -338,6 +392,7 @@ __global__ void k_atom_sums(const float* __restrict__ part, const int* __restric
   }
 }
 
+template <int LM>
 AL_DEV void geo_from_delta(float dx, float dy, float dz, float rc, float u[3], float& d, float& fc, float& dfc,
                            float* Y) {
   d = sqrtf(dx * dx + dy * dy + dz * dz);
@@ -346,12 +401,13 @@ AL_DEV void geo_from_delta(float dx, float dy, float dz, float rc, float u[3], f
   u[1] = dy * inv;
   u[2] = dz * inv;
   envelope(d, rc, fc, dfc);
-  sph_harm<2>(u[0], u[1], u[2], Y);
+  sph_harm<LM>(u[0], u[1], u[2], Y);
 }
 
 // Pass A: the pair separation in FP64 (the arithmetic that decides pair
 // membership), rounded to FP32 and kept per pair (tile-SoA, 3 floats) for the
 // later passes, which read it instead of gathering two FP64 positions.
+template <int LM>
 AL_DEV void geometry_first(const PassBufs& b, int tile, int r, float rc, int i, int j, int code, float u[3],
                            float& d, float& fc, float& dfc, float* Y) {
   Box box{{b.L[0], b.L[1], b.L[2]}};
@@ -361,12 +417,13 @@ AL_DEV void geometry_first(const PassBufs& b, int tile, int r, float rc, int i, 
   b.dR[sidx(tile, 3, 0, r)] = dx;
   b.dR[sidx(tile, 3, 1, r)] = dy;
   b.dR[sidx(tile, 3, 2, r)] = dz;
-  geo_from_delta(dx, dy, dz, rc, u, d, fc, dfc, Y);
+  geo_from_delta<LM>(dx, dy, dz, rc, u, d, fc, dfc, Y);
 }
+template <int LM>
 AL_DEV void geometry(const PassBufs& b, int tile, int r, float rc, float u[3], float& d, float& fc, float& dfc,
                      float* Y) {
-  geo_from_delta(b.dR[sidx(tile, 3, 0, r)], b.dR[sidx(tile, 3, 1, r)], b.dR[sidx(tile, 3, 2, r)], rc, u, d, fc, dfc,
-                 Y);
+  geo_from_delta<LM>(b.dR[sidx(tile, 3, 0, r)], b.dR[sidx(tile, 3, 1, r)], b.dR[sidx(tile, 3, 2, r)], rc, u, d, fc,
+                     dfc, Y);
 }
 
 // ---- MMA issue helpers (single thread) ----
@@ -648,8 +705,9 @@ AL_DEV void mma_split(uint32_t d, const uint8_t* A, const uint8_t* Alo, const ui
 // Split mode: the two-body MLP GEMMs take split operands.  The first one packs
 // [h_hi | h_lo | h_hi] against the image [W_hi | W_hi | W_lo] along K (12
 // inputs fit a 16-column K-step), the second adds the lo MMAs.
-template <class Tin, bool kSplit>
+template <class Tin, bool kSplit, int LM>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
+  constexpr int NLM = Tc<LM>::NLM, CL = Tc<LM>::CL;
   BF_PROLOGUE(kImgTb0 + (kSplit ? 2 : 1) * kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
     bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
@@ -683,7 +741,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
       if (r < m.np) {
         float u[3], d, dfc, B[NB];
-        geometry_first(b, tile, r, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
+        geometry_first<LM>(b, tile, r, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
         bessel<NB>(d, w.rc, B, nullptr);
         const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
 #pragma unroll
@@ -735,17 +793,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
 // ============================================================================
 // Pass B1_k: tensor product of layer k and channel mixing -> V^k, scalars S^k.
 // 512 threads: thread (r, h) owns tile row r and channels 4h..4h+3.
-template <class Tin>
+template <class Tin, int LM>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
-  BF_PROLOGUE(kImgEmb + 3 * kImgMix, {
-    bulk_g2s(sm, w.emb, kImgEmb, &bars[1]);
-    for (int l = 0; l < 3; ++l) bulk_g2s(sm + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
+  using Cf = Tc<LM>;
+  constexpr int NLM = Cf::NLM, NS = Cf::NS, CL = Cf::CL, NW0 = Cf::NW0, NL = LM + 1;
+  BF_PROLOGUE(Cf::kImgEmb + NL * kImgMix, {
+    bulk_g2s(sm, w.emb, Cf::kImgEmb, &bars[1]);
+    for (int l = 0; l < NL; ++l) bulk_g2s(sm + Cf::kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
   })
   uint8_t* Wemb = sm;
-  uint8_t* Wmix = Wemb + kImgEmb;
-  uint8_t* X = Wmix + 3 * kImgMix;
+  uint8_t* Wmix = Wemb + Cf::kImgEmb;
+  uint8_t* X = Wmix + NL * kImgMix;
   uint8_t* T = X + kOp128;
-  float* s_Y = reinterpret_cast<float*>(T + kOpT);
+  float* s_Y = reinterpret_cast<float*>(T + Cf::kOpT);
   float* s_g = s_Y + kT * NLM;            // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   uint32_t xw[16];                                    // x^0 operand words (k = 1), one tile ahead
@@ -765,33 +825,33 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       float u[3], d, fc, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (r < m.np) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
+      if (r < m.np) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
     if (k == 1) {
       st_row<Tin, 32>(X, r, 32 * h, xw);
-      stage_g(b.gsum[k], m, s_g);
-      mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, 48, 8, false, 0); });
+      stage_g<CL>(b.gsum[k], m, s_g);
+      mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, NW0, 8, false, 0); });
     } else {
-      stage_g(b.gsum[k], m, s_g);
+      stage_g<CL>(b.gsum[k], m, s_g);
       __syncthreads();
     }
-    float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc * 3 + l]
-    if (k == 1) tmem_ld16(lanes(tmem) + 12 * h, w0);
-    // channel pairs: for l3 >= 1 the P_l = 4 paths of channels c, c + 1 fill
-    // one 16-byte chunk of a mixing K-slice; the l3 = 0 slice (P_0 = 3) is
-    // written per element
+    float w0[16];                                     // w0 of channels 4h..4h+3: w0[cc NL + l]
+    if (k == 1) tmem_ld16(lanes(tmem) + 4 * NL * h, w0);
+    // channel pairs: for l3 >= 1 the P_l paths of channels c, c + 1 fill
+    // 2 P_l consecutive columns of a mixing K-slice (one 16-byte chunk at
+    // P_l = 4, 8 bytes at P_l = 2); the l3 = 0 slice is written per element
 #pragma unroll
     for (int cc = 0; cc < 4; cc += 2) {
-      float Tv[2][TP2_NT];
+      float Tv[2][Cf::NT];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int c = 4 * h + cc + e;
         float V[NLM], G[NLM];
         if (k == 1) {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[(cc + e) * 3 + l_of(lm)] * s_Y[r * NLM + lm];
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[(cc + e) * NL + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
@@ -799,37 +859,44 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
             V[lm] = (c & 1) ? t.y : t.x;
           }
         }
-        get_g(s_g, b.gsum[k], m, r, valid, c, G);
-        tp2_fwd(V, G, Tv[e]);
+        get_g<NLM>(s_g, b.gsum[k], m, r, valid, c, G);
+        Cf::fwd(V, G, Tv[e]);
 #pragma unroll
         for (int q = 0; q < NS; ++q) st1<Tin>(T, r, c * NS + q, Tv[e][q]);
       }
-      if (valid) {                                    // S of channels c0, c0 + 1: features 3 c0 .. 3 c0 + 5
+      if (valid) {                                    // S of channels c0, c0 + 1: features NS c0 .. NS c0 + 2 NS - 1
         const int f0 = (4 * h + cc) * NS;
-        sth2(b.S[k], hidx(tile, C * NS, f0, r), Tv[0][0], Tv[0][1]);
-        sth2(b.S[k], hidx(tile, C * NS, f0 + 2, r), Tv[0][2], Tv[1][0]);
-        sth2(b.S[k], hidx(tile, C * NS, f0 + 4, r), Tv[1][1], Tv[1][2]);
+        float s2[2 * NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          s2[q] = Tv[0][q];
+          s2[NS + q] = Tv[1][q];
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * NS; q += 2) sth2(b.S[k], hidx(tile, C * NS, f0 + q, r), s2[q], s2[q + 1]);
       }
       const int c0 = 4 * h + cc;
 #pragma unroll
-      for (int j = 1; j < 9; ++j) {
-        const int l3 = l_of(j), mm3 = j - l3 * l3, nm = 2 * l3 + 1;
+      for (int j = 1; j < NLM; ++j) {
+        const int l3 = l_of(j), mm3 = j - l3 * l3, nm = 2 * l3 + 1, pl = Cf::P(l3);
         float v8[8];
 #pragma unroll
         for (int e = 0; e < 2; ++e)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v8[4 * e + q] = Tv[e][tp2_toff(l3) + q * nm + mm3];
-        st8<Tin>(T, sw128_off(r, kSlice[j] + c0 * 4, 128), v8);
+          for (int q = 0; q < 4; ++q)
+            if (q < pl) v8[pl * e + q] = Tv[e][Cf::toff(l3) + q * nm + mm3];
+        if (pl == 4) st8<Tin>(T, sw128_off(r, Cf::slice(j) + c0 * 4, 128), v8);
+        else st4<Tin>(T, sw128_off(r, Cf::slice(j) + c0 * pl, 128), v8);
       }
     }
     mm.run([&] {
-      // K-step-major over the nine products: consecutive MMAs write different
+      // K-step-major over the NLM products: consecutive MMAs write different
       // accumulators, so none waits for the one before it
       for (int kk = 0; kk < 4; ++kk)
-        for (int j = 0; j < 9; ++j) {
+        for (int j = 0; j < NLM; ++j) {
           const int l3 = l_of(j);
-          if (kk < C * tp2_P(l3) / 16)
-            mma_k<Tin>(tmem + 64 + 16 * j, T, kSlice[j] / 16 + kk, Wmix + l3 * kImgMix + 32 * kk, 16, 1, false, 0,
+          if (kk < C * Cf::P(l3) / 16)
+            mma_k<Tin>(tmem + 64 + 16 * j, T, Cf::slice(j) / 16 + kk, Wmix + l3 * kImgMix + 32 * kk, 16, 1, false, 0,
                        kk > 0);
         }
     });
@@ -840,7 +907,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     {
       const uint32_t base = lanes(tmem);
-      for (int j = h; j < 9; j += 4) {                // components h, h + 4, h + 8
+      for (int j = h; j < NLM; j += 4) {              // components h, h + 4, h + 8
         float v[16];
         tmem_ld16(base + 64 + 16 * j, v);
         if (valid)
@@ -856,8 +923,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
 // ============================================================================
 // Pass B2_k: latent MLP of layer k (x^k) and env of layer k+1 -> Gamma^{k+1}.
 // 512 threads: column quarters for every epilogue.
-template <class Tin>
+template <class Tin, int LM>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
+  constexpr int NLM = Tc<LM>::NLM, NS = Tc<LM>::NS, CL = Tc<LM>::CL, KH = Tc<LM>::KH;
   BF_PROLOGUE(kImgLat0 + kImgLat1 + kImgEnv, {
     bulk_g2s(sm, w.lat0[k - 1], kImgLat0, &bars[1]);
     bulk_g2s(sm + kImgLat0, w.lat1[k - 1], kImgLat1, &bars[1]);
@@ -872,11 +940,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
-  uint32_t xw[16], sw[8];                             // [x^{k-1}, S^k] operand words, one tile ahead
+  // [x^{k-1}, S^k] operand words, one tile ahead: quarter h holds x^{k-1}
+  // columns 32h..32h+31 and, for 1 <= h <= NS, S^k columns 16(h-1)..
+  uint32_t xw[16], sw[8];
+  const bool has_s = h >= 1 && h <= NS;
   {
     const bool vt = r < min(kT, P - (int)blockIdx.x * kT);
     ld_row<32>(xw, b.X[k - 1], blockIdx.x, r, D, 32 * h, vt);
-    ld_row<16>(sw, b.S[k], blockIdx.x, r, C * NS, 16 * max(h - 1, 0), vt && h >= 1);
+    ld_row<16>(sw, b.S[k], blockIdx.x, r, C * NS, 16 * max(h - 1, 0), vt && has_s);
   }
   MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
@@ -894,19 +965,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
+      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
     st_row<Tin, 32>(HA, r, 32 * h, xw);
-    if (h >= 1) {
+    if (has_s) {
       st_row<Tin, 16>(HA, r, 128 + 16 * (h - 1), sw);
-    } else {
+    } else if (h == 0) {
       float z[16] = {};
-      st16<Tin>(HA, r, 176, z);
+      st16<Tin>(HA, r, KH, z);
     }
-    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, 11, false, 0); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, KH / 16, false, 0); });
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
 #pragma unroll
@@ -937,7 +1008,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       const int nt = tile + (int)gridDim.x;
       const bool vt = r < min(kT, P - nt * kT);
       ld_row<32>(xw, b.X[k - 1], nt, r, D, 32 * h, vt);
-      ld_row<16>(sw, b.S[k], nt, r, C * NS, 16 * max(h - 1, 0), vt && h >= 1);
+      ld_row<16>(sw, b.S[k], nt, r, C * NS, 16 * max(h - 1, 0), vt && has_s);
       mq = meta_load(b, nt, P);
     }
     if (threadIdx.x < kT) {
@@ -955,8 +1026,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 
 // V^{L-1} words of channel pairs (4h, 4h+1), (4h+2, 4h+3) and the x^{L-1}
 // operand words of pass C for tile t, thread (r, h) (zeros past the last tile)
+template <int NLM>
 AL_DEV void c_loads(const PassBufs& b, int L, int t, int P, int r, int h, __half2 (&vw)[2][NLM],
                     uint32_t (&xw)[16]) {
+  constexpr int CL = C * NLM;
   const bool vt = r < min(kT, P - t * kT);
 #pragma unroll
   for (int cp = 0; cp < 2; ++cp)
@@ -976,8 +1049,10 @@ AL_DEV void c_loads(const PassBufs& b, int L, int t, int P, int r, int h, __half
 // Split mode: the energy hidden layer takes split operands; the lo part of
 // x^L goes to A1 (free after the second latent MMA) and dz_E keeps its hi and
 // lo parts side by side in the 64 columns of AE.
-template <class Tin, bool kSplit>
+template <class Tin, bool kSplit, int LM>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
+  using Cf = Tc<LM>;
+  constexpr int NLM = Cf::NLM, NS = Cf::NS, CL = Cf::CL, KH = Cf::KH, CLP = Cf::CLP;
   const int L = w.n_layers;
   BF_PROLOGUE(kImgLat0 + kImgLat1 + (kSplit ? 2 : 1) * kImgE0, {
     bulk_g2s(sm, w.lat0[L - 1], kImgLat0, &bars[1]);
@@ -1018,21 +1093,21 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     const float* xg = b.X[L - 1];
     if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
-      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
+      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
       s_sig[r] = valid ? w.sigma[mq.zi] : 0.0f;
     }
-    stage_g(b.gsum[L], m, s_g);
+    stage_g<CL>(b.gsum[L], m, s_g);
     // z1 = [x^{L-1}, S] W_0: the x^{L-1} K-steps run while the tensor product
     // computes S
     st_row<Tin, 32>(HA, r, 32 * h, xw);
     if (h == 3) {
       float z[16] = {};
-      st16<Tin>(HA, r, 176, z);
+      st16<Tin>(HA, r, KH, z);
     }
     mm.issue([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, 8, false, 0); });
     {
-      float S[4 * NS];                                 // columns D + 12 h .. D + 12 h + 11
+      float S[4 * NS];                                 // columns D + 4 NS h .. D + 4 NS (h + 1) - 1
 #pragma unroll
       for (int cp = 0; cp < 4; cp += 2) {             // channel pairs share the V words
         float V2[2][NLM];
@@ -1045,14 +1120,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           float G[NLM];
-          get_g(s_g, b.gsum[L], m, r, valid, 4 * h + cp + e, G);
-          tp2_fwd_scalar(V2[e], G, S + (cp + e) * NS);
+          get_g<NLM>(s_g, b.gsum[L], m, r, valid, 4 * h + cp + e, G);
+          Cf::fwd_scalar(V2[e], G, S + (cp + e) * NS);
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 12 * h + q, S[q]);
+      for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 4 * NS * h + q, S[q]);
     }
-    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, 3, false, 0, true); });
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, NS, false, 0, true); });
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
@@ -1119,7 +1194,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 176, 8, true, 128); });      // [dx^{L-1}, ds]
+    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, KH, 8, true, 128); });       // [dx^{L-1}, ds]
 #pragma unroll
     for (int cp = 0; cp < 2; ++cp)                    // again, for the tensor-product adjoint
 #pragma unroll
@@ -1134,8 +1209,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
         for (int q = 0; q < 16; ++q) b.dX[sidx(tile, D, n0 + q, rr)] = dh[q] + dx[q] * kR2;
     });
     {
-      float ds[16];                                    // columns D + 12 h ..: ds of channels 4h..4h+3
-      tmem_ld16(lanes(tmem) + 128 + 12 * h, ds);
+      float ds[16];                                    // columns D + 4 NS h ..: ds of channels 4h..4h+3
+      tmem_ld16(lanes(tmem) + 128 + 4 * NS * h, ds);
       float dVe[NLM];                                  // dV of the even channel of a pair
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
@@ -1148,8 +1223,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
           dV[lm] = 0.0f;
           dG[lm] = 0.0f;
         }
-        get_g(s_g, b.gsum[L], m, r, valid, c, G);
-        tp2_bwd_scalar(V, G, ds + cc * NS, dV, dG);
+        get_g<NLM>(s_g, b.gsum[L], m, r, valid, c, G);
+        Cf::bwd_scalar(V, G, ds + cc * NS, dV, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLP + c * NLM + lm] = dG[lm];
         if (cc & 1) {
@@ -1200,30 +1275,53 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 // and at the end dw0 and the dy partials; A1 holds de, SiLU(z1), dz2 and
 // during the mixing-adjoint rounds the dGamma^k staging of eight channels.
 // TMEM columns: e [0, 16); z1 [32, 160); z2 and da1 [160, 288); dx [288,
-// 416); ds [416, 464); w0 [464, 512); in the rounds, the l3 = 0 component of
-// all channels [416, 464) and components j >= 1 of eight channels [0, 256).
+// 416); ds [416, 416 + C NS); w0 [464, 464 + NW0); in the rounds, the l3 = 0
+// component of all channels [416, 416 + C NS) and components j >= 1 from
+// column 32 (j - 1): at l_max 2 eight channels per round (32 columns each,
+// [0, 256)); below l_max 2 all channels in the first round (C P_l <= 32
+// columns each), which the second round reads again.
 // 512 threads: thread (r, h) owns tile row r, column quarter h of every
 // epilogue, channels 4h..4h+3 of the env adjoint and channels 8 hf + 2h + e
 // of mixing-adjoint round hf.
-constexpr int CLH = CL / 2 + 1;                     // odd stride of the half-round dGamma staging
-constexpr uint32_t kRegA1 = (4 * kT * CLH + 1023) / 1024 * 1024;
-static_assert(kRegA1 >= kOp128, "A1 region holds an operand tile");
-template <class Tin, bool kEmb>
+template <int LM>
+constexpr uint32_t reg_a1() {                        // A1 region: an operand tile or the round's dGamma staging
+  return std::max<uint32_t>(kOp128, (4 * kT * (Tc<LM>::CL / 2 + 1) + 1023) / 1024 * 1024);
+}
+// 2, 4 or 6 consecutive TMEM columns (no column past the N-th is read)
+template <int N>
+AL_DEV void tmem_ldn(uint32_t taddr, float* v) {
+  static_assert(N == 2 || N == 4 || N == 6, "2, 4 or 6 columns");
+  if constexpr (N == 6) {
+    tmem_ld6(taddr, v);
+  } else {
+    uint32_t t[4] = {0u, 0u, 0u, 0u};
+    if constexpr (N == 4) tmem_ld4_raw(taddr, t);
+    else tmem_ld2_raw(taddr, t);
+    tmem_wait4(t);
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = __uint_as_float(t[q]);
+  }
+}
+template <class Tin, bool kEmb, int LM>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
-  BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1 + kImgEmb + 3 * kImgMix, {
+  using Cf = Tc<LM>;
+  constexpr int NLM = Cf::NLM, NS = Cf::NS, CL = Cf::CL, KH = Cf::KH, NW0 = Cf::NW0, NL = LM + 1;
+  constexpr int CLH = CL / 2 + 1;                    // odd stride of the half-round dGamma staging
+  constexpr uint32_t kRegA1 = reg_a1<LM>();
+  BF_PROLOGUE(kImgEnv + kImgLat0 + kImgLat1 + Cf::kImgEmb + NL * kImgMix, {
     bulk_g2s(sm, w.env[k], kImgEnv, &bars[1]);
     bulk_g2s(sm + kImgEnv, w.lat0[k - 1], kImgLat0, &bars[1]);
     bulk_g2s(sm + kImgEnv + kImgLat0, w.lat1[k - 1], kImgLat1, &bars[1]);
-    bulk_g2s(sm + kImgEnv + kImgLat0 + kImgLat1, w.emb, kImgEmb, &bars[1]);
-    for (int l = 0; l < 3; ++l)
-      bulk_g2s(sm + kImgEnv + kImgLat0 + kImgLat1 + kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
+    bulk_g2s(sm + kImgEnv + kImgLat0 + kImgLat1, w.emb, Cf::kImgEmb, &bars[1]);
+    for (int l = 0; l < NL; ++l)
+      bulk_g2s(sm + kImgEnv + kImgLat0 + kImgLat1 + Cf::kImgEmb + l * kImgMix, w.mix[k - 1][l], kImgMix, &bars[1]);
   })
   uint8_t* Wenv = sm;
   uint8_t* Wl0 = Wenv + kImgEnv;
   uint8_t* Wl1 = Wl0 + kImgLat0;
   uint8_t* Wemb = Wl1 + kImgLat1;
-  uint8_t* Wmix = Wemb + kImgEmb;
-  uint8_t* HA = Wmix + 3 * kImgMix;
+  uint8_t* Wmix = Wemb + Cf::kImgEmb;
+  uint8_t* HA = Wmix + NL * kImgMix;
   uint8_t* A1 = HA + kOpH;
   uint8_t* DE = A1;
   uint8_t* DVT = HA;
@@ -1270,16 +1368,17 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
+      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
     st_row<Tin, 32>(HA, r, 32 * h, xw);
-    stage_g(b.dgsum[k + 1], m, s_g);
+    stage_g<CL>(b.dgsum[k + 1], m, s_g);
     uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env MMA
+    const bool has_s = h >= 1 && h <= NS;             // quarters 1..NS hold S^k columns 16 (h - 1)..
     ld_row<32>(xw2, b.X[k - 1], tile, r, D, 32 * h, valid);
-    ld_row<16>(sw, b.S[k], tile, r, C * NS, 16 * max(h - 1, 0), valid && h >= 1);
+    ld_row<16>(sw, b.S[k], tile, r, C * NS, 16 * max(h - 1, 0), valid && has_s);
     mm.run([&] { mma_k<Tin>(tmem + kE, HA, 0, Wenv, 16, 8, false, 0); });       // e^{k+1}
     float dy[NLM];                                    // dY of this thread's channels (env and embedding)
     {
@@ -1291,7 +1390,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
         float dG[NLM];
-        get_g(s_g, b.dgsum[k + 1], m, r, valid, c, dG);
+        get_g<NLM>(s_g, b.dgsum[k + 1], m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -1302,19 +1401,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       }
     }
     st_row<Tin, 32>(HA, r, 32 * h, xw2);
-    if (h >= 1) {
+    if (has_s) {
       st_row<Tin, 16>(HA, r, 128 + 16 * (h - 1), sw);
-    } else {
+    } else if (h == 0) {
       float z[16] = {};
-      st16<Tin>(HA, r, 176, z);
+      st16<Tin>(HA, r, KH, z);
     }
     float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
 #pragma unroll
     for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
     mm.run([&] {
       mma_k<Tin>(tmem + kDX, DE, 0, Wenv, 128, 1, true, 16);                    // env^T de
-      mma_k<Tin>(tmem + kZ1, HA, 0, Wl0, 128, 11, false, 0);                    // z1
-      if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, 48, 8, false, 0);           // w0 = emb x^0
+      mma_k<Tin>(tmem + kZ1, HA, 0, Wl0, 128, KH / 16, false, 0);               // z1
+      if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, NW0, 8, false, 0);          // w0 = emb x^0
     });
     epi_silu_keep_grad(tmem, kZ1, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.run([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, false, 0); });     // z2
@@ -1339,9 +1438,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
         st16<Tin>(A1, r, 32 * h + 16 * hf, o);
       }
       tmem_st32(lanes(tmem) + kDX + 32 * h, dx);
-      const float z[4] = {0.f, 0.f, 0.f, 0.f};       // ds columns start from zero (exactly its 48)
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};       // ds columns start from zero (exactly its C NS)
 #pragma unroll
-      for (int q = 0; q < 12; q += 4) tmem_st4(lanes(tmem) + kDS + 12 * h + q, z);
+      for (int q = 0; q < 4 * NS; q += 4) tmem_st4(lanes(tmem) + kDS + 4 * NS * h + q, z);
       tmem_wait_st();
       s_du[h * kT + r] = du * kR2;
     }
@@ -1353,55 +1452,67 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + kDX, HA, 0, Wl0, 176, 8, true, 128, true); });  // [dx, ds] += dz1 W
+    mm.run([&] { mma_k<Tin>(tmem + kDX, HA, 0, Wl0, KH, 8, true, 128, true); });   // [dx, ds] += dz1 W
     // ---- mixing and tensor-product adjoint of layer k ----
-    // ds and w0 of this thread's round channels (8 hf + 2h + e): 3 columns each
-    float dsv[2][6], w0[2][6];
+    // ds and w0 of this thread's round channels (8 hf + 2h + e): NS and
+    // LM + 1 columns each
+    float dsv[2][2 * NS], w0[2][2 * NL];
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
-      tmem_ld6(lanes(tmem) + kDS + 3 * (8 * hf + 2 * h), dsv[hf]);
-      if (kEmb) tmem_ld6(lanes(tmem) + kW0 + 3 * (8 * hf + 2 * h), w0[hf]);
+      tmem_ldn<2 * NS>(lanes(tmem) + kDS + NS * (8 * hf + 2 * h), dsv[hf]);
+      if (kEmb) tmem_ldn<2 * NL>(lanes(tmem) + kW0 + NL * (8 * hf + 2 * h), w0[hf]);
     }
     // column 16 lm + c of the operand: this thread's 4 channels of one lm
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
       *reinterpret_cast<uint2*>(DVT + sw128_off(r, 16 * lm + 4 * h, 128)) = make_uint2(dvw[lm][0], dvw[lm][1]);
-    stage_g(b.gsum[k], m, s_g);
-    float dw[2][6];
+    stage_g<CL>(b.gsum[k], m, s_g);
+    float dw[2][2 * NL];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) dw[0][q] = dw[1][q] = 0.0f;
+    for (int q = 0; q < 2 * NL; ++q) dw[0][q] = dw[1][q] = 0.0f;
     float dVe[NLM];                                   // k >= 2: dV^{k-1} of the even channel of a pair
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
-      mm.run([&] {
-        if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, 48, 1, true, 16);
-        for (int j = 1; j < 9; ++j)
-          mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l_of(j) * kImgMix + 64 * hf, 32, 1, true, 16);
-      });
+      if (hf == 0 || LM == 2) {
+        mm.run([&] {
+          if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, C * NS, 1, true, 16);
+          for (int j = 1; j < NLM; ++j) {
+            const int l3 = l_of(j);
+            if (LM == 2)                              // this round's eight channels
+              mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l3 * kImgMix + 64 * hf, C * Cf::P(l3) / 2, 1, true,
+                         16);
+            else
+              mma_k<Tin>(tmem + kJ + 32 * (j - 1), DVT, j, Wmix + l3 * kImgMix, C * Cf::P(l3), 1, true, 16);
+          }
+        });
+      } else {
+        __syncthreads();                              // the first round's staging has been stored
+      }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int c = 8 * hf + 2 * h + e;
-        uint32_t t[36];
-        tmem_ld4_raw(lanes(tmem) + kJ0 + 3 * c, t);                         // l3 = 0: columns 3c + q
+        const int cr = LM == 2 ? 2 * h + e : c;       // channel within a component's TMEM block
+        uint32_t t[4 * NLM];
+        tmem_ld4_raw(lanes(tmem) + kJ0 + NS * c, t);                        // l3 = 0: columns NS c + q
 #pragma unroll
-        for (int j = 1; j < 9; ++j) tmem_ld4_raw(lanes(tmem) + kJ + 32 * (j - 1) + 4 * (2 * h + e), t + 4 * j);
+        for (int j = 1; j < NLM; ++j)
+          tmem_ld4_raw(lanes(tmem) + kJ + 32 * (j - 1) + Cf::P(l_of(j)) * cr, t + 4 * j);
 #pragma unroll
-        for (int g = 0; g < 9; ++g) tmem_wait4(t + 4 * g);
-        float dT[TP2_NT];
+        for (int g = 0; g < NLM; ++g) tmem_wait4(t + 4 * g);
+        float dT[Cf::NT];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) dT[q] = __uint_as_float(t[q]) + dsv[hf][3 * e + q];
+        for (int q = 0; q < NS; ++q) dT[q] = __uint_as_float(t[q]) + dsv[hf][NS * e + q];
 #pragma unroll
-        for (int mm1 = 0; mm1 < 3; ++mm1)
+        for (int j = 1; j < NLM; ++j) {
+          const int l3 = l_of(j), mm3 = j - l3 * l3, nm = 2 * l3 + 1;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) dT[3 + q * 3 + mm1] = __uint_as_float(t[4 + 4 * mm1 + q]);
-#pragma unroll
-        for (int mm2 = 0; mm2 < 5; ++mm2)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) dT[15 + q * 5 + mm2] = __uint_as_float(t[16 + 4 * mm2 + q]);
+          for (int q = 0; q < 4; ++q)
+            if (q < Cf::P(l3)) dT[Cf::toff(l3) + q * nm + mm3] = __uint_as_float(t[4 * j + q]);
+        }
         float V[NLM], G[NLM], dG[NLM], dVp[NLM];
         if (kEmb) {
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[hf][3 * e + l_of(lm)] * s_Y[r * NLM + lm];
+          for (int lm = 0; lm < NLM; ++lm) V[lm] = w0[hf][NL * e + l_of(lm)] * s_Y[r * NLM + lm];
         } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
@@ -1409,10 +1520,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
             V[lm] = e ? v2.y : v2.x;
           }
         }
-        get_g(s_g, b.gsum[k], m, r, valid, c, G);
+        get_g<NLM>(s_g, b.gsum[k], m, r, valid, c, G);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) dG[lm] = dVp[lm] = 0.0f;
-        tp2_bwd(V, G, dT, dVp, dG);
+        Cf::bwd(V, G, dT, dVp, dG);
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) s_dg[r * CLH + (c - 8 * hf) * NLM + lm] = dG[lm];
         if (!kEmb) {                                  // dV^{k-1}: channel pairs (8 hf + 2h, + 1)
@@ -1426,20 +1537,20 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
         } else {
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm) {
-            dw[hf][3 * e + l_of(lm)] = fmaf(dVp[lm], s_Y[r * NLM + lm], dw[hf][3 * e + l_of(lm)]);
-            dy[lm] = fmaf(w0[hf][3 * e + l_of(lm)], dVp[lm], dy[lm]);
+            dw[hf][NL * e + l_of(lm)] = fmaf(dVp[lm], s_Y[r * NLM + lm], dw[hf][NL * e + l_of(lm)]);
+            dy[lm] = fmaf(w0[hf][NL * e + l_of(lm)], dVp[lm], dy[lm]);
           }
         }
       }
       __syncthreads();
-      seg_store_cols(b.dgam[k], m, CL, 72 * hf, 72, [&](int p, int x) { return s_dg[p * CLH + x]; });
+      seg_store_cols(b.dgam[k], m, CL, (CL / 2) * hf, CL / 2, [&](int p, int x) { return s_dg[p * CLH + x]; });
     }
     if (kEmb) {                                       // the DVT operand is dead: dw0 takes its place
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) st1<Tin>(DW0, r, 3 * (8 * hf + 2 * h) + q, dw[hf][q]);
-      mm.run([&] { mma_k<Tin>(tmem + kDX, DW0, 0, Wemb, 128, 3, true, 48, true); });   // dx += emb^T dw0
+        for (int q = 0; q < 2 * NL; ++q) st1<Tin>(DW0, r, NL * (8 * hf + 2 * h) + q, dw[hf][q]);
+      mm.run([&] { mma_k<Tin>(tmem + kDX, DW0, 0, Wemb, 128, NL, true, NW0, true); });   // dx += emb^T dw0
     } else {
       __syncthreads();
     }
@@ -1482,8 +1593,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
 // packed image [W_hi | W_hi | W_lo] (48 columns): dh0 = block 0 + block 2.
 // 512 threads: column quarters for every epilogue; the env adjoint's
 // channels are spread over the quarters.
-template <class Tin, bool kSplit>
+template <class Tin, bool kSplit, int LM>
 __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
+  constexpr int NLM = Tc<LM>::NLM, CL = Tc<LM>::CL;
   BF_PROLOGUE(kImgTb0 + (kSplit ? 2 : 1) * kImgTb1 + kImgEnv, {
     bulk_g2s(sm, w.tb0, kImgTb0, &bars[1]);
     bulk_g2s(sm + kImgTb0, w.tb1, kImgTb1, &bars[1]);
@@ -1526,7 +1638,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       float Y[NLM], u[3] = {0.f, 0.f, 0.f}, d = 1.0f, fc = 0.0f, dfc = 0.0f;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry(b, tile, r, w.rc, u, d, fc, dfc, Y);
+      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
       float* g = s_geo + r * GP;
       g[0] = u[0]; g[1] = u[1]; g[2] = u[2]; g[3] = d; g[4] = fc; g[5] = dfc;
 #pragma unroll
@@ -1553,7 +1665,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       for (int q = 0; q < NB; ++q) s_dB[r * GP + q] = dB[q];
       st_h0<Tin, kSplit>(H0, r, h0);
     }
-    stage_g(b.dgsum[1], m, s_g);
+    stage_g<CL>(b.dgsum[1], m, s_g);
     mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });   // z1
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o); });
     mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });   // z2
@@ -1574,7 +1686,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
         float dG[NLM];
-        get_g(s_g, b.dgsum[1], m, r, valid, c, dG);
+        get_g<NLM>(s_g, b.dgsum[1], m, r, valid, c, dG);
         float acc = 0.0f;
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) {
@@ -1653,7 +1765,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
 #pragma unroll
         for (int lm = 0; lm < NLM; ++lm) dY[lm] = s_dy[r * NLM + lm] + dyo[lm];
         float gu[3];
-        sph_harm_vjp<2>(u[0], u[1], u[2], dY, gu);
+        sph_harm_vjp<LM>(u[0], u[1], u[2], dY, gu);
         const float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
         const float inv = 1.0f / d;
 #pragma unroll
@@ -1666,43 +1778,55 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
 }
 
 // shared-memory bytes of each kernel (+1024 for the manual 1024-byte alignment)
-constexpr size_t sm_a(bool split) {
-  return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
-         4 * (kT + kT * NLM + kT * EP);
-}
-constexpr size_t kSmB1 = 1024 + kImgEmb + 3 * kImgMix + kOp128 + kOpT + 4 * (kT * NLM + kSegCap * CL);
-constexpr size_t kSmB2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * EP);
-constexpr size_t sm_c(bool split) {
-  return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 + 4 * (10 * kT + kSegCap * CL);
-}
-constexpr size_t kSmBT = 1024 + kImgEnv + kImgLat0 + kImgLat1 + kImgEmb + 3 * kImgMix + kOpH + kRegA1 +
-                         4 * (kT + kT * NLM + 4 * kT + kSegCap * CL);
-constexpr size_t sm_at(bool split) {
-  return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
-         4 * (2 * kT * GP + 2 * kT * NLM + 4 * kT + kSegCap * CL);
-}
-// 4 KB left for the static Meta, barriers and flags of every kernel
-constexpr size_t kSmLimit = 232448 - 4096;
-static_assert(sm_a(true) <= kSmLimit && kSmB1 <= kSmLimit && kSmB2 <= kSmLimit && sm_c(true) <= kSmLimit &&
-                  kSmBT <= kSmLimit && sm_at(true) <= kSmLimit,
-              "shared memory per kernel");
-static_assert(kOpH + kOp128 >= 4 * kT * CLP, "pass C reuses HA + A1 for the dGamma contributions");
-static_assert(kOp128 >= 4 * 4 * kT * NLM, "pass A^T keeps the dY partials in X");
+template <int LM>
+struct Smem {
+  static constexpr int NLM = Tc<LM>::NLM, CL = Tc<LM>::CL, NL = LM + 1;
+  static constexpr size_t a(bool split) {
+    return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
+           4 * (kT + kT * NLM + kT * EP);
+  }
+  static constexpr size_t b1 = 1024 + Tc<LM>::kImgEmb + NL * kImgMix + kOp128 + Tc<LM>::kOpT +
+                               4 * (kT * NLM + kSegCap * CL);
+  static constexpr size_t b2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * EP);
+  static constexpr size_t c(bool split) {
+    return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 +
+           4 * (10 * kT + kSegCap * CL);
+  }
+  static constexpr size_t bt = 1024 + kImgEnv + kImgLat0 + kImgLat1 + Tc<LM>::kImgEmb + NL * kImgMix + kOpH +
+                               reg_a1<LM>() + 4 * (kT + kT * NLM + 4 * kT + kSegCap * CL);
+  static constexpr size_t at(bool split) {
+    return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
+           4 * (2 * kT * GP + 2 * kT * NLM + 4 * kT + kSegCap * CL);
+  }
+  // 4 KB left for the static Meta, barriers and flags of every kernel
+  static constexpr size_t kLimit = 232448 - 4096;
+  static_assert(a(true) <= kLimit && b1 <= kLimit && b2 <= kLimit && c(true) <= kLimit && bt <= kLimit &&
+                    at(true) <= kLimit,
+                "shared memory per kernel");
+  static_assert(kOpH + kOp128 >= 4 * kT * Tc<LM>::CLP, "pass C reuses HA + A1 for the dGamma contributions");
+  static_assert(kOp128 >= 4 * 4 * kT * NLM, "pass A^T keeps the dY partials in X");
+  static_assert(kOpH >= kOp64 + 4 * 4 * kT * NLM, "pass B^T keeps the dY partials in HA after its first 64 columns");
+};
+template struct Smem<0>;
+template struct Smem<1>;
+template struct Smem<2>;
 
 int g_sms = 0;
 
-template <class Tin, bool kSplit>
+template <class Tin, bool kSplit, int LM>
 void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km) {
-  constexpr size_t kSmA = sm_a(kSplit), kSmC = sm_c(kSplit), kSmAT = sm_at(kSplit);
+  using Sm = Smem<LM>;
+  constexpr int CL = Tc<LM>::CL;
+  constexpr size_t kSmA = Sm::a(kSplit), kSmC = Sm::c(kSplit), kSmAT = Sm::at(kSplit);
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_bf_a<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
-    cudaFuncSetAttribute(k_bf_b1<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB1);
-    cudaFuncSetAttribute(k_bf_b2<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmB2);
-    cudaFuncSetAttribute(k_bf_c<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
-    cudaFuncSetAttribute(k_bf_bt<Tin, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBT);
-    cudaFuncSetAttribute(k_bf_bt<Tin, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBT);
-    cudaFuncSetAttribute(k_bf_at<Tin, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
+    cudaFuncSetAttribute(k_bf_a<Tin, kSplit, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmA);
+    cudaFuncSetAttribute(k_bf_b1<Tin, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::b1);
+    cudaFuncSetAttribute(k_bf_b2<Tin, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::b2);
+    cudaFuncSetAttribute(k_bf_c<Tin, kSplit, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmC);
+    cudaFuncSetAttribute(k_bf_bt<Tin, true, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::bt);
+    cudaFuncSetAttribute(k_bf_bt<Tin, false, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::bt);
+    cudaFuncSetAttribute(k_bf_at<Tin, kSplit, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmAT);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1719,36 +1843,45 @@ void run_tc(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     const int64_t items = (int64_t)b.n_atoms * (CL / 4);
     if (items == 0) return;
     const int blocks = (int)std::min<int64_t>((items + 255) / 256, (int64_t)(g_sms > 0 ? g_sms : 148) * 16);
-    k_atom_sums<<<blocks, 256, 0, s>>>(part, b.row_ptr, b.n_atoms, b.flags, gsum);
+    k_atom_sums<CL><<<blocks, 256, 0, s>>>(part, b.row_ptr, b.n_atoms, b.flags, gsum);
   };
   mark(kPhStart);
-  k_bf_a<Tin, kSplit><<<grid, kThr4, kSmA, s>>>(w, b);
+  k_bf_a<Tin, kSplit, LM><<<grid, kThr4, kSmA, s>>>(w, b);
   sums(b.gam[1], b.gsum[1]);
   mark(kPhA);
   for (int k = 1; k < L; ++k) {
-    k_bf_b1<Tin><<<grid, kThr4, kSmB1, s>>>(w, b, k);
+    k_bf_b1<Tin, LM><<<grid, kThr4, Sm::b1, s>>>(w, b, k);
     mark(kPhB);
-    k_bf_b2<Tin><<<grid, kThr4, kSmB2, s>>>(w, b, k);
+    k_bf_b2<Tin, LM><<<grid, kThr4, Sm::b2, s>>>(w, b, k);
     sums(b.gam[k + 1], b.gsum[k + 1]);
     mark(kPhB2);
   }
-  k_bf_c<Tin, kSplit><<<grid, kThr4, kSmC, s>>>(w, b);
+  k_bf_c<Tin, kSplit, LM><<<grid, kThr4, kSmC, s>>>(w, b);
   sums(b.dgam[L], b.dgsum[L]);
   mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
-    if (k == 1) k_bf_bt<Tin, true><<<grid, kThr4, kSmBT, s>>>(w, b, k);
-    else k_bf_bt<Tin, false><<<grid, kThr4, kSmBT, s>>>(w, b, k);
+    if (k == 1) k_bf_bt<Tin, true, LM><<<grid, kThr4, Sm::bt, s>>>(w, b, k);
+    else k_bf_bt<Tin, false, LM><<<grid, kThr4, Sm::bt, s>>>(w, b, k);
     sums(b.dgam[k], b.dgsum[k]);
     mark(kPhBT);
   }
-  k_bf_at<Tin, kSplit><<<grid, kThr4, kSmAT, s>>>(w, b);
+  k_bf_at<Tin, kSplit, LM><<<grid, kThr4, kSmAT, s>>>(w, b);
   mark(kPhAT);
+}
+
+template <int LM>
+void run_mode(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km, TcMode mode) {
+  switch (mode) {
+    case TcMode::kBf16: run_tc<__nv_bfloat16, false, LM>(w, b, capacity, s, km); break;
+    case TcMode::kFp16: run_tc<__half, false, LM>(w, b, capacity, s, km); break;
+    case TcMode::kFp16Split: run_tc<__half, true, LM>(w, b, capacity, s, km); break;
+  }
 }
 
 }  // namespace
 
 bool bf16_supported(int lmax, int C_, int D_, int E_, int L) {
-  return lmax == 2 && C_ == C && D_ == D && E_ == E && L >= 2 && L <= kMaxLayers;
+  return lmax >= 0 && lmax <= 2 && C_ == C && D_ == D && E_ == E && L >= 2 && L <= kMaxLayers;
 }
 
 int bf16_tile() { return kT; }
@@ -1770,10 +1903,10 @@ int bf16_inject_wait_timeout(int enable) {
 
 void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km,
                         TcMode mode) {
-  switch (mode) {
-    case TcMode::kBf16: run_tc<__nv_bfloat16, false>(w, b, capacity, s, km); break;
-    case TcMode::kFp16: run_tc<__half, false>(w, b, capacity, s, km); break;
-    case TcMode::kFp16Split: run_tc<__half, true>(w, b, capacity, s, km); break;
+  switch (w.lmax) {
+    case 0: run_mode<0>(w, b, capacity, s, km, mode); break;
+    case 1: run_mode<1>(w, b, capacity, s, km, mode); break;
+    default: run_mode<2>(w, b, capacity, s, km, mode); break;
   }
 }
 

@@ -1,5 +1,5 @@
 """Tensor-core pair passes (tcgen05, BF16 or FP16 operands, FP32 accumulation)
-for the 2-layer l_max 2 model.
+for the 2-layer l_max 2 model, its widths at l_max 0 and 1, and 3 layers.
 
 Two references:
   * the oracle in operand-emulation mode (oracle/model.py: GEMM operands,
@@ -170,6 +170,72 @@ def test_tensorcore_md_and_unsupported_model(main):
         al.allegro_energy_forces(tctx, p, s.astype(np.int32), c, None, None, al.ALLEGRO_BF16)
     assert err.value.code == 10
     al.allegro_destroy(tctx)
+
+
+def _lmax_cfg(l_max, n_layers=2):
+    return dataclasses.replace(synth.MAIN, l_max=l_max, n_layers=n_layers)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp16", "fp16split"])
+@pytest.mark.parametrize("l_max", [0, 1])
+def test_tensorcore_lmax_sweep_models(l_max, mode):
+    """The main model's widths at l_max 0 and 1 (Table 2's sweep) on the
+    tensor-core passes (components, scalar paths, mixing K-slices and the
+    mixing-adjoint layout all follow l_max): 432 atoms, about 178 tiles of 128
+    pairs with a ragged last tile, more tiles than CTAs; the same references
+    and bounds as for l_max 2, and a bitwise rerun."""
+    cfg = _lmax_cfg(l_max)
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    pos, sp, cell = synth.make_ammonia(108, 5)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        E, F, Ei = _gpu(ctx, pos, sp, cell, MODES[mode])
+        E2, F2, _ = _gpu(ctx, pos, sp, cell, MODES[mode])
+        n_pairs = al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS)
+    finally:
+        al.allegro_destroy(ctx)
+    assert n_pairs > 152 * 128 and n_pairs % 128 != 0
+    _check_against_oracles(blob, mode, pos, sp, cell, E, F, Ei)
+    assert E2 == E and np.array_equal(F2, F)
+
+
+def test_tensorcore_lmax1_three_layers_and_md():
+    """l_max 1 with three layers (pass B^T of k = 2 writes dV^1 at the l_max 1
+    layout), split mode, against the emulation-derived bounds and twice the
+    emulation's own force error; then 20 split-mode NVE steps of the 2-layer
+    l_max 1 model on 432 atoms against the exact oracle's trajectory, bounds
+    as in test_tensorcore_nve_trajectory_matches_oracle."""
+    from oracle.md import velocity_verlet
+    cfg = _lmax_cfg(1, n_layers=3)
+    blob = synth.make_blob(cfg, 44, sigma=energy_scale("main"))
+    pos, sp, cell = synth.make_ammonia(108, 0)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        E, F, Ei = _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP16_SPLIT)
+    finally:
+        al.allegro_destroy(ctx)
+    _check_against_oracles(blob, "fp16split", pos, sp, cell, E, F, Ei, method_bound=False)
+    cfg = _lmax_cfg(1)
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    orc = OracleModel(blob)
+    L = np.diag(cell)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        al.allegro_set_md_precision(ctx, al.ALLEGRO_FP16_SPLIT)
+        al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+        n = 20
+        en = np.zeros((n, 3))
+        al.allegro_md_step_nve(ctx, 0.25, n, None, en)
+        P, V = np.zeros_like(pos), np.zeros_like(pos)
+        assert al.allegro_md_get_state(ctx, P, V) == n
+    finally:
+        al.allegro_destroy(ctx)
+    ref = velocity_verlet(lambda p: orc.energy_forces(p, sp, L)[:2], pos, v0, MASS[sp], L, 0.25, n)
+    d = P - ref["pos"]
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() <= 1e-3
+    assert np.abs(V - ref["vel"]).max() <= 4e-4
 
 
 @pytest.mark.parametrize("mode", ["fp16", "fp16split"])
