@@ -78,7 +78,14 @@ const char* allegro_version(void);
  * hidden width, and (l_max, C, D, E) in {(1, 8, 32, 32), (0, 16, 128, 32),
  * (1, 16, 128, 32), (2, 16, 128, 32)} (the last three: the l_max sweep of
  * Table 2 at one width, in every precision; the tensor-core precisions need
- * at least two layers).
+ * at least two layers).  The header's parity flag: 0 (natural-parity coupling
+ * paths) or 1 (full O(3): parity-odd paths and pseudotensor features, Sec. 2.1
+ * E(3) equivariance including inversion).  Parity 1 is accepted for models of
+ * at most two layers, where the odd paths cannot reach the energy (a
+ * pseudotensor gives a true scalar only through a second odd path, and no
+ * path into l = 0 is odd), so the model computed is the natural-parity one and
+ * the pseudotensor mixing matrices are not loaded; E_UNSUPPORTED from three
+ * layers on.  An out-of-range flag is E_BLOB.
  * The paper defines only the pairwise-energy decomposition and equivariance
  * (Sec. 2.1); the layer structure follows the Allegro reading stated in the
  * oracle package.

@@ -1,5 +1,6 @@
 """Reader for the "ALW1" weights blob (oracle side, written independently of
-the C++ reader).  Layout: magic, 11 u32 header words, latent and energy widths,
+the C++ reader).  Layout: magic, 11 u32 header words (the last one the parity
+flag: 0 natural-parity paths only, 1 full O(3)), latent and energy widths,
 padding to 8 bytes, r_cut, nu, sigma[S], mu[S], a 48-byte-per-entry tensor
 directory (name[32], rows, cols, offset) and FP64 row-major tensors.
 """
@@ -13,9 +14,11 @@ def read_blob(buf):
     if buf[:4] != b"ALW1":
         raise ValueError("bad magic")
     (version, S, l_max, n_layers, C, Nb, p, n_lat, n_en, n_t,
-     _res) = struct.unpack_from("<11I", buf, 4)
+     parity) = struct.unpack_from("<11I", buf, 4)
     if version != 1:
         raise ValueError("unsupported version")
+    if parity not in (0, 1):
+        raise ValueError("parity flag must be 0 or 1")
     off = 48
     latent = struct.unpack_from(f"<{n_lat}I", buf, off)
     off += 4 * n_lat
@@ -39,5 +42,5 @@ def read_blob(buf):
         names.append(name)
     cfg = dict(n_species=S, l_max=l_max, n_layers=n_layers, n_channels=C,
                n_bessel=Nb, poly_p=p, latent=tuple(latent), energy=tuple(energy),
-               r_cut=r_cut, avg_num_neighbors=nu, sigma=tuple(sigma), mu=tuple(mu))
+               r_cut=r_cut, avg_num_neighbors=nu, sigma=tuple(sigma), mu=tuple(mu), parity=parity)
     return cfg, weights, names

@@ -19,6 +19,15 @@ Everything below that is not in the paper is a stated reading:
     if k < L: V^k[c', l3 m] = sum_{c, q} Wmix_l3[c', c P_l3 + q] T[c, q, m] / sqrt(C P_l3)
               (q runs over the paths ending in l3, in path order)
     s     = scalar (l3 = 0) outputs T[c, q, 0], index c P_0 + q
+  With the blob's parity flag set (full O(3)), features are irreps (l, s),
+  s = 1 for the parity opposite to Y_l's (pseudotensors); V^0 is all s = 0, the
+  paths of a layer run from every input irrep (l1, s1) present through Y_l2 to
+  l3 with l1 + l2 + l3 of either parity, landing in s3 = (l1 + s1 + l2 + l3)
+  mod 2; each output irrep (l3, s3) is mixed by its own matrix (mix{l3} for
+  s3 = 0, mix{l3}p for s3 = 1) over its paths, ordered by s1, then l1, then
+  l2; the latent MLP takes the true scalars (0, 0) only.  Without the flag
+  only paths with s1 = s3 = 0 exist (l1 + l2 + l3 even), which is the model
+  above.
     x^k   = (x^{k-1} + fc * MLP_k([x^{k-1}, s])) / sqrt(2)
   E_ij = MLP_E(x^L) (SiLU hidden layers, linear 1-wide output)
   E_i  = sigma_{Z_i} sum_j E_ij + mu_{Z_i},   E = sum_i E_i
@@ -126,8 +135,10 @@ class OracleModel:
         self.S = cfg["n_species"]
         self.rc = cfg["r_cut"]
         self.nu = cfg["avg_num_neighbors"]
+        self.o3 = cfg.get("parity", 0) == 1
         self.paths = coupling_paths(self.lmax)
-        self.cg = {p: torch.tensor(real_cg(*p), dtype=F64) for p in self.paths}
+        self.cg = {p: torch.tensor(real_cg(*p), dtype=F64)
+                   for p in coupling_paths(self.lmax, parity="all" if self.o3 else "even")}
         if cfg["poly_p"] != 6:
             raise ValueError("poly_p = 6 only")
         if emulate not in (None, "bf16", "fp16", "fp16split"):
@@ -206,6 +217,22 @@ class OracleModel:
                 x = self._act(x)
         return x
 
+    def layer_paths(self, irreps):
+        """{(l3, s3): [(l1, s1, l2), ...]} for a layer whose input features
+        carry the irreps in `irreps`; paths in (s1, l1, l2) order."""
+        out = {}
+        for s1 in (0, 1):
+            for l1 in range(self.lmax + 1):
+                if (l1, s1) not in irreps:
+                    continue
+                for l2 in range(self.lmax + 1):
+                    for l3 in range(abs(l1 - l2), min(l1 + l2, self.lmax) + 1):
+                        s3 = (l1 + s1 + l2 + l3) % 2
+                        if not self.o3 and (s1 or s3):
+                            continue
+                        out.setdefault((l3, s3), []).append((l1, s1, l2))
+        return out
+
     # ------------------------------------------------------------------ model
     def atom_energies(self, pos, species, lengths, pairs, w=None):
         """Per-atom energies E_i (torch float64, differentiable w.r.t. pos and w).
@@ -243,7 +270,8 @@ class OracleModel:
         nlat = len(cfg["latent"])
         x = self._qs(fc[:, None] * self._mlp(h, [w[f"twobody.{k}"] for k in range(nlat)], group="twobody"))
         w0 = self._qlin(x, w["embed"], group="embed").view(P, C, lmax + 1)
-        V = [w0[:, :, l, None] * Y[l][:, None, :] for l in range(lmax + 1)]
+        # features: irrep (l, s) -> (P, C, 2l + 1)
+        V = {(l, 0): w0[:, :, l, None] * Y[l][:, None, :] for l in range(lmax + 1)}
         for layer in range(1, self.L + 1):
             last = layer == self.L
             if self.op_dtype is None:
@@ -255,30 +283,28 @@ class OracleModel:
                 contrib = e[:, :, None] * Y[l][:, None, :]
                 Gl = torch.zeros((N, C, 2 * l + 1), dtype=F64).index_add(0, i, contrib)
                 G.append(Gl[i])
-            T = {}
-            for p in self.paths:
-                l1, l2, l3 = p
-                if last and l3 != 0:
+            T = {}                                    # output irrep -> [per-path (P, C, 2 l3 + 1)]
+            for (l3, s3), plist in self.layer_paths(set(V)).items():
+                if last and (l3, s3) != (0, 0):
                     continue
-                T[p] = torch.einsum("abc,pna,pnb->pnc", self.cg[p], V[l1], G[l2])
-            scal = [p for p in self.paths if p[2] == 0]
-            s = torch.stack([T[p][:, :, 0] for p in scal], dim=2).reshape(P, C * len(scal))
+                T[(l3, s3)] = [torch.einsum("abc,pna,pnb->pnc", self.cg[(l1, l2, l3)], V[(l1, s1)], G[l2])
+                               for (l1, s1, l2) in plist]
+            s = torch.stack([t[:, :, 0] for t in T[(0, 0)]], dim=2).reshape(P, C * len(T[(0, 0)]))
             if not last:
-                newV = []
-                for l3 in range(lmax + 1):
-                    ps = [p for p in self.paths if p[2] == l3]
-                    Tl = torch.stack([T[p] for p in ps], dim=2)        # (P, C, Pl, 2l3+1)
-                    Tl = Tl.reshape(P, C * len(ps), 2 * l3 + 1)
-                    Wm = w[f"layer{layer}.mix{l3}"]
+                newV = {}
+                for (l3, s3), tl in T.items():
+                    Tl = torch.stack(tl, dim=2)                       # (P, C, Pl, 2l3+1)
+                    Tl = Tl.reshape(P, C * len(tl), 2 * l3 + 1)
+                    Wm = w[f"layer{layer}.mix{l3}" + ("p" if s3 else "")]
                     if self.op_dtype is None:
-                        newV.append(torch.einsum("oi,pim->pom", Wm, Tl) / math.sqrt(C * len(ps)))
+                        newV[(l3, s3)] = torch.einsum("oi,pim->pom", Wm, Tl) / math.sqrt(C * len(tl))
                     else:
                         # one GEMM over the (pair, m) rows of the K = C P_l3 inputs
                         nm = 2 * l3 + 1
-                        rows = Tl.permute(0, 2, 1).reshape(P * nm, C * len(ps))
+                        rows = Tl.permute(0, 2, 1).reshape(P * nm, C * len(tl))
                         out = self._qlin(rows, Wm, group="mix")
-                        newV.append(out.reshape(P, nm, C).permute(0, 2, 1))
-                V = [self._qs(v) for v in newV]
+                        newV[(l3, s3)] = out.reshape(P, nm, C).permute(0, 2, 1)
+                V = {key: self._qs(v) for key, v in newV.items()}
             if not last:
                 s = self._qs(s)
             m = self._mlp(torch.cat([x, s], dim=1),

@@ -14,10 +14,14 @@ reading used here:
     coefficients (Racah's closed formula) carried into this real basis by the
     unitary complex-to-real change of basis, normalised to Frobenius norm 1,
     with the sign chosen so that contracting Y_l1(z) and Y_l2(z) gives a
-    positive multiple of Y_l3(z).
+    positive multiple of Y_l3(z).  For l1 + l2 + l3 odd that contraction is
+    zero (the coupling is odd under inversion: 1 x 1 -> 1 is the cross
+    product), and the sign is chosen instead so that the first nonzero entry
+    in (m1, m2, m3) order is positive.
   * Paths: every (l1, l2, l3) with l1, l2 <= l_max,
     |l1 - l2| <= l3 <= min(l1 + l2, l_max) and l1 + l2 + l3 even, in
-    lexicographic order.
+    lexicographic order (the natural-parity paths); with parity="odd" the
+    ones with l1 + l2 + l3 odd, with parity="all" both.
 """
 import math
 from functools import lru_cache
@@ -49,12 +53,13 @@ def sh_real(u, l_max):
     return out
 
 
-def coupling_paths(l_max, scalar_only=False):
+def coupling_paths(l_max, scalar_only=False, parity="even"):
+    want = {"even": (0,), "odd": (1,), "all": (0, 1)}[parity]
     paths = []
     for l1 in range(l_max + 1):
         for l2 in range(l_max + 1):
             for l3 in range(abs(l1 - l2), min(l1 + l2, l_max) + 1):
-                if (l1 + l2 + l3) % 2:
+                if (l1 + l2 + l3) % 2 not in want:
                     continue
                 if scalar_only and l3 != 0:
                     continue
@@ -123,10 +128,14 @@ def real_cg(l1, l2, l3):
     C = C.real if re >= im else C.imag
     assert min(re, im) < 1e-12, (l1, l2, l3)
     C = C / np.linalg.norm(C)
-    # sign rule: C(Y_l1(z), Y_l2(z)) must be a positive multiple of Y_l3(z)
-    zhat = torch.tensor([[0.0, 0.0, 1.0]], dtype=torch.float64)
-    Y = [t[0].numpy() for t in sh_real(zhat, max(l1, l2, l3))]
-    c = np.einsum("abc,a,b,c->", C, Y[l1], Y[l2], Y[l3])
+    if (l1 + l2 + l3) % 2 == 0:
+        # sign rule: C(Y_l1(z), Y_l2(z)) must be a positive multiple of Y_l3(z)
+        zhat = torch.tensor([[0.0, 0.0, 1.0]], dtype=torch.float64)
+        Y = [t[0].numpy() for t in sh_real(zhat, max(l1, l2, l3))]
+        c = np.einsum("abc,a,b,c->", C, Y[l1], Y[l2], Y[l3])
+    else:
+        # odd path: the first nonzero entry in (m1, m2, m3) order is positive
+        c = C.ravel()[np.flatnonzero(np.abs(C.ravel()) > 1e-12)[0]]
     if c < 0:
         C = -C
     return np.ascontiguousarray(C)

@@ -38,6 +38,7 @@ struct Tensor {
 
 struct Blob {
   uint32_t S, lmax, L, C, NB, p;
+  uint32_t parity;   // 0: natural-parity paths only; 1: full O(3) (odd paths, pseudotensors)
   std::vector<uint32_t> latent, energy;
   double rc, nu;
   std::vector<double> sigma, mu;
@@ -69,7 +70,8 @@ bool parse_blob(const void* data, size_t n, Blob& B, std::string& why) {
   uint32_t h[11];
   for (int k = 0; k < 11; ++k) rd32(b, 4 + 4 * k, h[k]);
   if (h[0] != 1) { why = "unsupported blob version"; return false; }
-  B.S = h[1]; B.lmax = h[2]; B.L = h[3]; B.C = h[4]; B.NB = h[5]; B.p = h[6];
+  B.S = h[1]; B.lmax = h[2]; B.L = h[3]; B.C = h[4]; B.NB = h[5]; B.p = h[6]; B.parity = h[10];
+  if (B.parity > 1) { why = "parity flag must be 0 or 1"; return false; }
   const uint32_t nlat = h[7], nen = h[8], nt = h[9];
   if (nlat > 16 || nen > 16 || B.S > 16 || nt > 4096) { why = "implausible header"; return false; }
   size_t off = 48;
@@ -1233,6 +1235,19 @@ int allegro_create(const void* weights_blob, size_t blob_bytes, const double* sp
                         fp32_supported((int)B.lmax, (int)B.C, (int)B.latent[0], (int)B.energy[0]);
   if (!shape_ok) {
     g_err = "model shape not compiled into this library";
+    delete c;
+    return ALLEGRO_E_UNSUPPORTED;
+  }
+  // Full O(3): a pseudotensor made by an odd path of layer k reaches a true
+  // scalar (0e) only through a further odd path, which no l3 = 0 output has
+  // (l1 = l2 there), so it first changes the energy through the mixing of
+  // layer k + 1 into a layer k + 2.  With at most two layers the full-O(3)
+  // model therefore is the natural-parity model (its pseudotensor mixing
+  // matrices, layer{k}.mix{l}p, have no effect and are not loaded); from
+  // three layers on the odd paths would be needed, which these passes do not
+  // build.
+  if (B.parity == 1 && B.L >= 3) {
+    g_err = "full-O(3) models of three or more layers are not built (odd coupling paths)";
     delete c;
     return ALLEGRO_E_UNSUPPORTED;
   }

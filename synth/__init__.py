@@ -12,12 +12,12 @@ density (0.68 g/cm^3) and molecular geometry, and weights are seeded Gaussians.
 """
 from .ammonia import (MASS_AMU, SPECIES_N, SPECIES_H, box_edge, make_ammonia,
                       make_velocities, make_sam_batch, atoms_per_volume)
-from .weights import (ModelConfig, TINY, MAIN, path_counts, tensor_shapes,
+from .weights import (ModelConfig, TINY, MAIN, path_counts, layer_path_counts, tensor_shapes,
                       make_weights, write_blob, make_blob)
 
 __all__ = [
     "MASS_AMU", "SPECIES_N", "SPECIES_H", "box_edge", "make_ammonia",
     "make_velocities", "make_sam_batch", "atoms_per_volume", "ModelConfig",
-    "TINY", "MAIN", "path_counts", "tensor_shapes", "make_weights",
+    "TINY", "MAIN", "path_counts", "layer_path_counts", "tensor_shapes", "make_weights",
     "write_blob", "make_blob",
 ]

@@ -15,7 +15,9 @@ C++ library:
    32  u32                  n_latent  (number of latent hidden widths)
    36  u32                  n_energy  (number of energy-MLP hidden widths)
    40  u32                  n_tensors
-   44  u32                  reserved (0)
+   44  u32                  parity: 0 = natural-parity coupling paths only,
+                            1 = full O(3) (parity-odd paths and pseudotensor
+                            features as well)
    48  u32[n_latent]        latent widths
        u32[n_energy]        energy hidden widths
        (zero padding to an 8-byte boundary)
@@ -37,6 +39,8 @@ Generator(PCG64(seed)), entries ~ N(0, 1)):
   for layer k = 1 .. L:
     layer{k}.env       C x D_last
     layer{k}.mix{l}    C x (C P_l)              only for k < L, l = 0 .. l_max
+    layer{k}.mix{l}p   C x (C Q_kl)             parity 1 only, k < L, every l whose
+                                                pseudotensor output has Q_kl > 0 paths
     layer{k}.latent.0  D0 x (D_last + C P_0)
     layer{k}.latent.j  Dj x D(j-1)              j = 1 .. n_latent-1
   energy.0             E0 x D_last
@@ -45,6 +49,11 @@ Generator(PCG64(seed)), entries ~ N(0, 1)):
 
 P_l counts the coupling paths (l1, l2, l) with l1, l2 <= l_max,
 |l1 - l2| <= l <= l1 + l2 and l1 + l2 + l even; it only fixes matrix shapes.
+With parity 1 the features of layer k carry irreps (l, s), s = 1 marking the
+parity opposite to Y_l's; a path from input (l1, s1) through Y_l2 to output
+order l3 lands in s3 = (l1 + s1 + l2 + l3) mod 2, and P_l (for layers k > 1)
+and Q_kl count the paths into (l, 0) and (l, 1) from the irreps present
+(layer_path_counts); only shapes follow from it here.
 """
 import math
 import struct
@@ -70,6 +79,24 @@ def path_counts(l_max):
     return counts
 
 
+def layer_path_counts(l_max, parity, n_layers):
+    """[{(l3, s3): number of paths}] for layers 1 .. n_layers (shape logic only)."""
+    irreps = {(l, 0) for l in range(l_max + 1)}
+    out = []
+    for _ in range(n_layers):
+        cnt = {}
+        for (l1, s1) in irreps:
+            for l2 in range(l_max + 1):
+                for l3 in range(abs(l1 - l2), min(l1 + l2, l_max) + 1):
+                    s3 = (l1 + s1 + l2 + l3) % 2
+                    if parity == 0 and (s1 or s3):
+                        continue
+                    cnt[(l3, s3)] = cnt.get((l3, s3), 0) + 1
+        out.append(cnt)
+        irreps = set(cnt)
+    return out
+
+
 @dataclass(frozen=True)
 class ModelConfig:
     r_cut: float
@@ -84,6 +111,7 @@ class ModelConfig:
     avg_num_neighbors: float = 0.0
     sigma: tuple = (1.0, 1.0)
     mu: tuple = (0.0, 0.0)
+    parity: int = 0
 
     def with_sigma(self, s):
         return replace(self, sigma=tuple(float(s) for _ in range(self.n_species)))
@@ -107,17 +135,21 @@ def tensor_shapes(cfg):
     """Ordered list of (name, rows, cols) for the config."""
     S, C, Nb = cfg.n_species, cfg.n_channels, cfg.n_bessel
     D, E = list(cfg.latent), list(cfg.energy)
-    P = path_counts(cfg.l_max)
+    counts = layer_path_counts(cfg.l_max, cfg.parity, cfg.n_layers)
     out = [("twobody.0", D[0], 2 * S + Nb)]
     for k in range(1, len(D)):
         out.append((f"twobody.{k}", D[k], D[k - 1]))
     out.append(("embed", C * (cfg.l_max + 1), D[-1]))
     for layer in range(1, cfg.n_layers + 1):
+        cnt = counts[layer - 1]
         out.append((f"layer{layer}.env", C, D[-1]))
         if layer < cfg.n_layers:
             for l in range(cfg.l_max + 1):
-                out.append((f"layer{layer}.mix{l}", C, C * P[l]))
-        out.append((f"layer{layer}.latent.0", D[0], D[-1] + C * P[0]))
+                out.append((f"layer{layer}.mix{l}", C, C * cnt[(l, 0)]))
+            for l in range(cfg.l_max + 1):
+                if cnt.get((l, 1), 0) > 0:
+                    out.append((f"layer{layer}.mix{l}p", C, C * cnt[(l, 1)]))
+        out.append((f"layer{layer}.latent.0", D[0], D[-1] + C * cnt[(0, 0)]))
         for k in range(1, len(D)):
             out.append((f"layer{layer}.latent.{k}", D[k], D[k - 1]))
     out.append(("energy.0", E[0], D[-1]))
@@ -139,7 +171,7 @@ def write_blob(cfg, weights):
     head = MAGIC + struct.pack(
         "<11I", VERSION, S, cfg.l_max, cfg.n_layers, cfg.n_channels,
         cfg.n_bessel, cfg.poly_p, len(cfg.latent), len(cfg.energy),
-        len(shapes), 0)
+        len(shapes), cfg.parity)
     head += struct.pack(f"<{len(cfg.latent)}I", *cfg.latent)
     head += struct.pack(f"<{len(cfg.energy)}I", *cfg.energy)
     head += b"\0" * ((-len(head)) % 8)

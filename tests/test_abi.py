@@ -63,6 +63,23 @@ def test_bad_blob_and_mismatch_rejected_on_host(built):
     assert e.value.code == 10
 
 
+def test_full_o3_blobs_on_host(built):
+    """The parity flag: full-O(3) models of three layers are refused
+    (E_UNSUPPORTED) and an out-of-range flag is a malformed blob (E_BLOB),
+    both before any GPU work."""
+    import dataclasses
+    mass = np.array([14.007, 1.008])
+    cfg3 = dataclasses.replace(synth.MAIN, n_layers=3, parity=1)
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_create(synth.make_blob(cfg3, 1), mass, cfg3.r_cut, cfg3.l_max, 3)
+    assert e.value.code == 10
+    blob = bytearray(synth.make_blob(synth.MAIN, 1))
+    blob[44:48] = (2).to_bytes(4, "little")
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_create(bytes(blob), mass, synth.MAIN.r_cut, 2, 2)
+    assert e.value.code == 11
+
+
 def test_null_arguments(built):
     out = ctypes.c_void_p()
     rc = built.allegro_create(None, 0, None, 2, 4.0, 1, 1, ctypes.byref(out))

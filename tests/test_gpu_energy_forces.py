@@ -4,8 +4,8 @@ Tolerances (FP32 path): |dE| / |E| <= 1e-5 (or |dE| / (N rms E_i) when |E| is
 small), max |dF| / max |F_ref| <= 1e-5, per-atom energies within
 1e-5 * rms(E_i).  Covers the 1-layer l_max 1 model (passes A, C, A^T) and the
 2-layer l_max 2 model (A, B, C, B^T, A^T), small boxes with several images of
-one partner, tile-straddling rows, and sampled atoms of the 110,592-atom
-system."""
+one partner, tile-straddling rows, sampled atoms of the 110,592-atom
+system, the l_max 0 / 1 widths and a full-O(3) blob."""
 import numpy as np
 import pytest
 import torch
@@ -178,3 +178,27 @@ def test_no_pairs_and_single_atom(main, precision):
     E, F, Ei = _gpu(ctx, p2, s2, c2)
     Er, Fr, Eir, _ = orc.energy_forces(p2, s2, np.diag(c2))
     _compare(E, F, Ei, Er, Fr, Eir)
+
+
+def test_full_o3_two_layer_blob():
+    """A full-O(3) blob (parity flag 1: pseudotensor mixing matrices for the
+    odd paths of layer 1) of the 2-layer main model, against the oracle's
+    full-O(3) evaluation, which forms the odd paths and pseudotensors: the
+    FP32 passes at 1e-5 and the split tensor-core mode within 2e-3 eV/A.
+    (With two layers the odd paths cannot reach the energy, which the oracle's
+    own pins show; the library builds the natural-parity passes.)"""
+    import dataclasses
+    cfg = dataclasses.replace(synth.MAIN, parity=1)
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    orc = OracleModel(blob)
+    assert orc.o3 and "layer1.mix1p" in orc.w
+    pos, sp, cell = synth.make_ammonia(108, 5)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        E, F, Ei = _gpu(ctx, pos, sp, cell)
+        Es, Fs, _ = _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP16_SPLIT)
+    finally:
+        al.allegro_destroy(ctx)
+    Er, Fr, Eir, _ = orc.energy_forces(pos, sp, np.diag(cell))
+    _compare(E, F, Ei, Er, Fr, Eir)
+    assert np.abs(Fs - Fr).max() <= 2e-3

@@ -117,6 +117,74 @@ def test_cg_special_cases():
     np.testing.assert_allclose(real_cg(1, 1, 0)[:, :, 0], np.eye(3) / math.sqrt(3), atol=1e-14)
 
 
+# ---- parity-odd coupling paths (full O(3)) ----
+
+def test_odd_paths():
+    assert coupling_paths(2, parity="odd") == [(1, 1, 1), (1, 2, 2), (2, 1, 2), (2, 2, 1)]
+    assert coupling_paths(1, parity="odd") == [(1, 1, 1)]
+    assert coupling_paths(0, parity="odd") == []
+    assert sorted(coupling_paths(2, parity="all")) == sorted(coupling_paths(2) + coupling_paths(2, parity="odd"))
+    assert not [p for p in coupling_paths(2, parity="odd") if p[2] == 0]   # no odd path into l = 0
+
+
+def _yzx(v):
+    """Cartesian vector -> the l = 1 component order (y, z, x)."""
+    return np.array([v[1], v[2], v[0]])
+
+
+def test_odd_cg_cross_product_closed_form():
+    """C^{111}(a, b) = (a x b) / sqrt(6) in the (y, z, x) order (Levi-Civita,
+    Frobenius norm 1, first nonzero entry C[y, z, x] = +1/sqrt(6))."""
+    C = real_cg(1, 1, 1)
+    for _ in range(5):
+        a, b = RNG.normal(size=3), RNG.normal(size=3)
+        got = np.einsum("abc,a,b->c", C, _yzx(a), _yzx(b))
+        np.testing.assert_allclose(got, _yzx(np.cross(a, b)) / math.sqrt(6.0), atol=1e-14)
+
+
+def test_odd_cg_221_closed_form():
+    """Y_2(u), Y_2(v) are the traceless parts of u u^T, v v^T; the only vector
+    bilinear in two such tensors, odd under inversion, is the axial vector of
+    the antisymmetric part of their product, eps_ijk (A B)_jk = (u . v) (u x v):
+    C^{221}(Y_2(u), Y_2(v)) = kappa (u . v) (u x v) with one constant kappa."""
+    C = real_cg(2, 2, 1)
+    ratios = []
+    for _ in range(6):
+        u, v = _unit(2)
+        Yu, Yv = _Y(u[None], 2)[2][0], _Y(v[None], 2)[2][0]
+        got = np.einsum("abc,a,b->c", C, Yu, Yv)
+        ref = _yzx(np.dot(u, v) * np.cross(u, v))
+        k = np.dot(got, ref) / np.dot(ref, ref)
+        np.testing.assert_allclose(got, k * ref, atol=1e-12)
+        ratios.append(k)
+    assert np.ptp(ratios) < 1e-12 and abs(ratios[0]) > 0.1
+
+
+@pytest.mark.parametrize("path", coupling_paths(2, parity="odd"))
+def test_odd_cg_pseudotensor_sign_norm_and_sign_rule(path):
+    """Proper rotations: D3 C(a, b) = C(D1 a, D2 b); improper ones (with the
+    D_l taken from the harmonics, D_l(-R) = (-1)^l D_l(R)): the opposite sign,
+    since (-1)^(l1 + l2) = -(-1)^l3 on an odd path.  Together with Frobenius
+    norm 1 and the first-nonzero sign rule this fixes the tensor (the
+    equivariant bilinear map of a triple (l1, l2, l3) is unique up to scale)."""
+    l1, l2, l3 = path
+    C = real_cg(*path)
+    assert abs(np.linalg.norm(C) - 1.0) < 1e-13
+    assert C.ravel()[np.flatnonzero(np.abs(C.ravel()) > 1e-12)[0]] > 0
+    for k in range(6):
+        R = _rand_rot()
+        sign = 1.0
+        if k % 2:
+            R, sign = -R, -1.0
+        D1, D2, D3 = (_wigner_D(R, l) for l in (l1, l2, l3))
+        a = RNG.normal(size=2 * l1 + 1)
+        b = RNG.normal(size=2 * l2 + 1)
+        lhs = D3 @ np.einsum("abc,a,b->c", C, a, b)
+        rhs = np.einsum("abc,a,b->c", C, D1 @ a, D2 @ b)
+        np.testing.assert_allclose(lhs, sign * rhs, atol=1e-11)
+        assert np.abs(rhs).max() > 1e-3
+
+
 def test_bessel_closed_form():
     d = torch.tensor([0.3, 1.7, 3.9], dtype=torch.float64)
     B = bessel(d, 4.0, 8).numpy()
