@@ -136,14 +136,34 @@ AL_DEV void stage_mix(const LayerW& LW, float* s_mix) {
   cp_async_commit();
 }
 
-// Tile GEMM: out[m][n] = sum_k A[m*lda + k] * Wt[k*N + n] for m < TT, n < N.
+// Tile GEMM: out[m][n] = sum_k A[m*LDA + k] * Wt[k*N + n] for m < TT, n < N.
 // A in shared memory, Wt ([K][N], 16-byte aligned) staged through wbuf
 // (>= 2 kKC N floats of shared memory); 256 threads with a TM x TN register
 // tile each; epi(m, n, value) consumes every output once.  All threads of the
 // block must call it; it begins and ends with a block barrier.
-template <int N, int K, int TT, class T, class Epi>
-AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt, float* wbuf,
-                 Epi&& epi) {
+//
+// Shared-memory traffic per k step of a warp (one wavefront = 128 bytes):
+// with TN % 4 == 0, at least 16 row groups and rows whose 16-byte chunk
+// stride is not a multiple of 4, the threads of a warp take 16 (or 32)
+// consecutive row groups and 2 (or 1) column groups: their weight loads fall
+// in one 64-byte run and A is read as float4 along k (rows in distinct
+// chunks of a wavefront), 12 wavefronts per 4 k steps against 16 FMA issue
+// cycles.  Otherwise a warp takes consecutive column groups (weights
+// contiguous across the warp, A nearly broadcast) and A is read per k.
+template <class T>
+AL_DEV void ld4(const T* p, T* out) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else {
+    static_assert(sizeof(T) == 8, "float or Dual");
+    const float4 v0 = reinterpret_cast<const float4*>(p)[0], v1 = reinterpret_cast<const float4*>(p)[1];
+    out[0] = T(v0.x, v0.y); out[1] = T(v0.z, v0.w); out[2] = T(v1.x, v1.y); out[3] = T(v1.z, v1.w);
+  }
+}
+
+template <int N, int K, int TT, int LDA, class T, class Epi>
+AL_DEV void gemm(const T* __restrict__ A, const float* __restrict__ Wt, float* wbuf, Epi&& epi) {
   constexpr int M = TT;
   constexpr int NCH = (K + kKC - 1) / kKC;
   static_assert(N % 4 == 0, "weights are staged in 16-byte units");
@@ -169,7 +189,7 @@ AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt,
         const int idx = threadIdx.x + r * kThreads;
         if (idx < M * N) {
           const int m = idx / N, n = idx % N;
-          for (int k = 0; k < kc; ++k) acc[r] = fmaf(A[m * lda + k0 + k], wb[k * N + n], acc[r]);
+          for (int k = 0; k < kc; ++k) acc[r] = fmaf(A[m * LDA + k0 + k], wb[k * N + n], acc[r]);
         }
       }
       __syncthreads();
@@ -187,7 +207,11 @@ AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt,
     constexpr int TX = N / TN;
     constexpr int TY = kThreads / TX;
     static_assert(TY * TM == M, "tile shape");
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    constexpr int kChunkStride = LDA * (int)sizeof(T) / 16;
+    constexpr bool kRows = TN % 4 == 0 && TY >= 16 && K % 4 == 0 && (LDA * (int)sizeof(T)) % 16 == 0 &&
+                           kChunkStride % 4 != 0;
+    const int tx = kRows ? (int)threadIdx.x / TY : (int)threadIdx.x % TX;
+    const int ty = kRows ? (int)threadIdx.x % TY : (int)threadIdx.x / TX;
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -201,42 +225,71 @@ AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt,
         cp_async_wait<0>();
       }
       __syncthreads();
-      // TN % 4 == 0: float4 group q of thread tx covers columns q TX 4 + tx 4 ..+3, so
-      // that the 16-byte loads of a warp are contiguous (no bank conflicts)
-      const float* wc = wbuf + (ch & 1) * kKC * N + (TN % 4 == 0 ? tx * 4 : tx * TN);
       const int k0 = ch * kKC;
-      const T* a0 = A + ty * lda + k0;
-      auto step = [&](int k) {
-        T a[TM];
-        float b[TN];
+      const T* a0 = A + ty * LDA + k0;
+      if constexpr (kRows) {
+        // thread tx's own TN columns, float4 groups at tx TN + 4 q
+        const float* wc = wbuf + (ch & 1) * kKC * N + tx * TN;
+        auto step4 = [&](int k) {
+          T a[TM][4];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = a0[i * TY * lda + k];
-        if constexpr (TN % 4 == 0) {
+          for (int i = 0; i < TM; ++i) ld4(a0 + i * TY * LDA + k, a[i]);
 #pragma unroll
-          for (int q = 0; q < TN / 4; ++q) {
-            const float4 v = *reinterpret_cast<const float4*>(wc + k * N + q * TX * 4);
-            b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+          for (int kk = 0; kk < 4; ++kk) {
+            float b[TN];
+#pragma unroll
+            for (int q = 0; q < TN / 4; ++q) {
+              const float4 v = *reinterpret_cast<const float4*>(wc + (k + kk) * N + 4 * q);
+              b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+              for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i][kk], b[j], acc[i][j]);
           }
-        } else if constexpr (TN % 2 == 0) {
+        };
+        if (K - k0 >= kKC) {
 #pragma unroll
-          for (int q = 0; q < TN / 2; ++q) {
-            const float2 v = reinterpret_cast<const float2*>(wc + k * N)[q];
-            b[2 * q] = v.x; b[2 * q + 1] = v.y;
-          }
+          for (int k = 0; k < kKC; k += 4) step4(k);
         } else {
-#pragma unroll
-          for (int j = 0; j < TN; ++j) b[j] = wc[k * N + j];
+          for (int k = 0; k < K - k0; k += 4) step4(k);
         }
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-      };
-      if (K - k0 >= kKC) {
-#pragma unroll
-        for (int k = 0; k < kKC; ++k) step(k);
       } else {
-        for (int k = 0; k < K - k0; ++k) step(k);
+        // TN % 4 == 0: float4 group q of thread tx covers columns q TX 4 + tx 4 ..+3, so
+        // that the 16-byte loads of a warp are contiguous (no bank conflicts)
+        const float* wc = wbuf + (ch & 1) * kKC * N + (TN % 4 == 0 ? tx * 4 : tx * TN);
+        auto step = [&](int k) {
+          T a[TM];
+          float b[TN];
+#pragma unroll
+          for (int i = 0; i < TM; ++i) a[i] = a0[i * TY * LDA + k];
+          if constexpr (TN % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < TN / 4; ++q) {
+              const float4 v = *reinterpret_cast<const float4*>(wc + k * N + q * TX * 4);
+              b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+            }
+          } else if constexpr (TN % 2 == 0) {
+#pragma unroll
+            for (int q = 0; q < TN / 2; ++q) {
+              const float2 v = reinterpret_cast<const float2*>(wc + k * N)[q];
+              b[2 * q] = v.x; b[2 * q + 1] = v.y;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = wc[k * N + j];
+          }
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        };
+        if (K - k0 >= kKC) {
+#pragma unroll
+          for (int k = 0; k < kKC; ++k) step(k);
+        } else {
+          for (int k = 0; k < K - k0; ++k) step(k);
+        }
       }
       __syncthreads();
     }
@@ -244,7 +297,8 @@ AL_DEV void gemm(const T* __restrict__ A, int lda, const float* __restrict__ Wt,
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j)
-        epi(ty + i * TY, TN % 4 == 0 ? (j / 4) * TX * 4 + tx * 4 + (j % 4) : tx * TN + j, acc[i][j]);
+        epi(ty + i * TY,
+            kRows ? tx * TN + j : (TN % 4 == 0 ? (j / 4) * TX * 4 + tx * 4 + (j % 4) : tx * TN + j), acc[i][j]);
   }
 }
 
@@ -428,16 +482,16 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(ModelW w, PassBufs b) {
     }
   }
   __syncthreads();
-  gemm<D, Cf::H0, TT>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, T v) { s_z1[m * LDD + n] = silu(v); });
+  gemm<D, Cf::H0, TT, Cf::LDH0>(s_h0, w.tb0.t, s_wb, [&](int m, int n, T v) { s_z1[m * LDD + n] = silu(v); });
   __syncthreads();
   T* X0 = as<T>(b.X[0]);
-  gemm<D, D, TT>(s_z1, LDD, w.tb1.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_z1, w.tb1.t, s_wb, [&](int m, int n, T v) {
     const T x = s_fc[m] * silu(v);
     s_x[m * LDD + n] = x;
     if (m < t.np) X0[(size_t)(t.p0 + m) * D + n] = x;
   });
   __syncthreads();
-  gemm<C, D, TT>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
+  gemm<C, D, TT, LDD>(s_x, w.layer[0].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
   __syncthreads();
   store_segments<Cf::CL>(as<T>(b.gam[1]), t, [&](int p, int x) {
     return s_e[p * C + x / NLM] * s_Y[p * NLM + x % NLM];
@@ -501,7 +555,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
   load_segments<CL>(as<T>(b.gam[k]), b.row_ptr, t, s_G);
   __syncthreads();
   if (k == 1) {
-    gemm<Cf::NW0, D, TT>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D, TT, LDH>(s_h, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -537,16 +591,16 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(ModelW w, PassBufs b, int k
       }
     }
   }
-  gemm<D, Cf::KH, TT>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, T v) { s_z1[m * LDD + n] = silu(v); });
+  gemm<D, Cf::KH, TT, LDH>(s_h, LW.lat0.t, s_wb, [&](int m, int n, T v) { s_z1[m * LDD + n] = silu(v); });
   __syncthreads();
   T* Xk = as<T>(b.X[k]);
-  gemm<D, D, TT>(s_z1, LDD, LW.lat1.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_z1, LW.lat1.t, s_wb, [&](int m, int n, T v) {
     const T x = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;
     s_h[m * LDH + n] = x;
     if (m < t.np) Xk[(size_t)(t.p0 + m) * D + n] = x;
   });
   __syncthreads();
-  gemm<C, D, TT>(s_h, LDH, w.layer[k].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
+  gemm<C, D, TT, LDH>(s_h, w.layer[k].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
   __syncthreads();
   store_segments<CL>(as<T>(b.gam[k + 1]), t, [&](int pp, int x) {
     return s_e[pp * C + x / NLM] * s_Y[pp * NLM + x % NLM];
@@ -619,7 +673,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   load_segments<CL>(as<T>(b.gam[L]), b.row_ptr, t, s_G);
   __syncthreads();
   if (L == 1) {
-    gemm<Cf::NW0, D, TT>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D, TT, LDH>(s_h, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -634,17 +688,17 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   }
   __syncthreads();
   if (b.train) dump_rows<C * NS>(b.tr.s[L], b.trt.s[L], t, s_h + D, LDH);
-  gemm<D, Cf::KH, TT>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, Cf::KH, TT, LDH>(s_h, LW.lat0.t, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D, TT>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_a1, LW.lat1.t, s_wb, [&](int m, int n, T v) {
     s_z2[m * LDD + n] = v;
     s_h[m * LDH + n] = (s_h[m * LDH + n] + s_fc[m] * silu(v)) * kRsqrt2;   // x^L
   });
   __syncthreads();
-  gemm<E, D, TT>(s_h, LDH, w.e0.t, s_wb, [&](int m, int n, T v) {
+  gemm<E, D, TT, LDH>(s_h, w.e0.t, s_wb, [&](int m, int n, T v) {
     s_ze[m * LDE + n] = v;
     s_ae[m * LDE + n] = silu(v);
   });
@@ -675,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
     b.epart[t.tile + t.atom[s]] = acc;
   }
   if (b.train) dump_rows<E>(b.tr.dze, b.trt.dze, t, s_ze, LDE);
-  gemm<D, E, TT>(s_ze, LDE, w.e0.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] = v; });  // dx^L
+  gemm<D, E, TT, LDE>(s_ze, w.e0.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] = v; });  // dx^L
   __syncthreads();
   {
     T du = 0.0f;
@@ -691,12 +745,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   }
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.dz2_l[L], b.trt.dz2_l[L], t, s_z2, LDD);
-  gemm<D, D, TT>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_z2, LW.lat1.n, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.dz1_l[L], b.trt.dz1_l[L], t, s_z1, LDD);
-  gemm<Cf::KH, D, TT>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, T v) {
+  gemm<Cf::KH, D, TT, LDD>(s_z1, LW.lat0.n, s_wb, [&](int m, int n, T v) {
     if (n < D) s_h[m * LDH + n] = v + s_h[m * LDH + n] * kRsqrt2;   // dx^{L-1}
     else s_h[m * LDH + n] = v;                                      // d(scalars)
   });
@@ -749,7 +803,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_c(ModelW w, PassBufs b) {
   __syncthreads();
   if (L == 1) {
     if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, b.trt.dw0, t, s_dw0, Cf::NW0);
-    gemm<D, Cf::NW0, TT>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] += v; });
+    gemm<D, Cf::NW0, TT, Cf::NW0>(s_dw0, w.emb.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
@@ -812,7 +866,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   load_segments<CL>(as<T>(b.gam[k]), b.row_ptr, t, s_G);
   load_segments<CL>(as<T>(b.dgam[k + 1]), b.row_ptr, t, s_dG);
   __syncthreads();
-  gemm<C, D, TT>(s_z2, LDD, LN.env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });  // e^{k+1}
+  gemm<C, D, TT, LDD>(s_z2, LN.env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });  // e^{k+1}
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   {
@@ -832,13 +886,13 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   __syncthreads();
   if (b.train) dump_rows<C>(b.tr.de[k], b.trt.de[k], t, s_de, C);
   const T* dXg = as<T>(b.dX);
-  gemm<D, C, TT>(s_de, C, LN.env.n, s_wb, [&](int m, int n, T v) {
+  gemm<D, C, TT, C>(s_de, LN.env.n, s_wb, [&](int m, int n, T v) {
     s_z2[m * LDD + n] = v + (m < t.np ? dXg[(size_t)(t.p0 + m) * D + n] : 0.0f);   // dx^k
   });
   __syncthreads();
   // recompute layer k forward (scalars, latent MLP)
   if (k == 1) {
-    gemm<Cf::NW0, D, TT>(s_h, LDH, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
+    gemm<Cf::NW0, D, TT, LDH>(s_h, w.emb.t, s_wb, [&](int m, int n, T v) { s_w0[m * Cf::NW0 + n] = v; });
     __syncthreads();
   }
   for (int c = sub; c < C; c += kSub) {
@@ -851,12 +905,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
     for (int q = 0; q < NS; ++q) s_h[p * LDH + D + c * NS + q] = S[q];
   }
   __syncthreads();
-  gemm<D, Cf::KH, TT>(s_h, LDH, LW.lat0.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, Cf::KH, TT, LDH>(s_h, LW.lat0.t, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D, TT>(s_a1, LDD, LW.lat1.t, s_wb, [&](int m, int n, T v) { s_tmp[m * LDD + n] = v; });  // z2
+  gemm<D, D, TT, LDD>(s_a1, LW.lat1.t, s_wb, [&](int m, int n, T v) { s_tmp[m * LDD + n] = v; });  // z2
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.a1_l[k], b.trt.a1_l[k], t, s_a1, LDD);
   {
@@ -875,12 +929,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.dz2_l[k], b.trt.dz2_l[k], t, s_z2, LDD);
   load_rows<CL>(as<T>(b.dV), t, s_tmp, CL);            // dV^k
-  gemm<D, D, TT>(s_z2, LDD, LW.lat1.n, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_z2, LW.lat1.n, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);     // dz1
   });
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.dz1_l[k], b.trt.dz1_l[k], t, s_z1, LDD);
-  gemm<Cf::KH, D, TT>(s_z1, LDD, LW.lat0.n, s_wb, [&](int m, int n, T v) {
+  gemm<Cf::KH, D, TT, LDD>(s_z1, LW.lat0.n, s_wb, [&](int m, int n, T v) {
     if (n < D) s_h[m * LDH + n] += v;
     else s_h[m * LDH + n] = v;
   });
@@ -945,7 +999,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b_bwd(ModelW w, PassBufs b, i
   __syncthreads();
   if (k == 1) {
     if (b.train) dump_rows<Cf::NW0>(b.tr.dw0, b.trt.dw0, t, s_dw0, Cf::NW0);
-    gemm<D, Cf::NW0, TT>(s_dw0, Cf::NW0, w.emb.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] += v; });
+    gemm<D, Cf::NW0, TT, Cf::NW0>(s_dw0, w.emb.n, s_wb, [&](int m, int n, T v) { s_h[m * LDH + n] += v; });
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < t.np * D; idx += kThreads) {
@@ -1011,12 +1065,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   load_rows<D>(as<T>(b.dX), t, s_dx, LDD);
   load_segments<CL>(as<T>(b.dgam[1]), b.row_ptr, t, s_dG);
   __syncthreads();
-  gemm<D, Cf::H0, TT>(s_h0, Cf::LDH0, w.tb0.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, Cf::H0, TT, Cf::LDH0>(s_h0, w.tb0.t, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v;
     s_a1[m * LDD + n] = silu(v);
   });
   __syncthreads();
-  gemm<D, D, TT>(s_a1, LDD, w.tb1.t, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_a1, w.tb1.t, s_wb, [&](int m, int n, T v) {
     s_z2[m * LDD + n] = v;
     s_x[m * LDD + n] = s_geo[m * 8 + 4] * silu(v);
   });
@@ -1025,7 +1079,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
     dump_rows<Cf::LDH0>(b.tr.h0, b.trt.h0, t, s_h0, Cf::LDH0);
     dump_rows<D>(b.tr.a1_tb, b.trt.a1_tb, t, s_a1, LDD);
   }
-  gemm<C, D, TT>(s_x, LDD, w.layer[0].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
+  gemm<C, D, TT, LDD>(s_x, w.layer[0].env.t, s_wb, [&](int m, int n, T v) { s_e[m * C + n] = v; });
   __syncthreads();
   const int p = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   {
@@ -1044,7 +1098,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   }
   __syncthreads();
   if (b.train) dump_rows<C>(b.tr.de[0], b.trt.de[0], t, s_de, C);
-  gemm<D, C, TT>(s_de, C, w.layer[0].env.n, s_wb, [&](int m, int n, T v) { s_dx[m * LDD + n] += v; });
+  gemm<D, C, TT, C>(s_de, w.layer[0].env.n, s_wb, [&](int m, int n, T v) { s_dx[m * LDD + n] += v; });
   __syncthreads();
   {
     T du = 0.0f;
@@ -1060,12 +1114,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_bwd(ModelW w, PassBufs b) {
   }
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.dz2_tb, b.trt.dz2_tb, t, s_z2, LDD);
-  gemm<D, D, TT>(s_z2, LDD, w.tb1.n, s_wb, [&](int m, int n, T v) {
+  gemm<D, D, TT, LDD>(s_z2, w.tb1.n, s_wb, [&](int m, int n, T v) {
     s_z1[m * LDD + n] = v * silu_grad(s_z1[m * LDD + n]);
   });
   __syncthreads();
   if (b.train) dump_rows<D>(b.tr.dz1_tb, b.trt.dz1_tb, t, s_z1, LDD);
-  gemm<Cf::H0, D, TT>(s_z1, LDD, w.tb0.n, s_wb, [&](int m, int n, T v) { s_dh0[m * Cf::LDH0 + n] = v; });
+  gemm<Cf::H0, D, TT, LDD>(s_z1, w.tb0.n, s_wb, [&](int m, int n, T v) { s_dh0[m * Cf::LDH0 + n] = v; });
   __syncthreads();
   if (threadIdx.x < t.np) {
     const int q = threadIdx.x;
