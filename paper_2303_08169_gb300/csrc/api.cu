@@ -949,10 +949,15 @@ int reduce_wgrad_tangent(allegro_ctx* c, int P) {
   };
   auto plane = [](const float* pv, const float* pt) { return In{pv, pt, 1}; };
   auto dual = [](const float* p) { return In{p, p + 1, 2}; };
+  // both terms on the tensor cores (BF16 x 3 split operands, FP32 accumulation)
   auto wg = [&](const float* dzv, const float* dzt, int ldz, In x, int ldx, int N, int K, float scale, float* dW,
                 int ldw, int k0) {
-    launch_wgrad(dzt, ldz, 1, x.v, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, s);
-    launch_wgrad(dzv, ldz, 1, x.t, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, s);
+    if (wgrad_tc_supported(N, K)) {
+      launch_wgrad_tc(dzt, dzv, ldz, x.v, x.t, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, c->nb.flags, s);
+    } else {
+      launch_wgrad(dzt, ldz, 1, x.v, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, s);
+      launch_wgrad(dzv, ldz, 1, x.t, ldx * x.es, x.es, P, N, K, scale, dW, ldw, k0, part, s);
+    }
   };
   const float isD = 1.0f / std::sqrt((float)D);
   const int H0 = 2 * (int)B.S + 8;

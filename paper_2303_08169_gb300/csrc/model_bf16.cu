@@ -891,8 +891,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     mm.run([&] {
       // K-step-major over the NLM products: consecutive MMAs write different
-      // accumulators, so none waits for the one before it
+      // accumulators, so none waits for the one before it (unrolled: the
+      // K-slice offsets are compile-time constants on the issuing thread)
+#pragma unroll
       for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
         for (int j = 0; j < NLM; ++j) {
           const int l3 = l_of(j);
           if (kk < C * Cf::P(l3) / 16)
@@ -1476,6 +1479,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       if (hf == 0 || LM == 2) {
         mm.run([&] {
           if (hf == 0) mma_k<Tin>(tmem + kJ0, DVT, 0, Wmix, C * NS, 1, true, 16);
+#pragma unroll
           for (int j = 1; j < NLM; ++j) {
             const int l3 = l_of(j);
             if (LM == 2)                              // this round's eight channels

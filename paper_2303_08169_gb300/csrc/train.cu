@@ -9,6 +9,8 @@
 
 #include <algorithm>
 
+#include "umma.cuh"
+
 namespace al {
 namespace {
 
@@ -297,6 +299,174 @@ void launch_seed_energy(int B, int64_t N, const int64_t* off, const int* sid, co
   k_seed_energy<<<(int)((N + 255) / 256), 256, 0, s>>>(B, N, off, sid, dE, w_energy, seed);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core weight gradient: part[z] = scale * sum over CTA z's pairs of
+// (R_a (x) Q_a + R_b (x) Q_b), R and Q per-pair operands of nR <= 128 and
+// nQ <= 128 features, written as the [N][K] partial of the layer's dW (R the
+// dz side, rows n, when r_is_n; else the x side, rows k).  The contraction
+// over pairs is the MMA K dimension: a CTA walks its contiguous range of
+// 64-pair chunks, term a then term b of each chunk (stage s: chunk s / 2,
+// term s % 2, shared-memory buffer s % 2), and stages both operands of the
+// stage as three BF16 parts, x = hi + mid + lo (hi = rn(x), mid = rn(x - hi),
+// lo = rn(x - hi - mid): 24 significant bits).  Thread 0 issues the six
+// products whose part orders sum to at most 2 (hi hi, hi mid, mid hi, hi lo,
+// lo hi, mid mid; the dropped ones are below 2^-24 of the product) for the
+// four 16-pair K-steps into one FP32 TMEM accumulator [128 x nQp] and commits
+// to the buffer's mbarrier; the next stage's global loads are in flight
+// meanwhile, and a buffer is rewritten only after the MMAs that read it have
+// completed.  Every wait is bounded; on a timeout the CTA stops issuing,
+// raises bit 4 of *flags and writes nothing.  k_chunk_sum adds the partials
+// in CTA order, so the gradient is the same bits on every run.
+namespace wtc {
+constexpr int kPairs = 64;                            // pairs per stage (one SW128 row of BF16)
+constexpr int kThr = 512;
+constexpr uint32_t kTileR = 128 * 128;                // bytes of one 128-row part tile
+constexpr uint32_t kBuf = 6 * kTileR;                 // 3 R parts + 3 Q parts (nQp <= 128)
+constexpr size_t kSmem = 1024 + 2 * (size_t)kBuf;
+constexpr int kFlagTimeoutBit = 4;
+}  // namespace wtc
+
+struct WgOp {
+  const float* p;
+  int ld, es;                                          // element (pair q, feature f) at p[q ld + f es]
+};
+
+// 8 consecutive pairs of feature f from pair q0 (zeros past P or past nf)
+__device__ __forceinline__ void wtc_load8(const WgOp& o, int q0, int P, int f, int nf, float* v) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int q = q0 + e;
+    v[e] = (q < P && f < nf) ? __ldg(o.p + (size_t)q * o.ld + (size_t)f * o.es) : 0.0f;
+  }
+}
+
+// the three BF16 parts of v[0..7] into row f, pairs 8 g .. 8 g + 7 of the
+// part tiles base + part * tile_bytes (R rows each)
+__device__ __forceinline__ void wtc_store8(uint8_t* base, uint32_t tile_bytes, int R, int f, int g, const float* v) {
+  uint32_t w[3][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float r0 = v[2 * q], r1 = v[2 * q + 1];
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+      const float2 b = __bfloat1622float2(h);
+      r0 -= b.x;
+      r1 -= b.y;
+      memcpy(&w[part][q], &h, 4);
+    }
+  }
+  const uint32_t off = umma::sw128_off(f, 8 * g, R);
+#pragma unroll
+  for (int part = 0; part < 3; ++part)
+    *reinterpret_cast<uint4*>(base + part * tile_bytes + off) = make_uint4(w[part][0], w[part][1], w[part][2], w[part][3]);
+}
+
+__global__ void __launch_bounds__(wtc::kThr, 1)
+    k_wgrad_tc(WgOp Ra, WgOp Qa, WgOp Rb, WgOp Qb, int nR, int nQ, int nQp, int P, int chunks_per_cta,
+               int r_is_n, int K, float scale, float* __restrict__ part, int* flags, long long wait_cycles) {
+  using namespace umma;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t done[2];
+  __shared__ uint32_t tslot;
+  __shared__ int err;
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x;
+  if (tid < 32) tmem_alloc(&tslot, 128);
+  if (tid == 0) {
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    mbar_fence_init();
+    err = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  const int nchunks = (P + wtc::kPairs - 1) / wtc::kPairs;
+  const int c0 = blockIdx.x * chunks_per_cta, c1 = min(nchunks, c0 + chunks_per_cta);
+  const int nstage = 2 * max(c1 - c0, 0);
+  const uint32_t tileQ = (uint32_t)nQp * 128;
+  const uint32_t idesc = idesc_f16kind(128, nQp, false, 1);
+  // per thread: up to two R tasks and two Q tasks of 8 pairs x 1 feature
+  float va[2][8], vb[2][8];
+  auto load_stage = [&](int st) {
+    const int q0 = (c0 + st / 2) * wtc::kPairs;
+    const WgOp& R = (st & 1) ? Rb : Ra;
+    const WgOp& Q = (st & 1) ? Qb : Qa;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int t = tid + i * wtc::kThr;              // 1024 R tasks: f = t % 128, g = t / 128
+      wtc_load8(R, q0 + 8 * (t >> 7), P, t & 127, nR, va[i]);
+      const int tq = tid + i * wtc::kThr;             // nQp * 8 Q tasks: f = tq % nQp, g = tq / nQp
+      if (tq < nQp * 8) wtc_load8(Q, q0 + 8 * (tq / nQp), P, tq % nQp, nQ, vb[i]);
+    }
+  };
+  if (nstage > 0) load_stage(0);
+  int issued = -1;                                     // last stage whose MMAs were committed (thread 0)
+  for (int st = 0; st < nstage && !err; ++st) {
+    const int b = st & 1;
+    uint8_t* buf = sm + b * wtc::kBuf;
+    if (st >= 2 && !mbar_wait(&done[b], (uint32_t)(((st >> 1) - 1) & 1), wait_cycles)) err = 1;
+    __syncthreads();
+    if (err) break;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int t = tid + i * wtc::kThr;
+      wtc_store8(buf, wtc::kTileR, 128, t & 127, t >> 7, va[i]);
+      const int tq = tid + i * wtc::kThr;
+      if (tq < nQp * 8) wtc_store8(buf + 3 * wtc::kTileR, tileQ, nQp, tq % nQp, tq / nQp, vb[i]);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a = smem_u32(buf), q = smem_u32(buf + 3 * wtc::kTileR);
+      const int pi[6] = {0, 0, 1, 0, 2, 1}, pj[6] = {0, 1, 0, 2, 0, 1};
+#pragma unroll
+      for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tmem, desc_sw128(a + pi[pr] * wtc::kTileR + kk * 32), desc_sw128(q + pj[pr] * tileQ + kk * 32),
+                   idesc, (st > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&done[b]);
+      issued = st;
+    }
+    if (st + 1 < nstage) load_stage(st + 1);
+  }
+  // the last commit covers every MMA issued before it; waited for (bounded)
+  // also after an error, so that no MMA is in flight when TMEM is freed
+  if (tid == 0 && issued >= 0 && !mbar_wait(&done[issued & 1], (uint32_t)((issued >> 1) & 1), wait_cycles)) err = 1;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (!err && tid < 128) {
+    // warp w reads TMEM lanes 32 w .. 32 w + 31: accumulator row r = tid
+    const int r = tid;
+    float* out = part + (size_t)blockIdx.x * (r_is_n ? (size_t)nR * K : (size_t)nQ * K);
+    for (int q0 = 0; q0 < nQp; q0 += 16) {
+      float v[16];
+      if (nstage > 0) {
+        tmem_ld16(tmem + ((uint32_t)((tid >> 5) * 32) << 16) + (uint32_t)q0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      }
+      if (r < nR)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int qq = q0 + j;
+          if (qq < nQ) out[r_is_n ? (size_t)r * K + qq : (size_t)qq * K + r] = scale * v[j];
+        }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) tmem_dealloc(tmem, 128);
+  if (err && tid == 0) atomicOr(flags, wtc::kFlagTimeoutBit);
+}
+
 int wgrad_chunks(int P, int N, int K) {
   // about four blocks per SM over all output tiles, chunks a multiple of the
   // staging depth
@@ -316,6 +486,34 @@ void launch_wgrad(const float* dz, int ldz, int esz, const float* x, int ldx, in
   k_wgrad<<<grid, 256, 0, s>>>(dz, ldz, esz, x, ldx, esx, P, N, K, scale, part, chunk);
   k_chunk_sum<<<(N * K + 255) / 256, 256, 0, s>>>(part, nz, N, K, dW, ldw, k0);
 }
+
+void launch_wgrad_tc(const float* dza, const float* dzb, int ldz, const float* xa, const float* xb, int ldx, int esx,
+                     int P, int N, int K, float scale, float* dW, int ldw, int k0, float* part, int* flags,
+                     cudaStream_t s) {
+  if (P <= 0) return;
+  static bool init = false;
+  static int sms = 0;
+  if (!init) {
+    cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wtc::kSmem);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    init = true;
+  }
+  // rows of the accumulator: the 128-wide side (dz when N >= K)
+  const bool r_is_n = N >= K;
+  const WgOp dA{dza, ldz, 1}, dB{dzb, ldz, 1}, xA{xa, ldx, esx}, xB{xb, ldx, esx};
+  const int nR = r_is_n ? N : K, nQ = r_is_n ? K : N;
+  const int nQp = (nQ + 15) / 16 * 16;
+  const int nchunks = (P + wtc::kPairs - 1) / wtc::kPairs;
+  const int cpc = (nchunks + std::max(sms, 1) - 1) / std::max(sms, 1);
+  const int nz = (nchunks + cpc - 1) / cpc;
+  k_wgrad_tc<<<nz, wtc::kThr, wtc::kSmem, s>>>(r_is_n ? dA : xA, r_is_n ? xA : dA, r_is_n ? dB : xB, r_is_n ? xB : dB,
+                                              nR, nQ, nQp, P, cpc, r_is_n ? 1 : 0, K, scale, part, flags, 1ll << 31);
+  k_chunk_sum<<<(N * K + 255) / 256, 256, 0, s>>>(part, nz, N, K, dW, ldw, k0);
+}
+
+bool wgrad_tc_supported(int N, int K) { return N >= 1 && K >= 1 && N <= 128 && K <= 128; }
 
 void launch_wgrad_mix(const float* dV, int esv, const float* T, int P, int C, int NLM, int NT, int l, int Pl,
                       int toff, float scale, float* dW, float* part, cudaStream_t s) {

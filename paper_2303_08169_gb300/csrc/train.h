@@ -10,6 +10,17 @@ namespace al {
 // order: bitwise reproducible
 void launch_wgrad(const float* dz, int ldz, int esz, const float* x, int ldx, int esx, int P, int N, int K,
                   float scale, float* dW, int ldw, int k0, float* part, cudaStream_t s);
+// Tensor-core version for N, K <= 128 (wgrad_tc_supported), both terms of the
+// tangent weight gradient in one launch:
+//   dW[n * ldw + k0 + k] += scale * sum_p (dza[p ldz + n] xa[p ldx + k esx]
+//                                          + dzb[p ldz + n] xb[p ldx + k esx])
+// BF16 x 3 split operands (24 significant bits) with FP32 accumulation in
+// TMEM; per-CTA partials added in a fixed order (bitwise reproducible).  A
+// bounded wait that runs out raises bit 4 of *flags (ALLEGRO_E_TIMEOUT).
+void launch_wgrad_tc(const float* dza, const float* dzb, int ldz, const float* xa, const float* xb, int ldx, int esx,
+                     int P, int N, int K, float scale, float* dW, int ldw, int k0, float* part, int* flags,
+                     cudaStream_t s);
+bool wgrad_tc_supported(int N, int K);
 // mixing matrix of order l (see train.cu); dV element stride esv
 void launch_wgrad_mix(const float* dV, int esv, const float* T, int P, int C, int NLM, int NT, int l, int Pl,
                       int toff, float scale, float* dW, float* part, cudaStream_t s);
