@@ -521,6 +521,9 @@ def sam_timing(al, torch, steps=5, n_sharp=64):
     kmax = int(np.argmax(ls[1:])) + 1
     surface = al.allegro_loss_scan(ctx, b, eps[kmax], np.linspace(-1.0, 1.0, 9))
     n_pairs = al.allegro_query(ctx, al.ALLEGRO_Q_BATCH_PAIRS)
+    launch = {name: [(al.allegro_query(ctx, key) >> (4 * q)) & 15 for q in range(5)]
+              for name, key in (("value_passes", al.ALLEGRO_Q_FP32_LAUNCH),
+                                ("tangent_passes", al.ALLEGRO_Q_TANGENT_LAUNCH))}
     al.allegro_destroy(ctx)
     n_atoms = int(sum(len(s["species"]) for s in structs))
     # algorithmic work of one SAM step: two loss gradients, each the forward
@@ -539,6 +542,8 @@ def sam_timing(al, torch, steps=5, n_sharp=64):
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"}
     return {"structures": len(structs), "atoms": n_atoms, "pairs": n_pairs, "ms_per_step": 1e3 * dt,
             "steps": steps, "roofline": sam_roof,
+            "fp32_launch_waves": dict(launch, order=["A", "B", "C", "B^T", "A^T"],
+                                      note="waves of one block per SM per pass, chosen by the library's autotuner"),
             "rho": 0.05, "lr": 2e-3, "loss_first": losses[0], "loss_last": losses[-1],
             "sharpness": {"value": float(ls[1:].max() - ls[0]), "samples": n_sharp, "loss_at_w": float(ls[0]),
                           "ms_per_loss_evaluation": 1e3 * dt_scan,

@@ -388,6 +388,14 @@ int allegro_pimd_get_state(allegro_ctx* ctx, double* positions, double* velociti
 #define ALLEGRO_Q_RP_STEP_KERNELS 5  /* kernel launches in one ring-polymer step */
 #define ALLEGRO_Q_BATCH_PAIRS  6  /* ordered pairs of the last training batch     */
 #define ALLEGRO_Q_REBUILDS     7  /* skin: neighbour builds since allegro_md_init  */
+/* Launch shapes the autotuner chose for the FP32 pass kernels (value passes;
+ * tangent passes of the training step): 4 bits per pass in the order A, B, C,
+ * B^T, A^T from the lowest, each the number of waves of one block per SM
+ * (1, 2, 4 or 8; 8 before the first tuning).  Tuning runs on the first FP32
+ * evaluation of a context (and again when the pair capacity has more than
+ * doubled); the results do not depend on the launch shape. */
+#define ALLEGRO_Q_FP32_LAUNCH   8
+#define ALLEGRO_Q_TANGENT_LAUNCH 9
 
 /* Read one integer property of the context into *value (host). */
 int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value);

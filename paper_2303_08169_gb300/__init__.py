@@ -45,6 +45,8 @@ ALLEGRO_Q_N_PARAMS = 4
 ALLEGRO_Q_RP_STEP_KERNELS = 5
 ALLEGRO_Q_BATCH_PAIRS = 6
 ALLEGRO_Q_REBUILDS = 7
+ALLEGRO_Q_FP32_LAUNCH = 8
+ALLEGRO_Q_TANGENT_LAUNCH = 9
 
 
 class _Batch(ctypes.Structure):

@@ -174,6 +174,10 @@ struct allegro_ctx {
   double* tepart = nullptr;
   float* wpart = nullptr;
   int64_t tr_rows = 0;
+  // launch shapes of the FP32 passes chosen by the autotuner: [0] value
+  // passes, [1] tangent passes; tuned for capacities up to fl_cap[i]
+  Fp32Launch fl[2];
+  int64_t fl_cap[2] = {0, 0};
   cudaStream_t stream = nullptr;
   Blob blob;
   double mass[2] = {14.007, 1.008};
@@ -764,6 +768,58 @@ bool valid_precision(int32_t p) {
   return p == ALLEGRO_FP32 || p == ALLEGRO_BF16 || p == ALLEGRO_FP16 || p == ALLEGRO_FP16_SPLIT;
 }
 
+// Launch-shape autotuner of the FP32 pass kernels (value passes: which = 0,
+// tangent passes: which = 1).  run(ls, km) enqueues one whole pass sequence
+// with launch shape ls and phase marks km.  For each candidate (1, 2, 4 or 8
+// waves of one block per SM for every pass) the sequence runs twice; each
+// pass takes the candidate of its shortest measured time.  The passes write
+// the same bits for every launch shape (every tile's work is fixed), so the
+// tuning runs leave the sequence's outputs as one run would; tuned again when
+// the pair capacity has grown past twice the tuned one.  Not called while a
+// stream is being captured (it synchronises).
+template <class Run>
+int autotune_fp32(allegro_ctx* c, int which, Run&& run) {
+  if (c->fl_cap[which] > 0 && c->capacity <= 2 * c->fl_cap[which]) return ALLEGRO_OK;
+  static const int kCand[4] = {1, 2, 4, 8};
+  KernelMarks km;
+  for (auto& e : km.ev) cudaEventCreate(&e);
+  double best[kPhCount];
+  int pick[kPhCount];
+  for (int k = 0; k < kPhCount; ++k) {
+    best[k] = 1e30;
+    pick[k] = 8;
+  }
+  int rc = ALLEGRO_OK;
+  for (int rep = 0; rep < 2 && !rc; ++rep)
+    for (int ci = 0; ci < 4 && !rc; ++ci) {
+      Fp32Launch ls;
+      for (int k = 0; k < kPhCount; ++k) ls.waves[k] = kCand[ci];
+      km.n = 0;
+      run(&ls, &km);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        rc = cuda_check(c, "launch-shape tuning");
+        break;
+      }
+      double ms_k[kPhCount] = {};
+      for (int i = 0; i + 1 < km.n; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, km.ev[i], km.ev[i + 1]);
+        const int kd = km.kind[i + 1];
+        if (kd >= 0 && kd < kPhCount) ms_k[kd] += ms;
+      }
+      for (int k = 0; k < kPhCount; ++k)
+        if (ms_k[k] > 0.0 && ms_k[k] < best[k]) {
+          best[k] = ms_k[k];
+          pick[k] = kCand[ci];
+        }
+    }
+  for (auto& e : km.ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (int k = 0; k < kPhCount; ++k) c->fl[which].waves[k] = pick[k];
+  c->fl_cap[which] = std::max<int64_t>(c->capacity, 1);
+  return ALLEGRO_OK;
+}
+
 // Pair passes of the requested precision followed by force assembly.
 void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, KernelMarks* km) {
   const Blob& B = c->blob;
@@ -778,7 +834,7 @@ void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, KernelMarks
     bf16_energy_forces(c->sw, c->pb, c->capacity, s, km, TcMode::kFp16Split);
     tile = bf16_tile();
   } else {
-    if (c->pb_fp32) fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km);
+    if (c->pb_fp32) fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km, &c->fl[0]);
     else c->fp32_bad = true;
     tile = fp32_tile();
   }
@@ -799,6 +855,13 @@ int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
     if (rc) return rc;
   }
   fill_passbufs(c, L);
+  if (precision == ALLEGRO_FP32 && c->pb_fp32) {
+    const Blob& B = c->blob;
+    const int rc = autotune_fp32(c, 0, [&](const Fp32Launch* ls, KernelMarks* km) {
+      fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, c->stream, km, ls);
+    });
+    if (rc) return rc;
+  }
   launch_model(c, precision, c->stream, nullptr);
   return cuda_check(c, "model launch");
 }
@@ -1133,7 +1196,11 @@ int batch_tangent_eval(allegro_ctx* c) {
   pb.trt = c->trt;
   pb.train = 1;
   pb.vdir = t.v;
-  fp32_tangent_passes((int)B.lmax, (int)B.C, c->D, c->E, c->w, pb, c->capacity, c->stream);
+  int rc = autotune_fp32(c, 1, [&](const Fp32Launch* ls, KernelMarks* km) {
+    fp32_tangent_passes((int)B.lmax, (int)B.C, c->D, c->E, c->w, pb, c->capacity, c->stream, km, ls);
+  });
+  if (rc) return rc;
+  fp32_tangent_passes((int)B.lmax, (int)B.C, c->D, c->E, c->w, pb, c->capacity, c->stream, nullptr, &c->fl[1]);
   c->pb.atomL = nullptr;
   return reduce_wgrad_tangent(c, (int)t.n_pairs);
 }
@@ -1148,8 +1215,14 @@ void batch_forward_loss(allegro_ctx* c, double w_energy, double w_force) {
   const int64_t N = t.n_atoms;
   const double cf = w_force / (3.0 * (double)N);
   fill_batch_passbufs(c, t.a.wpos);
-  if (c->pb_fp32) fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s);
-  else c->fp32_bad = true;
+  if (c->pb_fp32) {
+    autotune_fp32(c, 0, [&](const Fp32Launch* ls, KernelMarks* km) {
+      fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km, ls);
+    });
+    fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, nullptr, &c->fl[0]);
+  } else {
+    c->fp32_bad = true;
+  }
   AtomArgs aa = atom_args(c);
   aa.n = (int)N;
   aa.species = t.a.species;
@@ -1933,6 +2006,15 @@ int allegro_query(allegro_ctx* ctx, int32_t what, int64_t* value) {
     case ALLEGRO_Q_N_ATOMS: *value = ctx->n_atoms; return ALLEGRO_OK;
     case ALLEGRO_Q_N_PARAMS: *value = ctx->n_params; return ALLEGRO_OK;
     case ALLEGRO_Q_BATCH_PAIRS: *value = ctx->bt.n_pairs; return ALLEGRO_OK;
+    case ALLEGRO_Q_FP32_LAUNCH:
+    case ALLEGRO_Q_TANGENT_LAUNCH: {
+      const Fp32Launch& f = ctx->fl[what == ALLEGRO_Q_FP32_LAUNCH ? 0 : 1];
+      const int kinds[5] = {kPhA, kPhB, kPhC, kPhBT, kPhAT};
+      int64_t v = 0;
+      for (int q = 0; q < 5; ++q) v |= (int64_t)f.waves[kinds[q]] << (4 * q);
+      *value = v;
+      return ALLEGRO_OK;
+    }
     case ALLEGRO_Q_REBUILDS: {
       int f[4] = {0, 0, 0, 0};
       if (ctx->d_skin_flag) {

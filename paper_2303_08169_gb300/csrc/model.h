@@ -152,13 +152,23 @@ enum class TcMode { kBf16, kFp16, kFp16Split };
 void bf16_energy_forces(const BfW& w, const PassBufs& b, int64_t capacity, cudaStream_t s,
                         KernelMarks* km, TcMode mode);
 
+// Launch shape of the FP32 pass kernels: pass kind k (kPhA, kPhB, kPhC,
+// kPhBT, kPhAT) runs min(tiles of the capacity, waves[k] x SMs) blocks, each
+// looping over tiles.  Every tile's arithmetic and its partial rows are fixed
+// by the tile, so the results are the same bits for every launch shape; the
+// autotuner of api.cu picks the fastest from measured times.
+struct Fp32Launch {
+  int waves[kPhCount] = {8, 8, 8, 8, 8, 8};
+};
+
 // FP32 path: one launcher per pass sequence; templated on the model shape in
 // the .cu file, dispatched by (lmax, C, D, E).
 bool fp32_supported(int lmax, int C, int D, int E);
-// ev (optional, 6 events): recorded before pass A, after A, after the B
-// passes, after C, after the B^T passes and after A^T.
+// km (optional): events recorded at the phase boundaries; ls (optional):
+// launch shape (default eight waves for every pass).
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
-                        int64_t capacity, cudaStream_t s, KernelMarks* km = nullptr);
+                        int64_t capacity, cudaStream_t s, KernelMarks* km = nullptr,
+                        const Fp32Launch* ls = nullptr);
 int fp32_tile();
 // Tangent passes of the second-order adjoint: the FP32 pass sequence in
 // tangent numbers (value and derivative along the position direction b.vdir),
@@ -168,6 +178,6 @@ int fp32_tile();
 // 1-layer tiny model and the 2-layer main model.
 int fp32_tangent_tile();
 void fp32_tangent_passes(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b, int64_t capacity,
-                         cudaStream_t s);
+                         cudaStream_t s, KernelMarks* km = nullptr, const Fp32Launch* ls = nullptr);
 
 }  // namespace al

@@ -1166,11 +1166,17 @@ struct Smem {
                 "shared memory per block");
 };
 
+int g_sms_fp32 = 0;
+
 template <class Cf, class X, int TT>
-void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km) {
+void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, KernelMarks* km,
+         const Fp32Launch* ls) {
   using Sm = Smem<Cf, X, TT>;
   static bool init = false;
   if (!init) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_fp32, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_pass_a<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::a);
     cudaFuncSetAttribute(k_pass_b<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::b);
     cudaFuncSetAttribute(k_pass_c<Cf, X, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::c);
@@ -1179,27 +1185,31 @@ void run(const ModelW& w, const PassBufs& b, int64_t capacity, cudaStream_t s, K
     init = true;
   }
   // blocks loop over the tiles of the list (the pair count is known on the
-  // device only): eight waves of one resident block per SM, or one block per
-  // tile of the capacity if that is fewer
-  const int grid = (int)std::min<int64_t>((capacity + TT - 1) / TT, 152 * 8);
+  // device only): waves[k] waves of one resident block per SM (eight by
+  // default), or one block per tile of the capacity if that is fewer
+  const Fp32Launch dflt;
+  const Fp32Launch& sh = ls ? *ls : dflt;
+  const int64_t tiles = (capacity + TT - 1) / TT;
+  const int sms = g_sms_fp32 > 0 ? g_sms_fp32 : 152;
+  auto grid_of = [&](int k) { return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sh.waves[k] * sms)); };
   const int L = w.n_layers;
   auto mark = [&](int k) {
     if (km) km->mark(k, s);
   };
   mark(kPhStart);
-  k_pass_a<Cf, X, TT><<<grid, kThreads, Sm::a, s>>>(w, b);
+  k_pass_a<Cf, X, TT><<<grid_of(kPhA), kThreads, Sm::a, s>>>(w, b);
   mark(kPhA);
   for (int k = 1; k < L; ++k) {
-    k_pass_b<Cf, X, TT><<<grid, kThreads, Sm::b, s>>>(w, b, k);
+    k_pass_b<Cf, X, TT><<<grid_of(kPhB), kThreads, Sm::b, s>>>(w, b, k);
     mark(kPhB);
   }
-  k_pass_c<Cf, X, TT><<<grid, kThreads, Sm::c, s>>>(w, b);
+  k_pass_c<Cf, X, TT><<<grid_of(kPhC), kThreads, Sm::c, s>>>(w, b);
   mark(kPhC);
   for (int k = L - 1; k >= 1; --k) {
-    k_pass_b_bwd<Cf, X, TT><<<grid, kThreads, Sm::bb, s>>>(w, b, k);
+    k_pass_b_bwd<Cf, X, TT><<<grid_of(kPhBT), kThreads, Sm::bb, s>>>(w, b, k);
     mark(kPhBT);
   }
-  k_pass_a_bwd<Cf, X, TT><<<grid, kThreads, Sm::ab, s>>>(w, b);
+  k_pass_a_bwd<Cf, X, TT><<<grid_of(kPhAT), kThreads, Sm::ab, s>>>(w, b);
   mark(kPhAT);
 }
 
@@ -1218,19 +1228,19 @@ bool fp32_supported(int lmax, int C, int D, int E) {
 }
 
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
-                        int64_t capacity, cudaStream_t s, KernelMarks* km) {
-  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny, float, kTile>(w, b, capacity, s, km);
-  else if (lmax == 0) run<CfgMainL0, float, kTile>(w, b, capacity, s, km);
-  else if (lmax == 1) run<CfgMainL1, float, kTile>(w, b, capacity, s, km);
-  else run<CfgMain, float, kTile>(w, b, capacity, s, km);
+                        int64_t capacity, cudaStream_t s, KernelMarks* km, const Fp32Launch* ls) {
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny, float, kTile>(w, b, capacity, s, km, ls);
+  else if (lmax == 0) run<CfgMainL0, float, kTile>(w, b, capacity, s, km, ls);
+  else if (lmax == 1) run<CfgMainL1, float, kTile>(w, b, capacity, s, km, ls);
+  else run<CfgMain, float, kTile>(w, b, capacity, s, km, ls);
 }
 
 int fp32_tangent_tile() { return kTileDual; }
 
 void fp32_tangent_passes(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b, int64_t capacity,
-                         cudaStream_t s) {
-  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny, Dual, kTileDual>(w, b, capacity, s, nullptr);
-  else if (lmax == 2 && C == 16 && D == 128 && E == 32) run<CfgMain, Dual, kTileDual>(w, b, capacity, s, nullptr);
+                         cudaStream_t s, KernelMarks* km, const Fp32Launch* ls) {
+  if (lmax == 1 && C == 8 && D == 32 && E == 32) run<CfgTiny, Dual, kTileDual>(w, b, capacity, s, km, ls);
+  else if (lmax == 2 && C == 16 && D == 128 && E == 32) run<CfgMain, Dual, kTileDual>(w, b, capacity, s, km, ls);
 }
 
 }  // namespace al

@@ -202,3 +202,36 @@ def test_full_o3_two_layer_blob():
     Er, Fr, Eir, _ = orc.energy_forces(pos, sp, np.diag(cell))
     _compare(E, F, Ei, Er, Fr, Eir)
     assert np.abs(Fs - Fr).max() <= 2e-3
+
+
+def _waves(v):
+    return [(v >> (4 * q)) & 15 for q in range(5)]
+
+
+def test_launch_shape_autotuner_keeps_the_bits():
+    """The FP32 passes take their launch shapes (waves of one block per SM,
+    per pass) from the autotuner, tuned on the first evaluation of a
+    context.  A context tuned and sized on the 110,592-atom system and one
+    tuned on the 432-atom system launch the 432-atom evaluation with
+    different grids; energies, per-atom energies and forces must agree
+    bitwise (every tile's work and partial rows are fixed by the tile)."""
+    cfg, blob = _blob("main")
+    pos, sp, cell = synth.make_ammonia(108, 2)
+    bpos, bsp, bcell = synth.make_ammonia(27648, 0)
+    ctx2 = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        _gpu(ctx2, bpos, bsp, bcell)
+        E2, F2, Ei2 = _gpu(ctx2, pos, sp, cell)
+        w2 = al.allegro_query(ctx2, al.ALLEGRO_Q_FP32_LAUNCH)
+    finally:
+        al.allegro_destroy(ctx2)
+    ctx1 = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        E1, F1, Ei1 = _gpu(ctx1, pos, sp, cell)
+        w1 = al.allegro_query(ctx1, al.ALLEGRO_Q_FP32_LAUNCH)
+    finally:
+        al.allegro_destroy(ctx1)
+    print("tuned waves (A, B, C, B^T, A^T):", _waves(w1), _waves(w2))
+    for w in (w1, w2):
+        assert all(x in (1, 2, 4, 8) for x in _waves(w))
+    assert E1 == E2 and np.array_equal(F1, F2) and np.array_equal(Ei1, Ei2)

@@ -87,6 +87,9 @@ def test_loss_and_gradient_match_oracle(setup):
     gd = torch.zeros(len(gref), dtype=torch.float32, device="cuda")   # device output buffer
     al.allegro_loss_grad(ctx, b, 1.0, 100.0, gd)
     assert np.array_equal(gd.cpu().numpy(), g)  # bitwise rerun: no atomics in the reductions
+    for key in (al.ALLEGRO_Q_FP32_LAUNCH, al.ALLEGRO_Q_TANGENT_LAUNCH):   # launch shapes of the autotuner
+        v = al.allegro_query(ctx, key)
+        assert all(((v >> (4 * q)) & 15) in (1, 2, 4, 8) for q in range(5))
 
 
 def test_sam_step_matches_oracle(setup):
