@@ -294,3 +294,35 @@ def test_tensorcore_wait_timeout_is_reported(main):
     al.allegro_set_md_precision(ctx, al.ALLEGRO_FP32)
     E1, F1, _ = _gpu(ctx, pos, sp, cell, al.ALLEGRO_FP16_SPLIT)
     assert E1 == E0 and np.array_equal(F1, F0)
+
+
+@pytest.mark.parametrize("l_max", [0, 1, 2])
+def test_tensorcore_degenerate_lists(l_max):
+    """Edge cases of the tensor-core passes at every l_max, split mode: an
+    empty pair list (atoms farther apart than r_cut) and a single atom give
+    E_i = mu_Z and zero forces exactly; a lone N-H pair (two ordered pairs:
+    one tile with two valid rows of 128) and a pair straddling the periodic
+    boundary match the exact oracle within the 2e-3 eV/A bound."""
+    cfg = _lmax_cfg(l_max)
+    blob = synth.make_blob(cfg, 42, sigma=energy_scale("main"))
+    orc = OracleModel(blob)
+    cell = np.diag([30.0, 30.0, 30.0])
+    L = np.diag(cell)
+    ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        far = np.array([[1.0, 1.0, 1.0], [8.0, 1.0, 1.0], [1.0, 9.5, 20.0]])
+        for p, s in ((far, np.array([0, 1, 1])), (far[:1], np.array([0]))):
+            E, F, Ei = _gpu(ctx, p, s, cell, al.ALLEGRO_FP16_SPLIT)
+            Er, Fr, Eir, pairs = orc.energy_forces(p, s, L)
+            assert len(pairs[0]) == 0 and al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS) == 0
+            assert E == Er and np.array_equal(Ei, Eir) and not np.any(F)
+        for p in (np.array([[10.0, 10.0, 10.0], [10.6, 10.8, 10.3]]),      # N-H at 1.04 A
+                  np.array([[0.3, 15.0, 15.0], [29.4, 15.5, 15.2]])):      # across the boundary
+            s = np.array([0, 1])
+            E, F, Ei = _gpu(ctx, p, s, cell, al.ALLEGRO_FP16_SPLIT)
+            Er, Fr, Eir, pairs = orc.energy_forces(p, s, L)
+            assert len(pairs[0]) == 2 and al.allegro_query(ctx, al.ALLEGRO_Q_N_PAIRS) == 2
+            assert np.abs(F - Fr).max() <= FORCE_BOUND and np.abs(F.sum(0)).max() <= 1e-5
+            assert abs(E - Er) <= 2e-3 * max(1.0, abs(Er))
+    finally:
+        al.allegro_destroy(ctx)
