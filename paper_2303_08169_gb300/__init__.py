@@ -118,23 +118,40 @@ def lib():
     return L
 
 
-def _ptr(x):
-    """Raw address of a numpy array / torch tensor (None -> NULL)."""
+def _ptr(x, dtype=None, count=None, name="array"):
+    """Raw address of a numpy array / torch tensor (None -> NULL).  The
+    library takes typed pointers without sizes, so the element type (dtype:
+    'float64', 'float32', 'int32', 'int64', 'int8') and, where given, the
+    number of elements are checked here: a mismatch raises instead of being
+    reinterpreted by the library."""
     if x is None:
         return None
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
-            raise ValueError("arrays must be C-contiguous")
-        return x.ctypes.data
-    if hasattr(x, "data_ptr"):
+            raise ValueError(f"{name}: arrays must be C-contiguous")
+        kind, size, addr = str(x.dtype), int(x.size), x.ctypes.data
+    elif hasattr(x, "data_ptr"):
         if not x.is_contiguous():
-            raise ValueError("tensors must be contiguous")
-        return x.data_ptr()
-    raise TypeError(f"unsupported array type {type(x)}")
+            raise ValueError(f"{name}: tensors must be contiguous")
+        kind, size, addr = str(x.dtype).replace("torch.", ""), int(x.numel()), x.data_ptr()
+    else:
+        raise TypeError(f"{name}: unsupported array type {type(x)}")
+    if dtype is not None and kind != dtype:
+        raise TypeError(f"{name}: element type {kind}, expected {dtype}")
+    if count is not None and size != count:
+        raise ValueError(f"{name}: {size} elements, expected {count}")
+    return addr
 
 
 def _host(x, dtype):
     return None if x is None else np.ascontiguousarray(x, dtype=dtype)
+
+
+def _in(x, dtype):
+    """An input array: a host numpy array is converted to dtype (the library
+    copies host inputs anyway); a device tensor is passed as it is and its
+    element type is checked by _ptr."""
+    return np.ascontiguousarray(x, dtype=dtype) if isinstance(x, np.ndarray) else x
 
 
 def _check(ctx, rc):
@@ -169,46 +186,58 @@ def allegro_set_stream(ctx, stream):
 
 
 def allegro_build_neighbors(ctx, positions, cell):
+    positions = _in(positions, np.float64)
     n = int(positions.shape[0])
     cell = _host(cell, np.float64)
     np_ = _i64()
-    _check(ctx, lib().allegro_build_neighbors(ctx, n, _ptr(positions), _ptr(cell), ctypes.byref(np_)))
+    _check(ctx, lib().allegro_build_neighbors(ctx, n, _ptr(positions, "float64", 3 * n, "positions"), _ptr(cell),
+                                              ctypes.byref(np_)))
     return np_.value
 
 
 def allegro_get_neighbors(ctx, row_ptr=None, col=None, img=None, rev=None):
-    _check(ctx, lib().allegro_get_neighbors(ctx, _ptr(row_ptr), _ptr(col), _ptr(img), _ptr(rev)))
+    _check(ctx, lib().allegro_get_neighbors(ctx, _ptr(row_ptr, "int32", name="row_ptr"), _ptr(col, "int32", name="col"),
+                                            _ptr(img, "int8", name="img"), _ptr(rev, "int32", name="rev")))
 
 
 def allegro_energy_forces(ctx, positions, species, cell, forces_out=None, atom_energy=None,
                           precision=ALLEGRO_FP32):
+    positions, species = _in(positions, np.float64), _in(species, np.int32)
     n = int(positions.shape[0])
     cell = _host(cell, np.float64)
     e = _f64()
-    _check(ctx, lib().allegro_energy_forces(ctx, n, _ptr(positions), _ptr(species), _ptr(cell), ctypes.byref(e),
-                                            _ptr(forces_out), _ptr(atom_energy), int(precision)))
+    _check(ctx, lib().allegro_energy_forces(ctx, n, _ptr(positions, "float64", 3 * n, "positions"),
+                                            _ptr(species, "int32", n, "species"), _ptr(cell), ctypes.byref(e),
+                                            _ptr(forces_out, "float32", 3 * n, "forces_out"),
+                                            _ptr(atom_energy, "float64", n, "atom_energy"), int(precision)))
     return e.value
 
 
 def allegro_outlier_count(ctx, forces, threshold=5.0):
+    forces = _in(forces, np.float32)
     c = _i64()
-    _check(ctx, lib().allegro_outlier_count(ctx, int(forces.shape[0]), _ptr(forces), float(threshold),
+    n = int(forces.shape[0])
+    _check(ctx, lib().allegro_outlier_count(ctx, n, _ptr(forces, "float32", 3 * n, "forces"), float(threshold),
                                             ctypes.byref(c)))
     return c.value
 
 
 def allegro_md_init(ctx, positions, velocities, species, cell):
+    positions, velocities, species = _in(positions, np.float64), _in(velocities, np.float64), _in(species, np.int32)
     cell = _host(cell, np.float64)
-    _check(ctx, lib().allegro_md_init(ctx, int(positions.shape[0]), _ptr(positions), _ptr(velocities),
-                                      _ptr(species), _ptr(cell)))
+    n = int(positions.shape[0])
+    _check(ctx, lib().allegro_md_init(ctx, n, _ptr(positions, "float64", 3 * n, "positions"),
+                                      _ptr(velocities, "float64", 3 * n, "velocities"),
+                                      _ptr(species, "int32", n, "species"), _ptr(cell)))
 
 
 def allegro_outlier_count_noalloc(forces, threshold, count_out, stream=None):
     """Outlier count into the device int64 count_out, with no device
     allocation (see include/allegro.h); enqueued on stream, not synchronised."""
     handle = getattr(stream, "cuda_stream", stream)
-    _check(None, lib().allegro_outlier_count_noalloc(int(forces.shape[0]), _ptr(forces), float(threshold),
-                                                     _ptr(count_out), handle))
+    n = int(forces.shape[0])
+    _check(None, lib().allegro_outlier_count_noalloc(n, _ptr(forces, "float32", 3 * n, "forces"), float(threshold),
+                                                     _ptr(count_out, "int64", 1, "count_out"), handle))
 
 
 def make_batch(structs):
@@ -231,7 +260,7 @@ def make_batch(structs):
 def allegro_loss_grad(ctx, batch, w_energy=1.0, w_force=100.0, grad_out=None):
     loss = _f64()
     _check(ctx, lib().allegro_loss_grad(ctx, ctypes.byref(batch), float(w_energy), float(w_force),
-                                        ctypes.byref(loss), _ptr(grad_out)))
+                                        ctypes.byref(loss), _ptr(grad_out, "float32", name="grad_out")))
     return loss.value
 
 
@@ -251,17 +280,18 @@ def allegro_loss_scan(ctx, batch, dirs, scales, w_energy=1.0, w_force=100.0):
         raise ValueError("one direction per scale, or one direction for all")
     out = np.zeros(scales.shape[0], dtype=np.float64)
     d = dirs.contiguous()                             # kept alive across the call
-    _check(ctx, lib().allegro_loss_scan(ctx, ctypes.byref(batch), _ptr(d), stride, _ptr(scales),
+    _check(ctx, lib().allegro_loss_scan(ctx, ctypes.byref(batch), _ptr(d, "float32", name="dirs"), stride, _ptr(scales),
                                         int(scales.shape[0]), float(w_energy), float(w_force), _ptr(out)))
     return out
 
 
 def allegro_get_weights(ctx, out):
-    _check(ctx, lib().allegro_get_weights(ctx, _ptr(out), int(out.shape[0])))
+    _check(ctx, lib().allegro_get_weights(ctx, _ptr(out, "float32", name="out"), int(out.shape[0])))
 
 
 def allegro_set_weights(ctx, w):
-    _check(ctx, lib().allegro_set_weights(ctx, _ptr(w), int(w.shape[0])))
+    w = _in(w, np.float32)
+    _check(ctx, lib().allegro_set_weights(ctx, _ptr(w, "float32", name="weights"), int(w.shape[0])))
 
 
 def allegro_set_md_precision(ctx, precision):
@@ -269,13 +299,17 @@ def allegro_set_md_precision(ctx, precision):
 
 
 def allegro_md_step_nve(ctx, dt_fs, n_steps, outlier_counts=None, energies=None):
-    _check(ctx, lib().allegro_md_step_nve(ctx, float(dt_fs), int(n_steps), _ptr(outlier_counts), _ptr(energies)))
+    n = int(n_steps)
+    _check(ctx, lib().allegro_md_step_nve(ctx, float(dt_fs), n, _ptr(outlier_counts, "int64", n, "outlier_counts"),
+                                          _ptr(energies, "float64", 3 * n, "energies")))
 
 
 def allegro_md_step_nvt(ctx, dt_fs, n_steps, temperature_K, tau_fs, outlier_counts=None, energies=None):
     """energies: (n_steps, 4) FP64 (E_pot, E_kin, E_tot, H) or None."""
-    _check(ctx, lib().allegro_md_step_nvt(ctx, float(dt_fs), int(n_steps), float(temperature_K), float(tau_fs),
-                                          _ptr(outlier_counts), _ptr(energies)))
+    n = int(n_steps)
+    _check(ctx, lib().allegro_md_step_nvt(ctx, float(dt_fs), n, float(temperature_K), float(tau_fs),
+                                          _ptr(outlier_counts, "int64", n, "outlier_counts"),
+                                          _ptr(energies, "float64", 4 * n, "energies")))
 
 
 def allegro_md_get_thermostat(ctx):
@@ -287,23 +321,29 @@ def allegro_md_get_thermostat(ctx):
 
 def allegro_pimd_init(ctx, positions, velocities, species, cell, temperature_K):
     """positions, velocities: (P, N, 3) FP64 (host or device); species (N,)."""
+    positions, velocities, species = _in(positions, np.float64), _in(velocities, np.float64), _in(species, np.int32)
     cell = _host(cell, np.float64)
-    _check(ctx, lib().allegro_pimd_init(ctx, int(positions.shape[0]), int(positions.shape[1]), _ptr(positions),
-                                        _ptr(velocities), _ptr(species), _ptr(cell), float(temperature_K)))
+    P, n = int(positions.shape[0]), int(positions.shape[1])
+    _check(ctx, lib().allegro_pimd_init(ctx, P, n, _ptr(positions, "float64", 3 * P * n, "positions"),
+                                        _ptr(velocities, "float64", 3 * P * n, "velocities"),
+                                        _ptr(species, "int32", n, "species"), _ptr(cell), float(temperature_K)))
 
 
 def allegro_pimd_step(ctx, dt_fs, n_steps, energies=None):
     """energies: (n_steps, 3) FP64 (mean replica energy, kinetic, H_P) or None."""
-    _check(ctx, lib().allegro_pimd_step(ctx, float(dt_fs), int(n_steps), _ptr(energies)))
+    _check(ctx, lib().allegro_pimd_step(ctx, float(dt_fs), int(n_steps), _ptr(energies, "float64", 3 * int(n_steps), "energies")))
 
 
 def allegro_pimd_get_state(ctx, positions=None, velocities=None):
-    _check(ctx, lib().allegro_pimd_get_state(ctx, _ptr(positions), _ptr(velocities)))
+    _check(ctx, lib().allegro_pimd_get_state(ctx, _ptr(positions, "float64", name="positions"),
+                                             _ptr(velocities, "float64", name="velocities")))
 
 
 def allegro_md_get_state(ctx, positions=None, velocities=None, forces=None):
     s = _i64()
-    _check(ctx, lib().allegro_md_get_state(ctx, _ptr(positions), _ptr(velocities), _ptr(forces), ctypes.byref(s)))
+    _check(ctx, lib().allegro_md_get_state(ctx, _ptr(positions, "float64", name="positions"),
+                                           _ptr(velocities, "float64", name="velocities"),
+                                           _ptr(forces, "float32", name="forces"), ctypes.byref(s)))
     return s.value
 
 

@@ -80,6 +80,33 @@ def test_full_o3_blobs_on_host(built):
     assert e.value.code == 11
 
 
+def test_binding_checks_element_types_and_counts(built):
+    """The C entry points take typed pointers without sizes: the binding
+    converts host input arrays to the declared element type and rejects a
+    device tensor (here a CPU tensor, checked before any library call) or an
+    output of the wrong type or size, instead of letting the library
+    reinterpret it (an int64 species array read as int32 makes every other
+    atom species 0)."""
+    import torch
+    pos = np.zeros((4, 3))
+    with pytest.raises(TypeError):
+        al.allegro_energy_forces(None, torch.zeros((4, 3), dtype=torch.float64),
+                                 torch.zeros(4, dtype=torch.int64), np.eye(3) * 20.0)
+    with pytest.raises(TypeError):
+        al.allegro_energy_forces(None, pos, np.zeros(4, np.int32), np.eye(3) * 20.0,
+                                 torch.zeros((4, 3), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        al.allegro_energy_forces(None, pos, np.zeros(4, np.int32), np.eye(3) * 20.0,
+                                 np.zeros((3, 3), np.float32))
+    with pytest.raises(ValueError):
+        al.allegro_md_init(None, pos, np.zeros((4, 3)), torch.zeros(5, dtype=torch.int32), np.eye(3) * 20.0)
+    # host inputs of another type are converted; the NULL context is then
+    # rejected by the library itself
+    with pytest.raises(al.AllegroError) as e:
+        al.allegro_energy_forces(None, pos.astype(np.float32), np.zeros(4, np.int64), np.eye(3) * 20.0)
+    assert e.value.code == 1
+
+
 def test_null_arguments(built):
     out = ctypes.c_void_p()
     rc = built.allegro_create(None, 0, None, 2, 4.0, 1, 1, ctypes.byref(out))

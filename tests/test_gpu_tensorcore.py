@@ -64,7 +64,8 @@ def _gpu(ctx, pos, sp, cell, prec):
     N = len(pos)
     F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
     Ei = torch.empty(N, dtype=torch.float64, device="cuda")
-    E = al.allegro_energy_forces(ctx, torch.tensor(pos, device="cuda"), torch.tensor(sp, device="cuda"), cell,
+    E = al.allegro_energy_forces(ctx, torch.tensor(pos, device="cuda", dtype=torch.float64),
+                                 torch.tensor(sp, device="cuda", dtype=torch.int32), cell,
                                  F, Ei, prec)
     return E, F.cpu().numpy().astype(np.float64), Ei.cpu().numpy()
 
