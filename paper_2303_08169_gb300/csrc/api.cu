@@ -1041,8 +1041,14 @@ int reduce_wgrad_tangent(allegro_ctx* c, int P) {
         const int Pl = tp_pl((int)B.lmax, l), toff = tp_toff((int)B.lmax, l);
         const float sc = 1.0f / std::sqrt((float)(C * Pl));
         float* dW = g(pre + "mix" + std::to_string(l));
-        launch_wgrad_mix(c->tdV + 1, 2, v.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part, s);   // dV.t (x) T.v
-        launch_wgrad_mix(c->tdV, 2, t.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part, s);       // dV.v (x) T.t
+        if (wgrad_tc_supported(C, C * Pl) && (int64_t)P * (2 * l + 1) < (1ll << 31) - 1024) {
+          // dV.t (x) T.v + dV.v (x) T.t on the tensor cores, over (pair, m)
+          launch_wgrad_mix_tc(c->tdV + 1, c->tdV, 2, v.T[k], t.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part,
+                              c->nb.flags, s);
+        } else {
+          launch_wgrad_mix(c->tdV + 1, 2, v.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part, s);   // dV.t (x) T.v
+          launch_wgrad_mix(c->tdV, 2, t.T[k], P, C, NLM, NT, l, Pl, toff, sc, dW, part, s);       // dV.v (x) T.t
+        }
       }
   }
   wg(v.dze, t.dze, E, plane(v.xL, t.xL), D, E, D, isD, g("energy.0"), D, 0);

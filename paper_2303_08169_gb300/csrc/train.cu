@@ -311,8 +311,11 @@ void launch_seed_energy(int B, int64_t N, const int64_t* off, const int* sid, co
 // lo = rn(x - hi - mid): 24 significant bits).  Thread 0 issues the six
 // products whose part orders sum to at most 2 (hi hi, hi mid, mid hi, hi lo,
 // lo hi, mid mid; the dropped ones are below 2^-24 of the product) for the
-// four 16-pair K-steps into one FP32 TMEM accumulator [128 x nQp] and commits
-// to the buffer's mbarrier; the next stage's global loads are in flight
+// four 16-pair K-steps into an FP32 TMEM accumulator [128 x nQp] (stage s
+// into accumulator s % 4, the four added at the end: the tensor pipe's FP32
+// accumulation loses low bits as a chain grows, so the chains are kept four
+// times shorter) and commits to the buffer's mbarrier; the next stage's
+// global loads are in flight
 // meanwhile, and a buffer is rewritten only after the MMAs that read it have
 // completed.  Every wait is bounded; on a timeout the CTA stops issuing,
 // raises bit 4 of *flags and writes nothing.  k_chunk_sum adds the partials
@@ -324,19 +327,34 @@ constexpr uint32_t kTileR = 128 * 128;                // bytes of one 128-row pa
 constexpr uint32_t kBuf = 6 * kTileR;                 // 3 R parts + 3 Q parts (nQp <= 128)
 constexpr size_t kSmem = 1024 + 2 * (size_t)kBuf;
 constexpr int kFlagTimeoutBit = 4;
+// stages rotate over kAcc TMEM accumulators (128 columns each), added at the
+// end: each accumulation chain is a quarter as long
+constexpr int kAcc = 4;
 }  // namespace wtc
 
+// A per-pair operand.  The contraction index q runs over virtual pairs, nm
+// per pair (q = pair nm + m: the m components of an order-l feature for the
+// mixing matrices, nm = 1 otherwise); feature f splits as (f / fq, f % fq):
+//   element (q, f) at p[(q / nm) ld + (q % nm) ms + (f / fq) es + (f % fq) fs2]
+// (plain per-pair arrays: nm = 1, fq = 1, element (q, f) at p[q ld + f es]).
 struct WgOp {
   const float* p;
-  int ld, es;                                          // element (pair q, feature f) at p[q ld + f es]
+  int ld, es;
+  int nm = 1, ms = 0, fq = 1, fs2 = 0;
 };
 
-// 8 consecutive pairs of feature f from pair q0 (zeros past P or past nf)
+// 8 consecutive virtual pairs of feature f from q0 (zeros past P or past nf)
 __device__ __forceinline__ void wtc_load8(const WgOp& o, int q0, int P, int f, int nf, float* v) {
+  const size_t fo = (size_t)(f / o.fq) * o.es + (size_t)(f % o.fq) * o.fs2;
+  int qp = q0 / o.nm, qm = q0 - qp * o.nm;
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int q = q0 + e;
-    v[e] = (q < P && f < nf) ? __ldg(o.p + (size_t)q * o.ld + (size_t)f * o.es) : 0.0f;
+    v[e] = (q < P && f < nf) ? __ldg(o.p + (size_t)qp * o.ld + (size_t)qm * o.ms + fo) : 0.0f;
+    if (++qm == o.nm) {
+      qm = 0;
+      ++qp;
+    }
   }
 }
 
@@ -372,7 +390,7 @@ __global__ void __launch_bounds__(wtc::kThr, 1)
   __shared__ int err;
   uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x;
-  if (tid < 32) tmem_alloc(&tslot, 128);
+  if (tid < 32) tmem_alloc(&tslot, 128 * wtc::kAcc);
   if (tid == 0) {
     mbar_init(&done[0], 1);
     mbar_init(&done[1], 1);
@@ -392,8 +410,8 @@ __global__ void __launch_bounds__(wtc::kThr, 1)
   float va[2][8], vb[2][8];
   auto load_stage = [&](int st) {
     const int q0 = (c0 + st / 2) * wtc::kPairs;
-    const WgOp& R = (st & 1) ? Rb : Ra;
-    const WgOp& Q = (st & 1) ? Qb : Qa;
+    const WgOp R = (st & 1) ? Rb : Ra;                // copies: no address taken of the parameters
+    const WgOp Q = (st & 1) ? Qb : Qa;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int t = tid + i * wtc::kThr;              // 1024 R tasks: f = t % 128, g = t / 128
@@ -425,11 +443,13 @@ __global__ void __launch_bounds__(wtc::kThr, 1)
       const uint32_t a = smem_u32(buf), q = smem_u32(buf + 3 * wtc::kTileR);
       const int pi[6] = {0, 0, 1, 0, 2, 1}, pj[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
+      const uint32_t d = tmem + 128u * (uint32_t)(st % wtc::kAcc);   // stage st -> accumulator st % kAcc
+#pragma unroll
       for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma_bf16(tmem, desc_sw128(a + pi[pr] * wtc::kTileR + kk * 32), desc_sw128(q + pj[pr] * tileQ + kk * 32),
-                   idesc, (st > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(d, desc_sw128(a + pi[pr] * wtc::kTileR + kk * 32), desc_sw128(q + pj[pr] * tileQ + kk * 32),
+                   idesc, (st >= wtc::kAcc || pr > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&done[b]);
       issued = st;
     }
@@ -445,13 +465,16 @@ __global__ void __launch_bounds__(wtc::kThr, 1)
     // warp w reads TMEM lanes 32 w .. 32 w + 31: accumulator row r = tid
     const int r = tid;
     float* out = part + (size_t)blockIdx.x * (r_is_n ? (size_t)nR * K : (size_t)nQ * K);
+    const int nacc = min(nstage, wtc::kAcc);            // accumulators written, summed in order
     for (int q0 = 0; q0 < nQp; q0 += 16) {
       float v[16];
-      if (nstage > 0) {
-        tmem_ld16(tmem + ((uint32_t)((tid >> 5) * 32) << 16) + (uint32_t)q0, v);
-      } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      for (int ac = 0; ac < nacc; ++ac) {
+        float u[16];
+        tmem_ld16(tmem + ((uint32_t)((tid >> 5) * 32) << 16) + (uint32_t)(128 * ac + q0), u);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += u[j];
       }
       if (r < nR)
 #pragma unroll
@@ -463,7 +486,7 @@ __global__ void __launch_bounds__(wtc::kThr, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (tid < 32) tmem_dealloc(tmem, 128);
+  if (tid < 32) tmem_dealloc(tmem, 128 * wtc::kAcc);
   if (err && tid == 0) atomicOr(flags, wtc::kFlagTimeoutBit);
 }
 
@@ -514,6 +537,40 @@ void launch_wgrad_tc(const float* dza, const float* dzb, int ldz, const float* x
 }
 
 bool wgrad_tc_supported(int N, int K) { return N >= 1 && K >= 1 && N <= 128 && K <= 128; }
+
+// Mixing matrix of order l on the tensor cores: the contraction runs over
+// (pair, m), m = 0 .. 2l, for both tangent terms,
+//   dW[c'][c Pl + q] += scale sum_p sum_m (dVa[p][c' NLM + l l + m] Ta[p][c NT + toff + q nm + m]
+//                                          + dVb[..] Tb[..]),
+// dV arrays with element stride esv (tangent-number arrays: 2).
+void launch_wgrad_mix_tc(const float* dVa, const float* dVb, int esv, const float* Ta, const float* Tb, int P, int C,
+                         int NLM, int NT, int l, int Pl, int toff, float scale, float* dW, float* part, int* flags,
+                         cudaStream_t s) {
+  if (P <= 0) return;
+  static bool init = false;
+  static int sms = 0;
+  if (!init) {
+    cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wtc::kSmem);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    init = true;
+  }
+  const int nm = 2 * l + 1;
+  const int Pv = P * nm;                               // virtual pairs (pair, m)
+  // rows: the C Pl columns of dW (T side), cols: the C rows (dV side)
+  WgOp tA{Ta + toff, C * NT, NT, nm, 1, Pl, nm}, tB{Tb + toff, C * NT, NT, nm, 1, Pl, nm};
+  WgOp vA{dVa + (size_t)l * l * esv, C * NLM * esv, NLM * esv, nm, esv, 1, 0};
+  WgOp vB{dVb + (size_t)l * l * esv, C * NLM * esv, NLM * esv, nm, esv, 1, 0};
+  const int N = C, K = C * Pl;
+  const int nQp = (N + 15) / 16 * 16;
+  const int nchunks = (Pv + wtc::kPairs - 1) / wtc::kPairs;
+  const int cpc = (nchunks + std::max(sms, 1) - 1) / std::max(sms, 1);
+  const int nz = (nchunks + cpc - 1) / cpc;
+  k_wgrad_tc<<<nz, wtc::kThr, wtc::kSmem, s>>>(tA, vA, tB, vB, K, N, nQp, Pv, cpc, 0, K, scale, part, flags,
+                                              1ll << 31);
+  k_chunk_sum<<<(N * K + 255) / 256, 256, 0, s>>>(part, nz, N, K, dW, K, 0);
+}
 
 void launch_wgrad_mix(const float* dV, int esv, const float* T, int P, int C, int NLM, int NT, int l, int Pl,
                       int toff, float scale, float* dW, float* part, cudaStream_t s) {

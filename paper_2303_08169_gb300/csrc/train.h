@@ -21,6 +21,13 @@ void launch_wgrad_tc(const float* dza, const float* dzb, int ldz, const float* x
                      int P, int N, int K, float scale, float* dW, int ldw, int k0, float* part, int* flags,
                      cudaStream_t s);
 bool wgrad_tc_supported(int N, int K);
+// Mixing matrix of order l on the tensor cores, both tangent terms:
+//   dW[c' C Pl + c Pl + q] += scale sum_p sum_m (dVa[p][(c' NLM + l l + m) esv] Ta[p][c NT + toff + q (2l+1) + m]
+//                                                + dVb[..] Tb[..])
+// (C <= 128, C Pl <= 128), same arithmetic and reduction order as launch_wgrad_tc.
+void launch_wgrad_mix_tc(const float* dVa, const float* dVb, int esv, const float* Ta, const float* Tb, int P, int C,
+                         int NLM, int NT, int l, int Pl, int toff, float scale, float* dW, float* part, int* flags,
+                         cudaStream_t s);
 // mixing matrix of order l (see train.cu); dV element stride esv
 void launch_wgrad_mix(const float* dV, int esv, const float* T, int P, int C, int NLM, int NT, int l, int Pl,
                       int toff, float scale, float* dW, float* part, cudaStream_t s);
