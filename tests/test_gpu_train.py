@@ -207,3 +207,37 @@ def test_loss_scan_matches_oracle(setup):
     al.allegro_get_weights(ctx, back)
     assert np.array_equal(back, w0)
     assert al.allegro_loss_grad(ctx, b, 1.0, 100.0) == pytest.approx(got[0], rel=1e-6)
+
+
+def test_gradient_matches_central_finite_differences(setup):
+    """The GPU loss gradient against central finite differences of the GPU
+    loss itself (h = 1e-4): along the unit gradient direction (where the
+    directional derivative is |g|) and along the three largest components.
+    The perturbed weights are formed as allegro_loss_scan forms them (FP64
+    w + s d, one rounding to FP32), and the difference quotient divides by
+    the steps actually taken, so FP32 rounding of the step does not enter.
+    Noise: the loss is ~1e2 with FP32 per-pair arithmetic (~1e-7 relative)
+    against signals 2 h g of 1e-2 to 1e-1, hence 2e-3 / 1e-2."""
+    ctx, _, _, structs, w0 = setup
+    al.allegro_set_weights(ctx, w0)
+    b, keep = al.make_batch(structs)
+    g = np.zeros(len(w0), np.float32)
+    al.allegro_loss_grad(ctx, b, 1.0, 100.0, g)
+    g64 = g.astype(np.float64)
+    h = 1e-4
+    d = (g64 / np.linalg.norm(g64)).astype(np.float32)
+    dirs = [d]
+    for k in np.argsort(-np.abs(g64))[:3]:
+        e = np.zeros(len(w0), np.float32)
+        e[k] = 1.0
+        dirs.append(e)
+    for i, dv in enumerate(dirs):
+        wp = (w0.astype(np.float64) + h * dv.astype(np.float64)).astype(np.float32)
+        wm = (w0.astype(np.float64) - h * dv.astype(np.float64)).astype(np.float32)
+        lp, lm = al.allegro_loss_scan(ctx, b, torch.from_numpy(dv).cuda(), [h, -h])
+        step = wp.astype(np.float64) - wm.astype(np.float64)
+        fd = lp - lm
+        pred = float(g64 @ step)
+        tol = 2e-3 if i == 0 else 1e-2
+        print(f"direction {i}: FD {fd:.6e} vs g.step {pred:.6e} (rel {abs(fd - pred) / abs(pred):.2e})")
+        assert abs(fd - pred) <= tol * abs(pred)
