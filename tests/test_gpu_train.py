@@ -147,6 +147,38 @@ def test_set_weights_changes_the_model(setup):
     assert abs(E0 - Er0) <= 1e-5 * max(1.0, abs(Er0))
 
 
+def test_set_weights_refreshes_the_tensor_core_images(setup):
+    """After allegro_set_weights (and after a SAM step) the tensor-core
+    passes run the new weights: their swizzled weight images are rebuilt
+    from the context's FP32 weights before the next tensor-core evaluation.
+    Split mode against the oracle at the weights the context holds, within
+    the method's 2e-3 eV/A force bound (main model only: the tiny model has
+    no tensor-core path)."""
+    ctx, stu, tea, structs, w0 = setup
+    if stu.lmax != 2:
+        pytest.skip("tensor-core path: main model")
+    s = structs[1]
+    for w in (flat_params(tea).numpy().astype(np.float32), w0):
+        al.allegro_set_weights(ctx, w)
+        Er, Fr, _, _ = stu.energy_forces(s["pos"], s["species"], s["lengths"],
+                                         w=_unflat(stu, torch.tensor(w, dtype=torch.float64)))
+        F = np.zeros((len(s["species"]), 3), np.float32)
+        E = al.allegro_energy_forces(ctx, s["pos"], s["species"], s["cell"], F, None, al.ALLEGRO_FP16_SPLIT)
+        assert np.abs(F - Fr).max() <= 2e-3
+        assert abs(E - Er) <= 1e-3 * max(1.0, abs(Er))
+    b, keep = al.make_batch(structs)
+    al.allegro_sam_train_step(ctx, b, 0.05, 2e-3, 1.0, 100.0)
+    w1 = np.zeros_like(w0)
+    al.allegro_get_weights(ctx, w1)
+    assert not np.array_equal(w1, w0)
+    Er, Fr, _, _ = stu.energy_forces(s["pos"], s["species"], s["lengths"],
+                                     w=_unflat(stu, torch.tensor(w1, dtype=torch.float64)))
+    F = np.zeros((len(s["species"]), 3), np.float32)
+    al.allegro_energy_forces(ctx, s["pos"], s["species"], s["cell"], F, None, al.ALLEGRO_FP16_SPLIT)
+    assert np.abs(F - Fr).max() <= 2e-3
+    al.allegro_set_weights(ctx, w0)
+
+
 def test_sam_steps_reduce_loss(setup):
     ctx, _, _, structs, w0 = setup
     al.allegro_set_weights(ctx, w0)
