@@ -624,7 +624,15 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   }
   c->dfree(pb.dR);
   pb.dR = nullptr;
+  for (int k = 0; k <= kMaxLayers; ++k) {
+    c->dfree(pb.Ek[k]);
+    pb.Ek[k] = nullptr;
+  }
   if (c->bf16_ok) {
+    for (uint32_t k = 1; k <= B.L && ok; ++k) {       // env outputs, FP32
+      pb.Ek[k] = c->dalloc<float>((size_t)capr * B.C);
+      ok = ok && pb.Ek[k];
+    }
     const int NSC = B.C * (B.lmax + 1);               // layer scalars (P_0 = l_max + 1 per channel), FP16 pairs
     for (uint32_t k = 1; k < B.L && ok; ++k) {
       pb.S[k] = c->dalloc<float>((size_t)capr * (NSC / 2));

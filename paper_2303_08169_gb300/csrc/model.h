@@ -82,6 +82,11 @@ struct PassBufs {
   float* G;               // P x 3  (dE/dDelta)
   float* S[kMaxLayers];   // BF16 path: tensor-product scalars of layer k (P x C P_0)
   float* dR = nullptr;    // tensor-core path: pair separation in FP32 (P x 3), written by pass A
+  // tensor-core path: env output e^k = env_k(x^{k-1}) of layer k in FP32 (P x C,
+  // tile-SoA), written by the pass that forms Gamma^k (A for k = 1, B2 of
+  // layer k - 1 otherwise) and read by the adjoint passes instead of forming
+  // it again from x^{k-1}
+  float* Ek[kMaxLayers + 1] = {};
   // per (tile, atom) partial sums, index (tile + atom)
   float* gam[kMaxLayers + 1];   // Gamma^k partials, k = 1..L
   float* dgam[kMaxLayers + 1];  // dGamma^k partials

@@ -782,6 +782,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       tmem_ld16(lanes(tmem) + 256, v);
 #pragma unroll
       for (int q = 0; q < 16; ++q) s_e[threadIdx.x * EP + q] = v[q];
+      if ((int)threadIdx.x < m.np)                    // e^1 for pass A^T
+#pragma unroll
+        for (int q = 0; q < 16; ++q) b.Ek[1][sidx(tile, C, q, threadIdx.x)] = v[q];
     }
     __syncthreads();
     seg_store(b.gam[1], m, CL, [&](int p, int x) { return s_e[p * EP + x / NLM] * s_Y[p * NLM + x % NLM]; });
@@ -1019,6 +1022,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       tmem_ld16(lanes(tmem) + 256, v);
 #pragma unroll
       for (int q = 0; q < 16; ++q) s_e[r * EP + q] = v[q];
+      if (valid)                                      // e^{k+1} for pass B^T of layer k
+#pragma unroll
+        for (int q = 0; q < 16; ++q) b.Ek[k + 1][sidx(tile, C, q, r)] = v[q];
     }
     __syncthreads();
     seg_store(b.gam[k + 1], m, CL, [&](int p, int x) { return s_e[p * EP + x / NLM] * s_Y[p * NLM + x % NLM]; });
@@ -1268,8 +1274,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 }
 
 // ============================================================================
-// Pass B_k^T: adjoint of layer k.  First the Gamma^{k+1} scatter and the
-// latent MLP (forward recomputed), then mixing and the tensor product, and
+// Pass B_k^T: adjoint of layer k.  First the Gamma^{k+1} scatter (with the
+// env output e^{k+1} stored by pass B2) and the latent MLP (forward
+// recomputed), then mixing and the tensor product, and
 // for k = 1 the embedding; no per-atom sum lies between the two halves, so
 // they share one kernel.  dS^k stays in TMEM and dx^{k-1} is
 // accumulated in one set of TMEM columns (residual dx / sqrt 2, then
@@ -1277,7 +1284,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 // Shared memory: HA holds x^k, then [x^{k-1}, S^k], dz1, the dV^k operand
 // and at the end dw0 and the dy partials; A1 holds de, SiLU(z1), dz2 and
 // during the mixing-adjoint rounds the dGamma^k staging of eight channels.
-// TMEM columns: e [0, 16); z1 [32, 160); z2 and da1 [160, 288); dx [288,
+// e^{k+1} is read from memory (stored by pass B2).
+// TMEM columns: z1 [32, 160); z2 and da1 [160, 288); dx [288,
 // 416); ds [416, 416 + C NS); w0 [464, 464 + NW0); in the rounds, the l3 = 0
 // component of all channels [416, 416 + C NS) and components j >= 1 from
 // column 32 (j - 1): at l_max 2 eight channels per round (32 columns each,
@@ -1335,14 +1343,13 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
   float* s_Y = s_fc + kT;
   float* s_du = s_Y + kT * NLM;                        // [4][kT]
   float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
-  constexpr int kE = 0, kZ1 = 32, kZ2 = 160, kDX = 288, kDS = 416, kW0 = 464, kJ0 = 416, kJ = 0;
+  constexpr int kZ1 = 32, kZ2 = 160, kDX = 288, kDS = 416, kW0 = 464, kJ0 = 416, kJ = 0;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
-  // the next tile's x^k operand words, dV^k words (channels 4h..4h+3) and
-  // neighbour-list rows, loaded during this tile's tail
-  uint32_t xw[16], dvw[NLM][2];
+  // the next tile's dV^k words (channels 4h..4h+3) and neighbour-list rows,
+  // loaded during this tile's tail
+  uint32_t dvw[NLM][2];
   auto ld_next = [&](int t) {
     const bool vt = r < min(kT, P - t * kT);
-    ld_row<32>(xw, b.X[k], t, r, D, 32 * h, vt);
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
 #pragma unroll
@@ -1357,7 +1364,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       const int nt = tile + (int)gridDim.x;
       prefetch_meta(b, nt);
       prefetch_rows(b.dR, 3, nt);
-      prefetch_rows_h(b.X[k], D, nt);
+      prefetch_rows(b.Ek[k + 1], C, nt);
       prefetch_rows_h(b.X[k - 1], D, nt);
       prefetch_rows_h(b.S[k], C * NS, nt);
       prefetch_rows_h(b.dV, CL, nt);
@@ -1367,6 +1374,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       if (!kEmb) prefetch_rows_h(b.V[k - 1], CL, nt);
     }
     const bool valid = r < m.np;
+    float ew[4];                                      // e^{k+1} of channels 4h..4h+3 (stored by pass B2)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) ew[cc] = valid ? b.Ek[k + 1][sidx(tile, C, 4 * h + cc, r)] : 0.0f;
     if (h == 0) {
       float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
@@ -1376,17 +1386,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
     }
-    st_row<Tin, 32>(HA, r, 32 * h, xw);
     stage_g<CL>(b.dgsum[k + 1], m, s_g);
-    uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env MMA
+    uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env adjoint
     const bool has_s = h >= 1 && h <= NS;             // quarters 1..NS hold S^k columns 16 (h - 1)..
     ld_row<32>(xw2, b.X[k - 1], tile, r, D, 32 * h, valid);
     ld_row<16>(sw, b.S[k], tile, r, C * NS, 16 * max(h - 1, 0), valid && has_s);
-    mm.run([&] { mma_k<Tin>(tmem + kE, HA, 0, Wenv, 16, 8, false, 0); });       // e^{k+1}
+    __syncthreads();                                  // geometry rows and staged dGamma rows
     float dy[NLM];                                    // dY of this thread's channels (env and embedding)
     {
-      float e[8];
-      tmem_ld8(lanes(tmem) + kE + 4 * h, e);          // e of channels 4h..4h+3 in e[0..3]
+      const float* e = ew;                            // e^{k+1} of channels 4h..4h+3
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
 #pragma unroll
@@ -1589,8 +1597,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
 }
 
 // ============================================================================
-// Pass A^T: adjoint of the Gamma^1 scatter, of the two-body MLP (recomputed)
-// and of the geometry; writes g_ij = dE/dDelta_ij.
+// Pass A^T: adjoint of the Gamma^1 scatter (with the env output e^1 stored by
+// pass A), of the two-body MLP (recomputed) and of the geometry; writes
+// g_ij = dE/dDelta_ij.
 // DE shares H0's buffer (H0 is dead after the first MMA).  Split mode: both
 // two-body GEMMs and their adjoints take split operands; A1lo holds the lo
 // part of silu(z1), then of dz2, then of dz1.  The dh0 adjoint reads the
@@ -1621,8 +1630,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
   float* s_dy = s_Y + kT * NLM;                           // [kT][NLM]
   float* s_du = s_dy + kT * NLM;                          // [4][kT]
   float* s_g = s_du + 4 * kT;                             // [kSegCap][CL]
-  // [4][kT][NLM] per-quarter dY partials: X is dead from the end of the e^1
-  // MMA until the dz1 epilogue, and the partials are summed right after the
+  // [4][kT][NLM] per-quarter dY partials: X is free from the start of the
+  // tile until the dz1 epilogue, and the partials are summed right after the
   // env1^T MMA
   float* s_dyq = reinterpret_cast<float*>(X);
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
@@ -1636,6 +1645,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       prefetch_rows(b.dX, D, nt);
       prefetch_rows(b.dU, 1, nt);
       prefetch_rows(b.dY, NLM, nt);
+      prefetch_rows(b.Ek[1], C, nt);
     }
     const bool valid = r < m.np;
     if (h == 0) {                                     // geometry, envelope, harmonics
@@ -1670,20 +1680,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       st_h0<Tin, kSplit>(H0, r, h0);
     }
     stage_g<CL>(b.dgsum[1], m, s_g);
+    float e1[4];                                      // e^1 of channels 4h..4h+3 (stored by pass A)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) e1[cc] = valid ? b.Ek[1][sidx(tile, C, 4 * h + cc, r)] : 0.0f;
     mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });   // z1
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o); });
     mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });   // z2
-    epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
-      float o[16];
-      const float fc = s_geo[rr * GP + 4];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = r16(fc * silu_b(v[q]));   // as pass A
-      st16<Tin>(X, rr, n0, o);
-    });
-    mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });      // e^1
     {
-      float e[8], dy[NLM];
-      tmem_ld8(lanes(tmem) + 256 + 4 * h, e);         // e of channels 4h..4h+3 in e[0..3]
+      float dy[NLM];
+      const float* e = e1;
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
 #pragma unroll
