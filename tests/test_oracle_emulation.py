@@ -80,9 +80,13 @@ def test_storage_rounding_is_straight_through():
     assert g.tolist() == [2.0, 3.0, -1.0]
 
 
+@pytest.mark.parametrize("l_max", [0, 1, 2])
 @pytest.mark.parametrize("mode", MODES)
-def test_identity_rounding_is_the_exact_model(mode):
-    blob = synth.make_blob(MINI, 5)
+def test_identity_rounding_is_the_exact_model(mode, l_max):
+    """At every l_max the tensor-core passes run (the mixing GEMM over the
+    (pair, m) rows of each order's K-slice, the embedding width C (l_max + 1))."""
+    import dataclasses
+    blob = synth.make_blob(dataclasses.replace(MINI, l_max=l_max), 5)
     pos, sp = _cluster()
     E0, F0, Ei0, pairs = OracleModel(blob).energy_forces(pos, sp, BIG)
     m = OracleModel(blob, emulate=mode)
