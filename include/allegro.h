@@ -80,12 +80,17 @@ const char* allegro_version(void);
  * Table 2 at one width, in every precision; the tensor-core precisions need
  * at least two layers).  The header's parity flag: 0 (natural-parity coupling
  * paths) or 1 (full O(3): parity-odd paths and pseudotensor features, Sec. 2.1
- * E(3) equivariance including inversion).  Parity 1 is accepted for models of
- * at most two layers, where the odd paths cannot reach the energy (a
- * pseudotensor gives a true scalar only through a second odd path, and no
- * path into l = 0 is odd), so the model computed is the natural-parity one and
- * the pseudotensor mixing matrices are not loaded; E_UNSUPPORTED from three
- * layers on.  An out-of-range flag is E_BLOB.
+ * E(3) equivariance including inversion).  With at most two layers (or
+ * l_max 0) the odd paths cannot reach the energy (a pseudotensor gives a true
+ * scalar only through a second odd path, and no path into l = 0 is odd), so
+ * the model computed is the natural-parity one and the pseudotensor mixing
+ * matrices are not loaded (nor part of the weight vector); every precision
+ * runs it.  From three layers on (l_max 1 or 2) the FP32 passes run the
+ * full-O(3) model: features of both parities per channel, every even and odd
+ * coupling path, one mixing matrix per output irrep (l, s), each with one
+ * column per path of the irreps its layer receives (else E_BLOB); the
+ * tensor-core precisions and training are E_UNSUPPORTED for it.  An
+ * out-of-range flag is E_BLOB.
  * The paper defines only the pairwise-energy decomposition and equivariance
  * (Sec. 2.1); the layer structure follows the Allegro reading stated in the
  * oracle package.
@@ -141,7 +146,7 @@ int allegro_get_neighbors(allegro_ctx* ctx, int32_t* row_ptr, int32_t* col,
  *  precision    : ALLEGRO_FP32, ALLEGRO_BF16, ALLEGRO_FP16 or
  *                 ALLEGRO_FP16_SPLIT (the tensor-core modes: E_UNSUPPORTED
  *                 unless l_max <= 2, C = 16, D = 128, E = 32, at least two
- *                 layers).
+ *                 layers, and natural parity or at most two layers).
  * On ALLEGRO_E_PAIR_OVERFLOW nothing is written; the context has grown and
  * the call may simply be repeated.  The call reuses the MD state's buffers:
  * allegro_md_init again before the next allegro_md_step_* (which otherwise

@@ -17,7 +17,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBNAME = "libpaper_2303_08169_gb300.so"
 LIB = os.path.join(HERE, LIBNAME)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["neighbor.cu", "model_fp32.cu", "model_bf16.cu", "md.cu", "api.cu", "umma_selftest.cu", "noalloc.cu", "train.cu"]
+SOURCES = ["neighbor.cu", "model_fp32.cu", "model_fp32_o3.cu", "model_bf16.cu", "md.cu", "api.cu", "umma_selftest.cu", "noalloc.cu", "train.cu"]
 
 
 def _nvcc():

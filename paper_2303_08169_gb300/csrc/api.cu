@@ -2,6 +2,7 @@
 // device buffers, orchestration of the neighbour, pair-pass and per-atom
 // kernels, and the CUDA-graph MD step.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -127,7 +128,41 @@ struct WInfo {
   float scale;
   size_t t_off, n_off;   // offsets in floats inside d_w (t unused for some)
   bool has_t;
+  // full-O(3) mixing (mix_pl > 0): the [C][C P_l] blob matrix sits in a
+  // [C][C P_u] device block, column c P_l + q at c P_u + mix_q[q]
+  int mix_pl = 0, mix_pu = 0;
+  std::vector<int> mix_q;
 };
+
+// Coupling paths of the full-O(3) tables (gen_tp.cpp's tpLo_*): for output
+// block b = s3 (l_max + 1) + l3, every (s1, l1, l2) in that order with
+// |l1 - l2| <= l3 <= l1 + l2 and s3 = (l1 + s1 + l2 + l3) mod 2 whose input
+// irrep (l1, s1) has its bit s1 (l_max + 1) + l1 set in `in`.
+struct O3Path { int s1, l1, l2; };
+std::vector<O3Path> o3_paths(int lmax, int b, unsigned in) {
+  const int l3 = b % (lmax + 1), s3 = b / (lmax + 1);
+  std::vector<O3Path> out;
+  for (int s1 = 0; s1 <= 1; ++s1)
+    for (int l1 = 0; l1 <= lmax; ++l1) {
+      if (!(in >> (s1 * (lmax + 1) + l1) & 1u)) continue;
+      for (int l2 = 0; l2 <= lmax; ++l2)
+        if (std::abs(l1 - l2) <= l3 && l3 <= l1 + l2 && (l1 + s1 + l2 + l3) % 2 == s3) out.push_back({s1, l1, l2});
+    }
+  return out;
+}
+
+// Input irreps of layer k (bits as above): true tensors for layer 1, then
+// every output irrep that some path of the previous layer reaches.
+unsigned o3_layer_inputs(int lmax, int k) {
+  unsigned in = (1u << (lmax + 1)) - 1u;
+  for (int q = 1; q < k; ++q) {
+    unsigned out = 0;
+    for (int b = 0; b < 2 * (lmax + 1); ++b)
+      if (!o3_paths(lmax, b, in).empty()) out |= 1u << b;
+    in = out;
+  }
+  return in;
+}
 
 // Training batch (see build_batch): concatenated neighbour lists and atoms
 // of all structures, and the per-atom / per-structure loss buffers.
@@ -352,14 +387,53 @@ int upload_weights(allegro_ctx* c) {
     flat += (size_t)T->rows * T->cols;
     return true;
   };
+  // Full O(3): mixing block b of layer k as a [C][C P_u] matrix over the
+  // paths of all input irreps (the kernels' tables), the blob's columns (the
+  // paths of the irreps the layer receives) scattered into it, the rest zero.
+  // A block that no path of the layer reaches has no blob tensor: all zero.
+  auto push_mix_o3 = [&](uint32_t k, int b, const float** raw_n) -> bool {
+    const int lm = (int)B.lmax, C = (int)B.C;
+    const std::vector<O3Path> all = o3_paths(lm, b, (1u << (2 * (lm + 1))) - 1u);
+    const std::vector<O3Path> mine = o3_paths(lm, b, o3_layer_inputs(lm, (int)k));
+    const int pu = (int)all.size(), pl = (int)mine.size();
+    while (host.size() % 4) host.push_back(0.f);
+    const size_t n_off = host.size();
+    host.resize(host.size() + (size_t)C * C * pu, 0.f);
+    *raw_n = reinterpret_cast<const float*>(n_off);
+    const std::string name = "layer" + std::to_string(k) + ".mix" + std::to_string(b % (lm + 1)) +
+                             (b > lm ? "p" : "");
+    const Tensor* T = B.find(name);
+    if (pl == 0) return T == nullptr;
+    if (!T || T->rows != (uint32_t)C || T->cols != (uint32_t)(C * pl)) return false;
+    std::vector<int> q_of(pl);
+    for (int q = 0, u = 0; q < pl; ++q) {
+      while (all[u].s1 != mine[q].s1 || all[u].l1 != mine[q].l1 || all[u].l2 != mine[q].l2) ++u;
+      q_of[q] = u;
+    }
+    const double sc = 1.0 / std::sqrt((double)T->cols);
+    for (int o = 0; o < C; ++o)
+      for (int ci = 0; ci < C; ++ci)
+        for (int q = 0; q < pl; ++q)
+          host[n_off + (size_t)o * C * pu + ci * pu + q_of[q]] = (float)(T->data[(size_t)o * T->cols + ci * pl + q] * sc);
+    WInfo wi{T->name, (int)T->rows, (int)T->cols, flat, (float)sc, n_off, n_off, false};
+    wi.mix_pl = pl;
+    wi.mix_pu = pu;
+    wi.mix_q = q_of;
+    c->winfo.push_back(wi);
+    flat += (size_t)T->rows * T->cols;
+    return true;
+  };
   ModelW& w = c->w;
   bool ok = push(B.find("twobody.0"), 1.0, &w.tb0, nullptr) && push(B.find("twobody.1"), 1.0, &w.tb1, nullptr) &&
             push(B.find("embed"), 1.0, &w.emb, nullptr);
+  const int nblk = w.o3 ? 2 * ((int)B.lmax + 1) : (int)B.lmax + 1;
   for (uint32_t k = 1; ok && k <= B.L; ++k) {
     const std::string pre = "layer" + std::to_string(k) + ".";
     LayerW& LW = w.layer[k - 1];
     ok = ok && push(B.find(pre + "env"), 1.0 / std::sqrt(B.nu), &LW.env, nullptr);
-    if (k < B.L)
+    if (k < B.L && w.o3)
+      for (int b = 0; ok && b < nblk; ++b) ok = ok && push_mix_o3(k, b, &LW.mix[b]);
+    else if (k < B.L)
       for (uint32_t l = 0; ok && l <= B.lmax; ++l)
         ok = ok && push(B.find(pre + "mix" + std::to_string(l)), 1.0, nullptr, &LW.mix[l]);
     ok = ok && push(B.find(pre + "latent.0"), 1.0, &LW.lat0, nullptr) &&
@@ -379,7 +453,7 @@ int upload_weights(allegro_ctx* c) {
     LayerW& LW = w.layer[k - 1];
     fixl(LW.env); fixl(LW.lat0); fixl(LW.lat1);
     if (k < B.L)
-      for (uint32_t l = 0; l <= B.lmax; ++l) fix(LW.mix[l]);
+      for (int b = 0; b < nblk; ++b) fix(LW.mix[b]);
   }
   w.eout = c->d_w + reinterpret_cast<size_t>(eout);
   c->n_params = (int64_t)flat;
@@ -568,8 +642,9 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   const Blob& B = c->blob;
   const int NLM = (B.lmax + 1) * (B.lmax + 1);
   const int CL = B.C * NLM;
+  const int CV = c->w.o3 ? 2 * CL : CL;   // V^k per pair (full O(3): both parities)
   const bool full = c->want_fp32 || !c->bf16_ok;
-  const int tile = full ? fp32_tile() : bf16_tile();
+  const int tile = full ? fp32_tile(c->w.o3) : bf16_tile();
   const int64_t rows_needed = cap / tile + 2 + c->n_atoms_alloc;
   if (cap <= c->capacity && rows_needed <= c->part_rows && (c->pb_fp32 || !full)) return ALLEGRO_OK;
   if (cap > (int64_t)0x7fffffff - 1024) return c->fail(ALLEGRO_E_UNSUPPORTED, "more than 2^31 pairs");
@@ -604,7 +679,7 @@ int ensure_pairs(allegro_ctx* c, int64_t cap) {
   // x^k, V^k and dV: FP32 rows for the FP32 passes, FP16 (or 16-bit operand)
   // pairs, half the words, for the tensor-core passes
   const size_t xw = full ? (size_t)c->D : (size_t)c->D / 2;
-  const size_t vw = full ? (size_t)CL : (size_t)CL / 2;
+  const size_t vw = full ? (size_t)CV : (size_t)CL / 2;
   for (uint32_t k = 0; k < B.L && ok; ++k) {
     pb.X[k] = c->dalloc<float>((size_t)capr * xw);
     ok = ok && pb.X[k];
@@ -689,7 +764,7 @@ void fill_passbufs(allegro_ctx* c, const double L[3]) {
   pb.n_atoms = c->n_atoms;
   for (int a = 0; a < 3; ++a) pb.L[a] = L[a];
   pb.atomL = nullptr;
-  pb.tile = fp32_tile();
+  pb.tile = fp32_tile(c->w.o3);
 }
 
 AtomArgs atom_args(allegro_ctx* c) {
@@ -844,7 +919,7 @@ void launch_model(allegro_ctx* c, int32_t precision, cudaStream_t s, KernelMarks
   } else {
     if (c->pb_fp32) fp32_energy_forces((int)B.lmax, (int)B.C, c->D, c->E, c->w, c->pb, c->capacity, s, km, &c->fl[0]);
     else c->fp32_bad = true;
-    tile = fp32_tile();
+    tile = fp32_tile(c->w.o3);
   }
   launch_forces(atom_args(c), c->nb.row_ptr, c->nb.rev, c->pb.G, c->pb.epart, tile, c->d_F, c->d_Ei, c->d_blk,
                 c->d_stats, c->nb.flags, s);
@@ -857,7 +932,7 @@ int run_model(allegro_ctx* c, int32_t precision, const double L[3]) {
     return c->fail(ALLEGRO_E_INVALID_ARG,
                    "precision must be ALLEGRO_FP32, ALLEGRO_BF16, ALLEGRO_FP16 or ALLEGRO_FP16_SPLIT");
   if (precision != ALLEGRO_FP32 && !c->bf16_ok)
-    return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 16-channel, latent-128 model with 2+ layers and l_max <= 2 only");
+    return c->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 16-channel, latent-128 model with 2+ layers and l_max <= 2 (natural parity, or full O(3) with two layers) only");
   if (precision != ALLEGRO_FP32) {
     const int rc = refresh_tc(c);
     if (rc) return rc;
@@ -912,8 +987,13 @@ int init_master(allegro_ctx* c) {
 
 // FP32 pass weights <- flat vector (pre-scaled copies of every tensor)
 void apply_flat(allegro_ctx* c, const float* flat) {
-  for (const auto& wi : c->winfo)
-    launch_apply(flat + wi.flat_off, wi.rows, wi.cols, wi.scale, c->d_w + wi.t_off, c->d_w + wi.n_off, c->stream);
+  for (const auto& wi : c->winfo) {
+    if (wi.mix_pl > 0)
+      launch_apply_mix(flat + wi.flat_off, wi.rows, wi.cols / wi.mix_pl, wi.mix_pl, wi.mix_pu, wi.mix_q.data(),
+                       wi.scale, c->d_w + wi.n_off, c->stream);
+    else
+      launch_apply(flat + wi.flat_off, wi.rows, wi.cols, wi.scale, c->d_w + wi.t_off, c->d_w + wi.n_off, c->stream);
+  }
   c->tc_dirty = true;
 }
 
@@ -1178,7 +1258,7 @@ void fill_batch_passbufs(allegro_ctx* c, const double* wpos) {
   pb.n_atoms = (int)t.n_atoms;
   pb.atomL = t.a.atomL;
   for (int a = 0; a < 3; ++a) pb.L[a] = 0.0;
-  pb.tile = fp32_tile();
+  pb.tile = fp32_tile(c->w.o3);
 }
 
 // Tangent pass sequence over the batch (positions moving along v = dL/dF,
@@ -1240,7 +1320,7 @@ void batch_forward_loss(allegro_ctx* c, double w_energy, double w_force) {
   AtomArgs aa = atom_args(c);
   aa.n = (int)N;
   aa.species = t.a.species;
-  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, fp32_tile(), c->d_F, c->d_Ei, c->d_blk, c->d_stats,
+  launch_forces(aa, t.a.row_ptr, t.a.rev, c->pb.G, c->pb.epart, fp32_tile(c->w.o3), c->d_F, c->d_Ei, c->d_blk, c->d_stats,
                 c->nb.flags, s);
   c->pb.atomL = nullptr;
   launch_batch_loss((int)t.n_structs, N, t.atom_off, c->d_Ei, t.e_target, c->d_F, t.f_target, w_energy, cf, t.dE,
@@ -1322,24 +1402,21 @@ int allegro_create(const void* weights_blob, size_t blob_bytes, const double* sp
     delete c;
     return ALLEGRO_E_MISMATCH;
   }
-  const bool shape_ok = B.S == 2 && B.NB == 8 && B.p == 6 && B.latent.size() == 2 && B.latent[0] == B.latent[1] &&
-                        B.energy.size() == 1 && B.L >= 1 && B.L <= (uint32_t)kMaxLayers &&
-                        fp32_supported((int)B.lmax, (int)B.C, (int)B.latent[0], (int)B.energy[0]);
-  if (!shape_ok) {
-    g_err = "model shape not compiled into this library";
-    delete c;
-    return ALLEGRO_E_UNSUPPORTED;
-  }
   // Full O(3): a pseudotensor made by an odd path of layer k reaches a true
   // scalar (0e) only through a further odd path, which no l3 = 0 output has
   // (l1 = l2 there), so it first changes the energy through the mixing of
-  // layer k + 1 into a layer k + 2.  With at most two layers the full-O(3)
-  // model therefore is the natural-parity model (its pseudotensor mixing
-  // matrices, layer{k}.mix{l}p, have no effect and are not loaded); from
-  // three layers on the odd paths would be needed, which these passes do not
-  // build.
-  if (B.parity == 1 && B.L >= 3) {
-    g_err = "full-O(3) models of three or more layers are not built (odd coupling paths)";
+  // layer k + 1 into a layer k + 2.  With at most two layers (or l_max 0,
+  // where no path is odd) the full-O(3) model therefore is the natural-parity
+  // model (its pseudotensor mixing matrices, layer{k}.mix{l}p, have no effect
+  // and are not loaded) and runs on every pass implementation; from three
+  // layers on it runs the full-O(3) FP32 passes (features of both parities,
+  // every odd path).
+  c->w.o3 = (B.parity == 1 && B.L >= 3 && B.lmax >= 1) ? 1 : 0;
+  const bool shape_ok = B.S == 2 && B.NB == 8 && B.p == 6 && B.latent.size() == 2 && B.latent[0] == B.latent[1] &&
+                        B.energy.size() == 1 && B.L >= 1 && B.L <= (uint32_t)kMaxLayers &&
+                        fp32_supported((int)B.lmax, (int)B.C, (int)B.latent[0], (int)B.energy[0], c->w.o3 != 0);
+  if (!shape_ok) {
+    g_err = "model shape not compiled into this library";
     delete c;
     return ALLEGRO_E_UNSUPPORTED;
   }
@@ -1347,7 +1424,7 @@ int allegro_create(const void* weights_blob, size_t blob_bytes, const double* sp
   c->E = (int)B.energy[0];
   for (int s = 0; s < 2; ++s) c->mass[s] = species_mass[s];
   int rc = upload_weights(c);
-  c->bf16_ok = bf16_supported((int)B.lmax, (int)B.C, c->D, c->E, (int)B.L);
+  c->bf16_ok = !c->w.o3 && bf16_supported((int)B.lmax, (int)B.C, c->D, c->E, (int)B.L);
   if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, TcMode::kBf16);
   if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, TcMode::kFp16);
   if (!rc && c->bf16_ok) rc = upload_weights_bf16(c, TcMode::kFp16Split);
@@ -1463,7 +1540,7 @@ int allegro_set_skin(allegro_ctx* ctx, double skin_A) {
 int allegro_set_md_precision(allegro_ctx* ctx, int32_t precision) {
   if (!ctx || !valid_precision(precision)) return ALLEGRO_E_INVALID_ARG;
   if (precision != ALLEGRO_FP32 && !ctx->bf16_ok)
-    return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 16-channel, latent-128 model with 2+ layers and l_max <= 2 only");
+    return ctx->fail(ALLEGRO_E_UNSUPPORTED, "the tensor-core path is built for the 16-channel, latent-128 model with 2+ layers and l_max <= 2 (natural parity, or full O(3) with two layers) only");
   if (precision == ALLEGRO_FP32) {
     const int rc = require_fp32(ctx);
     if (rc) return rc;
@@ -1778,7 +1855,7 @@ void rp_launch_forces(allegro_ctx* c, cudaStream_t s) {
   if (prec == ALLEGRO_FP32) {
     if (c->pb_fp32) fp32_energy_forces((int)c->blob.lmax, (int)c->blob.C, c->D, c->E, c->w, c->pb, c->capacity, s);
     else c->fp32_bad = true;
-    tile = fp32_tile();
+    tile = fp32_tile(c->w.o3);
   } else {
     const TcMode mode = prec == ALLEGRO_BF16 ? TcMode::kBf16 : prec == ALLEGRO_FP16 ? TcMode::kFp16 : TcMode::kFp16Split;
     bf16_energy_forces(prec == ALLEGRO_BF16 ? c->bw : prec == ALLEGRO_FP16 ? c->hw : c->sw, c->pb, c->capacity, s,

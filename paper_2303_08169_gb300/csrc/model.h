@@ -16,9 +16,17 @@ struct Lin {
   const float* n = nullptr;
 };
 
+// Output blocks of a layer's channel mixing: one per order l <= l_max
+// (natural-parity models), or per irrep (l, s), block s (l_max + 1) + l,
+// for full-O(3) models of three or more layers.
+constexpr int kMaxMixBlocks = 6;
+
 struct LayerW {
   Lin env;                    // C x D, extra factor 1/sqrt(nu)
-  const float* mix[3] = {};   // [C][C P_l] (layers below the last)
+  // [C][C P_b] per output block b (layers below the last); full O(3): the
+  // columns of every block follow the paths of all input irreps (zero for
+  // paths whose input irrep the layer does not receive)
+  const float* mix[kMaxMixBlocks] = {};
   Lin lat0, lat1;             // (D + C P_0) -> D -> D
 };
 
@@ -31,6 +39,7 @@ struct ModelW {
   float sigma[2], mu[2];
   float rc;
   int n_layers;
+  int o3 = 0;                 // 1: full-O(3) features (both parities) and tables
 };
 
 // Training mode of the FP32 passes: every linear layer's input and the
@@ -167,14 +176,17 @@ struct Fp32Launch {
 };
 
 // FP32 path: one launcher per pass sequence; templated on the model shape in
-// the .cu file, dispatched by (lmax, C, D, E).
-bool fp32_supported(int lmax, int C, int D, int E);
+// the .cu files, dispatched by (lmax, C, D, E) and w.o3.  Full-O(3) models
+// (o3) carry features of both parities per channel, V^k of 2 (l_max+1)^2
+// components (index s (l_max+1)^2 + l^2 + m + l), and run tiles of
+// fp32_tile(true) pairs.
+bool fp32_supported(int lmax, int C, int D, int E, bool o3 = false);
 // km (optional): events recorded at the phase boundaries; ls (optional):
 // launch shape (default eight waves for every pass).
 void fp32_energy_forces(int lmax, int C, int D, int E, const ModelW& w, const PassBufs& b,
                         int64_t capacity, cudaStream_t s, KernelMarks* km = nullptr,
                         const Fp32Launch* ls = nullptr);
-int fp32_tile();
+int fp32_tile(bool o3 = false);
 // Tangent passes of the second-order adjoint: the FP32 pass sequence in
 // tangent numbers (value and derivative along the position direction b.vdir),
 // tiles of fp32_tangent_tile() pairs.  Every per-pair and per-(tile, atom)

@@ -193,6 +193,16 @@ __global__ void k_apply(const float* __restrict__ flat, int rows, int cols, floa
   if (n_out) n_out[i] = v;
 }
 
+// Full-O(3) mixing: blob matrix [rows][C pl] into the device block
+// [rows][C pu], column c pl + q at c pu + qm.q[q] (the other columns stay).
+__global__ void k_apply_mix(const float* __restrict__ flat, int rows, int C, int pl, int pu, MixQ qm, float scale,
+                            float* __restrict__ n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * C * pl) return;
+  const int o = i / (C * pl), k = i % (C * pl);
+  n_out[(size_t)o * C * pu + (k / pl) * pu + qm.q[k % pl]] = flat[i] * scale;
+}
+
 __global__ void k_append(BatchArrays bt, int n, int np, int64_t A0, int64_t P0, int b,
                          const int* __restrict__ pi, const int* __restrict__ pj, const int* __restrict__ pcode,
                          const int* __restrict__ rev, const int* __restrict__ row_ptr,
@@ -442,7 +452,6 @@ __global__ void __launch_bounds__(wtc::kThr, 1)
       tc_fence_after();
       const uint32_t a = smem_u32(buf), q = smem_u32(buf + 3 * wtc::kTileR);
       const int pi[6] = {0, 0, 1, 0, 2, 1}, pj[6] = {0, 1, 0, 2, 0, 1};
-#pragma unroll
       const uint32_t d = tmem + 128u * (uint32_t)(st % wtc::kAcc);   // stage st -> accumulator st % kAcc
 #pragma unroll
       for (int pr = 0; pr < 6; ++pr)
@@ -608,6 +617,14 @@ void launch_adam(float* w, const float* g, float* m, float* v, int n, double lr,
 
 void launch_apply(const float* flat, int rows, int cols, float scale, float* t_out, float* n_out, cudaStream_t s) {
   k_apply<<<(rows * cols + 255) / 256, 256, 0, s>>>(flat, rows, cols, scale, t_out, n_out);
+}
+
+void launch_apply_mix(const float* flat, int rows, int C, int pl, int pu, const int* q, float scale, float* n_out,
+                      cudaStream_t s) {
+  if (pl < 1 || pl > kMixQ || rows * C * pl <= 0) return;
+  MixQ qm{};
+  for (int k = 0; k < pl; ++k) qm.q[k] = q[k];
+  k_apply_mix<<<(rows * C * pl + 255) / 256, 256, 0, s>>>(flat, rows, C, pl, pu, qm, scale, n_out);
 }
 
 }  // namespace al

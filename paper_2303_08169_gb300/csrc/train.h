@@ -39,6 +39,12 @@ void launch_adam(float* w, const float* g, float* m, float* v, int n, double lr,
 // w_out = w + scale d (FP64 arithmetic, one rounding)
 void launch_axpy(const float* w, const float* d, double scale, int n, float* w_out, cudaStream_t s);
 void launch_apply(const float* flat, int rows, int cols, float scale, float* t_out, float* n_out, cudaStream_t s);
+// Full-O(3) mixing block: [rows][C pl] blob columns into the [rows][C pu]
+// device block, column c pl + q at c pu + q_map[q] (pl <= kMixQ).
+constexpr int kMixQ = 32;
+struct MixQ { int q[kMixQ]; };
+void launch_apply_mix(const float* flat, int rows, int C, int pl, int pu, const int* q_map, float scale,
+                      float* n_out, cudaStream_t s);
 
 // ---- training batches: all structures in one pass sequence ----
 // Append one structure's neighbour list and atoms at atom offset A0 and pair

@@ -64,15 +64,32 @@ def test_bad_blob_and_mismatch_rejected_on_host(built):
 
 
 def test_full_o3_blobs_on_host(built):
-    """The parity flag: full-O(3) models of three layers are refused
-    (E_UNSUPPORTED) and an out-of-range flag is a malformed blob (E_BLOB),
-    both before any GPU work."""
+    """The parity flag: a three-layer full-O(3) blob whose pseudotensor
+    mixing matrix does not have one column per path of the layer's input
+    irreps (layer 2, block (1, odd): 5 paths, (0, odd) is no input there), and
+    an out-of-range flag, are malformed blobs (E_BLOB), both before any GPU
+    work."""
     import dataclasses
+    from synth.weights import NAME_BYTES
     mass = np.array([14.007, 1.008])
     cfg3 = dataclasses.replace(synth.MAIN, n_layers=3, parity=1)
+    blob = bytearray(synth.make_blob(cfg3, 1))
+    off = blob.index(b"layer2.mix1p\0") + NAME_BYTES + 4          # directory entry: rows, cols, offset
+    assert int.from_bytes(blob[off:off + 4], "little") == cfg3.n_channels * 5
+    blob[off:off + 4] = (cfg3.n_channels * 4).to_bytes(4, "little")
     with pytest.raises(al.AllegroError) as e:
-        al.allegro_create(synth.make_blob(cfg3, 1), mass, cfg3.r_cut, cfg3.l_max, 3)
-    assert e.value.code == 10
+        al.allegro_create(bytes(blob), mass, cfg3.r_cut, cfg3.l_max, 3)
+    assert e.value.code == 11
+    # well-formed full-O(3) blobs of every compiled shape pass the blob and
+    # shape checks (without a GPU, creation then stops at the first device
+    # allocation)
+    for base, l_max, n_layers in [(synth.TINY, 1, 3), (synth.TINY, 1, 4), (synth.MAIN, 1, 3), (synth.MAIN, 2, 3),
+                                  (synth.MAIN, 2, 4), (synth.MAIN, 0, 3)]:
+        cfg = dataclasses.replace(base, l_max=l_max, n_layers=n_layers, parity=1)
+        try:
+            al.allegro_destroy(al.allegro_create(synth.make_blob(cfg, 2), mass, cfg.r_cut, l_max, n_layers))
+        except al.AllegroError as err:
+            assert err.code in (6, 9), (base, l_max, n_layers, err)        # E_OOM, E_CUDA
     blob = bytearray(synth.make_blob(synth.MAIN, 1))
     blob[44:48] = (2).to_bytes(4, "little")
     with pytest.raises(al.AllegroError) as e:

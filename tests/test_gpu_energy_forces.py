@@ -5,7 +5,8 @@ small), max |dF| / max |F_ref| <= 1e-5, per-atom energies within
 1e-5 * rms(E_i).  Covers the 1-layer l_max 1 model (passes A, C, A^T) and the
 2-layer l_max 2 model (A, B, C, B^T, A^T), small boxes with several images of
 one partner, tile-straddling rows, sampled atoms of the 110,592-atom
-system, the l_max 0 / 1 widths and a full-O(3) blob."""
+system, the l_max 0 / 1 widths, a two-layer full-O(3) blob and the
+full-O(3) passes of three- and four-layer models."""
 import numpy as np
 import pytest
 import torch
@@ -202,6 +203,101 @@ def test_full_o3_two_layer_blob():
     Er, Fr, Eir, _ = orc.energy_forces(pos, sp, np.diag(cell))
     _compare(E, F, Ei, Er, Fr, Eir)
     assert np.abs(Fs - Fr).max() <= 2e-3
+
+
+def _o3_pair(base, l_max, n_layers):
+    """(cfg, natural blob, full-O(3) blob) sharing the natural-parity model;
+    the pseudotensor weights scaled up (layer-1 pseudotensor mixing x100, the
+    pseudotensor-input columns of later mixings x30) so that the odd paths,
+    which reach the energy only through a second-order chain and weakly for
+    these synthetic weights, move the forces by ~5e-3 of max |F|."""
+    import dataclasses
+    from tests.test_oracle_o3 import _blobs
+    cfg = dataclasses.replace(synth.TINY if base == "tiny" else synth.MAIN, l_max=l_max, n_layers=n_layers)
+    nat, o3 = _blobs(cfg, 42, pseudo_scale=100.0, cross_scale=30.0)
+    return cfg, nat, o3
+
+
+@pytest.mark.parametrize("base,l_max,n_layers", [("tiny", 1, 3), ("tiny", 1, 4), ("main", 1, 3),
+                                                 ("main", 2, 3), ("main", 2, 4)])
+def test_full_o3_deep_models(base, l_max, n_layers):
+    """Full-O(3) models of three and four layers run the full-O(3) FP32 passes
+    (both parities per channel, every even and odd coupling path, one mixing
+    block per output irrep; with four layers also the pseudoscalars of layer 2
+    as inputs of layer 3).  Against the oracle's full-O(3) evaluation at the
+    FP32 bounds (1e-5); and the change from the natural-parity model with the
+    same shared weights (run by the natural passes) must match the oracle's
+    change to 1e-2 of its size (each evaluation rounds to ~1e-6 of max |F|):
+    the odd paths themselves, not only the shared part, are checked."""
+    cfg, nat, o3 = _o3_pair(base, l_max, n_layers)
+    pos, sp, cell = synth.make_ammonia(108, 5)
+    got, ref = {}, {}
+    for key, blob in (("nat", nat), ("o3", o3)):
+        ctx = al.allegro_create(blob, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+        try:
+            got[key] = _gpu(ctx, pos, sp, cell)
+        finally:
+            al.allegro_destroy(ctx)
+        ref[key] = OracleModel(blob).energy_forces(pos, sp, np.diag(cell))[:3]
+        _compare(*got[key], *ref[key])
+    dF, dFr = got["o3"][1] - got["nat"][1], ref["o3"][1] - ref["nat"][1]
+    dEi, dEir = got["o3"][2] - got["nat"][2], ref["o3"][2] - ref["nat"][2]
+    assert np.abs(dFr).max() >= 1e-3 * np.abs(ref["nat"][1]).max()       # the odd paths are active
+    assert np.abs(dF - dFr).max() <= 1e-2 * np.abs(dFr).max()
+    assert np.abs(dEi - dEir).max() <= 1e-2 * np.abs(dEir).max()
+
+
+def test_full_o3_nve_trajectory_and_weights():
+    """Twenty FP32 NVE steps of the 3-layer full-O(3) main model on 432 atoms
+    against the oracle's trajectory (bounds of the FP32 trajectory test); then
+    the weight vector: get_weights returns the blob's tensors in blob order
+    (pseudotensor mixing matrices after the natural ones of each layer), and
+    set_weights with layer 1's pseudotensor mixing zeroed gives the oracle's
+    energy of that model (the device blocks are filled through the same path
+    map as at creation)."""
+    from oracle.md import velocity_verlet
+    cfg, _, o3 = _o3_pair("main", 2, 3)
+    orc = OracleModel(o3)
+    pos, sp, cell = synth.make_ammonia(108, 5)
+    L = np.diag(cell)
+    v0 = synth.make_velocities(sp, 200.0, 1)
+    n = 20
+    ctx = al.allegro_create(o3, MASS, cfg.r_cut, cfg.l_max, cfg.n_layers)
+    try:
+        al.allegro_md_init(ctx, pos, v0, sp.astype(np.int32), cell)
+        en = np.zeros((n, 3))
+        al.allegro_md_step_nve(ctx, 0.5, n, None, en)
+        P, V = np.zeros_like(pos), np.zeros_like(pos)
+        assert al.allegro_md_get_state(ctx, P, V) == n
+        nw = al.allegro_query(ctx, al.ALLEGRO_Q_N_PARAMS)
+        wv = np.zeros(nw, np.float32)
+        al.allegro_get_weights(ctx, wv)
+        offs, o = {}, 0
+        for name in orc.names:
+            offs[name] = (o, orc.w[name].numel())
+            o += orc.w[name].numel()
+        assert o == nw
+        for name in ("layer1.mix1p", "layer2.mix2p", "layer2.mix0"):
+            a, m = offs[name]
+            np.testing.assert_array_equal(wv[a:a + m], orc.w[name].numpy().ravel().astype(np.float32))
+        w2 = wv.copy()
+        for name in orc.names:
+            if name.startswith("layer1.") and name.endswith("p"):
+                a, m = offs[name]
+                w2[a:a + m] = 0.0
+                orc.w[name] = orc.w[name] * 0.0
+        al.allegro_set_weights(ctx, w2)
+        E, F, Ei = _gpu(ctx, pos, sp, cell)
+    finally:
+        al.allegro_destroy(ctx)
+    ref = velocity_verlet(lambda p: OracleModel(o3).energy_forces(p, sp, L)[:2], pos, v0, MASS[sp], L, 0.5, n)
+    d = P - ref["pos"]
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() < 1e-5
+    assert np.abs(V - ref["vel"]).max() < 1e-5
+    np.testing.assert_allclose(en[:, 0], ref["epot"], rtol=0, atol=1e-4 * abs(ref["epot"]).max())
+    Er, Fr, Eir, _ = orc.energy_forces(pos, sp, L)
+    _compare(E, F, Ei, Er, Fr, Eir)
 
 
 def _waves(v):

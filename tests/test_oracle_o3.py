@@ -33,15 +33,15 @@ from tests.test_oracle_model import BIG, MINI, _cluster, _rot, dimer_energy
 MINI3 = dataclasses.replace(MINI, n_layers=3)
 
 
-def _blobs(cfg, seed, pseudo_scale=1.0, pseudo_seed=99):
+def _blobs(cfg, seed, pseudo_scale=1.0, pseudo_seed=99, cross_scale=1.0):
     """(natural blob, full-O(3) blob) with the same natural-parity model.
     A natural mixing matrix of a layer k > 1 has, per channel c, its
     natural-input paths first (columns c P + q, q < Pn) and then the paths
     from pseudotensor inputs (Pn <= q < P); the natural block is the natural
     model's matrix times sqrt(P / Pn), so that with the 1 / sqrt(C P)
     normalisation it acts as in the natural model, and the rest is drawn from
-    pseudo_seed, as are the pseudotensor mixing matrices (times
-    pseudo_scale)."""
+    pseudo_seed (times cross_scale), as are the pseudotensor mixing matrices
+    (times pseudo_scale)."""
     W = synth.make_weights(cfg, seed)
     cfg3 = dataclasses.replace(cfg, parity=1)
     C = cfg.n_channels
@@ -52,7 +52,7 @@ def _blobs(cfg, seed, pseudo_scale=1.0, pseudo_seed=99):
             W3[name] = W[name]
         elif name in W:
             Pn, Pt = W[name].shape[1] // C, c // C
-            M = rng.normal(size=(r, C, Pt))
+            M = cross_scale * rng.normal(size=(r, C, Pt))
             M[:, :, :Pn] = W[name].reshape(r, C, Pn) * np.sqrt(Pt / Pn)
             W3[name] = M.reshape(r, c)
         else:
