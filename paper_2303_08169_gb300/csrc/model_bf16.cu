@@ -480,6 +480,29 @@ struct Mma {
       f();
     }
   }
+  // run() in two halves: start() publishes, issues and commits; work that
+  // touches neither the MMAs' operands nor their accumulator columns may run
+  // before wait(), which every thread that called start() must reach
+  bool live = false;
+  template <class F>
+  AL_DEV void start(F&& issue) {
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    live = *err == 0;
+    if (live && threadIdx.x == 0) {
+      tc_fence_after();
+      issue();
+      mma_commit(bar);
+    }
+  }
+  AL_DEV void wait() {
+    if (live) {
+      if (!mbar_wait(bar, phase, c_wait_cycles)) *err = 1;
+      phase ^= 1u;
+    }
+    tc_fence_after();
+  }
 };
 
 AL_DEV uint32_t lanes(uint32_t tmem) { return tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16); }
@@ -725,7 +748,34 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
   float* s_fc = reinterpret_cast<float*>(A1lo + (kSplit ? kOp128 : 0));
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
+  // Two-body input row (species one-hot, Bessel basis), harmonics and
+  // envelope of tile row r (threads r < 128) from its neighbour-list entry
+  // q; zeros for a row past the list.  Row t of the next tile is formed
+  // while the current tile's z2 MMA runs and kept in registers.
+  float h0[16], Y[NLM], fc;
+  auto pair_row = [&](int t, const MetaPre& q) {
+    const int r = threadIdx.x;
+    fc = 0.0f;
+#pragma unroll
+    for (int x = 0; x < 16; ++x) h0[x] = 0.0f;
+#pragma unroll
+    for (int x = 0; x < NLM; ++x) Y[x] = 0.0f;
+    if (r < kT && q.i >= 0) {
+      float u[3], d, dfc, B[NB];
+      geometry_first<LM>(b, t, r, w.rc, q.i, q.j, q.code, u, d, fc, dfc, Y);
+      bessel<NB>(d, w.rc, B, nullptr);
+      const int zi = b.species[q.i], zj = b.species[q.j];
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {                   // one-hot species (no dynamic register index)
+        h0[x] = zi == x ? 1.0f : 0.0f;
+        h0[2 + x] = zj == x ? 1.0f : 0.0f;
+      }
+#pragma unroll
+      for (int x = 0; x < NB; ++x) h0[4 + x] = B[x];
+    }
+  };
   MetaPre mq = meta_load(b, blockIdx.x, P);
+  pair_row(blockIdx.x, mq);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m, mq);
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
@@ -734,24 +784,6 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
     }
     if (threadIdx.x < kT) {
       const int r = threadIdx.x;
-      float h0[16], Y[NLM], fc = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) h0[q] = 0.0f;
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (r < m.np) {
-        float u[3], d, dfc, B[NB];
-        geometry_first<LM>(b, tile, r, w.rc, m.pi[r], m.pj[r], m.code[r], u, d, fc, dfc, Y);
-        bessel<NB>(d, w.rc, B, nullptr);
-        const int zi = b.species[m.pi[r]], zj = b.species[m.pj[r]];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {                 // one-hot species (no dynamic register index)
-          h0[q] = zi == q ? 1.0f : 0.0f;
-          h0[2 + q] = zj == q ? 1.0f : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < NB; ++q) h0[4 + q] = B[q];
-      }
       s_fc[r] = fc;
 #pragma unroll
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
@@ -764,7 +796,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
       st16_op<Tin, kSplit>(A1, A1lo, r, n0, o);
     });
-    mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });
+    mq = meta_load(b, tile + (int)gridDim.x, P);     // (m holds this tile's entries from here on)
+    mm.start([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });
+    pair_row(tile + (int)gridDim.x, mq);              // next tile's rows: registers and the dR store only
+    mm.wait();
     epi(tmem, 128, 128, [&](int r, int n0, const float* v) {
       float o[16];
       const float fc = s_fc[r];
@@ -776,7 +811,6 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
         for (int q = 0; q < 16; q += 2) sth2(b.X[0], hidx(tile, D, n0 + q, r), o[q], o[q + 1]);
     });
     mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
-    mq = meta_load(b, tile + (int)gridDim.x, P);
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -892,7 +926,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
         else st4<Tin>(T, sw128_off(r, Cf::slice(j) + c0 * pl, 128), v8);
       }
     }
-    mm.run([&] {
+    mm.start([&] {
       // K-step-major over the NLM products: consecutive MMAs write different
       // accumulators, so none waits for the one before it (unrolled: the
       // K-slice offsets are compile-time constants on the issuing thread)
@@ -906,11 +940,12 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
                        kk > 0);
         }
     });
-    {
+    {                                                 // next tile's loads, issued under the mixing MMAs
       const int nt = tile + (int)gridDim.x;
       ld_row<32>(xw, b.X[0], nt, r, D, 32 * h, k == 1 && r < min(kT, P - nt * kT));
       mq = meta_load(b, nt, P);
     }
+    mm.wait();
     {
       const uint32_t base = lanes(tmem);
       for (int j = h; j < NLM; j += 4) {              // components h, h + 4, h + 8
@@ -955,6 +990,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     ld_row<32>(xw, b.X[k - 1], blockIdx.x, r, D, 32 * h, vt);
     ld_row<16>(sw, b.S[k], blockIdx.x, r, C * NS, 16 * max(h - 1, 0), vt && has_s);
   }
+  // envelope and harmonics of tile row r (threads r < 128), one tile ahead:
+  // the next tile's are formed while the current tile's z2 MMA runs
+  float fcn, Yn[NLM];
+  auto geo_row = [&](int t) {
+    fcn = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) Yn[q] = 0.0f;
+    if (threadIdx.x < kT && r < min(kT, P - t * kT)) {
+      float u[3], d, dfc;
+      geometry<LM>(b, t, r, w.rc, u, d, fcn, dfc, Yn);
+    }
+  };
+  geo_row(blockIdx.x);
   MetaPre mq = meta_load(b, blockIdx.x, P);
   for (int tile = blockIdx.x; tile < ntiles && !err; tile += gridDim.x) {
     meta_setup(b, tile, P, m, mq);
@@ -968,13 +1016,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     const bool valid = r < m.np;
     const float* xg = b.X[k - 1];
     if (threadIdx.x < kT) {
-      float u[3], d, fc = 0.0f, dfc, Y[NLM];
+      s_fc[r] = fcn;
 #pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
-      s_fc[r] = fc;
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
+      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Yn[q];
     }
     st_row<Tin, 32>(HA, r, 32 * h, xw);
     if (has_s) {
@@ -990,7 +1034,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       for (int q = 0; q < 16; ++q) o[q] = silu_b(v[q]);
       st16<Tin>(A1, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    mm.start([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    geo_row(tile + (int)gridDim.x);                   // registers only (zeros past the last tile)
+    mm.wait();
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16], xs[16];
       const float fc = s_fc[rr];
@@ -1009,14 +1055,15 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
 #pragma unroll
         for (int q = 0; q < 16; q += 2) sth2(b.X[k], hidx(tile, D, n0 + q, rr), o[q], o[q + 1]);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
-    {
+    mm.start([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
+    {                                                 // next tile's loads, issued under the env MMA
       const int nt = tile + (int)gridDim.x;
       const bool vt = r < min(kT, P - nt * kT);
       ld_row<32>(xw, b.X[k - 1], nt, r, D, 32 * h, vt);
       ld_row<16>(sw, b.S[k], nt, r, C * NS, 16 * max(h - 1, 0), vt && has_s);
       mq = meta_load(b, nt, P);
     }
+    mm.wait();
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -1203,13 +1250,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
       for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, KH, 8, true, 128); });       // [dx^{L-1}, ds]
+    mm.start([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, KH, 8, true, 128); });     // [dx^{L-1}, ds]
 #pragma unroll
-    for (int cp = 0; cp < 2; ++cp)                    // again, for the tensor-product adjoint
+    for (int cp = 0; cp < 2; ++cp)                    // again, for the tensor-product adjoint (under the MMA)
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
         vw[cp][lm] = valid ? reinterpret_cast<const __half2*>(b.V[L - 1])[hidx(tile, CL, lm * C + 4 * h + 2 * cp, r)]
                            : __floats2half2_rn(0.f, 0.f);
+    mm.wait();
     epi(tmem, 0, 128, [&](int rr, int n0, const float* dh) {
       float dx[16];
       tmem_ld16(lanes(tmem) + 288 + n0, dx);
@@ -1427,21 +1475,29 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, NW0, 8, false, 0);          // w0 = emb x^0
     });
     epi_silu_keep_grad(tmem, kZ1, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
-    mm.run([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, false, 0); });     // z2
+    mm.start([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, false, 0); });   // z2
     {
       // dx = dx^k + env^T de; its residual part dx / sqrt 2 goes back into
-      // the same TMEM columns, where the later MMAs accumulate onto it
+      // the same TMEM columns, where the later MMAs accumulate onto it.  The
+      // env^T de columns, the ds columns and dx^k are not the z2 MMA's, so
+      // they are read, zeroed and added while it runs.
       float du = 0.0f;
       float dx[32];
       tmem_ld32(lanes(tmem) + kDX + 32 * h, dx);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) dx[q] += dxo[q];
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};       // ds columns start from zero (exactly its C NS)
+#pragma unroll
+      for (int q = 0; q < 4 * NS; q += 4) tmem_st4(lanes(tmem) + kDS + 4 * NS * h + q, z);
       const float fc = s_fc[r];
+      mm.wait();
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float z2[16], o[16];
         tmem_ld16(lanes(tmem) + kZ2 + 32 * h + 16 * hf, z2);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const float x = dx[16 * hf + q] + dxo[16 * hf + q];
+          const float x = dx[16 * hf + q];
           du = fmaf(x, silu_b(z2[q]), du);
           o[q] = x * fc * kR2 * dsilu_b(z2[q]);
           dx[16 * hf + q] = x * kR2;
@@ -1449,9 +1505,6 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
         st16<Tin>(A1, r, 32 * h + 16 * hf, o);
       }
       tmem_st32(lanes(tmem) + kDX + 32 * h, dx);
-      const float z[4] = {0.f, 0.f, 0.f, 0.f};       // ds columns start from zero (exactly its C NS)
-#pragma unroll
-      for (int q = 0; q < 4 * NS; q += 4) tmem_st4(lanes(tmem) + kDS + 4 * NS * h + q, z);
       tmem_wait_st();
       s_du[h * kT + r] = du * kR2;
     }
@@ -1463,21 +1516,23 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       for (int q = 0; q < 16; ++q) o[q] = da[q] * g1[q];
       st16<Tin>(HA, rr, n0, o);
     });
-    mm.run([&] { mma_k<Tin>(tmem + kDX, HA, 0, Wl0, KH, 8, true, 128, true); });   // [dx, ds] += dz1 W
+    mm.start([&] { mma_k<Tin>(tmem + kDX, HA, 0, Wl0, KH, 8, true, 128, true); });   // [dx, ds] += dz1 W
     // ---- mixing and tensor-product adjoint of layer k ----
     // ds and w0 of this thread's round channels (8 hf + 2h + e): NS and
-    // LM + 1 columns each
+    // LM + 1 columns each; w0 (columns past dx and ds) and the Gamma^k rows
+    // are read while the MMA runs
     float dsv[2][2 * NS], w0[2][2 * NL];
+    if (kEmb)
 #pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      tmem_ldn<2 * NS>(lanes(tmem) + kDS + NS * (8 * hf + 2 * h), dsv[hf]);
-      if (kEmb) tmem_ldn<2 * NL>(lanes(tmem) + kW0 + NL * (8 * hf + 2 * h), w0[hf]);
-    }
+      for (int hf = 0; hf < 2; ++hf) tmem_ldn<2 * NL>(lanes(tmem) + kW0 + NL * (8 * hf + 2 * h), w0[hf]);
+    stage_g<CL>(b.gsum[k], m, s_g);
+    mm.wait();
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) tmem_ldn<2 * NS>(lanes(tmem) + kDS + NS * (8 * hf + 2 * h), dsv[hf]);
     // column 16 lm + c of the operand: this thread's 4 channels of one lm
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
       *reinterpret_cast<uint2*>(DVT + sw128_off(r, 16 * lm + 4 * h, 128)) = make_uint2(dvw[lm][0], dvw[lm][1]);
-    stage_g<CL>(b.gsum[k], m, s_g);
     float dw[2][2 * NL];
 #pragma unroll
     for (int q = 0; q < 2 * NL; ++q) dw[0][q] = dw[1][q] = 0.0f;
@@ -1685,7 +1740,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
     for (int cc = 0; cc < 4; ++cc) e1[cc] = valid ? b.Ek[1][sidx(tile, C, 4 * h + cc, r)] : 0.0f;
     mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });   // z1
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16_op<Tin, kSplit>(A1, A1lo, rr, n0, o); });
-    mm.run([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });   // z2
+    // z2; the env adjoint below (DE, the dY partials, Gamma rows) and the dx^0
+    // loads touch neither its operands nor its accumulator, and run under it
+    mm.start([&] { mma_split<Tin, kSplit>(tmem + 128, A1, A1lo, Wtb1, Wtb1lo, 128, 8, false, 0); });
     {
       float dy[NLM];
       const float* e = e1;
@@ -1707,9 +1764,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) s_dyq[(h * kT + r) * NLM + lm] = dy[lm];
     }
-    float dxo[32];                                    // dx^0, columns 32h..32h+31, in flight during the MMA
+    float dxo[32];                                    // dx^0, columns 32h..32h+31, in flight during the MMAs
 #pragma unroll
     for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
+    mm.wait();
     mm.run([&] { mma_k<Tin>(tmem + 288, DE, 0, Wenv, 128, 1, true, 16); });    // env1^T de
     if (h == 0)
 #pragma unroll
