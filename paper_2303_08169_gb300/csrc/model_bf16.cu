@@ -842,9 +842,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
   uint8_t* Wmix = Wemb + Cf::kImgEmb;
   uint8_t* X = Wmix + NL * kImgMix;
   uint8_t* T = X + kOp128;
-  float* s_Y = reinterpret_cast<float*>(T + Cf::kOpT);
-  float* s_g = s_Y + kT * NLM;            // [kSegCap][CL]
+  float* s_Yb = reinterpret_cast<float*>(T + Cf::kOpT);   // [2][kT][NLM] harmonics (k = 1), one tile ahead
+  float* s_g = s_Yb + 2 * kT * NLM;       // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  auto y_fill = [&](int t, float* g) {               // quarter 0: harmonics of row r of tile t (0 past the list)
+    float u[3], d, fc, dfc, Y[NLM];
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    if (r < min(kT, P - t * kT)) geometry<LM>(b, t, r, w.rc, u, d, fc, dfc, Y);
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) g[r * NLM + q] = Y[q];
+  };
+  if (k == 1 && h == 0) y_fill(blockIdx.x, s_Yb);
+  int gb = 0;
   uint32_t xw[16];                                    // x^0 operand words (k = 1), one tile ahead
   ld_row<32>(xw, b.X[0], blockIdx.x, r, D, 32 * h, k == 1 && r < min(kT, P - (int)blockIdx.x * kT));
   MetaPre mq = meta_load(b, blockIdx.x, P);
@@ -858,18 +868,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
       else prefetch_rows_h(b.V[k - 1], CL, nt);
     }
     const bool valid = r < m.np;
-    if (threadIdx.x < kT) {
-      float u[3], d, fc, dfc, Y[NLM];
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (r < m.np) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-    }
+    const float* s_Y = s_Yb + gb * kT * NLM;          // (the harmonics serve the embedding only)
     if (k == 1) {
       st_row<Tin, 32>(X, r, 32 * h, xw);
       stage_g<CL>(b.gsum[k], m, s_g);
-      mm.run([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, NW0, 8, false, 0); });
+      mm.start([&] { mma_k<Tin>(tmem + 0, X, 0, Wemb, NW0, 8, false, 0); });
+      if (h == 0) y_fill(tile + (int)gridDim.x, s_Yb + (gb ^ 1) * kT * NLM);   // the next tile's, under the MMA
+      gb ^= 1;
+      mm.wait();
     } else {
       stage_g<CL>(b.gsum[k], m, s_g);
       __syncthreads();
@@ -1124,12 +1130,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   uint8_t* A1 = HA + kOpH;
   uint8_t* AE = A1 + kOp128;
   float* s_dg = reinterpret_cast<float*>(HA);          // reuses HA + A1 after the last MMA
-  float* s_fc = reinterpret_cast<float*>(AE + kOp64);
-  float* s_sig = s_fc + kT;
+  float* s_fcb = reinterpret_cast<float*>(AE + kOp64);   // [2][kT] envelope; the next tile's filled under z2
+  float* s_sig = s_fcb + 2 * kT;
   float* s_eq = s_sig + kT;                            // [4][kT] energy partials per quarter
   float* s_du = s_eq + 4 * kT;                         // [4][kT]
   float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  auto fc_fill = [&](int t, float* g) {               // quarter 0: envelope of row r of tile t (0 past the list)
+    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+    if (r < min(kT, P - t * kT)) geometry<LM>(b, t, r, w.rc, u, d, fc, dfc, Y);
+    g[r] = fc;
+  };
+  if (h == 0) fc_fill(blockIdx.x, s_fcb);
+  int gb = 0;
   // V^{L-1} (one FP16 channel pair per word) and x^{L-1} operand words of a
   // tile, in registers; the next tile's are loaded during this tile's tail
   __half2 vw[2][NLM];
@@ -1147,12 +1160,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     }
     const bool valid = r < m.np;
     const float* xg = b.X[L - 1];
-    if (h == 0) {
-      float u[3], d, fc = 0.0f, dfc, Y[NLM];
-      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
-      s_fc[r] = fc;
-      s_sig[r] = valid ? w.sigma[mq.zi] : 0.0f;
-    }
+    const float* s_fc = s_fcb + gb * kT;
+    if (h == 0) s_sig[r] = valid ? w.sigma[mq.zi] : 0.0f;
     stage_g<CL>(b.gsum[L], m, s_g);
     // z1 = [x^{L-1}, S] W_0: the x^{L-1} K-steps run while the tensor product
     // computes S
@@ -1185,7 +1194,10 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     }
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, NS, false, 0, true); });
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
-    mm.run([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    mm.start([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
+    if (h == 0) fc_fill(tile + (int)gridDim.x, s_fcb + (gb ^ 1) * kT);   // the next tile's, under the MMA
+    gb ^= 1;
+    mm.wait();
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
       float o[16], xs[16];
       const float fc = s_fc[rr];
@@ -1387,12 +1399,27 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
   uint8_t* DW0 = HA;
   float* s_dg = reinterpret_cast<float*>(A1);          // [kT][CLH], rounds only
   float* s_dy = reinterpret_cast<float*>(HA + kOp64);  // [4][kT][NLM], tile end only
-  float* s_fc = reinterpret_cast<float*>(A1 + kRegA1);
-  float* s_Y = s_fc + kT;
-  float* s_du = s_Y + kT * NLM;                        // [4][kT]
+  // two geometry buffers [fc | Y] (the next tile's is filled under the
+  // current tile's first MMA)
+  float* s_geo = reinterpret_cast<float*>(A1 + kRegA1);
+  constexpr int kGeo = kT + kT * NLM;
+  float* s_du = s_geo + 2 * kGeo;                      // [4][kT]
   float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
   constexpr int kZ1 = 32, kZ2 = 160, kDX = 288, kDS = 416, kW0 = 464, kJ0 = 416, kJ = 0;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
+  // envelope and harmonics of row r of tile t into buffer g (quarter 0; zeros
+  // past the list)
+  auto geo_fill = [&](int t, float* g) {
+    float u[3], d, fc = 0.0f, dfc, Y[NLM];
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
+    if (r < min(kT, P - t * kT)) geometry<LM>(b, t, r, w.rc, u, d, fc, dfc, Y);
+    g[r] = fc;
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) g[kT + r * NLM + q] = Y[q];
+  };
+  if (h == 0) geo_fill(blockIdx.x, s_geo);
+  int gb = 0;                                         // this tile's geometry buffer
   // the next tile's dV^k words (channels 4h..4h+3) and neighbour-list rows,
   // loaded during this tile's tail
   uint32_t dvw[NLM][2];
@@ -1422,18 +1449,11 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       if (!kEmb) prefetch_rows_h(b.V[k - 1], CL, nt);
     }
     const bool valid = r < m.np;
+    const float* s_fc = s_geo + gb * kGeo;
+    const float* s_Y = s_fc + kT;
     float ew[4];                                      // e^{k+1} of channels 4h..4h+3 (stored by pass B2)
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) ew[cc] = valid ? b.Ek[k + 1][sidx(tile, C, 4 * h + cc, r)] : 0.0f;
-    if (h == 0) {
-      float u[3], d, fc = 0.0f, dfc, Y[NLM];
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-      if (valid) geometry<LM>(b, tile, r, w.rc, u, d, fc, dfc, Y);
-      s_fc[r] = fc;
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
-    }
     stage_g<CL>(b.dgsum[k + 1], m, s_g);
     uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env adjoint
     const bool has_s = h >= 1 && h <= NS;             // quarters 1..NS hold S^k columns 16 (h - 1)..
@@ -1469,11 +1489,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
     float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
 #pragma unroll
     for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
-    mm.run([&] {
+    mm.start([&] {
       mma_k<Tin>(tmem + kDX, DE, 0, Wenv, 128, 1, true, 16);                    // env^T de
       mma_k<Tin>(tmem + kZ1, HA, 0, Wl0, 128, KH / 16, false, 0);               // z1
       if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, NW0, 8, false, 0);          // w0 = emb x^0
     });
+    if (h == 0) geo_fill(tile + (int)gridDim.x, s_geo + (gb ^ 1) * kGeo);   // the next tile's, under the MMAs
+    gb ^= 1;
+    mm.wait();
     epi_silu_keep_grad(tmem, kZ1, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.start([&] { mma_k<Tin>(tmem + kZ2, A1, 0, Wl1, 128, 8, false, 0); });   // z2
     {
@@ -1853,14 +1876,14 @@ struct Smem {
            4 * (kT + kT * NLM + kT * EP);
   }
   static constexpr size_t b1 = 1024 + Tc<LM>::kImgEmb + NL * kImgMix + kOp128 + Tc<LM>::kOpT +
-                               4 * (kT * NLM + kSegCap * CL);
+                               4 * (2 * kT * NLM + kSegCap * CL);
   static constexpr size_t b2 = 1024 + kImgLat0 + kImgLat1 + kImgEnv + kOpH + kOp128 + 4 * (kT + kT * NLM + kT * EP);
   static constexpr size_t c(bool split) {
     return 1024 + kImgLat0 + kImgLat1 + (split ? 2 : 1) * kImgE0 + kOpH + kOp128 + kOp64 +
-           4 * (10 * kT + kSegCap * CL);
+           4 * (11 * kT + kSegCap * CL);
   }
   static constexpr size_t bt = 1024 + kImgEnv + kImgLat0 + kImgLat1 + Tc<LM>::kImgEmb + NL * kImgMix + kOpH +
-                               reg_a1<LM>() + 4 * (kT + kT * NLM + 4 * kT + kSegCap * CL);
+                               reg_a1<LM>() + 4 * (2 * (kT + kT * NLM) + 4 * kT + kSegCap * CL);
   static constexpr size_t at(bool split) {
     return 1024 + kImgTb0 + (split ? 2 : 1) * kImgTb1 + kImgEnv + kOp64 + (split ? 3 : 2) * kOp128 +
            4 * (2 * kT * GP + 2 * kT * NLM + 4 * kT + kSegCap * CL);
