@@ -1399,6 +1399,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
   uint8_t* DW0 = HA;
   float* s_dg = reinterpret_cast<float*>(A1);          // [kT][CLH], rounds only
   float* s_dy = reinterpret_cast<float*>(HA + kOp64);  // [4][kT][NLM], tile end only
+  float* s_dxs = reinterpret_cast<float*>(HA);         // [D][kT] dx^{k-1} staging, tile end only
   // two geometry buffers [fc | Y] (the next tile's is filled under the
   // current tile's first MMA)
   float* s_geo = reinterpret_cast<float*>(A1 + kRegA1);
@@ -1455,6 +1456,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) ew[cc] = valid ? b.Ek[k + 1][sidx(tile, C, 4 * h + cc, r)] : 0.0f;
     stage_g<CL>(b.dgsum[k + 1], m, s_g);
+    if (threadIdx.x == 0) bulk_wait_read();           // the previous tile's dx^{k-1} copy has read HA
     uint32_t xw2[16], sw[8];                          // [x^{k-1}, S^k] operand, in flight during the env adjoint
     const bool has_s = h >= 1 && h <= NS;             // quarters 1..NS hold S^k columns 16 (h - 1)..
     ld_row<32>(xw2, b.X[k - 1], tile, r, D, 32 * h, valid);
@@ -1486,14 +1488,14 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       float z[16] = {};
       st16<Tin>(HA, r, KH, z);
     }
-    float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
-#pragma unroll
-    for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
     mm.start([&] {
       mma_k<Tin>(tmem + kDX, DE, 0, Wenv, 128, 1, true, 16);                    // env^T de
       mma_k<Tin>(tmem + kZ1, HA, 0, Wl0, 128, KH / 16, false, 0);               // z1
       if (kEmb) mma_k<Tin>(tmem + kW0, HA, 0, Wemb, NW0, 8, false, 0);          // w0 = emb x^0
     });
+    float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
+#pragma unroll
+    for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
     if (h == 0) geo_fill(tile + (int)gridDim.x, s_geo + (gb ^ 1) * kGeo);   // the next tile's, under the MMAs
     gb ^= 1;
     mm.wait();
@@ -1650,13 +1652,8 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dyo[lm] = valid ? b.dY[sidx(tile, NLM, lm, r)] : 0.0f;
     }
-    {
-      float v[32];
-      tmem_ld32(lanes(tmem) + kDX + 32 * h, v);
-      if (valid)
-#pragma unroll
-        for (int q = 0; q < 32; ++q) b.dX[sidx(tile, D, 32 * h + q, r)] = v[q];
-    }
+    float dxv[32];                                    // dx^{k-1}, columns 32h..32h+31
+    tmem_ld32(lanes(tmem) + kDX + 32 * h, dxv);
     ld_next(tile + (int)gridDim.x);                   // zeros past the last tile
     mq = meta_load(b, tile + (int)gridDim.x, P);
 #pragma unroll
@@ -1670,7 +1667,20 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
                                                   (s_dy[(2 * kT + r) * NLM + lm] + s_dy[(3 * kT + r) * NLM + lm]));
     }
     __syncthreads();
+    // dx^{k-1} leaves by one bulk copy of the tile's contiguous tile-SoA block
+    // (feature-major, 128 rows per feature), staged over HA and the start of
+    // A1 (both dead here); rows past the list carry values nothing reads.
+    // Thread 0 waits for the copy's reads before the next tile writes there.
+#pragma unroll
+    for (int q = 0; q < 32; ++q) s_dxs[(32 * h + q) * kT + r] = dxv[q];
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk_s2g(b.dX + (size_t)tile * D * kT, s_dxs, (uint32_t)(D * kT * 4));
+      bulk_commit();
+    }
   }
+  if (threadIdx.x == 0) bulk_wait_all();
   BF_EPILOGUE
 }
 
@@ -1896,6 +1906,7 @@ struct Smem {
   static_assert(kOpH + kOp128 >= 4 * kT * Tc<LM>::CLP, "pass C reuses HA + A1 for the dGamma contributions");
   static_assert(kOp128 >= 4 * 4 * kT * NLM, "pass A^T keeps the dY partials in X");
   static_assert(kOpH >= kOp64 + 4 * 4 * kT * NLM, "pass B^T keeps the dY partials in HA after its first 64 columns");
+  static_assert(kOpH + reg_a1<LM>() >= 4 * D * kT, "pass B^T stages its dx^{k-1} tile over HA and A1");
 };
 template struct Smem<0>;
 template struct Smem<1>;

@@ -133,6 +133,19 @@ UM_DEV void bulk_g2s(void* smem, const void* gmem, uint32_t bytes, uint64_t* mba
       : "memory");
 }
 
+// ---- bulk copy shared -> global (16-byte aligned, size % 16 == 0) ----
+// Completion through bulk groups: commit after the copies, then wait until
+// their shared-memory sources have been read (the source may be rewritten)
+// or until the writes are done.  Neither wait depends on another thread.
+UM_DEV void bulk_s2g(void* gmem, const void* smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gmem), "r"(smem_u32(smem)),
+               "r"(bytes)
+               : "memory");
+}
+UM_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+UM_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+UM_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // Hint only: bring [gmem, gmem + bytes) into L2 (16-byte aligned, bytes a
 // multiple of 16); nothing waits for it.
 UM_DEV void bulk_prefetch_l2(const void* gmem, uint32_t bytes) {
