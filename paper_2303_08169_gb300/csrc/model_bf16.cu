@@ -294,6 +294,12 @@ AL_DEV size_t hidx(int tile, int W, int f, int r) { return ((size_t)tile * (W >>
 AL_DEV float r16(float x) { return __half2float(__float2half_rn(x)); }
 AL_DEV float2 ldh2(const float* a, size_t i) { return __half22float2(reinterpret_cast<const __half2*>(a)[i]); }
 AL_DEV void sth2(float* a, size_t i, float x, float y) { reinterpret_cast<__half2*>(a)[i] = __floats2half2_rn(x, y); }
+AL_DEV uint32_t h2word(float x, float y) {
+  const __half2 v = __floats2half2_rn(x, y);
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  return u;
+}
 // dV^k is consumed only as the mixing-adjoint MMA operand of pass B1^T, so
 // it is stored in the operand type itself (component-major, two channels per
 // word, the layout of V^k): the same values the operand held when dV^k was
@@ -748,6 +754,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
   float* s_fc = reinterpret_cast<float*>(A1lo + (kSplit ? kOp128 : 0));
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
+  uint32_t* s_xs = reinterpret_cast<uint32_t*>(A1);   // [D/2][kT] x^0 words, from the x^0 epilogue to the env MMA
   // Two-body input row (species one-hot, Bessel basis), harmonics and
   // envelope of tile row r (threads r < 128) from its neighbour-list entry
   // q; zeros for a row past the list.  Row t of the next tile is formed
@@ -789,6 +796,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
       for (int q = 0; q < NLM; ++q) s_Y[r * NLM + q] = Y[q];
       st_h0<Tin, kSplit>(H0, r, h0);
     }
+    if (threadIdx.x == 0) bulk_wait_read();           // the previous tile's x^0 copy has read A1
     mm.run([&] { mma_k<Tin>(tmem + 0, H0, 0, Wtb0, 128, kSplit ? 3 : 1, false, 0); });
     epi(tmem, 0, 128, [&](int r, int n0, const float* v) {
       float o[16];
@@ -806,11 +814,16 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = r16(fc * silu_b(v[q]));
       st16<Tin>(X, r, n0, o);
-      if (r < m.np)
 #pragma unroll
-        for (int q = 0; q < 16; q += 2) sth2(b.X[0], hidx(tile, D, n0 + q, r), o[q], o[q + 1]);
+      for (int q = 0; q < 16; q += 2) s_xs[((n0 + q) >> 1) * kT + r] = h2word(o[q], o[q + 1]);
     });
-    mm.run([&] { mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0); });
+    // env MMA; the x^0 tile (tile-SoA words, staged in A1, dead since z2)
+    // leaves by one bulk copy issued with it
+    mm.run([&] {
+      mma_k<Tin>(tmem + 256, X, 0, Wenv, 16, 8, false, 0);
+      bulk_s2g(b.X[0] + (size_t)tile * (D / 2) * kT, s_xs, (uint32_t)(D / 2 * kT * 4));
+      bulk_commit();
+    });
     if (threadIdx.x < kT) {
       float v[16];
       tmem_ld16(lanes(tmem) + 256, v);
@@ -824,6 +837,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_a(BfW w, PassBufs b) {
     seg_store(b.gam[1], m, CL, [&](int p, int x) { return s_e[p * EP + x / NLM] * s_Y[p * NLM + x % NLM]; });
     __syncthreads();
   }
+  if (threadIdx.x == 0) bulk_wait_all();
   BF_EPILOGUE
 }
 
@@ -869,6 +883,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     const bool valid = r < m.np;
     const float* s_Y = s_Yb + gb * kT * NLM;          // (the harmonics serve the embedding only)
+    if (threadIdx.x == 0) bulk_wait_read();           // the previous tile's V^k copy has read T
     if (k == 1) {
       st_row<Tin, 32>(X, r, 32 * h, xw);
       stage_g<CL>(b.gsum[k], m, s_g);
@@ -953,17 +968,25 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b1(BfW w, PassBufs b, int k) {
     }
     mm.wait();
     {
+      // V^k leaves by one bulk copy of its tile-SoA words, staged in T (the
+      // mixing MMAs have read it)
+      uint32_t* s_vs = reinterpret_cast<uint32_t*>(T);
       const uint32_t base = lanes(tmem);
       for (int j = h; j < NLM; j += 4) {              // components h, h + 4, h + 8
         float v[16];
         tmem_ld16(base + 64 + 16 * j, v);
-        if (valid)
 #pragma unroll
-          for (int co = 0; co < C; co += 2) sth2(b.V[k], hidx(tile, CL, j * C + co, r), v[co], v[co + 1]);
+        for (int co = 0; co < C; co += 2) s_vs[((j * C + co) >> 1) * kT + r] = h2word(v[co], v[co + 1]);
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        bulk_s2g(b.V[k] + (size_t)tile * (CL / 2) * kT, s_vs, (uint32_t)(CL / 2 * kT * 4));
+        bulk_commit();
       }
     }
-    __syncthreads();
   }
+  if (threadIdx.x == 0) bulk_wait_all();
   BF_EPILOGUE
 }
 
@@ -986,6 +1009,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
   float* s_fc = reinterpret_cast<float*>(A1 + kOp128);
   float* s_Y = s_fc + kT;
   float* s_e = s_Y + kT * NLM;
+  uint32_t* s_xs = reinterpret_cast<uint32_t*>(A1);   // [D/2][kT] x^k words, from the x^k epilogue to the env MMA
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   // [x^{k-1}, S^k] operand words, one tile ahead: quarter h holds x^{k-1}
   // columns 32h..32h+31 and, for 1 <= h <= NS, S^k columns 16(h-1)..
@@ -1033,6 +1057,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
       float z[16] = {};
       st16<Tin>(HA, r, KH, z);
     }
+    if (threadIdx.x == 0) bulk_wait_read();           // the previous tile's x^k copy has read A1
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 0, Wl0, 128, KH / 16, false, 0); });
     epi(tmem, 0, 128, [&](int rr, int n0, const float* v) {
       float o[16];
@@ -1057,11 +1082,16 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
         o[q + 1] = r16((x.y + fc * silu_b(v[q + 1])) * kR2);
       }
       st16<Tin>(HA, rr, n0, o);
-      if (valid)
 #pragma unroll
-        for (int q = 0; q < 16; q += 2) sth2(b.X[k], hidx(tile, D, n0 + q, rr), o[q], o[q + 1]);
+      for (int q = 0; q < 16; q += 2) s_xs[((n0 + q) >> 1) * kT + rr] = h2word(o[q], o[q + 1]);
     });
-    mm.start([&] { mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0); });
+    // env MMA; the x^k tile (tile-SoA words, staged in A1, dead since z2)
+    // leaves by one bulk copy issued with it
+    mm.start([&] {
+      mma_k<Tin>(tmem + 256, HA, 0, Wenv, 16, 8, false, 0);
+      bulk_s2g(b.X[k] + (size_t)tile * (D / 2) * kT, s_xs, (uint32_t)(D / 2 * kT * 4));
+      bulk_commit();
+    });
     {                                                 // next tile's loads, issued under the env MMA
       const int nt = tile + (int)gridDim.x;
       const bool vt = r < min(kT, P - nt * kT);
@@ -1083,6 +1113,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_b2(BfW w, PassBufs b, int k) {
     seg_store(b.gam[k + 1], m, CL, [&](int p, int x) { return s_e[p * EP + x / NLM] * s_Y[p * NLM + x % NLM]; });
     __syncthreads();
   }
+  if (threadIdx.x == 0) bulk_wait_all();
   BF_EPILOGUE
 }
 
@@ -1907,6 +1938,8 @@ struct Smem {
   static_assert(kOp128 >= 4 * 4 * kT * NLM, "pass A^T keeps the dY partials in X");
   static_assert(kOpH >= kOp64 + 4 * 4 * kT * NLM, "pass B^T keeps the dY partials in HA after its first 64 columns");
   static_assert(kOpH + reg_a1<LM>() >= 4 * D * kT, "pass B^T stages its dx^{k-1} tile over HA and A1");
+  static_assert(kOp128 >= 2 * D * kT, "passes A and B2 stage their x tile in A1");
+  static_assert(Tc<LM>::kOpT >= 2 * CL * kT, "pass B1 stages its V^k tile in T");
 };
 template struct Smem<0>;
 template struct Smem<1>;
