@@ -1167,12 +1167,24 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
   float* s_du = s_eq + 4 * kT;                         // [4][kT]
   float* s_g = s_du + 4 * kT;                          // [kSegCap][CL]
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
-  auto fc_fill = [&](int t, float* g) {               // quarter 0: envelope of row r of tile t (0 past the list)
+  // quarter 0: envelope of row r of tile t (0 past the list); the pair
+  // separation is loaded (fc_ld) well before it is used (fc_put)
+  auto fc_ld = [&](int t, float* d3) -> bool {
+    const bool v = r < min(kT, P - t * kT);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d3[a] = v ? b.dR[sidx(t, 3, a, r)] : 0.0f;
+    return v;
+  };
+  auto fc_put = [&](bool v, const float* d3, float* g) {
     float u[3], d, fc = 0.0f, dfc, Y[NLM];
-    if (r < min(kT, P - t * kT)) geometry<LM>(b, t, r, w.rc, u, d, fc, dfc, Y);
+    if (v) geo_from_delta<LM>(d3[0], d3[1], d3[2], w.rc, u, d, fc, dfc, Y);
     g[r] = fc;
   };
-  if (h == 0) fc_fill(blockIdx.x, s_fcb);
+  if (h == 0) {
+    float d3[3];
+    const bool v = fc_ld(blockIdx.x, d3);
+    fc_put(v, d3, s_fcb);
+  }
   int gb = 0;
   // V^{L-1} (one FP16 channel pair per word) and x^{L-1} operand words of a
   // tile, in registers; the next tile's are loaded during this tile's tail
@@ -1191,6 +1203,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     }
     const bool valid = r < m.np;
     const float* xg = b.X[L - 1];
+    float nd[3];                                      // the next tile's pair separation (quarter 0)
+    bool nv = false;
+    if (h == 0) nv = fc_ld(tile + (int)gridDim.x, nd);
     const float* s_fc = s_fcb + gb * kT;
     if (h == 0) s_sig[r] = valid ? w.sigma[mq.zi] : 0.0f;
     stage_g<CL>(b.gsum[L], m, s_g);
@@ -1226,7 +1241,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, NS, false, 0, true); });
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
     mm.start([&] { mma_k<Tin>(tmem + 128, A1, 0, Wl1, 128, 8, false, 0); });
-    if (h == 0) fc_fill(tile + (int)gridDim.x, s_fcb + (gb ^ 1) * kT);   // the next tile's, under the MMA
+    if (h == 0) fc_put(nv, nd, s_fcb + (gb ^ 1) * kT);   // the next tile's, under the MMA
     gb ^= 1;
     mm.wait();
     epi(tmem, 128, 128, [&](int rr, int n0, const float* v) {
@@ -1341,16 +1356,19 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
     mq = meta_load<true>(b, tile + (int)gridDim.x, P);
     __syncthreads();
     {
-      // energy partials in FP64, one warp per segment: lanes stride the
-      // segment's pairs, then a shuffle tree (fixed order)
+      // energy partials per (tile, centre atom), one warp per segment: lanes
+      // stride the segment's pairs, then a shuffle tree (fixed order) in
+      // FP32 (at most 128 pair energies; GB300's FP64 pipe is a small
+      // fraction of its FP32 rate); the partial is stored in FP64 and the
+      // per-atom and total sums over tiles stay FP64
       const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
       for (int sg = wid; sg < m.nseg; sg += (int)(blockDim.x >> 5)) {
-        double acc = 0.0;
+        float acc = 0.0f;
         for (int p = m.sstart[sg] + lane; p < m.sstart[sg + 1]; p += 32)
-          acc += (double)((s_eq[p] + s_eq[kT + p]) + (s_eq[2 * kT + p] + s_eq[3 * kT + p]));
+          acc += (s_eq[p] + s_eq[kT + p]) + (s_eq[2 * kT + p] + s_eq[3 * kT + p]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) b.epart[m.tile + m.atom[sg]] = acc;
+        if (lane == 0) b.epart[m.tile + m.atom[sg]] = (double)acc;
       }
     }
     if (threadIdx.x < kT && valid) {
@@ -1440,17 +1458,28 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
   constexpr int kZ1 = 32, kZ2 = 160, kDX = 288, kDS = 416, kW0 = 464, kJ0 = 416, kJ = 0;
   const int r = threadIdx.x & (kT - 1), h = threadIdx.x >> 7;
   // envelope and harmonics of row r of tile t into buffer g (quarter 0; zeros
-  // past the list)
-  auto geo_fill = [&](int t, float* g) {
+  // past the list); the pair separation is loaded (geo_ld) well before it is
+  // used (geo_put)
+  auto geo_ld = [&](int t, float* d3) -> bool {
+    const bool v = r < min(kT, P - t * kT);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d3[a] = v ? b.dR[sidx(t, 3, a, r)] : 0.0f;
+    return v;
+  };
+  auto geo_put = [&](bool v, const float* d3, float* g) {
     float u[3], d, fc = 0.0f, dfc, Y[NLM];
 #pragma unroll
     for (int q = 0; q < NLM; ++q) Y[q] = 0.0f;
-    if (r < min(kT, P - t * kT)) geometry<LM>(b, t, r, w.rc, u, d, fc, dfc, Y);
+    if (v) geo_from_delta<LM>(d3[0], d3[1], d3[2], w.rc, u, d, fc, dfc, Y);
     g[r] = fc;
 #pragma unroll
     for (int q = 0; q < NLM; ++q) g[kT + r * NLM + q] = Y[q];
   };
-  if (h == 0) geo_fill(blockIdx.x, s_geo);
+  if (h == 0) {
+    float d3[3];
+    const bool v = geo_ld(blockIdx.x, d3);
+    geo_put(v, d3, s_geo);
+  }
   int gb = 0;                                         // this tile's geometry buffer
   // the next tile's dV^k words (channels 4h..4h+3) and neighbour-list rows,
   // loaded during this tile's tail
@@ -1481,6 +1510,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       if (!kEmb) prefetch_rows_h(b.V[k - 1], CL, nt);
     }
     const bool valid = r < m.np;
+    float nd[3];                                      // the next tile's pair separation (quarter 0)
+    bool nv = false;
+    if (h == 0) nv = geo_ld(tile + (int)gridDim.x, nd);
     const float* s_fc = s_geo + gb * kGeo;
     const float* s_Y = s_fc + kT;
     float ew[4];                                      // e^{k+1} of channels 4h..4h+3 (stored by pass B2)
@@ -1527,7 +1559,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
     float dxo[32];                                    // dx^k from the layer above, columns 32h..32h+31
 #pragma unroll
     for (int q = 0; q < 32; ++q) dxo[q] = valid ? b.dX[sidx(tile, D, 32 * h + q, r)] : 0.0f;
-    if (h == 0) geo_fill(tile + (int)gridDim.x, s_geo + (gb ^ 1) * kGeo);   // the next tile's, under the MMAs
+    if (h == 0) geo_put(nv, nd, s_geo + (gb ^ 1) * kGeo);   // the next tile's, under the MMAs
     gb ^= 1;
     mm.wait();
     epi_silu_keep_grad(tmem, kZ1, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
