@@ -626,6 +626,30 @@ template <class Tin>
 AL_DEV void st1(uint8_t* A, int r, int c, float v) {
   *reinterpret_cast<uint16_t*>(A + sw128_off(r, c, 128)) = Op<Tin>::bits(v);
 }
+// N (4, 8 or 12) consecutive operand columns from c0 (c0 % 4 == 0) of row r
+// as 8- and 16-byte stores (one or two per row instead of N 2-byte ones)
+template <class Tin, int N>
+AL_DEV void st_cols(uint8_t* A, int r, int c0, const float* v) {
+  static_assert(N == 4 || N == 8 || N == 12, "4, 8 or 12 columns");
+  if constexpr (N == 4) {
+    st4<Tin>(A, sw128_off(r, c0, 128), v);
+  } else if constexpr (N == 8) {
+    if ((c0 & 7) == 0) {
+      st8<Tin>(A, sw128_off(r, c0, 128), v);
+    } else {
+      st4<Tin>(A, sw128_off(r, c0, 128), v);
+      st4<Tin>(A, sw128_off(r, c0 + 4, 128), v + 4);
+    }
+  } else {
+    if ((c0 & 7) == 0) {
+      st8<Tin>(A, sw128_off(r, c0, 128), v);
+      st4<Tin>(A, sw128_off(r, c0 + 8, 128), v + 8);
+    } else {
+      st4<Tin>(A, sw128_off(r, c0, 128), v);
+      st8<Tin>(A, sw128_off(r, c0 + 4, 128), v + 4);
+    }
+  }
+}
 
 // Operand staging of FP16-pair state in two steps, so that a tile's loads
 // are all issued before any of them is waited for: ld_row reads the N / 2
@@ -1235,8 +1259,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
           Cf::fwd_scalar(V2[e], G, S + (cp + e) * NS);
         }
       }
-#pragma unroll
-      for (int q = 0; q < 4 * NS; ++q) st1<Tin>(HA, r, D + 4 * NS * h + q, S[q]);
+      st_cols<Tin, 4 * NS>(HA, r, D + 4 * NS * h, S);
     }
     mm.run([&] { mma_k<Tin>(tmem + 0, HA, 8, Wl0 + 2 * (128 * 128), 128, NS, false, 0, true); });
     epi_silu_keep_grad(tmem, 0, [&](int rr, int n0, const float* o) { st16<Tin>(A1, rr, n0, o); });   // z1
@@ -1530,6 +1553,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
       const float* e = ew;                            // e^{k+1} of channels 4h..4h+3
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
+      float de[4];                                    // de of channels 4h..4h+3: one 8-byte store
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
@@ -1541,8 +1565,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_bt(BfW w, PassBufs b, int k) {
           acc = fmaf(dG[lm], s_Y[r * NLM + lm], acc);
           dy[lm] = fmaf(dG[lm], e[cc], dy[lm]);
         }
-        st1<Tin>(DE, r, c, acc);
+        de[cc] = acc;
       }
+      st_cols<Tin, 4>(DE, r, 4 * h, de);
     }
     st_row<Tin, 32>(HA, r, 32 * h, xw2);
     if (has_s) {
@@ -1844,6 +1869,7 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
       const float* e = e1;
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) dy[lm] = 0.0f;
+      float de[4];                                    // de of channels 4h..4h+3: one 8-byte store
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int c = 4 * h + cc;
@@ -1855,8 +1881,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_at(BfW w, PassBufs b) {
           acc = fmaf(dG[lm], s_Y[r * NLM + lm], acc);
           dy[lm] = fmaf(dG[lm], e[cc], dy[lm]);
         }
-        st1<Tin>(DE, r, c, acc);
+        de[cc] = acc;
       }
+      st_cols<Tin, 4>(DE, r, 4 * h, de);
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) s_dyq[(h * kT + r) * NLM + lm] = dy[lm];
     }
