@@ -1413,9 +1413,9 @@ __global__ void __launch_bounds__(kThr4, 1) k_bf_c(BfW w, PassBufs b) {
 // they share one kernel.  dS^k stays in TMEM and dx^{k-1} is
 // accumulated in one set of TMEM columns (residual dx / sqrt 2, then
 // dz1 W_0, then emb^T dw0) and written once.
-// Shared memory: HA holds x^k, then [x^{k-1}, S^k], dz1, the dV^k operand
-// and at the end dw0 and the dy partials; A1 holds de, SiLU(z1), dz2 and
-// during the mixing-adjoint rounds the dGamma^k staging of eight channels.
+// Shared memory: HA holds [x^{k-1}, S^k], dz1, the dV^k operand, then dw0,
+// the dy partials and (with A1) the dx^{k-1} staging; A1 holds de, SiLU(z1),
+// dz2 and during the mixing-adjoint rounds the dGamma^k staging of 8 channels.
 // e^{k+1} is read from memory (stored by pass B2).
 // TMEM columns: z1 [32, 160); z2 and da1 [160, 288); dx [288,
 // 416); ds [416, 416 + C NS); w0 [464, 464 + NW0); in the rounds, the l3 = 0

@@ -2,7 +2,7 @@
 // PTX: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation in TMEM),
 // shared-memory matrix descriptors for K-major 128-byte-swizzled tiles,
 // TMEM allocation and loads, mbarriers with bounded waits, and 1-D bulk
-// copies (cp.async.bulk) from global to shared memory.
+// copies (cp.async.bulk) from global to shared memory and back.
 //
 // Operand layout ("SW128 K-major"): a [R x K] bf16 tile (R % 8 == 0) is split
 // into K-blocks of 64 elements (128 bytes per row); block b occupies R * 128
